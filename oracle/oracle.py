@@ -1,0 +1,160 @@
+"""ctypes front end of the FP64 / exact-integer CPU oracle (oracle.c).
+
+TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the benchmark's
+CPU-baseline leg are the only callers.  The product library never imports this.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "oracle.c")
+OUT_DIR = os.path.join(HERE, "_build")
+SO = os.path.join(OUT_DIR, "liboracle.so")
+
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c with gcc (no fast-math, no FMA contraction)."""
+    os.makedirs(OUT_DIR, exist_ok=True)
+    if not force and os.path.exists(SO) and os.path.getmtime(SO) >= os.path.getmtime(SRC):
+        return SO
+    tmp = SO + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=gnu11", "-fno-fast-math", "-ffp-contract=off", "-frounding-math",
+           "-shared", "-fPIC", "-pthread", SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, SO)
+    return SO
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(SO)
+            P = ctypes.c_void_p
+            i64 = ctypes.c_int64
+            L.orc_label.argtypes = [ctypes.c_int, P, i64, ctypes.c_int, ctypes.c_int, P, P, P,
+                                    ctypes.c_int, P, ctypes.c_int]
+            L.orc_label.restype = ctypes.c_int
+            L.orc_mc_label.argtypes = [ctypes.c_int, P, i64, ctypes.c_int, P, P, ctypes.c_int,
+                                       ctypes.c_int, P]
+            L.orc_mc_label.restype = ctypes.c_int
+            L.orc_param_count.argtypes = [P, ctypes.c_int]
+            L.orc_param_count.restype = i64
+            L.orc_forward.argtypes = [P, ctypes.c_int, P, P, i64, P, ctypes.c_int]
+            L.orc_forward.restype = ctypes.c_int
+            L.orc_loss_grad.argtypes = [P, ctypes.c_int, P, P, P, i64, ctypes.c_double,
+                                        ctypes.c_double, P, P, ctypes.c_int]
+            L.orc_loss_grad.restype = ctypes.c_int
+            L.orc_adam.argtypes = [i64, P, P, P, P, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_double, ctypes.c_double, i64]
+            L.orc_adam.restype = None
+            L.orc_calibrate.argtypes = [P, P, i64, ctypes.c_double, P]
+            L.orc_calibrate.restype = i64
+            L.orc_count.argtypes = [P, P, i64, ctypes.c_double, P]
+            L.orc_count.restype = None
+            _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def _threads(nthreads):
+    return int(nthreads) if nthreads else (os.cpu_count() or 1)
+
+
+def label(kind: int, q: np.ndarray, scene, nthreads: int | None = None) -> np.ndarray:
+    """Exact labels (uint8 0/1) of ``n`` queries against ``scene`` (inputs.Scene)."""
+    q = np.ascontiguousarray(q, dtype=np.float32)
+    c = np.ascontiguousarray(scene.centres, dtype=np.float32)
+    r = np.ascontiguousarray(scene.radii, dtype=np.float32)
+    v = None if scene.vel is None else np.ascontiguousarray(scene.vel, dtype=np.float32)
+    n = q.shape[0]
+    out = np.zeros(n, dtype=np.uint8)
+    rc = lib().orc_label(int(kind), _ptr(q), n, c.shape[1], r.shape[0], _ptr(c), _ptr(r), _ptr(v),
+                         int(scene.qexp), _ptr(out), _threads(nthreads))
+    if rc != 0:
+        raise ValueError("oracle label: input off the grid, non-finite or malformed")
+    return out
+
+
+def mc_label(kind: int, q: np.ndarray, scene, density: int) -> np.ndarray:
+    """Alg. 1 labels: any() of the indicator over a lattice sample of each region."""
+    q = np.ascontiguousarray(q, dtype=np.float32)
+    c = np.ascontiguousarray(scene.centres, dtype=np.float32)
+    r = np.ascontiguousarray(scene.radii, dtype=np.float32)
+    out = np.zeros(q.shape[0], dtype=np.uint8)
+    rc = lib().orc_mc_label(int(kind), _ptr(q), q.shape[0], r.shape[0], _ptr(c), _ptr(r),
+                            int(scene.qexp), int(density), _ptr(out))
+    if rc != 0:
+        raise ValueError("oracle mc_label failed")
+    return out
+
+
+def param_count(widths) -> int:
+    w = np.ascontiguousarray(widths, dtype=np.int32)
+    return int(lib().orc_param_count(_ptr(w), len(widths) - 1))
+
+
+def forward(widths, params: np.ndarray, X: np.ndarray, nthreads: int | None = None) -> np.ndarray:
+    """FP64 logits z of the MLP on the FP32 parameters."""
+    w = np.ascontiguousarray(widths, dtype=np.int32)
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    z = np.zeros(X.shape[0], dtype=np.float64)
+    rc = lib().orc_forward(_ptr(w), len(widths) - 1, _ptr(p), _ptr(X), X.shape[0], _ptr(z),
+                           _threads(nthreads))
+    if rc != 0:
+        raise ValueError("oracle forward: bad widths")
+    return z
+
+
+def loss_grad(widths, params, X, y, alpha: float, beta: float, nthreads: int | None = None):
+    """Mean asymmetric BCE (Eq. loss) and its FP64 gradient w.r.t. the flat parameters."""
+    w = np.ascontiguousarray(widths, dtype=np.int32)
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    y = np.ascontiguousarray(np.asarray(y).astype(np.uint8))
+    g = np.zeros(p.shape[0], dtype=np.float64)
+    loss = np.zeros(1, dtype=np.float64)
+    rc = lib().orc_loss_grad(_ptr(w), len(widths) - 1, _ptr(p), _ptr(X), _ptr(y), X.shape[0],
+                             float(alpha), float(beta), _ptr(loss), _ptr(g), _threads(nthreads))
+    if rc != 0:
+        raise ValueError("oracle loss_grad failed")
+    return float(loss[0]), g
+
+
+def adam(theta, m, v, g, t: int, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam step (in place on float64 arrays theta, m, v)."""
+    for a in (theta, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    lib().orc_adam(theta.shape[0], _ptr(theta), _ptr(m), _ptr(v), _ptr(g), lr, b1, b2, eps, int(t))
+
+
+def calibrate(z, y, eps: float = 1e-5):
+    """tau = (min positive z) - eps rounded toward -inf; returns (tau, n_positive)."""
+    z = np.ascontiguousarray(z, dtype=np.float64)
+    y = np.ascontiguousarray(np.asarray(y).astype(np.uint8))
+    tau = np.zeros(1, dtype=np.float64)
+    npos = lib().orc_calibrate(_ptr(z), _ptr(y), z.shape[0], float(eps), _ptr(tau))
+    return float(tau[0]), int(npos)
+
+
+def count(z, y, tau: float) -> dict:
+    z = np.ascontiguousarray(z, dtype=np.float64)
+    y = np.ascontiguousarray(np.asarray(y).astype(np.uint8))
+    out = np.zeros(4, dtype=np.int64)
+    lib().orc_count(_ptr(z), _ptr(y), z.shape[0], float(tau), _ptr(out))
+    return {"FN": int(out[0]), "FP": int(out[1]), "TP": int(out[2]), "TN": int(out[3])}
