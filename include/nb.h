@@ -1,0 +1,172 @@
+/*
+ * nb.h -- C ABI of libnb, the GB300 (sm_103a) library for the data-parallel hot
+ * path of Neural Bounding (Liu, Fischer, Yoo, Ritschel; SIGGRAPH 2024).
+ *
+ * The paper learns a function h(r) (Sec. 3.1) that is 1 wherever the query
+ * function g(r) is 1 -- g(r) being 1 iff the region r (a point, space-time
+ * point, ray, plane or box) touches a point where the indicator f is 1 -- and
+ * may also be 1 elsewhere (false positives).  h is an MLP whose sigmoid output
+ * is rounded to {0,1} (Sec. 3.4 "Architecture"), trained with the dynamically
+ * weighted asymmetric binary cross-entropy of Eq. (loss) and Adam (Sec. 3.4
+ * "Training"), with an output epsilon added for numerics (Suppl. "Numerics").
+ *
+ * Conventions shared by every entry point:
+ *   - Pointers named q, out_bits, label_bits, opt_logits and every *_stats
+ *     argument are DEVICE pointers owned by the caller; the library never frees
+ *     them.  Host pointers are named host_*.
+ *   - stream is a cudaStream_t passed as void*; NULL means the legacy default
+ *     stream.  Calls enqueue work on it and return without synchronising,
+ *     except where a call is documented as synchronous.
+ *   - Queries are FP32, row-major, one encoding per row (widths: point2 2,
+ *     point3 3, point4t 4 = (x,y,z,t), ray3 6 = (origin, direction),
+ *     plane3 4 = (normal, offset) for {x : n.x = offset}, box3 6 =
+ *     (centre, half-extents)).
+ *   - Bit arrays hold query i in bit (i % 32) of word i / 32; the caller
+ *     provides ceil(n / 32) words.  Bits past n in the last word are written 0.
+ *   - Every call returns an nb_status.  Argument errors are detected on the
+ *     host before anything is enqueued and leave outputs untouched; the message
+ *     is available from nb_last_error() (thread-local).  Errors of earlier
+ *     asynchronous work surface as NB_ECUDA on a later call.  No call traps,
+ *     asserts or aborts on the device.
+ */
+#ifndef NB_H
+#define NB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    NB_OK = 0,
+    NB_EINVAL = 1,       /* bad argument (null pointer, size, kind, width) */
+    NB_ENOMEM = 2,       /* device or host allocation failed */
+    NB_ECUDA = 3,        /* a CUDA runtime call failed */
+    NB_ETIMEOUT = 4,     /* a bounded device wait gave up */
+    NB_ENUMERIC = 5,     /* non-finite loss; the step was not applied */
+    NB_EUNSUPPORTED = 6  /* configuration not supported by this build or device */
+} nb_status;
+
+typedef enum { NB_POINT2 = 0, NB_POINT3 = 1, NB_POINT4T = 2, NB_RAY3 = 3, NB_PLANE3 = 4, NB_BOX3 = 5 } nb_kind;
+
+typedef enum { NB_F32 = 0, NB_BF16 = 1, NB_FP8 = 2 } nb_prec;
+
+/* Indicator f of Sec. 3.1: a union of closed balls (disks when dim = 2).
+ * All values must be integer multiples of 2^-qexp with magnitude below 2^(31-qexp)
+ * (exact in FP32 and as 32-bit integers).  For NB_POINT4T the ball centre moves as
+ * c + v t, so vel must be given.  All pointers are device pointers. */
+typedef struct {
+    int32_t dim;          /* 2 or 3 */
+    int32_t n_spheres;    /* 1 .. 4096 */
+    int32_t qexp;         /* grid quantum 2^-qexp, 8 .. 24 */
+    int32_t reserved;     /* must be 0 */
+    const float *centres; /* [n_spheres][dim] */
+    const float *radii;   /* [n_spheres], >= 0 */
+    const float *vel;     /* [n_spheres][3] or NULL */
+} nb_shape;
+
+/* Device-side counters, zeroed by the call that fills them. */
+typedef struct {
+    unsigned long long n_positive; /* queries labelled 1 */
+    unsigned long long n_invalid;  /* off-grid / non-finite / out-of-range queries (labelled 1) */
+} nb_label_stats;
+
+typedef struct {
+    unsigned long long n_inside;      /* decisions "maybe inside" (bit = 1) */
+    unsigned long long n_flagged;     /* fast logit within the margin of tau: re-checked */
+    unsigned long long n_resolved_f32;/* settled by the FP32 forward with its error bound */
+    unsigned long long n_resolved_ff; /* settled by the float-float forward with its error bound */
+    unsigned long long n_unresolved;  /* still ambiguous: decided inside (conservative) */
+    unsigned long long n_nonfinite;   /* non-finite logit: decided inside and counted */
+} nb_query_stats;
+
+typedef struct {
+    float loss;                    /* mean asymmetric BCE of the batch, Eq. (loss) */
+    float reserved;
+    unsigned long long fn;         /* batch false negatives at logit >= tau */
+    unsigned long long fp;         /* batch false positives at logit >= tau */
+    unsigned long long n_nonfinite;/* samples with a non-finite logit */
+} nb_step_stats;
+
+typedef struct nb_model nb_model;
+
+/* ------------------------------------------------------------------ models */
+
+/* Create a bounding network h (Sec. 3.4 "Architecture"): widths[0] is the query
+ * encoding width, widths[1..n_layers-1] the hidden widths (ReLU), widths[n_layers]
+ * must be 1 (the logit).  Hidden widths 1..256.  infer_prec selects the nb_query
+ * fast path (NB_F32, NB_BF16: tcgen05 tensor cores, hidden widths multiple of 16
+ * and <= 256, or NB_FP8).  train_prec selects the training step (NB_F32 or NB_BF16).
+ * Parameters start at zero; load them with nb_model_set_params.  Adam uses lr 1e-3,
+ * betas (0.9, 0.999), eps 1e-8 (Sec. 3.4 "Training"); tau starts at 0, i.e. the
+ * sigmoid rounded at 1/2 (Sec. 3.4).  The device is the current CUDA device. */
+nb_status nb_model_create(const int32_t *widths, int32_t n_layers, int32_t infer_prec,
+                          int32_t train_prec, nb_model **out);
+nb_status nb_model_destroy(nb_model *m);
+int64_t nb_model_param_count(const nb_model *m);
+
+/* Flat FP32 parameters: for each layer l, W_l (widths[l+1] x widths[l], row-major)
+ * then b_l.  set_params also resets Adam's moments and step counter and refreshes
+ * the low-precision copies.  Both are synchronous. */
+nb_status nb_model_set_params(nb_model *m, const float *host_params, int64_t n_params);
+nb_status nb_model_get_params(const nb_model *m, float *host_params, int64_t n_params);
+/* Gradient of the last nb_train_step (before the Adam update); synchronous. */
+nb_status nb_model_get_grad(const nb_model *m, float *host_grad, int64_t n_params);
+
+nb_status nb_model_set_tau(nb_model *m, double tau);
+nb_status nb_model_get_tau(const nb_model *m, double *tau);
+nb_status nb_model_set_adam(nb_model *m, float lr, float beta1, float beta2, float eps);
+
+/* Checkpoint: parameters, Adam moments, step counter, tau.  Synchronous.
+ * nb_model_state_size gives the byte count for host_buf. */
+nb_status nb_model_state_size(const nb_model *m, size_t *bytes);
+nb_status nb_model_get_state(const nb_model *m, void *host_buf, size_t bytes);
+nb_status nb_model_set_state(nb_model *m, const void *host_buf, size_t bytes);
+
+/* ------------------------------------------------------------- hot path */
+
+/* Exact labels y_i = g(q_i) (Sec. 3.1; Alg. 1's Any(f(SampleRegion(r))) evaluated
+ * analytically instead of by sampling).  Inclusive of the surface.  Each query is
+ * tested against every ball in exact integer arithmetic on the 2^-qexp grid.
+ * A query that is non-finite, off the grid or out of range is labelled 1
+ * (conservative) and counted in n_invalid.  dev_stats may be NULL. */
+nb_status nb_label(const nb_shape *shape, int32_t kind, const float *q, int64_t n, uint32_t *out_bits,
+                   nb_label_stats *dev_stats, void *stream);
+
+/* One training iteration of Sec. 3.4 on a batch of n queries with labels y:
+ * forward, mean asymmetric BCE of Eq. (loss) with weights alpha (on y log yhat) and
+ * beta (on (1-y) log(1-yhat)), backward, deterministic gradient reduction and one
+ * Adam step on the FP32 master weights; the low-precision copies are refreshed.
+ * dev_stats may be NULL.  n >= 1. */
+nb_status nb_train_step(nb_model *m, const float *q, const uint32_t *label_bits, int64_t n, float alpha,
+                        float beta, nb_step_stats *dev_stats, void *stream);
+
+/* Decisions h(q_i) = [z_i >= tau] (sigmoid rounding of Sec. 3.4 shifted by the
+ * calibrated threshold).  The fast path evaluates z in the model's infer precision;
+ * every query whose fast logit lies within `margin` of tau is re-evaluated on the
+ * FP32 master weights with a rigorous error bound, then in float-float if needed,
+ * so decisions equal those of the exact real-valued network whenever the fast
+ * logit's error is below margin.  opt_logits (may be NULL) receives the fast
+ * logits.  dev_stats may be NULL.  Uses a library-owned workspace that grows on
+ * demand (a growth synchronises the device). */
+nb_status nb_query(nb_model *m, const float *q, int64_t n, float margin, uint32_t *out_bits, float *opt_logits,
+                   nb_query_stats *dev_stats, void *stream);
+
+/* Threshold calibration (Suppl. "Numerics", output epsilon): tau = (minimum over
+ * the queries labelled 1 of the network logit) - eps, rounded toward -infinity,
+ * so the calibration set has no false negative.  The minimum is located with FP32
+ * logits and rigorous bounds, and the candidates are re-evaluated in FP64.  With no
+ * positive query, tau = +infinity.  Stores tau in the model and in *host_tau.
+ * Synchronous on stream. */
+nb_status nb_calibrate(nb_model *m, const float *q, const uint32_t *label_bits, int64_t n, double eps,
+                       double *host_tau, void *stream);
+
+/* Thread-local message of the last failing call of this thread ("" if none). */
+const char *nb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NB_H */

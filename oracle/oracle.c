@@ -345,6 +345,23 @@ static void fwd_range(void *p, int64_t lo, int64_t hi, int tid) {
         c->z[i] = forward_one(c->widths, c->L, c->params, c->X + i * c->widths[0], NULL, NULL);
 }
 
+/* conditioning scale of the output logit: sum_k |W_L[k]| a_{L-1}[k] + |b_L|, the
+ * magnitude the FP32 rounding error of the last layer is relative to */
+int orc_forward_scale(const int *widths, int L, const float *params, const float *X, int64_t n,
+                      double *scale) {
+    if (L < 1 || widths[L] != 1) return -1;
+    double (*acts)[MAXW] = malloc(sizeof(double) * MAXW * (L + 1));
+    const float *W = params + layer_offset(widths, L - 1);
+    for (int64_t i = 0; i < n; i++) {
+        forward_one(widths, L, params, X + i * widths[0], acts, NULL);
+        double s = fabs((double)W[widths[L - 1]]);
+        for (int k = 0; k < widths[L - 1]; k++) s += fabs((double)W[k]) * fabs(acts[L - 1][k]);
+        scale[i] = s;
+    }
+    free(acts);
+    return 0;
+}
+
 int orc_forward(const int *widths, int L, const float *params, const float *X, int64_t n, double *z,
                 int nthreads) {
     if (L < 1 || widths[L] != 1) return -1;

@@ -52,7 +52,9 @@ def lib():
             L.orc_param_count.restype = i64
             L.orc_forward.argtypes = [P, ctypes.c_int, P, P, i64, P, ctypes.c_int]
             L.orc_forward.restype = ctypes.c_int
-            L.orc_loss_grad.argtypes = [P, ctypes.c_int, P, P, P, i64, ctypes.c_double,
+            L.orc_forward_scale.argtypes = [P, ctypes.c_int, P, P, i64, P]
+            L.orc_forward_scale.restype = ctypes.c_int
+            L.orc_loss_grad.argtypes =[P, ctypes.c_int, P, P, P, i64, ctypes.c_double,
                                         ctypes.c_double, P, P, ctypes.c_int]
             L.orc_loss_grad.restype = ctypes.c_int
             L.orc_adam.argtypes = [i64, P, P, P, P, ctypes.c_double, ctypes.c_double,
@@ -118,6 +120,18 @@ def forward(widths, params: np.ndarray, X: np.ndarray, nthreads: int | None = No
     if rc != 0:
         raise ValueError("oracle forward: bad widths")
     return z
+
+
+def forward_scale(widths, params: np.ndarray, X: np.ndarray) -> np.ndarray:
+    """sum_k |W_L[k]| a_{L-1}[k] + |b_L| per query (FP64): the scale the last layer's
+    rounding error is relative to."""
+    w = np.ascontiguousarray(widths, dtype=np.int32)
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    s = np.zeros(X.shape[0], dtype=np.float64)
+    if lib().orc_forward_scale(_ptr(w), len(widths) - 1, _ptr(p), _ptr(X), X.shape[0], _ptr(s)) != 0:
+        raise ValueError("oracle forward_scale: bad widths")
+    return s
 
 
 def loss_grad(widths, params, X, y, alpha: float, beta: float, nthreads: int | None = None):

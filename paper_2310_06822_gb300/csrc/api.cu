@@ -1,0 +1,430 @@
+// C ABI of libnb (include/nb.h): argument checking, model state, workspace and the
+// launch sequence of each hot-path call.
+#include <fenv.h>
+#include <math.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "tc.cuh"
+
+// ---------------------------------------------------------------- errors
+static thread_local std::string g_err;
+
+void nb_set_error(const std::string &msg) { g_err = msg; }
+
+nb_status nb_fail(nb_status s, const std::string &msg) {
+    g_err = msg;
+    return s;
+}
+
+nb_status nb_cuda_check(cudaError_t e, const char *what) {
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return NB_ECUDA;
+}
+
+extern "C" const char *nb_last_error(void) { return g_err.c_str(); }
+
+TauF nb_tau_bracket(double tau) {
+    TauF t;
+    if (isinf(tau)) {
+        t.dn = t.up = (float)tau;
+        return t;
+    }
+    float f = (float)tau;  // round to nearest
+    if ((double)f == tau) {
+        t.dn = t.up = f;
+    } else if ((double)f < tau) {
+        t.dn = f;
+        t.up = nextafterf(f, INFINITY);
+    } else {
+        t.up = f;
+        t.dn = nextafterf(f, -INFINITY);
+    }
+    return t;
+}
+
+// ---------------------------------------------------------------- model
+struct nb_model {
+    int device = 0;
+    int L = 0;
+    int widths[NB_MAXL + 1] = {0};
+    int off[NB_MAXL] = {0};
+    int64_t P = 0;
+    int infer_prec = NB_F32, train_prec = NB_F32;
+    float *params = nullptr, *adam_m = nullptr, *adam_v = nullptr, *grad = nullptr;
+    int64_t step = 0;
+    double tau = 0.0;
+    float lr = 1e-3f, b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    GammaTab gamma{};
+    // library-owned scratch, grown on demand
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    // low-precision weight images for the tensor-core paths
+    TcModel tc{};
+};
+
+static MlpDesc desc_of(const nb_model *m) {
+    MlpDesc d{};
+    d.L = m->L;
+    d.maxw = 0;
+    for (int l = 0; l <= m->L; l++) d.w[l] = m->widths[l];
+    for (int l = 0; l < m->L; l++) {
+        d.off[l] = m->off[l];
+        if (m->widths[l] > d.maxw) d.maxw = m->widths[l];
+    }
+    d.p = m->params;
+    return d;
+}
+
+static nb_status ensure_ws(nb_model *m, size_t bytes) {
+    if (bytes <= m->ws_bytes) return NB_OK;
+    if (m->ws) {
+        NB_CUDA(cudaDeviceSynchronize());
+        cudaFree(m->ws);
+        m->ws = nullptr;
+        m->ws_bytes = 0;
+    }
+    size_t want = bytes + bytes / 4 + 4096;
+    if (cudaMalloc(&m->ws, want) != cudaSuccess) {
+        cudaGetLastError();
+        m->ws = nullptr;
+        return nb_fail(NB_ENOMEM, "workspace allocation failed");
+    }
+    m->ws_bytes = want;
+    return NB_OK;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static int sm_count() {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
+
+static void free_model(nb_model *m) {
+    cudaFree(m->params);
+    cudaFree(m->adam_m);
+    cudaFree(m->adam_v);
+    cudaFree(m->grad);
+    cudaFree(m->ws);
+    nb_tc_free(&m->tc);
+    delete m;
+}
+
+extern "C" nb_status nb_model_create(const int32_t *widths, int32_t n_layers, int32_t infer_prec, int32_t train_prec,
+                                     nb_model **out) {
+    if (!widths || !out) return nb_fail(NB_EINVAL, "nb_model_create: null pointer");
+    *out = nullptr;
+    if (n_layers < 1 || n_layers > NB_MAXL) return nb_fail(NB_EINVAL, "nb_model_create: n_layers must be 1..8");
+    if (widths[n_layers] != 1) return nb_fail(NB_EINVAL, "nb_model_create: last width must be 1");
+    for (int l = 0; l < n_layers; l++)
+        if (widths[l] < 1 || widths[l] > NB_MAXW)
+            return nb_fail(NB_EINVAL, "nb_model_create: widths must be 1..256");
+    if (infer_prec < NB_F32 || infer_prec > NB_FP8 || train_prec < NB_F32 || train_prec > NB_BF16)
+        return nb_fail(NB_EINVAL, "nb_model_create: bad precision");
+    nb_model *m = new nb_model();
+    cudaGetDevice(&m->device);
+    m->L = n_layers;
+    for (int l = 0; l <= n_layers; l++) m->widths[l] = widths[l];
+    int64_t o = 0;
+    for (int l = 0; l < n_layers; l++) {
+        m->off[l] = (int)o;
+        o += (int64_t)widths[l + 1] * (widths[l] + 1);
+    }
+    m->P = o;
+    m->infer_prec = infer_prec;
+    m->train_prec = train_prec;
+    // gamma_k = k u / (1 - k u), u = 2^-24, with k = fan-in + 8 roundings per term; computed
+    // in double, then rounded up to float
+    for (int l = 0; l < n_layers; l++) {
+        const double u = ldexp(1.0, -24), k = widths[l] + 8.0;
+        const double gmm = k * u / (1.0 - k * u);
+        float gf = (float)gmm;
+        if ((double)gf < gmm) gf = nextafterf(gf, INFINITY);
+        m->gamma.g[l] = nextafterf(gf, INFINITY);
+    }
+    const size_t pb = (size_t)m->P * sizeof(float);
+    if (cudaMalloc(&m->params, pb) != cudaSuccess || cudaMalloc(&m->adam_m, pb) != cudaSuccess ||
+        cudaMalloc(&m->adam_v, pb) != cudaSuccess || cudaMalloc(&m->grad, pb) != cudaSuccess) {
+        cudaGetLastError();
+        free_model(m);
+        return nb_fail(NB_ENOMEM, "nb_model_create: allocation failed");
+    }
+    cudaMemset(m->params, 0, pb);
+    cudaMemset(m->adam_m, 0, pb);
+    cudaMemset(m->adam_v, 0, pb);
+    cudaMemset(m->grad, 0, pb);
+    if (infer_prec != NB_F32 || train_prec != NB_F32) {
+        nb_status s = nb_tc_init(&m->tc, desc_of(m), infer_prec, train_prec);
+        if (s != NB_OK) {
+            std::string msg = nb_last_error();
+            free_model(m);
+            return nb_fail(s, msg);
+        }
+    }
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        free_model(m);
+        return nb_fail(NB_ECUDA, "nb_model_create: device error");
+    }
+    *out = m;
+    return NB_OK;
+}
+
+extern "C" nb_status nb_model_destroy(nb_model *m) {
+    if (!m) return NB_OK;
+    cudaDeviceSynchronize();
+    free_model(m);
+    return NB_OK;
+}
+
+extern "C" int64_t nb_model_param_count(const nb_model *m) { return m ? m->P : -1; }
+
+static nb_status refresh_lowp(nb_model *m, cudaStream_t s) {
+    if (m->infer_prec == NB_F32 && m->train_prec == NB_F32) return NB_OK;
+    return nb_tc_refresh(&m->tc, desc_of(m), s);
+}
+
+extern "C" nb_status nb_model_set_params(nb_model *m, const float *host_params, int64_t n_params) {
+    if (!m || !host_params) return nb_fail(NB_EINVAL, "nb_model_set_params: null pointer");
+    if (n_params != m->P) return nb_fail(NB_EINVAL, "nb_model_set_params: wrong parameter count");
+    const size_t pb = (size_t)m->P * sizeof(float);
+    NB_CUDA(cudaMemcpy(m->params, host_params, pb, cudaMemcpyHostToDevice));
+    NB_CUDA(cudaMemset(m->adam_m, 0, pb));
+    NB_CUDA(cudaMemset(m->adam_v, 0, pb));
+    m->step = 0;
+    nb_status st = refresh_lowp(m, 0);
+    if (st != NB_OK) return st;
+    NB_CUDA(cudaDeviceSynchronize());
+    return NB_OK;
+}
+
+extern "C" nb_status nb_model_get_params(const nb_model *m, float *host_params, int64_t n_params) {
+    if (!m || !host_params) return nb_fail(NB_EINVAL, "nb_model_get_params: null pointer");
+    if (n_params != m->P) return nb_fail(NB_EINVAL, "nb_model_get_params: wrong parameter count");
+    NB_CUDA(cudaDeviceSynchronize());
+    NB_CUDA(cudaMemcpy(host_params, m->params, (size_t)m->P * sizeof(float), cudaMemcpyDeviceToHost));
+    return NB_OK;
+}
+
+extern "C" nb_status nb_model_get_grad(const nb_model *m, float *host_grad, int64_t n_params) {
+    if (!m || !host_grad) return nb_fail(NB_EINVAL, "nb_model_get_grad: null pointer");
+    if (n_params != m->P) return nb_fail(NB_EINVAL, "nb_model_get_grad: wrong parameter count");
+    NB_CUDA(cudaDeviceSynchronize());
+    NB_CUDA(cudaMemcpy(host_grad, m->grad, (size_t)m->P * sizeof(float), cudaMemcpyDeviceToHost));
+    return NB_OK;
+}
+
+extern "C" nb_status nb_model_set_tau(nb_model *m, double tau) {
+    if (!m) return nb_fail(NB_EINVAL, "nb_model_set_tau: null model");
+    if (isnan(tau)) return nb_fail(NB_EINVAL, "nb_model_set_tau: NaN");
+    m->tau = tau;
+    return NB_OK;
+}
+
+extern "C" nb_status nb_model_get_tau(const nb_model *m, double *tau) {
+    if (!m || !tau) return nb_fail(NB_EINVAL, "nb_model_get_tau: null pointer");
+    *tau = m->tau;
+    return NB_OK;
+}
+
+extern "C" nb_status nb_model_set_adam(nb_model *m, float lr, float beta1, float beta2, float eps) {
+    if (!m) return nb_fail(NB_EINVAL, "nb_model_set_adam: null model");
+    if (!(lr > 0) || !(beta1 >= 0 && beta1 < 1) || !(beta2 >= 0 && beta2 < 1) || !(eps > 0))
+        return nb_fail(NB_EINVAL, "nb_model_set_adam: bad hyper-parameter");
+    m->lr = lr;
+    m->b1 = beta1;
+    m->b2 = beta2;
+    m->eps = eps;
+    return NB_OK;
+}
+
+// checkpoint layout: magic, P, step, tau, L, widths[L+1], then params, m, v (FP32)
+static const uint64_t kMagic = 0x4e42434b50543031ull;  // "NBCKPT01"
+
+static size_t state_bytes(const nb_model *m) {
+    return 8 * 4 + 4 * (size_t)(NB_MAXL + 1) + 3 * (size_t)m->P * sizeof(float);
+}
+
+extern "C" nb_status nb_model_state_size(const nb_model *m, size_t *bytes) {
+    if (!m || !bytes) return nb_fail(NB_EINVAL, "nb_model_state_size: null pointer");
+    *bytes = state_bytes(m);
+    return NB_OK;
+}
+
+extern "C" nb_status nb_model_get_state(const nb_model *m, void *host_buf, size_t bytes) {
+    if (!m || !host_buf) return nb_fail(NB_EINVAL, "nb_model_get_state: null pointer");
+    if (bytes < state_bytes(m)) return nb_fail(NB_EINVAL, "nb_model_get_state: buffer too small");
+    NB_CUDA(cudaDeviceSynchronize());
+    char *p = (char *)host_buf;
+    uint64_t hdr[4] = {kMagic, (uint64_t)m->P, (uint64_t)m->step, 0};
+    memcpy(&hdr[3], &m->tau, 8);
+    memcpy(p, hdr, 32);
+    int32_t w[NB_MAXL + 1] = {0};
+    for (int l = 0; l <= m->L; l++) w[l] = m->widths[l];
+    memcpy(p + 32, w, sizeof(w));
+    char *q = p + 32 + sizeof(w);
+    const size_t pb = (size_t)m->P * sizeof(float);
+    NB_CUDA(cudaMemcpy(q, m->params, pb, cudaMemcpyDeviceToHost));
+    NB_CUDA(cudaMemcpy(q + pb, m->adam_m, pb, cudaMemcpyDeviceToHost));
+    NB_CUDA(cudaMemcpy(q + 2 * pb, m->adam_v, pb, cudaMemcpyDeviceToHost));
+    return NB_OK;
+}
+
+extern "C" nb_status nb_model_set_state(nb_model *m, const void *host_buf, size_t bytes) {
+    if (!m || !host_buf) return nb_fail(NB_EINVAL, "nb_model_set_state: null pointer");
+    if (bytes < state_bytes(m)) return nb_fail(NB_EINVAL, "nb_model_set_state: buffer too small");
+    const char *p = (const char *)host_buf;
+    uint64_t hdr[4];
+    memcpy(hdr, p, 32);
+    if (hdr[0] != kMagic || hdr[1] != (uint64_t)m->P) return nb_fail(NB_EINVAL, "nb_model_set_state: not a checkpoint of this network");
+    int32_t w[NB_MAXL + 1];
+    memcpy(w, p + 32, sizeof(w));
+    for (int l = 0; l <= m->L; l++)
+        if (w[l] != m->widths[l]) return nb_fail(NB_EINVAL, "nb_model_set_state: widths differ");
+    const char *q = p + 32 + sizeof(w);
+    const size_t pb = (size_t)m->P * sizeof(float);
+    NB_CUDA(cudaDeviceSynchronize());
+    NB_CUDA(cudaMemcpy(m->params, q, pb, cudaMemcpyHostToDevice));
+    NB_CUDA(cudaMemcpy(m->adam_m, q + pb, pb, cudaMemcpyHostToDevice));
+    NB_CUDA(cudaMemcpy(m->adam_v, q + 2 * pb, pb, cudaMemcpyHostToDevice));
+    m->step = (int64_t)hdr[2];
+    memcpy(&m->tau, &hdr[3], 8);
+    nb_status st = refresh_lowp(m, 0);
+    if (st != NB_OK) return st;
+    NB_CUDA(cudaDeviceSynchronize());
+    return NB_OK;
+}
+
+// ---------------------------------------------------------------- hot path
+static const int kEncW[6] = {2, 3, 4, 6, 4, 6};
+
+extern "C" nb_status nb_label(const nb_shape *shape, int32_t kind, const float *q, int64_t n, uint32_t *out_bits,
+                              nb_label_stats *dev_stats, void *stream) {
+    if (!shape) return nb_fail(NB_EINVAL, "nb_label: null shape");
+    if (kind < 0 || kind > 5) return nb_fail(NB_EINVAL, "nb_label: unknown kind");
+    if (n < 0) return nb_fail(NB_EINVAL, "nb_label: negative n");
+    if (n > 0 && (!q || !out_bits)) return nb_fail(NB_EINVAL, "nb_label: null query or output pointer");
+    if (shape->dim != 2 && shape->dim != 3) return nb_fail(NB_EINVAL, "nb_label: dim must be 2 or 3");
+    if ((kind == NB_POINT2) != (shape->dim == 2)) return nb_fail(NB_EINVAL, "nb_label: kind does not match the shape's dim");
+    if (shape->n_spheres < 1 || shape->n_spheres > 4096) return nb_fail(NB_EINVAL, "nb_label: n_spheres must be 1..4096");
+    if (shape->qexp < 8 || shape->qexp > 24) return nb_fail(NB_EINVAL, "nb_label: qexp must be 8..24");
+    if (shape->reserved != 0) return nb_fail(NB_EINVAL, "nb_label: reserved field must be 0");
+    if (!shape->centres || !shape->radii) return nb_fail(NB_EINVAL, "nb_label: null sphere arrays");
+    if (kind == NB_POINT4T && !shape->vel) return nb_fail(NB_EINVAL, "nb_label: point4t needs velocities");
+    (void)kEncW;
+    return nb_launch_label(shape, kind, q, n, out_bits, dev_stats, (cudaStream_t)stream);
+}
+
+extern "C" nb_status nb_train_step(nb_model *m, const float *q, const uint32_t *label_bits, int64_t n, float alpha,
+                                   float beta, nb_step_stats *dev_stats, void *stream) {
+    if (!m) return nb_fail(NB_EINVAL, "nb_train_step: null model");
+    if (n < 1) return nb_fail(NB_EINVAL, "nb_train_step: n must be >= 1");
+    if (!q || !label_bits) return nb_fail(NB_EINVAL, "nb_train_step: null pointer");
+    if (!(alpha >= 0) || !(beta >= 0) || isinf(alpha) || isinf(beta))
+        return nb_fail(NB_EINVAL, "nb_train_step: alpha and beta must be finite and >= 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    const MlpDesc d = desc_of(m);
+    const TauF tau = nb_tau_bracket(m->tau);
+    m->step += 1;
+    const double c1 = 1.0 - pow((double)m->b1, (double)m->step);
+    const double c2 = 1.0 - pow((double)m->b2, (double)m->step);
+    if (m->train_prec == NB_BF16) {
+        nb_status st = nb_tc_train_step(&m->tc, d, q, label_bits, n, alpha, beta, tau, m->params, m->adam_m,
+                                        m->adam_v, m->grad, m->lr, m->b1, m->b2, m->eps, (float)c1,
+                                        (float)sqrt(c2), dev_stats, s);
+        if (st != NB_OK) return st;
+        return refresh_lowp(m, s);
+    }
+    TrainWs tw{};
+    tw.G = nb_train_f32_ctas(d, n, sm_count());
+    const size_t need = align256((size_t)tw.G * m->P * sizeof(float)) + align256((size_t)tw.G * sizeof(float));
+    nb_status st = ensure_ws(m, need);
+    if (st != NB_OK) return st;
+    tw.partial = (float *)m->ws;
+    tw.loss_partial = (float *)((char *)m->ws + align256((size_t)tw.G * m->P * sizeof(float)));
+    st = nb_launch_train_f32(d, q, label_bits, n, alpha, beta, tau, tw, dev_stats, s);
+    if (st != NB_OK) return st;
+    st = nb_launch_adam(m->P, 1.0f / (float)n, m->params, m->adam_m, m->adam_v, m->grad, tw, m->lr, m->b1, m->b2,
+                        m->eps, (float)c1, (float)sqrt(c2), dev_stats, s);
+    if (st != NB_OK) return st;
+    return refresh_lowp(m, s);
+}
+
+extern "C" nb_status nb_query(nb_model *m, const float *q, int64_t n, float margin, uint32_t *out_bits,
+                              float *opt_logits, nb_query_stats *dev_stats, void *stream) {
+    if (!m) return nb_fail(NB_EINVAL, "nb_query: null model");
+    if (n < 0 || n >= (int64_t)1 << 32) return nb_fail(NB_EINVAL, "nb_query: n must be in [0, 2^32)");
+    if (n > 0 && (!q || !out_bits)) return nb_fail(NB_EINVAL, "nb_query: null pointer");
+    if (!(margin >= 0) || isinf(margin)) return nb_fail(NB_EINVAL, "nb_query: margin must be finite and >= 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (dev_stats) NB_CUDA(cudaMemsetAsync(dev_stats, 0, sizeof(nb_query_stats), s));
+    if (n == 0) return NB_OK;
+    nb_status st = ensure_ws(m, align256(sizeof(unsigned)) + align256((size_t)n * sizeof(unsigned)));
+    if (st != NB_OK) return st;
+    QueryWs ws;
+    ws.flag_count = (unsigned *)m->ws;
+    ws.flag_idx = (unsigned *)((char *)m->ws + align256(sizeof(unsigned)));
+    NB_CUDA(cudaMemsetAsync(ws.flag_count, 0, sizeof(unsigned), s));
+    const MlpDesc d = desc_of(m);
+    const TauF tau = nb_tau_bracket(m->tau);
+    if (m->infer_prec == NB_F32)
+        st = nb_launch_fwd_f32(d, q, n, tau, margin, out_bits, opt_logits, dev_stats, ws, s);
+    else
+        st = nb_tc_query(&m->tc, d, q, n, tau, margin, out_bits, opt_logits, dev_stats, ws, s);
+    if (st != NB_OK) return st;
+    return nb_launch_recheck(d, m->gamma, q, tau, out_bits, dev_stats, ws, n, s);
+}
+
+extern "C" nb_status nb_calibrate(nb_model *m, const float *q, const uint32_t *label_bits, int64_t n, double eps,
+                                  double *host_tau, void *stream) {
+    if (!m || !host_tau) return nb_fail(NB_EINVAL, "nb_calibrate: null pointer");
+    if (n < 0) return nb_fail(NB_EINVAL, "nb_calibrate: negative n");
+    if (n > 0 && (!q || !label_bits)) return nb_fail(NB_EINVAL, "nb_calibrate: null pointer");
+    if (!(eps >= 0) || isinf(eps)) return nb_fail(NB_EINVAL, "nb_calibrate: eps must be finite and >= 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n == 0) {
+        m->tau = INFINITY;
+        *host_tau = m->tau;
+        return NB_OK;
+    }
+    const size_t head = 256;
+    nb_status st = ensure_ws(m, head + align256((size_t)n * sizeof(float)));
+    if (st != NB_OK) return st;
+    CalibWs ws;
+    ws.umin_bits = (unsigned *)m->ws;
+    ws.zmin_bits = (unsigned long long *)((char *)m->ws + 64);
+    ws.npos = (unsigned long long *)((char *)m->ws + 128);
+    ws.lo = (float *)((char *)m->ws + head);
+    st = nb_launch_calibrate(desc_of(m), m->gamma, q, label_bits, n, ws, s);
+    if (st != NB_OK) return st;
+    unsigned long long h[2];
+    NB_CUDA(cudaMemcpyAsync(&h[0], ws.zmin_bits, 8, cudaMemcpyDeviceToHost, s));
+    NB_CUDA(cudaMemcpyAsync(&h[1], ws.npos, 8, cudaMemcpyDeviceToHost, s));
+    NB_CUDA(cudaStreamSynchronize(s));
+    double tau;
+    if (h[1] == 0) {
+        tau = INFINITY;
+    } else if (h[0] == 0ull) {
+        tau = -INFINITY;  // a positive query had a NaN logit: everything is inside
+    } else {
+        const unsigned long long u = (h[0] & 0x8000000000000000ull) ? (h[0] & 0x7fffffffffffffffull) : ~h[0];
+        double zmin;
+        memcpy(&zmin, &u, 8);
+        // tau = zmin - eps rounded toward -infinity; volatile operands keep the
+        // subtraction between the two rounding-mode switches
+        volatile double va = zmin, vb = eps;
+        const int old = fegetround();
+        fesetround(FE_DOWNWARD);
+        volatile double t = va - vb;
+        fesetround(old);
+        tau = t;
+    }
+    m->tau = tau;
+    *host_tau = tau;
+    return NB_OK;
+}

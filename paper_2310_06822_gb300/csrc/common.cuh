@@ -1,0 +1,82 @@
+// Internal definitions shared by the libnb translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "nb.h"
+
+#define NB_MAXL 8          // maximum number of layers (weight matrices)
+#define NB_MAXW 256        // maximum hidden width
+
+// ---------------------------------------------------------------- errors
+void nb_set_error(const std::string &msg);
+nb_status nb_fail(nb_status s, const std::string &msg);
+nb_status nb_cuda_check(cudaError_t e, const char *what);
+
+#define NB_CUDA(call)                                              \
+    do {                                                           \
+        cudaError_t _e = (call);                                   \
+        if (_e != cudaSuccess) return nb_cuda_check(_e, #call);    \
+    } while (0)
+
+// ---------------------------------------------------------------- network description
+// Plain-old-data view of an MLP passed by value to kernels.
+struct MlpDesc {
+    int L;                   // number of weight layers; widths w[0..L], w[L] == 1
+    int w[NB_MAXL + 1];
+    int off[NB_MAXL];        // offset of W_l in the flat parameter array; b_l follows W_l
+    int maxw;                // max(w[0..L-1])
+    const float *p;          // device FP32 master parameters
+};
+
+// Unit roundoff gammas gamma_k = k u / (1 - k u), u = 2^-24, rounded up, one per layer
+// (k = fan-in + 1), used by the rigorous FP32 error bounds.
+struct GammaTab {
+    float g[NB_MAXL];
+};
+
+struct nb_model_impl;
+
+// tau bracketed by two floats: tau_dn <= tau <= tau_up, equal when tau is a float.
+struct TauF {
+    float dn, up;
+};
+TauF nb_tau_bracket(double tau);
+
+// ---------------------------------------------------------------- launchers (per .cu)
+nb_status nb_launch_label(const nb_shape *shape, int kind, const float *q, int64_t n, uint32_t *bits,
+                          nb_label_stats *st, cudaStream_t s);
+
+struct QueryWs {
+    unsigned int *flag_count;   // [1]
+    unsigned int *flag_idx;     // [n]
+};
+
+nb_status nb_launch_fwd_f32(const MlpDesc &d, const float *q, int64_t n, TauF tau, float margin,
+                            uint32_t *bits, float *logits, nb_query_stats *st, QueryWs ws, cudaStream_t s);
+nb_status nb_launch_recheck(const MlpDesc &d, const GammaTab &gt, const float *q, TauF tau, uint32_t *bits,
+                            nb_query_stats *st, QueryWs ws, int64_t n, cudaStream_t s);
+
+struct CalibWs {
+    unsigned int *umin_bits;          // [1] order-preserving bits of min upper bound
+    unsigned long long *zmin_bits;    // [1] order-preserving bits of min FP64 logit
+    unsigned long long *npos;         // [1]
+    float *lo;                        // [n] lower bounds (positives) / +inf
+};
+nb_status nb_launch_calibrate(const MlpDesc &d, const GammaTab &gt, const float *q, const uint32_t *labels,
+                              int64_t n, CalibWs ws, cudaStream_t s);
+
+struct TrainWs {
+    float *partial;          // [G][P] per-CTA gradient partials
+    float *loss_partial;     // [G]
+    int G;                   // CTAs used
+};
+int nb_train_f32_ctas(const MlpDesc &d, int64_t n, int num_sms);
+nb_status nb_launch_train_f32(const MlpDesc &d, const float *q, const uint32_t *labels, int64_t n, float alpha,
+                              float beta, TauF tau, TrainWs ws, nb_step_stats *st, cudaStream_t s);
+nb_status nb_launch_adam(int64_t P, float inv_n, float *params, float *m, float *v, float *grad,
+                         TrainWs ws, float lr, float b1, float b2, float eps, float c1, float sqrt_c2,
+                         nb_step_stats *st, cudaStream_t s);

@@ -1,0 +1,24 @@
+// Tensor-core (tcgen05 / TMEM) paths: BF16 and FP8 forward, BF16 training step.
+#pragma once
+
+#include "common.cuh"
+
+// Low-precision weight images and their launch state, owned by a model.
+struct TcModel {
+    int infer_prec = 0, train_prec = 0;
+    void *img = nullptr;     // device: packed operand images of every layer
+    size_t img_bytes = 0;
+    float *scales = nullptr; // device: per-layer dequantisation scales (FP8)
+    void *train_ws = nullptr;
+    size_t train_ws_bytes = 0;
+};
+
+nb_status nb_tc_init(TcModel *tc, const MlpDesc &d, int infer_prec, int train_prec);
+void nb_tc_free(TcModel *tc);
+nb_status nb_tc_refresh(TcModel *tc, const MlpDesc &d, cudaStream_t s);
+nb_status nb_tc_query(TcModel *tc, const MlpDesc &d, const float *q, int64_t n, TauF tau, float margin,
+                      uint32_t *bits, float *logits, nb_query_stats *st, QueryWs ws, cudaStream_t s);
+nb_status nb_tc_train_step(TcModel *tc, const MlpDesc &d, const float *q, const uint32_t *labels, int64_t n,
+                           float alpha, float beta, TauF tau, float *params, float *m, float *v, float *grad,
+                           float lr, float b1, float b2, float eps, float c1, float sqrt_c2, nb_step_stats *st,
+                           cudaStream_t s);

@@ -1,0 +1,261 @@
+"""Thin ctypes binding of libnb (include/nb.h) over PyTorch device tensors.
+
+Argument marshalling only: every step of the hot path runs in libnb's CUDA kernels.
+PyTorch provides device memory and the current stream.  There is no CPU fallback:
+if libnb.so cannot be loaded the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+import torch
+
+from . import build as _build
+from .inputs import ENC_WIDTH, POINT2, POINT4T
+
+NB_F32, NB_BF16, NB_FP8 = 0, 1, 2
+PREC = {"f32": NB_F32, "bf16": NB_BF16, "fp8": NB_FP8}
+STATUS = {0: "NB_OK", 1: "NB_EINVAL", 2: "NB_ENOMEM", 3: "NB_ECUDA", 4: "NB_ETIMEOUT", 5: "NB_ENUMERIC",
+          6: "NB_EUNSUPPORTED"}
+
+# every symbol include/nb.h declares
+EXPORTS = ["nb_model_create", "nb_model_destroy", "nb_model_param_count", "nb_model_set_params",
+           "nb_model_get_params", "nb_model_get_grad", "nb_model_set_tau", "nb_model_get_tau",
+           "nb_model_set_adam", "nb_model_state_size", "nb_model_get_state", "nb_model_set_state",
+           "nb_label", "nb_train_step", "nb_query", "nb_calibrate", "nb_last_error"]
+
+
+class NBError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Shape(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("n_spheres", ctypes.c_int32), ("qexp", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("centres", ctypes.c_void_p), ("radii", ctypes.c_void_p),
+                ("vel", ctypes.c_void_p)]
+
+
+LABEL_STATS = np.dtype([("n_positive", "<u8"), ("n_invalid", "<u8")])
+QUERY_STATS = np.dtype([("n_inside", "<u8"), ("n_flagged", "<u8"), ("n_resolved_f32", "<u8"),
+                        ("n_resolved_ff", "<u8"), ("n_unresolved", "<u8"), ("n_nonfinite", "<u8")])
+STEP_STATS = np.dtype([("loss", "<f4"), ("reserved", "<f4"), ("fn", "<u8"), ("fp", "<u8"),
+                       ("n_nonfinite", "<u8")])
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """Load libnb.so (building it in-tree first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if _build._stale():
+                path = _build.build()
+            if not os.path.exists(path):
+                raise RuntimeError("libnb.so is not built; run paper_2310_06822_gb300/build.py")
+            L = ctypes.CDLL(path)
+            P, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+            st = ctypes.c_int
+            sig = {
+                "nb_model_create": ([P, i32, i32, i32, P], st),
+                "nb_model_destroy": ([P], st),
+                "nb_model_param_count": ([P], i64),
+                "nb_model_set_params": ([P, P, i64], st),
+                "nb_model_get_params": ([P, P, i64], st),
+                "nb_model_get_grad": ([P, P, i64], st),
+                "nb_model_set_tau": ([P, ctypes.c_double], st),
+                "nb_model_get_tau": ([P, P], st),
+                "nb_model_set_adam": ([P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float], st),
+                "nb_model_state_size": ([P, P], st),
+                "nb_model_get_state": ([P, P, ctypes.c_size_t], st),
+                "nb_model_set_state": ([P, P, ctypes.c_size_t], st),
+                "nb_label": ([P, i32, P, i64, P, P, P], st),
+                "nb_train_step": ([P, P, P, i64, ctypes.c_float, ctypes.c_float, P, P], st),
+                "nb_query": ([P, P, i64, ctypes.c_float, P, P, P, P], st),
+                "nb_calibrate": ([P, P, P, i64, ctypes.c_double, P, P], st),
+                "nb_last_error": ([], ctypes.c_char_p),
+            }
+            for name, (args, res) in sig.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != 0:
+        msg = lib().nb_last_error()
+        raise NBError(rc, msg.decode() if msg else "")
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _dev(x, dtype, device="cuda"):
+    if isinstance(x, torch.Tensor):
+        t = x.to(device=device, dtype=dtype)
+    else:
+        t = torch.as_tensor(np.ascontiguousarray(x), dtype=dtype, device=device)
+    return t.contiguous()
+
+
+def n_words(n: int) -> int:
+    return (n + 31) // 32
+
+
+def _read(t: torch.Tensor, dt: np.dtype) -> dict:
+    a = np.frombuffer(t.cpu().numpy().tobytes(), dtype=dt)[0]
+    return {k: (float(a[k]) if a[k].dtype.kind == "f" else int(a[k])) for k in dt.names if k != "reserved"}
+
+
+class Shape:
+    """A union of spheres resident on the device (nb_shape)."""
+
+    def __init__(self, scene, device="cuda"):
+        self.scene = scene
+        self.centres = _dev(scene.centres, torch.float32, device)
+        self.radii = _dev(scene.radii, torch.float32, device)
+        self.vel = None if scene.vel is None else _dev(scene.vel, torch.float32, device)
+        self._s = _Shape(scene.dim, scene.n_spheres, scene.qexp, 0, self.centres.data_ptr(),
+                         self.radii.data_ptr(), self.vel.data_ptr() if self.vel is not None else None)
+
+
+def label(shape: Shape, kind: int, q: torch.Tensor, out: torch.Tensor | None = None, stats: bool = False,
+          stream=None):
+    """Exact labels of n queries (packed bits, int32 words) via nb_label."""
+    n = q.shape[0]
+    if out is None:
+        out = torch.empty(n_words(n), dtype=torch.int32, device=q.device)
+    st = torch.empty(LABEL_STATS.itemsize, dtype=torch.uint8, device=q.device) if stats else None
+    _check(lib().nb_label(ctypes.byref(shape._s), int(kind), _ptr(q), n, _ptr(out), _ptr(st), _stream(stream)))
+    if stats:
+        return out, _read(st, LABEL_STATS)
+    return out
+
+
+class Model:
+    """A bounding network h (nb_model)."""
+
+    def __init__(self, widths, infer_prec="f32", train_prec="f32"):
+        self.widths = [int(w) for w in widths]
+        self.infer_prec = PREC[infer_prec] if isinstance(infer_prec, str) else int(infer_prec)
+        self.train_prec = PREC[train_prec] if isinstance(train_prec, str) else int(train_prec)
+        w = (ctypes.c_int32 * len(self.widths))(*self.widths)
+        h = ctypes.c_void_p()
+        _check(lib().nb_model_create(w, len(self.widths) - 1, self.infer_prec, self.train_prec, ctypes.byref(h)))
+        self._h = h
+        self.P = int(lib().nb_model_param_count(h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().nb_model_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- state
+    def set_params(self, p):
+        p = np.ascontiguousarray(np.asarray(p, dtype=np.float32))
+        _check(lib().nb_model_set_params(self._h, p.ctypes.data_as(ctypes.c_void_p), p.size))
+
+    def get_params(self) -> np.ndarray:
+        p = np.zeros(self.P, dtype=np.float32)
+        _check(lib().nb_model_get_params(self._h, p.ctypes.data_as(ctypes.c_void_p), self.P))
+        return p
+
+    def get_grad(self) -> np.ndarray:
+        g = np.zeros(self.P, dtype=np.float32)
+        _check(lib().nb_model_get_grad(self._h, g.ctypes.data_as(ctypes.c_void_p), self.P))
+        return g
+
+    @property
+    def tau(self) -> float:
+        t = ctypes.c_double()
+        _check(lib().nb_model_get_tau(self._h, ctypes.byref(t)))
+        return t.value
+
+    @tau.setter
+    def tau(self, v: float):
+        _check(lib().nb_model_set_tau(self._h, float(v)))
+
+    def set_adam(self, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+        _check(lib().nb_model_set_adam(self._h, lr, b1, b2, eps))
+
+    def get_state(self) -> bytes:
+        n = ctypes.c_size_t()
+        _check(lib().nb_model_state_size(self._h, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        _check(lib().nb_model_get_state(self._h, buf, n.value))
+        return buf.raw
+
+    def set_state(self, b: bytes):
+        buf = ctypes.create_string_buffer(b, len(b))
+        _check(lib().nb_model_set_state(self._h, buf, len(b)))
+
+    # -- hot path
+    def train_step(self, q, label_bits, alpha: float, beta: float = 1.0, stats=None, stream=None):
+        """One fused training iteration; stats (a uint8 device tensor of 32 bytes) optional."""
+        _check(lib().nb_train_step(self._h, _ptr(q), _ptr(label_bits), q.shape[0], float(alpha), float(beta),
+                                   _ptr(stats), _stream(stream)))
+
+    def query(self, q, margin: float = 0.0, out=None, logits: bool = False, stats: bool = False, stream=None):
+        n = q.shape[0]
+        if out is None:
+            out = torch.empty(n_words(n), dtype=torch.int32, device=q.device)
+        lg = torch.empty(n, dtype=torch.float32, device=q.device) if logits else None
+        st = torch.empty(QUERY_STATS.itemsize, dtype=torch.uint8, device=q.device) if stats else None
+        _check(lib().nb_query(self._h, _ptr(q), n, float(margin), _ptr(out), _ptr(lg), _ptr(st), _stream(stream)))
+        res = [out]
+        if logits:
+            res.append(lg)
+        if stats:
+            res.append(_read(st, QUERY_STATS))
+        return res[0] if len(res) == 1 else tuple(res)
+
+    def calibrate(self, q, label_bits, eps: float = 1e-5, stream=None) -> float:
+        t = ctypes.c_double()
+        _check(lib().nb_calibrate(self._h, _ptr(q), _ptr(label_bits), q.shape[0], float(eps), ctypes.byref(t),
+                                  _stream(stream)))
+        return t.value
+
+
+def step_stats_tensor(device="cuda") -> torch.Tensor:
+    return torch.zeros(STEP_STATS.itemsize, dtype=torch.uint8, device=device)
+
+
+def read_step_stats(t: torch.Tensor) -> dict:
+    return _read(t, STEP_STATS)
+
+
+def bits_to_numpy(words: torch.Tensor, n: int) -> np.ndarray:
+    from .inputs import unpack_bits
+    return unpack_bits(words.cpu().numpy().view(np.uint32), n)
+
+
+def numpy_bits_to_device(words: np.ndarray, device="cuda") -> torch.Tensor:
+    return torch.as_tensor(np.ascontiguousarray(words).view(np.int32), device=device)
+
+
+def enc_width(kind: int) -> int:
+    return ENC_WIDTH[kind]
+
+
+__all__ = ["Model", "Shape", "label", "lib", "NBError", "EXPORTS", "POINT2", "POINT4T"]

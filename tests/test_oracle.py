@@ -397,3 +397,27 @@ def test_count_cost_table():
     z = np.array([-1.0, 0.0, 2.0, 3.0, -5.0])
     y = np.array([1, 0, 1, 0, 0], dtype=np.uint8)
     assert O.count(z, y, 0.0) == {"FN": 1, "FP": 2, "TP": 1, "TN": 1}
+
+
+def test_forward_scale_definition():
+    # one layer: scale = sum |w| |x| + |b|
+    w = [2, 1]
+    p = np.array([0.5, -2.0, 0.25], dtype=np.float32)
+    X = np.array([[1.0, 1.0], [-4.0, 0.5]], dtype=np.float32)
+    assert O.forward_scale(w, p, X).tolist() == [2.75, 3.25]
+    # hidden layers: |W_L| . relu(...) + |b_L|, against the autograd forward
+    import torch
+    w = [3, 8, 8, 1]
+    p = I.init_params(31, w)
+    X = I.sample_queries("point3", 32, 50)
+    pt, _ = _torch_mlp_f64(w, p, X)
+    a = torch.tensor(X.astype(np.float64))
+    off = 0
+    for l in range(2):
+        fi, fo = w[l], w[l + 1]
+        W = pt[off:off + fo * fi].view(fo, fi)
+        off += fo * fi
+        a = torch.relu(a @ W.T + pt[off:off + fo])
+        off += fo
+    s = (a @ pt[off:off + 8].abs().detach() + pt[off + 8].abs()).detach().numpy()
+    np.testing.assert_allclose(O.forward_scale(w, p, X), s, rtol=1e-12)
