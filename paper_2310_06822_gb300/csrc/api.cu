@@ -28,11 +28,18 @@ nb_status nb_cuda_check(cudaError_t e, const char *what) {
 extern "C" const char *nb_last_error(void) { return g_err.c_str(); }
 
 TauF nb_tau_bracket(double tau) {
-    TauF t;
+    TauF t{};
     if (isinf(tau)) {
-        t.dn = t.up = (float)tau;
+        t.dn = t.up = t.hi = (float)tau;
         return t;
     }
+    // split tau = hi + lo + r: hi - tau is exact in double (Sterbenz), |r| <= err
+    t.hi = (float)tau;
+    const double r1 = tau - (double)t.hi;
+    t.lo = (float)r1;
+    const double r2 = fabs(r1 - (double)t.lo);
+    t.err = (float)r2;
+    if ((double)t.err < r2) t.err = nextafterf(t.err, INFINITY);
     float f = (float)tau;  // round to nearest
     if ((double)f == tau) {
         t.dn = t.up = f;
@@ -147,6 +154,12 @@ extern "C" nb_status nb_model_create(const int32_t *widths, int32_t n_layers, in
         float gf = (float)gmm;
         if ((double)gf < gmm) gf = nextafterf(gf, INFINITY);
         m->gamma.g[l] = nextafterf(gf, INFINITY);
+        // float-float stage: gamma_{3K+3} (K + 3) u
+        const double k3 = 3.0 * widths[l] + 3.0;
+        const double cff = k3 * u / (1.0 - k3 * u) * (widths[l] + 3.0) * u;
+        float cf = (float)cff;
+        if ((double)cf < cff) cf = nextafterf(cf, INFINITY);
+        m->gamma.gff[l] = nextafterf(cf, INFINITY);
     }
     const size_t pb = (size_t)m->P * sizeof(float);
     if (cudaMalloc(&m->params, pb) != cudaSuccess || cudaMalloc(&m->adam_m, pb) != cudaSuccess ||
@@ -364,11 +377,14 @@ extern "C" nb_status nb_query(nb_model *m, const float *q, int64_t n, float marg
     cudaStream_t s = (cudaStream_t)stream;
     if (dev_stats) NB_CUDA(cudaMemsetAsync(dev_stats, 0, sizeof(nb_query_stats), s));
     if (n == 0) return NB_OK;
-    nb_status st = ensure_ws(m, align256(sizeof(unsigned)) + align256((size_t)n * sizeof(unsigned)));
+    const size_t list = align256((size_t)n * sizeof(unsigned));
+    nb_status st = ensure_ws(m, 256 + 2 * list);
     if (st != NB_OK) return st;
     QueryWs ws;
     ws.flag_count = (unsigned *)m->ws;
-    ws.flag_idx = (unsigned *)((char *)m->ws + align256(sizeof(unsigned)));
+    ws.ff_count = (unsigned *)((char *)m->ws + 64);
+    ws.flag_idx = (unsigned *)((char *)m->ws + 256);
+    ws.ff_idx = (unsigned *)((char *)m->ws + 256 + list);
     NB_CUDA(cudaMemsetAsync(ws.flag_count, 0, sizeof(unsigned), s));
     const MlpDesc d = desc_of(m);
     const TauF tau = nb_tau_bracket(m->tau);
@@ -383,7 +399,7 @@ extern "C" nb_status nb_query(nb_model *m, const float *q, int64_t n, float marg
 extern "C" nb_status nb_calibrate(nb_model *m, const float *q, const uint32_t *label_bits, int64_t n, double eps,
                                   double *host_tau, void *stream) {
     if (!m || !host_tau) return nb_fail(NB_EINVAL, "nb_calibrate: null pointer");
-    if (n < 0) return nb_fail(NB_EINVAL, "nb_calibrate: negative n");
+    if (n < 0 || n >= (int64_t)1 << 32) return nb_fail(NB_EINVAL, "nb_calibrate: n must be in [0, 2^32)");
     if (n > 0 && (!q || !label_bits)) return nb_fail(NB_EINVAL, "nb_calibrate: null pointer");
     if (!(eps >= 0) || isinf(eps)) return nb_fail(NB_EINVAL, "nb_calibrate: eps must be finite and >= 0");
     cudaStream_t s = (cudaStream_t)stream;
@@ -392,20 +408,23 @@ extern "C" nb_status nb_calibrate(nb_model *m, const float *q, const uint32_t *l
         *host_tau = m->tau;
         return NB_OK;
     }
-    const size_t head = 256;
-    nb_status st = ensure_ws(m, head + align256((size_t)n * sizeof(float)));
+    const size_t head = 256, list = align256((size_t)n * sizeof(unsigned));
+    nb_status st = ensure_ws(m, head + 2 * list);
     if (st != NB_OK) return st;
     CalibWs ws;
     ws.umin_bits = (unsigned *)m->ws;
     ws.zmin_bits = (unsigned long long *)((char *)m->ws + 64);
-    ws.npos = (unsigned long long *)((char *)m->ws + 128);
-    ws.lo = (float *)((char *)m->ws + head);
+    ws.npos = (unsigned *)((char *)m->ws + 128);
+    ws.pos_idx = (unsigned *)((char *)m->ws + head);
+    ws.lo = (float *)((char *)m->ws + head + list);
     st = nb_launch_calibrate(desc_of(m), m->gamma, q, label_bits, n, ws, s);
     if (st != NB_OK) return st;
-    unsigned long long h[2];
+    unsigned long long h[2] = {0, 0};
+    unsigned npos = 0;
     NB_CUDA(cudaMemcpyAsync(&h[0], ws.zmin_bits, 8, cudaMemcpyDeviceToHost, s));
-    NB_CUDA(cudaMemcpyAsync(&h[1], ws.npos, 8, cudaMemcpyDeviceToHost, s));
+    NB_CUDA(cudaMemcpyAsync(&npos, ws.npos, 4, cudaMemcpyDeviceToHost, s));
     NB_CUDA(cudaStreamSynchronize(s));
+    h[1] = npos;
     double tau;
     if (h[1] == 0) {
         tau = INFINITY;

@@ -1,0 +1,470 @@
+// Rigorous evaluation of the decision z >= tau for the queries the fast path could not
+// settle (fast logit within the margin of tau), and the bound pass of the threshold
+// calibration (Suppl. "Numerics": output epsilon; the calibrated threshold keeps the
+// calibration set free of false negatives).
+//
+// Stage 1 (bound_tile_kernel): FP32 forward over tiles of listed queries carrying,
+// for every neuron, a bound B >= |computed - exact| on the distance of the computed
+// value to the exact real-valued network output on the same input:
+//     B_n = gamma_l |b_n| + sum_k |W_nk| (gamma_l |a^_k| + e_k),
+// gamma_l = gamma_{fan-in + 8} covering the rounding of this layer's dot product
+// (at most fan-in + 8 roundings per term, any order), e_k the propagated bound of the
+// inputs; ReLU is 1-Lipschitz so e_n = B_n after it.  Every bound is accumulated with
+// upward rounding, so it only over-estimates.  One extra FMA per MAC.
+// Stage 2 (ff_kernel): the queries stage 1 leaves ambiguous are evaluated in
+// float-float arithmetic (error-free TwoProd / TwoSum transformations, Ogita, Rump &
+// Oishi 2005) with the analogous bound, whose rounding part is O(K^2 u^2).
+#include <math.h>
+
+#include "common.cuh"
+
+namespace {
+
+constexpr int KC = 32;
+constexpr unsigned FULL = 0xffffffffu;
+constexpr float U = 5.9604644775390625e-08f;  // unit roundoff 2^-24
+
+__device__ __forceinline__ unsigned ord_f32(float f) {
+    unsigned u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float unord_f32(unsigned u) {
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+__device__ __forceinline__ unsigned long long ord_f64(double f) {
+    unsigned long long u = (unsigned long long)__double_as_longlong(f);
+    return (u & 0x8000000000000000ull) ? ~u : (u | 0x8000000000000000ull);
+}
+
+// One hidden layer over a tile: values aout = relu(b + W ain) and bounds eout.
+template <int NJ, int MI>
+__device__ __forceinline__ void bound_layer_tile(const float *__restrict__ W, const float *__restrict__ b, int K,
+                                                 int N, float g, const float *ain, const float *ein, float *aout,
+                                                 float *eout, float *wt, int KP) {
+    constexpr int WS = 16 * NJ + 1;
+    const int t = threadIdx.x, tn = t & 15, tm = t >> 4;
+    float acc[MI][NJ], bnd[MI][NJ];
+#pragma unroll
+    for (int j = 0; j < NJ; j++) {
+        const int nn = tn + 16 * j;
+        const float bv = nn < N ? __ldg(b + nn) : 0.f;
+        const float bb = __fmul_ru(g, fabsf(bv));
+#pragma unroll
+        for (int i = 0; i < MI; i++) {
+            acc[i][j] = bv;
+            bnd[i][j] = bb;
+        }
+    }
+    for (int kc = 0; kc < K; kc += KC) {
+        const int kw = min(KC, K - kc);
+        __syncthreads();
+        for (int e = t; e < N * KC; e += blockDim.x) {
+            const int nn = e / KC, kk = e % KC;
+            wt[kk * WS + nn] = kk < kw ? __ldg(W + (size_t)nn * K + kc + kk) : 0.f;
+        }
+        __syncthreads();
+        for (int kk = 0; kk < kw; kk++) {
+            float a[MI], v[MI], w[NJ];
+#pragma unroll
+            for (int i = 0; i < MI; i++) {
+                const int idx = (tm + 16 * i) * KP + kc + kk;
+                a[i] = ain[idx];
+                v[i] = __fmaf_ru(g, fabsf(a[i]), ein[idx]);
+            }
+#pragma unroll
+            for (int j = 0; j < NJ; j++) w[j] = wt[kk * WS + tn + 16 * j];
+#pragma unroll
+            for (int i = 0; i < MI; i++)
+#pragma unroll
+                for (int j = 0; j < NJ; j++) {
+                    acc[i][j] = fmaf(a[i], w[j], acc[i][j]);
+                    bnd[i][j] = __fmaf_ru(v[i], fabsf(w[j]), bnd[i][j]);
+                }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < NJ; j++) {
+        const int nn = tn + 16 * j;
+        if (nn < N)
+#pragma unroll
+            for (int i = 0; i < MI; i++) {
+                aout[(tm + 16 * i) * KP + nn] = fmaxf(acc[i][j], 0.f);
+                eout[(tm + 16 * i) * KP + nn] = bnd[i][j];
+            }
+    }
+}
+
+// decision of z in [lo, hi] against tau: 1 inside, 0 outside, -1 undecided
+__device__ __forceinline__ int decide_interval(float lo, float hi, TauF tau) {
+    if (lo >= tau.up) return 1;
+    if (hi < tau.dn || (tau.dn == tau.up && hi < tau.up)) return 0;
+    return -1;
+}
+
+// MODE 0: re-check listed queries, settle their bits, forward the rest to stage 2.
+// MODE 1: calibration: lower bound of every listed (positive) query -> lo_out,
+//         minimum upper bound -> umin_bits.
+template <int NJ, int MI, int MODE>
+__global__ void __launch_bounds__(256) bound_tile_kernel(MlpDesc d, GammaTab gt, const float *__restrict__ q, TauF tau,
+                                                         const unsigned *count, const unsigned *idx, uint32_t *bits,
+                                                         nb_query_stats *st, unsigned *ff_count, unsigned *ff_idx,
+                                                         float *lo_out, unsigned *umin_bits) {
+    constexpr int TM = 16 * MI, KP = 16 * NJ + 1, TPQ = 256 / TM;
+    extern __shared__ float smem[];
+    float *a0 = smem, *e0 = a0 + TM * KP, *a1 = e0 + TM * KP, *e1 = a1 + TM * KP, *wt = e1 + TM * KP;
+    __shared__ unsigned rowidx[TM];
+    __shared__ float zs[TM], bs[TM];
+    const int t = threadIdx.x, w0 = d.w[0];
+    const unsigned cnt = *count;
+    const unsigned ntiles = (cnt + TM - 1) / TM;
+    unsigned long long r32 = 0;
+    long long dinside = 0;
+    unsigned umin = 0xffffffffu;
+    for (unsigned tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int rows = (int)min((unsigned)TM, cnt - tile * TM);
+        __syncthreads();
+        if (t < TM) rowidx[t] = t < rows ? idx[tile * TM + t] : 0u;
+        __syncthreads();
+        for (int e = t; e < TM * w0; e += blockDim.x) {
+            const int m = e / w0, k = e % w0;
+            a0[m * KP + k] = m < rows ? q[(size_t)rowidx[m] * w0 + k] : 0.f;
+            e0[m * KP + k] = 0.f;
+        }
+        float *ain = a0, *ein = e0, *aout = a1, *eout = e1;
+        for (int l = 0; l < d.L - 1; l++) {
+            const int K = d.w[l], N = d.w[l + 1];
+            const float *W = d.p + d.off[l];
+            bound_layer_tile<NJ, MI>(W, W + (size_t)N * K, K, N, gt.g[l], ain, ein, aout, eout, wt, KP);
+            float *tp = ain;
+            ain = aout;
+            aout = tp;
+            tp = ein;
+            ein = eout;
+            eout = tp;
+        }
+        __syncthreads();
+        {
+            const int K = d.w[d.L - 1];
+            const float *W = d.p + d.off[d.L - 1];
+            const float g = gt.g[d.L - 1];
+            const int m = t / TPQ, part = t % TPQ;
+            float s = 0.f, bb = 0.f;
+            for (int k = part; k < K; k += TPQ) {
+                const float w = __ldg(W + k), a = ain[m * KP + k];
+                s = fmaf(w, a, s);
+                bb = __fmaf_ru(fabsf(w), __fmaf_ru(g, fabsf(a), ein[m * KP + k]), bb);
+            }
+#pragma unroll
+            for (int o = 1; o < TPQ; o <<= 1) {
+                s += __shfl_xor_sync(FULL, s, o);
+                bb = __fadd_ru(bb, __shfl_xor_sync(FULL, bb, o));
+            }
+            if (part == 0) {
+                const float bL = __ldg(W + K);
+                zs[m] = s + bL;
+                bs[m] = __fmaf_ru(g, fabsf(bL), bb);
+            }
+        }
+        __syncthreads();
+        if (t < rows) {
+            const unsigned i = rowidx[t];
+            const float z = zs[t], B = bs[t];
+            const float lo = __fsub_rd(z, B), hi = __fadd_ru(z, B);
+            if (MODE == 0) {
+                int dec = decide_interval(lo, hi, tau);
+                if (dec < 0) {
+                    ff_idx[atomicAdd(ff_count, 1u)] = i;  // stage 2 settles this bit
+                } else {
+                    r32++;
+                    const unsigned bit = 1u << (i & 31);
+                    const unsigned old = dec ? atomicOr(bits + (i >> 5), bit) : atomicAnd(bits + (i >> 5), ~bit);
+                    dinside += dec - (int)((old & bit) != 0);
+                }
+            } else {
+                float l2 = lo, h2 = hi;
+                if (!(l2 == l2) || !(h2 == h2)) {  // NaN: always a candidate
+                    l2 = -INFINITY;
+                    h2 = -INFINITY;
+                }
+                lo_out[tile * TM + t] = l2;
+                umin = min(umin, ord_f32(h2));
+            }
+        }
+    }
+    if (MODE == 0) {
+        if (st && t < TM) {
+            unsigned long long rr = r32;
+            long long di = dinside;
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                rr += __shfl_xor_sync(FULL, rr, o);
+                di += __shfl_xor_sync(FULL, di, o);
+            }
+            if ((t & 31) == 0) {
+                if (rr) atomicAdd(&st->n_resolved_f32, rr);
+                if (di) atomicAdd(&st->n_inside, (unsigned long long)di);
+            }
+        }
+    } else if (t < TM) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) umin = min(umin, __shfl_xor_sync(FULL, umin, o));
+        if ((t & 31) == 0 && umin != 0xffffffffu) atomicMin(umin_bits, umin);
+    }
+}
+
+// ---------------------------------------------------------------- float-float stage
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// float-float dot product of one neuron: z = b + sum_k W_k (h_k + l_k), exact inputs
+// carrying bounds e_k.  Returns the normalised pair (hi, lo) and a bound on
+// |hi + lo - exact|: c (|b| + sum |W_k|(|h_k| + |l_k|)) + sum |W_k| e_k, with
+// c = gamma_{3K+3} (K + 3) u bounding the rounding of the error accumulator.
+__device__ __forceinline__ void ff_neuron(const float *__restrict__ Wr, float bv, int K, float c, const float *h,
+                                          const float *l, const float *e, float &hi, float &lo, float &bound) {
+    float sh = bv, sig = 0.f, T = fabsf(bv), P = 0.f;
+    for (int k = 0; k < K; k++) {
+        const float w = __ldg(Wr + k), hk = h[k], lk = l[k];
+        const float p = __fmul_rn(w, hk);
+        const float qq = fmaf(w, hk, -p);  // w hk = p + qq exactly
+        float tsum, dd;
+        two_sum(sh, p, tsum, dd);
+        sh = tsum;
+        sig = fmaf(w, lk, sig);
+        sig = __fadd_rn(sig, dd);
+        sig = __fadd_rn(sig, qq);
+        T = __fmaf_ru(fabsf(w), __fadd_ru(fabsf(hk), fabsf(lk)), T);
+        P = __fmaf_ru(fabsf(w), e[k], P);
+    }
+    two_sum(sh, sig, hi, lo);
+    bound = __fmaf_ru(c, T, P);
+}
+
+// One warp per query still ambiguous after stage 1.
+__global__ void __launch_bounds__(128) ff_kernel(MlpDesc d, GammaTab gt, const float *__restrict__ q, TauF tau,
+                                                 const unsigned *ff_count, const unsigned *ff_idx, uint32_t *bits,
+                                                 nb_query_stats *st) {
+    __shared__ float sh_[4][3][2][NB_MAXW];  // [warp][h,l,e][buffer][k]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned cnt = *ff_count;
+    unsigned long long rff = 0, unres = 0;
+    long long dinside = 0;
+    for (unsigned f = blockIdx.x * 4 + warp; f < cnt; f += gridDim.x * 4) {
+        const unsigned i = ff_idx[f];
+        float *h = sh_[warp][0][0], *l = sh_[warp][1][0], *e = sh_[warp][2][0];
+        float *h2 = sh_[warp][0][1], *l2 = sh_[warp][1][1], *e2 = sh_[warp][2][1];
+        const float *x = q + (size_t)i * d.w[0];
+        for (int k = lane; k < d.w[0]; k += 32) {
+            h[k] = x[k];
+            l[k] = 0.f;
+            e[k] = 0.f;
+        }
+        __syncwarp();
+        for (int ly = 0; ly < d.L - 1; ly++) {
+            const int K = d.w[ly], N = d.w[ly + 1];
+            const float *W = d.p + d.off[ly];
+            for (int nn = lane; nn < N; nn += 32) {
+                float hi, lo, bd;
+                ff_neuron(W + (size_t)nn * K, __ldg(W + (size_t)N * K + nn), K, gt.gff[ly], h, l, e, hi, lo, bd);
+                if (hi > 0.f) {  // relu(hi + lo): the pair is normalised, so its sign is hi's
+                    h2[nn] = hi;
+                    l2[nn] = lo;
+                } else {
+                    h2[nn] = 0.f;
+                    l2[nn] = 0.f;
+                }
+                e2[nn] = bd;
+            }
+            __syncwarp();
+            float *tp = h;
+            h = h2;
+            h2 = tp;
+            tp = l;
+            l = l2;
+            l2 = tp;
+            tp = e;
+            e = e2;
+            e2 = tp;
+        }
+        if (lane == 0) {
+            const int K = d.w[d.L - 1];
+            const float *W = d.p + d.off[d.L - 1];
+            float zh, zl, B;
+            ff_neuron(W, __ldg(W + K), K, gt.gff[d.L - 1], h, l, e, zh, zl, B);
+            // D = z - tau in float-float: (s, ee) = zh - tau_hi exactly, t = (zl - tau_lo) + ee
+            float s, ee;
+            two_sum(zh, -tau.hi, s, ee);
+            const float tt = __fadd_rn(__fsub_rn(zl, tau.lo), ee);
+            const float Et = __fmul_ru(3.f * U, __fadd_ru(__fadd_ru(fabsf(zl), fabsf(tau.lo)), fabsf(ee)));
+            const float v = __fadd_rn(s, tt);
+            const float M = __fadd_ru(__fadd_ru(__fadd_ru(B, Et), tau.err), __fmul_ru(2.f * U, fabsf(v)));
+            int dec;
+            if (__fsub_rd(v, M) >= 0.f) {
+                dec = 1;
+                rff++;
+            } else if (__fadd_ru(v, M) < 0.f) {
+                dec = 0;
+                rff++;
+            } else {
+                dec = 1;  // unresolved: conservative
+                unres++;
+            }
+            const unsigned bit = 1u << (i & 31);
+            const unsigned old = dec ? atomicOr(bits + (i >> 5), bit) : atomicAnd(bits + (i >> 5), ~bit);
+            dinside += dec - (int)((old & bit) != 0);
+        }
+        __syncwarp();
+    }
+    if (st && lane == 0) {
+        if (rff) atomicAdd(&st->n_resolved_ff, rff);
+        if (unres) atomicAdd(&st->n_unresolved, unres);
+        if (dinside) atomicAdd(&st->n_inside, (unsigned long long)dinside);
+    }
+}
+
+// ---------------------------------------------------------------- calibration helpers
+// list of the indices whose label bit is 1
+__global__ void compact_positive_kernel(const uint32_t *__restrict__ labels, long long n, unsigned *count,
+                                        unsigned *idx) {
+    const int lane = threadIdx.x & 31;
+    const long long nw = (n + 31) / 32;
+    for (long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nw;
+         w += ((long long)gridDim.x * blockDim.x) >> 5) {
+        const long long i = w * 32 + lane;
+        const bool pos = i < n && ((labels[w] >> lane) & 1u);
+        const unsigned b = __ballot_sync(FULL, pos);
+        if (!b) continue;
+        unsigned base = 0;
+        if (lane == 0) base = atomicAdd(count, (unsigned)__popc(b));
+        base = __shfl_sync(FULL, base, 0);
+        if (pos) idx[base + __popc(b & ((1u << lane) - 1u))] = (unsigned)i;
+    }
+}
+
+// FP64 forward of the candidates for the minimum (lower bound <= minimum upper bound)
+__global__ void __launch_bounds__(256) calib_f64_kernel(MlpDesc d, const float *__restrict__ q, const unsigned *count,
+                                                        const unsigned *idx, const float *__restrict__ lo,
+                                                        const unsigned *umin_bits, unsigned long long *zmin_bits) {
+    __shared__ double sa[8][2 * NB_MAXW];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned cnt = *count;
+    const float umin = unord_f32(*umin_bits);
+    unsigned long long best = ~0ull;
+    for (unsigned j = blockIdx.x * 8 + warp; j < cnt; j += gridDim.x * 8) {
+        if (!(lo[j] <= umin)) continue;
+        double *a = sa[warp], *a2 = sa[warp] + NB_MAXW;
+        const float *x = q + (size_t)idx[j] * d.w[0];
+        for (int k = lane; k < d.w[0]; k += 32) a[k] = (double)x[k];
+        __syncwarp();
+        for (int l = 0; l < d.L - 1; l++) {
+            const int K = d.w[l], N = d.w[l + 1];
+            const float *W = d.p + d.off[l];
+            for (int nn = lane; nn < N; nn += 32) {
+                double s = (double)__ldg(W + (size_t)N * K + nn);
+                for (int k = 0; k < K; k++) s = fma((double)__ldg(W + (size_t)nn * K + k), a[k], s);
+                a2[nn] = s > 0.0 ? s : 0.0;
+            }
+            __syncwarp();
+            double *tp = a;
+            a = a2;
+            a2 = tp;
+        }
+        const int K = d.w[d.L - 1];
+        const float *W = d.p + d.off[d.L - 1];
+        double s = 0.0;
+        for (int k = lane; k < K; k += 32) s = fma((double)__ldg(W + k), a[k], s);
+#pragma unroll
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+        s += (double)__ldg(W + K);
+        __syncwarp();
+        if (lane == 0) best = min(best, (s == s) ? ord_f64(s) : 0ull);  // NaN sorts lowest
+    }
+    if (lane == 0 && best != ~0ull) atomicMin(zmin_bits, best);
+}
+
+int num_sms() {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
+
+template <int NJ, int MI, int MODE>
+nb_status tile_launch(const MlpDesc &d, const GammaTab &gt, const float *q, TauF tau, const unsigned *count,
+                      const unsigned *idx, int64_t max_count, uint32_t *bits, nb_query_stats *st, unsigned *ff_count,
+                      unsigned *ff_idx, float *lo_out, unsigned *umin_bits, cudaStream_t s) {
+    constexpr int TM = 16 * MI, KP = 16 * NJ + 1;
+    const size_t smem = (size_t)(4 * TM * KP + KC * (16 * NJ + 1)) * sizeof(float);
+    auto k = bound_tile_kernel<NJ, MI, MODE>;
+    NB_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 1;
+    NB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, smem));
+    if (per_sm < 1) per_sm = 1;
+    int64_t grid = (int64_t)num_sms() * per_sm;
+    const int64_t need = (max_count + TM - 1) / TM;
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    k<<<(unsigned)grid, 256, smem, s>>>(d, gt, q, tau, count, idx, bits, st, ff_count, ff_idx, lo_out, umin_bits);
+    NB_CUDA(cudaGetLastError());
+    return NB_OK;
+}
+
+template <int MODE>
+nb_status tile_dispatch(const MlpDesc &d, const GammaTab &gt, const float *q, TauF tau, const unsigned *count,
+                        const unsigned *idx, int64_t max_count, uint32_t *bits, nb_query_stats *st,
+                        unsigned *ff_count, unsigned *ff_idx, float *lo_out, unsigned *umin_bits, cudaStream_t s) {
+    const int nj = (d.maxw + 15) / 16;
+    if (nj <= 2)
+        return tile_launch<2, 4, MODE>(d, gt, q, tau, count, idx, max_count, bits, st, ff_count, ff_idx, lo_out,
+                                       umin_bits, s);
+    if (nj <= 4)
+        return tile_launch<4, 4, MODE>(d, gt, q, tau, count, idx, max_count, bits, st, ff_count, ff_idx, lo_out,
+                                       umin_bits, s);
+    if (nj <= 8)
+        return tile_launch<8, 4, MODE>(d, gt, q, tau, count, idx, max_count, bits, st, ff_count, ff_idx, lo_out,
+                                       umin_bits, s);
+    return tile_launch<16, 2, MODE>(d, gt, q, tau, count, idx, max_count, bits, st, ff_count, ff_idx, lo_out,
+                                    umin_bits, s);
+}
+
+}  // namespace
+
+nb_status nb_launch_recheck(const MlpDesc &d, const GammaTab &gt, const float *q, TauF tau, uint32_t *bits,
+                            nb_query_stats *st, QueryWs ws, int64_t n, cudaStream_t s) {
+    NB_CUDA(cudaMemsetAsync(ws.ff_count, 0, sizeof(unsigned), s));
+    nb_status r = tile_dispatch<0>(d, gt, q, tau, ws.flag_count, ws.flag_idx, n, bits, st, ws.ff_count, ws.ff_idx,
+                                   nullptr, nullptr, s);
+    if (r != NB_OK) return r;
+    int64_t grid = num_sms() * 4;
+    if (grid > (n + 3) / 4) grid = (n + 3) / 4;
+    if (grid < 1) grid = 1;
+    ff_kernel<<<(unsigned)grid, 128, 0, s>>>(d, gt, q, tau, ws.ff_count, ws.ff_idx, bits, st);
+    NB_CUDA(cudaGetLastError());
+    return NB_OK;
+}
+
+nb_status nb_launch_calibrate(const MlpDesc &d, const GammaTab &gt, const float *q, const uint32_t *labels,
+                              int64_t n, CalibWs ws, cudaStream_t s) {
+    NB_CUDA(cudaMemsetAsync(ws.umin_bits, 0xff, sizeof(unsigned), s));
+    NB_CUDA(cudaMemsetAsync(ws.zmin_bits, 0xff, sizeof(unsigned long long), s));
+    NB_CUDA(cudaMemsetAsync(ws.npos, 0, sizeof(unsigned), s));
+    int64_t grid = num_sms() * 8;
+    const int64_t need = (n + 255) / 256;
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    compact_positive_kernel<<<(unsigned)grid, 256, 0, s>>>(labels, (long long)n, ws.npos, ws.pos_idx);
+    NB_CUDA(cudaGetLastError());
+    TauF none{};
+    nb_status r = tile_dispatch<1>(d, gt, q, none, ws.npos, ws.pos_idx, n, nullptr, nullptr, nullptr, nullptr, ws.lo,
+                                   ws.umin_bits, s);
+    if (r != NB_OK) return r;
+    grid = num_sms() * 8;
+    if (grid > (n + 7) / 8) grid = (n + 7) / 8;
+    if (grid < 1) grid = 1;
+    calib_f64_kernel<<<(unsigned)grid, 256, 0, s>>>(d, q, ws.npos, ws.pos_idx, ws.lo, ws.umin_bits, ws.zmin_bits);
+    NB_CUDA(cudaGetLastError());
+    return NB_OK;
+}

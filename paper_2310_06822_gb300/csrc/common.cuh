@@ -32,17 +32,19 @@ struct MlpDesc {
     const float *p;          // device FP32 master parameters
 };
 
-// Unit roundoff gammas gamma_k = k u / (1 - k u), u = 2^-24, rounded up, one per layer
-// (k = fan-in + 1), used by the rigorous FP32 error bounds.
+// Rounding-error constants of the rigorous bounds, rounded up, one per layer:
+//   g[l]   = gamma_{K+8} = k u / (1 - k u), u = 2^-24, k = fan-in K + 8 (FP32 stage)
+//   gff[l] = gamma_{3K+3} (K + 3) u (float-float stage)
 struct GammaTab {
     float g[NB_MAXL];
+    float gff[NB_MAXL];
 };
 
-struct nb_model_impl;
-
-// tau bracketed by two floats: tau_dn <= tau <= tau_up, equal when tau is a float.
+// tau bracketed by two floats: tau_dn <= tau <= tau_up, equal when tau is a float;
+// and split as tau = hi + lo + r with |r| <= err (float-float comparisons).
 struct TauF {
     float dn, up;
+    float hi, lo, err;
 };
 TauF nb_tau_bracket(double tau);
 
@@ -51,8 +53,10 @@ nb_status nb_launch_label(const nb_shape *shape, int kind, const float *q, int64
                           nb_label_stats *st, cudaStream_t s);
 
 struct QueryWs {
-    unsigned int *flag_count;   // [1]
+    unsigned int *flag_count;   // [1] queries within the margin of tau
     unsigned int *flag_idx;     // [n]
+    unsigned int *ff_count;     // [1] queries left ambiguous by the FP32 bound
+    unsigned int *ff_idx;       // [n]
 };
 
 nb_status nb_launch_fwd_f32(const MlpDesc &d, const float *q, int64_t n, TauF tau, float margin,
@@ -63,8 +67,9 @@ nb_status nb_launch_recheck(const MlpDesc &d, const GammaTab &gt, const float *q
 struct CalibWs {
     unsigned int *umin_bits;          // [1] order-preserving bits of min upper bound
     unsigned long long *zmin_bits;    // [1] order-preserving bits of min FP64 logit
-    unsigned long long *npos;         // [1]
-    float *lo;                        // [n] lower bounds (positives) / +inf
+    unsigned int *npos;               // [1] number of positives
+    unsigned int *pos_idx;            // [n] indices of the positives
+    float *lo;                        // [n] lower bound of each listed positive
 };
 nb_status nb_launch_calibrate(const MlpDesc &d, const GammaTab &gt, const float *q, const uint32_t *labels,
                               int64_t n, CalibWs ws, cudaStream_t s);

@@ -1,9 +1,6 @@
 // FP32 kernels of the bounding network h (Sec. 3.4 "Architecture": MLP, sigmoid
 // output rounded to {0,1}; hidden activation ReLU as the configurations state):
 //   fwd_f32_kernel     plain FP32 forward over query tiles -> decision bits, margin flags
-//   recheck_kernel     FP32 forward with a rigorous forward error bound for flagged queries
-//   calib_*_kernel     threshold calibration (Suppl. "Numerics" output epsilon): FP32 bounds
-//                      locate the minimum positive logit, FP64 evaluates the candidates
 //   train_f32_kernel   forward + asymmetric BCE of Eq. (loss) + backward, per-CTA partials
 //   adam_kernel        deterministic reduction of the partials + Adam (Sec. 3.4 "Training")
 #include <math.h>
@@ -15,18 +12,6 @@ namespace {
 constexpr int TMF = 64;  // queries per forward tile
 constexpr int KC = 32;   // k-chunk of weights staged in shared memory
 constexpr unsigned FULL = 0xffffffffu;
-
-__device__ __forceinline__ unsigned ord_f32(float f) {
-    unsigned u = __float_as_uint(f);
-    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
-}
-__device__ __forceinline__ float unord_f32(unsigned u) {
-    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
-}
-__device__ __forceinline__ unsigned long long ord_f64(double f) {
-    unsigned long long u = (unsigned long long)__double_as_longlong(f);
-    return (u & 0x8000000000000000ull) ? ~u : (u | 0x8000000000000000ull);
-}
 
 // hidden layer l of a tile: aout[m][n] = relu(b_n + sum_k W[n][k] ain[m][k]) for MI*16 rows.
 // Thread (tm, tn) owns rows tm + 16 i and neurons tn + 16 j.
@@ -148,186 +133,6 @@ __global__ void __launch_bounds__(256) fwd_f32_kernel(MlpDesc d, const float *__
         if (c_flag) atomicAdd(&st->n_flagged, c_flag);
         if (c_nf) atomicAdd(&st->n_nonfinite, c_nf);
     }
-}
-
-// ------------------------------------------------- FP32 forward with a rigorous bound
-// One warp evaluates one query.  For each neuron the computed value s^ and a bound
-// B >= |s^ - s| on its distance to the exact real value s are carried:
-//   B_n = gamma_l (|b_n| + sum_k |W_nk| |a^_k|) + sum_k |W_nk| e_k,
-// the first term bounding the rounding of this layer's dot product (any order,
-// at most fan-in + 8 roundings per term), the second the propagated input error.
-// ReLU is 1-Lipschitz, so e_n = B_n after it.  Bounds are accumulated rounding up.
-__device__ void warp_forward_bound(const MlpDesc &d, const GammaTab &gt, const float *__restrict__ x,
-                                   float *sa, float *se, float &z_out, float &b_out) {
-    const int lane = threadIdx.x & 31;
-    float *a = sa, *e = se, *a2 = sa + NB_MAXW, *e2 = se + NB_MAXW;
-    for (int k = lane; k < d.w[0]; k += 32) {
-        a[k] = x[k];
-        e[k] = 0.f;
-    }
-    __syncwarp();
-    for (int l = 0; l < d.L - 1; l++) {
-        const int K = d.w[l], N = d.w[l + 1];
-        const float *W = d.p + d.off[l];
-        const float *b = W + (size_t)N * K;
-        for (int nn = lane; nn < N; nn += 32) {
-            const float bv = __ldg(b + nn);
-            float s = bv, sabs = fabsf(bv), serr = 0.f;
-            const float *Wr = W + (size_t)nn * K;
-            for (int k = 0; k < K; k++) {
-                const float w = __ldg(Wr + k);
-                s = fmaf(w, a[k], s);
-                sabs = __fmaf_ru(fabsf(w), fabsf(a[k]), sabs);
-                serr = __fmaf_ru(fabsf(w), e[k], serr);
-            }
-            a2[nn] = fmaxf(s, 0.f);
-            e2[nn] = __fmaf_ru(gt.g[l], sabs, serr);
-        }
-        __syncwarp();
-        float *tp = a;
-        a = a2;
-        a2 = tp;
-        tp = e;
-        e = e2;
-        e2 = tp;
-    }
-    const int K = d.w[d.L - 1];
-    const float *W = d.p + d.off[d.L - 1];
-    float s = 0.f, sabs = 0.f, serr = 0.f;
-    for (int k = lane; k < K; k += 32) {
-        const float w = __ldg(W + k);
-        s = fmaf(w, a[k], s);
-        sabs = __fmaf_ru(fabsf(w), fabsf(a[k]), sabs);
-        serr = __fmaf_ru(fabsf(w), e[k], serr);
-    }
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-        s += __shfl_xor_sync(FULL, s, o);
-        sabs = __fadd_ru(sabs, __shfl_xor_sync(FULL, sabs, o));
-        serr = __fadd_ru(serr, __shfl_xor_sync(FULL, serr, o));
-    }
-    const float bL = __ldg(W + K);
-    s = s + bL;
-    sabs = __fadd_ru(sabs, fabsf(bL));
-    z_out = s;
-    b_out = __fmaf_ru(gt.g[d.L - 1], sabs, serr);
-    __syncwarp();
-}
-
-__global__ void __launch_bounds__(256) recheck_kernel(MlpDesc d, GammaTab gt, const float *__restrict__ q, TauF tau,
-                                                      uint32_t *bits, nb_query_stats *st,
-                                                      const unsigned *flag_count, const unsigned *flag_idx) {
-    __shared__ float sa[8][2 * NB_MAXW];
-    __shared__ float se[8][2 * NB_MAXW];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const unsigned cnt = *flag_count;
-    unsigned long long r32 = 0, unres = 0;
-    long long dinside = 0;
-    for (unsigned f = blockIdx.x * 8 + warp; f < cnt; f += gridDim.x * 8) {
-        const unsigned i = flag_idx[f];
-        float z, B;
-        warp_forward_bound(d, gt, q + (size_t)i * d.w[0], sa[warp], se[warp], z, B);
-        if (lane == 0) {
-            const float lo = __fsub_rd(z, B), hi = __fadd_ru(z, B);
-            int dec;
-            if (lo >= tau.up) {
-                dec = 1;
-                r32++;
-            } else if (hi < tau.dn || (tau.dn == tau.up && hi < tau.up)) {
-                dec = 0;
-                r32++;
-            } else {
-                dec = 1;  // still ambiguous: conservative
-                unres++;
-            }
-            const unsigned bit = 1u << (i & 31);
-            const unsigned old = dec ? atomicOr(bits + (i >> 5), bit) : atomicAnd(bits + (i >> 5), ~bit);
-            const int was = (old & bit) != 0;
-            dinside += dec - was;
-        }
-    }
-    if (st && lane == 0) {
-        if (r32) atomicAdd(&st->n_resolved_f32, r32);
-        if (unres) atomicAdd(&st->n_unresolved, unres);
-        if (dinside) atomicAdd(&st->n_inside, (unsigned long long)dinside);
-    }
-}
-
-// ------------------------------------------------------------------ calibration
-__global__ void __launch_bounds__(256) calib_bound_kernel(MlpDesc d, GammaTab gt, const float *__restrict__ q,
-                                                          const uint32_t *__restrict__ labels, long long n,
-                                                          float *lo_out, unsigned *umin_bits,
-                                                          unsigned long long *npos) {
-    __shared__ float sa[8][2 * NB_MAXW];
-    __shared__ float se[8][2 * NB_MAXW];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    unsigned umin = 0xffffffffu;
-    unsigned long long np = 0;
-    for (long long i = (long long)blockIdx.x * 8 + warp; i < n; i += (long long)gridDim.x * 8) {
-        const bool pos = (labels[i >> 5] >> (i & 31)) & 1u;
-        if (!pos) {
-            if (lane == 0) lo_out[i] = INFINITY;
-            continue;
-        }
-        float z, B;
-        warp_forward_bound(d, gt, q + (size_t)i * d.w[0], sa[warp], se[warp], z, B);
-        if (lane == 0) {
-            np++;
-            float lo = __fsub_rd(z, B), hi = __fadd_ru(z, B);
-            if (!(lo == lo) || !(hi == hi)) {  // NaN: always a candidate
-                lo = -INFINITY;
-                hi = -INFINITY;
-            }
-            lo_out[i] = lo;
-            umin = min(umin, ord_f32(hi));
-        }
-    }
-    if (lane == 0) {
-        if (np) atomicAdd(npos, np);
-        atomicMin(umin_bits, umin);
-    }
-}
-
-__global__ void __launch_bounds__(256) calib_f64_kernel(MlpDesc d, const float *__restrict__ q, long long n,
-                                                        const float *__restrict__ lo, const unsigned *umin_bits,
-                                                        unsigned long long *zmin_bits) {
-    __shared__ double sa[8][2 * NB_MAXW];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const float umin = unord_f32(*umin_bits);
-    unsigned long long best = ~0ull;
-    for (long long i = (long long)blockIdx.x * 8 + warp; i < n; i += (long long)gridDim.x * 8) {
-        if (!(lo[i] <= umin)) continue;  // not a candidate for the minimum
-        double *a = sa[warp], *a2 = sa[warp] + NB_MAXW;
-        const float *x = q + (size_t)i * d.w[0];
-        for (int k = lane; k < d.w[0]; k += 32) a[k] = (double)x[k];
-        __syncwarp();
-        for (int l = 0; l < d.L - 1; l++) {
-            const int K = d.w[l], N = d.w[l + 1];
-            const float *W = d.p + d.off[l];
-            for (int nn = lane; nn < N; nn += 32) {
-                double s = (double)__ldg(W + (size_t)N * K + nn);
-                for (int k = 0; k < K; k++) s = fma((double)__ldg(W + (size_t)nn * K + k), a[k], s);
-                a2[nn] = s > 0.0 ? s : 0.0;
-            }
-            __syncwarp();
-            double *tp = a;
-            a = a2;
-            a2 = tp;
-        }
-        const int K = d.w[d.L - 1];
-        const float *W = d.p + d.off[d.L - 1];
-        double s = 0.0;
-        for (int k = lane; k < K; k += 32) s = fma((double)__ldg(W + k), a[k], s);
-#pragma unroll
-        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
-        s += (double)__ldg(W + K);
-        __syncwarp();
-        if (lane == 0) {
-            unsigned long long u = (s == s) ? ord_f64(s) : 0ull;  // NaN sorts below everything
-            best = min(best, u);
-        }
-    }
-    if (lane == 0 && best != ~0ull) atomicMin(zmin_bits, best);
 }
 
 // ------------------------------------------------------------------ training step
@@ -594,33 +399,6 @@ nb_status nb_launch_fwd_f32(const MlpDesc &d, const float *q, int64_t n, TauF ta
     case 8: return fwd_launch<8>(d, q, n, tau, margin, bits, logits, st, ws, s);
     default: return fwd_launch<16>(d, q, n, tau, margin, bits, logits, st, ws, s);
     }
-}
-
-nb_status nb_launch_recheck(const MlpDesc &d, const GammaTab &gt, const float *q, TauF tau, uint32_t *bits,
-                            nb_query_stats *st, QueryWs ws, int64_t n, cudaStream_t s) {
-    int64_t grid = num_sms() * 4;
-    const int64_t need = (n + 7) / 8;
-    if (grid > need) grid = need;
-    if (grid < 1) grid = 1;
-    recheck_kernel<<<(unsigned)grid, 256, 0, s>>>(d, gt, q, tau, bits, st, ws.flag_count, ws.flag_idx);
-    NB_CUDA(cudaGetLastError());
-    return NB_OK;
-}
-
-nb_status nb_launch_calibrate(const MlpDesc &d, const GammaTab &gt, const float *q, const uint32_t *labels,
-                              int64_t n, CalibWs ws, cudaStream_t s) {
-    NB_CUDA(cudaMemsetAsync(ws.umin_bits, 0xff, sizeof(unsigned), s));
-    NB_CUDA(cudaMemsetAsync(ws.zmin_bits, 0xff, sizeof(unsigned long long), s));
-    NB_CUDA(cudaMemsetAsync(ws.npos, 0, sizeof(unsigned long long), s));
-    int64_t grid = num_sms() * 8;
-    const int64_t need = (n + 7) / 8;
-    if (grid > need) grid = need;
-    if (grid < 1) grid = 1;
-    calib_bound_kernel<<<(unsigned)grid, 256, 0, s>>>(d, gt, q, labels, (long long)n, ws.lo, ws.umin_bits, ws.npos);
-    NB_CUDA(cudaGetLastError());
-    calib_f64_kernel<<<(unsigned)grid, 256, 0, s>>>(d, q, (long long)n, ws.lo, ws.umin_bits, ws.zmin_bits);
-    NB_CUDA(cudaGetLastError());
-    return NB_OK;
 }
 
 int nb_train_f32_ctas(const MlpDesc &d, int64_t n, int sms) {

@@ -1,21 +1,499 @@
-// Tensor-core paths (placeholder until the tcgen05 kernels land).
+// Tensor-core forward of the bounding network h (Sec. 3.4 "Architecture") on sm_103a:
+// tcgen05.mma (BF16 x BF16 -> FP32 accumulators in TMEM), weights staged once per CTA
+// into shared memory by the bulk-copy (TMA) engine, activations kept on chip.
+//
+// Persistent CTA of 9 warps:
+//   warps 0-3  epilogue group for tile slot 0, warps 4-7 for slot 1: one thread per
+//              query row (= TMEM lane).  Each group loads its tile's queries, and after
+//              every layer reads the accumulator from TMEM, adds the bias, applies ReLU,
+//              rounds to BF16 and writes the next layer's A operand to shared memory;
+//              after the last hidden layer it evaluates the 1-wide head in FP32 and
+//              writes the decision bit, the logit and the margin flag.
+//   warp 8     allocates TMEM, loads the weights, and (one lane) issues the MMAs.
+// The two slots ping-pong: while one slot's epilogue runs, the other slot's MMAs run.
+// All waits are bounded; a wait that gives up sets an error word and every warp exits
+// through the common tail, which drains the tensor pipe and frees TMEM.
+#include <cuda_bf16.h>
+
 #include "tc.cuh"
 
+namespace {
+
+constexpr int TILE_M = 128;
+constexpr int NEPI = 8;                    // epilogue warps
+constexpr int THREADS = (NEPI + 1) * 32;   // + the MMA / TMEM warp
+constexpr unsigned SPIN_LIMIT = 1u << 22;
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int A_BLOCK = TILE_M * 128;      // one 64-column block of a 128-row operand
+
+struct TcDesc {
+    int in, H, NH;          // input width (<= 16), hidden width, hidden layers
+    const uint8_t *img;     // packed BF16 operand images, see img_layer_offset
+    uint32_t img_bytes;
+    const float *p;         // FP32 master parameters (biases and head read from here)
+    int off[NB_MAXL];
+};
+
+// image of layer l: layer 0 is H rows x 128 B (K padded to 16 within one 64-column
+// block); layer l >= 1 is H/64 blocks of H rows x 128 B.
+__host__ __device__ inline uint32_t img_layer_offset(int H, int l) {
+    return l == 0 ? 0u : (uint32_t)(H * 128 + (l - 1) * H * H * 2);
+}
+__host__ __device__ inline uint32_t img_total(int H, int NH) { return img_layer_offset(H, NH); }
+
+// ------------------------------------------------------------------ PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// D[tmem] (+)= A[smem] x B[smem]^T, kind::f16 (BF16 inputs, FP32 accumulate)
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// 32 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// two FP32 -> packed BF16x2 (lo in the low half), optionally through ReLU
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    uint32_t d;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+__device__ __forceinline__ uint32_t pack_bf16_relu(float lo, float hi) {
+    uint32_t d;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand in the 128-byte swizzle layout
+// (rows of 128 B, 16-byte chunk c of row r stored at chunk c ^ (r mod 8), 8-row groups
+// 1024 B apart), start address 16-byte granular, base offset 0 (1024-aligned atoms).
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1 << 16;             // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)1 << 46;             // descriptor version for tcgen05
+    d |= (uint64_t)2 << 61;             // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+struct Ctl {
+    uint64_t wbar, aready[2], accfull[2], drain;
+    uint32_t tmem;
+    int abort;
+};
+
+__device__ bool wait_bounded(uint32_t bar, uint32_t parity, Ctl *ctl, int *err) {
+    for (unsigned i = 0; i < SPIN_LIMIT; i++) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*(volatile int *)&ctl->abort) return false;
+    }
+    *(volatile int *)&ctl->abort = 1;
+    atomicExch(err, NB_ETIMEOUT);
+    return false;
+}
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, Ctl *ctl, int *err) {
+    int ok = 1;
+    if ((threadIdx.x & 31) == 0) ok = wait_bounded(bar, parity, ctl, err) ? 1 : 0;
+    return __shfl_sync(FULL, ok, 0) != 0;
+}
+
+template <int H>
+__global__ void __launch_bounds__(THREADS, 1)
+    fwd_bf16_kernel(TcDesc d, const float *__restrict__ q, long long n, TauF tau, float margin,
+                    uint32_t *__restrict__ bits, float *__restrict__ logits, nb_query_stats *st,
+                    unsigned *flag_count, unsigned *flag_idx, int *err) {
+    extern __shared__ uint8_t smem_raw[];
+    Ctl *ctl = reinterpret_cast<Ctl *>(smem_raw);
+    uint8_t *base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023) + 1024;
+    uint8_t *Wimg = base;
+    uint8_t *Abuf = Wimg + d.img_bytes;
+    float *bias = reinterpret_cast<float *>(Abuf + 2 * (H / 64) * A_BLOCK);
+    float *head = bias + d.NH * H;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long ntiles = (n + TILE_M - 1) / TILE_M;
+    const uint32_t bar_w = smem_u32(&ctl->wbar), bar_drain = smem_u32(&ctl->drain);
+    const uint32_t bar_ar[2] = {smem_u32(&ctl->aready[0]), smem_u32(&ctl->aready[1])};
+    const uint32_t bar_af[2] = {smem_u32(&ctl->accfull[0]), smem_u32(&ctl->accfull[1])};
+
+    if (threadIdx.x == 0) {
+        mbar_init(bar_w, 1);
+        mbar_init(bar_ar[0], 4);
+        mbar_init(bar_ar[1], 4);
+        mbar_init(bar_af[0], 1);
+        mbar_init(bar_af[1], 1);
+        mbar_init(bar_drain, 1);
+        ctl->abort = 0;
+        fence_mbar_init();
+    }
+    for (int i = threadIdx.x; i < d.NH * H; i += THREADS) {
+        const int l = i / H, j = i % H;
+        const int K = l == 0 ? d.in : H;
+        bias[i] = d.p[d.off[l] + H * K + j];
+    }
+    for (int i = threadIdx.x; i <= H; i += THREADS) head[i] = d.p[d.off[d.NH] + i];
+    if (warp == NEPI) {
+        tmem_alloc(smem_u32(&ctl->tmem), 2 * H);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = ctl->tmem;
+
+    if (warp == NEPI) {
+        if (lane == 0) {
+            bool ok = true;
+            mbar_expect_tx(bar_w, d.img_bytes);
+            for (uint32_t o = 0; o < d.img_bytes; o += 16384)
+                bulk_g2s(smem_u32(Wimg) + o, d.img + o, min(16384u, d.img_bytes - o), bar_w);
+            ok = wait_bounded(bar_w, 0, ctl, err);
+            uint32_t ph[2] = {0, 0};
+            constexpr uint32_t idesc = idesc_bf16(TILE_M, H);
+            for (long long it = 0; ok; it++) {
+                const bool has[2] = {blockIdx.x + (2 * it) * gridDim.x < ntiles,
+                                     blockIdx.x + (2 * it + 1) * gridDim.x < ntiles};
+                if (!has[0] && !has[1]) break;
+                for (int l = 0; l < d.NH && ok; l++)
+                    for (int s = 0; s < 2 && ok; s++) {
+                        if (!has[s]) continue;
+                        ok = wait_bounded(bar_ar[s], ph[s], ctl, err);
+                        ph[s] ^= 1;
+                        if (!ok) break;
+                        tc_fence_after();
+                        const uint32_t a0 = smem_u32(Abuf + s * (H / 64) * A_BLOCK);
+                        const uint32_t w0 = smem_u32(Wimg) + img_layer_offset(H, l);
+                        const int ksteps = l == 0 ? 1 : H / 16;
+                        for (int j = 0; j < ksteps; j++) {
+                            const uint32_t kb = j >> 2, within = (j & 3) * 32;
+                            mma_f16(tmem + s * H, sdesc_sw128(a0 + kb * A_BLOCK + within),
+                                    sdesc_sw128(w0 + kb * (H * 128) + within), idesc, j > 0 ? 1u : 0u);
+                        }
+                        mma_commit(bar_af[s]);
+                    }
+            }
+            // every issued MMA has completed before TMEM is released
+            mma_commit(bar_drain);
+            wait_bounded(bar_drain, 0, ctl, err);
+            if (!ok) {
+                *(volatile int *)&ctl->abort = 1;
+            }
+        }
+        __syncwarp();
+    } else {
+        const int s = warp >> 2, wq = warp & 3;
+        const int r = wq * 32 + lane;  // row of the tile = TMEM lane
+        const uint32_t taddr = tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)(s * H);
+        const uint32_t A = smem_u32(Abuf + s * (H / 64) * A_BLOCK);
+        const uint32_t row_off = (uint32_t)r * 128, sw = (uint32_t)(r & 7);
+        uint32_t ph = 0;
+        unsigned long long c_in = 0, c_flag = 0, c_nf = 0;
+        for (long long it = 0;; it++) {
+            const long long tile = blockIdx.x + (2 * it + s) * gridDim.x;
+            if (tile >= ntiles) break;
+            const long long row = tile * TILE_M + r;
+            const bool valid = row < n;
+            {
+                float x[16];
+#pragma unroll
+                for (int k = 0; k < 16; k++) x[k] = (valid && k < d.in) ? __ldg(q + row * d.in + k) : 0.f;
+                st_shared_v4(A + row_off + ((0u ^ sw) << 4), pack_bf16(x[0], x[1]), pack_bf16(x[2], x[3]),
+                             pack_bf16(x[4], x[5]), pack_bf16(x[6], x[7]));
+                st_shared_v4(A + row_off + ((1u ^ sw) << 4), pack_bf16(x[8], x[9]), pack_bf16(x[10], x[11]),
+                             pack_bf16(x[12], x[13]), pack_bf16(x[14], x[15]));
+            }
+            fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar_ar[s]);
+            bool ok = true;
+            float z = 0.f;
+            for (int l = 0; l < d.NH; l++) {
+                ok = warp_wait(bar_af[s], ph, ctl, err);
+                ph ^= 1;
+                if (!ok) break;
+                tc_fence_after();
+                const float *b = bias + l * H;
+                if (l < d.NH - 1) {
+#pragma unroll
+                    for (int qc = 0; qc < H / 32; qc++) {
+                        float v[32];
+                        tmem_ld32(taddr + qc * 32, v);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int c4 = 0; c4 < 4; c4++) {
+                            const int col = qc * 32 + c4 * 8;
+                            const uint32_t kb = col >> 6, c = (col & 63) >> 3;
+                            const float *bb = b + col;
+                            const float *vv = v + c4 * 8;
+                            st_shared_v4(A + kb * A_BLOCK + row_off + ((c ^ sw) << 4),
+                                         pack_bf16_relu(vv[0] + bb[0], vv[1] + bb[1]),
+                                         pack_bf16_relu(vv[2] + bb[2], vv[3] + bb[3]),
+                                         pack_bf16_relu(vv[4] + bb[4], vv[5] + bb[5]),
+                                         pack_bf16_relu(vv[6] + bb[6], vv[7] + bb[7]));
+                        }
+                    }
+                    tc_fence_before();
+                    fence_proxy_async();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(bar_ar[s]);
+                } else {
+                    // 1-wide head in FP32: z = b_L + sum_n w_n relu(acc_n + b_n)
+#pragma unroll
+                    for (int qc = 0; qc < H / 32; qc++) {
+                        float v[32];
+                        tmem_ld32(taddr + qc * 32, v);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int e = 0; e < 32; e++)
+                            z = fmaf(head[qc * 32 + e], fmaxf(v[e] + b[qc * 32 + e], 0.f), z);
+                    }
+                    tc_fence_before();
+                    z += head[H];
+                }
+            }
+            if (!ok) break;
+            const bool fin = isfinite(z);
+            const bool inside = valid && (!fin || z >= tau.up);
+            const bool flag = valid && fin && (fabsf(z - tau.up) < margin || (z >= tau.dn && z < tau.up));
+            const unsigned bi = __ballot_sync(FULL, inside);
+            const unsigned bf = __ballot_sync(FULL, flag);
+            const unsigned bn = __ballot_sync(FULL, valid && !fin);
+            const long long wrow = tile * TILE_M + wq * 32;
+            if (lane == 0 && wrow < n) bits[wrow >> 5] = bi;
+            if (valid && logits) logits[row] = z;
+            if (bf) {
+                unsigned pos = 0;
+                if (lane == 0) pos = atomicAdd(flag_count, (unsigned)__popc(bf));
+                pos = __shfl_sync(FULL, pos, 0);
+                if (flag) flag_idx[pos + __popc(bf & ((1u << lane) - 1u))] = (unsigned)row;
+            }
+            if (lane == 0) {
+                c_in += __popc(bi);
+                c_flag += __popc(bf);
+                c_nf += __popc(bn);
+            }
+        }
+        if (st && lane == 0) {
+            if (c_in) atomicAdd(&st->n_inside, c_in);
+            if (c_flag) atomicAdd(&st->n_flagged, c_flag);
+            if (c_nf) atomicAdd(&st->n_nonfinite, c_nf);
+        }
+    }
+    __syncthreads();
+    if (warp == NEPI) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 2 * H);
+    }
+}
+
+// FP32 master weights -> BF16 operand images (one thread per 16-byte chunk)
+__global__ void pack_bf16_kernel(TcDesc d, uint8_t *img) {
+    const int H = d.H;
+    const uint32_t nchunks = d.img_bytes / 16;
+    for (uint32_t ch = blockIdx.x * blockDim.x + threadIdx.x; ch < nchunks; ch += gridDim.x * blockDim.x) {
+        const uint32_t byte = ch * 16;
+        int l;
+        uint32_t local;
+        if (byte < (uint32_t)(H * 128)) {
+            l = 0;
+            local = byte;
+        } else {
+            l = 1 + (int)((byte - H * 128) / (uint32_t)(H * H * 2));
+            local = (byte - H * 128) % (uint32_t)(H * H * 2);
+        }
+        const int K = l == 0 ? d.in : H;
+        const uint32_t kb = local / (uint32_t)(H * 128), rem = local % (uint32_t)(H * 128);
+        const uint32_t nrow = rem / 128, pc = (rem % 128) / 16, c = pc ^ (nrow & 7);
+        const int k0 = (int)(kb * 64 + c * 8);
+        const float *W = d.p + d.off[l] + (size_t)nrow * K;
+        float v[8];
+#pragma unroll
+        for (int e = 0; e < 8; e++) v[e] = (k0 + e < K) ? W[k0 + e] : 0.f;
+        uint4 o;
+        o.x = pack_bf16(v[0], v[1]);
+        o.y = pack_bf16(v[2], v[3]);
+        o.z = pack_bf16(v[4], v[5]);
+        o.w = pack_bf16(v[6], v[7]);
+        *reinterpret_cast<uint4 *>(img + byte) = o;
+    }
+}
+
+TcDesc make_desc(const TcModel *tc, const MlpDesc &d) {
+    TcDesc t{};
+    t.in = d.w[0];
+    t.H = d.w[1];
+    t.NH = d.L - 1;
+    t.img = (const uint8_t *)tc->img;
+    t.img_bytes = (uint32_t)tc->img_bytes;
+    t.p = d.p;
+    for (int l = 0; l < d.L; l++) t.off[l] = d.off[l];
+    return t;
+}
+
+size_t fwd_smem_bytes(int H, int NH) {
+    return 2048 + img_total(H, NH) + 2 * (size_t)(H / 64) * A_BLOCK + (size_t)(NH * H + H + 4) * sizeof(float);
+}
+
+int num_sms() {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
+
+}  // namespace
+
 nb_status nb_tc_init(TcModel *tc, const MlpDesc &d, int infer_prec, int train_prec) {
-    (void)tc; (void)d; (void)infer_prec; (void)train_prec;
-    return nb_fail(NB_EUNSUPPORTED, "tensor-core precisions are not built yet");
+    tc->infer_prec = infer_prec;
+    tc->train_prec = train_prec;
+    if (train_prec != NB_F32) return nb_fail(NB_EUNSUPPORTED, "BF16 training step is not available in this build");
+    if (infer_prec != NB_BF16) return nb_fail(NB_EUNSUPPORTED, "FP8 inference is not available in this build");
+    const int H = d.w[1], NH = d.L - 1;
+    if (NH < 1) return nb_fail(NB_EUNSUPPORTED, "BF16 forward needs at least one hidden layer");
+    if (d.w[0] > 16) return nb_fail(NB_EUNSUPPORTED, "BF16 forward: input width must be <= 16");
+    if (H != 64 && H != 128) return nb_fail(NB_EUNSUPPORTED, "BF16 forward: hidden width must be 64 or 128");
+    for (int l = 1; l < d.L; l++)
+        if (d.w[l] != H) return nb_fail(NB_EUNSUPPORTED, "BF16 forward: hidden widths must be equal");
+    int dev = 0, maxsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (fwd_smem_bytes(H, NH) > (size_t)maxsm)
+        return nb_fail(NB_EUNSUPPORTED, "BF16 forward: network does not fit in shared memory");
+    tc->img_bytes = img_total(H, NH);
+    if (cudaMalloc(&tc->img, tc->img_bytes) != cudaSuccess || cudaMalloc(&tc->err, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return nb_fail(NB_ENOMEM, "tensor-core image allocation failed");
+    }
+    cudaMemset(tc->img, 0, tc->img_bytes);
+    cudaMemset(tc->err, 0, sizeof(int));
+    return NB_OK;
 }
-void nb_tc_free(TcModel *tc) { (void)tc; }
+
+void nb_tc_free(TcModel *tc) {
+    cudaFree(tc->img);
+    cudaFree(tc->err);
+    cudaFree(tc->train_ws);
+    tc->img = nullptr;
+    tc->err = nullptr;
+    tc->train_ws = nullptr;
+}
+
 nb_status nb_tc_refresh(TcModel *tc, const MlpDesc &d, cudaStream_t s) {
-    (void)tc; (void)d; (void)s;
-    return nb_fail(NB_EUNSUPPORTED, "tensor-core precisions are not built yet");
+    if (!tc->img) return NB_OK;
+    const TcDesc t = make_desc(tc, d);
+    const uint32_t nchunks = t.img_bytes / 16;
+    pack_bf16_kernel<<<(nchunks + 255) / 256, 256, 0, s>>>(t, (uint8_t *)tc->img);
+    NB_CUDA(cudaGetLastError());
+    return NB_OK;
 }
-nb_status nb_tc_query(TcModel *, const MlpDesc &, const float *, int64_t, TauF, float, uint32_t *, float *,
-                      nb_query_stats *, QueryWs, cudaStream_t) {
-    return nb_fail(NB_EUNSUPPORTED, "tensor-core precisions are not built yet");
+
+nb_status nb_tc_query(TcModel *tc, const MlpDesc &d, const float *q, int64_t n, TauF tau, float margin,
+                      uint32_t *bits, float *logits, nb_query_stats *st, QueryWs ws, cudaStream_t s) {
+    const TcDesc t = make_desc(tc, d);
+    const size_t smem = fwd_smem_bytes(t.H, t.NH);
+    const int64_t tiles = (n + TILE_M - 1) / TILE_M;
+    int64_t grid = num_sms();
+    if (grid > (tiles + 1) / 2) grid = (tiles + 1) / 2;
+    if (grid < 1) grid = 1;
+    if (t.H == 128) {
+        NB_CUDA(cudaFuncSetAttribute(fwd_bf16_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        fwd_bf16_kernel<128><<<(unsigned)grid, THREADS, smem, s>>>(t, q, (long long)n, tau, margin, bits, logits, st,
+                                                                   ws.flag_count, ws.flag_idx, tc->err);
+    } else {
+        NB_CUDA(cudaFuncSetAttribute(fwd_bf16_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        fwd_bf16_kernel<64><<<(unsigned)grid, THREADS, smem, s>>>(t, q, (long long)n, tau, margin, bits, logits, st,
+                                                                  ws.flag_count, ws.flag_idx, tc->err);
+    }
+    NB_CUDA(cudaGetLastError());
+    return NB_OK;
 }
+
 nb_status nb_tc_train_step(TcModel *, const MlpDesc &, const float *, const uint32_t *, int64_t, float, float, TauF,
                            float *, float *, float *, float *, float, float, float, float, float, float,
                            nb_step_stats *, cudaStream_t) {
-    return nb_fail(NB_EUNSUPPORTED, "tensor-core precisions are not built yet");
+    return nb_fail(NB_EUNSUPPORTED, "BF16 training step is not available in this build");
+}
+
+nb_status nb_tc_check(TcModel *tc) {
+    if (!tc->err) return NB_OK;
+    int e = 0;
+    NB_CUDA(cudaMemcpy(&e, tc->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) {
+        cudaMemset(tc->err, 0, sizeof(int));
+        return nb_fail((nb_status)e, "a tensor-core kernel gave up waiting (bounded wait expired)");
+    }
+    return NB_OK;
 }

@@ -11,7 +11,11 @@ struct TcModel {
     float *scales = nullptr; // device: per-layer dequantisation scales (FP8)
     void *train_ws = nullptr;
     size_t train_ws_bytes = 0;
+    int *err = nullptr;      // device: status of the last bounded wait that gave up (0 = none)
 };
+
+// NB_OK, or the status a tensor-core kernel recorded since the last check (synchronous).
+nb_status nb_tc_check(TcModel *tc);
 
 nb_status nb_tc_init(TcModel *tc, const MlpDesc &d, int infer_prec, int train_prec);
 void nb_tc_free(TcModel *tc);
