@@ -67,7 +67,11 @@ def test_decisions_bit_exact_with_recheck(nb, kind, widths):
         bits, st = m.query(_dev(q), margin=1e-3, stats=True)
         dec = nb.bits_to_numpy(bits, n)
         assert np.array_equal(dec, z64 >= tau), tau
-        assert st["n_unresolved"] == 0
+        # a query whose logit equals tau to ~1e-12 cannot be settled by any bounded
+        # evaluation (tau = the median is one query's own FP64 logit); it is decided
+        # inside, which is the conservative side and agrees with z64 >= tau
+        near = int(np.sum(np.abs(z64 - tau) <= 1e-12 * max(1.0, abs(tau))))
+        assert st["n_unresolved"] <= near
         assert st["n_inside"] == int((z64 >= tau).sum())
 
 
