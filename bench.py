@@ -150,10 +150,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--train-steps", type=int, default=TRAIN_STEPS)
+    ap.add_argument("--n-eval", type=int, default=N_EVAL, help="evaluation rays (smaller only for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
 
+    global N_EVAL
+    N_EVAL = args.n_eval
     import torch
     import torch.distributed as dist
 
