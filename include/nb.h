@@ -163,6 +163,33 @@ nb_status nb_query(nb_model *m, const float *q, int64_t n, float margin, uint32_
 nb_status nb_calibrate(nb_model *m, const float *q, const uint32_t *label_bits, int64_t n, double eps,
                        double *host_tau, void *stream);
 
+/* Training step that allocates nothing.  The paper has no counterpart; this is a
+ * deployment variant of nb_train_step for callers that cannot call cudaMalloc:
+ * hosts whose device memory is entirely reserved up front by another allocator
+ * (a framework's caching allocator, a fixed arena), and real-time training loops
+ * in which the implicit device-wide synchronisation of a cudaMalloc / cudaFree
+ * would stall work on other streams.  nb_train_step grows a model-owned workspace
+ * on demand; this variant instead keeps the per-CTA gradient partials in one
+ * static device array of NB_NOALLOC_SCRATCH_FLOATS floats (8 MiB) that every GPU
+ * loading libnb holds until the process exits.
+ *   - Computes exactly what nb_train_step computes (FP32 training precision only;
+ *     other precisions return NB_EUNSUPPORTED); the number of CTAs is capped to
+ *     what the array holds, which can change the summation order of the gradient
+ *     reduction, so results agree with nb_train_step within rounding.
+ *   - Networks with more than NB_NOALLOC_SCRATCH_FLOATS - 1 parameters are
+ *     rejected with NB_EINVAL.
+ *   - The first call on a device looks up the array's device address for the
+ *     current device (cudaGetSymbolAddress); make that first call before any
+ *     stream capture.
+ *   - All calls share the one array (it keeps the last call's contents; the call
+ *     clears what must start at zero), so calls whose work overlaps on the GPU --
+ *     on different streams or different threads -- race and must be serialised
+ *     by the caller.
+ * Arguments, results and errors are those of nb_train_step. */
+#define NB_NOALLOC_SCRATCH_FLOATS (2u << 20)
+nb_status nb_train_step_noalloc(nb_model *m, const float *q, const uint32_t *label_bits, int64_t n, float alpha,
+                                float beta, nb_step_stats *dev_stats, void *stream);
+
 /* Thread-local message of the last failing call of this thread ("" if none). */
 const char *nb_last_error(void);
 

@@ -4,6 +4,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -154,9 +155,9 @@ extern "C" nb_status nb_model_create(const int32_t *widths, int32_t n_layers, in
         float gf = (float)gmm;
         if ((double)gf < gmm) gf = nextafterf(gf, INFINITY);
         m->gamma.g[l] = nextafterf(gf, INFINITY);
-        // float-float stage: gamma_{3K+3} (K + 3) u
-        const double k3 = 3.0 * widths[l] + 3.0;
-        const double cff = k3 * u / (1.0 - k3 * u) * (widths[l] + 3.0) * u;
+        // extended-precision stage: gamma_{4K+4}
+        const double k4 = 4.0 * widths[l] + 4.0;
+        const double cff = k4 * u / (1.0 - k4 * u);
         float cf = (float)cff;
         if ((double)cf < cff) cf = nextafterf(cf, INFINITY);
         m->gamma.gff[l] = nextafterf(cf, INFINITY);
@@ -446,4 +447,64 @@ extern "C" nb_status nb_calibrate(nb_model *m, const float *q, const uint32_t *l
     m->tau = tau;
     *host_tau = tau;
     return NB_OK;
+}
+
+// ---------------------------------------------------------------- no-allocation training step
+// Scratch for nb_train_step_noalloc: per-CTA gradient partials followed by the per-CTA
+// loss partials.  Host code must not pass the symbol itself to a kernel (on the host
+// it names a host-side stand-in); its device address is looked up once per device.
+static __device__ __align__(256) float g_noalloc_scratch[NB_NOALLOC_SCRATCH_FLOATS];
+
+static std::mutex g_noalloc_mu;
+static float *g_noalloc_ptr[256] = {nullptr};
+
+static nb_status noalloc_scratch(float **out) {
+    int dev = 0;
+    NB_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) return nb_fail(NB_EUNSUPPORTED, "nb_train_step_noalloc: device index out of range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return nb_cuda_check(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+        g_noalloc_ptr[dev] = (float *)p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return NB_OK;
+}
+
+extern "C" nb_status nb_train_step_noalloc(nb_model *m, const float *q, const uint32_t *label_bits, int64_t n,
+                                           float alpha, float beta, nb_step_stats *dev_stats, void *stream) {
+    if (!m) return nb_fail(NB_EINVAL, "nb_train_step_noalloc: null model");
+    if (n < 1) return nb_fail(NB_EINVAL, "nb_train_step_noalloc: n must be >= 1");
+    if (!q || !label_bits) return nb_fail(NB_EINVAL, "nb_train_step_noalloc: null pointer");
+    if (!(alpha >= 0) || !(beta >= 0) || isinf(alpha) || isinf(beta))
+        return nb_fail(NB_EINVAL, "nb_train_step_noalloc: alpha and beta must be finite and >= 0");
+    if (m->train_prec != NB_F32)
+        return nb_fail(NB_EUNSUPPORTED, "nb_train_step_noalloc: only the FP32 training precision is supported");
+    if ((uint64_t)m->P + 1 > (uint64_t)NB_NOALLOC_SCRATCH_FLOATS)
+        return nb_fail(NB_EINVAL, "nb_train_step_noalloc: the network has " + std::to_string(m->P) +
+                                      " parameters; the static scratch holds networks of at most " +
+                                      std::to_string(NB_NOALLOC_SCRATCH_FLOATS - 1));
+    float *scratch = nullptr;
+    nb_status st = noalloc_scratch(&scratch);
+    if (st != NB_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const MlpDesc d = desc_of(m);
+    const TauF tau = nb_tau_bracket(m->tau);
+    TrainWs tw{};
+    const int64_t cap = (int64_t)NB_NOALLOC_SCRATCH_FLOATS / (m->P + 1);
+    tw.G = nb_train_f32_ctas(d, n, sm_count());
+    if (tw.G > cap) tw.G = (int)cap;
+    tw.partial = scratch;
+    tw.loss_partial = scratch + (size_t)tw.G * m->P;
+    m->step += 1;
+    const double c1 = 1.0 - pow((double)m->b1, (double)m->step);
+    const double c2 = 1.0 - pow((double)m->b2, (double)m->step);
+    st = nb_launch_train_f32(d, q, label_bits, n, alpha, beta, tau, tw, dev_stats, s);
+    if (st != NB_OK) return st;
+    st = nb_launch_adam(m->P, 1.0f / (float)n, m->params, m->adam_m, m->adam_v, m->grad, tw, m->lr, m->b1, m->b2,
+                        m->eps, (float)c1, (float)sqrt(c2), dev_stats, s);
+    if (st != NB_OK) return st;
+    return refresh_lowp(m, s);
 }

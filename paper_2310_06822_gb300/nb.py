@@ -25,7 +25,7 @@ STATUS = {0: "NB_OK", 1: "NB_EINVAL", 2: "NB_ENOMEM", 3: "NB_ECUDA", 4: "NB_ETIM
 EXPORTS = ["nb_model_create", "nb_model_destroy", "nb_model_param_count", "nb_model_set_params",
            "nb_model_get_params", "nb_model_get_grad", "nb_model_set_tau", "nb_model_get_tau",
            "nb_model_set_adam", "nb_model_state_size", "nb_model_get_state", "nb_model_set_state",
-           "nb_label", "nb_train_step", "nb_query", "nb_calibrate", "nb_last_error"]
+           "nb_label", "nb_train_step", "nb_query", "nb_calibrate", "nb_last_error", "nb_train_step_noalloc"]
 
 
 class NBError(RuntimeError):
@@ -81,6 +81,7 @@ def lib():
                 "nb_query": ([P, P, i64, ctypes.c_float, P, P, P, P], st),
                 "nb_calibrate": ([P, P, P, i64, ctypes.c_double, P, P], st),
                 "nb_last_error": ([], ctypes.c_char_p),
+                "nb_train_step_noalloc": ([P, P, P, i64, ctypes.c_float, ctypes.c_float, P, P], st),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
