@@ -219,28 +219,46 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// float-float dot product of one neuron: z = b + sum_k W_k (h_k + l_k), exact inputs
-// carrying bounds e_k.  Returns the normalised pair (hi, lo) and a bound on
-// |hi + lo - exact|: c (|b| + sum |W_k|(|h_k| + |l_k|)) + sum |W_k| e_k, with
-// c = gamma_{3K+3} (K + 3) u bounding the rounding of the error accumulator.
-__device__ __forceinline__ void ff_neuron(const float *__restrict__ Wr, float bv, int K, float c, const float *h,
+// Extended-precision dot product of one neuron: z = b + sum_k W_k (h_k + l_k) on
+// inputs given as float pairs (h, l) carrying bounds e_k.  Every product is split
+// exactly (TwoProd) and accumulated in three words s1 + s2 + s3: s1 and s2 by
+// error-free TwoSum chains, s3 (terms of size O(K u^2)) by plain additions.  The
+// result is renormalised to a pair (hi, lo).  s1 + s2 + (exact sum of the s3 terms)
+// equals the exact dot product, so the only roundings are the 4K additions into s3
+// and the last addition lo = t4 + t3.  Bound on |hi + lo - exact|, all evaluated with
+// upward rounding at run time:
+//     gamma_{4K+4} A3 + 2u (|t4| + |t3|) + sum_k |W_k| e_k,
+// A3 = sum of the magnitudes of the terms added into s3, g4 = gamma_{4K+4}.
+__device__ __forceinline__ void ff_neuron(const float *__restrict__ Wr, float bv, int K, float g4, const float *h,
                                           const float *l, const float *e, float &hi, float &lo, float &bound) {
-    float sh = bv, sig = 0.f, T = fabsf(bv), P = 0.f;
+    float s1 = bv, s2 = 0.f, s3 = 0.f, A3 = 0.f, P = 0.f;
     for (int k = 0; k < K; k++) {
         const float w = __ldg(Wr + k), hk = h[k], lk = l[k];
         const float p = __fmul_rn(w, hk);
-        const float qq = fmaf(w, hk, -p);  // w hk = p + qq exactly
-        float tsum, dd;
-        two_sum(sh, p, tsum, dd);
-        sh = tsum;
-        sig = fmaf(w, lk, sig);
-        sig = __fadd_rn(sig, dd);
-        sig = __fadd_rn(sig, qq);
-        T = __fmaf_ru(fabsf(w), __fadd_ru(fabsf(hk), fabsf(lk)), T);
+        const float pq = fmaf(w, hk, -p);  // w hk = p + pq exactly
+        const float r = __fmul_rn(w, lk);
+        const float rq = fmaf(w, lk, -r);  // w lk = r + rq exactly
+        float t, e1, e2, e3, e4;
+        two_sum(s1, p, t, e1);
+        s1 = t;
+        two_sum(s2, e1, t, e2);
+        s2 = t;
+        two_sum(s2, pq, t, e3);
+        s2 = t;
+        two_sum(s2, r, t, e4);
+        s2 = t;
+        s3 = __fadd_rn(s3, e2);
+        s3 = __fadd_rn(s3, e3);
+        s3 = __fadd_rn(s3, e4);
+        s3 = __fadd_rn(s3, rq);
+        A3 = __fadd_ru(A3, __fadd_ru(__fadd_ru(fabsf(e2), fabsf(e3)), __fadd_ru(fabsf(e4), fabsf(rq))));
         P = __fmaf_ru(fabsf(w), e[k], P);
     }
-    two_sum(sh, sig, hi, lo);
-    bound = __fmaf_ru(c, T, P);
+    float t2, t3, t4;
+    two_sum(s2, s3, t2, t3);
+    two_sum(s1, t2, hi, t4);
+    lo = __fadd_rn(t4, t3);
+    bound = __fmaf_ru(g4, A3, __fmaf_ru(2.f * U, __fadd_ru(fabsf(t4), fabsf(t3)), P));
 }
 
 // One warp per query still ambiguous after stage 1.
@@ -269,11 +287,12 @@ __global__ void __launch_bounds__(128) ff_kernel(MlpDesc d, GammaTab gt, const f
             for (int nn = lane; nn < N; nn += 32) {
                 float hi, lo, bd;
                 ff_neuron(W + (size_t)nn * K, __ldg(W + (size_t)N * K + nn), K, gt.gff[ly], h, l, e, hi, lo, bd);
-                if (hi > 0.f) {  // relu(hi + lo): the pair is normalised, so its sign is hi's
+                // relu(hi + lo): |lo| is far below |hi| unless hi = 0, so the sign is hi's
+                if (hi > 0.f) {
                     h2[nn] = hi;
                     l2[nn] = lo;
                 } else {
-                    h2[nn] = 0.f;
+                    h2[nn] = hi == 0.f ? fmaxf(lo, 0.f) : 0.f;
                     l2[nn] = 0.f;
                 }
                 e2[nn] = bd;

@@ -34,7 +34,7 @@ struct MlpDesc {
 
 // Rounding-error constants of the rigorous bounds, rounded up, one per layer:
 //   g[l]   = gamma_{K+8} = k u / (1 - k u), u = 2^-24, k = fan-in K + 8 (FP32 stage)
-//   gff[l] = gamma_{3K+3} (K + 3) u (float-float stage)
+//   gff[l] = gamma_{4K+4} (extended-precision stage)
 struct GammaTab {
     float g[NB_MAXL];
     float gff[NB_MAXL];

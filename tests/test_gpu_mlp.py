@@ -210,3 +210,52 @@ def test_c1_end_to_end_zero_fn_on_grid(nb):
     # the trained bound is much tighter than "everything inside"
     assert fp < 0.5 * int((~yo).sum()), fp
     torch.cuda.synchronize()
+
+
+def test_trained_ray_network_bf16_and_f32_decisions(nb):
+    """3D rays, 64 spheres, 6->128x4->1 trained briefly with the asymmetric ramp:
+    BF16 logits within 2e-2 of the oracle, and decisions of both the BF16 and the
+    FP32 forms equal to the oracle's after calibration (FN = 0)."""
+    import torch
+    widths = [6, 128, 128, 128, 128, 1]
+    sc = I.make_scene(1001, 64, 3, 0.02, 0.2)
+    shape = nb.Shape(sc)
+    trainer, _ = _model(nb, widths, 4001)
+    T, B = 400, 65536
+    pool = _dev(I.sample_queries("ray3", 2018, T * B // 4))
+    bits = nb.label(shape, I.RAY3, pool)
+    per = pool.shape[0] // B
+    for t in range(T):
+        j = t % per
+        trainer.train_step(pool[j * B:(j + 1) * B], bits[j * B // 32:(j + 1) * B // 32], 1.0 + 99.0 * t / (T - 1), 1.0)
+    p = trainer.get_params()
+    n = 200_003
+    q = I.sample_queries("ray3", 2019, n)
+    qd = _dev(q)
+    y = O.label(I.RAY3, q, sc).astype(bool)
+    yd = nb.label(shape, I.RAY3, qd)
+    mb = nb.Model(widths, infer_prec="bf16")
+    mb.set_params(p)
+    tau = mb.calibrate(qd, yd)
+    z64 = O.forward(widths, p, q)
+    bits_b, zb, st = mb.query(qd, margin=0.05, logits=True, stats=True)
+    err = np.abs(zb.cpu().numpy().astype(np.float64) - z64)
+    assert err.max() <= 2e-2, err.max()
+    truth = z64 >= tau
+    tie = np.abs(z64 - tau) <= 1e-12 * max(1.0, abs(tau))
+    db = nb.bits_to_numpy(bits_b, n)
+    assert np.array_equal(db[~tie], truth[~tie])
+    assert not np.any(y & ~db)
+    assert st["n_unresolved"] <= int(tie.sum())
+    mf = nb.Model(widths)
+    mf.set_params(p)
+    mf.tau = tau
+    _, zf = mf.query(qd, logits=True)
+    S = O.forward_scale(widths, p, q)
+    ef = np.abs(zf.cpu().numpy().astype(np.float64) - z64) / np.maximum(np.abs(z64), S)
+    assert ef.max() <= 1e-5
+    # the FP32 form needs a margin above its own logit error
+    m32 = float(4 * np.max(np.abs(zf.cpu().numpy().astype(np.float64) - z64))) + 1e-6
+    df = nb.bits_to_numpy(mf.query(qd, margin=max(m32, 1e-3)), n)
+    assert np.array_equal(df[~tie], truth[~tie])
+    torch.cuda.synchronize()
