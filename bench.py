@@ -36,8 +36,8 @@ N_EVAL = 16 << 20
 MARGIN = 0.05
 MARGIN32 = 1e-2  # FP32 form: re-check band above its own logit error
 SEED_SCENE, SEED_QUERY, SEED_INIT = 1001, 2001, 4001
-METRIC = "neural-bound queries/s at 0 FN (3D rays, BF16 tcgen05 forward + FP32 re-check)"
-WORKLOAD = "3D ray queries: 64-sphere union, MLP 6->128x4->1 BF16, 16M eval rays (configs[1])"
+METRIC = "neural-bound queries/s at 0 FN (3D rays, split-FP16 tcgen05 forward + FP32 re-check)"
+WORKLOAD = "3D ray queries: 64-sphere union, MLP 6->128x4->1, tensor-core 16-bit, 16M eval rays (configs[1])"
 
 
 def peaks():
@@ -209,7 +209,7 @@ def main():
     t_train = time.perf_counter() - t_train0
     params = trainer.get_params()
 
-    model = nb.Model(WIDTHS, infer_prec="bf16", train_prec="f32")
+    model = nb.Model(WIDTHS, infer_prec="f16x3", train_prec="f32")
     model.set_params(params)
     tau = model.calibrate(eval_q, eval_bits, eps=1e-5)
     plain = nb.Model(WIDTHS, infer_prec="f32")
@@ -262,6 +262,26 @@ def main():
     torch.cuda.synchronize()
     f32_ms = e0.elapsed_time(e1) / 3
 
+    # plain single-product BF16 on the same weights: margin = 4x its largest logit
+    # deviation from the FP32 form on the evaluation set
+    bf = nb.Model(WIDTHS, infer_prec="bf16")
+    bf.set_params(params)
+    bf.tau = tau
+    _, zbf = bf.query(eval_q, logits=True)
+    _, z32 = plain.query(eval_q, logits=True)
+    bf_dev = float((zbf - z32).abs().max().item())
+    bf_margin = 4 * bf_dev + 1e-3
+    bbits, bst = bf.query(eval_q, margin=bf_margin, out=out, stats=True)
+    bf_fn = int(np.sum(y & ~nb.bits_to_numpy(bbits, n_eval)))
+    e0.record()
+    for _ in range(5):
+        bf.query(eval_q, margin=bf_margin, out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    bf_ms = e0.elapsed_time(e1) / 5
+    _, zsp = model.query(eval_q, logits=True)
+    split_dev = float((zsp - z32).abs().max().item())
+
     # end to end through the public API: pinned host rays -> device -> bits -> host
     host_q = torch.empty((n_eval, 6), dtype=torch.float32, pin_memory=True)
     host_q.copy_(torch.as_tensor(eval_q_host))
@@ -296,7 +316,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f16x3 (split fp16, fp32 accumulate)", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_eval": n_eval, "batch": BATCH, "train_steps": T, "margin": MARGIN,
                    "l2": "inputs 384 MB per step > 129 MB L2, no flush", "parallelism": f"replicas{world}"},
         "fn": fn, "fp": fp, "fp_rate": fp / n_eval, "positives": int(y.sum()), "tau": tau,
@@ -304,10 +324,13 @@ def main():
         "band": {"flagged": qst["n_flagged"], "resolved_f32": qst["n_resolved_f32"],
                  "resolved_ff": qst["n_resolved_ff"], "unresolved": qst["n_unresolved"]},
         "fp32_plain_queries_per_s": n_eval / (f32_ms / 1000.0),
+        "max_logit_dev_vs_fp32_form": {"f16x3": split_dev, "bf16": bf_dev},
+        "bf16_plain": {"queries_per_s": n_eval / (bf_ms / 1000.0), "margin": bf_margin, "fn": bf_fn,
+                       "flagged": bst["n_flagged"], "unresolved": bst["n_unresolved"]},
         "speedup_vs_fp32_plain": f32_ms / ms,
         "train_samples_per_s_fp32": (BATCH / (train_ms / 1000.0)) if train_ms else None,
         "train_wall_s": t_train,
-        "roofline": {"kernel": "fwd_bf16_kernel (tcgen05)", "bound": "tensor", "achieved": achieved, "peak": peak,
+        "roofline": {"kernel": "fwd_split_kernel (tcgen05, 3 products per k-step)", "bound": "tensor", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                      "peak_kind": f"{pk_kind} bf16 burst", "fwd_ms": fwd_ms,
                      "algorithmic_flops_per_launch": flops},

@@ -51,7 +51,14 @@ typedef enum {
 
 typedef enum { NB_POINT2 = 0, NB_POINT3 = 1, NB_POINT4T = 2, NB_RAY3 = 3, NB_PLANE3 = 4, NB_BOX3 = 5 } nb_kind;
 
-typedef enum { NB_F32 = 0, NB_BF16 = 1, NB_FP8 = 2 } nb_prec;
+/* Arithmetic of the fast forward path:
+ *   NB_F32    FP32 FMA (CUDA cores), the plain single-object form;
+ *   NB_BF16   tcgen05 tensor cores, BF16 operands, FP32 accumulation (one product);
+ *   NB_FP8    tensor cores, FP8 e4m3 operands with per-layer scales;
+ *   NB_F16X3  tcgen05 tensor cores, weights and activations split into FP16 hi + lo
+ *             pairs and three products per layer (hi.hi + hi.lo + lo.hi), FP32
+ *             accumulation: logits within a few FP32 roundings of the FP32 network. */
+typedef enum { NB_F32 = 0, NB_BF16 = 1, NB_FP8 = 2, NB_F16X3 = 3 } nb_prec;
 
 /* Indicator f of Sec. 3.1: a union of closed balls (disks when dim = 2).
  * All values must be integer multiples of 2^-qexp with magnitude below 2^(31-qexp)
@@ -97,8 +104,9 @@ typedef struct nb_model nb_model;
 /* Create a bounding network h (Sec. 3.4 "Architecture"): widths[0] is the query
  * encoding width, widths[1..n_layers-1] the hidden widths (ReLU), widths[n_layers]
  * must be 1 (the logit).  Hidden widths 1..256.  infer_prec selects the nb_query
- * fast path (NB_F32, NB_BF16: tcgen05 tensor cores, hidden widths multiple of 16
- * and <= 256, or NB_FP8).  train_prec selects the training step (NB_F32 or NB_BF16).
+ * fast path (see nb_prec; the tensor-core paths need equal hidden widths of 64 or
+ * 128, an input width <= 16 and weights that fit in shared memory, else
+ * NB_EUNSUPPORTED).  train_prec selects the training step (NB_F32 or NB_BF16).
  * Parameters start at zero; load them with nb_model_set_params.  Adam uses lr 1e-3,
  * betas (0.9, 0.999), eps 1e-8 (Sec. 3.4 "Training"); tau starts at 0, i.e. the
  * sigmoid rounded at 1/2 (Sec. 3.4).  The device is the current CUDA device. */

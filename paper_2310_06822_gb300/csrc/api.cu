@@ -133,7 +133,7 @@ extern "C" nb_status nb_model_create(const int32_t *widths, int32_t n_layers, in
     for (int l = 0; l < n_layers; l++)
         if (widths[l] < 1 || widths[l] > NB_MAXW)
             return nb_fail(NB_EINVAL, "nb_model_create: widths must be 1..256");
-    if (infer_prec < NB_F32 || infer_prec > NB_FP8 || train_prec < NB_F32 || train_prec > NB_BF16)
+    if (infer_prec < NB_F32 || infer_prec > NB_F16X3 || train_prec < NB_F32 || train_prec > NB_BF16)
         return nb_fail(NB_EINVAL, "nb_model_create: bad precision");
     nb_model *m = new nb_model();
     cudaGetDevice(&m->device);

@@ -16,8 +16,11 @@
 #include <cuda_bf16.h>
 
 #include "tc.cuh"
+#include "tc_ptx.cuh"
 
 namespace {
+
+using namespace nbtc;
 
 constexpr int TILE_M = 128;
 constexpr int NEPI = 8;                    // epilogue warps
@@ -40,109 +43,6 @@ __host__ __device__ inline uint32_t img_layer_offset(int H, int l) {
     return l == 0 ? 0u : (uint32_t)(H * 128 + (l - 1) * H * H * 2);
 }
 __host__ __device__ inline uint32_t img_total(int H, int NH) { return img_layer_offset(H, NH); }
-
-// ------------------------------------------------------------------ PTX wrappers
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(bar)
-                 : "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_alloc(uint32_t dst, uint32_t ncols) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst), "r"(ncols) : "memory");
-}
-__device__ __forceinline__ void tmem_relinquish() {
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// D[tmem] (+)= A[smem] x B[smem]^T, kind::f16 (BF16 inputs, FP32 accumulate)
-__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                        uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-
-// 32 consecutive FP32 columns of this thread's TMEM lane
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr)
-        : "memory");
-#pragma unroll
-    for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
-}
-__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
-// two FP32 -> packed BF16x2 (lo in the low half), optionally through ReLU
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-    uint32_t d;
-    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
-    return d;
-}
-__device__ __forceinline__ uint32_t pack_bf16_relu(float lo, float hi) {
-    uint32_t d;
-    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
-    return d;
-}
-__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
-    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major operand in the 128-byte swizzle layout
-// (rows of 128 B, 16-byte chunk c of row r stored at chunk c ^ (r mod 8), 8-row groups
-// 1024 B apart), start address 16-byte granular, base offset 0 (1024-aligned atoms).
-__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-    d |= (uint64_t)1 << 16;             // leading byte offset (unused for swizzled K-major)
-    d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset: 8 rows x 128 B
-    d |= (uint64_t)1 << 46;             // descriptor version for tcgen05
-    d |= (uint64_t)2 << 61;             // 128-byte swizzle
-    return d;
-}
 
 // Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M x N.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
@@ -420,19 +320,21 @@ nb_status nb_tc_init(TcModel *tc, const MlpDesc &d, int infer_prec, int train_pr
     tc->infer_prec = infer_prec;
     tc->train_prec = train_prec;
     if (train_prec != NB_F32) return nb_fail(NB_EUNSUPPORTED, "BF16 training step is not available in this build");
-    if (infer_prec != NB_BF16) return nb_fail(NB_EUNSUPPORTED, "FP8 inference is not available in this build");
+    if (infer_prec != NB_BF16 && infer_prec != NB_F16X3)
+        return nb_fail(NB_EUNSUPPORTED, "FP8 inference is not available in this build");
     const int H = d.w[1], NH = d.L - 1;
-    if (NH < 1) return nb_fail(NB_EUNSUPPORTED, "BF16 forward needs at least one hidden layer");
-    if (d.w[0] > 16) return nb_fail(NB_EUNSUPPORTED, "BF16 forward: input width must be <= 16");
-    if (H != 64 && H != 128) return nb_fail(NB_EUNSUPPORTED, "BF16 forward: hidden width must be 64 or 128");
+    if (NH < 1) return nb_fail(NB_EUNSUPPORTED, "tensor-core forward needs at least one hidden layer");
+    if (d.w[0] > 16) return nb_fail(NB_EUNSUPPORTED, "tensor-core forward: input width must be <= 16");
+    if (H != 64 && H != 128) return nb_fail(NB_EUNSUPPORTED, "tensor-core forward: hidden width must be 64 or 128");
     for (int l = 1; l < d.L; l++)
-        if (d.w[l] != H) return nb_fail(NB_EUNSUPPORTED, "BF16 forward: hidden widths must be equal");
+        if (d.w[l] != H) return nb_fail(NB_EUNSUPPORTED, "tensor-core forward: hidden widths must be equal");
     int dev = 0, maxsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (fwd_smem_bytes(H, NH) > (size_t)maxsm)
-        return nb_fail(NB_EUNSUPPORTED, "BF16 forward: network does not fit in shared memory");
-    tc->img_bytes = img_total(H, NH);
+    const size_t need = infer_prec == NB_BF16 ? fwd_smem_bytes(H, NH) : nb_split_smem_bytes(H, NH);
+    if (need > (size_t)maxsm)
+        return nb_fail(NB_EUNSUPPORTED, "tensor-core forward: the network's weights do not fit in shared memory");
+    tc->img_bytes = infer_prec == NB_BF16 ? img_total(H, NH) : nb_split_img_bytes(H, NH);
     if (cudaMalloc(&tc->img, tc->img_bytes) != cudaSuccess || cudaMalloc(&tc->err, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         return nb_fail(NB_ENOMEM, "tensor-core image allocation failed");
@@ -453,6 +355,7 @@ void nb_tc_free(TcModel *tc) {
 
 nb_status nb_tc_refresh(TcModel *tc, const MlpDesc &d, cudaStream_t s) {
     if (!tc->img) return NB_OK;
+    if (tc->infer_prec == NB_F16X3) return nb_split_refresh(tc, d, s);
     const TcDesc t = make_desc(tc, d);
     const uint32_t nchunks = t.img_bytes / 16;
     pack_bf16_kernel<<<(nchunks + 255) / 256, 256, 0, s>>>(t, (uint8_t *)tc->img);
@@ -462,6 +365,7 @@ nb_status nb_tc_refresh(TcModel *tc, const MlpDesc &d, cudaStream_t s) {
 
 nb_status nb_tc_query(TcModel *tc, const MlpDesc &d, const float *q, int64_t n, TauF tau, float margin,
                       uint32_t *bits, float *logits, nb_query_stats *st, QueryWs ws, cudaStream_t s) {
+    if (tc->infer_prec == NB_F16X3) return nb_split_query(tc, d, q, n, tau, margin, bits, logits, st, ws, s);
     const TcDesc t = make_desc(tc, d);
     const size_t smem = fwd_smem_bytes(t.H, t.NH);
     const int64_t tiles = (n + TILE_M - 1) / TILE_M;

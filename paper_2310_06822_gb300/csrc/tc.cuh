@@ -14,6 +14,13 @@ struct TcModel {
     int *err = nullptr;      // device: status of the last bounded wait that gave up (0 = none)
 };
 
+// split-FP16 forward (tc_split.cu)
+size_t nb_split_img_bytes(int H, int NH);
+size_t nb_split_smem_bytes(int H, int NH);
+nb_status nb_split_refresh(TcModel *tc, const MlpDesc &d, cudaStream_t s);
+nb_status nb_split_query(TcModel *tc, const MlpDesc &d, const float *q, int64_t n, TauF tau, float margin,
+                         uint32_t *bits, float *logits, nb_query_stats *st, QueryWs ws, cudaStream_t s);
+
 // NB_OK, or the status a tensor-core kernel recorded since the last check (synchronous).
 nb_status nb_tc_check(TcModel *tc);
 

@@ -1,0 +1,384 @@
+// Split-FP16 tensor-core forward of the bounding network h (Sec. 3.4 "Architecture").
+//
+// Every weight and every activation is carried as an FP16 pair hi + lo (about 22
+// significant bits), and each layer is evaluated with three tcgen05 products per
+// k-step, W_hi a_hi + W_hi a_lo + W_lo a_hi, accumulated in FP32 in tensor memory.
+// The dropped W_lo a_lo term is ~2^-22 relative, so the logits track the FP32 network
+// to a few FP32 roundings, where a single BF16 product loses ~2^-9 per operand.
+//
+// Data placement (one persistent CTA per SM):
+//   shared memory  the split weight images of every layer, loaded once by the bulk-copy
+//                  (TMA) engine, 128-byte-swizzled K-major (B operands);
+//   tensor memory  per tile slot: the FP32 accumulator (H columns) and the next layer's
+//                  activations as FP16 hi and lo halves (H/2 + H/2 columns), which the
+//                  MMA reads directly as its A operand -- activations never leave the SM.
+// Warp roles as in the BF16 kernel: warps 0-3 and 4-7 are the epilogue groups of tile
+// slots 0 and 1 (one thread per query row = TMEM lane), warp 8 allocates TMEM, loads
+// the weights and issues the MMAs.  Layer 0 takes the input split the same way,
+// A0 = [x_hi | x_lo | x_hi | 0] against B0 = [W_hi | W_hi | W_lo | 0] (K = 64).
+// All waits are bounded; on expiry the kernel records NB_ETIMEOUT, drains the tensor
+// pipe and frees TMEM before returning.
+#include <cuda_fp16.h>
+
+#include "tc.cuh"
+#include "tc_ptx.cuh"
+
+namespace {
+
+using namespace nbtc;
+
+constexpr int TILE_M = 128;
+constexpr int NEPI = 8;
+constexpr int THREADS = (NEPI + 1) * 32;
+constexpr unsigned SPIN_LIMIT = 1u << 22;
+constexpr unsigned FULL = 0xffffffffu;
+
+struct SplitDesc {
+    int in, H, NH;
+    const uint8_t *img;
+    uint32_t img_bytes;
+    const float *p;
+    int off[NB_MAXL];
+};
+
+// layer 0: H rows x 128 B; layer l >= 1: hi image then lo image, each H/64 blocks of
+// H rows x 128 B
+__host__ __device__ inline uint32_t split_off(int H, int l) {
+    return l == 0 ? 0u : (uint32_t)(H * 128 + (l - 1) * 4 * H * H);
+}
+
+struct Ctl {
+    uint64_t wbar, aready[2], accfull[2], drain;
+    uint32_t tmem;
+    int abort;
+};
+
+__device__ bool wait_bounded(uint32_t bar, uint32_t parity, Ctl *ctl, int *err) {
+    for (unsigned i = 0; i < SPIN_LIMIT; i++) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*(volatile int *)&ctl->abort) return false;
+    }
+    *(volatile int *)&ctl->abort = 1;
+    atomicExch(err, NB_ETIMEOUT);
+    return false;
+}
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, Ctl *ctl, int *err) {
+    int ok = 1;
+    if ((threadIdx.x & 31) == 0) ok = wait_bounded(bar, parity, ctl, err) ? 1 : 0;
+    return __shfl_sync(FULL, ok, 0) != 0;
+}
+
+template <int H>
+__global__ void __launch_bounds__(THREADS, 1)
+    fwd_split_kernel(SplitDesc d, const float *__restrict__ q, long long n, TauF tau, float margin,
+                     uint32_t *__restrict__ bits, float *__restrict__ logits, nb_query_stats *st,
+                     unsigned *flag_count, unsigned *flag_idx, int *err) {
+    constexpr uint32_t SLOT_COLS = 2 * H;  // accumulator H + activations H/2 hi + H/2 lo
+    extern __shared__ uint8_t smem_raw[];
+    Ctl *ctl = reinterpret_cast<Ctl *>(smem_raw);
+    uint8_t *Wimg = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023) + 1024;
+    float *bias = reinterpret_cast<float *>(Wimg + d.img_bytes);
+    float *head = bias + d.NH * H;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long ntiles = (n + TILE_M - 1) / TILE_M;
+    const uint32_t bar_w = smem_u32(&ctl->wbar), bar_drain = smem_u32(&ctl->drain);
+    const uint32_t bar_ar[2] = {smem_u32(&ctl->aready[0]), smem_u32(&ctl->aready[1])};
+    const uint32_t bar_af[2] = {smem_u32(&ctl->accfull[0]), smem_u32(&ctl->accfull[1])};
+
+    if (threadIdx.x == 0) {
+        mbar_init(bar_w, 1);
+        mbar_init(bar_ar[0], 4);
+        mbar_init(bar_ar[1], 4);
+        mbar_init(bar_af[0], 1);
+        mbar_init(bar_af[1], 1);
+        mbar_init(bar_drain, 1);
+        ctl->abort = 0;
+        fence_mbar_init();
+    }
+    for (int i = threadIdx.x; i < d.NH * H; i += THREADS) {
+        const int l = i / H, j = i % H;
+        const int K = l == 0 ? d.in : H;
+        bias[i] = d.p[d.off[l] + H * K + j];
+    }
+    for (int i = threadIdx.x; i <= H; i += THREADS) head[i] = d.p[d.off[d.NH] + i];
+    if (warp == NEPI) {
+        tmem_alloc(smem_u32(&ctl->tmem), 2 * SLOT_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = ctl->tmem;
+
+    if (warp == NEPI) {
+        if (lane == 0) {
+            mbar_expect_tx(bar_w, d.img_bytes);
+            for (uint32_t o = 0; o < d.img_bytes; o += 16384)
+                bulk_g2s(smem_u32(Wimg) + o, d.img + o, min(16384u, d.img_bytes - o), bar_w);
+            bool ok = wait_bounded(bar_w, 0, ctl, err);
+            uint32_t ph[2] = {0, 0};
+            constexpr uint32_t idesc = idesc_f16(TILE_M, H);
+            const uint32_t wbase = smem_u32(Wimg);
+            for (long long it = 0; ok; it++) {
+                const bool has[2] = {blockIdx.x + (2 * it) * gridDim.x < ntiles,
+                                     blockIdx.x + (2 * it + 1) * gridDim.x < ntiles};
+                if (!has[0] && !has[1]) break;
+                for (int l = 0; l < d.NH && ok; l++)
+                    for (int s = 0; s < 2 && ok; s++) {
+                        if (!has[s]) continue;
+                        ok = wait_bounded(bar_ar[s], ph[s], ctl, err);
+                        ph[s] ^= 1;
+                        if (!ok) break;
+                        tc_fence_after();
+                        const uint32_t dt = tmem + s * SLOT_COLS;
+                        const uint32_t ahi = dt + H, alo = dt + H + H / 2;
+                        if (l == 0) {
+                            for (int j = 0; j < 4; j++)
+                                mma_f16_ts(dt, ahi + 8 * j, sdesc_sw128(wbase + 32 * j), idesc, j > 0 ? 1u : 0u);
+                        } else {
+                            const uint32_t whi = wbase + split_off(H, l), wlo = whi + 2 * H * H;
+                            for (int j = 0; j < H / 16; j++) {
+                                const uint32_t kb = j >> 2, within = (j & 3) * 32;
+                                const uint64_t bhi = sdesc_sw128(whi + kb * (H * 128) + within);
+                                const uint64_t blo = sdesc_sw128(wlo + kb * (H * 128) + within);
+                                mma_f16_ts(dt, ahi + 8 * j, bhi, idesc, j > 0 ? 1u : 0u);
+                                mma_f16_ts(dt, alo + 8 * j, bhi, idesc, 1u);
+                                mma_f16_ts(dt, ahi + 8 * j, blo, idesc, 1u);
+                            }
+                        }
+                        mma_commit(bar_af[s]);
+                    }
+            }
+            mma_commit(bar_drain);
+            wait_bounded(bar_drain, 0, ctl, err);
+            if (!ok) *(volatile int *)&ctl->abort = 1;
+        }
+        __syncwarp();
+    } else {
+        const int s = warp >> 2, wq = warp & 3;
+        const int r = wq * 32 + lane;
+        const uint32_t trow = tmem + ((uint32_t)(wq * 32) << 16) + s * SLOT_COLS;
+        const uint32_t tD = trow, tAhi = trow + H, tAlo = trow + H + H / 2;
+        uint32_t ph = 0;
+        unsigned long long c_in = 0, c_flag = 0, c_nf = 0;
+        const int in = d.in;
+        float x[16];
+        {
+            const long long tile0 = blockIdx.x + (long long)s * gridDim.x;
+            const long long row0 = tile0 * TILE_M + r;
+#pragma unroll
+            for (int k = 0; k < 16; k++) x[k] = (row0 < n && k < in) ? __ldg(q + row0 * in + k) : 0.f;
+        }
+        for (long long it = 0;; it++) {
+            const long long tile = blockIdx.x + (2 * it + s) * gridDim.x;
+            if (tile >= ntiles) break;
+            const long long row = tile * TILE_M + r;
+            const bool valid = row < n;
+            {
+                // A0 = [x_hi | x_lo | x_hi | 0], 16 FP16 each, two per 32-bit column
+                uint32_t w0[16], w1[16];
+#pragma unroll
+                for (int k = 0; k < 8; k++) {
+                    uint32_t hi, lo;
+                    split_f16x2(x[2 * k], x[2 * k + 1], hi, lo);
+                    w0[k] = hi;
+                    w0[8 + k] = lo;
+                    w1[k] = hi;
+                    w1[8 + k] = 0u;
+                }
+                tmem_st16(tAhi, w0);
+                tmem_st16(tAhi + 16, w1);
+                tmem_st_wait();
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar_ar[s]);
+            {
+                // prefetch the next tile's rows while this tile runs through the layers
+                const long long nrow = (tile + 2 * (long long)gridDim.x) * TILE_M + r;
+#pragma unroll
+                for (int k = 0; k < 16; k++) x[k] = (nrow < n && k < in) ? __ldg(q + nrow * in + k) : 0.f;
+            }
+            bool ok = true;
+            float z = 0.f;
+            for (int l = 0; l < d.NH; l++) {
+                ok = warp_wait(bar_af[s], ph, ctl, err);
+                ph ^= 1;
+                if (!ok) break;
+                tc_fence_after();
+                const float *b = bias + l * H;
+                if (l < d.NH - 1) {
+#pragma unroll
+                    for (int c = 0; c < H / 32; c++) {
+                        float v[32];
+                        tmem_ld32(tD + c * 32, v);
+                        tmem_ld_wait();
+                        uint32_t hi[16], lo[16];
+#pragma unroll
+                        for (int e = 0; e < 16; e++) {
+                            const float a0 = fmaxf(v[2 * e] + b[c * 32 + 2 * e], 0.f);
+                            const float a1 = fmaxf(v[2 * e + 1] + b[c * 32 + 2 * e + 1], 0.f);
+                            split_f16x2(a0, a1, hi[e], lo[e]);
+                        }
+                        tmem_st16(tAhi + c * 16, hi);
+                        tmem_st16(tAlo + c * 16, lo);
+                    }
+                    tmem_st_wait();
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(bar_ar[s]);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < H / 32; c++) {
+                        float v[32];
+                        tmem_ld32(tD + c * 32, v);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int e = 0; e < 32; e++) z = fmaf(head[c * 32 + e], fmaxf(v[e] + b[c * 32 + e], 0.f), z);
+                    }
+                    tc_fence_before();
+                    z += head[H];
+                }
+            }
+            if (!ok) break;
+            const bool fin = isfinite(z);
+            const bool inside = valid && fin && z >= tau.up;
+            // a non-finite fast logit (e.g. an FP16 overflow) goes to the FP32 re-check
+            const bool flag =
+                valid && (!fin || fabsf(z - tau.up) < margin || (z >= tau.dn && z < tau.up));
+            const unsigned bi = __ballot_sync(FULL, inside);
+            const unsigned bf = __ballot_sync(FULL, flag);
+            const unsigned bn = __ballot_sync(FULL, valid && !fin);
+            const long long wrow = tile * TILE_M + wq * 32;
+            if (lane == 0 && wrow < n) bits[wrow >> 5] = bi;
+            if (valid && logits) logits[row] = z;
+            if (bf) {
+                unsigned pos = 0;
+                if (lane == 0) pos = atomicAdd(flag_count, (unsigned)__popc(bf));
+                pos = __shfl_sync(FULL, pos, 0);
+                if (flag) flag_idx[pos + __popc(bf & ((1u << lane) - 1u))] = (unsigned)row;
+            }
+            if (lane == 0) {
+                c_in += __popc(bi);
+                c_flag += __popc(bf);
+                c_nf += __popc(bn);
+            }
+        }
+        if (st && lane == 0) {
+            if (c_in) atomicAdd(&st->n_inside, c_in);
+            if (c_flag) atomicAdd(&st->n_flagged, c_flag);
+            if (c_nf) atomicAdd(&st->n_nonfinite, c_nf);
+        }
+    }
+    __syncthreads();
+    if (warp == NEPI) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 2 * SLOT_COLS);
+    }
+}
+
+// FP32 master weights -> split FP16 operand images (one thread per 16-byte chunk)
+__global__ void pack_split_kernel(SplitDesc d, uint8_t *img) {
+    const int H = d.H;
+    const uint32_t nchunks = d.img_bytes / 16;
+    for (uint32_t ch = blockIdx.x * blockDim.x + threadIdx.x; ch < nchunks; ch += gridDim.x * blockDim.x) {
+        const uint32_t byte = ch * 16;
+        int l, part = 0;  // part 0: hi image, 1: lo image
+        uint32_t local;
+        if (byte < (uint32_t)(H * 128)) {
+            l = 0;
+            local = byte;
+        } else {
+            const uint32_t rel = byte - H * 128;
+            l = 1 + (int)(rel / (uint32_t)(4 * H * H));
+            const uint32_t in_layer = rel % (uint32_t)(4 * H * H);
+            part = in_layer >= (uint32_t)(2 * H * H);
+            local = in_layer % (uint32_t)(2 * H * H);
+        }
+        const int K = l == 0 ? d.in : H;
+        const uint32_t kb = local / (uint32_t)(H * 128), rem = local % (uint32_t)(H * 128);
+        const uint32_t nrow = rem / 128, pc = (rem % 128) / 16, c = pc ^ (nrow & 7);
+        const float *W = d.p + d.off[l] + (size_t)nrow * K;
+        float v[8];
+#pragma unroll
+        for (int e = 0; e < 8; e++) {
+            const int k = (int)(kb * 64 + c * 8) + e;
+            float w = 0.f;
+            int sel = part;  // 0: hi, 1: lo
+            int kk = k;
+            if (l == 0) {  // [W_hi | W_hi | W_lo | 0], 16 columns each
+                kk = k & 15;
+                sel = k < 32 ? 0 : (k < 48 ? 1 : 2);
+            }
+            if (sel < 2 && kk < K) {
+                const float wf = W[kk];
+                const float wh = __half2float(__float2half_rn(wf));
+                w = sel == 0 ? wh : __half2float(__float2half_rn(wf - wh));
+            }
+            v[e] = w;
+        }
+        uint4 o;
+        o.x = pack_f16(v[0], v[1]);
+        o.y = pack_f16(v[2], v[3]);
+        o.z = pack_f16(v[4], v[5]);
+        o.w = pack_f16(v[6], v[7]);
+        *reinterpret_cast<uint4 *>(img + byte) = o;
+    }
+}
+
+SplitDesc make_desc(const TcModel *tc, const MlpDesc &d) {
+    SplitDesc t{};
+    t.in = d.w[0];
+    t.H = d.w[1];
+    t.NH = d.L - 1;
+    t.img = (const uint8_t *)tc->img;
+    t.img_bytes = (uint32_t)tc->img_bytes;
+    t.p = d.p;
+    for (int l = 0; l < d.L; l++) t.off[l] = d.off[l];
+    return t;
+}
+
+int num_sms() {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
+
+}  // namespace
+
+size_t nb_split_img_bytes(int H, int NH) { return split_off(H, NH); }
+
+size_t nb_split_smem_bytes(int H, int NH) {
+    return 2048 + nb_split_img_bytes(H, NH) + (size_t)(NH * H + H + 4) * sizeof(float);
+}
+
+nb_status nb_split_refresh(TcModel *tc, const MlpDesc &d, cudaStream_t s) {
+    const SplitDesc t = make_desc(tc, d);
+    const uint32_t nchunks = t.img_bytes / 16;
+    pack_split_kernel<<<(nchunks + 255) / 256, 256, 0, s>>>(t, (uint8_t *)tc->img);
+    NB_CUDA(cudaGetLastError());
+    return NB_OK;
+}
+
+nb_status nb_split_query(TcModel *tc, const MlpDesc &d, const float *q, int64_t n, TauF tau, float margin,
+                         uint32_t *bits, float *logits, nb_query_stats *st, QueryWs ws, cudaStream_t s) {
+    const SplitDesc t = make_desc(tc, d);
+    const size_t smem = nb_split_smem_bytes(t.H, t.NH);
+    const int64_t tiles = (n + TILE_M - 1) / TILE_M;
+    int64_t grid = num_sms();
+    if (grid > (tiles + 1) / 2) grid = (tiles + 1) / 2;
+    if (grid < 1) grid = 1;
+    if (t.H == 128) {
+        NB_CUDA(cudaFuncSetAttribute(fwd_split_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        fwd_split_kernel<128><<<(unsigned)grid, THREADS, smem, s>>>(t, q, (long long)n, tau, margin, bits, logits,
+                                                                    st, ws.flag_count, ws.flag_idx, tc->err);
+    } else {
+        NB_CUDA(cudaFuncSetAttribute(fwd_split_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        fwd_split_kernel<64><<<(unsigned)grid, THREADS, smem, s>>>(t, q, (long long)n, tau, margin, bits, logits, st,
+                                                                   ws.flag_count, ws.flag_idx, tc->err);
+    }
+    NB_CUDA(cudaGetLastError());
+    return NB_OK;
+}

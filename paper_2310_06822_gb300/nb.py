@@ -16,8 +16,8 @@ import torch
 from . import build as _build
 from .inputs import ENC_WIDTH, POINT2, POINT4T
 
-NB_F32, NB_BF16, NB_FP8 = 0, 1, 2
-PREC = {"f32": NB_F32, "bf16": NB_BF16, "fp8": NB_FP8}
+NB_F32, NB_BF16, NB_FP8, NB_F16X3 = 0, 1, 2, 3
+PREC = {"f32": NB_F32, "bf16": NB_BF16, "fp8": NB_FP8, "f16x3": NB_F16X3}
 STATUS = {0: "NB_OK", 1: "NB_EINVAL", 2: "NB_ENOMEM", 3: "NB_ECUDA", 4: "NB_ETIMEOUT", 5: "NB_ENUMERIC",
           6: "NB_EUNSUPPORTED"}
 

@@ -234,7 +234,7 @@ def test_trained_ray_network_bf16_and_f32_decisions(nb):
     qd = _dev(q)
     y = O.label(I.RAY3, q, sc).astype(bool)
     yd = nb.label(shape, I.RAY3, qd)
-    mb = nb.Model(widths, infer_prec="bf16")
+    mb = nb.Model(widths, infer_prec="f16x3")
     mb.set_params(p)
     tau = mb.calibrate(qd, yd)
     z64 = O.forward(widths, p, q)
@@ -247,6 +247,14 @@ def test_trained_ray_network_bf16_and_f32_decisions(nb):
     assert np.array_equal(db[~tie], truth[~tie])
     assert not np.any(y & ~db)
     assert st["n_unresolved"] <= int(tie.sum())
+    # plain single-product BF16: decisions exact with a margin above its measured error
+    m16 = nb.Model(widths, infer_prec="bf16")
+    m16.set_params(p)
+    m16.tau = tau
+    _, z16 = m16.query(qd, logits=True)
+    e16 = float(np.max(np.abs(z16.cpu().numpy().astype(np.float64) - z64)))
+    d16 = nb.bits_to_numpy(m16.query(qd, margin=4 * e16 + 1e-3), n)
+    assert np.array_equal(d16[~tie], truth[~tie])
     mf = nb.Model(widths)
     mf.set_params(p)
     mf.tau = tau
