@@ -36,6 +36,9 @@ N_EVAL = 16 << 20
 MARGIN = 0.05
 MARGIN32 = 1e-2  # FP32 form: re-check band above its own logit error
 SEED_SCENE, SEED_QUERY, SEED_INIT = 1001, 2001, 4001
+# DRAM bytes (read + write) per ray of the forward kernel, from one ncu capture of
+# fwd_split_kernel at 1,048,576 rays (25,459,968 bytes); None once the kernel changes
+TRAFFIC_BYTES_PER_RAY = 25459968 / 1048576
 METRIC = "neural-bound queries/s at 0 FN (3D rays, split-FP16 tcgen05 forward + FP32 re-check)"
 WORKLOAD = "3D ray queries: 64-sphere union, MLP 6->128x4->1, tensor-core 16-bit, 16M eval rays (configs[1])"
 
@@ -331,7 +334,8 @@ def main():
         "train_samples_per_s_fp32": (BATCH / (train_ms / 1000.0)) if train_ms else None,
         "train_wall_s": t_train,
         "roofline": {"kernel": "fwd_split_kernel (tcgen05, 3 products per k-step)", "bound": "tensor", "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": (TRAFFIC_BYTES_PER_RAY * n_eval) if TRAFFIC_BYTES_PER_RAY else None,
                      "peak_kind": f"{pk_kind} bf16 burst", "fwd_ms": fwd_ms,
                      "algorithmic_flops_per_launch": flops},
         "cpu_baseline": {"value": cpu_v, "unit": "queries/s", "cores": cores, "kind": "oracle",
