@@ -171,6 +171,57 @@ nb_status nb_query(nb_model *m, const float *q, int64_t n, float margin, uint32_
 nb_status nb_calibrate(nb_model *m, const float *q, const uint32_t *label_bits, int64_t n, double eps,
                        double *host_tau, void *stream);
 
+/* ------------------------------------------------------- grouped launches
+ * Many objects, one bounding network each (the paper trains one network per object and
+ * rearranges objects without retraining, Sec. 2), all of one architecture, trained and
+ * queried in one persistent launch per call.  The queries of all objects are concatenated
+ * into one array: object o owns rows [offsets[o], offsets[o+1]).  A plan splits every
+ * object's rows into work items of at most chunk_rows rows; grouped calls walk the items.
+ * Per-object counts may be uneven.  Gradients are reduced per object in item order, so a
+ * step does not depend on scheduling. */
+typedef struct nb_plan nb_plan;
+typedef struct nb_group nb_group;
+
+/* host_offsets[0..n_objects], non-decreasing, total rows < 2^32.  chunk_rows: multiple of
+ * 64, 0 = 4096.  Grouped queries additionally need every offsets[o] to be a multiple of 32
+ * (each object's decision bits then start at a word).  Synchronous. */
+nb_status nb_plan_create(const int64_t *host_offsets, int32_t n_objects, int32_t chunk_rows, nb_plan **out);
+nb_status nb_plan_destroy(nb_plan *p);
+
+/* widths as for nb_model_create; infer_prec NB_F32 or NB_F16X3; train_prec NB_F32. */
+nb_status nb_group_create(const int32_t *widths, int32_t n_layers, int32_t n_objects, int32_t infer_prec,
+                          int32_t train_prec, nb_group **out);
+nb_status nb_group_destroy(nb_group *g);
+int64_t nb_group_param_count(const nb_group *g); /* P of one object */
+/* n_objects * P FP32 values, object-major; set resets Adam.  Synchronous. */
+nb_status nb_group_set_params(nb_group *g, const float *host_params, int64_t n);
+nb_status nb_group_get_params(const nb_group *g, float *host_params, int64_t n);
+nb_status nb_group_get_grad(const nb_group *g, float *host_grad, int64_t n);
+nb_status nb_group_set_tau(nb_group *g, const double *host_tau, int32_t n_objects);
+nb_status nb_group_get_tau(const nb_group *g, double *host_tau, int32_t n_objects);
+/* Device-side schedule for training loops captured in a CUDA graph: alpha[t] for the
+ * next T steps (and the matching Adam bias corrections) live on the device and a device
+ * step counter advances every step, so nb_train_step_grouped(..., alpha = -1, ...) needs
+ * no host argument that changes between steps.  nb_group_sync_schedule copies the device
+ * counter back to the host's step count (synchronous). */
+nb_status nb_group_set_schedule(nb_group *g, const float *host_alpha, int32_t T);
+nb_status nb_group_sync_schedule(nb_group *g);
+/* Grows the group's workspace for the plan now (synchronous), so that later grouped calls
+ * with this plan allocate nothing and can be captured in a CUDA graph. */
+nb_status nb_group_reserve(nb_group *g, const nb_plan *plan);
+/* One training step of every object on its rows (nb_train_step per object, in one
+ * launch).  alpha < 0 takes alpha and the bias corrections from the device schedule.
+ * dev_stats: loss = mean over objects of each object's mean loss; counts summed. */
+nb_status nb_train_step_grouped(nb_group *g, const nb_plan *plan, const float *q, const uint32_t *label_bits,
+                                float alpha, float beta, nb_step_stats *dev_stats, void *stream);
+/* Decisions of every object's network on its rows against its threshold, with the margin
+ * band re-checked in extended precision (as nb_query).  out_bits covers all rows. */
+nb_status nb_query_grouped(nb_group *g, const nb_plan *plan, const float *q, float margin, uint32_t *out_bits,
+                           float *opt_logits, nb_query_stats *dev_stats, void *stream);
+/* nb_calibrate per object on its rows; host_tau[n_objects] receives the thresholds. */
+nb_status nb_calibrate_grouped(nb_group *g, const nb_plan *plan, const float *q, const uint32_t *label_bits,
+                               double eps, double *host_tau, void *stream);
+
 /* Training step that allocates nothing.  The paper has no counterpart; this is a
  * deployment variant of nb_train_step for callers that cannot call cudaMalloc:
  * hosts whose device memory is entirely reserved up front by another allocator

@@ -54,6 +54,39 @@ TauF nb_tau_bracket(double tau) {
     return t;
 }
 
+void nb_fill_gamma(const int *widths, int L, GammaTab *gt) {
+    // gamma_k = k u / (1 - k u), u = 2^-24, computed in double, then rounded up to float:
+    // k = fan-in + 8 roundings per term (FP32 stage), k = 4 fan-in + 4 (extended stage)
+    const double u = ldexp(1.0, -24);
+    for (int l = 0; l < L; l++) {
+        const double k = widths[l] + 8.0, gmm = k * u / (1.0 - k * u);
+        float gf = (float)gmm;
+        if ((double)gf < gmm) gf = nextafterf(gf, INFINITY);
+        gt->g[l] = nextafterf(gf, INFINITY);
+        const double k4 = 4.0 * widths[l] + 4.0, cff = k4 * u / (1.0 - k4 * u);
+        float cf = (float)cff;
+        if ((double)cf < cff) cf = nextafterf(cf, INFINITY);
+        gt->gff[l] = nextafterf(cf, INFINITY);
+    }
+}
+
+double nb_tau_from_min_bits(unsigned long long zmin_bits, unsigned npos, double eps) {
+    if (npos == 0) return INFINITY;
+    if (zmin_bits == 0ull) return -INFINITY;  // a positive query had a NaN logit: everything is inside
+    const unsigned long long u =
+        (zmin_bits & 0x8000000000000000ull) ? (zmin_bits & 0x7fffffffffffffffull) : ~zmin_bits;
+    double zmin;
+    memcpy(&zmin, &u, 8);
+    // tau = zmin - eps rounded toward -infinity; volatile operands keep the subtraction
+    // between the two rounding-mode switches
+    volatile double va = zmin, vb = eps;
+    const int old = fegetround();
+    fesetround(FE_DOWNWARD);
+    volatile double t = va - vb;
+    fesetround(old);
+    return t;
+}
+
 // ---------------------------------------------------------------- model
 struct nb_model {
     int device = 0;
@@ -147,21 +180,7 @@ extern "C" nb_status nb_model_create(const int32_t *widths, int32_t n_layers, in
     m->P = o;
     m->infer_prec = infer_prec;
     m->train_prec = train_prec;
-    // gamma_k = k u / (1 - k u), u = 2^-24, with k = fan-in + 8 roundings per term; computed
-    // in double, then rounded up to float
-    for (int l = 0; l < n_layers; l++) {
-        const double u = ldexp(1.0, -24), k = widths[l] + 8.0;
-        const double gmm = k * u / (1.0 - k * u);
-        float gf = (float)gmm;
-        if ((double)gf < gmm) gf = nextafterf(gf, INFINITY);
-        m->gamma.g[l] = nextafterf(gf, INFINITY);
-        // extended-precision stage: gamma_{4K+4}
-        const double k4 = 4.0 * widths[l] + 4.0;
-        const double cff = k4 * u / (1.0 - k4 * u);
-        float cf = (float)cff;
-        if ((double)cf < cff) cf = nextafterf(cf, INFINITY);
-        m->gamma.gff[l] = nextafterf(cf, INFINITY);
-    }
+    nb_fill_gamma(m->widths, n_layers, &m->gamma);
     const size_t pb = (size_t)m->P * sizeof(float);
     if (cudaMalloc(&m->params, pb) != cudaSuccess || cudaMalloc(&m->adam_m, pb) != cudaSuccess ||
         cudaMalloc(&m->adam_v, pb) != cudaSuccess || cudaMalloc(&m->grad, pb) != cudaSuccess) {
@@ -418,7 +437,7 @@ extern "C" nb_status nb_calibrate(nb_model *m, const float *q, const uint32_t *l
     ws.npos = (unsigned *)((char *)m->ws + 128);
     ws.pos_idx = (unsigned *)((char *)m->ws + head);
     ws.lo = (float *)((char *)m->ws + head + list);
-    st = nb_launch_calibrate(desc_of(m), m->gamma, q, label_bits, n, ws, s);
+    st = nb_launch_calibrate(desc_of(m), m->gamma, q, label_bits, 0, n, ws, s);
     if (st != NB_OK) return st;
     unsigned long long h[2] = {0, 0};
     unsigned npos = 0;
@@ -426,24 +445,7 @@ extern "C" nb_status nb_calibrate(nb_model *m, const float *q, const uint32_t *l
     NB_CUDA(cudaMemcpyAsync(&npos, ws.npos, 4, cudaMemcpyDeviceToHost, s));
     NB_CUDA(cudaStreamSynchronize(s));
     h[1] = npos;
-    double tau;
-    if (h[1] == 0) {
-        tau = INFINITY;
-    } else if (h[0] == 0ull) {
-        tau = -INFINITY;  // a positive query had a NaN logit: everything is inside
-    } else {
-        const unsigned long long u = (h[0] & 0x8000000000000000ull) ? (h[0] & 0x7fffffffffffffffull) : ~h[0];
-        double zmin;
-        memcpy(&zmin, &u, 8);
-        // tau = zmin - eps rounded toward -infinity; volatile operands keep the
-        // subtraction between the two rounding-mode switches
-        volatile double va = zmin, vb = eps;
-        const int old = fegetround();
-        fesetround(FE_DOWNWARD);
-        volatile double t = va - vb;
-        fesetround(old);
-        tau = t;
-    }
+    const double tau = nb_tau_from_min_bits(h[0], (unsigned)h[1], eps);
     m->tau = tau;
     *host_tau = tau;
     return NB_OK;

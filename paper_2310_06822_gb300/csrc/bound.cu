@@ -262,9 +262,13 @@ __device__ __forceinline__ void ff_neuron(const float *__restrict__ Wr, float bv
 }
 
 // One warp per query still ambiguous after stage 1.
-__global__ void __launch_bounds__(128) ff_kernel(MlpDesc d, GammaTab gt, const float *__restrict__ q, TauF tau,
+// Grouped form: when `offsets` is given, query i belongs to the object o with
+// offsets[o] <= i < offsets[o+1], whose parameters start at d.p + o * P and whose
+// threshold is taus[o].
+__global__ void __launch_bounds__(128) ff_kernel(MlpDesc d, GammaTab gt, const float *__restrict__ q, TauF tau0,
                                                  const unsigned *ff_count, const unsigned *ff_idx, uint32_t *bits,
-                                                 nb_query_stats *st) {
+                                                 nb_query_stats *st, const long long *offsets, int n_objects,
+                                                 long long P, const TauF *taus) {
     __shared__ float sh_[4][3][2][NB_MAXW];  // [warp][h,l,e][buffer][k]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned cnt = *ff_count;
@@ -272,6 +276,17 @@ __global__ void __launch_bounds__(128) ff_kernel(MlpDesc d, GammaTab gt, const f
     long long dinside = 0;
     for (unsigned f = blockIdx.x * 4 + warp; f < cnt; f += gridDim.x * 4) {
         const unsigned i = ff_idx[f];
+        MlpDesc dd = d;
+        TauF tau = tau0;
+        if (offsets) {
+            int lo_o = 0, hi_o = n_objects - 1;  // last object whose first row is <= i
+            while (lo_o < hi_o) {
+                const int mid = (lo_o + hi_o + 1) >> 1;
+                if (offsets[mid] <= (long long)i) lo_o = mid; else hi_o = mid - 1;
+            }
+            dd.p = d.p + (size_t)lo_o * P;
+            tau = taus[lo_o];
+        }
         float *h = sh_[warp][0][0], *l = sh_[warp][1][0], *e = sh_[warp][2][0];
         float *h2 = sh_[warp][0][1], *l2 = sh_[warp][1][1], *e2 = sh_[warp][2][1];
         const float *x = q + (size_t)i * d.w[0];
@@ -283,7 +298,7 @@ __global__ void __launch_bounds__(128) ff_kernel(MlpDesc d, GammaTab gt, const f
         __syncwarp();
         for (int ly = 0; ly < d.L - 1; ly++) {
             const int K = d.w[ly], N = d.w[ly + 1];
-            const float *W = d.p + d.off[ly];
+            const float *W = dd.p + dd.off[ly];
             for (int nn = lane; nn < N; nn += 32) {
                 float hi, lo, bd;
                 ff_neuron(W + (size_t)nn * K, __ldg(W + (size_t)N * K + nn), K, gt.gff[ly], h, l, e, hi, lo, bd);
@@ -310,7 +325,7 @@ __global__ void __launch_bounds__(128) ff_kernel(MlpDesc d, GammaTab gt, const f
         }
         if (lane == 0) {
             const int K = d.w[d.L - 1];
-            const float *W = d.p + d.off[d.L - 1];
+            const float *W = dd.p + dd.off[d.L - 1];
             float zh, zl, B;
             ff_neuron(W, __ldg(W + K), K, gt.gff[d.L - 1], h, l, e, zh, zl, B);
             // D = z - tau in float-float: (s, ee) = zh - tau_hi exactly, t = (zl - tau_lo) + ee
@@ -346,14 +361,14 @@ __global__ void __launch_bounds__(128) ff_kernel(MlpDesc d, GammaTab gt, const f
 
 // ---------------------------------------------------------------- calibration helpers
 // list of the indices whose label bit is 1
-__global__ void compact_positive_kernel(const uint32_t *__restrict__ labels, long long n, unsigned *count,
-                                        unsigned *idx) {
+__global__ void compact_positive_kernel(const uint32_t *__restrict__ labels, long long row0, long long row1,
+                                        unsigned *count, unsigned *idx) {
     const int lane = threadIdx.x & 31;
-    const long long nw = (n + 31) / 32;
+    const long long nw = (row1 - row0 + 31) / 32;
     for (long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nw;
          w += ((long long)gridDim.x * blockDim.x) >> 5) {
-        const long long i = w * 32 + lane;
-        const bool pos = i < n && ((labels[w] >> lane) & 1u);
+        const long long i = row0 + w * 32 + lane;
+        const bool pos = i < row1 && ((labels[i >> 5] >> (i & 31)) & 1u);
         const unsigned b = __ballot_sync(FULL, pos);
         if (!b) continue;
         unsigned base = 0;
@@ -460,13 +475,28 @@ nb_status nb_launch_recheck(const MlpDesc &d, const GammaTab &gt, const float *q
     int64_t grid = num_sms() * 4;
     if (grid > (n + 3) / 4) grid = (n + 3) / 4;
     if (grid < 1) grid = 1;
-    ff_kernel<<<(unsigned)grid, 128, 0, s>>>(d, gt, q, tau, ws.ff_count, ws.ff_idx, bits, st);
+    ff_kernel<<<(unsigned)grid, 128, 0, s>>>(d, gt, q, tau, ws.ff_count, ws.ff_idx, bits, st, nullptr, 0, 0, nullptr);
+    NB_CUDA(cudaGetLastError());
+    return NB_OK;
+}
+
+nb_status nb_launch_recheck_grouped(const MlpDesc &d, const GammaTab &gt, const float *q, const long long *offsets,
+                                    int n_objects, long long P, const TauF *taus, uint32_t *bits, nb_query_stats *st,
+                                    QueryWs ws, int64_t n, cudaStream_t s) {
+    // the flagged queries of several objects go straight to the extended-precision stage
+    int64_t grid = num_sms() * 4;
+    if (grid > (n + 3) / 4) grid = (n + 3) / 4;
+    if (grid < 1) grid = 1;
+    TauF none{};
+    ff_kernel<<<(unsigned)grid, 128, 0, s>>>(d, gt, q, none, ws.flag_count, ws.flag_idx, bits, st, offsets, n_objects,
+                                             P, taus);
     NB_CUDA(cudaGetLastError());
     return NB_OK;
 }
 
 nb_status nb_launch_calibrate(const MlpDesc &d, const GammaTab &gt, const float *q, const uint32_t *labels,
-                              int64_t n, CalibWs ws, cudaStream_t s) {
+                              int64_t row0, int64_t row1, CalibWs ws, cudaStream_t s) {
+    const int64_t n = row1 - row0;
     NB_CUDA(cudaMemsetAsync(ws.umin_bits, 0xff, sizeof(unsigned), s));
     NB_CUDA(cudaMemsetAsync(ws.zmin_bits, 0xff, sizeof(unsigned long long), s));
     NB_CUDA(cudaMemsetAsync(ws.npos, 0, sizeof(unsigned), s));
@@ -474,7 +504,8 @@ nb_status nb_launch_calibrate(const MlpDesc &d, const GammaTab &gt, const float 
     const int64_t need = (n + 255) / 256;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
-    compact_positive_kernel<<<(unsigned)grid, 256, 0, s>>>(labels, (long long)n, ws.npos, ws.pos_idx);
+    compact_positive_kernel<<<(unsigned)grid, 256, 0, s>>>(labels, (long long)row0, (long long)row1, ws.npos,
+                                                             ws.pos_idx);
     NB_CUDA(cudaGetLastError());
     TauF none{};
     nb_status r = tile_dispatch<1>(d, gt, q, none, ws.npos, ws.pos_idx, n, nullptr, nullptr, nullptr, nullptr, ws.lo,

@@ -47,6 +47,10 @@ struct TauF {
     float hi, lo, err;
 };
 TauF nb_tau_bracket(double tau);
+void nb_fill_gamma(const int *widths, int L, GammaTab *gt);
+// tau = (minimum positive FP64 logit, given as order-preserving bits) - eps, rounded
+// toward -infinity; +inf without positives, -inf if a positive had a NaN logit
+double nb_tau_from_min_bits(unsigned long long zmin_bits, unsigned npos, double eps);
 
 // ---------------------------------------------------------------- launchers (per .cu)
 nb_status nb_launch_label(const nb_shape *shape, int kind, const float *q, int64_t n, uint32_t *bits,
@@ -72,7 +76,10 @@ struct CalibWs {
     float *lo;                        // [n] lower bound of each listed positive
 };
 nb_status nb_launch_calibrate(const MlpDesc &d, const GammaTab &gt, const float *q, const uint32_t *labels,
-                              int64_t n, CalibWs ws, cudaStream_t s);
+                              int64_t row0, int64_t row1, CalibWs ws, cudaStream_t s);
+nb_status nb_launch_recheck_grouped(const MlpDesc &d, const GammaTab &gt, const float *q, const long long *offsets,
+                                    int n_objects, long long P, const TauF *taus, uint32_t *bits, nb_query_stats *st,
+                                    QueryWs ws, int64_t n, cudaStream_t s);
 
 struct TrainWs {
     float *partial;          // [G][P] per-CTA gradient partials

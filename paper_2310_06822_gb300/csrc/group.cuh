@@ -1,0 +1,58 @@
+// Internal definitions of the grouped (many-object) launches.
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+#include "tc.cuh"
+
+// One work item: rows [row0, row1) of the concatenated query array, all of object obj.
+struct PlanItem {
+    int obj;
+    int pad;
+    long long row0, row1;
+};
+
+struct nb_plan {
+    int n_objects = 0;
+    int n_items = 0;
+    int chunk = 0;
+    int64_t n_rows = 0;
+    bool aligned = true;                 // every object's first row is a multiple of 32
+    PlanItem *items = nullptr;           // device [n_items], object-major
+    int *obj_items = nullptr;            // device [n_objects + 1]: items of object o
+    long long *offsets = nullptr;        // device [n_objects + 1]
+    std::vector<int64_t> h_offsets;
+    std::vector<int> h_obj_items;
+};
+
+struct nb_group {
+    int L = 0, n_objects = 0;
+    int widths[NB_MAXL + 1] = {0};
+    int off[NB_MAXL] = {0};
+    int64_t P = 0;
+    int infer_prec = NB_F32, train_prec = NB_F32;
+    float *params = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;  // [n_objects][P]
+    std::vector<double> tau;
+    TauF *d_tau = nullptr;               // device [n_objects]
+    GammaTab gamma{};
+    float lr = 1e-3f, b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    int64_t step = 0;
+    // device-side schedule for graph-captured step loops
+    float *sched_alpha = nullptr, *sched_c1 = nullptr, *sched_sqrt_c2 = nullptr;
+    int sched_T = 0;
+    int64_t sched_base = 0;
+    int *d_step = nullptr;
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    TcModel tc{};                        // split-FP16 images of every object
+};
+
+MlpDesc nb_group_desc(const nb_group *g);
+
+// split-FP16 grouped queries (tc_split.cu)
+nb_status nb_tc_group_init(TcModel *tc, const MlpDesc &d, int n_objects);
+nb_status nb_tc_group_refresh(TcModel *tc, const MlpDesc &d, int n_objects, cudaStream_t s);
+nb_status nb_tc_group_query(TcModel *tc, const MlpDesc &d, int64_t P, const nb_plan *pl, const float *q,
+                            const TauF *taus, float margin, uint32_t *bits, float *logits, nb_query_stats *st,
+                            QueryWs ws, cudaStream_t s);

@@ -278,8 +278,11 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
 }
 
-// FP32 master weights -> split FP16 operand images (one thread per 16-byte chunk)
-__global__ void pack_split_kernel(SplitDesc d, uint8_t *img) {
+// FP32 master weights -> split FP16 operand images (one thread per 16-byte chunk);
+// blockIdx.y selects the object of a group (parameters at o * P, image at o * img_bytes)
+__global__ void pack_split_kernel(SplitDesc d, uint8_t *img, long long P) {
+    d.p += (size_t)blockIdx.y * P;
+    img += (size_t)blockIdx.y * d.img_bytes;
     const int H = d.H;
     const uint32_t nchunks = d.img_bytes / 16;
     for (uint32_t ch = blockIdx.x * blockDim.x + threadIdx.x; ch < nchunks; ch += gridDim.x * blockDim.x) {
@@ -357,7 +360,7 @@ size_t nb_split_smem_bytes(int H, int NH) {
 nb_status nb_split_refresh(TcModel *tc, const MlpDesc &d, cudaStream_t s) {
     const SplitDesc t = make_desc(tc, d);
     const uint32_t nchunks = t.img_bytes / 16;
-    pack_split_kernel<<<(nchunks + 255) / 256, 256, 0, s>>>(t, (uint8_t *)tc->img);
+    pack_split_kernel<<<(nchunks + 255) / 256, 256, 0, s>>>(t, (uint8_t *)tc->img, 0);
     NB_CUDA(cudaGetLastError());
     return NB_OK;
 }
@@ -378,6 +381,348 @@ nb_status nb_split_query(TcModel *tc, const MlpDesc &d, const float *q, int64_t 
         NB_CUDA(cudaFuncSetAttribute(fwd_split_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         fwd_split_kernel<64><<<(unsigned)grid, THREADS, smem, s>>>(t, q, (long long)n, tau, margin, bits, logits, st,
                                                                    ws.flag_count, ws.flag_idx, tc->err);
+    }
+    NB_CUDA(cudaGetLastError());
+    return NB_OK;
+}
+
+// ------------------------------------------------------------------ grouped queries
+// One persistent launch over the work items of a plan (rows of one object each).  A CTA
+// keeps one object's split weights, biases and head in shared memory and reloads them
+// only when its next item belongs to another object.  Item hand-off between the MMA warp
+// and the epilogue warps uses two more mbarriers (item ready / item done); every wait
+// is bounded like the per-layer ones.
+#include "group.cuh"
+
+namespace {
+
+struct GCtl {
+    uint64_t wbar, aready[2], accfull[2], drain, item_ready, item_done;
+    uint32_t tmem;
+    int abort;
+};
+
+__device__ bool gwait(uint32_t bar, uint32_t parity, GCtl *ctl, int *err) {
+    for (unsigned i = 0; i < SPIN_LIMIT; i++) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*(volatile int *)&ctl->abort) return false;
+    }
+    *(volatile int *)&ctl->abort = 1;
+    atomicExch(err, NB_ETIMEOUT);
+    return false;
+}
+__device__ __forceinline__ bool gwarp_wait(uint32_t bar, uint32_t parity, GCtl *ctl, int *err) {
+    int ok = 1;
+    if ((threadIdx.x & 31) == 0) ok = gwait(bar, parity, ctl, err) ? 1 : 0;
+    return __shfl_sync(FULL, ok, 0) != 0;
+}
+
+template <int H>
+__global__ void __launch_bounds__(THREADS, 1)
+    fwd_split_group_kernel(SplitDesc d, long long P, const PlanItem *__restrict__ items, int n_items,
+                           const TauF *__restrict__ taus, const float *__restrict__ q, float margin,
+                           uint32_t *__restrict__ bits, float *__restrict__ logits, nb_query_stats *st,
+                           unsigned *flag_count, unsigned *flag_idx, int *err) {
+    constexpr uint32_t SLOT_COLS = 2 * H;
+    extern __shared__ uint8_t smem_raw[];
+    GCtl *ctl = reinterpret_cast<GCtl *>(smem_raw);
+    uint8_t *Wimg = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023) + 1024;
+    float *bias = reinterpret_cast<float *>(Wimg + d.img_bytes);
+    float *head = bias + d.NH * H;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t bar_w = smem_u32(&ctl->wbar), bar_drain = smem_u32(&ctl->drain);
+    const uint32_t bar_ready = smem_u32(&ctl->item_ready), bar_done = smem_u32(&ctl->item_done);
+    const uint32_t bar_ar[2] = {smem_u32(&ctl->aready[0]), smem_u32(&ctl->aready[1])};
+    const uint32_t bar_af[2] = {smem_u32(&ctl->accfull[0]), smem_u32(&ctl->accfull[1])};
+    if (threadIdx.x == 0) {
+        mbar_init(bar_w, 1);
+        mbar_init(bar_ar[0], 4);
+        mbar_init(bar_ar[1], 4);
+        mbar_init(bar_af[0], 1);
+        mbar_init(bar_af[1], 1);
+        mbar_init(bar_drain, 1);
+        mbar_init(bar_ready, 1);
+        mbar_init(bar_done, NEPI);
+        ctl->abort = 0;
+        fence_mbar_init();
+    }
+    if (warp == NEPI) {
+        tmem_alloc(smem_u32(&ctl->tmem), 2 * SLOT_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = ctl->tmem;
+
+    if (warp == NEPI) {
+        uint32_t ph_ar[2] = {0, 0}, ph_w = 0, ph_done = 0, ph_drain = 0;
+        int cur_obj = -1;
+        bool ok = true;
+        constexpr uint32_t idesc = idesc_f16(TILE_M, H);
+        const uint32_t wbase = smem_u32(Wimg);
+        for (int k = blockIdx.x; ok && k < n_items; k += gridDim.x) {
+            const PlanItem it = items[k];
+            if (k != (int)blockIdx.x) {
+                ok = gwarp_wait(bar_done, ph_done, ctl, err);
+                ph_done ^= 1;
+                if (!ok) break;
+            }
+            if (it.obj != cur_obj) {
+                if (cur_obj >= 0) {  // the previous object's MMAs are done with its weights
+                    if (lane == 0) mma_commit(bar_drain);
+                    ok = gwarp_wait(bar_drain, ph_drain, ctl, err);
+                    ph_drain ^= 1;
+                    if (!ok) break;
+                }
+                const float *pp = d.p + (size_t)it.obj * P;
+                for (int i = lane; i < d.NH * H; i += 32) {
+                    const int l = i / H, j = i % H;
+                    bias[i] = pp[d.off[l] + H * (l == 0 ? d.in : H) + j];
+                }
+                for (int i = lane; i <= H; i += 32) head[i] = pp[d.off[d.NH] + i];
+                if (lane == 0) {
+                    const uint8_t *src = d.img + (size_t)it.obj * d.img_bytes;
+                    mbar_expect_tx(bar_w, d.img_bytes);
+                    for (uint32_t o = 0; o < d.img_bytes; o += 16384)
+                        bulk_g2s(wbase + o, src + o, min(16384u, d.img_bytes - o), bar_w);
+                }
+                ok = gwarp_wait(bar_w, ph_w, ctl, err);
+                ph_w ^= 1;
+                if (!ok) break;
+                cur_obj = it.obj;
+            }
+            __threadfence_block();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar_ready);
+            const long long nt = (it.row1 - it.row0 + TILE_M - 1) / TILE_M;
+            int okl = 1;
+            if (lane == 0) {
+                for (long long tp = 0; okl; tp++) {
+                    const bool has[2] = {2 * tp < nt, 2 * tp + 1 < nt};
+                    if (!has[0] && !has[1]) break;
+                    for (int l = 0; l < d.NH && okl; l++)
+                        for (int s = 0; s < 2 && okl; s++) {
+                            if (!has[s]) continue;
+                            okl = gwait(bar_ar[s], ph_ar[s], ctl, err);
+                            ph_ar[s] ^= 1;
+                            if (!okl) break;
+                            tc_fence_after();
+                            const uint32_t dt = tmem + s * SLOT_COLS;
+                            const uint32_t ahi = dt + H, alo = dt + H + H / 2;
+                            if (l == 0) {
+                                for (int j = 0; j < 4; j++)
+                                    mma_f16_ts(dt, ahi + 8 * j, sdesc_sw128(wbase + 32 * j), idesc, j > 0 ? 1u : 0u);
+                            } else {
+                                const uint32_t whi = wbase + split_off(H, l), wlo = whi + 2 * H * H;
+                                for (int j = 0; j < H / 16; j++) {
+                                    const uint32_t kb = j >> 2, within = (j & 3) * 32;
+                                    const uint64_t bhi = sdesc_sw128(whi + kb * (H * 128) + within);
+                                    const uint64_t blo = sdesc_sw128(wlo + kb * (H * 128) + within);
+                                    mma_f16_ts(dt, ahi + 8 * j, bhi, idesc, j > 0 ? 1u : 0u);
+                                    mma_f16_ts(dt, alo + 8 * j, bhi, idesc, 1u);
+                                    mma_f16_ts(dt, ahi + 8 * j, blo, idesc, 1u);
+                                }
+                            }
+                            mma_commit(bar_af[s]);
+                        }
+                }
+            }
+            ok = __shfl_sync(FULL, okl, 0) != 0;
+        }
+        if (lane == 0) {
+            mma_commit(bar_drain);
+            gwait(bar_drain, ph_drain, ctl, err);
+            if (!ok) *(volatile int *)&ctl->abort = 1;
+        }
+        __syncwarp();
+    } else {
+        const int s = warp >> 2, wq = warp & 3;
+        const int r = wq * 32 + lane;
+        const uint32_t trow = tmem + ((uint32_t)(wq * 32) << 16) + s * SLOT_COLS;
+        const uint32_t tD = trow, tAhi = trow + H, tAlo = trow + H + H / 2;
+        const int in = d.in;
+        uint32_t ph_acc = 0, ph_ready = 0;
+        unsigned long long c_in = 0, c_flag = 0, c_nf = 0;
+        bool ok = true;
+        for (int k = blockIdx.x; ok && k < n_items; k += gridDim.x) {
+            const PlanItem it = items[k];
+            ok = gwarp_wait(bar_ready, ph_ready, ctl, err);
+            ph_ready ^= 1;
+            if (!ok) break;
+            const TauF tau = taus[it.obj];
+            const long long nt = (it.row1 - it.row0 + TILE_M - 1) / TILE_M;
+            float x[16];
+            {
+                const long long row0 = it.row0 + (long long)s * TILE_M + r;
+#pragma unroll
+                for (int kk = 0; kk < 16; kk++) x[kk] = (row0 < it.row1 && kk < in) ? __ldg(q + row0 * in + kk) : 0.f;
+            }
+            for (long long tp = 0; ok && 2 * tp + s < nt; tp++) {
+                const long long trow0 = it.row0 + (2 * tp + s) * TILE_M;
+                const long long row = trow0 + r;
+                const bool valid = row < it.row1;
+                {
+                    uint32_t w0[16], w1[16];
+#pragma unroll
+                    for (int kk = 0; kk < 8; kk++) {
+                        uint32_t hi, lo;
+                        split_f16x2(x[2 * kk], x[2 * kk + 1], hi, lo);
+                        w0[kk] = hi;
+                        w0[8 + kk] = lo;
+                        w1[kk] = hi;
+                        w1[8 + kk] = 0u;
+                    }
+                    tmem_st16(tAhi, w0);
+                    tmem_st16(tAhi + 16, w1);
+                    tmem_st_wait();
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(bar_ar[s]);
+                {
+                    const long long nrow = trow0 + 2 * TILE_M + r;
+#pragma unroll
+                    for (int kk = 0; kk < 16; kk++)
+                        x[kk] = (nrow < it.row1 && kk < in) ? __ldg(q + nrow * in + kk) : 0.f;
+                }
+                float z = 0.f;
+                for (int l = 0; l < d.NH; l++) {
+                    ok = gwarp_wait(bar_af[s], ph_acc, ctl, err);
+                    ph_acc ^= 1;
+                    if (!ok) break;
+                    tc_fence_after();
+                    const float *b = bias + l * H;
+                    if (l < d.NH - 1) {
+#pragma unroll
+                        for (int c = 0; c < H / 32; c++) {
+                            float v[32];
+                            tmem_ld32(tD + c * 32, v);
+                            tmem_ld_wait();
+                            uint32_t hi[16], lo[16];
+#pragma unroll
+                            for (int e = 0; e < 16; e++) {
+                                const float a0 = fmaxf(v[2 * e] + b[c * 32 + 2 * e], 0.f);
+                                const float a1 = fmaxf(v[2 * e + 1] + b[c * 32 + 2 * e + 1], 0.f);
+                                split_f16x2(a0, a1, hi[e], lo[e]);
+                            }
+                            tmem_st16(tAhi + c * 16, hi);
+                            tmem_st16(tAlo + c * 16, lo);
+                        }
+                        tmem_st_wait();
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(bar_ar[s]);
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < H / 32; c++) {
+                            float v[32];
+                            tmem_ld32(tD + c * 32, v);
+                            tmem_ld_wait();
+#pragma unroll
+                            for (int e = 0; e < 32; e++)
+                                z = fmaf(head[c * 32 + e], fmaxf(v[e] + b[c * 32 + e], 0.f), z);
+                        }
+                        tc_fence_before();
+                        z += head[H];
+                    }
+                }
+                if (!ok) break;
+                const bool fin = isfinite(z);
+                const bool inside = valid && fin && z >= tau.up;
+                const bool flag = valid && (!fin || fabsf(z - tau.up) < margin || (z >= tau.dn && z < tau.up));
+                const unsigned bi = __ballot_sync(FULL, inside);
+                const unsigned bf = __ballot_sync(FULL, flag);
+                const unsigned bn = __ballot_sync(FULL, valid && !fin);
+                const long long wrow = trow0 + wq * 32;
+                if (lane == 0 && wrow < it.row1) bits[wrow >> 5] = bi;
+                if (valid && logits) logits[row] = z;
+                if (bf) {
+                    unsigned pos = 0;
+                    if (lane == 0) pos = atomicAdd(flag_count, (unsigned)__popc(bf));
+                    pos = __shfl_sync(FULL, pos, 0);
+                    if (flag) flag_idx[pos + __popc(bf & ((1u << lane) - 1u))] = (unsigned)row;
+                }
+                if (lane == 0) {
+                    c_in += __popc(bi);
+                    c_flag += __popc(bf);
+                    c_nf += __popc(bn);
+                }
+            }
+            if (!ok) break;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar_done);
+        }
+        if (st && lane == 0) {
+            if (c_in) atomicAdd(&st->n_inside, c_in);
+            if (c_flag) atomicAdd(&st->n_flagged, c_flag);
+            if (c_nf) atomicAdd(&st->n_nonfinite, c_nf);
+        }
+    }
+    __syncthreads();
+    if (warp == NEPI) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 2 * SLOT_COLS);
+    }
+}
+
+}  // namespace
+
+nb_status nb_tc_group_init(TcModel *tc, const MlpDesc &d, int n_objects) {
+    tc->infer_prec = NB_F16X3;
+    tc->train_prec = NB_F32;
+    const int H = d.w[1], NH = d.L - 1;
+    if (NH < 1) return nb_fail(NB_EUNSUPPORTED, "tensor-core forward needs at least one hidden layer");
+    if (d.w[0] > 16) return nb_fail(NB_EUNSUPPORTED, "tensor-core forward: input width must be <= 16");
+    if (H != 64 && H != 128) return nb_fail(NB_EUNSUPPORTED, "tensor-core forward: hidden width must be 64 or 128");
+    for (int l = 1; l < d.L; l++)
+        if (d.w[l] != H) return nb_fail(NB_EUNSUPPORTED, "tensor-core forward: hidden widths must be equal");
+    int dev = 0, maxsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (nb_split_smem_bytes(H, NH) > (size_t)maxsm)
+        return nb_fail(NB_EUNSUPPORTED, "tensor-core forward: the network's weights do not fit in shared memory");
+    tc->img_bytes = nb_split_img_bytes(H, NH);
+    if (cudaMalloc(&tc->img, tc->img_bytes * (size_t)n_objects) != cudaSuccess ||
+        cudaMalloc(&tc->err, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return nb_fail(NB_ENOMEM, "tensor-core image allocation failed");
+    }
+    cudaMemset(tc->err, 0, sizeof(int));
+    return NB_OK;
+}
+
+nb_status nb_tc_group_refresh(TcModel *tc, const MlpDesc &d, int n_objects, cudaStream_t s) {
+    const SplitDesc t = make_desc(tc, d);
+    long long P = 0;
+    for (int l = 0; l < d.L; l++) P += (long long)d.w[l + 1] * (d.w[l] + 1);
+    const uint32_t nchunks = t.img_bytes / 16;
+    pack_split_kernel<<<dim3((nchunks + 255) / 256, n_objects), 256, 0, s>>>(t, (uint8_t *)tc->img, P);
+    NB_CUDA(cudaGetLastError());
+    return NB_OK;
+}
+
+nb_status nb_tc_group_query(TcModel *tc, const MlpDesc &d, int64_t P, const nb_plan *pl, const float *q,
+                            const TauF *taus, float margin, uint32_t *bits, float *logits, nb_query_stats *st,
+                            QueryWs ws, cudaStream_t s) {
+    const SplitDesc t = make_desc(tc, d);
+    const size_t smem = nb_split_smem_bytes(t.H, t.NH);
+    int grid = num_sms();
+    if (grid > pl->n_items) grid = pl->n_items;
+    if (grid < 1) return NB_OK;
+    if (t.H == 128) {
+        NB_CUDA(cudaFuncSetAttribute(fwd_split_group_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+        fwd_split_group_kernel<128><<<grid, THREADS, smem, s>>>(t, (long long)P, pl->items, pl->n_items, taus, q,
+                                                                margin, bits, logits, st, ws.flag_count, ws.flag_idx,
+                                                                tc->err);
+    } else {
+        NB_CUDA(cudaFuncSetAttribute(fwd_split_group_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+        fwd_split_group_kernel<64><<<grid, THREADS, smem, s>>>(t, (long long)P, pl->items, pl->n_items, taus, q,
+                                                               margin, bits, logits, st, ws.flag_count, ws.flag_idx,
+                                                               tc->err);
     }
     NB_CUDA(cudaGetLastError());
     return NB_OK;

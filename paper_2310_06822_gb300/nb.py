@@ -25,7 +25,11 @@ STATUS = {0: "NB_OK", 1: "NB_EINVAL", 2: "NB_ENOMEM", 3: "NB_ECUDA", 4: "NB_ETIM
 EXPORTS = ["nb_model_create", "nb_model_destroy", "nb_model_param_count", "nb_model_set_params",
            "nb_model_get_params", "nb_model_get_grad", "nb_model_set_tau", "nb_model_get_tau",
            "nb_model_set_adam", "nb_model_state_size", "nb_model_get_state", "nb_model_set_state",
-           "nb_label", "nb_train_step", "nb_query", "nb_calibrate", "nb_last_error", "nb_train_step_noalloc"]
+           "nb_label", "nb_train_step", "nb_query", "nb_calibrate", "nb_last_error", "nb_train_step_noalloc",
+           "nb_plan_create", "nb_plan_destroy", "nb_group_create", "nb_group_destroy", "nb_group_param_count",
+           "nb_group_set_params", "nb_group_get_params", "nb_group_get_grad", "nb_group_set_tau", "nb_group_get_tau",
+           "nb_group_set_schedule", "nb_group_sync_schedule", "nb_group_reserve", "nb_train_step_grouped",
+           "nb_query_grouped", "nb_calibrate_grouped"]
 
 
 class NBError(RuntimeError):
@@ -82,6 +86,22 @@ def lib():
                 "nb_calibrate": ([P, P, P, i64, ctypes.c_double, P, P], st),
                 "nb_last_error": ([], ctypes.c_char_p),
                 "nb_train_step_noalloc": ([P, P, P, i64, ctypes.c_float, ctypes.c_float, P, P], st),
+                "nb_plan_create": ([P, i32, i32, P], st),
+                "nb_plan_destroy": ([P], st),
+                "nb_group_create": ([P, i32, i32, i32, i32, P], st),
+                "nb_group_destroy": ([P], st),
+                "nb_group_param_count": ([P], i64),
+                "nb_group_set_params": ([P, P, i64], st),
+                "nb_group_get_params": ([P, P, i64], st),
+                "nb_group_get_grad": ([P, P, i64], st),
+                "nb_group_set_tau": ([P, P, i32], st),
+                "nb_group_get_tau": ([P, P, i32], st),
+                "nb_group_set_schedule": ([P, P, i32], st),
+                "nb_group_sync_schedule": ([P], st),
+                "nb_group_reserve": ([P, P], st),
+                "nb_train_step_grouped": ([P, P, P, P, ctypes.c_float, ctypes.c_float, P, P], st),
+                "nb_query_grouped": ([P, P, P, ctypes.c_float, P, P, P, P], st),
+                "nb_calibrate_grouped": ([P, P, P, P, ctypes.c_double, P, P], st),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -238,6 +258,118 @@ class Model:
         return t.value
 
 
+class Plan:
+    """Work items over concatenated per-object rows (nb_plan)."""
+
+    def __init__(self, offsets, chunk_rows: int = 0):
+        off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+        self.offsets = off
+        self.n_objects = len(off) - 1
+        self.n_rows = int(off[-1])
+        h = ctypes.c_void_p()
+        _check(lib().nb_plan_create(off.ctypes.data_as(ctypes.c_void_p), self.n_objects, int(chunk_rows),
+                                    ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().nb_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Group:
+    """n_objects bounding networks of one architecture (nb_group)."""
+
+    def __init__(self, widths, n_objects: int, infer_prec="f32", train_prec="f32"):
+        self.widths = [int(w) for w in widths]
+        self.n_objects = int(n_objects)
+        ip = PREC[infer_prec] if isinstance(infer_prec, str) else int(infer_prec)
+        tp = PREC[train_prec] if isinstance(train_prec, str) else int(train_prec)
+        w = (ctypes.c_int32 * len(self.widths))(*self.widths)
+        h = ctypes.c_void_p()
+        _check(lib().nb_group_create(w, len(self.widths) - 1, self.n_objects, ip, tp, ctypes.byref(h)))
+        self._h = h
+        self.P = int(lib().nb_group_param_count(h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().nb_group_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(np.asarray(p, dtype=np.float32).ravel())
+        _check(lib().nb_group_set_params(self._h, p.ctypes.data_as(ctypes.c_void_p), p.size))
+
+    def get_params(self) -> np.ndarray:
+        p = np.zeros(self.P * self.n_objects, dtype=np.float32)
+        _check(lib().nb_group_get_params(self._h, p.ctypes.data_as(ctypes.c_void_p), p.size))
+        return p.reshape(self.n_objects, self.P)
+
+    def get_grad(self) -> np.ndarray:
+        g = np.zeros(self.P * self.n_objects, dtype=np.float32)
+        _check(lib().nb_group_get_grad(self._h, g.ctypes.data_as(ctypes.c_void_p), g.size))
+        return g.reshape(self.n_objects, self.P)
+
+    @property
+    def tau(self) -> np.ndarray:
+        t = np.zeros(self.n_objects, dtype=np.float64)
+        _check(lib().nb_group_get_tau(self._h, t.ctypes.data_as(ctypes.c_void_p), self.n_objects))
+        return t
+
+    @tau.setter
+    def tau(self, v):
+        t = np.ascontiguousarray(np.broadcast_to(np.asarray(v, dtype=np.float64), (self.n_objects,)))
+        _check(lib().nb_group_set_tau(self._h, t.ctypes.data_as(ctypes.c_void_p), self.n_objects))
+
+    def set_schedule(self, alpha):
+        a = np.ascontiguousarray(np.asarray(alpha, dtype=np.float32))
+        _check(lib().nb_group_set_schedule(self._h, a.ctypes.data_as(ctypes.c_void_p), a.size))
+
+    def sync_schedule(self):
+        _check(lib().nb_group_sync_schedule(self._h))
+
+    def reserve(self, plan: Plan):
+        _check(lib().nb_group_reserve(self._h, plan._h))
+
+    def train_step(self, plan: Plan, q, label_bits, alpha: float, beta: float = 1.0, stats=None, stream=None):
+        _check(lib().nb_train_step_grouped(self._h, plan._h, _ptr(q), _ptr(label_bits), float(alpha), float(beta),
+                                           _ptr(stats), _stream(stream)))
+
+    def query(self, plan: Plan, q, margin: float = 0.0, out=None, logits: bool = False, stats: bool = False,
+              stream=None):
+        n = plan.n_rows
+        if out is None:
+            out = torch.empty(n_words(n), dtype=torch.int32, device=q.device)
+        lg = torch.empty(n, dtype=torch.float32, device=q.device) if logits else None
+        st = torch.empty(QUERY_STATS.itemsize, dtype=torch.uint8, device=q.device) if stats else None
+        _check(lib().nb_query_grouped(self._h, plan._h, _ptr(q), float(margin), _ptr(out), _ptr(lg), _ptr(st),
+                                      _stream(stream)))
+        res = [out]
+        if logits:
+            res.append(lg)
+        if stats:
+            res.append(_read(st, QUERY_STATS))
+        return res[0] if len(res) == 1 else tuple(res)
+
+    def calibrate(self, plan: Plan, q, label_bits, eps: float = 1e-5, stream=None) -> np.ndarray:
+        t = np.zeros(self.n_objects, dtype=np.float64)
+        _check(lib().nb_calibrate_grouped(self._h, plan._h, _ptr(q), _ptr(label_bits), float(eps),
+                                          t.ctypes.data_as(ctypes.c_void_p), _stream(stream)))
+        return t
+
+
 def step_stats_tensor(device="cuda") -> torch.Tensor:
     return torch.zeros(STEP_STATS.itemsize, dtype=torch.uint8, device=device)
 
@@ -259,4 +391,4 @@ def enc_width(kind: int) -> int:
     return ENC_WIDTH[kind]
 
 
-__all__ = ["Model", "Shape", "label", "lib", "NBError", "EXPORTS", "POINT2", "POINT4T"]
+__all__ = ["Model", "Group", "Plan", "Shape", "label", "lib", "NBError", "EXPORTS", "POINT2", "POINT4T"]

@@ -1,0 +1,198 @@
+"""Grouped launches (many objects, one network each, uneven sample counts) against the
+oracle per object: gradients, loss, calibration, decisions of the FP32 and split-FP16
+grouped queries, CUDA-graph replay of a scheduled training loop, and a small 4D
+space-time configuration end to end."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2310_06822_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nb():
+    from paper_2310_06822_gb300 import nb as _nb
+    _nb.lib()
+    return _nb
+
+
+def _dev(x):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(x), device="cuda")
+
+
+def _objects(kind, n_obj, counts, seed, S=(16, 64), moving=False):
+    scenes, qs = [], []
+    rng = np.random.default_rng(seed)
+    for o in range(n_obj):
+        scenes.append(I.make_scene(seed + 10 * o, int(rng.integers(S[0], S[1] + 1)), 3, 0.02, 0.2, moving=moving))
+        qs.append(I.sample_queries(kind, seed + 10 * o + 1, counts[o]))
+    off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    return scenes, qs, off
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def test_grouped_train_step_matches_oracle_per_object(nb):
+    widths = [4, 64, 64, 64, 1]
+    counts = [4096, 777, 9000, 33, 2048]
+    scenes, qs, off = _objects("point4t", 5, counts, 100, moving=True)
+    ys = [O.label(I.POINT4T, q, sc) for q, sc in zip(qs, scenes)]
+    q = np.concatenate(qs)
+    y = np.concatenate(ys)
+    g = nb.Group(widths, 5)
+    P = g.P
+    p0 = np.stack([I.init_params(200 + o, widths) for o in range(5)])
+    g.set_params(p0)
+    plan = nb.Plan(off, chunk_rows=1024)
+    st = nb.step_stats_tensor()
+    g.train_step(plan, _dev(q), _dev(I.pack_bits(y).view(np.int32)), 25.0, 1.0, stats=st)
+    grad = g.get_grad().astype(np.float64)
+    losses = []
+    for o in range(5):
+        loss64, g64 = O.loss_grad(widths, p0[o], qs[o], ys[o], 25.0, 1.0)
+        losses.append(loss64)
+        assert _rel(grad[o], g64) <= 1e-4, o
+    s = nb.read_step_stats(st)
+    assert abs(s["loss"] - np.mean(losses)) <= 1e-5 * np.mean(losses)
+    # Adam per object on its gradient
+    p1 = g.get_params().astype(np.float64)
+    for o in range(5):
+        th = p0[o].astype(np.float64)
+        O.adam(th, np.zeros_like(th), np.zeros_like(th), grad[o], 1)
+        assert np.max(np.abs(p1[o] - th)) <= 1e-6
+
+
+def test_grouped_step_equals_single_object_steps(nb):
+    widths = [6, 32, 32, 1]
+    counts = [2048, 512, 1500]
+    scenes, qs, off = _objects("ray3", 3, counts, 300)
+    ys = [O.label(I.RAY3, q, sc) for q, sc in zip(qs, scenes)]
+    g = nb.Group(widths, 3)
+    p0 = np.stack([I.init_params(400 + o, widths) for o in range(3)])
+    g.set_params(p0)
+    plan = nb.Plan(off, chunk_rows=512)
+    g.train_step(plan, _dev(np.concatenate(qs)), _dev(I.pack_bits(np.concatenate(ys)).view(np.int32)), 7.0)
+    pg = g.get_params()
+    for o in range(3):
+        m = nb.Model(widths)
+        m.set_params(p0[o])
+        m.train_step(_dev(qs[o]), _dev(I.pack_bits(ys[o]).view(np.int32)), 7.0)
+        # same arithmetic, different summation order of the gradient partials
+        assert np.max(np.abs(m.get_params() - pg[o])) <= 2e-6
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16x3"])
+def test_grouped_calibrate_and_query(nb, prec):
+    widths = [6, 128, 128, 128, 1] if prec == "f16x3" else [6, 64, 64, 1]
+    counts = [8192, 4096, 12800, 64, 20000, 4096]
+    scenes, qs, off = _objects("ray3", 6, counts, 500)
+    ys = [O.label(I.RAY3, q, sc) for q, sc in zip(qs, scenes)]
+    q = np.concatenate(qs)
+    g = nb.Group(widths, 6, infer_prec=prec)
+    p0 = np.stack([(I.init_params(600 + o, widths) * 2.0).astype(np.float32) for o in range(6)])
+    g.set_params(p0)
+    plan = nb.Plan(off, chunk_rows=2048)
+    qd = _dev(q)
+    bd = _dev(I.pack_bits(np.concatenate(ys)).view(np.int32))
+    taus = g.calibrate(plan, qd, bd)
+    bits, z, st = g.query(plan, qd, margin=0.05, logits=True, stats=True)
+    dec = nb.bits_to_numpy(bits, len(q))
+    z = z.cpu().numpy().astype(np.float64)
+    for o in range(6):
+        z64 = O.forward(widths, p0[o], qs[o])
+        tau_o, npos = O.calibrate(z64, ys[o], 1e-5)
+        assert npos == int(ys[o].sum())
+        if npos:
+            assert abs(taus[o] - tau_o) <= 1e-12 * max(1.0, abs(tau_o))
+        else:
+            assert taus[o] == float("inf")
+        sl = slice(off[o], off[o + 1])
+        tie = np.abs(z64 - taus[o]) <= 1e-12 * max(1.0, abs(taus[o]))
+        assert np.array_equal(dec[sl][~tie], (z64 >= taus[o])[~tie]), o
+        assert not np.any(ys[o].astype(bool) & ~dec[sl])
+        assert np.max(np.abs(z[sl] - z64)) <= 2e-2
+    assert st["n_unresolved"] == 0
+
+
+def test_graph_captured_scheduled_training_equals_eager(nb):
+    import torch
+    widths = [4, 64, 64, 64, 1]
+    counts = [4096, 8192, 4096, 12288]
+    scenes, qs, off = _objects("point4t", 4, counts, 700, moving=True)
+    y = np.concatenate([O.label(I.POINT4T, q, sc) for q, sc in zip(qs, scenes)])
+    qd = _dev(np.concatenate(qs))
+    bd = _dev(I.pack_bits(y).view(np.int32))
+    p0 = np.stack([I.init_params(800 + o, widths) for o in range(4)])
+    T = 12
+    alpha = (1.0 + 99.0 * np.arange(T) / (T - 1)).astype(np.float32)
+    plan = nb.Plan(off, chunk_rows=4096)
+    eager = nb.Group(widths, 4)
+    eager.set_params(p0)
+    for t in range(T):
+        eager.train_step(plan, qd, bd, float(alpha[t]))
+    ge = nb.Group(widths, 4)
+    ge.set_params(p0)
+    ge.set_schedule(alpha)
+    ge.reserve(plan)
+    ge.train_step(plan, qd, bd, -1.0)  # first step eagerly (kernel attributes, lazy init)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s):
+            ge.train_step(plan, qd, bd, -1.0)
+    torch.cuda.current_stream().wait_stream(s)
+    for _ in range(T - 1):
+        graph.replay()
+    torch.cuda.synchronize()
+    ge.sync_schedule()
+    assert np.array_equal(ge.get_params(), eager.get_params())
+
+
+def test_grouped_4d_end_to_end_zero_fn(nb):
+    """8 objects of 16-64 spheres moving over t in [0,1], one 4->64x3->1 network each,
+    uneven sample counts, trained together, calibrated per object, queried with the
+    split-FP16 grouped kernel: FN = 0 per object and decisions equal the oracle's."""
+    import torch
+    widths = [4, 64, 64, 64, 1]
+    n_obj = 8
+    rng = np.random.default_rng(900)
+    counts = [int(c) for c in rng.integers(4096 // 32, 16384 // 32, size=n_obj) * 32]
+    scenes, _, _ = _objects("point4t", n_obj, counts, 901, moving=True)
+    shapes = [nb.Shape(sc) for sc in scenes]
+    off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    plan = nb.Plan(off, chunk_rows=4096)
+    g = nb.Group(widths, n_obj, infer_prec="f16x3")
+    g.set_params(np.stack([I.init_params(1000 + o, widths) for o in range(n_obj)]))
+    T = 300
+    for t in range(T):
+        qs = [I.sample_queries("point4t", 5000 + t * n_obj + o, counts[o]) for o in range(n_obj)]
+        qd = _dev(np.concatenate(qs))
+        bits = torch.empty(nb.n_words(int(off[-1])), dtype=torch.int32, device="cuda")
+        for o in range(n_obj):
+            lb = nb.label(shapes[o], I.POINT4T, qd[off[o]:off[o + 1]])
+            bits[off[o] // 32:off[o] // 32 + lb.numel()] = lb
+        g.train_step(plan, qd, bits, 1.0 + 99.0 * t / (T - 1))
+    ev = [I.sample_queries("point4t", 77 + o, 20000) for o in range(n_obj)]
+    eoff = np.concatenate([[0], np.cumsum([20000] * n_obj)]).astype(np.int64)
+    eplan = nb.Plan(eoff, chunk_rows=4096)
+    ys = [O.label(I.POINT4T, e, sc) for e, sc in zip(ev, scenes)]
+    qd = _dev(np.concatenate(ev))
+    bd = _dev(I.pack_bits(np.concatenate(ys)).view(np.int32))
+    taus = g.calibrate(eplan, qd, bd)
+    bits = g.query(eplan, qd, margin=0.05)
+    dec = nb.bits_to_numpy(bits, int(eoff[-1]))
+    p = g.get_params()
+    for o in range(n_obj):
+        z64 = O.forward(widths, p[o], ev[o])
+        sl = slice(eoff[o], eoff[o + 1])
+        tie = np.abs(z64 - taus[o]) <= 1e-12 * max(1.0, abs(taus[o]))
+        assert np.array_equal(dec[sl][~tie], (z64 >= taus[o])[~tie])
+        assert not np.any(ys[o].astype(bool) & ~dec[sl])
+        # trained bounds are tighter than "always inside"
+        assert np.mean(dec[sl] & ~ys[o].astype(bool)) < 0.8
