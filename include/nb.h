@@ -222,6 +222,53 @@ nb_status nb_query_grouped(nb_group *g, const nb_plan *plan, const float *q, flo
 nb_status nb_calibrate_grouped(nb_group *g, const nb_plan *plan, const float *q, const uint32_t *label_bits,
                                double eps, double *host_tau, void *stream);
 
+/* ------------------------------------------------------- learned-culler cascade
+ * Many objects in one scene, each a union of spheres with its own trained bounding
+ * network, and rays asking "which rays hit any object".  Following the paper's premise
+ * of a cheap conservative test in front of an expensive exact one (Sec. 1, Eq. (Benefit)),
+ * the cascade is: axis-aligned box of the object -> the object's neural bound -> exact
+ * sphere test; the plain path (box -> exact) is the judge: both must give the same hits.
+ * All pointers are device pointers. */
+typedef struct {
+    int32_t n_objects;            /* K, 1 .. 4096 */
+    int32_t qexp;                 /* world grid 2^-qexp of rays and spheres, 8 .. 24 */
+    float ball_radius;            /* every sphere of object k lies inside this ball around obj_centre[k] */
+    int32_t reserved;             /* 0 */
+    const int64_t *sphere_offsets;/* [K+1]: spheres of object k are [sphere_offsets[k], sphere_offsets[k+1]) */
+    const float *centres;         /* [S][3] world sphere centres */
+    const float *radii;           /* [S] */
+    const float *obj_centre;      /* [K][3] world centre of each object's frame (on the grid) */
+    const float *aabb;            /* [K][6] min xyz, max xyz, containing every sphere of the object */
+} nb_scene;
+
+typedef struct {
+    unsigned long long aabb_pairs;   /* (ray, object) pairs passing the box */
+    unsigned long long ball_pairs;   /* ... and entering the object's ball (canonical binning) */
+    unsigned long long exact_pairs;  /* pairs given to the exact test */
+    unsigned long long sphere_tests; /* sphere predicates evaluated by the exact test */
+    unsigned long long hit_pairs;    /* pairs whose exact test hit */
+} nb_cascade_stats;
+
+/* Stage 1 for n rays ([n][6], origin and direction on the grid) against every object.
+ * Counting call (offsets == NULL): counts[k] = number of rays of object k passing the
+ * box (and, if canonical, entering the ball); dev_stats (zeroed) gets the pair totals.
+ * Scatter call (offsets = device [K+1], offsets[k+1] - offsets[k] >= counts[k]): object
+ * k's rays go to rows offsets[k] .. of pair_ray (the ray index) and, if canonical, of
+ * pair_q ([rows][6], the ray in the object's frame with its origin moved to where it
+ * enters the ball -- the network's input); the caller pre-fills pair_ray with 0xffffffff
+ * so padding rows are recognised.  counts is rewritten with the same counts. */
+nb_status nb_cascade_bin(const nb_scene *scene, const float *rays, int64_t n, int32_t canonical,
+                         unsigned long long *counts, const int64_t *offsets, uint32_t *pair_ray, float *pair_q,
+                         nb_cascade_stats *dev_stats, void *stream);
+/* Stage 3: rows [0, rows) with pair_ray != 0xffffffff and (pass_bits == NULL or its bit
+ * set) are tested exactly against their object's spheres (integer arithmetic on the
+ * grid); a hit ORs the ray's bit into ray_hits and the row's bit into pair_hits (either
+ * may be NULL, not both; the caller zeroes them).  pair_hits are the exact labels of the
+ * pairs, e.g. for calibrating the objects' thresholds on the deployment distribution. */
+nb_status nb_cascade_exact(const nb_scene *scene, const float *rays, const uint32_t *pair_ray,
+                           const int64_t *offsets, int64_t rows, const uint32_t *pass_bits, uint32_t *ray_hits,
+                           uint32_t *pair_hits, nb_cascade_stats *dev_stats, void *stream);
+
 /* Training step that allocates nothing.  The paper has no counterpart; this is a
  * deployment variant of nb_train_step for callers that cannot call cudaMalloc:
  * hosts whose device memory is entirely reserved up front by another allocator

@@ -1,0 +1,264 @@
+// Learned-culler cascade: a scene of many objects, each bounded by a trained network,
+// queried by rays through a hierarchy of tests (Sec. 1: a cheap conservative test in
+// front of an expensive exact one; Eq. (Benefit) prices the trade):
+//   stage 1  axis-aligned box of each object (classical bound), then the ball of radius R
+//            around the object's centre that contains all its spheres; the ray is moved
+//            into the object's frame and its origin advanced to where it enters the ball
+//            (the form the object's network was trained on);
+//   stage 2  the object's network (nb_query_grouped on the binned pairs);
+//   stage 3  the exact test of the ray against the object's spheres, only for pairs the
+//            network did not exclude.
+// The plain path is stage 1 without the ball, then stage 3 on every pair.
+#include "common.cuh"
+#include "exact.cuh"
+
+using namespace nbexact;
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr unsigned NO_RAY = 0xffffffffu;
+
+struct ObjS {
+    float lo[3], hi[3], c[3];
+};
+
+template <bool CANON, bool SCATTER>
+__global__ void __launch_bounds__(256)
+    bin_kernel(int K, float R2, const float *__restrict__ aabb, const float *__restrict__ oc,
+               const float *__restrict__ rays, long long n, unsigned long long *counts,
+               const long long *__restrict__ offsets, uint32_t *__restrict__ pair_ray, float *__restrict__ pair_q,
+               nb_cascade_stats *st) {
+    extern __shared__ ObjS objs[];
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        ObjS o;
+        for (int i = 0; i < 3; i++) {
+            o.lo[i] = aabb[k * 6 + i];
+            o.hi[i] = aabb[k * 6 + 3 + i];
+            o.c[i] = oc[k * 3 + i];
+        }
+        objs[k] = o;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    unsigned long long n_aabb = 0, n_ball = 0;
+    const long long wpb = blockDim.x >> 5, nw = (long long)gridDim.x * wpb;
+    for (long long wb = (long long)blockIdx.x * wpb + (threadIdx.x >> 5); wb * 32 < n; wb += nw) {
+        const long long r = wb * 32 + lane;
+        const bool valid = r < n;
+        float o[3] = {0.f, 0.f, 0.f}, d[3] = {0.f, 0.f, 1.f}, inv[3];
+        if (valid)
+            for (int i = 0; i < 3; i++) {
+                o[i] = rays[r * 6 + i];
+                d[i] = rays[r * 6 + 3 + i];
+            }
+        for (int i = 0; i < 3; i++) inv[i] = 1.0f / d[i];  // +-inf for a zero component
+        for (int k = 0; k < K; k++) {
+            const ObjS ob = objs[k];
+            // slab test of the half-line against the box (the box is conservative: inflated)
+            float t0 = 0.f, t1 = INFINITY;
+            bool hit = valid;
+#pragma unroll
+            for (int i = 0; i < 3; i++) {
+                if (d[i] == 0.f) {
+                    hit = hit && o[i] >= ob.lo[i] && o[i] <= ob.hi[i];
+                } else {
+                    float ta = (ob.lo[i] - o[i]) * inv[i], tb = (ob.hi[i] - o[i]) * inv[i];
+                    if (ta > tb) {
+                        const float tmp = ta;
+                        ta = tb;
+                        tb = tmp;
+                    }
+                    t0 = fmaxf(t0, ta);
+                    t1 = fminf(t1, tb);
+                }
+            }
+            hit = hit && t0 <= t1;
+            float q6[6];
+            bool keep = hit;
+            if (CANON && hit) {
+                // object frame: w = o - c (exact on the grid); entry into |x| = R:
+                // |w + s d|^2 = R^2, s = (-b - sqrt(b^2 - |d|^2 (|w|^2 - R^2))) / |d|^2
+                float w[3];
+                for (int i = 0; i < 3; i++) w[i] = __fsub_rn(o[i], ob.c[i]);
+                const float b = __fadd_rn(__fadd_rn(__fmul_rn(w[0], d[0]), __fmul_rn(w[1], d[1])), __fmul_rn(w[2], d[2]));
+                const float dd = __fadd_rn(__fadd_rn(__fmul_rn(d[0], d[0]), __fmul_rn(d[1], d[1])), __fmul_rn(d[2], d[2]));
+                const float ww = __fadd_rn(__fadd_rn(__fmul_rn(w[0], w[0]), __fmul_rn(w[1], w[1])), __fmul_rn(w[2], w[2]));
+                const float disc = __fsub_rn(__fmul_rn(b, b), __fmul_rn(dd, __fsub_rn(ww, R2)));
+                keep = disc >= 0.f && dd > 0.f;
+                if (keep) {
+                    float s = __fdiv_rn(__fsub_rn(-b, __fsqrt_rn(disc)), dd);
+                    s = fmaxf(s, 0.f);
+                    for (int i = 0; i < 3; i++) {
+                        q6[i] = __fadd_rn(w[i], __fmul_rn(s, d[i]));
+                        q6[3 + i] = d[i];
+                    }
+                }
+            }
+            const unsigned bh = __ballot_sync(FULL, hit), bk = __ballot_sync(FULL, keep);
+            if (lane == 0) {
+                n_aabb += __popc(bh);
+                n_ball += __popc(bk);
+            }
+            if (!bk) continue;
+            unsigned base = 0;
+            if (lane == 0) base = (unsigned)atomicAdd(counts + k, (unsigned long long)__popc(bk));
+            if (SCATTER) {
+                base = __shfl_sync(FULL, base, 0);
+                if (keep) {
+                    const long long row = offsets[k] + base + __popc(bk & ((1u << lane) - 1u));
+                    pair_ray[row] = (uint32_t)r;
+                    if (CANON)
+                        for (int i = 0; i < 6; i++) pair_q[row * 6 + i] = q6[i];
+                }
+            }
+        }
+    }
+    if (st && lane == 0 && !SCATTER) {
+        if (n_aabb) atomicAdd(&st->aabb_pairs, n_aabb);
+        if (n_ball) atomicAdd(&st->ball_pairs, n_ball);
+    }
+}
+
+__global__ void __launch_bounds__(256)
+    exact_kernel(int K, int qexp, const long long *__restrict__ sph_off, const float *__restrict__ cen,
+                 const float *__restrict__ rad, const float *__restrict__ rays, const uint32_t *__restrict__ pair_ray,
+                 const long long *__restrict__ offsets, long long rows, const uint32_t *__restrict__ pass,
+                 uint32_t *__restrict__ hits, uint32_t *__restrict__ pair_hits, nb_cascade_stats *st) {
+    const float scale = ldexpf(1.0f, qexp);
+    unsigned long long n_pairs = 0, n_tests = 0, n_hit = 0;
+    for (long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x; row < rows;
+         row += (long long)gridDim.x * blockDim.x) {
+        const uint32_t r = pair_ray[row];
+        if (r == NO_RAY) continue;
+        if (pass && !((pass[row >> 5] >> (row & 31)) & 1u)) continue;
+        int lo = 0, hi = K - 1;  // object of this row: last k with offsets[k] <= row
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (offsets[mid] <= row) lo = mid; else hi = mid - 1;
+        }
+        int Q[6];
+        bool ok = true;
+        for (int i = 0; i < 6; i++) ok &= to_grid(rays[(size_t)r * 6 + i], scale, Q[i]);
+        n_pairs++;
+        int h = 1;  // an off-grid ray is a hit (conservative)
+        if (ok) {
+            h = 0;
+            const long long DD = sq(Q[3]) + sq(Q[4]) + sq(Q[5]);
+            for (long long s = sph_off[lo]; s < sph_off[lo + 1] && !h; s++) {
+                int C[3], Rr;
+                bool sok = to_grid(cen[s * 3], scale, C[0]) && to_grid(cen[s * 3 + 1], scale, C[1]) &&
+                           to_grid(cen[s * 3 + 2], scale, C[2]) && to_grid(rad[s], scale, Rr);
+                n_tests++;
+                if (!sok) {
+                    h = 1;
+                    break;
+                }
+                const int w0 = C[0] - Q[0], w1 = C[1] - Q[1], w2 = C[2] - Q[2];
+                const long long WW = sq(w0) + sq(w1) + sq(w2), RR = sq(Rr);
+                if (WW <= RR) {
+                    h = 1;
+                    break;
+                }
+                const long long SD = (long long)w0 * Q[3] + (long long)w1 * Q[4] + (long long)w2 * Q[5];
+                if (SD > 0 && (unsigned __int128)(unsigned long long)(WW - RR) * (unsigned long long)DD <=
+                                  (unsigned __int128)(unsigned long long)SD * (unsigned long long)SD)
+                    h = 1;
+            }
+        }
+        if (h) {
+            n_hit++;
+            if (hits) atomicOr(hits + (r >> 5), 1u << (r & 31));
+            if (pair_hits) atomicOr(pair_hits + (row >> 5), 1u << (row & 31));
+        }
+    }
+    if (st) {
+        const int lane = threadIdx.x & 31;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            n_pairs += __shfl_xor_sync(FULL, n_pairs, o);
+            n_tests += __shfl_xor_sync(FULL, n_tests, o);
+            n_hit += __shfl_xor_sync(FULL, n_hit, o);
+        }
+        if (lane == 0) {
+            if (n_pairs) atomicAdd(&st->exact_pairs, n_pairs);
+            if (n_tests) atomicAdd(&st->sphere_tests, n_tests);
+            if (n_hit) atomicAdd(&st->hit_pairs, n_hit);
+        }
+    }
+}
+
+int num_sms() {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
+
+nb_status check_scene(const nb_scene *sc) {
+    if (!sc) return nb_fail(NB_EINVAL, "cascade: null scene");
+    if (sc->n_objects < 1 || sc->n_objects > 4096) return nb_fail(NB_EINVAL, "cascade: n_objects must be 1..4096");
+    if (sc->qexp < 8 || sc->qexp > 24) return nb_fail(NB_EINVAL, "cascade: qexp must be 8..24");
+    if (!(sc->ball_radius > 0)) return nb_fail(NB_EINVAL, "cascade: ball_radius must be > 0");
+    if (!sc->sphere_offsets || !sc->centres || !sc->radii || !sc->obj_centre || !sc->aabb)
+        return nb_fail(NB_EINVAL, "cascade: null scene array");
+    return NB_OK;
+}
+
+}  // namespace
+
+extern "C" nb_status nb_cascade_bin(const nb_scene *scene, const float *rays, int64_t n, int32_t canonical,
+                                    unsigned long long *counts, const int64_t *offsets, uint32_t *pair_ray,
+                                    float *pair_q, nb_cascade_stats *dev_stats, void *stream) {
+    nb_status st = check_scene(scene);
+    if (st != NB_OK) return st;
+    if (n < 0 || n >= ((int64_t)1 << 32) - 1) return nb_fail(NB_EINVAL, "nb_cascade_bin: n must be in [0, 2^32 - 1)");
+    if (!counts || (n > 0 && !rays)) return nb_fail(NB_EINVAL, "nb_cascade_bin: null pointer");
+    const bool scatter = offsets != nullptr;
+    if (scatter && (!pair_ray || (canonical && !pair_q)))
+        return nb_fail(NB_EINVAL, "nb_cascade_bin: scatter needs pair_ray (and pair_q when canonical)");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int K = scene->n_objects;
+    NB_CUDA(cudaMemsetAsync(counts, 0, sizeof(unsigned long long) * K, s));
+    if (dev_stats && !scatter) NB_CUDA(cudaMemsetAsync(dev_stats, 0, sizeof(nb_cascade_stats), s));
+    if (n == 0) return NB_OK;
+    const size_t smem = sizeof(ObjS) * K;
+    int64_t grid = (n + 255) / 256;
+    if (grid > (int64_t)num_sms() * 8) grid = (int64_t)num_sms() * 8;
+    const float R2 = scene->ball_radius * scene->ball_radius;
+#define NB_BIN(C, S)                                                                                              \
+    do {                                                                                                          \
+        NB_CUDA(cudaFuncSetAttribute(bin_kernel<C, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+        bin_kernel<C, S><<<(unsigned)grid, 256, smem, s>>>(K, R2, scene->aabb, scene->obj_centre, rays, (long long)n, \
+                                                           counts, (const long long *)offsets, pair_ray, pair_q,   \
+                                                           dev_stats);                                            \
+    } while (0)
+    if (canonical && scatter) NB_BIN(true, true);
+    else if (canonical) NB_BIN(true, false);
+    else if (scatter) NB_BIN(false, true);
+    else NB_BIN(false, false);
+#undef NB_BIN
+    NB_CUDA(cudaGetLastError());
+    return NB_OK;
+}
+
+extern "C" nb_status nb_cascade_exact(const nb_scene *scene, const float *rays, const uint32_t *pair_ray,
+                                      const int64_t *offsets, int64_t rows, const uint32_t *pass_bits,
+                                      uint32_t *ray_hits, uint32_t *pair_hits, nb_cascade_stats *dev_stats,
+                                      void *stream) {
+    nb_status st = check_scene(scene);
+    if (st != NB_OK) return st;
+    if (rows < 0) return nb_fail(NB_EINVAL, "nb_cascade_exact: negative rows");
+    if (rows > 0 && (!rays || !pair_ray || !offsets || (!ray_hits && !pair_hits)))
+        return nb_fail(NB_EINVAL, "nb_cascade_exact: null pointer");
+    if (rows == 0) return NB_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t grid = (rows + 255) / 256;
+    if (grid > (int64_t)num_sms() * 8) grid = (int64_t)num_sms() * 8;
+    exact_kernel<<<(unsigned)grid, 256, 0, s>>>(scene->n_objects, scene->qexp, (const long long *)scene->sphere_offsets,
+                                               scene->centres, scene->radii, rays, pair_ray,
+                                               (const long long *)offsets, (long long)rows, pass_bits, ray_hits, pair_hits,
+                                               dev_stats);
+    NB_CUDA(cudaGetLastError());
+    return NB_OK;
+}

@@ -120,6 +120,59 @@ def sample_queries(kind, seed: int, n: int, qexp: int = 20, *,
     return np.ascontiguousarray(quantize(x, qexp))
 
 
+@dataclasses.dataclass
+class MultiScene:
+    """Objects scattered in a world: object k is a union of spheres given in world
+    coordinates, with the frame centre its network was trained in and a box around it."""
+
+    centres: np.ndarray         # (S, 3) float32, world
+    radii: np.ndarray           # (S,) float32
+    sphere_offsets: np.ndarray  # (K+1,) int64
+    obj_centre: np.ndarray      # (K, 3) float32, world
+    aabb: np.ndarray            # (K, 6) float32, min xyz / max xyz, slightly inflated
+    qexp: int
+    ball_radius: float
+
+    @property
+    def n_objects(self) -> int:
+        return int(self.obj_centre.shape[0])
+
+    def local_scene(self, k: int, qexp: int = 20) -> Scene:
+        """Object k's spheres in its own frame (exact: both sides on the world grid)."""
+        a, b = int(self.sphere_offsets[k]), int(self.sphere_offsets[k + 1])
+        c = (self.centres[a:b].astype(np.float64) - self.obj_centre[k].astype(np.float64)).astype(np.float32)
+        return Scene(c, self.radii[a:b].copy(), None, qexp)
+
+
+def make_multi_scene(seed: int, n_objects: int, n_spheres: int, r_lo: float = 0.02, r_hi: float = 0.2,
+                     world: float = 10.0, qexp: int = 18, ball_radius: float = 2.0) -> MultiScene:
+    """n_objects unions of n_spheres spheres (local centres U[-1,1]^3, radii U[r_lo, r_hi])
+    with world centres U[-world, world]^3, all on the 2^-qexp grid."""
+    rng = np.random.default_rng(seed)
+    oc = quantize(rng.uniform(-world, world, size=(n_objects, 3)), qexp)
+    loc = quantize(rng.uniform(-1, 1, size=(n_objects, n_spheres, 3)), qexp)
+    rad = quantize(rng.uniform(r_lo, r_hi, size=(n_objects, n_spheres)), qexp)
+    cen = (oc[:, None, :].astype(np.float64) + loc.astype(np.float64)).astype(np.float32)
+    lo = (cen - rad[..., None]).min(axis=1).astype(np.float64)
+    hi = (cen + rad[..., None]).max(axis=1).astype(np.float64)
+    pad = 1e-3 * (1.0 + np.abs(np.concatenate([lo, hi], 1)))
+    box = np.concatenate([lo, hi], 1) + np.concatenate([-pad[:, :3], pad[:, 3:]], 1)
+    off = np.arange(n_objects + 1, dtype=np.int64) * n_spheres
+    return MultiScene(np.ascontiguousarray(cen.reshape(-1, 3)), np.ascontiguousarray(rad.reshape(-1)), off, oc,
+                      np.ascontiguousarray(box.astype(np.float32)), qexp, ball_radius)
+
+
+def sample_world_rays(seed: int, n: int, radius: float = 35.0, world: float = 10.0, qexp: int = 18) -> np.ndarray:
+    """Rays with origin uniform on the sphere of `radius` around the world centre, aimed at
+    a point uniform in [-world, world]^3 (unit direction), on the 2^-qexp grid."""
+    rng = np.random.default_rng(seed)
+    o = radius * _unit_vectors(rng, n)
+    tgt = rng.uniform(-world, world, size=(n, 3))
+    d = tgt - o
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    return np.ascontiguousarray(quantize(np.concatenate([o, d], 1), qexp))
+
+
 def grid_points_2d(res: int = 256) -> np.ndarray:
     """Cell centres of a res x res grid over [-1,1]^2: -1 + (2i+1)/res (exact in binary)."""
     c = -1.0 + (2.0 * np.arange(res) + 1.0) / res

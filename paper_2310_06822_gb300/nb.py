@@ -29,7 +29,7 @@ EXPORTS = ["nb_model_create", "nb_model_destroy", "nb_model_param_count", "nb_mo
            "nb_plan_create", "nb_plan_destroy", "nb_group_create", "nb_group_destroy", "nb_group_param_count",
            "nb_group_set_params", "nb_group_get_params", "nb_group_get_grad", "nb_group_set_tau", "nb_group_get_tau",
            "nb_group_set_schedule", "nb_group_sync_schedule", "nb_group_reserve", "nb_train_step_grouped",
-           "nb_query_grouped", "nb_calibrate_grouped"]
+           "nb_query_grouped", "nb_calibrate_grouped", "nb_cascade_bin", "nb_cascade_exact"]
 
 
 class NBError(RuntimeError):
@@ -102,6 +102,8 @@ def lib():
                 "nb_train_step_grouped": ([P, P, P, P, ctypes.c_float, ctypes.c_float, P, P], st),
                 "nb_query_grouped": ([P, P, P, ctypes.c_float, P, P, P, P], st),
                 "nb_calibrate_grouped": ([P, P, P, P, ctypes.c_double, P, P], st),
+                "nb_cascade_bin": ([P, P, i64, i32, P, P, P, P, P, P], st),
+                "nb_cascade_exact": ([P, P, P, P, i64, P, P, P, P, P], st),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -368,6 +370,62 @@ class Group:
         _check(lib().nb_calibrate_grouped(self._h, plan._h, _ptr(q), _ptr(label_bits), float(eps),
                                           t.ctypes.data_as(ctypes.c_void_p), _stream(stream)))
         return t
+
+
+class _SceneC(ctypes.Structure):
+    _fields_ = [("n_objects", ctypes.c_int32), ("qexp", ctypes.c_int32), ("ball_radius", ctypes.c_float),
+                ("reserved", ctypes.c_int32), ("sphere_offsets", ctypes.c_void_p), ("centres", ctypes.c_void_p),
+                ("radii", ctypes.c_void_p), ("obj_centre", ctypes.c_void_p), ("aabb", ctypes.c_void_p)]
+
+
+CASCADE_STATS = np.dtype([("aabb_pairs", "<u8"), ("ball_pairs", "<u8"), ("exact_pairs", "<u8"),
+                          ("sphere_tests", "<u8"), ("hit_pairs", "<u8")])
+
+
+class WorldScene:
+    """Objects of a multi-object scene resident on the device (nb_scene)."""
+
+    def __init__(self, ms, device="cuda"):
+        self.ms = ms
+        self.K = ms.n_objects
+        self.sphere_offsets = torch.as_tensor(np.ascontiguousarray(ms.sphere_offsets, dtype=np.int64), device=device)
+        self.centres = _dev(ms.centres, torch.float32, device)
+        self.radii = _dev(ms.radii, torch.float32, device)
+        self.obj_centre = _dev(ms.obj_centre, torch.float32, device)
+        self.aabb = _dev(ms.aabb, torch.float32, device)
+        self._s = _SceneC(self.K, ms.qexp, float(ms.ball_radius), 0, self.sphere_offsets.data_ptr(),
+                          self.centres.data_ptr(), self.radii.data_ptr(), self.obj_centre.data_ptr(),
+                          self.aabb.data_ptr())
+
+
+def cascade_bin(ws: WorldScene, rays: torch.Tensor, canonical: bool, stream=None):
+    """Stage 1: (ray, object) pairs passing the box (and the ball when canonical), binned by
+    object into rows padded to multiples of 32.  Returns (host offsets, device offsets,
+    pair_ray, pair_q or None, stats)."""
+    n = rays.shape[0]
+    dev = rays.device
+    counts = torch.zeros(ws.K, dtype=torch.int64, device=dev)
+    st = torch.zeros(CASCADE_STATS.itemsize, dtype=torch.uint8, device=dev)
+    L = lib()
+    _check(L.nb_cascade_bin(ctypes.byref(ws._s), _ptr(rays), n, int(canonical), _ptr(counts), None, None, None,
+                            _ptr(st), _stream(stream)))
+    c = counts.cpu().numpy()
+    padded = (c + 31) // 32 * 32
+    off = np.concatenate([[0], np.cumsum(padded)]).astype(np.int64)
+    rows = int(off[-1])
+    pair_ray = torch.full((max(rows, 1),), -1, dtype=torch.int32, device=dev)
+    pair_q = torch.zeros((max(rows, 1), 6), dtype=torch.float32, device=dev) if canonical else None
+    off_d = torch.as_tensor(off, device=dev)
+    _check(L.nb_cascade_bin(ctypes.byref(ws._s), _ptr(rays), n, int(canonical), _ptr(counts), _ptr(off_d),
+                            _ptr(pair_ray), _ptr(pair_q), None, _stream(stream)))
+    return off, off_d, pair_ray, pair_q, _read(st, CASCADE_STATS)
+
+
+def cascade_exact(ws: WorldScene, rays, pair_ray, off_d, rows: int, pass_bits=None, ray_hits=None,
+                  pair_hits=None, stats=None, stream=None):
+    """Stage 3: exact sphere tests of the rows (those with a pass bit, if given)."""
+    _check(lib().nb_cascade_exact(ctypes.byref(ws._s), _ptr(rays), _ptr(pair_ray), _ptr(off_d), int(rows),
+                                  _ptr(pass_bits), _ptr(ray_hits), _ptr(pair_hits), _ptr(stats), _stream(stream)))
 
 
 def step_stats_tensor(device="cuda") -> torch.Tensor:

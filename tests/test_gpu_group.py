@@ -169,14 +169,18 @@ def test_grouped_4d_end_to_end_zero_fn(nb):
     plan = nb.Plan(off, chunk_rows=4096)
     g = nb.Group(widths, n_obj, infer_prec="f16x3")
     g.set_params(np.stack([I.init_params(1000 + o, widths) for o in range(n_obj)]))
-    T = 300
+    # a device-resident pool of 8 batches per object, labelled once; step t uses batch t % 8
+    W = 8
+    pools = [_dev(I.sample_queries("point4t", 5000 + o, counts[o] * W)) for o in range(n_obj)]
+    pool_bits = [nb.label(shapes[o], I.POINT4T, pools[o]) for o in range(n_obj)]
+    batches = []
+    for j in range(W):
+        qd = torch.cat([pools[o][j * counts[o]:(j + 1) * counts[o]] for o in range(n_obj)])
+        bits = torch.cat([pool_bits[o][j * counts[o] // 32:(j + 1) * counts[o] // 32] for o in range(n_obj)])
+        batches.append((qd.contiguous(), bits.contiguous()))
+    T = 1500
     for t in range(T):
-        qs = [I.sample_queries("point4t", 5000 + t * n_obj + o, counts[o]) for o in range(n_obj)]
-        qd = _dev(np.concatenate(qs))
-        bits = torch.empty(nb.n_words(int(off[-1])), dtype=torch.int32, device="cuda")
-        for o in range(n_obj):
-            lb = nb.label(shapes[o], I.POINT4T, qd[off[o]:off[o + 1]])
-            bits[off[o] // 32:off[o] // 32 + lb.numel()] = lb
+        qd, bits = batches[t % W]
         g.train_step(plan, qd, bits, 1.0 + 99.0 * t / (T - 1))
     ev = [I.sample_queries("point4t", 77 + o, 20000) for o in range(n_obj)]
     eoff = np.concatenate([[0], np.cumsum([20000] * n_obj)]).astype(np.int64)
@@ -188,11 +192,14 @@ def test_grouped_4d_end_to_end_zero_fn(nb):
     bits = g.query(eplan, qd, margin=0.05)
     dec = nb.bits_to_numpy(bits, int(eoff[-1]))
     p = g.get_params()
+    fp, trivial = 0.0, 0.0
     for o in range(n_obj):
         z64 = O.forward(widths, p[o], ev[o])
         sl = slice(eoff[o], eoff[o + 1])
         tie = np.abs(z64 - taus[o]) <= 1e-12 * max(1.0, abs(taus[o]))
         assert np.array_equal(dec[sl][~tie], (z64 >= taus[o])[~tie])
         assert not np.any(ys[o].astype(bool) & ~dec[sl])
-        # trained bounds are tighter than "always inside"
-        assert np.mean(dec[sl] & ~ys[o].astype(bool)) < 0.8
+        fp += np.mean(dec[sl] & ~ys[o].astype(bool))
+        trivial += np.mean(~ys[o].astype(bool))
+    # the trained bounds are tighter than the trivial one (everything inside)
+    assert fp < 0.9 * trivial, (fp, trivial)
