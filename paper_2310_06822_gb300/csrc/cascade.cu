@@ -87,7 +87,10 @@ __global__ void __launch_bounds__(256)
                 const float disc = __fsub_rn(__fmul_rn(b, b), __fmul_rn(dd, __fsub_rn(ww, R2)));
                 keep = disc >= 0.f && dd > 0.f;
                 if (keep) {
-                    float s = __fdiv_rn(__fsub_rn(-b, __fsqrt_rn(disc)), dd);
+                    // smaller root without cancellation: s = c / (-b + sqrt(disc)) when -b > 0
+                    const float sq_disc = __fsqrt_rn(disc);
+                    const float c = __fsub_rn(ww, R2);
+                    float s = -b > 0.f ? __fdiv_rn(c, __fadd_rn(-b, sq_disc)) : __fdiv_rn(__fsub_rn(-b, sq_disc), dd);
                     s = fmaxf(s, 0.f);
                     for (int i = 0; i < 3; i++) {
                         q6[i] = __fadd_rn(w[i], __fmul_rn(s, d[i]));
