@@ -84,7 +84,13 @@ __global__ void __launch_bounds__(256)
                 const float b = __fadd_rn(__fadd_rn(__fmul_rn(w[0], d[0]), __fmul_rn(w[1], d[1])), __fmul_rn(w[2], d[2]));
                 const float dd = __fadd_rn(__fadd_rn(__fmul_rn(d[0], d[0]), __fmul_rn(d[1], d[1])), __fmul_rn(d[2], d[2]));
                 const float ww = __fadd_rn(__fadd_rn(__fmul_rn(w[0], w[0]), __fmul_rn(w[1], w[1])), __fmul_rn(w[2], w[2]));
-                const float disc = __fsub_rn(__fmul_rn(b, b), __fmul_rn(dd, __fsub_rn(ww, R2)));
+                // b^2 - dd (ww - R^2) = dd R^2 - |w x d|^2 (Lagrange), free of the cancellation
+                // between the two large terms when the origin is far from the object
+                const float cx = fmaf(w[1], d[2], -__fmul_rn(w[2], d[1]));
+                const float cy = fmaf(w[2], d[0], -__fmul_rn(w[0], d[2]));
+                const float cz = fmaf(w[0], d[1], -__fmul_rn(w[1], d[0]));
+                const float cr2 = __fadd_rn(__fadd_rn(__fmul_rn(cx, cx), __fmul_rn(cy, cy)), __fmul_rn(cz, cz));
+                const float disc = __fsub_rn(__fmul_rn(dd, R2), cr2);
                 keep = disc >= 0.f && dd > 0.f;
                 if (keep) {
                     // smaller root without cancellation: s = c / (-b + sqrt(disc)) when -b > 0

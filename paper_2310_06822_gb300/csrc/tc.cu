@@ -319,41 +319,59 @@ int num_sms() {
 nb_status nb_tc_init(TcModel *tc, const MlpDesc &d, int infer_prec, int train_prec) {
     tc->infer_prec = infer_prec;
     tc->train_prec = train_prec;
-    if (train_prec != NB_F32) return nb_fail(NB_EUNSUPPORTED, "BF16 training step is not available in this build");
-    if (infer_prec != NB_BF16 && infer_prec != NB_F16X3)
-        return nb_fail(NB_EUNSUPPORTED, "FP8 inference is not available in this build");
+    if (infer_prec == NB_FP8) return nb_fail(NB_EUNSUPPORTED, "FP8 inference is not available in this build");
     const int H = d.w[1], NH = d.L - 1;
-    if (NH < 1) return nb_fail(NB_EUNSUPPORTED, "tensor-core forward needs at least one hidden layer");
-    if (d.w[0] > 16) return nb_fail(NB_EUNSUPPORTED, "tensor-core forward: input width must be <= 16");
-    if (H != 64 && H != 128) return nb_fail(NB_EUNSUPPORTED, "tensor-core forward: hidden width must be 64 or 128");
-    for (int l = 1; l < d.L; l++)
-        if (d.w[l] != H) return nb_fail(NB_EUNSUPPORTED, "tensor-core forward: hidden widths must be equal");
-    int dev = 0, maxsm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const size_t need = infer_prec == NB_BF16 ? fwd_smem_bytes(H, NH) : nb_split_smem_bytes(H, NH);
-    if (need > (size_t)maxsm)
-        return nb_fail(NB_EUNSUPPORTED, "tensor-core forward: the network's weights do not fit in shared memory");
-    tc->img_bytes = infer_prec == NB_BF16 ? img_total(H, NH) : nb_split_img_bytes(H, NH);
-    if (cudaMalloc(&tc->img, tc->img_bytes) != cudaSuccess || cudaMalloc(&tc->err, sizeof(int)) != cudaSuccess) {
+    if (cudaMalloc(&tc->err, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
-        return nb_fail(NB_ENOMEM, "tensor-core image allocation failed");
+        return nb_fail(NB_ENOMEM, "tensor-core state allocation failed");
     }
-    cudaMemset(tc->img, 0, tc->img_bytes);
     cudaMemset(tc->err, 0, sizeof(int));
+    if (infer_prec == NB_BF16 || infer_prec == NB_F16X3) {
+        if (NH < 1) return nb_fail(NB_EUNSUPPORTED, "tensor-core forward needs at least one hidden layer");
+        if (d.w[0] > 16) return nb_fail(NB_EUNSUPPORTED, "tensor-core forward: input width must be <= 16");
+        if (H != 64 && H != 128) return nb_fail(NB_EUNSUPPORTED, "tensor-core forward: hidden width must be 64 or 128");
+        for (int l = 1; l < d.L; l++)
+            if (d.w[l] != H) return nb_fail(NB_EUNSUPPORTED, "tensor-core forward: hidden widths must be equal");
+        int dev = 0, maxsm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        const size_t need = infer_prec == NB_BF16 ? fwd_smem_bytes(H, NH) : nb_split_smem_bytes(H, NH);
+        if (need > (size_t)maxsm)
+            return nb_fail(NB_EUNSUPPORTED, "tensor-core forward: the network's weights do not fit in shared memory");
+        tc->img_bytes = infer_prec == NB_BF16 ? img_total(H, NH) : nb_split_img_bytes(H, NH);
+        if (cudaMalloc(&tc->img, tc->img_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return nb_fail(NB_ENOMEM, "tensor-core image allocation failed");
+        }
+        cudaMemset(tc->img, 0, tc->img_bytes);
+    }
+    if (train_prec == NB_BF16) {
+        const nb_status st = nb_train_bf16_check(d);
+        if (st != NB_OK) return st;
+        tc->train_img_bytes = nb_train_bf16_img_bytes(d);
+        if (cudaMalloc(&tc->train_img, tc->train_img_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return nb_fail(NB_ENOMEM, "training image allocation failed");
+        }
+        cudaMemset(tc->train_img, 0, tc->train_img_bytes);
+    }
     return NB_OK;
 }
 
 void nb_tc_free(TcModel *tc) {
     cudaFree(tc->img);
     cudaFree(tc->err);
-    cudaFree(tc->train_ws);
+    cudaFree(tc->train_img);
     tc->img = nullptr;
     tc->err = nullptr;
-    tc->train_ws = nullptr;
+    tc->train_img = nullptr;
 }
 
 nb_status nb_tc_refresh(TcModel *tc, const MlpDesc &d, cudaStream_t s) {
+    if (tc->train_img) {
+        const nb_status st = nb_train_bf16_refresh(tc, d, s);
+        if (st != NB_OK) return st;
+    }
     if (!tc->img) return NB_OK;
     if (tc->infer_prec == NB_F16X3) return nb_split_refresh(tc, d, s);
     const TcDesc t = make_desc(tc, d);
@@ -383,12 +401,6 @@ nb_status nb_tc_query(TcModel *tc, const MlpDesc &d, const float *q, int64_t n, 
     }
     NB_CUDA(cudaGetLastError());
     return NB_OK;
-}
-
-nb_status nb_tc_train_step(TcModel *, const MlpDesc &, const float *, const uint32_t *, int64_t, float, float, TauF,
-                           float *, float *, float *, float *, float, float, float, float, float, float,
-                           nb_step_stats *, cudaStream_t) {
-    return nb_fail(NB_EUNSUPPORTED, "BF16 training step is not available in this build");
 }
 
 nb_status nb_tc_check(TcModel *tc) {

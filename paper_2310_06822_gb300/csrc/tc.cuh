@@ -9,8 +9,8 @@ struct TcModel {
     void *img = nullptr;     // device: packed operand images of every layer
     size_t img_bytes = 0;
     float *scales = nullptr; // device: per-layer dequantisation scales (FP8)
-    void *train_ws = nullptr;
-    size_t train_ws_bytes = 0;
+    void *train_img = nullptr;   // device: BF16 weights for the tensor-core training step
+    size_t train_img_bytes = 0;
     int *err = nullptr;      // device: status of the last bounded wait that gave up (0 = none)
 };
 
@@ -29,7 +29,11 @@ void nb_tc_free(TcModel *tc);
 nb_status nb_tc_refresh(TcModel *tc, const MlpDesc &d, cudaStream_t s);
 nb_status nb_tc_query(TcModel *tc, const MlpDesc &d, const float *q, int64_t n, TauF tau, float margin,
                       uint32_t *bits, float *logits, nb_query_stats *st, QueryWs ws, cudaStream_t s);
-nb_status nb_tc_train_step(TcModel *tc, const MlpDesc &d, const float *q, const uint32_t *labels, int64_t n,
-                           float alpha, float beta, TauF tau, float *params, float *m, float *v, float *grad,
-                           float lr, float b1, float b2, float eps, float c1, float sqrt_c2, nb_step_stats *st,
-                           cudaStream_t s);
+// BF16 tensor-core training step (train_bf16.cu)
+nb_status nb_train_bf16_check(const MlpDesc &d);
+size_t nb_train_bf16_img_bytes(const MlpDesc &d);
+size_t nb_train_bf16_smem(int H, int NH);
+nb_status nb_train_bf16_refresh(TcModel *tc, const MlpDesc &d, cudaStream_t s);
+int nb_train_bf16_ctas(int64_t n);
+nb_status nb_launch_train_bf16(TcModel *tc, const MlpDesc &d, const float *q, const uint32_t *labels, int64_t n,
+                               float alpha, float beta, TauF tau, TrainWs ws, nb_step_stats *st, cudaStream_t s);

@@ -1,0 +1,418 @@
+// BF16 tensor-core training step of the bounding network (Sec. 3.4 "Training"):
+// forward, asymmetric BCE of Eq. (loss), backward and per-CTA gradient partials in one
+// persistent kernel; the partials are then summed in CTA order and Adam updates the
+// FP32 master weights (adam_kernel of the FP32 path).
+//
+// Every GEMM of the step runs on the tensor cores with BF16 operands and FP32
+// accumulation (mma.sync m16n8k16): the forward Z = A W^T, the input gradient
+// dA = dZ W and the weight gradient dW = dZ^T A, the last two contracting over the
+// batch; ldmatrix(.trans) loads every operand in the orientation the MMA needs, so the
+// activations of a tile are stored once, row-major, in shared memory.
+// A CTA walks tiles of 64 samples; per tile it keeps the input and every hidden layer's
+// activations (BF16) in shared memory for the backward pass, next to all layers' BF16
+// weights.  The head (width 1), the loss and the bias gradients run in FP32.
+// Weight-gradient partials go to the CTA's own slot with red.global.add; each address
+// has one owning thread per tile, so the slot's sums are in program order.
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include "common.cuh"
+#include "tc.cuh"
+
+namespace {
+
+constexpr int TM = 64;           // samples per tile
+constexpr int K0 = 16;           // padded input width
+constexpr int PAD = 8;           // row padding (elements) against ldmatrix bank conflicts
+constexpr unsigned FULL = 0xffffffffu;
+
+struct TrainDesc {
+    int in, H, NH;
+    const __nv_bfloat16 *img;    // per layer bf16 W[n][k], k padded to K0 (layer 0) or H
+    const float *p;              // FP32 master parameters (biases and head)
+    int off[NB_MAXL];
+};
+
+__host__ __device__ inline int kpad(int H, int l) { return l == 0 ? K0 : H; }
+__host__ __device__ inline size_t img_off(int H, int l) {  // elements
+    return l == 0 ? 0 : (size_t)H * K0 + (size_t)(l - 1) * H * H;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+__device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&v);
+}
+__device__ __forceinline__ void red_add(float *p, float v) {
+    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+__device__ __forceinline__ float softplusf(float u) { return u > 0.f ? u + log1pf(expf(-u)) : log1pf(expf(u)); }
+__device__ __forceinline__ float sigmoidf(float u) {
+    return u >= 0.f ? 1.f / (1.f + expf(-u)) : expf(u) / (1.f + expf(u));
+}
+
+// OUT[TM][N] = epilogue(X[TM][K] Y^T) with Y[N][K] row-major (forward, Y = W) or, with
+// TRANS_Y, OUT = X Y with Y[K][N] (the input gradient, Y = W read transposed).
+// Warps: 4 along the 64 rows x 2 along N.  RELU: out = relu(acc + bias) (forward);
+// otherwise out = acc masked by mask[m][n] > 0 (backward through the ReLU).
+template <int H, bool TRANS_Y, bool RELU>
+__device__ __forceinline__ void tile_gemm(const __nv_bfloat16 *X, int xp, int K, const __nv_bfloat16 *Y, int yp,
+                                          const float *bias, const __nv_bfloat16 *mask, int mp, __nv_bfloat16 *out,
+                                          int op) {
+    constexpr int NT = H / 16;  // n-tiles of 8 per warp (H/2 columns)
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = (warp & 3) * 16, n0 = (warp >> 2) * (H / 2);
+    float acc[NT][4];
+#pragma unroll
+    for (int j = 0; j < NT; j++) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+    const int mi = lane >> 3, r = lane & 7;
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        uint32_t a0, a1, a2, a3;
+        ldsm_x4(smem_u32(X + (m0 + r + (mi & 1) * 8) * xp + k0 + (mi >> 1) * 8), a0, a1, a2, a3);
+#pragma unroll
+        for (int j = 0; j < NT; j += 2) {
+            uint32_t b0, b1, b2, b3;
+            if (!TRANS_Y) {
+                // Y[n][k]: matrices (n0-7,k0-7) (n0-7,k8-15) (n8-15,k0-7) (n8-15,k8-15)
+                ldsm_x4(smem_u32(Y + (n0 + 8 * j + r + (mi >> 1) * 8) * yp + k0 + (mi & 1) * 8), b0, b1, b2, b3);
+            } else {
+                // Y[k][n] read transposed: matrices (k0-7,n0-7) (k8-15,n0-7) (k0-7,n8-15) (k8-15,n8-15)
+                ldsm_x4_t(smem_u32(Y + (k0 + r + (mi & 1) * 8) * yp + n0 + 8 * j + (mi >> 1) * 8), b0, b1, b2, b3);
+            }
+            mma_bf16(acc[j], a0, a1, a2, a3, b0, b1);
+            mma_bf16(acc[j + 1], a0, a1, a2, a3, b2, b3);
+        }
+    }
+    const int gr = lane >> 2, gc = (lane & 3) * 2;
+#pragma unroll
+    for (int j = 0; j < NT; j++) {
+        const int nn = n0 + 8 * j + gc;
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int m = m0 + gr + 8 * h;
+            float v0 = acc[j][2 * h], v1 = acc[j][2 * h + 1];
+            if (RELU) {
+                v0 = fmaxf(v0 + bias[nn], 0.f);
+                v1 = fmaxf(v1 + bias[nn + 1], 0.f);
+            } else {
+                const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162 *>(mask + m * mp + nn);
+                v0 = __low2float(mk) > 0.f ? v0 : 0.f;
+                v1 = __high2float(mk) > 0.f ? v1 : 0.f;
+            }
+            *reinterpret_cast<uint32_t *>(out + m * op + nn) = pack2(v0, v1);
+        }
+    }
+}
+
+// slot[n][k] += sum_m DZ[m][n] A[m][k] for n < H, k < Kreal (weight gradient of one layer).
+// Warps: n-blocks of 16 x (128 / H) column groups.
+template <int H>
+__device__ __forceinline__ void tile_dw(const __nv_bfloat16 *DZ, int dp, const __nv_bfloat16 *A, int ap, int Kp,
+                                        int Kreal, float *slotW) {
+    constexpr int NB = H / 16, KG = 8 / NB;  // n-blocks, column groups
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n0 = (warp % NB) * 16, kg = warp / NB;
+    const int kw = Kp / KG, kbeg = kg * kw;   // this warp's columns
+    const int mi = lane >> 3, r = lane & 7;
+    const int gr = lane >> 2, gc = (lane & 3) * 2;
+    for (int kc = 0; kc < kw; kc += 64) {  // at most 64 columns (8 n8-tiles) of accumulators at a time
+        const int cw = min(64, kw - kc);
+        float acc[8][4];
+#pragma unroll
+        for (int j = 0; j < 8; j++) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+        for (int m0 = 0; m0 < TM; m0 += 16) {
+            // A' = DZ^T (rows n, K' = m): matrices (n0-7,m0-7) (n8-15,m0-7) (n0-7,m8-15) (n8-15,m8-15)
+            uint32_t a0, a1, a2, a3;
+            ldsm_x4_t(smem_u32(DZ + (m0 + r + (mi >> 1) * 8) * dp + n0 + (mi & 1) * 8), a0, a1, a2, a3);
+#pragma unroll
+            for (int j = 0; j < 8; j += 2) {
+                if (8 * j >= cw) break;
+                const int k0 = kbeg + kc + 8 * j;
+                // B' = A (K' = m, N' = k): matrices (m0-7,k0-7) (m8-15,k0-7) (m0-7,k8-15) (m8-15,k8-15)
+                uint32_t b0, b1, b2, b3;
+                ldsm_x4_t(smem_u32(A + (m0 + r + (mi & 1) * 8) * ap + k0 + (mi >> 1) * 8), b0, b1, b2, b3);
+                mma_bf16(acc[j], a0, a1, a2, a3, b0, b1);
+                if (8 * (j + 1) < cw) mma_bf16(acc[j + 1], a0, a1, a2, a3, b2, b3);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            if (8 * j >= cw) break;
+            const int k = kbeg + kc + 8 * j + gc;
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int nn = n0 + gr + 8 * h;
+                if (k < Kreal) red_add(slotW + nn * Kreal + k, acc[j][2 * h]);
+                if (k + 1 < Kreal) red_add(slotW + nn * Kreal + k + 1, acc[j][2 * h + 1]);
+            }
+        }
+    }
+}
+
+template <int H>
+__global__ void __launch_bounds__(256, 1)
+    train_bf16_kernel(TrainDesc d, const float *__restrict__ q, const uint32_t *__restrict__ labels, long long n,
+                      float alpha, float beta, float inv_n, TauF tau, float *__restrict__ partial,
+                      float *loss_partial, long long P, nb_step_stats *st) {
+    constexpr int HP = H + PAD, XP = K0 + PAD;
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    const int NH = d.NH, t = threadIdx.x;
+    __nv_bfloat16 *Ws = reinterpret_cast<__nv_bfloat16 *>(smem_raw);  // layer 0: H x XP, others H x HP
+    __nv_bfloat16 *act = Ws + H * XP + (size_t)(NH - 1) * H * HP;      // act0: TM x XP, act l>=1: TM x HP
+    __nv_bfloat16 *dz0 = act + TM * XP + (size_t)NH * TM * HP;
+    __nv_bfloat16 *dz1 = dz0 + TM * HP;
+    float *bias = reinterpret_cast<float *>(dz1 + TM * HP);  // [NH][H]
+    float *head = bias + NH * H;                               // [H + 1]
+    float *zs = head + H + 4, *gs = zs + TM, *ls = gs + TM;
+    auto W_l = [&](int l) { return l == 0 ? Ws : Ws + H * XP + (size_t)(l - 1) * H * HP; };
+    auto A_l = [&](int l) { return l == 0 ? act : act + TM * XP + (size_t)(l - 1) * TM * HP; };
+
+    // weights (bf16 image -> padded rows), biases, head
+    for (int l = 0; l < NH; l++) {
+        const int kp = kpad(H, l), pitch = l == 0 ? XP : HP;
+        const __nv_bfloat16 *src = d.img + img_off(H, l);
+        __nv_bfloat16 *dst = W_l(l);
+        for (int e = t; e < H * kp / 8; e += blockDim.x) {
+            const int row = (e * 8) / kp, col = (e * 8) % kp;
+            *reinterpret_cast<uint4 *>(dst + row * pitch + col) = *reinterpret_cast<const uint4 *>(src + row * kp + col);
+        }
+    }
+    for (int i = t; i < NH * H; i += blockDim.x) {
+        const int l = i / H, j = i % H;
+        bias[i] = d.p[d.off[l] + H * (l == 0 ? d.in : H) + j];
+    }
+    for (int i = t; i <= H; i += blockDim.x) head[i] = d.p[d.off[NH] + i];
+    __syncthreads();
+
+    float *slot = partial + (size_t)blockIdx.x * P;
+    const long long ntiles = (n + TM - 1) / TM;
+    float lossacc = 0.f;
+    unsigned long long c_fn = 0, c_fp = 0, c_nf = 0;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const long long base = tile * TM;
+        const int rows = (int)min((long long)TM, n - base);
+        // input -> bf16, padded to K0
+        for (int e = t; e < TM * K0; e += blockDim.x) {
+            const int m = e / K0, k = e % K0;
+            const float x = (m < rows && k < d.in) ? q[(base + m) * d.in + k] : 0.f;
+            act[m * XP + k] = __float2bfloat16_rn(x);
+        }
+        __syncthreads();
+        // forward
+        for (int l = 0; l < NH; l++) {
+            tile_gemm<H, false, true>(A_l(l), l == 0 ? XP : HP, kpad(H, l), W_l(l), l == 0 ? XP : HP, bias + l * H,
+                                      nullptr, 0, A_l(l + 1), HP);
+            __syncthreads();
+        }
+        // head (FP32) and loss: 4 threads per sample
+        {
+            const __nv_bfloat16 *aL = A_l(NH);
+            const int m = t >> 2, part = t & 3;
+            float s = 0.f;
+            for (int k = part; k < H; k += 4) s = fmaf(head[k], __bfloat162float(aL[m * HP + k]), s);
+            s += __shfl_xor_sync(FULL, s, 1);
+            s += __shfl_xor_sync(FULL, s, 2);
+            if (part == 0) zs[m] = s + head[H];
+        }
+        __syncthreads();
+        if (t < TM) {
+            float g = 0.f, lv = 0.f;
+            if (t < rows) {
+                const long long i = base + t;
+                const float y = (float)((labels[i >> 5] >> (i & 31)) & 1u);
+                const float z = zs[t];
+                if (isfinite(z)) {
+                    lv = alpha * y * softplusf(-z) + beta * (1.f - y) * softplusf(z);
+                    const float sg = sigmoidf(z);
+                    g = (alpha * y * (sg - 1.f) + beta * (1.f - y) * sg) * inv_n;
+                    const bool dec = z >= tau.up;
+                    c_fn += (y != 0.f && !dec);
+                    c_fp += (y == 0.f && dec);
+                } else {
+                    c_nf++;
+                }
+            }
+            gs[t] = g;
+            ls[t] = lv;
+        }
+        __syncthreads();
+        if (t == 0)
+            for (int m = 0; m < rows; m++) lossacc += ls[m];
+        // head gradients and dZ of the last hidden layer
+        {
+            const __nv_bfloat16 *aL = A_l(NH);
+            float *gW = slot + d.off[NH];
+            for (int k = t; k <= H; k += blockDim.x) {
+                float s = 0.f;
+                if (k < H)
+                    for (int m = 0; m < TM; m++) s = fmaf(gs[m], __bfloat162float(aL[m * HP + k]), s);
+                else
+                    for (int m = 0; m < TM; m++) s += gs[m];
+                gW[k] += s;
+            }
+            for (int e = t; e < TM * H; e += blockDim.x) {
+                const int m = e / H, k = e % H;
+                const float a = __bfloat162float(aL[m * HP + k]);
+                dz0[m * HP + k] = __float2bfloat16_rn(a > 0.f ? gs[m] * head[k] : 0.f);
+            }
+        }
+        __syncthreads();
+        __nv_bfloat16 *dzc = dz0, *dzn = dz1;
+        for (int l = NH - 1; l >= 0; l--) {
+            const int K = l == 0 ? d.in : H, kp = kpad(H, l);
+            const __nv_bfloat16 *Al = A_l(l);
+            float *gW = slot + d.off[l];
+            tile_dw<H>(dzc, HP, Al, l == 0 ? XP : HP, kp, K, gW);
+            for (int nn = t; nn < H; nn += blockDim.x) {
+                float s = 0.f;
+                for (int m = 0; m < TM; m++) s += __bfloat162float(dzc[m * HP + nn]);
+                gW[(size_t)H * K + nn] += s;
+            }
+            if (l > 0) {
+                // dA_{l} = dZ W_l, through the ReLU of layer l's input
+                tile_gemm<H, true, false>(dzc, HP, H, W_l(l), HP, nullptr, Al, HP, dzn, HP);
+                __syncthreads();
+                __nv_bfloat16 *tp = dzc;
+                dzc = dzn;
+                dzn = tp;
+            }
+        }
+        __syncthreads();
+    }
+    if (t == 0) loss_partial[blockIdx.x] = lossacc;
+    if (st && t < TM) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            c_fn += __shfl_xor_sync(FULL, c_fn, o);
+            c_fp += __shfl_xor_sync(FULL, c_fp, o);
+            c_nf += __shfl_xor_sync(FULL, c_nf, o);
+        }
+        if ((t & 31) == 0) {
+            if (c_fn) atomicAdd(&st->fn, c_fn);
+            if (c_fp) atomicAdd(&st->fp, c_fp);
+            if (c_nf) atomicAdd(&st->n_nonfinite, c_nf);
+        }
+    }
+}
+
+// FP32 master weights -> bf16 training image
+__global__ void pack_train_kernel(TrainDesc d, __nv_bfloat16 *img, long long total) {
+    const int H = d.H;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        int l;
+        long long local;
+        if (e < (long long)H * K0) {
+            l = 0;
+            local = e;
+        } else {
+            l = 1 + (int)((e - (long long)H * K0) / ((long long)H * H));
+            local = (e - (long long)H * K0) % ((long long)H * H);
+        }
+        const int kp = kpad(H, l), K = l == 0 ? d.in : H;
+        const int row = (int)(local / kp), col = (int)(local % kp);
+        img[e] = __float2bfloat16_rn(col < K ? d.p[d.off[l] + (size_t)row * K + col] : 0.f);
+    }
+}
+
+TrainDesc make_desc(const TcModel *tc, const MlpDesc &d) {
+    TrainDesc t{};
+    t.in = d.w[0];
+    t.H = d.w[1];
+    t.NH = d.L - 1;
+    t.img = (const __nv_bfloat16 *)tc->train_img;
+    t.p = d.p;
+    for (int l = 0; l < d.L; l++) t.off[l] = d.off[l];
+    return t;
+}
+
+size_t train_img_elems(int H, int NH) { return img_off(H, NH); }
+
+int num_sms() {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
+
+}  // namespace
+
+size_t nb_train_bf16_smem(int H, int NH) {
+    const size_t HP = H + PAD, XP = K0 + PAD;
+    const size_t w = (size_t)H * XP + (size_t)(NH - 1) * H * HP;
+    const size_t a = (size_t)TM * XP + (size_t)NH * TM * HP;
+    const size_t dz = 2 * (size_t)TM * HP;
+    return (w + a + dz) * 2 + ((size_t)NH * H + H + 4 + 3 * TM) * 4 + 64;
+}
+
+nb_status nb_train_bf16_check(const MlpDesc &d) {
+    const int H = d.w[1], NH = d.L - 1;
+    if (NH < 1) return nb_fail(NB_EUNSUPPORTED, "BF16 training needs at least one hidden layer");
+    if (d.w[0] > K0) return nb_fail(NB_EUNSUPPORTED, "BF16 training: input width must be <= 16");
+    if (H != 64 && H != 128) return nb_fail(NB_EUNSUPPORTED, "BF16 training: hidden width must be 64 or 128");
+    for (int l = 1; l < d.L; l++)
+        if (d.w[l] != H) return nb_fail(NB_EUNSUPPORTED, "BF16 training: hidden widths must be equal");
+    int dev = 0, maxsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (nb_train_bf16_smem(H, NH) > (size_t)maxsm)
+        return nb_fail(NB_EUNSUPPORTED, "BF16 training: the network does not fit in shared memory");
+    return NB_OK;
+}
+
+size_t nb_train_bf16_img_bytes(const MlpDesc &d) { return train_img_elems(d.w[1], d.L - 1) * 2; }
+
+nb_status nb_train_bf16_refresh(TcModel *tc, const MlpDesc &d, cudaStream_t s) {
+    const TrainDesc t = make_desc(tc, d);
+    const long long total = (long long)train_img_elems(t.H, t.NH);
+    pack_train_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(t, (__nv_bfloat16 *)tc->train_img, total);
+    NB_CUDA(cudaGetLastError());
+    return NB_OK;
+}
+
+int nb_train_bf16_ctas(int64_t n) {
+    const int64_t tiles = (n + TM - 1) / TM;
+    int64_t g = num_sms();
+    if (g > tiles) g = tiles;
+    return (int)(g < 1 ? 1 : g);
+}
+
+nb_status nb_launch_train_bf16(TcModel *tc, const MlpDesc &d, const float *q, const uint32_t *labels, int64_t n,
+                               float alpha, float beta, TauF tau, TrainWs ws, nb_step_stats *st, cudaStream_t s) {
+    const TrainDesc t = make_desc(tc, d);
+    long long P = 0;
+    for (int l = 0; l < d.L; l++) P += (long long)d.w[l + 1] * (d.w[l] + 1);
+    NB_CUDA(cudaMemsetAsync(ws.partial, 0, (size_t)ws.G * P * sizeof(float), s));
+    if (st) NB_CUDA(cudaMemsetAsync(st, 0, sizeof(nb_step_stats), s));
+    const size_t smem = nb_train_bf16_smem(t.H, t.NH);
+    if (t.H == 128) {
+        NB_CUDA(cudaFuncSetAttribute(train_bf16_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        train_bf16_kernel<128><<<ws.G, 256, smem, s>>>(t, q, labels, (long long)n, alpha, beta, 1.0f / (float)n, tau,
+                                                       ws.partial, ws.loss_partial, P, st);
+    } else {
+        NB_CUDA(cudaFuncSetAttribute(train_bf16_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        train_bf16_kernel<64><<<ws.G, 256, smem, s>>>(t, q, labels, (long long)n, alpha, beta, 1.0f / (float)n, tau,
+                                                      ws.partial, ws.loss_partial, P, st);
+    }
+    NB_CUDA(cudaGetLastError());
+    return NB_OK;
+}
