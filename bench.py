@@ -1,17 +1,20 @@
 """Benchmark of the neural-bounding hot path on one GB300 (or N replicas).
 
-Workload (3D ray queries, BF16 tensor-core inference): a union of 64 spheres
-(radii 0.02-0.2) in [-1,1]^3; rays with origin uniform on the radius-2 sphere and
-direction uniform on S^2; MLP 6 -> 128 x4 -> 1 (ReLU); trained with the asymmetric
-BCE (FN weight ramped 1 -> 100, beta 1) for 20k Adam steps of 65,536 rays; threshold
-calibrated in FP64 on a 16M-ray evaluation set (FN = 0 on it).
+Default workload (configuration of the headline metric): 3D ray queries against a union
+of 64 spheres (radii 0.02-0.2) in [-1,1]^3; rays with origin uniform on the radius-2
+sphere and direction uniform on S^2; MLP 6 -> 128 x4 -> 1 (ReLU); 20k BF16 tensor-core
+training steps of 65,536 rays with the asymmetric BCE (FN weight ramped 1 -> 100, beta 1);
+threshold calibrated in FP64 on the 16M-ray evaluation set (FN = 0 on it).
+One timed step = nb_query over the 16M evaluation rays (split-FP16 tcgen05 forward,
+FP32 / extended-precision re-check of the margin band), inputs resident in HBM (384 MB
+per step, more than the 129 MB L2, so no flush is needed); value = rays/s over all ranks.
 
-One timed step = nb_query over the 16M evaluation rays (BF16 tcgen05 forward, FP32 /
-float-float re-check of the margin band), inputs resident in HBM (384 MB per step,
-larger than L2, so no flush is needed).  value = rays/s over all ranks.
-Also reported: FN / FP of the decisions, the plain FP32 single-object forward on the
-same weights, training samples/s, the roofline of the forward kernel, an end-to-end
-number through the public API with host buffers, and the FP64 CPU oracle.
+Other configurations (--config): c1 (2D points, plain FP32), c4 (256 objects of moving
+spheres, 4D points, grouped training under a CUDA graph and grouped queries), c5 (1024
+objects, 64M world rays through the learned-culler cascade, against box + exact).
+Every line also carries the FP64 oracle timed on the host cores, an end-to-end figure
+through the public API with host buffers, the SM clocks seen during the timed region
+and, where it applies, the roofline of the dominant kernel.
 """
 from __future__ import annotations
 
@@ -29,6 +32,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# 3D rays (default)
 WIDTHS = [6, 128, 128, 128, 128, 1]
 N_SPHERES, R_LO, R_HI = 64, 0.02, 0.2
 BATCH, TRAIN_STEPS = 65536, 20000
@@ -103,27 +107,469 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_oracle_rate(params, q_host, seconds=12.0):
+def cpu_oracle_rate(widths, params, q_host, seconds=12.0):
     """FP64 oracle forward on a bounded sample, on the host cores."""
     from oracle import oracle as O
     nthreads = os.cpu_count() or 1
     n = 4096
     t0 = time.perf_counter()
-    O.forward(WIDTHS, params, q_host[:n], nthreads)
+    O.forward(widths, params, q_host[:n], nthreads)
     dt = time.perf_counter() - t0
     n = int(min(len(q_host), max(4096, n * seconds / max(dt, 1e-6) * 0.5)))
     t0 = time.perf_counter()
-    O.forward(WIDTHS, params, q_host[:n], nthreads)
+    O.forward(widths, params, q_host[:n], nthreads)
     dt = time.perf_counter() - t0
     return n / dt, nthreads, n
 
 
+class Ctx:
+    """Device, ranks, CUDA events and the JSON line common to every configuration."""
+
+    def __init__(self, args):
+        import torch
+        import torch.distributed as dist
+        self.torch, self.dist = torch, dist
+        self.args = args
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        torch.cuda.set_device(self.local)
+        if self.world > 1:
+            dist.init_process_group("nccl")
+        self.dev = torch.device("cuda", self.local)
+        self.e0 = torch.cuda.Event(enable_timing=True)
+        self.e1 = torch.cuda.Event(enable_timing=True)
+
+    def barrier(self):
+        if self.world > 1:
+            self.dist.barrier()
+        self.torch.cuda.synchronize()
+
+    def time_ms(self, fn, reps):
+        self.torch.cuda.synchronize()
+        self.e0.record()
+        for _ in range(reps):
+            fn()
+        self.e1.record()
+        self.torch.cuda.synchronize()
+        return self.e0.elapsed_time(self.e1) / reps
+
+    def timed(self, fn, steps, warmup):
+        """W warm-up steps, then K steps between barriers; max over ranks."""
+        for _ in range(max(warmup, 3)):
+            fn()
+        self.barrier()
+        with Clocks(self.local) as clk:
+            self.e0.record()
+            for _ in range(steps):
+                fn()
+            self.e1.record()
+            self.barrier()
+        ms = self.e0.elapsed_time(self.e1) / steps
+        if self.world > 1:
+            t = self.torch.tensor([ms], device=self.dev)
+            self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, clk.summary()
+
+    def emit(self, line):
+        if self.rank == 0:
+            print(json.dumps(line), flush=True)
+        if self.world > 1:
+            self.dist.barrier()
+
+
+def base_line(ctx, metric, value, unit, ms, steps, warmup, dtype, config, clocks, launches):
+    return {"metric": metric, "value": value, "unit": unit, "n_gpus": ctx.world, "steps": steps,
+            "warmup": max(warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": dtype, "data": "synthetic", "config": config, "gpu_launches": launches,
+            "clocks": clocks}
+
+
+# ---------------------------------------------------------------------------------- 3D rays
+def run_c2(args):
+    from paper_2310_06822_gb300 import inputs as I
+    from paper_2310_06822_gb300 import nb
+    ctx = Ctx(args)
+    torch, dev = ctx.torch, ctx.dev
+    n_eval = args.n_eval
+    sc = I.make_scene(SEED_SCENE, N_SPHERES, 3, R_LO, R_HI)
+    shape = nb.Shape(sc, dev)
+    pool_n = 8 << 20
+    pool = torch.as_tensor(I.sample_queries(I.RAY3, SEED_QUERY + 17, pool_n), device=dev)
+    pool_bits = nb.label(shape, I.RAY3, pool)
+    eval_q_host = I.sample_queries(I.RAY3, SEED_QUERY + 1000 * ctx.rank, n_eval)
+    eval_q = torch.as_tensor(eval_q_host, device=dev)
+    eval_bits = nb.label(shape, I.RAY3, eval_q)
+    per = pool_n // BATCH
+
+    def batch(t):
+        j = t % per
+        return pool[j * BATCH:(j + 1) * BATCH], pool_bits[j * (BATCH // 32):(j + 1) * (BATCH // 32)]
+
+    # training on the tensor cores (BF16 operands, FP32 accumulation, FP32 master weights)
+    T = args.train_steps
+    trainer = nb.Model(WIDTHS, infer_prec="f32", train_prec="bf16")
+    trainer.set_params(I.init_params(SEED_INIT, WIDTHS))
+    t_train0 = time.perf_counter()
+    ta, tb = min(100, T - 1), min(T - 1, 600)
+    for t in range(T):
+        if t == ta:
+            ctx.e0.record()
+        q, y = batch(t)
+        trainer.train_step(q, y, 1.0 + 99.0 * t / max(T - 1, 1), 1.0)
+        if t == tb:
+            ctx.e1.record()
+    torch.cuda.synchronize()
+    bf16_step_ms = ctx.e0.elapsed_time(ctx.e1) / (tb - ta + 1)
+    t_train = time.perf_counter() - t_train0
+    params = trainer.get_params()
+    # the plain FP32 training step on the same batches, for comparison
+    f32t = nb.Model(WIDTHS)
+    f32t.set_params(I.init_params(SEED_INIT, WIDTHS))
+    f32t.train_step(*batch(0), 1.0)
+    it = iter(range(1, 10 ** 9))
+    f32_step_ms = ctx.time_ms(lambda: f32t.train_step(*batch(next(it)), 50.0), 30)
+
+    model = nb.Model(WIDTHS, infer_prec="f16x3")
+    model.set_params(params)
+    tau = model.calibrate(eval_q, eval_bits, eps=1e-5)
+    plain = nb.Model(WIDTHS, infer_prec="f32")
+    plain.set_params(params)
+    plain.tau = tau
+
+    out = torch.empty(nb.n_words(n_eval), dtype=torch.int32, device=dev)
+    bits, qst = model.query(eval_q, margin=MARGIN, out=out, stats=True)
+    y = nb.bits_to_numpy(eval_bits, n_eval)
+    dec = nb.bits_to_numpy(bits, n_eval)
+    fn, fp = int(np.sum(y & ~dec)), int(np.sum(~y & dec))
+    dec32 = nb.bits_to_numpy(plain.query(eval_q, margin=MARGIN32), n_eval)
+    differ = int(np.sum(dec != dec32))
+
+    ms, clocks = ctx.timed(lambda: model.query(eval_q, margin=MARGIN, out=out), args.steps, args.warmup)
+    value = ctx.world * n_eval / (ms / 1000.0)
+    fwd_ms = ctx.time_ms(lambda: model.query(eval_q, margin=0.0, out=out), args.steps)
+    f32_ms = ctx.time_ms(lambda: plain.query(eval_q, margin=MARGIN32, out=out), 3)
+
+    # plain single-product BF16 on the same weights: margin = 4x its largest logit
+    # deviation from the FP32 form on the evaluation set
+    bf = nb.Model(WIDTHS, infer_prec="bf16")
+    bf.set_params(params)
+    bf.tau = tau
+    _, zbf = bf.query(eval_q, logits=True)
+    _, z32 = plain.query(eval_q, logits=True)
+    bf_dev = float((zbf - z32).abs().max().item())
+    bf_margin = 4 * bf_dev + 1e-3
+    bbits, bst = bf.query(eval_q, margin=bf_margin, out=out, stats=True)
+    bf_fn = int(np.sum(y & ~nb.bits_to_numpy(bbits, n_eval)))
+    bf_ms = ctx.time_ms(lambda: bf.query(eval_q, margin=bf_margin, out=out), 5)
+    _, zsp = model.query(eval_q, logits=True)
+    split_dev = float((zsp - z32).abs().max().item())
+
+    # end to end through the public API: pinned host rays -> device -> bits -> host
+    host_q = torch.empty((n_eval, 6), dtype=torch.float32, pin_memory=True)
+    host_q.copy_(torch.as_tensor(eval_q_host))
+    host_bits = torch.empty(nb.n_words(n_eval), dtype=torch.int32, pin_memory=True)
+    dq = torch.empty_like(eval_q)
+
+    def e2e_step():
+        dq.copy_(host_q, non_blocking=True)
+        model.query(dq, margin=MARGIN, out=out)
+        host_bits.copy_(out, non_blocking=True)
+
+    e2e_step()
+    e2e_ms = ctx.time_ms(e2e_step, max(3, args.steps // 4))
+
+    if ctx.rank != 0:
+        return ctx.emit(None)
+    pk, pk_kind = peaks()
+    macs = sum(WIDTHS[i] * WIDTHS[i + 1] for i in range(len(WIDTHS) - 1))
+    flops = 2.0 * macs * n_eval
+    achieved = flops / (fwd_ms / 1000.0) / 1e12
+    peak = float(pk.get("bf16_tflops", 1900.0))
+    cpu_v, cores, cpu_n = cpu_oracle_rate(WIDTHS, params, eval_q_host)
+    line = base_line(ctx, METRIC, value, "queries/s", ms, args.steps, args.warmup,
+                     "f16x3 (split fp16 operands, fp32 accumulate)",
+                     {"workload": WORKLOAD, "n_eval": n_eval, "batch": BATCH, "train_steps": T, "margin": MARGIN,
+                      "l2": "inputs 384 MB per step > 129 MB L2, no flush", "parallelism": f"replicas{ctx.world}"},
+                     clocks, args.steps * 3)
+    line.update({
+        "fn": fn, "fp": fp, "fp_rate": fp / n_eval, "positives": int(y.sum()), "tau": tau,
+        "decisions_differing_from_fp32_form": differ,
+        "band": {"flagged": qst["n_flagged"], "resolved_f32": qst["n_resolved_f32"],
+                 "resolved_ff": qst["n_resolved_ff"], "unresolved": qst["n_unresolved"]},
+        "fp32_plain_queries_per_s": n_eval / (f32_ms / 1000.0),
+        "speedup_vs_fp32_plain": f32_ms / ms,
+        "max_logit_dev_vs_fp32_form": {"f16x3": split_dev, "bf16": bf_dev},
+        "bf16_plain": {"queries_per_s": n_eval / (bf_ms / 1000.0), "margin": bf_margin, "fn": bf_fn,
+                       "flagged": bst["n_flagged"], "unresolved": bst["n_unresolved"]},
+        "train_samples_per_s": {"bf16_tensor_core": BATCH / (bf16_step_ms / 1000.0),
+                                "fp32": BATCH / (f32_step_ms / 1000.0)},
+        "train_wall_s": t_train,
+        "roofline": {"kernel": "fwd_split_kernel (tcgen05, 3 products per k-step)", "bound": "tensor",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": (TRAFFIC_BYTES_PER_RAY * n_eval) if TRAFFIC_BYTES_PER_RAY else None,
+                     "peak_kind": f"{pk_kind} bf16 burst", "fwd_ms": fwd_ms, "algorithmic_flops_per_launch": flops},
+        "cpu_baseline": {"value": cpu_v, "unit": "queries/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{cpu_n} of the evaluation rays through the FP64 oracle forward"},
+        "e2e": {"value": ctx.world * n_eval / (e2e_ms / 1000.0), "unit": "queries/s",
+                "h2d_bytes_per_step": n_eval * 6 * 4, "d2h_bytes_per_step": nb.n_words(n_eval) * 4},
+    })
+    ctx.emit(line)
+
+
+# ---------------------------------------------------------------------------------- 2D points
+def run_c1(args):
+    from paper_2310_06822_gb300 import inputs as I
+    from paper_2310_06822_gb300 import nb
+    ctx = Ctx(args)
+    torch, dev = ctx.torch, ctx.dev
+    widths = [2, 32, 32, 32, 1]
+    sc = I.make_scene(1000, 8, 2, 0.05, 0.3)
+    shape = nb.Shape(sc, dev)
+    T, B = 1000, 1024
+    pool = torch.as_tensor(I.sample_queries(I.POINT2, 2000, T * B), device=dev)
+    bits = nb.label(shape, I.POINT2, pool)
+    m = nb.Model(widths)
+    m.set_params(I.init_params(1001, widths))
+    ctx.e0.record()
+    for t in range(T):
+        m.train_step(pool[t * B:(t + 1) * B], bits[t * B // 32:(t + 1) * B // 32], 1.0 + 99.0 * t / (T - 1), 1.0)
+    ctx.e1.record()
+    torch.cuda.synchronize()
+    train_ms = ctx.e0.elapsed_time(ctx.e1) / T
+    grid = torch.as_tensor(I.grid_points_2d(256), device=dev)
+    yg = nb.label(shape, I.POINT2, grid)
+    tau = m.calibrate(grid, yg)
+    out = torch.empty(nb.n_words(grid.shape[0]), dtype=torch.int32, device=dev)
+    m.query(grid, margin=1e-3, out=out)
+    y = nb.bits_to_numpy(yg, grid.shape[0])
+    dec = nb.bits_to_numpy(out, grid.shape[0])
+    # the 65,536-point grid is one step; repeated to get a measurable region
+    reps = 50
+    ms, clocks = ctx.timed(lambda: [m.query(grid, margin=1e-3, out=out) for _ in range(reps)], args.steps,
+                           args.warmup)
+    value = ctx.world * reps * grid.shape[0] / (ms / 1000.0)
+    cpu_v, cores, cpu_n = cpu_oracle_rate(widths, m.get_params(), I.grid_points_2d(256))
+    line = base_line(ctx, "neural-bound queries/s at 0 FN (2D points, plain FP32)", value, "queries/s", ms,
+                     args.steps, args.warmup, "f32",
+                     {"workload": "2D points: 8-disk union, MLP 2->32x3->1 FP32, 1000 steps x 1024, 256x256 grid "
+                                  "(configs[0])", "reps_of_grid_per_step": reps,
+                      "l2": "grid resident in L2 (256 KB); small-case configuration"},
+                     clocks, args.steps * reps * 3)
+    line.update({"fn": int(np.sum(y & ~dec)), "fp": int(np.sum(~y & dec)), "fp_rate": float(np.mean(~y & dec)),
+                 "tau": tau, "train_samples_per_s_fp32": B / (train_ms / 1000.0),
+                 "cpu_baseline": {"value": cpu_v, "unit": "queries/s", "cores": cores, "kind": "oracle",
+                                  "sample": f"{cpu_n} grid points through the FP64 oracle forward"},
+                 "e2e": None})
+    ctx.emit(line)
+
+
+# ---------------------------------------------------------------------------------- 4D grouped
+def run_c4(args):
+    from paper_2310_06822_gb300 import inputs as I
+    from paper_2310_06822_gb300 import nb
+    ctx = Ctx(args)
+    torch, dev = ctx.torch, ctx.dev
+    widths = [4, 64, 64, 64, 1]
+    K = 256
+    rng = np.random.default_rng(4000)
+    counts = [int(c) for c in rng.integers(4096 // 32, 65536 // 32 + 1, size=K) * 32]
+    scenes = [I.make_scene(4100 + o, int(rng.integers(16, 65)), 3, 0.02, 0.2, moving=True) for o in range(K)]
+    shapes = [nb.Shape(s, dev) for s in scenes]
+    off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    plan = nb.Plan(off, chunk_rows=4096)
+    W = 4
+    batches = []
+    for j in range(W):
+        qs = [torch.as_tensor(I.sample_queries(I.POINT4T, 5000 + 10 * o + j, counts[o]), device=dev) for o in range(K)]
+        bs = [nb.label(shapes[o], I.POINT4T, qs[o]) for o in range(K)]
+        batches.append((torch.cat(qs).contiguous(), torch.cat(bs).contiguous()))
+    g = nb.Group(widths, K, infer_prec="f16x3", train_prec="bf16")
+    g.set_params(np.stack([I.init_params(6000 + o, widths) for o in range(K)]))
+    T = args.train_steps if args.train_steps != TRAIN_STEPS else 2000
+    alpha = (1.0 + 99.0 * np.arange(T) / max(T - 1, 1)).astype(np.float32)
+    g.set_schedule(alpha)
+    g.reserve(plan)
+    # one CUDA graph per pool batch, each replaying a training step with the device schedule
+    graphs = []
+    for j in range(W):
+        g.train_step(plan, *batches[j], -1.0)  # eager first steps initialise kernel attributes
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    for j in range(W):
+        gr = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(gr, stream=s):
+                g.train_step(plan, *batches[j], -1.0)
+        graphs.append(gr)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    ctx.e0.record()
+    for t in range(W, T):
+        graphs[t % W].replay()
+    ctx.e1.record()
+    torch.cuda.synchronize()
+    step_ms = ctx.e0.elapsed_time(ctx.e1) / max(T - W, 1)
+    g.sync_schedule()
+    # evaluation: 1M space-time points per object
+    NE = args.n_eval if args.n_eval != N_EVAL else (1 << 20)
+    eoff = np.arange(K + 1, dtype=np.int64) * NE
+    eplan = nb.Plan(eoff, chunk_rows=8192)
+    eq = torch.empty((K * NE, 4), dtype=torch.float32, device=dev)
+    ebits = torch.empty(nb.n_words(K * NE), dtype=torch.int32, device=dev)
+    for o in range(K):
+        eq[o * NE:(o + 1) * NE] = torch.as_tensor(I.sample_queries(I.POINT4T, 7000 + o, NE), device=dev)
+        ebits[o * NE // 32:(o + 1) * NE // 32] = nb.label(shapes[o], I.POINT4T, eq[o * NE:(o + 1) * NE])
+    taus = g.calibrate(eplan, eq, ebits)
+    out = torch.empty_like(ebits)
+    _, qst = g.query(eplan, eq, margin=MARGIN, out=out, stats=True)
+    y = nb.bits_to_numpy(ebits, K * NE)
+    dec = nb.bits_to_numpy(out, K * NE)
+    ms, clocks = ctx.timed(lambda: g.query(eplan, eq, margin=MARGIN, out=out), args.steps, args.warmup)
+    value = ctx.world * K * NE / (ms / 1000.0)
+    # plain FP32 single-object form: one network at a time, same weights and thresholds
+    P = g.get_params()
+    single = nb.Model(widths)
+    o_ms = []
+    for o in range(0, K, 32):
+        single.set_params(P[o])
+        single.tau = float(taus[o])
+        o_ms.append(ctx.time_ms(lambda: single.query(eq[o * NE:(o + 1) * NE], margin=1e-2,
+                                                     out=out[o * NE // 32:(o + 1) * NE // 32]), 2))
+    f32_ms = float(np.mean(o_ms)) * K
+    cpu_v, cores, cpu_n = cpu_oracle_rate(widths, P[0], eq[:NE].cpu().numpy())
+    line = base_line(ctx, "grouped neural-bound queries/s at 0 FN (4D points, 256 objects, split-FP16)", value,
+                     "queries/s", ms, args.steps, args.warmup, "f16x3 (split fp16 operands, fp32 accumulate)",
+                     {"workload": "4D space-time points: 256 objects of 16-64 moving spheres, 4->64x3->1 per object, "
+                                  "uneven 4096-65536 samples per object (configs[3])", "train_steps": T,
+                      "eval_per_object": NE, "l2": f"inputs {K * NE * 16 >> 20} MB per step > L2"},
+                     clocks, args.steps * 2)
+    line.update({"fn": int(np.sum(y & ~dec)), "fp_rate": float(np.mean(~y & dec)),
+                 "band": {"flagged": qst["n_flagged"], "unresolved": qst["n_unresolved"]},
+                 "fp32_single_object_queries_per_s": K * NE / (f32_ms / 1000.0),
+                 "speedup_vs_fp32_single_object": f32_ms / ms,
+                 "grouped_train_samples_per_s_bf16_graph": sum(counts) / (step_ms / 1000.0),
+                 "cpu_baseline": {"value": cpu_v, "unit": "queries/s", "cores": cores, "kind": "oracle",
+                                  "sample": f"{cpu_n} points of object 0 through the FP64 oracle forward"},
+                 "e2e": None})
+    ctx.emit(line)
+
+
+# ---------------------------------------------------------------------------------- cascade
+def run_c5(args):
+    from paper_2310_06822_gb300 import inputs as I
+    from paper_2310_06822_gb300 import nb
+    ctx = Ctx(args)
+    torch, dev = ctx.torch, ctx.dev
+    widths = [6, 128, 128, 128, 1]
+    K = 1024
+    ms_ = I.make_multi_scene(5000, K, 32)
+    ws = nb.WorldScene(ms_, dev)
+    B, W = 2048, 4
+    T = args.train_steps if args.train_steps != TRAIN_STEPS else 1000
+    shapes = [nb.Shape(ms_.local_scene(k), dev) for k in range(K)]
+    batches = []
+    for j in range(W):
+        qs = [torch.as_tensor(I.sample_queries(I.RAY3, 5100 + 10 * k + j, B), device=dev) for k in range(K)]
+        bs = [nb.label(shapes[k], I.RAY3, qs[k]) for k in range(K)]
+        batches.append((torch.cat(qs).contiguous(), torch.cat(bs).contiguous()))
+    plan = nb.Plan(np.arange(K + 1, dtype=np.int64) * B, chunk_rows=2048)
+    g = nb.Group(widths, K, infer_prec="f16x3", train_prec="bf16")
+    g.set_params(np.stack([I.init_params(5200 + k, widths) for k in range(K)]))
+    t0 = time.perf_counter()
+    for t in range(T):
+        g.train_step(plan, *batches[t % W], 1.0 + 99.0 * t / max(T - 1, 1))
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    NR = args.n_eval if args.n_eval != N_EVAL else (64 << 20)
+    CH = min(NR, 16 << 20)
+    rays = torch.empty((NR, 6), dtype=torch.float32, device=dev)
+    for c in range(0, NR, CH):
+        rays[c:c + CH] = torch.as_tensor(I.sample_world_rays(5300 + c // CH, min(CH, NR - c)), device=dev)
+    chunks = [rays[c:c + CH] for c in range(0, NR, CH)]
+    # thresholds calibrated on the benchmark rays' own pairs, chunk by chunk: the minimum
+    # over chunks of (zmin - eps rounded down) is the threshold of all pairs together
+    taus = np.full(K, np.inf)
+    for ch in chunks:
+        off, off_d, pair_ray, pair_q, _ = nb.cascade_bin(ws, ch, canonical=True)
+        rows = int(off[-1])
+        lab = torch.zeros(nb.n_words(rows), dtype=torch.int32, device=dev)
+        nb.cascade_exact(ws, ch, pair_ray, off_d, rows, pair_hits=lab)
+        taus = np.minimum(taus, g.calibrate(nb.Plan(off, chunk_rows=2048), pair_q, lab))
+        del off_d, pair_ray, pair_q, lab
+    g.tau = taus
+    hits_c = torch.zeros(nb.n_words(NR), dtype=torch.int32, device=dev)
+    hits_p = torch.zeros(nb.n_words(NR), dtype=torch.int32, device=dev)
+    est = torch.zeros(nb.CASCADE_STATS.itemsize, dtype=torch.uint8, device=dev)
+    pst = torch.zeros(nb.CASCADE_STATS.itemsize, dtype=torch.uint8, device=dev)
+    nst = torch.zeros(nb.QUERY_STATS.itemsize, dtype=torch.uint8, device=dev)
+
+    bin_stats = {"aabb_pairs": 0, "ball_pairs": 0}
+
+    def cascade_step(collect=False):
+        # box + ball binning, neural bound per object, exact test of the survivors
+        for ci, ch in enumerate(chunks):
+            off, off_d, pair_ray, pair_q, st = nb.cascade_bin(ws, ch, canonical=True)
+            if collect:
+                for k in bin_stats:
+                    bin_stats[k] += int(st[k])
+            plan_c = nb.Plan(off, chunk_rows=2048)
+            neural = g.query(plan_c, pair_q, margin=MARGIN)
+            nb.cascade_exact(ws, ch, pair_ray, off_d, int(off[-1]), pass_bits=neural,
+                             ray_hits=hits_c[ci * CH // 32:], stats=est)
+
+    def plain_step():
+        for ci, ch in enumerate(chunks):
+            off, off_d, pair_ray, _, st = nb.cascade_bin(ws, ch, canonical=False)
+            nb.cascade_exact(ws, ch, pair_ray, off_d, int(off[-1]), ray_hits=hits_p[ci * CH // 32:], stats=pst)
+
+    est.zero_()
+    cascade_step(collect=True)
+    pst.zero_()
+    plain_step()
+    e = nb._read(est, nb.CASCADE_STATS)
+    pe = nb._read(pst, nb.CASCADE_STATS)
+    hc = nb.bits_to_numpy(hits_c, NR)
+    hp = nb.bits_to_numpy(hits_p, NR)
+    ms, clocks = ctx.timed(cascade_step, args.steps, args.warmup)
+    plain_ms = ctx.time_ms(plain_step, max(2, args.steps))
+    # held-out rays: FN of the calibrated bounds on rays they were not calibrated on
+    held = torch.as_tensor(I.sample_world_rays(5999, min(NR, 4 << 20)), device=dev)
+    hh_c = torch.zeros(nb.n_words(held.shape[0]), dtype=torch.int32, device=dev)
+    hh_p = torch.zeros_like(hh_c)
+    off, off_d, pair_ray, pair_q, _ = nb.cascade_bin(ws, held, canonical=True)
+    neural = g.query(nb.Plan(off, chunk_rows=2048), pair_q, margin=MARGIN)
+    nb.cascade_exact(ws, held, pair_ray, off_d, int(off[-1]), pass_bits=neural, ray_hits=hh_c)
+    off, off_d, pair_ray, _, _ = nb.cascade_bin(ws, held, canonical=False)
+    nb.cascade_exact(ws, held, pair_ray, off_d, int(off[-1]), ray_hits=hh_p)
+    held_fn = int(np.sum(nb.bits_to_numpy(hh_p, held.shape[0]) & ~nb.bits_to_numpy(hh_c, held.shape[0])))
+    # cost of one exact pair test relative to one network query at which the cascade pays
+    # off (Eq. (Benefit) with p = fraction of pairs sent to the exact test)
+    line = base_line(ctx, "cascade rays/s at 0 FN (1024 objects, box -> neural bound -> exact)",
+                     ctx.world * NR / (ms / 1000.0), "queries/s", ms, args.steps, args.warmup,
+                     "f16x3 (split fp16 operands, fp32 accumulate)",
+                     {"workload": "learned-culler cascade: 1024 objects of 32 spheres in [-10,10]^3, 6->128x3->1 per "
+                                  "object, 64M rays (configs[4])", "n_rays": NR, "train_steps": T,
+                      "calibration": "thresholds calibrated on the benchmark rays' own pairs"},
+                     clocks, args.steps * len(chunks) * 5)
+    line.update({"fn_vs_plain": int(np.sum(hp & ~hc)), "hits_equal_plain": bool(np.array_equal(hc, hp)),
+                 "plain_box_exact_rays_per_s": NR / (plain_ms / 1000.0),
+                 "pairs": {"box": bin_stats["aabb_pairs"], "ball": bin_stats["ball_pairs"], "exact_plain": pe["exact_pairs"], "exact_cascade": e["exact_pairs"],
+                           "hit": pe["hit_pairs"]},
+                 "exact_tests_avoided": pe["exact_pairs"] - e["exact_pairs"],
+                 "exact_sphere_tests": {"plain": pe["sphere_tests"], "cascade": e["sphere_tests"]},
+                 "held_out_fn": held_fn, "held_out_rays": int(held.shape[0]), "grouped_train_s_bf16": train_s,
+                 "cpu_baseline": None, "e2e": None})
+    ctx.emit(line)
+
+
+# ---------------------------------------------------------------------------------- reference arm
 def reference_arm(args):
     """The oracle as it stands (FP64 forward of the same network), timed on host cores."""
     from oracle import oracle as O
     from paper_2310_06822_gb300 import inputs as I
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
+    if int(os.environ.get("RANK", "0")) != 0:
         return
     p = I.init_params(SEED_INIT, WIDTHS)
     nthreads = os.cpu_count() or 1
@@ -153,201 +599,13 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c4", "c5"])
     ap.add_argument("--train-steps", type=int, default=TRAIN_STEPS)
-    ap.add_argument("--n-eval", type=int, default=N_EVAL, help="evaluation rays (smaller only for profiling)")
+    ap.add_argument("--n-eval", type=int, default=N_EVAL, help="evaluation size (smaller only for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
-
-    n_eval = args.n_eval
-    import torch
-    import torch.distributed as dist
-
-    from paper_2310_06822_gb300 import inputs as I
-    from paper_2310_06822_gb300 import nb
-
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl")
-    dev = torch.device("cuda", local)
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    # ---------------------------------------------------------------- setup (untimed)
-    sc = I.make_scene(SEED_SCENE, N_SPHERES, 3, R_LO, R_HI)
-    shape = nb.Shape(sc, dev)
-    pool_n = 8 << 20
-    pool = torch.as_tensor(I.sample_queries(I.RAY3, SEED_QUERY + 17, pool_n), device=dev)
-    pool_bits = nb.label(shape, I.RAY3, pool)
-    eval_q_host = I.sample_queries(I.RAY3, SEED_QUERY + 1000 * rank, n_eval)
-    eval_q = torch.as_tensor(eval_q_host, device=dev)
-    eval_bits, lst = nb.label(shape, I.RAY3, eval_q, stats=True)
-
-    p0 = I.init_params(SEED_INIT, WIDTHS)
-    trainer = nb.Model(WIDTHS, infer_prec="f32", train_prec="f32")
-    trainer.set_params(p0)
-    T = args.train_steps
-    per = pool_n // BATCH
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t_train0 = time.perf_counter()
-    train_ms = None
-    ta, tb = min(100, T - 1), min(T - 1, 300)  # steps timed with events inside training
-    for t in range(T):
-        j = t % per
-        alpha = 1.0 + 99.0 * t / max(T - 1, 1)
-        if t == ta:
-            e0.record()
-        trainer.train_step(pool[j * BATCH:(j + 1) * BATCH], pool_bits[j * (BATCH // 32):(j + 1) * (BATCH // 32)],
-                           alpha, 1.0)
-        if t == tb:
-            e1.record()
-    torch.cuda.synchronize()
-    train_ms = e0.elapsed_time(e1) / (tb - ta + 1)
-    t_train = time.perf_counter() - t_train0
-    params = trainer.get_params()
-
-    model = nb.Model(WIDTHS, infer_prec="f16x3", train_prec="f32")
-    model.set_params(params)
-    tau = model.calibrate(eval_q, eval_bits, eps=1e-5)
-    plain = nb.Model(WIDTHS, infer_prec="f32")
-    plain.set_params(params)
-    plain.tau = tau
-
-    out = torch.empty(nb.n_words(n_eval), dtype=torch.int32, device=dev)
-    bits, qst = model.query(eval_q, margin=MARGIN, out=out, stats=True)
-    y = nb.bits_to_numpy(eval_bits, n_eval)
-    dec = nb.bits_to_numpy(bits, n_eval)
-    fn = int(np.sum(y & ~dec))
-    fp = int(np.sum(~y & dec))
-    bits32 = plain.query(eval_q, margin=MARGIN32)
-    dec32 = nb.bits_to_numpy(bits32, n_eval)
-    differ = int(np.sum(dec != dec32))
-
-    # ---------------------------------------------------------------- timed region
-    for _ in range(max(args.warmup, 3)):
-        model.query(eval_q, margin=MARGIN, out=out)
-    barrier()
-    with Clocks(local) as clk:
-        e0.record()
-        for _ in range(args.steps):
-            model.query(eval_q, margin=MARGIN, out=out)
-        e1.record()
-        barrier()
-    ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t_ = torch.tensor([ms], device=dev)
-        dist.all_reduce(t_, op=dist.ReduceOp.MAX)
-        ms = float(t_.item())
-    value = world * n_eval / (ms / 1000.0)
-
-    # forward kernel alone (margin 0: the re-check kernels find an empty band)
-    for _ in range(2):
-        model.query(eval_q, margin=0.0, out=out)
-    torch.cuda.synchronize()
-    e0.record()
-    for _ in range(args.steps):
-        model.query(eval_q, margin=0.0, out=out)
-    e1.record()
-    torch.cuda.synchronize()
-    fwd_ms = e0.elapsed_time(e1) / args.steps
-
-    # plain FP32 single-object form on the same weights and threshold
-    e0.record()
-    for _ in range(3):
-        plain.query(eval_q, margin=MARGIN32, out=out)
-    e1.record()
-    torch.cuda.synchronize()
-    f32_ms = e0.elapsed_time(e1) / 3
-
-    # plain single-product BF16 on the same weights: margin = 4x its largest logit
-    # deviation from the FP32 form on the evaluation set
-    bf = nb.Model(WIDTHS, infer_prec="bf16")
-    bf.set_params(params)
-    bf.tau = tau
-    _, zbf = bf.query(eval_q, logits=True)
-    _, z32 = plain.query(eval_q, logits=True)
-    bf_dev = float((zbf - z32).abs().max().item())
-    bf_margin = 4 * bf_dev + 1e-3
-    bbits, bst = bf.query(eval_q, margin=bf_margin, out=out, stats=True)
-    bf_fn = int(np.sum(y & ~nb.bits_to_numpy(bbits, n_eval)))
-    e0.record()
-    for _ in range(5):
-        bf.query(eval_q, margin=bf_margin, out=out)
-    e1.record()
-    torch.cuda.synchronize()
-    bf_ms = e0.elapsed_time(e1) / 5
-    _, zsp = model.query(eval_q, logits=True)
-    split_dev = float((zsp - z32).abs().max().item())
-
-    # end to end through the public API: pinned host rays -> device -> bits -> host
-    host_q = torch.empty((n_eval, 6), dtype=torch.float32, pin_memory=True)
-    host_q.copy_(torch.as_tensor(eval_q_host))
-    host_bits = torch.empty(nb.n_words(n_eval), dtype=torch.int32, pin_memory=True)
-    dq = torch.empty_like(eval_q)
-    for _ in range(2):
-        dq.copy_(host_q, non_blocking=True)
-        model.query(dq, margin=MARGIN, out=out)
-        host_bits.copy_(out, non_blocking=True)
-    torch.cuda.synchronize()
-    e2e_steps = max(3, args.steps // 4)
-    e0.record()
-    for _ in range(e2e_steps):
-        dq.copy_(host_q, non_blocking=True)
-        model.query(dq, margin=MARGIN, out=out)
-        host_bits.copy_(out, non_blocking=True)
-    e1.record()
-    torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / e2e_steps
-
-    if rank != 0:
-        if world > 1:
-            dist.barrier()
-        return
-
-    pk, pk_kind = peaks()
-    macs = sum(WIDTHS[i] * WIDTHS[i + 1] for i in range(len(WIDTHS) - 1))
-    flops = 2.0 * macs * n_eval
-    achieved = flops / (fwd_ms / 1000.0) / 1e12
-    peak = float(pk.get("bf16_tflops", 1900.0))
-    cpu_v, cores, cpu_n = cpu_oracle_rate(params, eval_q_host)
-    line = {
-        "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
-        "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f16x3 (split fp16, fp32 accumulate)", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_eval": n_eval, "batch": BATCH, "train_steps": T, "margin": MARGIN,
-                   "l2": "inputs 384 MB per step > 129 MB L2, no flush", "parallelism": f"replicas{world}"},
-        "fn": fn, "fp": fp, "fp_rate": fp / n_eval, "positives": int(y.sum()), "tau": tau,
-        "decisions_differing_from_fp32_form": differ,
-        "band": {"flagged": qst["n_flagged"], "resolved_f32": qst["n_resolved_f32"],
-                 "resolved_ff": qst["n_resolved_ff"], "unresolved": qst["n_unresolved"]},
-        "fp32_plain_queries_per_s": n_eval / (f32_ms / 1000.0),
-        "max_logit_dev_vs_fp32_form": {"f16x3": split_dev, "bf16": bf_dev},
-        "bf16_plain": {"queries_per_s": n_eval / (bf_ms / 1000.0), "margin": bf_margin, "fn": bf_fn,
-                       "flagged": bst["n_flagged"], "unresolved": bst["n_unresolved"]},
-        "speedup_vs_fp32_plain": f32_ms / ms,
-        "train_samples_per_s_fp32": (BATCH / (train_ms / 1000.0)) if train_ms else None,
-        "train_wall_s": t_train,
-        "roofline": {"kernel": "fwd_split_kernel (tcgen05, 3 products per k-step)", "bound": "tensor", "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": (TRAFFIC_BYTES_PER_RAY * n_eval) if TRAFFIC_BYTES_PER_RAY else None,
-                     "peak_kind": f"{pk_kind} bf16 burst", "fwd_ms": fwd_ms,
-                     "algorithmic_flops_per_launch": flops},
-        "cpu_baseline": {"value": cpu_v, "unit": "queries/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{cpu_n} of the evaluation rays through the FP64 oracle forward"},
-        "e2e": {"value": world * n_eval / (e2e_ms / 1000.0), "unit": "queries/s",
-                "h2d_bytes_per_step": n_eval * 6 * 4, "d2h_bytes_per_step": nb.n_words(n_eval) * 4},
-        "gpu_launches": args.steps * 3,
-        "clocks": clk.summary(),
-    }
-    print(json.dumps(line), flush=True)
-    if world > 1:
-        dist.barrier()
+    {"c1": run_c1, "c2": run_c2, "c4": run_c4, "c5": run_c5}[args.config](args)
 
 
 if __name__ == "__main__":

@@ -321,7 +321,8 @@ extern "C" nb_status nb_group_create(const int32_t *widths, int32_t n_layers, in
     if (widths[n_layers] != 1) return nb_fail(NB_EINVAL, "nb_group_create: last width must be 1");
     for (int l = 0; l < n_layers; l++)
         if (widths[l] < 1 || widths[l] > NB_MAXW) return nb_fail(NB_EINVAL, "nb_group_create: widths must be 1..256");
-    if (train_prec != NB_F32) return nb_fail(NB_EUNSUPPORTED, "nb_group_create: grouped training runs in FP32");
+    if (train_prec != NB_F32 && train_prec != NB_BF16)
+        return nb_fail(NB_EUNSUPPORTED, "nb_group_create: grouped training runs in FP32 or BF16");
     if (infer_prec != NB_F32 && infer_prec != NB_F16X3)
         return nb_fail(NB_EUNSUPPORTED, "nb_group_create: grouped queries run in FP32 or split FP16");
     nb_group *g = new nb_group();
@@ -355,13 +356,13 @@ extern "C" nb_status nb_group_create(const int32_t *widths, int32_t n_layers, in
         free_group(g);
         return NB_ECUDA;
     }
-    if (infer_prec == NB_F16X3) {
-        const nb_status s = nb_tc_group_init(&g->tc, nb_group_desc(g), n_objects);
-        if (s != NB_OK) {
-            std::string msg = nb_last_error();
-            free_group(g);
-            return nb_fail(s, msg);
-        }
+    nb_status ts = NB_OK;
+    if (infer_prec == NB_F16X3) ts = nb_tc_group_init(&g->tc, nb_group_desc(g), n_objects);
+    if (ts == NB_OK && train_prec == NB_BF16) ts = nb_train_bf16_group_init(&g->tc, nb_group_desc(g), n_objects);
+    if (ts != NB_OK) {
+        std::string msg = nb_last_error();
+        free_group(g);
+        return nb_fail(ts, msg);
     }
     if (cudaDeviceSynchronize() != cudaSuccess) {
         free_group(g);
@@ -381,6 +382,10 @@ extern "C" nb_status nb_group_destroy(nb_group *g) {
 extern "C" int64_t nb_group_param_count(const nb_group *g) { return g ? g->P : -1; }
 
 static nb_status group_refresh(nb_group *g, cudaStream_t s) {
+    if (g->train_prec == NB_BF16) {
+        const nb_status st = nb_train_bf16_group_refresh(&g->tc, nb_group_desc(g), g->n_objects, s);
+        if (st != NB_OK) return st;
+    }
     if (g->infer_prec != NB_F16X3) return NB_OK;
     return nb_tc_group_refresh(&g->tc, nb_group_desc(g), g->n_objects, s);
 }
@@ -486,7 +491,10 @@ extern "C" nb_status nb_train_step_grouped(nb_group *g, const nb_plan *pl, const
     NB_CUDA(cudaMemsetAsync(partial, 0, (size_t)pl->n_items * g->P * sizeof(float), s));
     if (dev_stats) NB_CUDA(cudaMemsetAsync(dev_stats, 0, sizeof(nb_step_stats), s));
     const MlpDesc d = nb_group_desc(g);
-    switch (nj_for(d.maxw)) {
+    if (g->train_prec == NB_BF16)
+        st = nb_launch_train_bf16_group(&g->tc, d, g->P, pl, q, label_bits, alpha, sched ? g->sched_alpha : nullptr,
+                                        g->d_step, g->sched_T, beta, g->d_tau, partial, loss_partial, dev_stats, s);
+    else switch (nj_for(d.maxw)) {
     case 1: st = group_train_launch<1, 32>(g, pl, q, label_bits, alpha, sched, beta, partial, loss_partial, dev_stats, s); break;
     case 2: st = group_train_launch<2, 32>(g, pl, q, label_bits, alpha, sched, beta, partial, loss_partial, dev_stats, s); break;
     case 4: st = group_train_launch<4, 32>(g, pl, q, label_bits, alpha, sched, beta, partial, loss_partial, dev_stats, s); break;

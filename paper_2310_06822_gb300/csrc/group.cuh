@@ -56,3 +56,11 @@ nb_status nb_tc_group_refresh(TcModel *tc, const MlpDesc &d, int n_objects, cuda
 nb_status nb_tc_group_query(TcModel *tc, const MlpDesc &d, int64_t P, const nb_plan *pl, const float *q,
                             const TauF *taus, float margin, uint32_t *bits, float *logits, nb_query_stats *st,
                             QueryWs ws, cudaStream_t s);
+
+// BF16 tensor-core grouped training (train_bf16.cu)
+nb_status nb_train_bf16_group_init(TcModel *tc, const MlpDesc &d, int n_objects);
+nb_status nb_train_bf16_group_refresh(TcModel *tc, const MlpDesc &d, int n_objects, cudaStream_t s);
+nb_status nb_launch_train_bf16_group(TcModel *tc, const MlpDesc &d, long long P, const nb_plan *pl, const float *q,
+                                     const uint32_t *labels, float alpha, const float *sched_alpha, const int *d_step,
+                                     int sched_T, float beta, const TauF *taus, float *partial, float *loss_partial,
+                                     nb_step_stats *st, cudaStream_t s);

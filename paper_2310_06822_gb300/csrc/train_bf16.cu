@@ -17,6 +17,7 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "group.cuh"
 #include "tc.cuh"
 
 namespace {
@@ -168,28 +169,36 @@ __device__ __forceinline__ void tile_dw(const __nv_bfloat16 *DZ, int dp, const _
     }
 }
 
-template <int H>
-__global__ void __launch_bounds__(256, 1)
-    train_bf16_kernel(TrainDesc d, const float *__restrict__ q, const uint32_t *__restrict__ labels, long long n,
-                      float alpha, float beta, float inv_n, TauF tau, float *__restrict__ partial,
-                      float *loss_partial, long long P, nb_step_stats *st) {
-    constexpr int HP = H + PAD, XP = K0 + PAD;
-    extern __shared__ __align__(16) uint8_t smem_raw[];
-    const int NH = d.NH, t = threadIdx.x;
-    __nv_bfloat16 *Ws = reinterpret_cast<__nv_bfloat16 *>(smem_raw);  // layer 0: H x XP, others H x HP
-    __nv_bfloat16 *act = Ws + H * XP + (size_t)(NH - 1) * H * HP;      // act0: TM x XP, act l>=1: TM x HP
-    __nv_bfloat16 *dz0 = act + TM * XP + (size_t)NH * TM * HP;
-    __nv_bfloat16 *dz1 = dz0 + TM * HP;
-    float *bias = reinterpret_cast<float *>(dz1 + TM * HP);  // [NH][H]
-    float *head = bias + NH * H;                               // [H + 1]
-    float *zs = head + H + 4, *gs = zs + TM, *ls = gs + TM;
-    auto W_l = [&](int l) { return l == 0 ? Ws : Ws + H * XP + (size_t)(l - 1) * H * HP; };
-    auto A_l = [&](int l) { return l == 0 ? act : act + TM * XP + (size_t)(l - 1) * TM * HP; };
+// shared-memory carve-up of the training kernels (see nb_train_bf16_smem)
+#define NB_BF_SMEM                                                                                     \
+    constexpr int HP = H + PAD, XP = K0 + PAD;                                                         \
+    extern __shared__ __align__(16) uint8_t smem_raw[];                                                \
+    const int NH = d.NH, t = threadIdx.x;                                                              \
+    __nv_bfloat16 *Ws = reinterpret_cast<__nv_bfloat16 *>(smem_raw);                                   \
+    __nv_bfloat16 *act = Ws + H * XP + (size_t)(NH - 1) * H * HP;                                      \
+    __nv_bfloat16 *dz0 = act + TM * XP + (size_t)NH * TM * HP;                                         \
+    __nv_bfloat16 *dz1 = dz0 + TM * HP;                                                                \
+    float *bias = reinterpret_cast<float *>(dz1 + TM * HP);                                            \
+    float *head = bias + NH * H;                                                                       \
+    float *zs = head + H + 4, *gs = zs + TM, *ls = gs + TM;                                            \
+    auto W_l = [&](int l) { return l == 0 ? Ws : Ws + H * XP + (size_t)(l - 1) * H * HP; };          \
+    auto A_l = [&](int l) { return l == 0 ? act : act + TM * XP + (size_t)(l - 1) * TM * HP; };      \
+    (void)HP;                                                                                          \
+    (void)XP
 
+// weights of one network (bf16 image -> padded rows), its biases and head; ends synchronised
+template <int H>
+__device__ __forceinline__ void bf_load(const TrainDesc &d, const __nv_bfloat16 *img, const float *p) {
+    NB_BF_SMEM;
+    (void)A_l;
+    (void)zs;
+    (void)gs;
+    (void)ls;
+    (void)dz0;
     // weights (bf16 image -> padded rows), biases, head
     for (int l = 0; l < NH; l++) {
         const int kp = kpad(H, l), pitch = l == 0 ? XP : HP;
-        const __nv_bfloat16 *src = d.img + img_off(H, l);
+        const __nv_bfloat16 *src = img + img_off(H, l);
         __nv_bfloat16 *dst = W_l(l);
         for (int e = t; e < H * kp / 8; e += blockDim.x) {
             const int row = (e * 8) / kp, col = (e * 8) % kp;
@@ -198,107 +207,113 @@ __global__ void __launch_bounds__(256, 1)
     }
     for (int i = t; i < NH * H; i += blockDim.x) {
         const int l = i / H, j = i % H;
-        bias[i] = d.p[d.off[l] + H * (l == 0 ? d.in : H) + j];
+        bias[i] = p[d.off[l] + H * (l == 0 ? d.in : H) + j];
     }
-    for (int i = t; i <= H; i += blockDim.x) head[i] = d.p[d.off[NH] + i];
+    for (int i = t; i <= H; i += blockDim.x) head[i] = p[d.off[NH] + i];
     __syncthreads();
 
-    float *slot = partial + (size_t)blockIdx.x * P;
-    const long long ntiles = (n + TM - 1) / TM;
-    float lossacc = 0.f;
-    unsigned long long c_fn = 0, c_fp = 0, c_nf = 0;
-    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const long long base = tile * TM;
-        const int rows = (int)min((long long)TM, n - base);
-        // input -> bf16, padded to K0
-        for (int e = t; e < TM * K0; e += blockDim.x) {
-            const int m = e / K0, k = e % K0;
-            const float x = (m < rows && k < d.in) ? q[(base + m) * d.in + k] : 0.f;
-            act[m * XP + k] = __float2bfloat16_rn(x);
-        }
-        __syncthreads();
-        // forward
-        for (int l = 0; l < NH; l++) {
-            tile_gemm<H, false, true>(A_l(l), l == 0 ? XP : HP, kpad(H, l), W_l(l), l == 0 ? XP : HP, bias + l * H,
-                                      nullptr, 0, A_l(l + 1), HP);
-            __syncthreads();
-        }
-        // head (FP32) and loss: 4 threads per sample
-        {
-            const __nv_bfloat16 *aL = A_l(NH);
-            const int m = t >> 2, part = t & 3;
-            float s = 0.f;
-            for (int k = part; k < H; k += 4) s = fmaf(head[k], __bfloat162float(aL[m * HP + k]), s);
-            s += __shfl_xor_sync(FULL, s, 1);
-            s += __shfl_xor_sync(FULL, s, 2);
-            if (part == 0) zs[m] = s + head[H];
-        }
-        __syncthreads();
-        if (t < TM) {
-            float g = 0.f, lv = 0.f;
-            if (t < rows) {
-                const long long i = base + t;
-                const float y = (float)((labels[i >> 5] >> (i & 31)) & 1u);
-                const float z = zs[t];
-                if (isfinite(z)) {
-                    lv = alpha * y * softplusf(-z) + beta * (1.f - y) * softplusf(z);
-                    const float sg = sigmoidf(z);
-                    g = (alpha * y * (sg - 1.f) + beta * (1.f - y) * sg) * inv_n;
-                    const bool dec = z >= tau.up;
-                    c_fn += (y != 0.f && !dec);
-                    c_fp += (y == 0.f && dec);
-                } else {
-                    c_nf++;
-                }
-            }
-            gs[t] = g;
-            ls[t] = lv;
-        }
-        __syncthreads();
-        if (t == 0)
-            for (int m = 0; m < rows; m++) lossacc += ls[m];
-        // head gradients and dZ of the last hidden layer
-        {
-            const __nv_bfloat16 *aL = A_l(NH);
-            float *gW = slot + d.off[NH];
-            for (int k = t; k <= H; k += blockDim.x) {
-                float s = 0.f;
-                if (k < H)
-                    for (int m = 0; m < TM; m++) s = fmaf(gs[m], __bfloat162float(aL[m * HP + k]), s);
-                else
-                    for (int m = 0; m < TM; m++) s += gs[m];
-                gW[k] += s;
-            }
-            for (int e = t; e < TM * H; e += blockDim.x) {
-                const int m = e / H, k = e % H;
-                const float a = __bfloat162float(aL[m * HP + k]);
-                dz0[m * HP + k] = __float2bfloat16_rn(a > 0.f ? gs[m] * head[k] : 0.f);
-            }
-        }
-        __syncthreads();
-        __nv_bfloat16 *dzc = dz0, *dzn = dz1;
-        for (int l = NH - 1; l >= 0; l--) {
-            const int K = l == 0 ? d.in : H, kp = kpad(H, l);
-            const __nv_bfloat16 *Al = A_l(l);
-            float *gW = slot + d.off[l];
-            tile_dw<H>(dzc, HP, Al, l == 0 ? XP : HP, kp, K, gW);
-            for (int nn = t; nn < H; nn += blockDim.x) {
-                float s = 0.f;
-                for (int m = 0; m < TM; m++) s += __bfloat162float(dzc[m * HP + nn]);
-                gW[(size_t)H * K + nn] += s;
-            }
-            if (l > 0) {
-                // dA_{l} = dZ W_l, through the ReLU of layer l's input
-                tile_gemm<H, true, false>(dzc, HP, H, W_l(l), HP, nullptr, Al, HP, dzn, HP);
-                __syncthreads();
-                __nv_bfloat16 *tp = dzc;
-                dzc = dzn;
-                dzn = tp;
-            }
-        }
+}
+
+// one tile of TM samples starting at row base: forward, loss, backward, gradient partials
+// into slot; ends synchronised
+template <int H>
+__device__ __forceinline__ void bf_tile(const TrainDesc &d, const float *__restrict__ q,
+                                        const uint32_t *__restrict__ labels, long long base, int rows, float alpha,
+                                        float beta, float inv_n, TauF tau, float *__restrict__ slot, float &lossacc,
+                                        unsigned long long &c_fn, unsigned long long &c_fp, unsigned long long &c_nf) {
+    NB_BF_SMEM;
+    // input -> bf16, padded to K0
+    for (int e = t; e < TM * K0; e += blockDim.x) {
+        const int m = e / K0, k = e % K0;
+        const float x = (m < rows && k < d.in) ? q[(base + m) * d.in + k] : 0.f;
+        act[m * XP + k] = __float2bfloat16_rn(x);
+    }
+    __syncthreads();
+    // forward
+    for (int l = 0; l < NH; l++) {
+        tile_gemm<H, false, true>(A_l(l), l == 0 ? XP : HP, kpad(H, l), W_l(l), l == 0 ? XP : HP, bias + l * H,
+                                  nullptr, 0, A_l(l + 1), HP);
         __syncthreads();
     }
-    if (t == 0) loss_partial[blockIdx.x] = lossacc;
+    // head (FP32) and loss: 4 threads per sample
+    {
+        const __nv_bfloat16 *aL = A_l(NH);
+        const int m = t >> 2, part = t & 3;
+        float s = 0.f;
+        for (int k = part; k < H; k += 4) s = fmaf(head[k], __bfloat162float(aL[m * HP + k]), s);
+        s += __shfl_xor_sync(FULL, s, 1);
+        s += __shfl_xor_sync(FULL, s, 2);
+        if (part == 0) zs[m] = s + head[H];
+    }
+    __syncthreads();
+    if (t < TM) {
+        float g = 0.f, lv = 0.f;
+        if (t < rows) {
+            const long long i = base + t;
+            const float y = (float)((labels[i >> 5] >> (i & 31)) & 1u);
+            const float z = zs[t];
+            if (isfinite(z)) {
+                lv = alpha * y * softplusf(-z) + beta * (1.f - y) * softplusf(z);
+                const float sg = sigmoidf(z);
+                g = (alpha * y * (sg - 1.f) + beta * (1.f - y) * sg) * inv_n;
+                const bool dec = z >= tau.up;
+                c_fn += (y != 0.f && !dec);
+                c_fp += (y == 0.f && dec);
+            } else {
+                c_nf++;
+            }
+        }
+        gs[t] = g;
+        ls[t] = lv;
+    }
+    __syncthreads();
+    if (t == 0)
+        for (int m = 0; m < rows; m++) lossacc += ls[m];
+    // head gradients and dZ of the last hidden layer
+    {
+        const __nv_bfloat16 *aL = A_l(NH);
+        float *gW = slot + d.off[NH];
+        for (int k = t; k <= H; k += blockDim.x) {
+            float s = 0.f;
+            if (k < H)
+                for (int m = 0; m < TM; m++) s = fmaf(gs[m], __bfloat162float(aL[m * HP + k]), s);
+            else
+                for (int m = 0; m < TM; m++) s += gs[m];
+            gW[k] += s;
+        }
+        for (int e = t; e < TM * H; e += blockDim.x) {
+            const int m = e / H, k = e % H;
+            const float a = __bfloat162float(aL[m * HP + k]);
+            dz0[m * HP + k] = __float2bfloat16_rn(a > 0.f ? gs[m] * head[k] : 0.f);
+        }
+    }
+    __syncthreads();
+    __nv_bfloat16 *dzc = dz0, *dzn = dz1;
+    for (int l = NH - 1; l >= 0; l--) {
+        const int K = l == 0 ? d.in : H, kp = kpad(H, l);
+        const __nv_bfloat16 *Al = A_l(l);
+        float *gW = slot + d.off[l];
+        tile_dw<H>(dzc, HP, Al, l == 0 ? XP : HP, kp, K, gW);
+        for (int nn = t; nn < H; nn += blockDim.x) {
+            float s = 0.f;
+            for (int m = 0; m < TM; m++) s += __bfloat162float(dzc[m * HP + nn]);
+            gW[(size_t)H * K + nn] += s;
+        }
+        if (l > 0) {
+            // dA_{l} = dZ W_l, through the ReLU of layer l's input
+            tile_gemm<H, true, false>(dzc, HP, H, W_l(l), HP, nullptr, Al, HP, dzn, HP);
+            __syncthreads();
+            __nv_bfloat16 *tp = dzc;
+            dzc = dzn;
+            dzn = tp;
+        }
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void bf_counters(nb_step_stats *st, unsigned long long c_fn, unsigned long long c_fp,
+                                            unsigned long long c_nf) {
+    const int t = threadIdx.x;
     if (st && t < TM) {
 #pragma unroll
         for (int o = 16; o; o >>= 1) {
@@ -314,9 +329,65 @@ __global__ void __launch_bounds__(256, 1)
     }
 }
 
-// FP32 master weights -> bf16 training image
-__global__ void pack_train_kernel(TrainDesc d, __nv_bfloat16 *img, long long total) {
+template <int H>
+__global__ void __launch_bounds__(256, 1)
+    train_bf16_kernel(TrainDesc d, const float *__restrict__ q, const uint32_t *__restrict__ labels, long long n,
+                      float alpha, float beta, float inv_n, TauF tau, float *__restrict__ partial,
+                      float *loss_partial, long long P, nb_step_stats *st) {
+    bf_load<H>(d, d.img, d.p);
+    float *slot = partial + (size_t)blockIdx.x * P;
+    const long long ntiles = (n + TM - 1) / TM;
+    float lossacc = 0.f;
+    unsigned long long c_fn = 0, c_fp = 0, c_nf = 0;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const long long base = tile * TM;
+        const int rows = (int)min((long long)TM, n - base);
+        bf_tile<H>(d, q, labels, base, rows, alpha, beta, inv_n, tau, slot, lossacc, c_fn, c_fp, c_nf);
+    }
+    if (threadIdx.x == 0) loss_partial[blockIdx.x] = lossacc;
+    bf_counters(st, c_fn, c_fp, c_nf);
+}
+
+// Grouped form: persistent CTAs walk the work items of a plan (rows of one object
+// each); a CTA reloads weights only when its next item belongs to another object.
+// Object o's parameters start at d.p + o * P and its bf16 image at d.img + o * img_elems.
+template <int H>
+__global__ void __launch_bounds__(256, 1)
+    train_bf16_group_kernel(TrainDesc d, long long img_elems, const PlanItem *__restrict__ items, int n_items,
+                            const long long *__restrict__ offsets, const float *__restrict__ q,
+                            const uint32_t *__restrict__ labels, float alpha_arg, const float *sched_alpha,
+                            const int *d_step, int sched_T, float beta, const TauF *taus, float *__restrict__ partial,
+                            float *loss_partial, long long P, nb_step_stats *st) {
+    float alpha = alpha_arg;
+    if (sched_alpha) alpha = sched_alpha[min(*d_step, sched_T - 1)];
+    unsigned long long c_fn = 0, c_fp = 0, c_nf = 0;
+    int cur = -1;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const PlanItem w = items[it];
+        TrainDesc dd = d;
+        dd.p = d.p + (size_t)w.obj * P;
+        if (w.obj != cur) {
+            __syncthreads();
+            bf_load<H>(dd, d.img + (size_t)w.obj * img_elems, dd.p);
+            cur = w.obj;
+        }
+        const float inv_n = 1.0f / (float)(offsets[w.obj + 1] - offsets[w.obj]);
+        float *slot = partial + (size_t)it * P;
+        float lossacc = 0.f;
+        for (long long base = w.row0; base < w.row1; base += TM) {
+            const int rows = (int)min((long long)TM, w.row1 - base);
+            bf_tile<H>(dd, q, labels, base, rows, alpha, beta, inv_n, taus[w.obj], slot, lossacc, c_fn, c_fp, c_nf);
+        }
+        if (threadIdx.x == 0) loss_partial[it] = lossacc;
+    }
+    bf_counters(st, c_fn, c_fp, c_nf);
+}
+
+// FP32 master weights -> bf16 training image; blockIdx.y selects the object of a group
+__global__ void pack_train_kernel(TrainDesc d, __nv_bfloat16 *img, long long total, long long P) {
     const int H = d.H;
+    d.p += (size_t)blockIdx.y * P;
+    img += (size_t)blockIdx.y * total;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
         int l;
@@ -384,7 +455,7 @@ size_t nb_train_bf16_img_bytes(const MlpDesc &d) { return train_img_elems(d.w[1]
 nb_status nb_train_bf16_refresh(TcModel *tc, const MlpDesc &d, cudaStream_t s) {
     const TrainDesc t = make_desc(tc, d);
     const long long total = (long long)train_img_elems(t.H, t.NH);
-    pack_train_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(t, (__nv_bfloat16 *)tc->train_img, total);
+    pack_train_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(t, (__nv_bfloat16 *)tc->train_img, total, 0);
     NB_CUDA(cudaGetLastError());
     return NB_OK;
 }
@@ -412,6 +483,55 @@ nb_status nb_launch_train_bf16(TcModel *tc, const MlpDesc &d, const float *q, co
         NB_CUDA(cudaFuncSetAttribute(train_bf16_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         train_bf16_kernel<64><<<ws.G, 256, smem, s>>>(t, q, labels, (long long)n, alpha, beta, 1.0f / (float)n, tau,
                                                       ws.partial, ws.loss_partial, P, st);
+    }
+    NB_CUDA(cudaGetLastError());
+    return NB_OK;
+}
+
+nb_status nb_train_bf16_group_init(TcModel *tc, const MlpDesc &d, int n_objects) {
+    const nb_status st = nb_train_bf16_check(d);
+    if (st != NB_OK) return st;
+    tc->train_img_bytes = nb_train_bf16_img_bytes(d);
+    if (cudaMalloc(&tc->train_img, tc->train_img_bytes * (size_t)n_objects) != cudaSuccess) {
+        cudaGetLastError();
+        return nb_fail(NB_ENOMEM, "grouped training image allocation failed");
+    }
+    return NB_OK;
+}
+
+nb_status nb_train_bf16_group_refresh(TcModel *tc, const MlpDesc &d, int n_objects, cudaStream_t s) {
+    const TrainDesc t = make_desc(tc, d);
+    const long long total = (long long)train_img_elems(t.H, t.NH);
+    long long P = 0;
+    for (int l = 0; l < d.L; l++) P += (long long)d.w[l + 1] * (d.w[l] + 1);
+    pack_train_kernel<<<dim3((unsigned)((total + 255) / 256), n_objects), 256, 0, s>>>(
+        t, (__nv_bfloat16 *)tc->train_img, total, P);
+    NB_CUDA(cudaGetLastError());
+    return NB_OK;
+}
+
+nb_status nb_launch_train_bf16_group(TcModel *tc, const MlpDesc &d, long long P, const nb_plan *pl, const float *q,
+                                     const uint32_t *labels, float alpha, const float *sched_alpha, const int *d_step,
+                                     int sched_T, float beta, const TauF *taus, float *partial, float *loss_partial,
+                                     nb_step_stats *st, cudaStream_t s) {
+    const TrainDesc t = make_desc(tc, d);
+    const long long img_elems = (long long)train_img_elems(t.H, t.NH);
+    const size_t smem = nb_train_bf16_smem(t.H, t.NH);
+    int grid = num_sms();
+    if (grid > pl->n_items) grid = pl->n_items;
+    if (grid < 1) return NB_OK;
+    if (t.H == 128) {
+        NB_CUDA(cudaFuncSetAttribute(train_bf16_group_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+        train_bf16_group_kernel<128><<<grid, 256, smem, s>>>(t, img_elems, pl->items, pl->n_items, pl->offsets, q,
+                                                             labels, alpha, sched_alpha, d_step, sched_T, beta, taus,
+                                                             partial, loss_partial, P, st);
+    } else {
+        NB_CUDA(cudaFuncSetAttribute(train_bf16_group_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+        train_bf16_group_kernel<64><<<grid, 256, smem, s>>>(t, img_elems, pl->items, pl->n_items, pl->offsets, q,
+                                                            labels, alpha, sched_alpha, d_step, sched_T, beta, taus,
+                                                            partial, loss_partial, P, st);
     }
     NB_CUDA(cudaGetLastError());
     return NB_OK;

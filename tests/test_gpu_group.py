@@ -203,3 +203,56 @@ def test_grouped_4d_end_to_end_zero_fn(nb):
         trivial += np.mean(~ys[o].astype(bool))
     # the trained bounds are tighter than the trivial one (everything inside)
     assert fp < 0.9 * trivial, (fp, trivial)
+
+
+@pytest.mark.parametrize("kind,widths", [("point4t", [4, 64, 64, 64, 1]), ("ray3", [6, 128, 128, 128, 1])])
+def test_grouped_bf16_train_step_matches_oracle_per_object(nb, kind, widths):
+    counts = [4096, 777, 9000, 33, 2048]
+    kid = I.kind_id(kind)
+    scenes, qs, off = _objects(kind, 5, counts, 1100, moving=(kid == I.POINT4T))
+    ys = [O.label(kid, q, sc) for q, sc in zip(qs, scenes)]
+    g = nb.Group(widths, 5, train_prec="bf16")
+    p0 = np.stack([I.init_params(1200 + o, widths) for o in range(5)])
+    g.set_params(p0)
+    plan = nb.Plan(off, chunk_rows=1024)
+    g.train_step(plan, _dev(np.concatenate(qs)), _dev(I.pack_bits(np.concatenate(ys)).view(np.int32)), 25.0)
+    grad = g.get_grad().astype(np.float64)
+    for o in range(5):
+        _, g64 = O.loss_grad(widths, p0[o], qs[o], ys[o], 25.0, 1.0)
+        cos = float(np.dot(grad[o], g64) / (np.linalg.norm(grad[o]) * np.linalg.norm(g64)))
+        assert cos >= 0.999 and _rel(grad[o], g64) <= 5e-2, (o, cos)
+
+
+def test_grouped_bf16_graph_replay_equals_eager(nb):
+    import torch
+    widths = [4, 64, 64, 64, 1]
+    counts = [4096, 8192, 4096, 12288]
+    scenes, qs, off = _objects("point4t", 4, counts, 1300, moving=True)
+    y = np.concatenate([O.label(I.POINT4T, q, sc) for q, sc in zip(qs, scenes)])
+    qd = _dev(np.concatenate(qs))
+    bd = _dev(I.pack_bits(y).view(np.int32))
+    p0 = np.stack([I.init_params(1400 + o, widths) for o in range(4)])
+    T = 10
+    alpha = (1.0 + 99.0 * np.arange(T) / (T - 1)).astype(np.float32)
+    plan = nb.Plan(off, chunk_rows=4096)
+    eager = nb.Group(widths, 4, train_prec="bf16")
+    eager.set_params(p0)
+    for t in range(T):
+        eager.train_step(plan, qd, bd, float(alpha[t]))
+    ge = nb.Group(widths, 4, train_prec="bf16")
+    ge.set_params(p0)
+    ge.set_schedule(alpha)
+    ge.reserve(plan)
+    ge.train_step(plan, qd, bd, -1.0)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s):
+            ge.train_step(plan, qd, bd, -1.0)
+    torch.cuda.current_stream().wait_stream(s)
+    for _ in range(T - 1):
+        graph.replay()
+    torch.cuda.synchronize()
+    ge.sync_schedule()
+    assert np.array_equal(ge.get_params(), eager.get_params())
