@@ -25,6 +25,9 @@
  *   orc_calibrate   output epsilon of Suppl. Sec. "Numerics": threshold
  *                   tau = (min over positives of z) - eps, rounded toward -inf.
  *   orc_count       FN / FP / TP / TN of the cost table of Sec. 3.1.
+ *   orc_sample      Alg. 1's per-iteration draw of queries r ~ Uniform, made
+ *                   reproducible by the counter-based Philox4x64-10 generator
+ *                   (orc_philox4x64 exposes one block for its pin).
  *
  * Number formats: every query and sphere value is an integer multiple of
  * 2^-qexp (see inputs.py).  Integer "units" below are multiples of 2^-qexp.
@@ -493,4 +496,165 @@ void orc_count(const double *z, const uint8_t *y, int64_t n, double tau, int64_t
         else if (y[i] && d) out[2]++;
         else out[3]++;
     }
+}
+
+/* ----------------------------------------------------------- query sampling
+ * Alg. 1 draws a fresh batch of queries r ~ Uniform every iteration.  The
+ * uniform draws are made reproducible, independently of how they are computed,
+ * by a counter-based generator: Philox4x64-10 (Salmon, Moraes, Dror and Shaw,
+ * "Parallel random numbers: as easy as 1, 2, 3", SC 2011), written here from
+ * its published definition (round function, multipliers and Weyl key
+ * increments of that paper).  Query i of a stream (seed, kind) reads the blocks
+ *     philox(counter = (i, j, p, 0), key = (seed, kind)),
+ * p = 0 for its scalars (j = 0) and p = 1, 2 for its first and second unit
+ * vector (j = 0, 1, ... for the rejection attempts).
+ *
+ * From the 64-bit words w of a block (all values integer multiples of 2^-qexp,
+ * 8 <= qexp <= 20):
+ *   coordinate U[-1,1):  field s (21 bits at bit 21 s) of w, minus 2^20, read
+ *                        in units of 2^-20 and truncated to the grid;
+ *                        here: the top qexp+1 bits of the field, minus 2^qexp.
+ *   time U[0,1):         the low qexp bits of w1 (4D points).
+ *   unit vector:         v = three 21-bit fields minus 2^20 of one word,
+ *                        accepted when 2^30 <= |v|^2 <= 2^40 (uniform in a
+ *                        shell, so v/|v| is uniform on S^2); words are tried in
+ *                        order w0..w3 of blocks j = 0..15, (0,0,1) if none is
+ *                        accepted; u = v / sqrt(|v|^2) in FP64 (IEEE division
+ *                        and square root), rounded to the grid (nearest, ties
+ *                        to even).
+ *   log-uniform [a, b]:  a * 2^(x log2(b/a)), x = (w >> 11) 2^-53, with 2^f for
+ *                        the fractional part f evaluated as the degree-20
+ *                        Taylor polynomial of exp(f ln 2) in the nested form
+ *                        p = 1 + (t/k) p, k = 20 .. 1; rounded to the grid.
+ * Encodings: point (x from the fields of w0), 4D point (x, t), ray (2 u1, u2),
+ * plane (u1, off from field 0 of w0), box (centre from w0, half-extent of axis
+ * d log-uniform in [0.01, 0.5] from w_{1+d}).
+ */
+static const uint64_t PH_M0 = 0xD2E7470EE14C6C93ull, PH_M1 = 0xCA5A826395121157ull;
+static const uint64_t PH_W0 = 0x9E3779B97F4A7C15ull, PH_W1 = 0xBB67AE8584CAA73Bull;
+
+static void philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]) {
+    uint64_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint64_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; round++) {
+        unsigned __int128 p0 = (unsigned __int128)PH_M0 * x0;
+        unsigned __int128 p1 = (unsigned __int128)PH_M1 * x2;
+        uint64_t hi0 = (uint64_t)(p0 >> 64), lo0 = (uint64_t)p0;
+        uint64_t hi1 = (uint64_t)(p1 >> 64), lo1 = (uint64_t)p1;
+        x0 = hi1 ^ x1 ^ k0;
+        x1 = lo1;
+        x2 = hi0 ^ x3 ^ k1;
+        x3 = lo0;
+        k0 += PH_W0;
+        k1 += PH_W1;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* Test hook: one Philox4x64-10 block. */
+void orc_philox4x64(const uint64_t *ctr, const uint64_t *key, uint64_t *out) { philox4x64_10(ctr, key, out); }
+
+static void sample_block(uint64_t seed, int kind, int64_t i, uint64_t j, uint64_t p, uint64_t w[4]) {
+    const uint64_t ctr[4] = {(uint64_t)i, j, p, 0};
+    const uint64_t key[2] = {seed, (uint64_t)kind};
+    philox4x64_10(ctr, key, w);
+}
+
+static int64_t field21(uint64_t w, int s) { return (int64_t)((w >> (21 * s)) & 0x1FFFFF) - 1048576; }
+
+/* U[-1,1) coordinate in units of 2^-qexp */
+static int64_t coord_units(uint64_t w, int s, int qexp) {
+    const int64_t f = (int64_t)((w >> (21 * s)) & 0x1FFFFF);  /* [0, 2^21) */
+    return (f >> (20 - qexp)) - ((int64_t)1 << qexp);
+}
+
+static double grid_round(double x, int qexp) { return ldexp(rint(ldexp(x, qexp)), -qexp); }
+
+static void unit_vector(uint64_t seed, int kind, int64_t i, uint64_t p, double u[3]) {
+    for (uint64_t j = 0; j < 16; j++) {
+        uint64_t w[4];
+        sample_block(seed, kind, i, j, p, w);
+        for (int m = 0; m < 4; m++) {
+            const int64_t v0 = field21(w[m], 0), v1 = field21(w[m], 1), v2 = field21(w[m], 2);
+            const int64_t n2 = v0 * v0 + v1 * v1 + v2 * v2;
+            if (n2 >= ((int64_t)1 << 30) && n2 <= ((int64_t)1 << 40)) {
+                const double len = sqrt((double)n2);
+                u[0] = (double)v0 / len;
+                u[1] = (double)v1 / len;
+                u[2] = (double)v2 / len;
+                return;
+            }
+        }
+    }
+    u[0] = 0.0; u[1] = 0.0; u[2] = 1.0;
+}
+
+static double exp2_taylor(double y) {  /* y >= 0 */
+    const double n = floor(y);
+    const double t = (y - n) * 0.6931471805599453;
+    double p = 1.0;
+    for (int k = 20; k >= 1; k--) p = 1.0 + (t / (double)k) * p;
+    return ldexp(p, (int)n);
+}
+
+typedef struct {
+    int kind, qexp;
+    uint64_t seed;
+    int64_t first;
+    float *q;
+} sample_ctx;
+
+static void sample_range(void *pc, int64_t lo, int64_t hi, int tid) {
+    (void)tid;
+    const sample_ctx *c = (const sample_ctx *)pc;
+    const int qe = c->qexp;
+    const double quantum = ldexp(1.0, -qe);
+    for (int64_t r = lo; r < hi; r++) {
+        const int64_t i = c->first + r;
+        float *o = c->q + r * ENC_W[c->kind];
+        uint64_t w[4];
+        sample_block(c->seed, c->kind, i, 0, 0, w);
+        double u[3], v[3];
+        switch (c->kind) {
+        case K_POINT2:
+            for (int d = 0; d < 2; d++) o[d] = (float)((double)coord_units(w[0], d, qe) * quantum);
+            break;
+        case K_POINT3:
+            for (int d = 0; d < 3; d++) o[d] = (float)((double)coord_units(w[0], d, qe) * quantum);
+            break;
+        case K_POINT4T:
+            for (int d = 0; d < 3; d++) o[d] = (float)((double)coord_units(w[0], d, qe) * quantum);
+            o[3] = (float)((double)(int64_t)(w[1] & (((uint64_t)1 << qe) - 1)) * quantum);
+            break;
+        case K_RAY3:
+            unit_vector(c->seed, c->kind, i, 1, u);
+            unit_vector(c->seed, c->kind, i, 2, v);
+            for (int d = 0; d < 3; d++) {
+                o[d] = (float)grid_round(2.0 * u[d], qe);
+                o[3 + d] = (float)grid_round(v[d], qe);
+            }
+            break;
+        case K_PLANE3:
+            unit_vector(c->seed, c->kind, i, 1, u);
+            for (int d = 0; d < 3; d++) o[d] = (float)grid_round(u[d], qe);
+            o[3] = (float)((double)coord_units(w[0], 0, qe) * quantum);
+            break;
+        case K_BOX3:
+            for (int d = 0; d < 3; d++) {
+                o[d] = (float)((double)coord_units(w[0], d, qe) * quantum);
+                const double x = (double)(w[1 + d] >> 11) * 0x1p-53;
+                o[3 + d] = (float)grid_round(0.01 * exp2_taylor(x * 5.643856189774724), qe);
+            }
+            break;
+        }
+    }
+}
+
+/* Queries first .. first+n-1 of the stream (seed, kind) into q[n][enc width].
+ * Returns 0, or -1 for an unknown kind or qexp outside [8, 20]. */
+int orc_sample(int kind, int qexp, uint64_t seed, int64_t first, int64_t n, float *q, int nthreads) {
+    if (kind < 0 || kind > 5 || qexp < 8 || qexp > 20 || first < 0 || n < 0) return -1;
+    sample_ctx c = {kind, qexp, seed, first, q};
+    parallel_for(n, nthreads, sample_range, &c);
+    return 0;
 }

@@ -64,6 +64,10 @@ def lib():
             L.orc_calibrate.restype = i64
             L.orc_count.argtypes = [P, P, i64, ctypes.c_double, P]
             L.orc_count.restype = None
+            L.orc_philox4x64.argtypes = [P, P, P]
+            L.orc_philox4x64.restype = None
+            L.orc_sample.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint64, i64, i64, P, ctypes.c_int]
+            L.orc_sample.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -172,3 +176,25 @@ def count(z, y, tau: float) -> dict:
     out = np.zeros(4, dtype=np.int64)
     lib().orc_count(_ptr(z), _ptr(y), z.shape[0], float(tau), _ptr(out))
     return {"FN": int(out[0]), "FP": int(out[1]), "TP": int(out[2]), "TN": int(out[3])}
+
+
+ENC_W = (2, 3, 4, 6, 4, 6)
+
+
+def philox4x64(counter, key) -> np.ndarray:
+    """One Philox4x64-10 block (four uint64 words) for a 4-word counter and 2-word key."""
+    c = np.ascontiguousarray(np.asarray(counter, dtype=np.uint64))
+    k = np.ascontiguousarray(np.asarray(key, dtype=np.uint64))
+    out = np.zeros(4, dtype=np.uint64)
+    lib().orc_philox4x64(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def sample(kind: int, n: int, seed: int, first: int = 0, qexp: int = 20,
+           nthreads: int | None = None) -> np.ndarray:
+    """Queries first .. first+n-1 of the counter-based stream (seed, kind): the
+    per-iteration Uniform draw of Alg. 1, float32 [n][enc width] on the 2^-qexp grid."""
+    q = np.zeros((n, ENC_W[kind]), dtype=np.float32)
+    if lib().orc_sample(int(kind), int(qexp), int(seed), int(first), int(n), _ptr(q), _threads(nthreads)) != 0:
+        raise ValueError("oracle sample: bad kind, qexp or range")
+    return q
