@@ -3,7 +3,8 @@
 Default workload (configuration of the headline metric): 3D ray queries against a union
 of 64 spheres (radii 0.02-0.2) in [-1,1]^3; rays with origin uniform on the radius-2
 sphere and direction uniform on S^2; MLP 6 -> 128 x4 -> 1 (ReLU); 20k BF16 tensor-core
-training steps of 65,536 rays with the asymmetric BCE (FN weight ramped 1 -> 100, beta 1);
+training steps, each on a fresh batch of 65,536 rays sampled and labelled on the GPU, with
+the asymmetric BCE (FN weight ramped 1 -> 100, beta 1);
 threshold calibrated in FP64 on the 16M-ray evaluation set (FN = 0 on it).
 One timed step = nb_query over the 16M evaluation rays (split-FP16 tcgen05 forward,
 FP32 / extended-precision re-check of the margin band), inputs resident in HBM (384 MB
@@ -39,7 +40,7 @@ BATCH, TRAIN_STEPS = 65536, 20000
 N_EVAL = 16 << 20
 MARGIN = 0.05
 MARGIN32 = 1e-2  # FP32 form: re-check band above its own logit error
-SEED_SCENE, SEED_QUERY, SEED_INIT = 1001, 2001, 4001
+SEED_SCENE, SEED_QUERY, SEED_INIT, SEED_TRAIN = 1001, 2001, 4001, 2018
 # DRAM bytes (read + write) per ray of the forward kernel, from one ncu capture of
 # fwd_split_kernel at 1,048,576 rays (25,459,968 bytes); None once the kernel changes
 TRAFFIC_BYTES_PER_RAY = 25459968 / 1048576
@@ -195,41 +196,43 @@ def run_c2(args):
     n_eval = args.n_eval
     sc = I.make_scene(SEED_SCENE, N_SPHERES, 3, R_LO, R_HI)
     shape = nb.Shape(sc, dev)
-    pool_n = 8 << 20
-    pool = torch.as_tensor(I.sample_queries(I.RAY3, SEED_QUERY + 17, pool_n), device=dev)
-    pool_bits = nb.label(shape, I.RAY3, pool)
     eval_q_host = I.sample_queries(I.RAY3, SEED_QUERY + 1000 * ctx.rank, n_eval)
     eval_q = torch.as_tensor(eval_q_host, device=dev)
     eval_bits = nb.label(shape, I.RAY3, eval_q)
-    per = pool_n // BATCH
 
-    def batch(t):
-        j = t % per
-        return pool[j * BATCH:(j + 1) * BATCH], pool_bits[j * (BATCH // 32):(j + 1) * (BATCH // 32)]
-
-    # training on the tensor cores (BF16 operands, FP32 accumulation, FP32 master weights)
+    # training on the tensor cores (BF16 operands, FP32 accumulation, FP32 master weights),
+    # a fresh batch every iteration as in Alg. 1: sampled and labelled on the GPU
     T = args.train_steps
     trainer = nb.Model(WIDTHS, infer_prec="f32", train_prec="bf16")
     trainer.set_params(I.init_params(SEED_INIT, WIDTHS))
+    qb = torch.empty((BATCH, 6), dtype=torch.float32, device=dev)
+    yb = torch.empty(nb.n_words(BATCH), dtype=torch.int32, device=dev)
+
+    def fresh(t, model_, alpha):
+        nb.sample(I.RAY3, BATCH, SEED_TRAIN, first=t * BATCH, out=qb)
+        nb.label(shape, I.RAY3, qb, out=yb)
+        model_.train_step(qb, yb, alpha, 1.0)
+
     t_train0 = time.perf_counter()
     ta, tb = min(100, T - 1), min(T - 1, 600)
     for t in range(T):
         if t == ta:
             ctx.e0.record()
-        q, y = batch(t)
-        trainer.train_step(q, y, 1.0 + 99.0 * t / max(T - 1, 1), 1.0)
+        fresh(t, trainer, 1.0 + 99.0 * t / max(T - 1, 1))
         if t == tb:
             ctx.e1.record()
     torch.cuda.synchronize()
-    bf16_step_ms = ctx.e0.elapsed_time(ctx.e1) / (tb - ta + 1)
+    loop_ms = ctx.e0.elapsed_time(ctx.e1) / (tb - ta + 1)
     t_train = time.perf_counter() - t_train0
     params = trainer.get_params()
-    # the plain FP32 training step on the same batches, for comparison
+    # the training step alone (BF16 tensor cores), and the plain FP32 step, on one batch
+    bft = nb.Model(WIDTHS, infer_prec="f32", train_prec="bf16")
+    bft.set_params(params)
+    bf16_step_ms = ctx.time_ms(lambda: bft.train_step(qb, yb, 50.0), 50)
     f32t = nb.Model(WIDTHS)
-    f32t.set_params(I.init_params(SEED_INIT, WIDTHS))
-    f32t.train_step(*batch(0), 1.0)
-    it = iter(range(1, 10 ** 9))
-    f32_step_ms = ctx.time_ms(lambda: f32t.train_step(*batch(next(it)), 50.0), 30)
+    f32t.set_params(params)
+    f32_step_ms = ctx.time_ms(lambda: f32t.train_step(qb, yb, 50.0), 20)
+    del bft, f32t
 
     model = nb.Model(WIDTHS, infer_prec="f16x3")
     model.set_params(params)
@@ -304,6 +307,7 @@ def run_c2(args):
         "bf16_plain": {"queries_per_s": n_eval / (bf_ms / 1000.0), "margin": bf_margin, "fn": bf_fn,
                        "flagged": bst["n_flagged"], "unresolved": bst["n_unresolved"]},
         "train_samples_per_s": {"bf16_tensor_core": BATCH / (bf16_step_ms / 1000.0),
+                                "bf16_incl_gpu_sampling_and_labelling": BATCH / (loop_ms / 1000.0),
                                 "fp32": BATCH / (f32_step_ms / 1000.0)},
         "train_wall_s": t_train,
         "roofline": {"kernel": "fwd_split_kernel (tcgen05, 3 products per k-step)", "bound": "tensor",
@@ -378,7 +382,6 @@ def run_c4(args):
     scenes = [I.make_scene(4100 + o, int(rng.integers(16, 65)), 3, 0.02, 0.2, moving=True) for o in range(K)]
     shapes = [nb.Shape(s, dev) for s in scenes]
     off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
-    plan = nb.Plan(off, chunk_rows=4096)
     W = 4
     batches = []
     for j in range(W):
@@ -387,6 +390,10 @@ def run_c4(args):
         batches.append((torch.cat(qs).contiguous(), torch.cat(bs).contiguous()))
     g = nb.Group(widths, K, infer_prec="f16x3", train_prec="bf16")
     g.set_params(np.stack([I.init_params(6000 + o, widths) for o in range(K)]))
+    # rows per work item of the grouped launches, measured by the autotuner
+    cands = (1024, 2048, 4096, 8192, 16384)
+    chunk_train, ms_train = g.autotune(off, *batches[0], op="train", candidates=cands)
+    plan = nb.Plan(off, chunk_rows=chunk_train)
     T = args.train_steps if args.train_steps != TRAIN_STEPS else 2000
     alpha = (1.0 + 99.0 * np.arange(T) / max(T - 1, 1)).astype(np.float32)
     g.set_schedule(alpha)
@@ -415,12 +422,13 @@ def run_c4(args):
     # evaluation: 1M space-time points per object
     NE = args.n_eval if args.n_eval != N_EVAL else (1 << 20)
     eoff = np.arange(K + 1, dtype=np.int64) * NE
-    eplan = nb.Plan(eoff, chunk_rows=8192)
     eq = torch.empty((K * NE, 4), dtype=torch.float32, device=dev)
     ebits = torch.empty(nb.n_words(K * NE), dtype=torch.int32, device=dev)
     for o in range(K):
         eq[o * NE:(o + 1) * NE] = torch.as_tensor(I.sample_queries(I.POINT4T, 7000 + o, NE), device=dev)
         ebits[o * NE // 32:(o + 1) * NE // 32] = nb.label(shapes[o], I.POINT4T, eq[o * NE:(o + 1) * NE])
+    chunk_query, ms_query = g.autotune(eoff, eq, op="query", candidates=cands + (32768,))
+    eplan = nb.Plan(eoff, chunk_rows=chunk_query)
     taus = g.calibrate(eplan, eq, ebits)
     out = torch.empty_like(ebits)
     _, qst = g.query(eplan, eq, margin=MARGIN, out=out, stats=True)
@@ -450,6 +458,8 @@ def run_c4(args):
                  "fp32_single_object_queries_per_s": K * NE / (f32_ms / 1000.0),
                  "speedup_vs_fp32_single_object": f32_ms / ms,
                  "grouped_train_samples_per_s_bf16_graph": sum(counts) / (step_ms / 1000.0),
+                 "autotune": {"train_chunk_rows": chunk_train, "train_ms": ms_train,
+                              "query_chunk_rows": chunk_query, "query_ms": ms_query},
                  "cpu_baseline": {"value": cpu_v, "unit": "queries/s", "cores": cores, "kind": "oracle",
                                   "sample": f"{cpu_n} points of object 0 through the FP64 oracle forward"},
                  "e2e": None})

@@ -143,6 +143,20 @@ nb_status nb_model_set_state(nb_model *m, const void *host_buf, size_t bytes);
 nb_status nb_label(const nb_shape *shape, int32_t kind, const float *q, int64_t n, uint32_t *out_bits,
                    nb_label_stats *dev_stats, void *stream);
 
+/* Query sampling: Alg. 1 draws a fresh batch r ~ Uniform at every training
+ * iteration.  Writes queries first .. first+n-1 of the stream (seed, kind) as float
+ * rows q[n][enc width] (2, 3, 4, 6, 4, 6 floats), every value on the 2^-qexp grid,
+ * 8 <= qexp <= 20: points U[-1,1)^d; 4D points (x, t) with t U[0,1); rays with origin
+ * on the radius-2 sphere and direction uniform on S^2; planes with normal uniform on
+ * S^2 and offset U[-1,1); boxes with centre U[-1,1)^3 and half-extents log-uniform
+ * in [0.01, 0.5].  Query i is a function of (seed, kind, i) alone: it reads the
+ * counter-based generator Philox4x64-10 (Salmon et al., SC 2011) at counters
+ * (i, j, p, 0) under key (seed, kind), and every transform is integer or correctly
+ * rounded, so any split of a stream into calls gives the same bits.  q is a device
+ * buffer owned by the caller (4-byte aligned).  Asynchronous on stream; EINVAL for an
+ * unknown kind, qexp outside [8, 20], a negative range or a null q with n > 0. */
+nb_status nb_sample(int32_t kind, int32_t qexp, uint64_t seed, int64_t first, int64_t n, float *q, void *stream);
+
 /* One training iteration of Sec. 3.4 on a batch of n queries with labels y:
  * forward, mean asymmetric BCE of Eq. (loss) with weights alpha (on y log yhat) and
  * beta (on (1-y) log(1-yhat)), backward, deterministic gradient reduction and one
@@ -221,6 +235,22 @@ nb_status nb_query_grouped(nb_group *g, const nb_plan *plan, const float *q, flo
 /* nb_calibrate per object on its rows; host_tau[n_objects] receives the thresholds. */
 nb_status nb_calibrate_grouped(nb_group *g, const nb_plan *plan, const float *q, const uint32_t *label_bits,
                                double eps, double *host_tau, void *stream);
+
+/* Autotuner of the grouped launches' work split (the paper has no counterpart: its
+ * networks are trained one at a time).  For each candidate chunk_rows (multiples of
+ * 64) it builds the plan of host_offsets[n_objects + 1], runs op (NB_TUNE_QUERY: the
+ * grouped query at margin 0 into a scratch bit buffer; NB_TUNE_TRAIN: grouped training
+ * steps with alpha = beta = 1 on label_bits) once untimed and `reps` times timed with
+ * CUDA events on stream, and returns the fastest candidate in *best_chunk_rows and,
+ * when host_ms is not NULL, the mean milliseconds of every candidate in host_ms[].
+ * Training trials run on a snapshot: parameters, Adam moments, gradient and step
+ * counters are restored before returning, also on error.  Synchronous; allocates
+ * a scratch buffer and the trial plans (not capturable in a CUDA graph). */
+#define NB_TUNE_QUERY 0
+#define NB_TUNE_TRAIN 1
+nb_status nb_group_autotune(nb_group *g, const int64_t *host_offsets, int32_t n_objects, int32_t op, const float *q,
+                            const uint32_t *label_bits, const int32_t *candidates, int32_t n_candidates, int32_t reps,
+                            int32_t *best_chunk_rows, float *host_ms, void *stream);
 
 /* ------------------------------------------------------- learned-culler cascade
  * Many objects in one scene, each a union of spheres with its own trained bounding

@@ -607,3 +607,111 @@ extern "C" nb_status nb_calibrate_grouped(nb_group *g, const nb_plan *pl, const 
     }
     return upload_tau(g);
 }
+
+// ------------------------------------------------------------------ autotuner
+// The grouped launches split every object's rows into work items of chunk_rows rows;
+// small items balance uneven objects across the SMs, large ones load each object's
+// weights into shared memory fewer times.  The best split depends on the widths, the
+// object count and the spread of the counts, so it is measured: every candidate plan
+// runs the operation (one untimed launch, then `reps` timed with CUDA events on the
+// stream) and the fastest is returned.  Training trials run on a snapshot of the
+// parameters, Adam moments, gradient and step counters, restored afterwards.
+extern "C" nb_status nb_group_autotune(nb_group *g, const int64_t *host_offsets, int32_t n_objects, int32_t op,
+                                       const float *q, const uint32_t *label_bits, const int32_t *candidates,
+                                       int32_t n_candidates, int32_t reps, int32_t *best_chunk_rows, float *host_ms,
+                                       void *stream) {
+    if (!g || !host_offsets || !candidates || !best_chunk_rows) return nb_fail(NB_EINVAL, "nb_group_autotune: null pointer");
+    if (n_objects != g->n_objects) return nb_fail(NB_EINVAL, "nb_group_autotune: wrong object count");
+    if (op != NB_TUNE_QUERY && op != NB_TUNE_TRAIN) return nb_fail(NB_EINVAL, "nb_group_autotune: unknown operation");
+    if (n_candidates < 1 || n_candidates > 64 || reps < 1 || reps > 1000)
+        return nb_fail(NB_EINVAL, "nb_group_autotune: 1..64 candidates and 1..1000 repetitions");
+    if (!q || (op == NB_TUNE_TRAIN && !label_bits)) return nb_fail(NB_EINVAL, "nb_group_autotune: null pointer");
+    for (int c = 0; c < n_candidates; c++)
+        if (candidates[c] < 64 || candidates[c] % 64)
+            return nb_fail(NB_EINVAL, "nb_group_autotune: candidates must be multiples of 64");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n_rows = host_offsets[n_objects];
+    uint32_t *bits = nullptr;
+    float *snap = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    const size_t pb = (size_t)g->P * g->n_objects * sizeof(float);
+    nb_status st = NB_OK;
+    int best = -1;
+    float best_ms = INFINITY;
+    const int64_t step0 = g->step;
+    int dstep0 = 0;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        st = nb_fail(NB_ECUDA, "nb_group_autotune: event creation failed");
+        goto done;
+    }
+    if (op == NB_TUNE_QUERY) {
+        if (cudaMalloc(&bits, (size_t)((n_rows + 31) / 32 + 1) * sizeof(uint32_t)) != cudaSuccess) {
+            cudaGetLastError();
+            st = nb_fail(NB_ENOMEM, "nb_group_autotune: allocation failed");
+            goto done;
+        }
+    } else {
+        if (cudaMalloc(&snap, 4 * pb) != cudaSuccess) {
+            cudaGetLastError();
+            st = nb_fail(NB_ENOMEM, "nb_group_autotune: allocation failed");
+            goto done;
+        }
+        if (cudaStreamSynchronize(s) != cudaSuccess ||
+            cudaMemcpy(&dstep0, g->d_step, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            st = nb_fail(NB_ECUDA, "nb_group_autotune: device error");
+            goto done;
+        }
+        float *src[4] = {g->params, g->m, g->v, g->grad};
+        for (int k = 0; k < 4; k++)
+            if (cudaMemcpyAsync((char *)snap + k * pb, src[k], pb, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+                st = nb_fail(NB_ECUDA, "nb_group_autotune: snapshot failed");
+                goto done;
+            }
+    }
+    for (int c = 0; c < n_candidates && st == NB_OK; c++) {
+        nb_plan *pl = nullptr;
+        st = nb_plan_create(host_offsets, n_objects, candidates[c], &pl);
+        if (st != NB_OK) break;
+        float ms = 0.f;
+        for (int r = 0; r <= reps && st == NB_OK; r++) {
+            if (r == 1 && cudaEventRecord(e0, s) != cudaSuccess) st = nb_fail(NB_ECUDA, "nb_group_autotune: event");
+            if (st != NB_OK) break;
+            st = op == NB_TUNE_QUERY
+                     ? nb_query_grouped(g, pl, q, 0.0f, bits, nullptr, nullptr, stream)
+                     : nb_train_step_grouped(g, pl, q, label_bits, 1.0f, 1.0f, nullptr, stream);
+        }
+        if (st == NB_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+            st = nb_fail(NB_ECUDA, "nb_group_autotune: timing failed");
+        nb_plan_destroy(pl);
+        if (st != NB_OK) break;
+        ms /= (float)reps;
+        if (host_ms) host_ms[c] = ms;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+done:
+    if (snap) {
+        // restore the training state whatever happened above
+        float *dst[4] = {g->params, g->m, g->v, g->grad};
+        for (int k = 0; k < 4; k++) cudaMemcpyAsync(dst[k], (char *)snap + k * pb, pb, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(g->d_step, &dstep0, sizeof(int), cudaMemcpyHostToDevice, s);
+        g->step = step0;
+        if (cudaStreamSynchronize(s) != cudaSuccess && st == NB_OK) st = nb_fail(NB_ECUDA, "nb_group_autotune: restore failed");
+        const nb_status rs = group_refresh(g, s);
+        if (st == NB_OK) st = rs;
+        cudaStreamSynchronize(s);
+        cudaFree(snap);
+    }
+    if (bits) {
+        cudaStreamSynchronize(s);
+        cudaFree(bits);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st == NB_OK) *best_chunk_rows = candidates[best];
+    return st;
+}

@@ -29,7 +29,7 @@ EXPORTS = ["nb_model_create", "nb_model_destroy", "nb_model_param_count", "nb_mo
            "nb_plan_create", "nb_plan_destroy", "nb_group_create", "nb_group_destroy", "nb_group_param_count",
            "nb_group_set_params", "nb_group_get_params", "nb_group_get_grad", "nb_group_set_tau", "nb_group_get_tau",
            "nb_group_set_schedule", "nb_group_sync_schedule", "nb_group_reserve", "nb_train_step_grouped",
-           "nb_query_grouped", "nb_calibrate_grouped", "nb_cascade_bin", "nb_cascade_exact"]
+           "nb_query_grouped", "nb_calibrate_grouped", "nb_cascade_bin", "nb_cascade_exact", "nb_sample", "nb_group_autotune"]
 
 
 class NBError(RuntimeError):
@@ -104,6 +104,8 @@ def lib():
                 "nb_calibrate_grouped": ([P, P, P, P, ctypes.c_double, P, P], st),
                 "nb_cascade_bin": ([P, P, i64, i32, P, P, P, P, P, P], st),
                 "nb_cascade_exact": ([P, P, P, P, i64, P, P, P, P, P], st),
+                "nb_sample": ([i32, i32, ctypes.c_uint64, i64, i64, P, P], st),
+                "nb_group_autotune": ([P, P, i32, i32, P, P, P, i32, i32, P, P, P], st),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -155,6 +157,15 @@ class Shape:
         self.vel = None if scene.vel is None else _dev(scene.vel, torch.float32, device)
         self._s = _Shape(scene.dim, scene.n_spheres, scene.qexp, 0, self.centres.data_ptr(),
                          self.radii.data_ptr(), self.vel.data_ptr() if self.vel is not None else None)
+
+
+def sample(kind: int, n: int, seed: int, first: int = 0, qexp: int = 20, out: torch.Tensor | None = None,
+           device="cuda", stream=None) -> torch.Tensor:
+    """Queries first .. first+n-1 of the counter-based stream (seed, kind) (nb_sample)."""
+    if out is None:
+        out = torch.empty((n, ENC_WIDTH[kind]), dtype=torch.float32, device=device)
+    _check(lib().nb_sample(int(kind), int(qexp), int(seed), int(first), int(n), _ptr(out), _stream(stream)))
+    return out
 
 
 def label(shape: Shape, kind: int, q: torch.Tensor, out: torch.Tensor | None = None, stats: bool = False,
@@ -364,6 +375,20 @@ class Group:
         if stats:
             res.append(_read(st, QUERY_STATS))
         return res[0] if len(res) == 1 else tuple(res)
+
+    def autotune(self, offsets, q, label_bits=None, op: str = "query", candidates=(1024, 2048, 4096, 8192, 16384),
+                 reps: int = 3, stream=None):
+        """Fastest chunk_rows of the candidates for the grouped query or training step on
+        these rows (nb_group_autotune); returns (best, {candidate: ms})."""
+        off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+        cand = np.ascontiguousarray(np.asarray(candidates, dtype=np.int32))
+        ms = np.zeros(cand.size, dtype=np.float32)
+        best = ctypes.c_int32(0)
+        _check(lib().nb_group_autotune(self._h, off.ctypes.data_as(ctypes.c_void_p), self.n_objects,
+                                       {"query": 0, "train": 1}[op], _ptr(q), _ptr(label_bits),
+                                       cand.ctypes.data_as(ctypes.c_void_p), cand.size, int(reps), ctypes.byref(best),
+                                       ms.ctypes.data_as(ctypes.c_void_p), _stream(stream)))
+        return int(best.value), {int(c): float(m) for c, m in zip(cand, ms)}
 
     def calibrate(self, plan: Plan, q, label_bits, eps: float = 1e-5, stream=None) -> np.ndarray:
         t = np.zeros(self.n_objects, dtype=np.float64)

@@ -256,3 +256,40 @@ def test_grouped_bf16_graph_replay_equals_eager(nb):
     torch.cuda.synchronize()
     ge.sync_schedule()
     assert np.array_equal(ge.get_params(), eager.get_params())
+
+
+@pytest.mark.parametrize("train_prec,infer_prec", [("f32", "f32"), ("bf16", "f16x3")])
+def test_autotuner_picks_a_candidate_and_leaves_training_state_intact(nb, train_prec, infer_prec):
+    widths = [4, 64, 64, 64, 1]
+    counts = [4096, 800, 9024, 32, 2048, 20000]  # multiples of 32: queries need aligned objects
+    scenes, qs, off = _objects("point4t", 6, counts, 1500, moving=True)
+    y = np.concatenate([O.label(I.POINT4T, q, sc) for q, sc in zip(qs, scenes)])
+    qd = _dev(np.concatenate(qs))
+    bd = _dev(I.pack_bits(y).view(np.int32))
+    p0 = np.stack([I.init_params(1600 + o, widths) for o in range(6)])
+    plan = nb.Plan(off, chunk_rows=2048)
+    ref = nb.Group(widths, 6, infer_prec=infer_prec, train_prec=train_prec)
+    ref.set_params(p0)
+    ref.train_step(plan, qd, bd, 3.0)
+    g = nb.Group(widths, 6, infer_prec=infer_prec, train_prec=train_prec)
+    g.set_params(p0)
+    g.train_step(plan, qd, bd, 3.0)
+    cands = (512, 1024, 4096, 16384)
+    best, ms = g.autotune(off, qd, bd, op="train", candidates=cands, reps=2)
+    assert best in cands and set(ms) == set(cands) and all(v > 0 for v in ms.values())
+    assert ms[best] == min(ms.values())
+    # the trials left parameters, moments and step count as they were: one more step on
+    # both groups gives the same parameters
+    assert np.array_equal(g.get_params(), ref.get_params())
+    ref.train_step(plan, qd, bd, 3.0)
+    g.train_step(plan, qd, bd, 3.0)
+    assert np.array_equal(g.get_params(), ref.get_params())
+    bq, msq = g.autotune(off, qd, op="query", candidates=cands, reps=2)
+    assert bq in cands and msq[bq] == min(msq.values())
+    g.tau = 0.0
+    ref.tau = 0.0
+    tuned = nb.Plan(off, chunk_rows=bq)
+    assert np.array_equal(nb.bits_to_numpy(g.query(tuned, qd, margin=0.05), len(y)),
+                          nb.bits_to_numpy(ref.query(plan, qd, margin=0.05), len(y)))
+    with pytest.raises(nb.NBError):
+        g.autotune(off, qd, bd, op="train", candidates=(100,))
