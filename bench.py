@@ -476,21 +476,28 @@ def run_c5(args):
     K = 1024
     ms_ = I.make_multi_scene(5000, K, 32)
     ws = nb.WorldScene(ms_, dev)
-    B, W = 2048, 4
-    T = args.train_steps if args.train_steps != TRAIN_STEPS else 1000
-    shapes = [nb.Shape(ms_.local_scene(k), dev) for k in range(K)]
-    batches = []
-    for j in range(W):
-        qs = [torch.as_tensor(I.sample_queries(I.RAY3, 5100 + 10 * k + j, B), device=dev) for k in range(K)]
-        bs = [nb.label(shapes[k], I.RAY3, qs[k]) for k in range(K)]
-        batches.append((torch.cat(qs).contiguous(), torch.cat(bs).contiguous()))
-    plan = nb.Plan(np.arange(K + 1, dtype=np.int64) * B, chunk_rows=2048)
+    T = args.train_steps if args.train_steps != TRAIN_STEPS else 2000
+    # training pairs from the deployment distribution: world rays binned and moved into
+    # each object's frame by the cascade's own first stage, labelled by the exact stage
+    # (uneven pair counts per object, one grouped launch per step)
+    n_pools, pool_rays = 16, 1 << 18
+    pools = []
+    for j in range(n_pools):
+        r = torch.as_tensor(I.sample_world_rays(5100 + j, pool_rays), device=dev)
+        off, off_d, pair_ray, pair_q, _ = nb.cascade_bin(ws, r, canonical=True)
+        rows = int(off[-1])
+        lab = torch.zeros(nb.n_words(rows), dtype=torch.int32, device=dev)
+        nb.cascade_exact(ws, r, pair_ray, off_d, rows, pair_hits=lab)
+        pools.append((nb.Plan(off, chunk_rows=2048), pair_q, lab))
+        del r, off_d, pair_ray
     g = nb.Group(widths, K, infer_prec="f16x3", train_prec="bf16")
     g.set_params(np.stack([I.init_params(5200 + k, widths) for k in range(K)]))
     t0 = time.perf_counter()
     for t in range(T):
-        g.train_step(plan, *batches[t % W], 1.0 + 99.0 * t / max(T - 1, 1))
+        pl, pq, pb = pools[t % n_pools]
+        g.train_step(pl, pq, pb, 1.0 + 99.0 * t / max(T - 1, 1))
     torch.cuda.synchronize()
+    train_pairs_per_step = int(np.mean([p[0].n_rows for p in pools]))
     train_s = time.perf_counter() - t0
     NR = args.n_eval if args.n_eval != N_EVAL else (64 << 20)
     CH = min(NR, 16 << 20)
@@ -544,6 +551,27 @@ def run_c5(args):
     hp = nb.bits_to_numpy(hits_p, NR)
     ms, clocks = ctx.timed(cascade_step, args.steps, args.warmup)
     plain_ms = ctx.time_ms(plain_step, max(2, args.steps))
+    # per-stage times on the first chunk, for Eq. (Benefit): with the box (and ball) test
+    # alone every pair goes to the exact test (p_b = 1); with the network in front a
+    # fraction p_a does, at t_nn more per pair.  The network pays off when an exact pair
+    # test costs more than t_nn / (1 - p_a).
+    ch = chunks[0]
+    off, off_d, pair_ray, pair_q, _ = nb.cascade_bin(ws, ch, canonical=True)
+    rows = int(off[-1])
+    plan_c = nb.Plan(off, chunk_rows=2048)
+    hb = torch.zeros(nb.n_words(ch.shape[0]), dtype=torch.int32, device=dev)
+    neural = g.query(plan_c, pair_q, margin=MARGIN)
+    t_bin = ctx.time_ms(lambda: nb.cascade_bin(ws, ch, canonical=True), 2)
+    t_nn = ctx.time_ms(lambda: g.query(plan_c, pair_q, margin=MARGIN, out=neural), 3)
+    t_exact_all = ctx.time_ms(lambda: nb.cascade_exact(ws, ch, pair_ray, off_d, rows, ray_hits=hb), 3)
+    t_exact_pass = ctx.time_ms(lambda: nb.cascade_exact(ws, ch, pair_ray, off_d, rows, pass_bits=neural,
+                                                        ray_hits=hb), 3)
+    live = int((pair_ray != -1).sum().item())
+    p_a = e["exact_pairs"] / max(bin_stats["ball_pairs"], 1)
+    t_nn_pair = t_nn / max(live, 1)
+    t_exact_pair = t_exact_all / max(live, 1)
+    break_even = t_nn_pair / max(1.0 - p_a, 1e-12)
+    del off_d, pair_ray, pair_q, neural, plan_c
     # held-out rays: FN of the calibrated bounds on rays they were not calibrated on
     held = torch.as_tensor(I.sample_world_rays(5999, min(NR, 4 << 20)), device=dev)
     hh_c = torch.zeros(nb.n_words(held.shape[0]), dtype=torch.int32, device=dev)
@@ -561,15 +589,22 @@ def run_c5(args):
                      "f16x3 (split fp16 operands, fp32 accumulate)",
                      {"workload": "learned-culler cascade: 1024 objects of 32 spheres in [-10,10]^3, 6->128x3->1 per "
                                   "object, 64M rays (configs[4])", "n_rays": NR, "train_steps": T,
+                      "training": f"{n_pools} x {pool_rays} world rays through the box/ball stage, exact labels",
                       "calibration": "thresholds calibrated on the benchmark rays' own pairs"},
                      clocks, args.steps * len(chunks) * 5)
     line.update({"fn_vs_plain": int(np.sum(hp & ~hc)), "hits_equal_plain": bool(np.array_equal(hc, hp)),
+                 "stages_first_chunk_ms": {"bin": t_bin, "neural": t_nn, "exact_all_pairs": t_exact_all,
+                                           "exact_passed_pairs": t_exact_pass},
+                 "benefit": {"p_a": p_a, "t_nn_per_pair_ns": 1e6 * t_nn_pair, "t_exact_per_pair_ns": 1e6 * t_exact_pair,
+                             "break_even_exact_ns": 1e6 * break_even,
+                             "exact_cost_factor_needed": break_even / max(t_exact_pair, 1e-30)},
                  "plain_box_exact_rays_per_s": NR / (plain_ms / 1000.0),
                  "pairs": {"box": bin_stats["aabb_pairs"], "ball": bin_stats["ball_pairs"], "exact_plain": pe["exact_pairs"], "exact_cascade": e["exact_pairs"],
                            "hit": pe["hit_pairs"]},
                  "exact_tests_avoided": pe["exact_pairs"] - e["exact_pairs"],
                  "exact_sphere_tests": {"plain": pe["sphere_tests"], "cascade": e["sphere_tests"]},
                  "held_out_fn": held_fn, "held_out_rays": int(held.shape[0]), "grouped_train_s_bf16": train_s,
+                 "train_pairs_per_step": train_pairs_per_step,
                  "cpu_baseline": None, "e2e": None})
     ctx.emit(line)
 

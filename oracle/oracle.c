@@ -519,13 +519,15 @@ void orc_count(const double *z, const uint8_t *y, int64_t n, double tau, int64_t
  *                        accepted when 2^30 <= |v|^2 <= 2^40 (uniform in a
  *                        shell, so v/|v| is uniform on S^2); words are tried in
  *                        order w0..w3 of blocks j = 0..15, (0,0,1) if none is
- *                        accepted; u = v / sqrt(|v|^2) in FP64 (IEEE division
- *                        and square root), rounded to the grid (nearest, ties
- *                        to even).
- *   log-uniform [a, b]:  a * 2^(x log2(b/a)), x = (w >> 11) 2^-53, with 2^f for
- *                        the fractional part f evaluated as the degree-20
- *                        Taylor polynomial of exp(f ln 2) in the nested form
- *                        p = 1 + (t/k) p, k = 20 .. 1; rounded to the grid.
+ *                        accepted; u = v / sqrt(|v|^2) in FP32 (|v|^2 rounded to
+ *                        float, IEEE square root and division), rounded to the
+ *                        grid (nearest, ties to even).
+ *   log-uniform [a, b]:  a * 2^(x log2(b/a)) in FP32, x = (w >> 40) 2^-24, with
+ *                        2^f for the fractional part f evaluated as the degree-9
+ *                        Taylor polynomial of exp(f ln 2) (coefficients 1/k!
+ *                        rounded to float, Horner form); rounded to the grid.
+ *                        Every constant is a float literal; every operation is
+ *                        one IEEE float operation (no contraction).
  * Encodings: point (x from the fields of w0), 4D point (x, t), ray (2 u1, u2),
  * plane (u1, off from field 0 of w0), box (centre from w0, half-extent of axis
  * d log-uniform in [0.01, 0.5] from w_{1+d}).
@@ -568,9 +570,9 @@ static int64_t coord_units(uint64_t w, int s, int qexp) {
     return (f >> (20 - qexp)) - ((int64_t)1 << qexp);
 }
 
-static double grid_round(double x, int qexp) { return ldexp(rint(ldexp(x, qexp)), -qexp); }
+static float grid_round(float x, int qexp) { return ldexpf(rintf(ldexpf(x, qexp)), -qexp); }
 
-static void unit_vector(uint64_t seed, int kind, int64_t i, uint64_t p, double u[3]) {
+static void unit_vector(uint64_t seed, int kind, int64_t i, uint64_t p, float u[3]) {
     for (uint64_t j = 0; j < 16; j++) {
         uint64_t w[4];
         sample_block(seed, kind, i, j, p, w);
@@ -578,23 +580,28 @@ static void unit_vector(uint64_t seed, int kind, int64_t i, uint64_t p, double u
             const int64_t v0 = field21(w[m], 0), v1 = field21(w[m], 1), v2 = field21(w[m], 2);
             const int64_t n2 = v0 * v0 + v1 * v1 + v2 * v2;
             if (n2 >= ((int64_t)1 << 30) && n2 <= ((int64_t)1 << 40)) {
-                const double len = sqrt((double)n2);
-                u[0] = (double)v0 / len;
-                u[1] = (double)v1 / len;
-                u[2] = (double)v2 / len;
+                const float len = sqrtf((float)n2);
+                u[0] = (float)v0 / len;
+                u[1] = (float)v1 / len;
+                u[2] = (float)v2 / len;
                 return;
             }
         }
     }
-    u[0] = 0.0; u[1] = 0.0; u[2] = 1.0;
+    u[0] = 0.0f; u[1] = 0.0f; u[2] = 1.0f;
 }
 
-static double exp2_taylor(double y) {  /* y >= 0 */
-    const double n = floor(y);
-    const double t = (y - n) * 0.6931471805599453;
-    double p = 1.0;
-    for (int k = 20; k >= 1; k--) p = 1.0 + (t / (double)k) * p;
-    return ldexp(p, (int)n);
+/* 2^y for 0 <= y < 8: 2^floor(y) times the Taylor polynomial of exp(f ln 2) of degree 9,
+ * f = y - floor(y), with the coefficients 1/k! rounded to float, in Horner form */
+static float exp2_taylor(float y) {
+    static const float c[10] = {0x1p+0f, 0x1p+0f, 0x1p-1f, 0x1.555556p-3f, 0x1.555556p-5f,
+                                0x1.111112p-7f, 0x1.6c16c2p-10f, 0x1.a01a02p-13f, 0x1.a01a02p-16f,
+                                0x1.71de3ap-19f};
+    const float n = floorf(y);
+    const float t = (y - n) * 0x1.62e43p-1f;
+    float p = c[9];
+    for (int k = 8; k >= 0; k--) p = p * t + c[k];
+    return ldexpf(p, (int)n);
 }
 
 typedef struct {
@@ -614,7 +621,7 @@ static void sample_range(void *pc, int64_t lo, int64_t hi, int tid) {
         float *o = c->q + r * ENC_W[c->kind];
         uint64_t w[4];
         sample_block(c->seed, c->kind, i, 0, 0, w);
-        double u[3], v[3];
+        float u[3], v[3];
         switch (c->kind) {
         case K_POINT2:
             for (int d = 0; d < 2; d++) o[d] = (float)((double)coord_units(w[0], d, qe) * quantum);
@@ -630,20 +637,20 @@ static void sample_range(void *pc, int64_t lo, int64_t hi, int tid) {
             unit_vector(c->seed, c->kind, i, 1, u);
             unit_vector(c->seed, c->kind, i, 2, v);
             for (int d = 0; d < 3; d++) {
-                o[d] = (float)grid_round(2.0 * u[d], qe);
-                o[3 + d] = (float)grid_round(v[d], qe);
+                o[d] = grid_round(2.0f * u[d], qe);
+                o[3 + d] = grid_round(v[d], qe);
             }
             break;
         case K_PLANE3:
             unit_vector(c->seed, c->kind, i, 1, u);
-            for (int d = 0; d < 3; d++) o[d] = (float)grid_round(u[d], qe);
+            for (int d = 0; d < 3; d++) o[d] = grid_round(u[d], qe);
             o[3] = (float)((double)coord_units(w[0], 0, qe) * quantum);
             break;
         case K_BOX3:
             for (int d = 0; d < 3; d++) {
                 o[d] = (float)((double)coord_units(w[0], d, qe) * quantum);
-                const double x = (double)(w[1 + d] >> 11) * 0x1p-53;
-                o[3 + d] = (float)grid_round(0.01 * exp2_taylor(x * 5.643856189774724), qe);
+                const float x = (float)(w[1 + d] >> 40) * 0x1p-24f;
+                o[3 + d] = grid_round(0x1.47ae14p-7f * exp2_taylor(x * 0x1.6934fp+2f), qe);
             }
             break;
         }

@@ -23,6 +23,7 @@ namespace {
 constexpr int KC = 32;
 constexpr unsigned FULL = 0xffffffffu;
 constexpr float U = 5.9604644775390625e-08f;  // unit roundoff 2^-24
+constexpr int FF_WARPS_PER_SM = 32;              // stage-2 launch: 8 blocks of 4 warps per SM
 
 __device__ __forceinline__ unsigned ord_f32(float f) {
     unsigned u = __float_as_uint(f);
@@ -108,7 +109,7 @@ template <int NJ, int MI, int MODE>
 __global__ void __launch_bounds__(256) bound_tile_kernel(MlpDesc d, GammaTab gt, const float *__restrict__ q, TauF tau,
                                                          const unsigned *count, const unsigned *idx, uint32_t *bits,
                                                          nb_query_stats *st, unsigned *ff_count, unsigned *ff_idx,
-                                                         float *lo_out, unsigned *umin_bits) {
+                                                         float *lo_out, unsigned *umin_bits, unsigned direct_max) {
     constexpr int TM = 16 * MI, KP = 16 * NJ + 1, TPQ = 256 / TM;
     extern __shared__ float smem[];
     float *a0 = smem, *e0 = a0 + TM * KP, *a1 = e0 + TM * KP, *e1 = a1 + TM * KP, *wt = e1 + TM * KP;
@@ -116,6 +117,12 @@ __global__ void __launch_bounds__(256) bound_tile_kernel(MlpDesc d, GammaTab gt,
     __shared__ float zs[TM], bs[TM];
     const int t = threadIdx.x, w0 = d.w[0];
     const unsigned cnt = *count;
+    if (MODE == 0 && cnt <= direct_max) {
+        // a band this small is settled sooner by stage 2 alone: hand it over whole
+        for (unsigned f = blockIdx.x * blockDim.x + t; f < cnt; f += gridDim.x * blockDim.x) ff_idx[f] = idx[f];
+        if (blockIdx.x == 0 && t == 0) *ff_count = cnt;
+        return;
+    }
     const unsigned ntiles = (cnt + TM - 1) / TM;
     unsigned long long r32 = 0;
     long long dinside = 0;
@@ -261,6 +268,75 @@ __device__ __forceinline__ void ff_neuron(const float *__restrict__ Wr, float bv
     bound = __fmaf_ru(g4, A3, __fmaf_ru(2.f * U, __fadd_ru(fabsf(t4), fabsf(t3)), P));
 }
 
+// ff_neuron for the neurons nn0, nn0 + 32, ..., nn0 + 32 (NB - 1) of one layer (those
+// below N), their chains interleaved so that the dependent TwoSum sequences of different
+// neurons overlap; every neuron's arithmetic is exactly that of ff_neuron.  Writes
+// relu(hi + lo) as a pair and the propagated bound.
+template <int NB>
+__device__ __forceinline__ void ff_neurons_relu(const float *__restrict__ W, const float *__restrict__ bias, int K,
+                                                int N, int nn0, float g4, const float *h, const float *l,
+                                                const float *e, float *h2, float *l2, float *e2) {
+    float s1[NB], s2[NB], s3[NB], A3[NB], P[NB];
+    const float *Wr[NB];
+#pragma unroll
+    for (int j = 0; j < NB; j++) {
+        const int nn = nn0 + 32 * j;
+        const bool ok = nn < N;
+        Wr[j] = W + (size_t)(ok ? nn : 0) * K;
+        s1[j] = ok ? __ldg(bias + nn) : 0.f;
+        s2[j] = 0.f;
+        s3[j] = 0.f;
+        A3[j] = 0.f;
+        P[j] = 0.f;
+    }
+    for (int k = 0; k < K; k++) {
+        const float hk = h[k], lk = l[k], ek = e[k];
+#pragma unroll
+        for (int j = 0; j < NB; j++) {
+            const float w = __ldg(Wr[j] + k);
+            const float p = __fmul_rn(w, hk);
+            const float pq = fmaf(w, hk, -p);
+            const float r = __fmul_rn(w, lk);
+            const float rq = fmaf(w, lk, -r);
+            float t, e1, ea, eb, ec;
+            two_sum(s1[j], p, t, e1);
+            s1[j] = t;
+            two_sum(s2[j], e1, t, ea);
+            s2[j] = t;
+            two_sum(s2[j], pq, t, eb);
+            s2[j] = t;
+            two_sum(s2[j], r, t, ec);
+            s2[j] = t;
+            s3[j] = __fadd_rn(s3[j], ea);
+            s3[j] = __fadd_rn(s3[j], eb);
+            s3[j] = __fadd_rn(s3[j], ec);
+            s3[j] = __fadd_rn(s3[j], rq);
+            A3[j] = __fadd_ru(A3[j], __fadd_ru(__fadd_ru(fabsf(ea), fabsf(eb)), __fadd_ru(fabsf(ec), fabsf(rq))));
+            P[j] = __fmaf_ru(fabsf(w), ek, P[j]);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < NB; j++) {
+        const int nn = nn0 + 32 * j;
+        if (nn < N) {
+            float t2, t3, t4, hi;
+            two_sum(s2[j], s3[j], t2, t3);
+            two_sum(s1[j], t2, hi, t4);
+            const float lo = __fadd_rn(t4, t3);
+            const float bd = __fmaf_ru(g4, A3[j], __fmaf_ru(2.f * U, __fadd_ru(fabsf(t4), fabsf(t3)), P[j]));
+            // relu(hi + lo): |lo| is far below |hi| unless hi = 0, so the sign is hi's
+            if (hi > 0.f) {
+                h2[nn] = hi;
+                l2[nn] = lo;
+            } else {
+                h2[nn] = hi == 0.f ? fmaxf(lo, 0.f) : 0.f;
+                l2[nn] = 0.f;
+            }
+            e2[nn] = bd;
+        }
+    }
+}
+
 // One warp per query still ambiguous after stage 1.
 // Grouped form: when `offsets` is given, query i belongs to the object o with
 // offsets[o] <= i < offsets[o+1], whose parameters start at d.p + o * P and whose
@@ -299,19 +375,8 @@ __global__ void __launch_bounds__(128) ff_kernel(MlpDesc d, GammaTab gt, const f
         for (int ly = 0; ly < d.L - 1; ly++) {
             const int K = d.w[ly], N = d.w[ly + 1];
             const float *W = dd.p + dd.off[ly];
-            for (int nn = lane; nn < N; nn += 32) {
-                float hi, lo, bd;
-                ff_neuron(W + (size_t)nn * K, __ldg(W + (size_t)N * K + nn), K, gt.gff[ly], h, l, e, hi, lo, bd);
-                // relu(hi + lo): |lo| is far below |hi| unless hi = 0, so the sign is hi's
-                if (hi > 0.f) {
-                    h2[nn] = hi;
-                    l2[nn] = lo;
-                } else {
-                    h2[nn] = hi == 0.f ? fmaxf(lo, 0.f) : 0.f;
-                    l2[nn] = 0.f;
-                }
-                e2[nn] = bd;
-            }
+            for (int nn0 = lane; nn0 < N; nn0 += 32 * 4)
+                ff_neurons_relu<4>(W, W + (size_t)N * K, K, N, nn0, gt.gff[ly], h, l, e, h2, l2, e2);
             __syncwarp();
             float *tp = h;
             h = h2;
@@ -441,7 +506,10 @@ nb_status tile_launch(const MlpDesc &d, const GammaTab &gt, const float *q, TauF
     const int64_t need = (max_count + TM - 1) / TM;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
-    k<<<(unsigned)grid, 256, smem, s>>>(d, gt, q, tau, count, idx, bits, st, ff_count, ff_idx, lo_out, umin_bits);
+    // bands of at most a few queries per stage-2 warp skip stage 1 (MODE 0 only)
+    const unsigned direct_max = MODE == 0 ? (unsigned)(FF_WARPS_PER_SM * 2) * (unsigned)num_sms() : 0u;
+    k<<<(unsigned)grid, 256, smem, s>>>(d, gt, q, tau, count, idx, bits, st, ff_count, ff_idx, lo_out, umin_bits,
+                                        direct_max);
     NB_CUDA(cudaGetLastError());
     return NB_OK;
 }
@@ -472,7 +540,7 @@ nb_status nb_launch_recheck(const MlpDesc &d, const GammaTab &gt, const float *q
     nb_status r = tile_dispatch<0>(d, gt, q, tau, ws.flag_count, ws.flag_idx, n, bits, st, ws.ff_count, ws.ff_idx,
                                    nullptr, nullptr, s);
     if (r != NB_OK) return r;
-    int64_t grid = num_sms() * 4;
+    int64_t grid = num_sms() * (FF_WARPS_PER_SM / 4);
     if (grid > (n + 3) / 4) grid = (n + 3) / 4;
     if (grid < 1) grid = 1;
     ff_kernel<<<(unsigned)grid, 128, 0, s>>>(d, gt, q, tau, ws.ff_count, ws.ff_idx, bits, st, nullptr, 0, 0, nullptr);
@@ -484,7 +552,7 @@ nb_status nb_launch_recheck_grouped(const MlpDesc &d, const GammaTab &gt, const 
                                     int n_objects, long long P, const TauF *taus, uint32_t *bits, nb_query_stats *st,
                                     QueryWs ws, int64_t n, cudaStream_t s) {
     // the flagged queries of several objects go straight to the extended-precision stage
-    int64_t grid = num_sms() * 4;
+    int64_t grid = num_sms() * (FF_WARPS_PER_SM / 4);
     if (grid > (n + 3) / 4) grid = (n + 3) / 4;
     if (grid < 1) grid = 1;
     TauF none{};

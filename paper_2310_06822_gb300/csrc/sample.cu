@@ -5,10 +5,11 @@
 // philox(counter = (i, j, p, 0), key = (seed, kind)), p = 0 for its scalars and
 // p = 1, 2 for its first and second unit vector (j counts rejection attempts), so
 // any range of a stream can be drawn by any launch in any order.  Every value is
-// built in integers or in correctly rounded IEEE operations (division, square root,
+// built in integers or in single IEEE float operations (division, square root,
 // products and sums written with explicit round-to-nearest intrinsics, no
-// contraction), then rounded to the 2^-qexp grid, so a stream is the same bits on
-// every device.
+// contraction; FP32 rather than FP64, whose rate on this GPU is a small fraction of
+// FP32's), then rounded to the 2^-qexp grid, so a stream is the same bits on every
+// device.
 #include "common.cuh"
 
 namespace {
@@ -48,13 +49,14 @@ __device__ __forceinline__ float coord(unsigned long long w, int s, int qexp, fl
     return (float)((f >> (20 - qexp)) - (1ll << qexp)) * quantum;
 }
 
-__device__ __forceinline__ float grid_round(double x, double scale, double quantum) {
-    return (float)__dmul_rn(rint(__dmul_rn(x, scale)), quantum);
+__device__ __forceinline__ float grid_round(float x, float scale, float quantum) {
+    return __fmul_rn(rintf(__fmul_rn(x, scale)), quantum);
 }
 
 // uniform direction: the first of up to 64 words whose three signed 21-bit fields
-// lie in the shell 2^30 <= |v|^2 <= 2^40, normalised in FP64
-__device__ void unit_vector(unsigned long long seed, int kind, long long i, unsigned p, double u[3]) {
+// lie in the shell 2^30 <= |v|^2 <= 2^40, normalised in FP32 (|v|^2 rounded to float,
+// IEEE square root and division)
+__device__ void unit_vector(unsigned long long seed, int kind, long long i, unsigned p, float u[3]) {
     for (unsigned j = 0; j < 16; j++) {
         const Block4 b = philox((unsigned long long)i, j, p, seed, (unsigned long long)kind);
 #pragma unroll
@@ -62,48 +64,52 @@ __device__ void unit_vector(unsigned long long seed, int kind, long long i, unsi
             const long long v0 = field21(b.w[m], 0), v1 = field21(b.w[m], 1), v2 = field21(b.w[m], 2);
             const long long n2 = v0 * v0 + v1 * v1 + v2 * v2;
             if (n2 >= (1ll << 30) && n2 <= (1ll << 40)) {
-                const double len = __dsqrt_rn((double)n2);
-                u[0] = __ddiv_rn((double)v0, len);
-                u[1] = __ddiv_rn((double)v1, len);
-                u[2] = __ddiv_rn((double)v2, len);
+                const float len = __fsqrt_rn(__ll2float_rn(n2));
+                u[0] = __fdiv_rn((float)v0, len);
+                u[1] = __fdiv_rn((float)v1, len);
+                u[2] = __fdiv_rn((float)v2, len);
                 return;
             }
         }
     }
-    u[0] = 0.0;
-    u[1] = 0.0;
-    u[2] = 1.0;
+    u[0] = 0.f;
+    u[1] = 0.f;
+    u[2] = 1.f;
 }
 
-// 2^y for y >= 0: 2^floor(y) times the degree-20 Taylor polynomial of exp(f ln 2),
-// f = y - floor(y), in the nested form p = 1 + (t/k) p, k = 20 .. 1
-__device__ double exp2_taylor(double y) {
-    const double n = floor(y);
-    const double t = __dmul_rn(__dadd_rn(y, -n), 0.6931471805599453);
-    double p = 1.0;
-    for (int k = 20; k >= 1; k--) p = __dadd_rn(1.0, __dmul_rn(__ddiv_rn(t, (double)k), p));
-    return scalbn(p, (int)n);
+// 2^y for 0 <= y < 8: 2^floor(y) times the degree-9 Taylor polynomial of exp(f ln 2),
+// f = y - floor(y), coefficients 1/k! rounded to float, Horner form, one IEEE float
+// operation per step
+__device__ float exp2_taylor(float y) {
+    constexpr float c[10] = {0x1p+0f, 0x1p+0f, 0x1p-1f, 0x1.555556p-3f, 0x1.555556p-5f,
+                             0x1.111112p-7f, 0x1.6c16c2p-10f, 0x1.a01a02p-13f, 0x1.a01a02p-16f,
+                             0x1.71de3ap-19f};
+    const float n = floorf(y);
+    const float t = __fmul_rn(__fsub_rn(y, n), 0x1.62e43p-1f);
+    float p = c[9];
+#pragma unroll
+    for (int k = 8; k >= 0; k--) p = __fadd_rn(__fmul_rn(p, t), c[k]);
+    return ldexpf(p, (int)n);
 }
 
 template <int KIND, int W>
 __global__ void __launch_bounds__(TPB) sample_kernel(unsigned long long seed, int qexp, long long first,
                                                      long long n, float *__restrict__ q) {
     __shared__ float buf[TPB * W];
-    const float quantum = ldexpf(1.0f, -qexp);
-    const double dscale = ldexp(1.0, qexp), dquantum = ldexp(1.0, -qexp);
+    const float quantum = ldexpf(1.0f, -qexp), scale = ldexpf(1.0f, qexp);
     for (long long base = (long long)blockIdx.x * TPB; base < n; base += (long long)gridDim.x * TPB) {
         const long long r = base + threadIdx.x;
         if (r < n) {
             const long long i = first + r;
             float *o = buf + threadIdx.x * W;
             if (KIND == NB_RAY3) {
-                double u[3], v[3];
+                float u[3], v[3];
                 unit_vector(seed, KIND, i, 1, u);
                 unit_vector(seed, KIND, i, 2, v);
 #pragma unroll
                 for (int d = 0; d < 3; d++) {
-                    o[d] = grid_round(2.0 * u[d], dscale, dquantum);
-                    o[3 + d] = grid_round(v[d], dscale, dquantum);
+                    o[d] = grid_round(2.f * u[d], scale, quantum);
+                    o[3 + d] = grid_round(v[d], scale, quantum);
                 }
             } else {
                 const Block4 b = philox((unsigned long long)i, 0, 0, seed, (unsigned long long)KIND);
@@ -118,16 +124,16 @@ __global__ void __launch_bounds__(TPB) sample_kernel(unsigned long long seed, in
                     if (KIND == NB_BOX3) {
 #pragma unroll
                         for (int d = 0; d < 3; d++) {
-                            const double x = __dmul_rn((double)(b.w[1 + d] >> 11), 0x1p-53);
-                            const double e = __dmul_rn(0.01, exp2_taylor(__dmul_rn(x, 5.643856189774724)));
-                            o[3 + d] = grid_round(e, dscale, dquantum);
+                            const float x = __fmul_rn((float)(b.w[1 + d] >> 40), 0x1p-24f);
+                            const float e = __fmul_rn(0x1.47ae14p-7f, exp2_taylor(__fmul_rn(x, 0x1.6934fp+2f)));
+                            o[3 + d] = grid_round(e, scale, quantum);
                         }
                     }
                 } else if (KIND == NB_PLANE3) {
-                    double u[3];
+                    float u[3];
                     unit_vector(seed, KIND, i, 1, u);
 #pragma unroll
-                    for (int d = 0; d < 3; d++) o[d] = grid_round(u[d], dscale, dquantum);
+                    for (int d = 0; d < 3; d++) o[d] = grid_round(u[d], scale, quantum);
                     o[3] = coord(b.w[0], 0, qexp, quantum);
                 }
             }

@@ -69,8 +69,9 @@ def test_points_uniform_on_the_grid(kind):
 
 def _check_directions(u, radius):
     r = np.linalg.norm(u.astype(np.float64), axis=1)
-    # each component is within half a grid step of the exact point on the sphere
-    assert np.all(np.abs(r - radius) <= math.sqrt(3) * Q / 2 + 1e-12)
+    # each component is within half a grid step, plus the FP32 normalisation error
+    # (square root and division, at most 1.5 ulp of a value below 1), of the exact point
+    assert np.all(np.abs(r - radius) <= math.sqrt(3) * radius * (Q / 2 + 1.5 * 2.0 ** -24))
     v = u.astype(np.float64) / radius
     # Archimedes: every coordinate of a uniform point on S^2 is uniform on [-1, 1]
     for j in range(3):
@@ -106,9 +107,11 @@ def test_box_half_extents_are_log_uniform():
 
 
 def test_box_half_extent_transform_against_library_exp2():
-    # the half-extent of axis d reads word 1+d of block (i, 0, 0, 0) under key (seed, kind);
-    # numpy's Philox and exp2 give the same value to within one grid step, and the same
-    # grid value away from rounding ties
+    # the half-extent of axis d reads the top 24 bits of word 1+d of block (i, 0, 0, 0)
+    # under key (seed, kind); against numpy's Philox and a float64 exp2 the FP32 value is
+    # within half a grid step plus the FP32 error (the rounding of x log2(50), up to
+    # 2^-24 * 5.7 in the exponent, dominates: below 5e-7 relative), and on the same grid
+    # point except where the exact value lies within that error of a rounding boundary
     seed, n = 23, 2000
     q = O.sample(BOX3, n, seed=seed)
     agree = 0
@@ -116,12 +119,13 @@ def test_box_half_extent_transform_against_library_exp2():
         prev = [i - 1, 0, 0, 0] if i > 0 else [2 ** 64 - 1, 2 ** 64 - 1, 2 ** 64 - 1, 2 ** 64 - 1]
         w = np.random.Philox(key=[seed, BOX3], counter=prev).random_raw(4)
         for d in range(3):
-            x = float(int(w[1 + d]) >> 11) * 2.0 ** -53
+            x = float(int(w[1 + d]) >> 40) * 2.0 ** -24
             e = 0.01 * np.exp2(x * math.log2(50.0))
             ref = np.rint(e / Q) * Q
-            assert abs(float(q[i, 3 + d]) - ref) <= Q
-            agree += float(q[i, 3 + d]) == ref
-    assert agree >= 3 * n - 2
+            got = float(q[i, 3 + d])
+            assert abs(got - e) <= Q / 2 + 5e-7 * e
+            agree += got == ref
+    assert agree >= 0.97 * 3 * n
 
 
 def test_coarser_grid():
