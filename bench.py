@@ -10,7 +10,8 @@ One timed step = nb_query over the 16M evaluation rays (split-FP16 tcgen05 forwa
 FP32 / extended-precision re-check of the margin band), inputs resident in HBM (384 MB
 per step, more than the 129 MB L2, so no flush is needed); value = rays/s over all ranks.
 
-Other configurations (--config): c1 (2D points, plain FP32), c4 (256 objects of moving
+Other configurations (--config): c1 (2D points, plain FP32), c3 (3D boxes and planes,
+256 spheres, 256-wide networks, FP8 E4M3 inference), c4 (256 objects of moving
 spheres, 4D points, grouped training under a CUDA graph and grouped queries), c5 (1024
 objects, 64M world rays through the learned-culler cascade, against box + exact).
 Every line also carries the FP64 oracle timed on the host cores, an end-to-end figure
@@ -319,6 +320,113 @@ def run_c2(args):
         "e2e": {"value": ctx.world * n_eval / (e2e_ms / 1000.0), "unit": "queries/s",
                 "h2d_bytes_per_step": n_eval * 6 * 4, "d2h_bytes_per_step": nb.n_words(n_eval) * 4},
     })
+    ctx.emit(line)
+
+
+# ---------------------------------------------------------------------------------- 3D boxes, planes (FP8)
+def run_c3(args):
+    from paper_2310_06822_gb300 import inputs as I
+    from paper_2310_06822_gb300 import nb
+    ctx = Ctx(args)
+    torch, dev = ctx.torch, ctx.dev
+    sc = I.make_scene(1003, 256, 3, R_LO, R_HI)
+    shape = nb.Shape(sc, dev)
+    T = args.train_steps if args.train_steps != TRAIN_STEPS else 2000
+    B = 131072
+    n_eval = args.n_eval if args.n_eval != N_EVAL else (64 << 20)
+    res = {}
+    for kind, w0 in ((I.BOX3, 6), (I.PLANE3, 4)):
+        widths = [w0, 256, 256, 256, 256, 1]
+        # FP32 training (the BF16 training kernel holds at most 128-wide layers), a fresh
+        # GPU-sampled and labelled batch per step
+        tr = nb.Model(widths)
+        tr.set_params(I.init_params(4003 + kind, widths))
+        qb = torch.empty((B, w0), dtype=torch.float32, device=dev)
+        yb = torch.empty(nb.n_words(B), dtype=torch.int32, device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for t in range(T):
+            nb.sample(kind, B, 2003 + kind, first=t * B, out=qb)
+            nb.label(shape, kind, qb, out=yb)
+            tr.train_step(qb, yb, 1.0 + 99.0 * t / max(T - 1, 1), 1.0)
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t0
+        params = tr.get_params()
+        # evaluation queries drawn by the GPU sampler (another stream), exact labels
+        eq = nb.sample(kind, n_eval, 3003 + kind + 1000 * ctx.rank)
+        ey = nb.label(shape, kind, eq)
+        f32 = nb.Model(widths)
+        f32.set_params(params)
+        tau = f32.calibrate(eq, ey, eps=1e-5)
+        f8 = nb.Model(widths, infer_prec="fp8")
+        f8.set_params(params)
+        f8.tau = tau
+        _, z8 = f8.query(eq, logits=True)
+        _, z32 = f32.query(eq, logits=True)
+        err = float((z8 - z32).abs().max().item())
+        del z8, z32
+        margin = max(2.0 * err, 0.05)
+        out = torch.empty(nb.n_words(n_eval), dtype=torch.int32, device=dev)
+        bits, qst = f8.query(eq, margin=margin, out=out, stats=True)
+        y = nb.bits_to_numpy(ey, n_eval)
+        dec = nb.bits_to_numpy(bits, n_eval)
+        dec32 = nb.bits_to_numpy(f32.query(eq, margin=1e-2), n_eval)
+        res[kind] = dict(widths=widths, params=params, eq=eq, f8=f8, f32=f32, out=out, margin=margin, err=err,
+                         fn=int(np.sum(y & ~dec)), fp=int(np.sum(~y & dec)), differ=int(np.sum(dec != dec32)),
+                         qst=qst, tau=tau, train_s=train_s, pos=int(y.sum()))
+        torch.cuda.empty_cache()
+    box = res[I.BOX3]
+    ms, clocks = ctx.timed(lambda: box["f8"].query(box["eq"], margin=box["margin"], out=box["out"]), args.steps,
+                           args.warmup)
+    value = ctx.world * n_eval / (ms / 1000.0)
+    fwd_ms = ctx.time_ms(lambda: box["f8"].query(box["eq"], margin=0.0, out=box["out"]), max(3, args.steps // 4))
+    f32_ms = ctx.time_ms(lambda: box["f32"].query(box["eq"], margin=1e-2, out=box["out"]), 2)
+    pl = res[I.PLANE3]
+    pl_ms = ctx.time_ms(lambda: pl["f8"].query(pl["eq"], margin=pl["margin"], out=pl["out"]), max(3, args.steps // 4))
+    pl32_ms = ctx.time_ms(lambda: pl["f32"].query(pl["eq"], margin=1e-2, out=pl["out"]), 2)
+    tr_ms = {}
+    for kind, r in res.items():
+        qb = nb.sample(kind, B, 9)
+        yb = nb.label(shape, kind, qb)
+        m = nb.Model(r["widths"])
+        m.set_params(r["params"])
+        tr_ms[kind] = ctx.time_ms(lambda: m.train_step(qb, yb, 50.0), 10)
+    if ctx.rank != 0:
+        return ctx.emit(None)
+    pk, pk_kind = peaks()
+    macs = sum(box["widths"][i] * box["widths"][i + 1] for i in range(5))
+    flops = 2.0 * macs * n_eval
+    achieved = flops / (fwd_ms / 1000.0) / 1e12
+    peak = 2.0 * float(pk.get("bf16_tflops", 1900.0))  # E4M3 dense rate = 2x BF16 (nominal 4.5 vs 2.25 PF)
+    cpu_v, cores, cpu_n = cpu_oracle_rate(box["widths"], box["params"], box["eq"][:200000].cpu().numpy(), seconds=8.0)
+
+    def summary(r, q_ms, q32_ms):
+        return {"fn": r["fn"], "fp": r["fp"], "fp_rate": r["fp"] / n_eval, "positives": r["pos"], "tau": r["tau"],
+                "margin": r["margin"], "max_logit_dev_fp8_vs_fp32_form": r["err"],
+                "decisions_differing_from_fp32_form": r["differ"],
+                "band": {"flagged": r["qst"]["n_flagged"], "resolved_f32": r["qst"]["n_resolved_f32"],
+                         "resolved_ff": r["qst"]["n_resolved_ff"], "unresolved": r["qst"]["n_unresolved"]},
+                "fp8_queries_per_s": n_eval / (q_ms / 1000.0), "fp32_plain_queries_per_s": n_eval / (q32_ms / 1000.0),
+                "train_s_fp32": r["train_s"]}
+
+    line = base_line(ctx, "neural-bound queries/s at 0 FN (3D boxes, FP8 E4M3 tcgen05 forward + FP32 re-check)",
+                     value, "queries/s", ms, args.steps, args.warmup, "e4m3 (fp8 operands, fp32 accumulate)",
+                     {"workload": "3D box and plane queries: 256-sphere union, MLP in->256x4->1, FP8 inference, "
+                                  "64M eval queries (configs[2])", "n_eval": n_eval, "batch": B, "train_steps": T,
+                      "train_precision": "fp32 (BF16 training kernel limited to width 128)",
+                      "l2": f"inputs {n_eval * 24 >> 20} MB per step > L2"},
+                     clocks, args.steps * 3)
+    line.update({"box": summary(box, ms, f32_ms), "plane": summary(pl, pl_ms, pl32_ms),
+                 "speedup_vs_fp32_plain": f32_ms / ms,
+                 "train_samples_per_s_fp32": {"box": B / (tr_ms[I.BOX3] / 1000.0),
+                                              "plane": B / (tr_ms[I.PLANE3] / 1000.0)},
+                 "roofline": {"kernel": "fwd_fp8_kernel (tcgen05 kind::f8f6f4)", "bound": "tensor",
+                              "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                              "traffic": None, "peak_kind": f"{pk_kind} bf16 burst x 2 (E4M3 nominal ratio)",
+                              "fwd_ms": fwd_ms, "algorithmic_flops_per_launch": flops},
+                 "cpu_baseline": {"value": cpu_v, "unit": "queries/s", "cores": cores, "kind": "oracle",
+                                  "sample": f"{cpu_n} box queries through the FP64 oracle forward"},
+                 "e2e": None})
     ctx.emit(line)
 
 
@@ -644,13 +752,13 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c4", "c5"])
+    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4", "c5"])
     ap.add_argument("--train-steps", type=int, default=TRAIN_STEPS)
     ap.add_argument("--n-eval", type=int, default=N_EVAL, help="evaluation size (smaller only for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
-    {"c1": run_c1, "c2": run_c2, "c4": run_c4, "c5": run_c5}[args.config](args)
+    {"c1": run_c1, "c2": run_c2, "c3": run_c3, "c4": run_c4, "c5": run_c5}[args.config](args)
 
 
 if __name__ == "__main__":

@@ -319,13 +319,33 @@ int num_sms() {
 nb_status nb_tc_init(TcModel *tc, const MlpDesc &d, int infer_prec, int train_prec) {
     tc->infer_prec = infer_prec;
     tc->train_prec = train_prec;
-    if (infer_prec == NB_FP8) return nb_fail(NB_EUNSUPPORTED, "FP8 inference is not available in this build");
     const int H = d.w[1], NH = d.L - 1;
     if (cudaMalloc(&tc->err, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         return nb_fail(NB_ENOMEM, "tensor-core state allocation failed");
     }
     cudaMemset(tc->err, 0, sizeof(int));
+    if (infer_prec == NB_FP8) {
+        const int NHH = d.L - 2;
+        if (NHH < 1) return nb_fail(NB_EUNSUPPORTED, "FP8 forward needs at least two hidden layers");
+        if (d.w[0] > 16) return nb_fail(NB_EUNSUPPORTED, "FP8 forward: input width must be <= 16");
+        if (H != 128 && H != 256) return nb_fail(NB_EUNSUPPORTED, "FP8 forward: hidden width must be 128 or 256");
+        for (int l = 1; l < d.L; l++)
+            if (d.w[l] != H) return nb_fail(NB_EUNSUPPORTED, "FP8 forward: hidden widths must be equal");
+        int dev = 0, maxsm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (nb_fp8_smem_bytes(H, NHH) > (size_t)maxsm)
+            return nb_fail(NB_EUNSUPPORTED, "FP8 forward: the network's weights do not fit in shared memory");
+        tc->img_bytes = nb_fp8_img_bytes(H, NHH);
+        if (cudaMalloc(&tc->img, tc->img_bytes) != cudaSuccess ||
+            cudaMalloc(&tc->scales, sizeof(float) * NHH * H) != cudaSuccess) {
+            cudaGetLastError();
+            return nb_fail(NB_ENOMEM, "tensor-core image allocation failed");
+        }
+        cudaMemset(tc->img, 0, tc->img_bytes);
+        cudaMemset(tc->scales, 0, sizeof(float) * NHH * H);
+    }
     if (infer_prec == NB_BF16 || infer_prec == NB_F16X3) {
         if (NH < 1) return nb_fail(NB_EUNSUPPORTED, "tensor-core forward needs at least one hidden layer");
         if (d.w[0] > 16) return nb_fail(NB_EUNSUPPORTED, "tensor-core forward: input width must be <= 16");
@@ -362,6 +382,8 @@ void nb_tc_free(TcModel *tc) {
     cudaFree(tc->img);
     cudaFree(tc->err);
     cudaFree(tc->train_img);
+    cudaFree(tc->scales);
+    tc->scales = nullptr;
     tc->img = nullptr;
     tc->err = nullptr;
     tc->train_img = nullptr;
@@ -374,6 +396,7 @@ nb_status nb_tc_refresh(TcModel *tc, const MlpDesc &d, cudaStream_t s) {
     }
     if (!tc->img) return NB_OK;
     if (tc->infer_prec == NB_F16X3) return nb_split_refresh(tc, d, s);
+    if (tc->infer_prec == NB_FP8) return nb_fp8_refresh(tc, d, s);
     const TcDesc t = make_desc(tc, d);
     const uint32_t nchunks = t.img_bytes / 16;
     pack_bf16_kernel<<<(nchunks + 255) / 256, 256, 0, s>>>(t, (uint8_t *)tc->img);
@@ -384,6 +407,7 @@ nb_status nb_tc_refresh(TcModel *tc, const MlpDesc &d, cudaStream_t s) {
 nb_status nb_tc_query(TcModel *tc, const MlpDesc &d, const float *q, int64_t n, TauF tau, float margin,
                       uint32_t *bits, float *logits, nb_query_stats *st, QueryWs ws, cudaStream_t s) {
     if (tc->infer_prec == NB_F16X3) return nb_split_query(tc, d, q, n, tau, margin, bits, logits, st, ws, s);
+    if (tc->infer_prec == NB_FP8) return nb_fp8_query(tc, d, q, n, tau, margin, bits, logits, st, ws, s);
     const TcDesc t = make_desc(tc, d);
     const size_t smem = fwd_smem_bytes(t.H, t.NH);
     const int64_t tiles = (n + TILE_M - 1) / TILE_M;

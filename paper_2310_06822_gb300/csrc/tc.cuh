@@ -8,7 +8,7 @@ struct TcModel {
     int infer_prec = 0, train_prec = 0;
     void *img = nullptr;     // device: packed operand images of every layer
     size_t img_bytes = 0;
-    float *scales = nullptr; // device: per-layer dequantisation scales (FP8)
+    float *scales = nullptr; // device: 1 / (power-of-two scale) of every FP8 weight row
     void *train_img = nullptr;   // device: BF16 weights for the tensor-core training step
     size_t train_img_bytes = 0;
     int *err = nullptr;      // device: status of the last bounded wait that gave up (0 = none)
@@ -20,6 +20,13 @@ size_t nb_split_smem_bytes(int H, int NH);
 nb_status nb_split_refresh(TcModel *tc, const MlpDesc &d, cudaStream_t s);
 nb_status nb_split_query(TcModel *tc, const MlpDesc &d, const float *q, int64_t n, TauF tau, float margin,
                          uint32_t *bits, float *logits, nb_query_stats *st, QueryWs ws, cudaStream_t s);
+
+// FP8 (E4M3) forward (tc_fp8.cu)
+size_t nb_fp8_img_bytes(int H, int NHH);
+size_t nb_fp8_smem_bytes(int H, int NHH);
+nb_status nb_fp8_refresh(TcModel *tc, const MlpDesc &d, cudaStream_t s);
+nb_status nb_fp8_query(TcModel *tc, const MlpDesc &d, const float *q, int64_t n, TauF tau, float margin,
+                       uint32_t *bits, float *logits, nb_query_stats *st, QueryWs ws, cudaStream_t s);
 
 // NB_OK, or the status a tensor-core kernel recorded since the last check (synchronous).
 nb_status nb_tc_check(TcModel *tc);

@@ -156,5 +156,32 @@ __device__ __forceinline__ void split_f16x2(float v0, float v1, uint32_t &hi, ui
     lo = pack_f16(v0 - h0, v1 - h1);
 }
 
+// D[tmem] (+)= A[tmem] x B[smem]^T, kind::f8f6f4 (formats in the instruction descriptor;
+// E4M3 x E4M3 here), FP32 accumulate; A row i in lane i, four 8-bit elements per 32-bit
+// column (element k in byte k mod 4), K along the columns
+__device__ __forceinline__ void mma_f8_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Instruction descriptor, kind::f8f6f4: D = F32, A = B = E4M3 (format code 0), both
+// K-major, M x N
+__host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N) {
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// four FP32 -> packed E4M3x4 (e0 in the lowest byte), round to nearest, saturating to
+// the largest finite E4M3 value (448)
+__device__ __forceinline__ uint32_t pack_e4m3x4(float e0, float e1, float e2, float e3) {
+    uint16_t lo, hi;
+    asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(lo) : "f"(e1), "f"(e0));
+    asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(hi) : "f"(e3), "f"(e2));
+    return (uint32_t)lo | ((uint32_t)hi << 16);
+}
 
 }  // namespace nbtc
