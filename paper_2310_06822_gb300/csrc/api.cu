@@ -56,13 +56,18 @@ TauF nb_tau_bracket(double tau) {
 
 void nb_fill_gamma(const int *widths, int L, GammaTab *gt) {
     // gamma_k = k u / (1 - k u), u = 2^-24, computed in double, then rounded up to float:
-    // k = fan-in + 8 roundings per term (FP32 stage), k = 4 fan-in + 4 (extended stage)
+    // k = fan-in + 8 roundings per term (FP32 stage), k = 3 fan-in + 4 (compensated stage),
+    // k = 4 fan-in + 4 (three-word stage)
     const double u = ldexp(1.0, -24);
     for (int l = 0; l < L; l++) {
         const double k = widths[l] + 8.0, gmm = k * u / (1.0 - k * u);
         float gf = (float)gmm;
         if ((double)gf < gmm) gf = nextafterf(gf, INFINITY);
         gt->g[l] = nextafterf(gf, INFINITY);
+        const double k3 = 3.0 * widths[l] + 4.0, cd2 = k3 * u / (1.0 - k3 * u);
+        float c2 = (float)cd2;
+        if ((double)c2 < cd2) c2 = nextafterf(c2, INFINITY);
+        gt->gd2[l] = nextafterf(c2, INFINITY);
         const double k4 = 4.0 * widths[l] + 4.0, cff = k4 * u / (1.0 - k4 * u);
         float cf = (float)cff;
         if ((double)cf < cff) cf = nextafterf(cf, INFINITY);

@@ -11,9 +11,11 @@
 // (at most fan-in + 8 roundings per term, any order), e_k the propagated bound of the
 // inputs; ReLU is 1-Lipschitz so e_n = B_n after it.  Every bound is accumulated with
 // upward rounding, so it only over-estimates.  One extra FMA per MAC.
-// Stage 2 (ff_kernel): the queries stage 1 leaves ambiguous are evaluated in
-// float-float arithmetic (error-free TwoProd / TwoSum transformations, Ogita, Rump &
-// Oishi 2005) with the analogous bound, whose rounding part is O(K^2 u^2).
+// Stage 2 (ff_kernel): the queries stage 1 leaves ambiguous are evaluated with
+// error-free transformations (TwoProd / TwoSum, Ogita, Rump & Oishi 2005) on activations
+// carried as float pairs, first as compensated dot products (2a, bound about
+// gamma_{3K} u |terms|), then, for the few still ambiguous, in three-word accumulation
+// (2b, bound about gamma_{4K} u^2 |terms|), each with its bound evaluated at run time.
 #include <math.h>
 
 #include "common.cuh"
@@ -268,6 +270,82 @@ __device__ __forceinline__ void ff_neuron(const float *__restrict__ Wr, float bv
     bound = __fmaf_ru(g4, A3, __fmaf_ru(2.f * U, __fadd_ru(fabsf(t4), fabsf(t3)), P));
 }
 
+// Compensated dot products (Dot2, Ogita, Rump & Oishi 2005) of the neurons nn0, nn0 + 32,
+// ..., nn0 + 32 (NB - 1) of one layer (those below N), on inputs given as float pairs
+// (h, l) carrying bounds e.  Per input: the product w h is split exactly (p + pq), p is
+// added to the running sum s by an error-free TwoSum (error er), and er, pq and w l are
+// accumulated in a second word c.  s plus the exact sum of the c terms equals
+// b + sum_k w (h_k + l_k), so the only roundings are the 3K additions into c:
+//     |hi + lo - exact| <= gamma_{3K} A + sum_k |w_k| e_k,
+// A = sum of the magnitudes of the c terms, both evaluated with upward rounding, and
+// (hi, lo) = TwoSum(s, c) holding s + c exactly.  About 15 operations per product, where
+// the three-word evaluation below takes about 40 and a bound near u^2 instead of u.
+template <int NB>
+__device__ __forceinline__ void dot2_core(const float *__restrict__ W, const float *__restrict__ bias, int K, int N,
+                                          int nn0, float g3, const float *h, const float *l, const float *e,
+                                          float (&hi)[NB], float (&lo)[NB], float (&bd)[NB]) {
+    float s[NB], c[NB], A[NB], P[NB];
+    const float *Wr[NB];
+#pragma unroll
+    for (int j = 0; j < NB; j++) {
+        const int nn = nn0 + 32 * j;
+        const bool ok = nn < N;
+        Wr[j] = W + (size_t)(ok ? nn : 0) * K;
+        s[j] = ok ? __ldg(bias + nn) : 0.f;
+        c[j] = 0.f;
+        A[j] = 0.f;
+        P[j] = 0.f;
+    }
+    for (int k = 0; k < K; k++) {
+        const float hk = h[k], lk = l[k], ek = e[k];
+#pragma unroll
+        for (int j = 0; j < NB; j++) {
+            const float w = __ldg(Wr[j] + k);
+            const float p = __fmul_rn(w, hk);
+            const float pq = fmaf(w, hk, -p);  // w hk = p + pq exactly
+            float t, er;
+            two_sum(s[j], p, t, er);
+            s[j] = t;
+            c[j] = __fadd_rn(__fadd_rn(c[j], er), pq);
+            c[j] = fmaf(w, lk, c[j]);
+            A[j] = __fmaf_ru(fabsf(w), fabsf(lk), __fadd_ru(A[j], __fadd_ru(fabsf(er), fabsf(pq))));
+            P[j] = __fmaf_ru(fabsf(w), ek, P[j]);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < NB; j++) {
+        two_sum(s[j], c[j], hi[j], lo[j]);
+        bd[j] = __fmaf_ru(g3, A[j], P[j]);
+    }
+}
+
+// relu(hi + lo) as a pair: |lo| is far below |hi| unless hi = 0, so the sign is hi's
+__device__ __forceinline__ void relu_pair(float hi, float lo, float &h2, float &l2) {
+    if (hi > 0.f) {
+        h2 = hi;
+        l2 = lo;
+    } else {
+        h2 = hi == 0.f ? fmaxf(lo, 0.f) : 0.f;
+        l2 = 0.f;
+    }
+}
+
+template <int NB>
+__device__ __forceinline__ void dot2_neurons_relu(const float *__restrict__ W, const float *__restrict__ bias, int K,
+                                                  int N, int nn0, float g3, const float *h, const float *l,
+                                                  const float *e, float *h2, float *l2, float *e2) {
+    float hi[NB], lo[NB], bd[NB];
+    dot2_core<NB>(W, bias, K, N, nn0, g3, h, l, e, hi, lo, bd);
+#pragma unroll
+    for (int j = 0; j < NB; j++) {
+        const int nn = nn0 + 32 * j;
+        if (nn < N) {
+            relu_pair(hi[j], lo[j], h2[nn], l2[nn]);
+            e2[nn] = bd[j];
+        }
+    }
+}
+
 // ff_neuron for the neurons nn0, nn0 + 32, ..., nn0 + 32 (NB - 1) of one layer (those
 // below N), their chains interleaved so that the dependent TwoSum sequences of different
 // neurons overlap; every neuron's arithmetic is exactly that of ff_neuron.  Writes
@@ -337,14 +415,19 @@ __device__ __forceinline__ void ff_neurons_relu(const float *__restrict__ W, con
     }
 }
 
-// One warp per query still ambiguous after stage 1.
+// One warp per query still ambiguous after stage 1.  STAGE 0: compensated (Dot2)
+// evaluation; queries it cannot decide are appended to (out_count, out_idx).  STAGE 1:
+// three-word evaluation; queries it cannot decide are decided inside (conservative) and
+// counted as unresolved.
 // Grouped form: when `offsets` is given, query i belongs to the object o with
 // offsets[o] <= i < offsets[o+1], whose parameters start at d.p + o * P and whose
 // threshold is taus[o].
+template <int STAGE>
 __global__ void __launch_bounds__(128) ff_kernel(MlpDesc d, GammaTab gt, const float *__restrict__ q, TauF tau0,
                                                  const unsigned *ff_count, const unsigned *ff_idx, uint32_t *bits,
                                                  nb_query_stats *st, const long long *offsets, int n_objects,
-                                                 long long P, const TauF *taus) {
+                                                 long long P, const TauF *taus, unsigned *out_count,
+                                                 unsigned *out_idx) {
     __shared__ float sh_[4][3][2][NB_MAXW];  // [warp][h,l,e][buffer][k]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned cnt = *ff_count;
@@ -375,8 +458,12 @@ __global__ void __launch_bounds__(128) ff_kernel(MlpDesc d, GammaTab gt, const f
         for (int ly = 0; ly < d.L - 1; ly++) {
             const int K = d.w[ly], N = d.w[ly + 1];
             const float *W = dd.p + dd.off[ly];
-            for (int nn0 = lane; nn0 < N; nn0 += 32 * 4)
-                ff_neurons_relu<4>(W, W + (size_t)N * K, K, N, nn0, gt.gff[ly], h, l, e, h2, l2, e2);
+            for (int nn0 = lane; nn0 < N; nn0 += 32 * 4) {
+                if (STAGE == 0)
+                    dot2_neurons_relu<4>(W, W + (size_t)N * K, K, N, nn0, gt.gd2[ly], h, l, e, h2, l2, e2);
+                else
+                    ff_neurons_relu<4>(W, W + (size_t)N * K, K, N, nn0, gt.gff[ly], h, l, e, h2, l2, e2);
+            }
             __syncwarp();
             float *tp = h;
             h = h2;
@@ -392,7 +479,15 @@ __global__ void __launch_bounds__(128) ff_kernel(MlpDesc d, GammaTab gt, const f
             const int K = d.w[d.L - 1];
             const float *W = dd.p + dd.off[d.L - 1];
             float zh, zl, B;
-            ff_neuron(W, __ldg(W + K), K, gt.gff[d.L - 1], h, l, e, zh, zl, B);
+            if (STAGE == 0) {
+                float hh[1], ll[1], bb[1];
+                dot2_core<1>(W, W + K, K, 1, 0, gt.gd2[d.L - 1], h, l, e, hh, ll, bb);
+                zh = hh[0];
+                zl = ll[0];
+                B = bb[0];
+            } else {
+                ff_neuron(W, __ldg(W + K), K, gt.gff[d.L - 1], h, l, e, zh, zl, B);
+            }
             // D = z - tau in float-float: (s, ee) = zh - tau_hi exactly, t = (zl - tau_lo) + ee
             float s, ee;
             two_sum(zh, -tau.hi, s, ee);
@@ -407,13 +502,18 @@ __global__ void __launch_bounds__(128) ff_kernel(MlpDesc d, GammaTab gt, const f
             } else if (__fadd_ru(v, M) < 0.f) {
                 dec = 0;
                 rff++;
+            } else if (STAGE == 0) {
+                out_idx[atomicAdd(out_count, 1u)] = i;  // the three-word stage settles this bit
+                dec = -1;
             } else {
                 dec = 1;  // unresolved: conservative
                 unres++;
             }
-            const unsigned bit = 1u << (i & 31);
-            const unsigned old = dec ? atomicOr(bits + (i >> 5), bit) : atomicAnd(bits + (i >> 5), ~bit);
-            dinside += dec - (int)((old & bit) != 0);
+            if (dec >= 0) {
+                const unsigned bit = 1u << (i & 31);
+                const unsigned old = dec ? atomicOr(bits + (i >> 5), bit) : atomicAnd(bits + (i >> 5), ~bit);
+                dinside += dec - (int)((old & bit) != 0);
+            }
         }
         __syncwarp();
     }
@@ -543,7 +643,14 @@ nb_status nb_launch_recheck(const MlpDesc &d, const GammaTab &gt, const float *q
     int64_t grid = num_sms() * (FF_WARPS_PER_SM / 4);
     if (grid > (n + 3) / 4) grid = (n + 3) / 4;
     if (grid < 1) grid = 1;
-    ff_kernel<<<(unsigned)grid, 128, 0, s>>>(d, gt, q, tau, ws.ff_count, ws.ff_idx, bits, st, nullptr, 0, 0, nullptr);
+    // stage 2a (Dot2) on the stage-1 leftovers; its own leftovers go to the flag list,
+    // free again once stage 1 has read it, and from there to stage 2b (three words)
+    NB_CUDA(cudaMemsetAsync(ws.flag_count, 0, sizeof(unsigned), s));
+    ff_kernel<0><<<(unsigned)grid, 128, 0, s>>>(d, gt, q, tau, ws.ff_count, ws.ff_idx, bits, st, nullptr, 0, 0,
+                                                nullptr, ws.flag_count, ws.flag_idx);
+    NB_CUDA(cudaGetLastError());
+    ff_kernel<1><<<(unsigned)grid, 128, 0, s>>>(d, gt, q, tau, ws.flag_count, ws.flag_idx, bits, st, nullptr, 0, 0,
+                                                nullptr, nullptr, nullptr);
     NB_CUDA(cudaGetLastError());
     return NB_OK;
 }
@@ -556,8 +663,12 @@ nb_status nb_launch_recheck_grouped(const MlpDesc &d, const GammaTab &gt, const 
     if (grid > (n + 3) / 4) grid = (n + 3) / 4;
     if (grid < 1) grid = 1;
     TauF none{};
-    ff_kernel<<<(unsigned)grid, 128, 0, s>>>(d, gt, q, none, ws.flag_count, ws.flag_idx, bits, st, offsets, n_objects,
-                                             P, taus);
+    NB_CUDA(cudaMemsetAsync(ws.ff_count, 0, sizeof(unsigned), s));
+    ff_kernel<0><<<(unsigned)grid, 128, 0, s>>>(d, gt, q, none, ws.flag_count, ws.flag_idx, bits, st, offsets,
+                                                n_objects, P, taus, ws.ff_count, ws.ff_idx);
+    NB_CUDA(cudaGetLastError());
+    ff_kernel<1><<<(unsigned)grid, 128, 0, s>>>(d, gt, q, none, ws.ff_count, ws.ff_idx, bits, st, offsets, n_objects,
+                                                P, taus, nullptr, nullptr);
     NB_CUDA(cudaGetLastError());
     return NB_OK;
 }

@@ -34,9 +34,11 @@ struct MlpDesc {
 
 // Rounding-error constants of the rigorous bounds, rounded up, one per layer:
 //   g[l]   = gamma_{K+8} = k u / (1 - k u), u = 2^-24, k = fan-in K + 8 (FP32 stage)
-//   gff[l] = gamma_{4K+4} (extended-precision stage)
+//   gd2[l] = gamma_{3K+4} (compensated stage)
+//   gff[l] = gamma_{4K+4} (three-word stage)
 struct GammaTab {
     float g[NB_MAXL];
+    float gd2[NB_MAXL];
     float gff[NB_MAXL];
 };
 
