@@ -101,6 +101,7 @@ struct nb_model {
     int64_t P = 0;
     int infer_prec = NB_F32, train_prec = NB_F32;
     float *params = nullptr, *adam_m = nullptr, *adam_v = nullptr, *grad = nullptr;
+    float *paramsT = nullptr;  // weights transposed, for the margin re-check and calibration
     int64_t step = 0;
     double tau = 0.0;
     float lr = 1e-3f, b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
@@ -122,6 +123,7 @@ static MlpDesc desc_of(const nb_model *m) {
         if (m->widths[l] > d.maxw) d.maxw = m->widths[l];
     }
     d.p = m->params;
+    d.pT = m->paramsT;
     return d;
 }
 
@@ -157,6 +159,7 @@ static void free_model(nb_model *m) {
     cudaFree(m->adam_m);
     cudaFree(m->adam_v);
     cudaFree(m->grad);
+    cudaFree(m->paramsT);
     cudaFree(m->ws);
     nb_tc_free(&m->tc);
     delete m;
@@ -188,12 +191,14 @@ extern "C" nb_status nb_model_create(const int32_t *widths, int32_t n_layers, in
     nb_fill_gamma(m->widths, n_layers, &m->gamma);
     const size_t pb = (size_t)m->P * sizeof(float);
     if (cudaMalloc(&m->params, pb) != cudaSuccess || cudaMalloc(&m->adam_m, pb) != cudaSuccess ||
-        cudaMalloc(&m->adam_v, pb) != cudaSuccess || cudaMalloc(&m->grad, pb) != cudaSuccess) {
+        cudaMalloc(&m->adam_v, pb) != cudaSuccess || cudaMalloc(&m->grad, pb) != cudaSuccess ||
+        cudaMalloc(&m->paramsT, pb) != cudaSuccess) {
         cudaGetLastError();
         free_model(m);
         return nb_fail(NB_ENOMEM, "nb_model_create: allocation failed");
     }
     cudaMemset(m->params, 0, pb);
+    cudaMemset(m->paramsT, 0, pb);
     cudaMemset(m->adam_m, 0, pb);
     cudaMemset(m->adam_v, 0, pb);
     cudaMemset(m->grad, 0, pb);
@@ -222,7 +227,10 @@ extern "C" nb_status nb_model_destroy(nb_model *m) {
 
 extern "C" int64_t nb_model_param_count(const nb_model *m) { return m ? m->P : -1; }
 
+// every copy derived from the FP32 master weights, after each change of them
 static nb_status refresh_lowp(nb_model *m, cudaStream_t s) {
+    const nb_status st = nb_launch_transpose(desc_of(m), m->paramsT, 1, m->P, s);
+    if (st != NB_OK) return st;
     if (m->infer_prec == NB_F32 && m->train_prec == NB_F32) return NB_OK;
     return nb_tc_refresh(&m->tc, desc_of(m), s);
 }

@@ -41,7 +41,7 @@ __device__ __forceinline__ unsigned long long ord_f64(double f) {
 
 // One hidden layer over a tile: values aout = relu(b + W ain) and bounds eout.
 template <int NJ, int MI>
-__device__ __forceinline__ void bound_layer_tile(const float *__restrict__ W, const float *__restrict__ b, int K,
+__device__ __forceinline__ void bound_layer_tile(const float *__restrict__ Wt, const float *__restrict__ b, int K,
                                                  int N, float g, const float *ain, const float *ein, float *aout,
                                                  float *eout, float *wt, int KP) {
     constexpr int WS = 16 * NJ + 1;
@@ -62,8 +62,8 @@ __device__ __forceinline__ void bound_layer_tile(const float *__restrict__ W, co
         const int kw = min(KC, K - kc);
         __syncthreads();
         for (int e = t; e < N * KC; e += blockDim.x) {
-            const int nn = e / KC, kk = e % KC;
-            wt[kk * WS + nn] = kk < kw ? __ldg(W + (size_t)nn * K + kc + kk) : 0.f;
+            const int kk = e / N, nn = e % N;
+            wt[kk * WS + nn] = kk < kw ? __ldg(Wt + (size_t)(kc + kk) * N + nn) : 0.f;
         }
         __syncthreads();
         for (int kk = 0; kk < kw; kk++) {
@@ -142,8 +142,8 @@ __global__ void __launch_bounds__(256) bound_tile_kernel(MlpDesc d, GammaTab gt,
         float *ain = a0, *ein = e0, *aout = a1, *eout = e1;
         for (int l = 0; l < d.L - 1; l++) {
             const int K = d.w[l], N = d.w[l + 1];
-            const float *W = d.p + d.off[l];
-            bound_layer_tile<NJ, MI>(W, W + (size_t)N * K, K, N, gt.g[l], ain, ein, aout, eout, wt, KP);
+            const float *Wt = d.pT + d.off[l];
+            bound_layer_tile<NJ, MI>(Wt, Wt + (size_t)N * K, K, N, gt.g[l], ain, ein, aout, eout, wt, KP);
             float *tp = ain;
             ain = aout;
             aout = tp;
@@ -238,11 +238,12 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
 // upward rounding at run time:
 //     gamma_{4K+4} A3 + 2u (|t4| + |t3|) + sum_k |W_k| e_k,
 // A3 = sum of the magnitudes of the terms added into s3, g4 = gamma_{4K+4}.
-__device__ __forceinline__ void ff_neuron(const float *__restrict__ Wr, float bv, int K, float g4, const float *h,
-                                          const float *l, const float *e, float &hi, float &lo, float &bound) {
+__device__ __forceinline__ void ff_neuron(const float *__restrict__ Wr, int stride, float bv, int K, float g4,
+                                          const float *h, const float *l, const float *e, float &hi, float &lo,
+                                          float &bound) {
     float s1 = bv, s2 = 0.f, s3 = 0.f, A3 = 0.f, P = 0.f;
     for (int k = 0; k < K; k++) {
-        const float w = __ldg(Wr + k), hk = h[k], lk = l[k];
+        const float w = __ldg(Wr + (size_t)k * stride), hk = h[k], lk = l[k];
         const float p = __fmul_rn(w, hk);
         const float pq = fmaf(w, hk, -p);  // w hk = p + pq exactly
         const float r = __fmul_rn(w, lk);
@@ -281,7 +282,7 @@ __device__ __forceinline__ void ff_neuron(const float *__restrict__ Wr, float bv
 // (hi, lo) = TwoSum(s, c) holding s + c exactly.  About 15 operations per product, where
 // the three-word evaluation below takes about 40 and a bound near u^2 instead of u.
 template <int NB>
-__device__ __forceinline__ void dot2_core(const float *__restrict__ W, const float *__restrict__ bias, int K, int N,
+__device__ __forceinline__ void dot2_core(const float *__restrict__ Wt, const float *__restrict__ bias, int K, int N,
                                           int nn0, float g3, const float *h, const float *l, const float *e,
                                           float (&hi)[NB], float (&lo)[NB], float (&bd)[NB]) {
     float s[NB], c[NB], A[NB], P[NB];
@@ -290,7 +291,7 @@ __device__ __forceinline__ void dot2_core(const float *__restrict__ W, const flo
     for (int j = 0; j < NB; j++) {
         const int nn = nn0 + 32 * j;
         const bool ok = nn < N;
-        Wr[j] = W + (size_t)(ok ? nn : 0) * K;
+        Wr[j] = Wt + (ok ? nn : 0);
         s[j] = ok ? __ldg(bias + nn) : 0.f;
         c[j] = 0.f;
         A[j] = 0.f;
@@ -300,7 +301,7 @@ __device__ __forceinline__ void dot2_core(const float *__restrict__ W, const flo
         const float hk = h[k], lk = l[k], ek = e[k];
 #pragma unroll
         for (int j = 0; j < NB; j++) {
-            const float w = __ldg(Wr[j] + k);
+            const float w = __ldg(Wr[j] + (size_t)k * N);
             const float p = __fmul_rn(w, hk);
             const float pq = fmaf(w, hk, -p);  // w hk = p + pq exactly
             float t, er;
@@ -331,11 +332,11 @@ __device__ __forceinline__ void relu_pair(float hi, float lo, float &h2, float &
 }
 
 template <int NB>
-__device__ __forceinline__ void dot2_neurons_relu(const float *__restrict__ W, const float *__restrict__ bias, int K,
+__device__ __forceinline__ void dot2_neurons_relu(const float *__restrict__ Wt, const float *__restrict__ bias, int K,
                                                   int N, int nn0, float g3, const float *h, const float *l,
                                                   const float *e, float *h2, float *l2, float *e2) {
     float hi[NB], lo[NB], bd[NB];
-    dot2_core<NB>(W, bias, K, N, nn0, g3, h, l, e, hi, lo, bd);
+    dot2_core<NB>(Wt, bias, K, N, nn0, g3, h, l, e, hi, lo, bd);
 #pragma unroll
     for (int j = 0; j < NB; j++) {
         const int nn = nn0 + 32 * j;
@@ -351,7 +352,7 @@ __device__ __forceinline__ void dot2_neurons_relu(const float *__restrict__ W, c
 // neurons overlap; every neuron's arithmetic is exactly that of ff_neuron.  Writes
 // relu(hi + lo) as a pair and the propagated bound.
 template <int NB>
-__device__ __forceinline__ void ff_neurons_relu(const float *__restrict__ W, const float *__restrict__ bias, int K,
+__device__ __forceinline__ void ff_neurons_relu(const float *__restrict__ Wt, const float *__restrict__ bias, int K,
                                                 int N, int nn0, float g4, const float *h, const float *l,
                                                 const float *e, float *h2, float *l2, float *e2) {
     float s1[NB], s2[NB], s3[NB], A3[NB], P[NB];
@@ -360,7 +361,7 @@ __device__ __forceinline__ void ff_neurons_relu(const float *__restrict__ W, con
     for (int j = 0; j < NB; j++) {
         const int nn = nn0 + 32 * j;
         const bool ok = nn < N;
-        Wr[j] = W + (size_t)(ok ? nn : 0) * K;
+        Wr[j] = Wt + (ok ? nn : 0);
         s1[j] = ok ? __ldg(bias + nn) : 0.f;
         s2[j] = 0.f;
         s3[j] = 0.f;
@@ -371,7 +372,7 @@ __device__ __forceinline__ void ff_neurons_relu(const float *__restrict__ W, con
         const float hk = h[k], lk = l[k], ek = e[k];
 #pragma unroll
         for (int j = 0; j < NB; j++) {
-            const float w = __ldg(Wr[j] + k);
+            const float w = __ldg(Wr[j] + (size_t)k * N);
             const float p = __fmul_rn(w, hk);
             const float pq = fmaf(w, hk, -p);
             const float r = __fmul_rn(w, lk);
@@ -420,7 +421,7 @@ __device__ __forceinline__ void ff_neurons_relu(const float *__restrict__ W, con
 // three-word evaluation; queries it cannot decide are decided inside (conservative) and
 // counted as unresolved.
 // Grouped form: when `offsets` is given, query i belongs to the object o with
-// offsets[o] <= i < offsets[o+1], whose parameters start at d.p + o * P and whose
+// offsets[o] <= i < offsets[o+1], whose parameters start at d.pT + o * P and whose
 // threshold is taus[o].
 template <int STAGE>
 __global__ void __launch_bounds__(128) ff_kernel(MlpDesc d, GammaTab gt, const float *__restrict__ q, TauF tau0,
@@ -443,7 +444,7 @@ __global__ void __launch_bounds__(128) ff_kernel(MlpDesc d, GammaTab gt, const f
                 const int mid = (lo_o + hi_o + 1) >> 1;
                 if (offsets[mid] <= (long long)i) lo_o = mid; else hi_o = mid - 1;
             }
-            dd.p = d.p + (size_t)lo_o * P;
+            dd.pT = d.pT + (size_t)lo_o * P;
             tau = taus[lo_o];
         }
         float *h = sh_[warp][0][0], *l = sh_[warp][1][0], *e = sh_[warp][2][0];
@@ -457,7 +458,7 @@ __global__ void __launch_bounds__(128) ff_kernel(MlpDesc d, GammaTab gt, const f
         __syncwarp();
         for (int ly = 0; ly < d.L - 1; ly++) {
             const int K = d.w[ly], N = d.w[ly + 1];
-            const float *W = dd.p + dd.off[ly];
+            const float *W = dd.pT + dd.off[ly];  // W_l transposed: [K][N]
             for (int nn0 = lane; nn0 < N; nn0 += 32 * 4) {
                 if (STAGE == 0)
                     dot2_neurons_relu<4>(W, W + (size_t)N * K, K, N, nn0, gt.gd2[ly], h, l, e, h2, l2, e2);
@@ -477,7 +478,7 @@ __global__ void __launch_bounds__(128) ff_kernel(MlpDesc d, GammaTab gt, const f
         }
         if (lane == 0) {
             const int K = d.w[d.L - 1];
-            const float *W = dd.p + dd.off[d.L - 1];
+            const float *W = dd.pT + dd.off[d.L - 1];
             float zh, zl, B;
             if (STAGE == 0) {
                 float hh[1], ll[1], bb[1];
@@ -486,7 +487,7 @@ __global__ void __launch_bounds__(128) ff_kernel(MlpDesc d, GammaTab gt, const f
                 zl = ll[0];
                 B = bb[0];
             } else {
-                ff_neuron(W, __ldg(W + K), K, gt.gff[d.L - 1], h, l, e, zh, zl, B);
+                ff_neuron(W, 1, __ldg(W + K), K, gt.gff[d.L - 1], h, l, e, zh, zl, B);
             }
             // D = z - tau in float-float: (s, ee) = zh - tau_hi exactly, t = (zl - tau_lo) + ee
             float s, ee;
@@ -560,10 +561,10 @@ __global__ void __launch_bounds__(256) calib_f64_kernel(MlpDesc d, const float *
         __syncwarp();
         for (int l = 0; l < d.L - 1; l++) {
             const int K = d.w[l], N = d.w[l + 1];
-            const float *W = d.p + d.off[l];
+            const float *Wt = d.pT + d.off[l];
             for (int nn = lane; nn < N; nn += 32) {
-                double s = (double)__ldg(W + (size_t)N * K + nn);
-                for (int k = 0; k < K; k++) s = fma((double)__ldg(W + (size_t)nn * K + k), a[k], s);
+                double s = (double)__ldg(Wt + (size_t)N * K + nn);
+                for (int k = 0; k < K; k++) s = fma((double)__ldg(Wt + (size_t)k * N + nn), a[k], s);
                 a2[nn] = s > 0.0 ? s : 0.0;
             }
             __syncwarp();
@@ -582,6 +583,24 @@ __global__ void __launch_bounds__(256) calib_f64_kernel(MlpDesc d, const float *
         if (lane == 0) best = min(best, (s == s) ? ord_f64(s) : 0ull);  // NaN sorts lowest
     }
     if (lane == 0 && best != ~0ull) atomicMin(zmin_bits, best);
+}
+
+// pT[o][.] <- p[o][.] with W_l[n][k] moved to [k][n]; biases copied in place
+__global__ void transpose_params_kernel(MlpDesc d, float *__restrict__ pT, long long P) {
+    const float *p = d.p + (size_t)blockIdx.y * P;
+    float *o = pT + (size_t)blockIdx.y * P;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < P; e += (long long)gridDim.x * blockDim.x) {
+        int l = 0;
+        while (l + 1 < d.L && e >= d.off[l + 1]) l++;
+        const long long local = e - d.off[l];
+        const int K = d.w[l], N = d.w[l + 1];
+        if (local < (long long)N * K) {
+            const long long nn = local / K, k = local % K;
+            o[d.off[l] + k * N + nn] = p[e];
+        } else {
+            o[e] = p[e];
+        }
+    }
 }
 
 int num_sms() {
@@ -633,6 +652,14 @@ nb_status tile_dispatch(const MlpDesc &d, const GammaTab &gt, const float *q, Ta
 }
 
 }  // namespace
+
+nb_status nb_launch_transpose(const MlpDesc &d, float *pT, int n_objects, long long P, cudaStream_t s) {
+    const long long blocks = (P + 255) / 256;
+    transpose_params_kernel<<<dim3((unsigned)(blocks < 1024 ? blocks : 1024), (unsigned)n_objects), 256, 0, s>>>(
+        d, pT, P);
+    NB_CUDA(cudaGetLastError());
+    return NB_OK;
+}
 
 nb_status nb_launch_recheck(const MlpDesc &d, const GammaTab &gt, const float *q, TauF tau, uint32_t *bits,
                             nb_query_stats *st, QueryWs ws, int64_t n, cudaStream_t s) {

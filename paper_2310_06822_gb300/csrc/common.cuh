@@ -30,6 +30,7 @@ struct MlpDesc {
     int off[NB_MAXL];        // offset of W_l in the flat parameter array; b_l follows W_l
     int maxw;                // max(w[0..L-1])
     const float *p;          // device FP32 master parameters
+    const float *pT;         // the same with every W_l stored transposed ([K][N]), biases as in p
 };
 
 // Rounding-error constants of the rigorous bounds, rounded up, one per layer:
@@ -67,6 +68,8 @@ struct QueryWs {
 
 nb_status nb_launch_fwd_f32(const MlpDesc &d, const float *q, int64_t n, TauF tau, float margin,
                             uint32_t *bits, float *logits, nb_query_stats *st, QueryWs ws, cudaStream_t s);
+// pT <- p with every weight matrix transposed, for n_objects parameter sets P apart
+nb_status nb_launch_transpose(const MlpDesc &d, float *pT, int n_objects, long long P, cudaStream_t s);
 nb_status nb_launch_recheck(const MlpDesc &d, const GammaTab &gt, const float *q, TauF tau, uint32_t *bits,
                             nb_query_stats *st, QueryWs ws, int64_t n, cudaStream_t s);
 

@@ -222,6 +222,7 @@ void free_group(nb_group *g) {
     cudaFree(g->m);
     cudaFree(g->v);
     cudaFree(g->grad);
+    cudaFree(g->paramsT);
     cudaFree(g->d_tau);
     cudaFree(g->ws);
     cudaFree(g->sched_alpha);
@@ -251,6 +252,7 @@ MlpDesc nb_group_desc(const nb_group *g) {
         if (g->widths[l] > d.maxw) d.maxw = g->widths[l];
     }
     d.p = g->params;
+    d.pT = g->paramsT;
     return d;
 }
 
@@ -342,6 +344,7 @@ extern "C" nb_status nb_group_create(const int32_t *widths, int32_t n_layers, in
     const size_t pb = (size_t)g->P * n_objects * sizeof(float);
     if (cudaMalloc(&g->params, pb) != cudaSuccess || cudaMalloc(&g->m, pb) != cudaSuccess ||
         cudaMalloc(&g->v, pb) != cudaSuccess || cudaMalloc(&g->grad, pb) != cudaSuccess ||
+        cudaMalloc(&g->paramsT, pb) != cudaSuccess ||
         cudaMalloc(&g->d_tau, sizeof(TauF) * n_objects) != cudaSuccess || cudaMalloc(&g->d_step, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         free_group(g);
@@ -351,6 +354,7 @@ extern "C" nb_status nb_group_create(const int32_t *widths, int32_t n_layers, in
     cudaMemset(g->m, 0, pb);
     cudaMemset(g->v, 0, pb);
     cudaMemset(g->grad, 0, pb);
+    cudaMemset(g->paramsT, 0, pb);
     cudaMemset(g->d_step, 0, sizeof(int));
     if (upload_tau(g) != NB_OK) {
         free_group(g);
@@ -382,6 +386,8 @@ extern "C" nb_status nb_group_destroy(nb_group *g) {
 extern "C" int64_t nb_group_param_count(const nb_group *g) { return g ? g->P : -1; }
 
 static nb_status group_refresh(nb_group *g, cudaStream_t s) {
+    const nb_status ts = nb_launch_transpose(nb_group_desc(g), g->paramsT, g->n_objects, g->P, s);
+    if (ts != NB_OK) return ts;
     if (g->train_prec == NB_BF16) {
         const nb_status st = nb_train_bf16_group_refresh(&g->tc, nb_group_desc(g), g->n_objects, s);
         if (st != NB_OK) return st;
@@ -593,6 +599,7 @@ extern "C" nb_status nb_calibrate_grouped(nb_group *g, const nb_plan *pl, const 
         double tau = INFINITY;
         if (r1 > r0) {
             d.p = g->params + (size_t)o * g->P;
+            d.pT = g->paramsT + (size_t)o * g->P;
             st = nb_launch_calibrate(d, g->gamma, q, label_bits, r0, r1, ws, s);
             if (st != NB_OK) return st;
             unsigned long long zb = 0;

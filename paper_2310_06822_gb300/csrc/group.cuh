@@ -33,6 +33,7 @@ struct nb_group {
     int64_t P = 0;
     int infer_prec = NB_F32, train_prec = NB_F32;
     float *params = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;  // [n_objects][P]
+    float *paramsT = nullptr;            // [n_objects][P], weights transposed (re-check)
     std::vector<double> tau;
     TauF *d_tau = nullptr;               // device [n_objects]
     GammaTab gamma{};

@@ -12,9 +12,9 @@
 //   tensor memory  per tile slot: the FP32 accumulator (H columns) and the next layer's
 //                  activations as FP16 hi and lo halves (H/2 + H/2 columns), which the
 //                  MMA reads directly as its A operand -- activations never leave the SM.
-// Warp roles as in the BF16 kernel: warps 0-3 and 4-7 are the epilogue groups of tile
-// slots 0 and 1 (one thread per query row = TMEM lane), warp 8 allocates TMEM, loads
-// the weights and issues the MMAs.  Layer 0 takes the input split the same way,
+// Warp roles: two tile slots, each with its epilogue warps (one thread per query row =
+// TMEM lane; the single-model kernel splits every row's columns between two warps), and
+// one warp that allocates TMEM, loads the weights and issues the MMAs.  Layer 0 takes the input split the same way,
 // A0 = [x_hi | x_lo | x_hi | 0] against B0 = [W_hi | W_hi | W_lo | 0] (K = 64).
 // All waits are bounded; on expiry the kernel records NB_ETIMEOUT, drains the tensor
 // pipe and frees TMEM before returning.
@@ -28,8 +28,6 @@ namespace {
 using namespace nbtc;
 
 constexpr int TILE_M = 128;
-constexpr int NEPI = 8;
-constexpr int THREADS = (NEPI + 1) * 32;
 constexpr unsigned SPIN_LIMIT = 1u << 22;
 constexpr unsigned FULL = 0xffffffffu;
 
@@ -68,17 +66,49 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, Ctl *ct
     return __shfl_sync(FULL, ok, 0) != 0;
 }
 
+// Single-model kernel: 16 epilogue warps, 8 per tile slot; warps w and w + 4 of a slot
+// share the TMEM lanes of quarter w mod 4 and take one half of the columns each, so a
+// layer's epilogue (TMEM load, bias, ReLU, hi/lo split, TMEM store) takes half as long
+// and the tensor pipe waits less between layers.  The two halves of a row exchange their
+// partial head sums through shared memory under a bounded mbarrier handshake.
+constexpr int SEPI = 16;
+constexpr int STHREADS = (SEPI + 1) * 32;
+
+struct SCtl {
+    uint64_t wbar, aready[2], accfull[2], drain;
+    uint64_t pair[8];  // head-sum handshake of the two warps of each (slot, lane quarter)
+    uint32_t tmem;
+    int abort;
+};
+
+__device__ bool swait(uint32_t bar, uint32_t parity, SCtl *ctl, int *err) {
+    for (unsigned i = 0; i < SPIN_LIMIT; i++) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*(volatile int *)&ctl->abort) return false;
+    }
+    *(volatile int *)&ctl->abort = 1;
+    atomicExch(err, NB_ETIMEOUT);
+    return false;
+}
+__device__ __forceinline__ bool swarp_wait(uint32_t bar, uint32_t parity, SCtl *ctl, int *err) {
+    int ok = 1;
+    if ((threadIdx.x & 31) == 0) ok = swait(bar, parity, ctl, err) ? 1 : 0;
+    return __shfl_sync(FULL, ok, 0) != 0;
+}
+
 template <int H>
-__global__ void __launch_bounds__(THREADS, 1)
+__global__ void __launch_bounds__(STHREADS, 1)
     fwd_split_kernel(SplitDesc d, const float *__restrict__ q, long long n, TauF tau, float margin,
                      uint32_t *__restrict__ bits, float *__restrict__ logits, nb_query_stats *st,
                      unsigned *flag_count, unsigned *flag_idx, int *err) {
     constexpr uint32_t SLOT_COLS = 2 * H;  // accumulator H + activations H/2 hi + H/2 lo
+    constexpr int HALF = H / 2;            // columns (neurons) per epilogue warp
     extern __shared__ uint8_t smem_raw[];
-    Ctl *ctl = reinterpret_cast<Ctl *>(smem_raw);
+    SCtl *ctl = reinterpret_cast<SCtl *>(smem_raw);
     uint8_t *Wimg = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023) + 1024;
     float *bias = reinterpret_cast<float *>(Wimg + d.img_bytes);
     float *head = bias + d.NH * H;
+    float *xbuf = head + H + 4;  // [16 warps][32 lanes] partial head sums
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long ntiles = (n + TILE_M - 1) / TILE_M;
@@ -88,21 +118,22 @@ __global__ void __launch_bounds__(THREADS, 1)
 
     if (threadIdx.x == 0) {
         mbar_init(bar_w, 1);
-        mbar_init(bar_ar[0], 4);
-        mbar_init(bar_ar[1], 4);
+        mbar_init(bar_ar[0], 8);
+        mbar_init(bar_ar[1], 8);
         mbar_init(bar_af[0], 1);
         mbar_init(bar_af[1], 1);
         mbar_init(bar_drain, 1);
+        for (int i = 0; i < 8; i++) mbar_init(smem_u32(&ctl->pair[i]), 64);
         ctl->abort = 0;
         fence_mbar_init();
     }
-    for (int i = threadIdx.x; i < d.NH * H; i += THREADS) {
+    for (int i = threadIdx.x; i < d.NH * H; i += STHREADS) {
         const int l = i / H, j = i % H;
         const int K = l == 0 ? d.in : H;
         bias[i] = d.p[d.off[l] + H * K + j];
     }
-    for (int i = threadIdx.x; i <= H; i += THREADS) head[i] = d.p[d.off[d.NH] + i];
-    if (warp == NEPI) {
+    for (int i = threadIdx.x; i <= H; i += STHREADS) head[i] = d.p[d.off[d.NH] + i];
+    if (warp == SEPI) {
         tmem_alloc(smem_u32(&ctl->tmem), 2 * SLOT_COLS);
         tmem_relinquish();
     }
@@ -111,12 +142,12 @@ __global__ void __launch_bounds__(THREADS, 1)
     tc_fence_after();
     const uint32_t tmem = ctl->tmem;
 
-    if (warp == NEPI) {
+    if (warp == SEPI) {
         if (lane == 0) {
             mbar_expect_tx(bar_w, d.img_bytes);
             for (uint32_t o = 0; o < d.img_bytes; o += 16384)
                 bulk_g2s(smem_u32(Wimg) + o, d.img + o, min(16384u, d.img_bytes - o), bar_w);
-            bool ok = wait_bounded(bar_w, 0, ctl, err);
+            bool ok = swait(bar_w, 0, ctl, err);
             uint32_t ph[2] = {0, 0};
             constexpr uint32_t idesc = idesc_f16(TILE_M, H);
             const uint32_t wbase = smem_u32(Wimg);
@@ -127,7 +158,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 for (int l = 0; l < d.NH && ok; l++)
                     for (int s = 0; s < 2 && ok; s++) {
                         if (!has[s]) continue;
-                        ok = wait_bounded(bar_ar[s], ph[s], ctl, err);
+                        ok = swait(bar_ar[s], ph[s], ctl, err);
                         ph[s] ^= 1;
                         if (!ok) break;
                         tc_fence_after();
@@ -151,20 +182,22 @@ __global__ void __launch_bounds__(THREADS, 1)
                     }
             }
             mma_commit(bar_drain);
-            wait_bounded(bar_drain, 0, ctl, err);
+            swait(bar_drain, 0, ctl, err);
             if (!ok) *(volatile int *)&ctl->abort = 1;
         }
         __syncwarp();
     } else {
-        const int s = warp >> 2, wq = warp & 3;
+        const int s = warp >> 3, ws = warp & 7, wq = ws & 3, hf = ws >> 2;
         const int r = wq * 32 + lane;
+        const int c0 = hf * HALF;  // first neuron of this warp
         const uint32_t trow = tmem + ((uint32_t)(wq * 32) << 16) + s * SLOT_COLS;
-        const uint32_t tD = trow, tAhi = trow + H, tAlo = trow + H + H / 2;
-        uint32_t ph = 0;
+        const uint32_t tD = trow + c0, tAhi = trow + H, tAlo = trow + H + H / 2;
+        const uint32_t bar_pair = smem_u32(&ctl->pair[s * 4 + wq]);
+        uint32_t ph = 0, pp = 0;
         unsigned long long c_in = 0, c_flag = 0, c_nf = 0;
         const int in = d.in;
         float x[16];
-        {
+        if (hf == 0) {
             const long long tile0 = blockIdx.x + (long long)s * gridDim.x;
             const long long row0 = tile0 * TILE_M + r;
 #pragma unroll
@@ -175,7 +208,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             if (tile >= ntiles) break;
             const long long row = tile * TILE_M + r;
             const bool valid = row < n;
-            {
+            if (hf == 0) {
                 // A0 = [x_hi | x_lo | x_hi | 0], 16 FP16 each, two per 32-bit column
                 uint32_t w0[16], w1[16];
 #pragma unroll
@@ -194,7 +227,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(bar_ar[s]);
-            {
+            if (hf == 0) {
                 // prefetch the next tile's rows while this tile runs through the layers
                 const long long nrow = (tile + 2 * (long long)gridDim.x) * TILE_M + r;
 #pragma unroll
@@ -203,14 +236,14 @@ __global__ void __launch_bounds__(THREADS, 1)
             bool ok = true;
             float z = 0.f;
             for (int l = 0; l < d.NH; l++) {
-                ok = warp_wait(bar_af[s], ph, ctl, err);
+                ok = swarp_wait(bar_af[s], ph, ctl, err);
                 ph ^= 1;
                 if (!ok) break;
                 tc_fence_after();
-                const float *b = bias + l * H;
+                const float *b = bias + l * H + c0;
                 if (l < d.NH - 1) {
 #pragma unroll
-                    for (int c = 0; c < H / 32; c++) {
+                    for (int c = 0; c < HALF / 32; c++) {
                         float v[32];
                         tmem_ld32(tD + c * 32, v);
                         tmem_ld_wait();
@@ -221,58 +254,70 @@ __global__ void __launch_bounds__(THREADS, 1)
                             const float a1 = fmaxf(v[2 * e + 1] + b[c * 32 + 2 * e + 1], 0.f);
                             split_f16x2(a0, a1, hi[e], lo[e]);
                         }
-                        tmem_st16(tAhi + c * 16, hi);
-                        tmem_st16(tAlo + c * 16, lo);
+                        tmem_st16(tAhi + c0 / 2 + c * 16, hi);
+                        tmem_st16(tAlo + c0 / 2 + c * 16, lo);
                     }
                     tmem_st_wait();
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(bar_ar[s]);
                 } else {
+                    float zp = 0.f;
 #pragma unroll
-                    for (int c = 0; c < H / 32; c++) {
+                    for (int c = 0; c < HALF / 32; c++) {
                         float v[32];
                         tmem_ld32(tD + c * 32, v);
                         tmem_ld_wait();
 #pragma unroll
-                        for (int e = 0; e < 32; e++) z = fmaf(head[c * 32 + e], fmaxf(v[e] + b[c * 32 + e], 0.f), z);
+                        for (int e = 0; e < 32; e++)
+                            zp = fmaf(head[c0 + c * 32 + e], fmaxf(v[e] + b[c * 32 + e], 0.f), zp);
                     }
                     tc_fence_before();
-                    z += head[H];
+                    // exchange the partial sums with the other half of the row
+                    xbuf[warp * 32 + lane] = zp;
+                    mbar_arrive(bar_pair);
+                    ok = swait(bar_pair, pp, ctl, err);
+                    pp ^= 1;
+                    const float zo = xbuf[(warp ^ 4) * 32 + lane];
+                    ok = __all_sync(FULL, ok);
+                    if (!ok) break;
+                    z = (hf == 0 ? zp + zo : zo + zp) + head[H];
                 }
             }
             if (!ok) break;
-            const bool fin = isfinite(z);
-            const bool inside = valid && fin && z >= tau.up;
-            // a non-finite fast logit (e.g. an FP16 overflow) goes to the FP32 re-check
-            const bool flag =
-                valid && (!fin || fabsf(z - tau.up) < margin || (z >= tau.dn && z < tau.up));
-            const unsigned bi = __ballot_sync(FULL, inside);
-            const unsigned bf = __ballot_sync(FULL, flag);
-            const unsigned bn = __ballot_sync(FULL, valid && !fin);
-            const long long wrow = tile * TILE_M + wq * 32;
-            if (lane == 0 && wrow < n) bits[wrow >> 5] = bi;
-            if (valid && logits) logits[row] = z;
-            if (bf) {
-                unsigned pos = 0;
-                if (lane == 0) pos = atomicAdd(flag_count, (unsigned)__popc(bf));
-                pos = __shfl_sync(FULL, pos, 0);
-                if (flag) flag_idx[pos + __popc(bf & ((1u << lane) - 1u))] = (unsigned)row;
-            }
-            if (lane == 0) {
-                c_in += __popc(bi);
-                c_flag += __popc(bf);
-                c_nf += __popc(bn);
+            if (hf == 0) {
+                const bool fin = isfinite(z);
+                const bool inside = valid && fin && z >= tau.up;
+                // a non-finite fast logit (e.g. an FP16 overflow) goes to the FP32 re-check
+                const bool flag =
+                    valid && (!fin || fabsf(z - tau.up) < margin || (z >= tau.dn && z < tau.up));
+                const unsigned bi = __ballot_sync(FULL, inside);
+                const unsigned bf = __ballot_sync(FULL, flag);
+                const unsigned bn = __ballot_sync(FULL, valid && !fin);
+                const long long wrow = tile * TILE_M + wq * 32;
+                if (lane == 0 && wrow < n) bits[wrow >> 5] = bi;
+                if (valid && logits) logits[row] = z;
+                if (bf) {
+                    unsigned pos = 0;
+                    if (lane == 0) pos = atomicAdd(flag_count, (unsigned)__popc(bf));
+                    pos = __shfl_sync(FULL, pos, 0);
+                    if (flag) flag_idx[pos + __popc(bf & ((1u << lane) - 1u))] = (unsigned)row;
+                }
+                if (lane == 0) {
+                    c_in += __popc(bi);
+                    c_flag += __popc(bf);
+                    c_nf += __popc(bn);
+                }
             }
         }
-        if (st && lane == 0) {
+        if (st && lane == 0 && hf == 0) {
             if (c_in) atomicAdd(&st->n_inside, c_in);
             if (c_flag) atomicAdd(&st->n_flagged, c_flag);
             if (c_nf) atomicAdd(&st->n_nonfinite, c_nf);
         }
     }
     __syncthreads();
-    if (warp == NEPI) {
+    if (warp == SEPI) {
         tc_fence_after();
         tmem_dealloc(tmem, 2 * SLOT_COLS);
     }
@@ -354,7 +399,7 @@ int num_sms() {
 size_t nb_split_img_bytes(int H, int NH) { return split_off(H, NH); }
 
 size_t nb_split_smem_bytes(int H, int NH) {
-    return 2048 + nb_split_img_bytes(H, NH) + (size_t)(NH * H + H + 4) * sizeof(float);
+    return 2048 + nb_split_img_bytes(H, NH) + (size_t)(NH * H + H + 4 + SEPI * 32) * sizeof(float);
 }
 
 nb_status nb_split_refresh(TcModel *tc, const MlpDesc &d, cudaStream_t s) {
@@ -375,11 +420,11 @@ nb_status nb_split_query(TcModel *tc, const MlpDesc &d, const float *q, int64_t 
     if (grid < 1) grid = 1;
     if (t.H == 128) {
         NB_CUDA(cudaFuncSetAttribute(fwd_split_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        fwd_split_kernel<128><<<(unsigned)grid, THREADS, smem, s>>>(t, q, (long long)n, tau, margin, bits, logits,
+        fwd_split_kernel<128><<<(unsigned)grid, STHREADS, smem, s>>>(t, q, (long long)n, tau, margin, bits, logits,
                                                                     st, ws.flag_count, ws.flag_idx, tc->err);
     } else {
         NB_CUDA(cudaFuncSetAttribute(fwd_split_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        fwd_split_kernel<64><<<(unsigned)grid, THREADS, smem, s>>>(t, q, (long long)n, tau, margin, bits, logits, st,
+        fwd_split_kernel<64><<<(unsigned)grid, STHREADS, smem, s>>>(t, q, (long long)n, tau, margin, bits, logits, st,
                                                                    ws.flag_count, ws.flag_idx, tc->err);
     }
     NB_CUDA(cudaGetLastError());
@@ -398,6 +443,7 @@ namespace {
 
 struct GCtl {
     uint64_t wbar, aready[2], accfull[2], drain, item_ready, item_done;
+    uint64_t pair[8];  // head-sum handshake of the two warps of each (slot, lane quarter)
     uint32_t tmem;
     int abort;
 };
@@ -418,17 +464,19 @@ __device__ __forceinline__ bool gwarp_wait(uint32_t bar, uint32_t parity, GCtl *
 }
 
 template <int H>
-__global__ void __launch_bounds__(THREADS, 1)
+__global__ void __launch_bounds__(STHREADS, 1)
     fwd_split_group_kernel(SplitDesc d, long long P, const PlanItem *__restrict__ items, int n_items,
                            const TauF *__restrict__ taus, const float *__restrict__ q, float margin,
                            uint32_t *__restrict__ bits, float *__restrict__ logits, nb_query_stats *st,
                            unsigned *flag_count, unsigned *flag_idx, int *err) {
     constexpr uint32_t SLOT_COLS = 2 * H;
+    constexpr int HALF = H / 2;
     extern __shared__ uint8_t smem_raw[];
     GCtl *ctl = reinterpret_cast<GCtl *>(smem_raw);
     uint8_t *Wimg = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023) + 1024;
     float *bias = reinterpret_cast<float *>(Wimg + d.img_bytes);
     float *head = bias + d.NH * H;
+    float *xbuf = head + H + 4;  // [16 warps][32 lanes] partial head sums
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t bar_w = smem_u32(&ctl->wbar), bar_drain = smem_u32(&ctl->drain);
@@ -437,17 +485,18 @@ __global__ void __launch_bounds__(THREADS, 1)
     const uint32_t bar_af[2] = {smem_u32(&ctl->accfull[0]), smem_u32(&ctl->accfull[1])};
     if (threadIdx.x == 0) {
         mbar_init(bar_w, 1);
-        mbar_init(bar_ar[0], 4);
-        mbar_init(bar_ar[1], 4);
+        mbar_init(bar_ar[0], 8);
+        mbar_init(bar_ar[1], 8);
         mbar_init(bar_af[0], 1);
         mbar_init(bar_af[1], 1);
         mbar_init(bar_drain, 1);
         mbar_init(bar_ready, 1);
-        mbar_init(bar_done, NEPI);
+        mbar_init(bar_done, SEPI);
+        for (int i = 0; i < 8; i++) mbar_init(smem_u32(&ctl->pair[i]), 64);
         ctl->abort = 0;
         fence_mbar_init();
     }
-    if (warp == NEPI) {
+    if (warp == SEPI) {
         tmem_alloc(smem_u32(&ctl->tmem), 2 * SLOT_COLS);
         tmem_relinquish();
     }
@@ -456,7 +505,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     tc_fence_after();
     const uint32_t tmem = ctl->tmem;
 
-    if (warp == NEPI) {
+    if (warp == SEPI) {
         uint32_t ph_ar[2] = {0, 0}, ph_w = 0, ph_done = 0, ph_drain = 0;
         int cur_obj = -1;
         bool ok = true;
@@ -538,12 +587,14 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         __syncwarp();
     } else {
-        const int s = warp >> 2, wq = warp & 3;
+        const int s = warp >> 3, ws = warp & 7, wq = ws & 3, hf = ws >> 2;
         const int r = wq * 32 + lane;
+        const int c0 = hf * HALF;  // first neuron of this warp
         const uint32_t trow = tmem + ((uint32_t)(wq * 32) << 16) + s * SLOT_COLS;
-        const uint32_t tD = trow, tAhi = trow + H, tAlo = trow + H + H / 2;
+        const uint32_t tD = trow + c0, tAhi = trow + H, tAlo = trow + H + H / 2;
+        const uint32_t bar_pair = smem_u32(&ctl->pair[s * 4 + wq]);
         const int in = d.in;
-        uint32_t ph_acc = 0, ph_ready = 0;
+        uint32_t ph_acc = 0, ph_ready = 0, pp = 0;
         unsigned long long c_in = 0, c_flag = 0, c_nf = 0;
         bool ok = true;
         for (int k = blockIdx.x; ok && k < n_items; k += gridDim.x) {
@@ -554,7 +605,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             const TauF tau = taus[it.obj];
             const long long nt = (it.row1 - it.row0 + TILE_M - 1) / TILE_M;
             float x[16];
-            {
+            if (hf == 0) {
                 const long long row0 = it.row0 + (long long)s * TILE_M + r;
 #pragma unroll
                 for (int kk = 0; kk < 16; kk++) x[kk] = (row0 < it.row1 && kk < in) ? __ldg(q + row0 * in + kk) : 0.f;
@@ -563,7 +614,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const long long trow0 = it.row0 + (2 * tp + s) * TILE_M;
                 const long long row = trow0 + r;
                 const bool valid = row < it.row1;
-                {
+                if (hf == 0) {
                     uint32_t w0[16], w1[16];
 #pragma unroll
                     for (int kk = 0; kk < 8; kk++) {
@@ -581,7 +632,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(bar_ar[s]);
-                {
+                if (hf == 0) {
                     const long long nrow = trow0 + 2 * TILE_M + r;
 #pragma unroll
                     for (int kk = 0; kk < 16; kk++)
@@ -593,10 +644,10 @@ __global__ void __launch_bounds__(THREADS, 1)
                     ph_acc ^= 1;
                     if (!ok) break;
                     tc_fence_after();
-                    const float *b = bias + l * H;
+                    const float *b = bias + l * H + c0;
                     if (l < d.NH - 1) {
 #pragma unroll
-                        for (int c = 0; c < H / 32; c++) {
+                        for (int c = 0; c < HALF / 32; c++) {
                             float v[32];
                             tmem_ld32(tD + c * 32, v);
                             tmem_ld_wait();
@@ -607,28 +658,38 @@ __global__ void __launch_bounds__(THREADS, 1)
                                 const float a1 = fmaxf(v[2 * e + 1] + b[c * 32 + 2 * e + 1], 0.f);
                                 split_f16x2(a0, a1, hi[e], lo[e]);
                             }
-                            tmem_st16(tAhi + c * 16, hi);
-                            tmem_st16(tAlo + c * 16, lo);
+                            tmem_st16(tAhi + c0 / 2 + c * 16, hi);
+                            tmem_st16(tAlo + c0 / 2 + c * 16, lo);
                         }
                         tmem_st_wait();
                         tc_fence_before();
                         __syncwarp();
                         if (lane == 0) mbar_arrive(bar_ar[s]);
                     } else {
+                        float zp = 0.f;
 #pragma unroll
-                        for (int c = 0; c < H / 32; c++) {
+                        for (int c = 0; c < HALF / 32; c++) {
                             float v[32];
                             tmem_ld32(tD + c * 32, v);
                             tmem_ld_wait();
 #pragma unroll
                             for (int e = 0; e < 32; e++)
-                                z = fmaf(head[c * 32 + e], fmaxf(v[e] + b[c * 32 + e], 0.f), z);
+                                zp = fmaf(head[c0 + c * 32 + e], fmaxf(v[e] + b[c * 32 + e], 0.f), zp);
                         }
                         tc_fence_before();
-                        z += head[H];
+                        // exchange the partial sums with the other half of the row
+                        xbuf[warp * 32 + lane] = zp;
+                        mbar_arrive(bar_pair);
+                        ok = gwait(bar_pair, pp, ctl, err);
+                        pp ^= 1;
+                        const float zo = xbuf[(warp ^ 4) * 32 + lane];
+                        ok = __all_sync(FULL, ok);
+                        if (!ok) break;
+                        z = (hf == 0 ? zp + zo : zo + zp) + head[H];
                     }
                 }
                 if (!ok) break;
+                if (hf != 0) continue;
                 const bool fin = isfinite(z);
                 const bool inside = valid && fin && z >= tau.up;
                 const bool flag = valid && (!fin || fabsf(z - tau.up) < margin || (z >= tau.dn && z < tau.up));
@@ -654,14 +715,14 @@ __global__ void __launch_bounds__(THREADS, 1)
             __syncwarp();
             if (lane == 0) mbar_arrive(bar_done);
         }
-        if (st && lane == 0) {
+        if (st && lane == 0 && hf == 0) {
             if (c_in) atomicAdd(&st->n_inside, c_in);
             if (c_flag) atomicAdd(&st->n_flagged, c_flag);
             if (c_nf) atomicAdd(&st->n_nonfinite, c_nf);
         }
     }
     __syncthreads();
-    if (warp == NEPI) {
+    if (warp == SEPI) {
         tc_fence_after();
         tmem_dealloc(tmem, 2 * SLOT_COLS);
     }
@@ -714,13 +775,13 @@ nb_status nb_tc_group_query(TcModel *tc, const MlpDesc &d, int64_t P, const nb_p
     if (t.H == 128) {
         NB_CUDA(cudaFuncSetAttribute(fwd_split_group_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
-        fwd_split_group_kernel<128><<<grid, THREADS, smem, s>>>(t, (long long)P, pl->items, pl->n_items, taus, q,
+        fwd_split_group_kernel<128><<<grid, STHREADS, smem, s>>>(t, (long long)P, pl->items, pl->n_items, taus, q,
                                                                 margin, bits, logits, st, ws.flag_count, ws.flag_idx,
                                                                 tc->err);
     } else {
         NB_CUDA(cudaFuncSetAttribute(fwd_split_group_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
-        fwd_split_group_kernel<64><<<grid, THREADS, smem, s>>>(t, (long long)P, pl->items, pl->n_items, taus, q,
+        fwd_split_group_kernel<64><<<grid, STHREADS, smem, s>>>(t, (long long)P, pl->items, pl->n_items, taus, q,
                                                                margin, bits, logits, st, ws.flag_count, ws.flag_idx,
                                                                tc->err);
     }
