@@ -198,3 +198,16 @@ def sample(kind: int, n: int, seed: int, first: int = 0, qexp: int = 20,
     if lib().orc_sample(int(kind), int(qexp), int(seed), int(first), int(n), _ptr(q), _threads(nthreads)) != 0:
         raise ValueError("oracle sample: bad kind, qexp or range")
     return q
+
+
+def benefit_break_even(t_a: float, t_b: float, p_a: float, p_b: float):
+    """Eq. (Benefit), Sec. 4.3 "Tightness": with bounding method A (query time t_a,
+    fraction p_a of queries passed to the exact test) against method B (t_b, p_b),
+    the total time of N queries is N t_i + p_i N t for an exact test of cost t, so A
+    wins iff t_a + p_a t < t_b + p_b t.  Returns (t*, side): A wins for t > t* when
+    side is '>' (p_a < p_b), for t < t* when side is '<' (p_a > p_b); t* is None
+    when p_a == p_b (then A wins iff t_a < t_b)."""
+    if p_a == p_b:
+        return None, "<" if t_a < t_b else ">"
+    t_star = (t_b - t_a) / (p_a - p_b)
+    return t_star, ">" if p_a < p_b else "<"

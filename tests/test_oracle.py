@@ -421,3 +421,19 @@ def test_forward_scale_definition():
         off += fo
     s = (a @ pt[off:off + 8].abs().detach() + pt[off + 8].abs()).detach().numpy()
     np.testing.assert_allclose(O.forward_scale(w, p, X), s, rtol=1e-12)
+
+
+def test_benefit_break_even_worked_example():
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "benefit_worked_example.json")))
+    t_star, side = O.benefit_break_even(g["t_a"], g["t_b"], g["p_a"], g["p_b"])
+    assert abs(t_star - g["t_star"]) <= 1e-12 and side == g["side"]
+    # the inequality itself: A's total time is below B's just above t*, above it just below
+    for t, wins in ((t_star * 1.001, True), (t_star * 0.999, False)):
+        assert (g["t_a"] + g["p_a"] * t < g["t_b"] + g["p_b"] * t) == wins
+    # a cascade with the network in front of the exact test against the box test alone
+    # (p_b = 1, t_a = t_b + t_nn) pays off once t > t_nn / (1 - p_a)
+    t_nn, p = 0.37, 0.82
+    t_star, side = O.benefit_break_even(1.0 + t_nn, 1.0, p, 1.0)
+    assert side == ">" and abs(t_star - t_nn / (1 - p)) <= 1e-12
