@@ -28,6 +28,8 @@ namespace {
 using namespace nbtc;
 
 constexpr int TILE_M = 128;
+constexpr int NEPI = 8;                    // single-model kernel: 4 epilogue warps per slot
+constexpr int THREADS = (NEPI + 1) * 32;
 constexpr unsigned SPIN_LIMIT = 1u << 22;
 constexpr unsigned FULL = 0xffffffffu;
 
@@ -66,49 +68,26 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, Ctl *ct
     return __shfl_sync(FULL, ok, 0) != 0;
 }
 
-// Single-model kernel: 16 epilogue warps, 8 per tile slot; warps w and w + 4 of a slot
-// share the TMEM lanes of quarter w mod 4 and take one half of the columns each, so a
-// layer's epilogue (TMEM load, bias, ReLU, hi/lo split, TMEM store) takes half as long
-// and the tensor pipe waits less between layers.  The two halves of a row exchange their
-// partial head sums through shared memory under a bounded mbarrier handshake.
+// Grouped kernel: 16 epilogue warps, 8 per tile slot; warps w and w + 4 of a slot share
+// the TMEM lanes of quarter w mod 4 and take one half of the columns each, so a layer's
+// epilogue (TMEM load, bias, ReLU, hi/lo split, TMEM store) has twice the warps; the two
+// halves of a row exchange their partial head sums through shared memory under a bounded
+// mbarrier handshake.  (At width 64 this is 10 % faster than 4 warps per slot; at width
+// 128 the single-model kernel keeps 4 warps per slot, 2 % faster there.)
 constexpr int SEPI = 16;
 constexpr int STHREADS = (SEPI + 1) * 32;
 
-struct SCtl {
-    uint64_t wbar, aready[2], accfull[2], drain;
-    uint64_t pair[8];  // head-sum handshake of the two warps of each (slot, lane quarter)
-    uint32_t tmem;
-    int abort;
-};
-
-__device__ bool swait(uint32_t bar, uint32_t parity, SCtl *ctl, int *err) {
-    for (unsigned i = 0; i < SPIN_LIMIT; i++) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (*(volatile int *)&ctl->abort) return false;
-    }
-    *(volatile int *)&ctl->abort = 1;
-    atomicExch(err, NB_ETIMEOUT);
-    return false;
-}
-__device__ __forceinline__ bool swarp_wait(uint32_t bar, uint32_t parity, SCtl *ctl, int *err) {
-    int ok = 1;
-    if ((threadIdx.x & 31) == 0) ok = swait(bar, parity, ctl, err) ? 1 : 0;
-    return __shfl_sync(FULL, ok, 0) != 0;
-}
-
 template <int H>
-__global__ void __launch_bounds__(STHREADS, 1)
+__global__ void __launch_bounds__(THREADS, 1)
     fwd_split_kernel(SplitDesc d, const float *__restrict__ q, long long n, TauF tau, float margin,
                      uint32_t *__restrict__ bits, float *__restrict__ logits, nb_query_stats *st,
                      unsigned *flag_count, unsigned *flag_idx, int *err) {
     constexpr uint32_t SLOT_COLS = 2 * H;  // accumulator H + activations H/2 hi + H/2 lo
-    constexpr int HALF = H / 2;            // columns (neurons) per epilogue warp
     extern __shared__ uint8_t smem_raw[];
-    SCtl *ctl = reinterpret_cast<SCtl *>(smem_raw);
+    Ctl *ctl = reinterpret_cast<Ctl *>(smem_raw);
     uint8_t *Wimg = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023) + 1024;
     float *bias = reinterpret_cast<float *>(Wimg + d.img_bytes);
     float *head = bias + d.NH * H;
-    float *xbuf = head + H + 4;  // [16 warps][32 lanes] partial head sums
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long ntiles = (n + TILE_M - 1) / TILE_M;
@@ -118,22 +97,21 @@ __global__ void __launch_bounds__(STHREADS, 1)
 
     if (threadIdx.x == 0) {
         mbar_init(bar_w, 1);
-        mbar_init(bar_ar[0], 8);
-        mbar_init(bar_ar[1], 8);
+        mbar_init(bar_ar[0], 4);
+        mbar_init(bar_ar[1], 4);
         mbar_init(bar_af[0], 1);
         mbar_init(bar_af[1], 1);
         mbar_init(bar_drain, 1);
-        for (int i = 0; i < 8; i++) mbar_init(smem_u32(&ctl->pair[i]), 64);
         ctl->abort = 0;
         fence_mbar_init();
     }
-    for (int i = threadIdx.x; i < d.NH * H; i += STHREADS) {
+    for (int i = threadIdx.x; i < d.NH * H; i += THREADS) {
         const int l = i / H, j = i % H;
         const int K = l == 0 ? d.in : H;
         bias[i] = d.p[d.off[l] + H * K + j];
     }
-    for (int i = threadIdx.x; i <= H; i += STHREADS) head[i] = d.p[d.off[d.NH] + i];
-    if (warp == SEPI) {
+    for (int i = threadIdx.x; i <= H; i += THREADS) head[i] = d.p[d.off[d.NH] + i];
+    if (warp == NEPI) {
         tmem_alloc(smem_u32(&ctl->tmem), 2 * SLOT_COLS);
         tmem_relinquish();
     }
@@ -142,12 +120,12 @@ __global__ void __launch_bounds__(STHREADS, 1)
     tc_fence_after();
     const uint32_t tmem = ctl->tmem;
 
-    if (warp == SEPI) {
+    if (warp == NEPI) {
         if (lane == 0) {
             mbar_expect_tx(bar_w, d.img_bytes);
             for (uint32_t o = 0; o < d.img_bytes; o += 16384)
                 bulk_g2s(smem_u32(Wimg) + o, d.img + o, min(16384u, d.img_bytes - o), bar_w);
-            bool ok = swait(bar_w, 0, ctl, err);
+            bool ok = wait_bounded(bar_w, 0, ctl, err);
             uint32_t ph[2] = {0, 0};
             constexpr uint32_t idesc = idesc_f16(TILE_M, H);
             const uint32_t wbase = smem_u32(Wimg);
@@ -158,7 +136,7 @@ __global__ void __launch_bounds__(STHREADS, 1)
                 for (int l = 0; l < d.NH && ok; l++)
                     for (int s = 0; s < 2 && ok; s++) {
                         if (!has[s]) continue;
-                        ok = swait(bar_ar[s], ph[s], ctl, err);
+                        ok = wait_bounded(bar_ar[s], ph[s], ctl, err);
                         ph[s] ^= 1;
                         if (!ok) break;
                         tc_fence_after();
@@ -182,22 +160,20 @@ __global__ void __launch_bounds__(STHREADS, 1)
                     }
             }
             mma_commit(bar_drain);
-            swait(bar_drain, 0, ctl, err);
+            wait_bounded(bar_drain, 0, ctl, err);
             if (!ok) *(volatile int *)&ctl->abort = 1;
         }
         __syncwarp();
     } else {
-        const int s = warp >> 3, ws = warp & 7, wq = ws & 3, hf = ws >> 2;
+        const int s = warp >> 2, wq = warp & 3;
         const int r = wq * 32 + lane;
-        const int c0 = hf * HALF;  // first neuron of this warp
         const uint32_t trow = tmem + ((uint32_t)(wq * 32) << 16) + s * SLOT_COLS;
-        const uint32_t tD = trow + c0, tAhi = trow + H, tAlo = trow + H + H / 2;
-        const uint32_t bar_pair = smem_u32(&ctl->pair[s * 4 + wq]);
-        uint32_t ph = 0, pp = 0;
+        const uint32_t tD = trow, tAhi = trow + H, tAlo = trow + H + H / 2;
+        uint32_t ph = 0;
         unsigned long long c_in = 0, c_flag = 0, c_nf = 0;
         const int in = d.in;
         float x[16];
-        if (hf == 0) {
+        {
             const long long tile0 = blockIdx.x + (long long)s * gridDim.x;
             const long long row0 = tile0 * TILE_M + r;
 #pragma unroll
@@ -208,7 +184,7 @@ __global__ void __launch_bounds__(STHREADS, 1)
             if (tile >= ntiles) break;
             const long long row = tile * TILE_M + r;
             const bool valid = row < n;
-            if (hf == 0) {
+            {
                 // A0 = [x_hi | x_lo | x_hi | 0], 16 FP16 each, two per 32-bit column
                 uint32_t w0[16], w1[16];
 #pragma unroll
@@ -227,7 +203,7 @@ __global__ void __launch_bounds__(STHREADS, 1)
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(bar_ar[s]);
-            if (hf == 0) {
+            {
                 // prefetch the next tile's rows while this tile runs through the layers
                 const long long nrow = (tile + 2 * (long long)gridDim.x) * TILE_M + r;
 #pragma unroll
@@ -236,14 +212,14 @@ __global__ void __launch_bounds__(STHREADS, 1)
             bool ok = true;
             float z = 0.f;
             for (int l = 0; l < d.NH; l++) {
-                ok = swarp_wait(bar_af[s], ph, ctl, err);
+                ok = warp_wait(bar_af[s], ph, ctl, err);
                 ph ^= 1;
                 if (!ok) break;
                 tc_fence_after();
-                const float *b = bias + l * H + c0;
+                const float *b = bias + l * H;
                 if (l < d.NH - 1) {
 #pragma unroll
-                    for (int c = 0; c < HALF / 32; c++) {
+                    for (int c = 0; c < H / 32; c++) {
                         float v[32];
                         tmem_ld32(tD + c * 32, v);
                         tmem_ld_wait();
@@ -254,70 +230,58 @@ __global__ void __launch_bounds__(STHREADS, 1)
                             const float a1 = fmaxf(v[2 * e + 1] + b[c * 32 + 2 * e + 1], 0.f);
                             split_f16x2(a0, a1, hi[e], lo[e]);
                         }
-                        tmem_st16(tAhi + c0 / 2 + c * 16, hi);
-                        tmem_st16(tAlo + c0 / 2 + c * 16, lo);
+                        tmem_st16(tAhi + c * 16, hi);
+                        tmem_st16(tAlo + c * 16, lo);
                     }
                     tmem_st_wait();
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(bar_ar[s]);
                 } else {
-                    float zp = 0.f;
 #pragma unroll
-                    for (int c = 0; c < HALF / 32; c++) {
+                    for (int c = 0; c < H / 32; c++) {
                         float v[32];
                         tmem_ld32(tD + c * 32, v);
                         tmem_ld_wait();
 #pragma unroll
-                        for (int e = 0; e < 32; e++)
-                            zp = fmaf(head[c0 + c * 32 + e], fmaxf(v[e] + b[c * 32 + e], 0.f), zp);
+                        for (int e = 0; e < 32; e++) z = fmaf(head[c * 32 + e], fmaxf(v[e] + b[c * 32 + e], 0.f), z);
                     }
                     tc_fence_before();
-                    // exchange the partial sums with the other half of the row
-                    xbuf[warp * 32 + lane] = zp;
-                    mbar_arrive(bar_pair);
-                    ok = swait(bar_pair, pp, ctl, err);
-                    pp ^= 1;
-                    const float zo = xbuf[(warp ^ 4) * 32 + lane];
-                    ok = __all_sync(FULL, ok);
-                    if (!ok) break;
-                    z = (hf == 0 ? zp + zo : zo + zp) + head[H];
+                    z += head[H];
                 }
             }
             if (!ok) break;
-            if (hf == 0) {
-                const bool fin = isfinite(z);
-                const bool inside = valid && fin && z >= tau.up;
-                // a non-finite fast logit (e.g. an FP16 overflow) goes to the FP32 re-check
-                const bool flag =
-                    valid && (!fin || fabsf(z - tau.up) < margin || (z >= tau.dn && z < tau.up));
-                const unsigned bi = __ballot_sync(FULL, inside);
-                const unsigned bf = __ballot_sync(FULL, flag);
-                const unsigned bn = __ballot_sync(FULL, valid && !fin);
-                const long long wrow = tile * TILE_M + wq * 32;
-                if (lane == 0 && wrow < n) bits[wrow >> 5] = bi;
-                if (valid && logits) logits[row] = z;
-                if (bf) {
-                    unsigned pos = 0;
-                    if (lane == 0) pos = atomicAdd(flag_count, (unsigned)__popc(bf));
-                    pos = __shfl_sync(FULL, pos, 0);
-                    if (flag) flag_idx[pos + __popc(bf & ((1u << lane) - 1u))] = (unsigned)row;
-                }
-                if (lane == 0) {
-                    c_in += __popc(bi);
-                    c_flag += __popc(bf);
-                    c_nf += __popc(bn);
-                }
+            const bool fin = isfinite(z);
+            const bool inside = valid && fin && z >= tau.up;
+            // a non-finite fast logit (e.g. an FP16 overflow) goes to the FP32 re-check
+            const bool flag =
+                valid && (!fin || fabsf(z - tau.up) < margin || (z >= tau.dn && z < tau.up));
+            const unsigned bi = __ballot_sync(FULL, inside);
+            const unsigned bf = __ballot_sync(FULL, flag);
+            const unsigned bn = __ballot_sync(FULL, valid && !fin);
+            const long long wrow = tile * TILE_M + wq * 32;
+            if (lane == 0 && wrow < n) bits[wrow >> 5] = bi;
+            if (valid && logits) logits[row] = z;
+            if (bf) {
+                unsigned pos = 0;
+                if (lane == 0) pos = atomicAdd(flag_count, (unsigned)__popc(bf));
+                pos = __shfl_sync(FULL, pos, 0);
+                if (flag) flag_idx[pos + __popc(bf & ((1u << lane) - 1u))] = (unsigned)row;
+            }
+            if (lane == 0) {
+                c_in += __popc(bi);
+                c_flag += __popc(bf);
+                c_nf += __popc(bn);
             }
         }
-        if (st && lane == 0 && hf == 0) {
+        if (st && lane == 0) {
             if (c_in) atomicAdd(&st->n_inside, c_in);
             if (c_flag) atomicAdd(&st->n_flagged, c_flag);
             if (c_nf) atomicAdd(&st->n_nonfinite, c_nf);
         }
     }
     __syncthreads();
-    if (warp == SEPI) {
+    if (warp == NEPI) {
         tc_fence_after();
         tmem_dealloc(tmem, 2 * SLOT_COLS);
     }
@@ -420,11 +384,11 @@ nb_status nb_split_query(TcModel *tc, const MlpDesc &d, const float *q, int64_t 
     if (grid < 1) grid = 1;
     if (t.H == 128) {
         NB_CUDA(cudaFuncSetAttribute(fwd_split_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        fwd_split_kernel<128><<<(unsigned)grid, STHREADS, smem, s>>>(t, q, (long long)n, tau, margin, bits, logits,
+        fwd_split_kernel<128><<<(unsigned)grid, THREADS, smem, s>>>(t, q, (long long)n, tau, margin, bits, logits,
                                                                     st, ws.flag_count, ws.flag_idx, tc->err);
     } else {
         NB_CUDA(cudaFuncSetAttribute(fwd_split_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        fwd_split_kernel<64><<<(unsigned)grid, STHREADS, smem, s>>>(t, q, (long long)n, tau, margin, bits, logits, st,
+        fwd_split_kernel<64><<<(unsigned)grid, THREADS, smem, s>>>(t, q, (long long)n, tau, margin, bits, logits, st,
                                                                    ws.flag_count, ws.flag_idx, tc->err);
     }
     NB_CUDA(cudaGetLastError());
