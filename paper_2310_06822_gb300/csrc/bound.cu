@@ -22,7 +22,6 @@
 
 namespace {
 
-constexpr int KC = 32;
 constexpr unsigned FULL = 0xffffffffu;
 constexpr float U = 5.9604644775390625e-08f;  // unit roundoff 2^-24
 constexpr int FF_WARPS_PER_SM = 32;              // stage-2 launch: 8 blocks of 4 warps per SM
@@ -39,12 +38,13 @@ __device__ __forceinline__ unsigned long long ord_f64(double f) {
     return (u & 0x8000000000000000ull) ? ~u : (u | 0x8000000000000000ull);
 }
 
-// One hidden layer over a tile: values aout = relu(b + W ain) and bounds eout.
+// One hidden layer over a tile, in place: a <- relu(b + W a) and e <- its bound.  Each
+// thread owns MI rows x NJ neurons; the weights come straight from the transposed copy
+// (row k of W^T: 16 consecutive neurons per half-warp, shared by every warp through L1),
+// so the layer needs no staging and only two block barriers: inputs ready, inputs read.
 template <int NJ, int MI>
 __device__ __forceinline__ void bound_layer_tile(const float *__restrict__ Wt, const float *__restrict__ b, int K,
-                                                 int N, float g, const float *ain, const float *ein, float *aout,
-                                                 float *eout, float *wt, int KP) {
-    constexpr int WS = 16 * NJ + 1;
+                                                 int N, float g, float *a_s, float *e_s, int KP) {
     const int t = threadIdx.x, tn = t & 15, tm = t >> 4;
     float acc[MI][NJ], bnd[MI][NJ];
 #pragma unroll
@@ -58,41 +58,35 @@ __device__ __forceinline__ void bound_layer_tile(const float *__restrict__ Wt, c
             bnd[i][j] = bb;
         }
     }
-    for (int kc = 0; kc < K; kc += KC) {
-        const int kw = min(KC, K - kc);
-        __syncthreads();
-        for (int e = t; e < N * KC; e += blockDim.x) {
-            const int kk = e / N, nn = e % N;
-            wt[kk * WS + nn] = kk < kw ? __ldg(Wt + (size_t)(kc + kk) * N + nn) : 0.f;
-        }
-        __syncthreads();
-        for (int kk = 0; kk < kw; kk++) {
-            float a[MI], v[MI], w[NJ];
+    __syncthreads();  // the layer's inputs are in place
+    for (int k = 0; k < K; k++) {
+        float a[MI], v[MI], w[NJ];
 #pragma unroll
-            for (int i = 0; i < MI; i++) {
-                const int idx = (tm + 16 * i) * KP + kc + kk;
-                a[i] = ain[idx];
-                v[i] = __fmaf_ru(g, fabsf(a[i]), ein[idx]);
+        for (int i = 0; i < MI; i++) {
+            const int idx = (tm + 16 * i) * KP + k;
+            a[i] = a_s[idx];
+            v[i] = __fmaf_ru(g, fabsf(a[i]), e_s[idx]);
+        }
+        const float *wk = Wt + (size_t)k * N + tn;
+#pragma unroll
+        for (int j = 0; j < NJ; j++) w[j] = tn + 16 * j < N ? __ldg(wk + 16 * j) : 0.f;
+#pragma unroll
+        for (int i = 0; i < MI; i++)
+#pragma unroll
+            for (int j = 0; j < NJ; j++) {
+                acc[i][j] = fmaf(a[i], w[j], acc[i][j]);
+                bnd[i][j] = __fmaf_ru(v[i], fabsf(w[j]), bnd[i][j]);
             }
-#pragma unroll
-            for (int j = 0; j < NJ; j++) w[j] = wt[kk * WS + tn + 16 * j];
-#pragma unroll
-            for (int i = 0; i < MI; i++)
-#pragma unroll
-                for (int j = 0; j < NJ; j++) {
-                    acc[i][j] = fmaf(a[i], w[j], acc[i][j]);
-                    bnd[i][j] = __fmaf_ru(v[i], fabsf(w[j]), bnd[i][j]);
-                }
-        }
     }
+    __syncthreads();  // every thread has read the inputs: overwrite them
 #pragma unroll
     for (int j = 0; j < NJ; j++) {
         const int nn = tn + 16 * j;
         if (nn < N)
 #pragma unroll
             for (int i = 0; i < MI; i++) {
-                aout[(tm + 16 * i) * KP + nn] = fmaxf(acc[i][j], 0.f);
-                eout[(tm + 16 * i) * KP + nn] = bnd[i][j];
+                a_s[(tm + 16 * i) * KP + nn] = fmaxf(acc[i][j], 0.f);
+                e_s[(tm + 16 * i) * KP + nn] = bnd[i][j];
             }
     }
 }
@@ -114,7 +108,7 @@ __global__ void __launch_bounds__(256) bound_tile_kernel(MlpDesc d, GammaTab gt,
                                                          float *lo_out, unsigned *umin_bits, unsigned direct_max) {
     constexpr int TM = 16 * MI, KP = 16 * NJ + 1, TPQ = 256 / TM;
     extern __shared__ float smem[];
-    float *a0 = smem, *e0 = a0 + TM * KP, *a1 = e0 + TM * KP, *e1 = a1 + TM * KP, *wt = e1 + TM * KP;
+    float *a0 = smem, *e0 = a0 + TM * KP;
     __shared__ unsigned rowidx[TM];
     __shared__ float zs[TM], bs[TM];
     const int t = threadIdx.x, w0 = d.w[0];
@@ -139,17 +133,11 @@ __global__ void __launch_bounds__(256) bound_tile_kernel(MlpDesc d, GammaTab gt,
             a0[m * KP + k] = m < rows ? q[(size_t)rowidx[m] * w0 + k] : 0.f;
             e0[m * KP + k] = 0.f;
         }
-        float *ain = a0, *ein = e0, *aout = a1, *eout = e1;
+        const float *ain = a0, *ein = e0;
         for (int l = 0; l < d.L - 1; l++) {
             const int K = d.w[l], N = d.w[l + 1];
             const float *Wt = d.pT + d.off[l];
-            bound_layer_tile<NJ, MI>(Wt, Wt + (size_t)N * K, K, N, gt.g[l], ain, ein, aout, eout, wt, KP);
-            float *tp = ain;
-            ain = aout;
-            aout = tp;
-            tp = ein;
-            ein = eout;
-            eout = tp;
+            bound_layer_tile<NJ, MI>(Wt, Wt + (size_t)N * K, K, N, gt.g[l], a0, e0, KP);
         }
         __syncthreads();
         {
@@ -615,7 +603,7 @@ nb_status tile_launch(const MlpDesc &d, const GammaTab &gt, const float *q, TauF
                       const unsigned *idx, int64_t max_count, uint32_t *bits, nb_query_stats *st, unsigned *ff_count,
                       unsigned *ff_idx, float *lo_out, unsigned *umin_bits, cudaStream_t s) {
     constexpr int TM = 16 * MI, KP = 16 * NJ + 1;
-    const size_t smem = (size_t)(4 * TM * KP + KC * (16 * NJ + 1)) * sizeof(float);
+    const size_t smem = (size_t)(2 * TM * KP) * sizeof(float);
     auto k = bound_tile_kernel<NJ, MI, MODE>;
     NB_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 1;
