@@ -11,7 +11,8 @@ FP32 / extended-precision re-check of the margin band), inputs resident in HBM (
 per step, more than the 129 MB L2, so no flush is needed); value = rays/s over all ranks.
 
 Other configurations (--config): c1 (2D points, plain FP32), c3 (3D boxes and planes,
-256 spheres, 256-wide networks, FP8 E4M3 inference), c4 (256 objects of moving
+256 spheres, 256-wide networks, FP8 E4M3 inference), c2e (3D points behind the neural
+early-out of Sec. 3.3), c4 (256 objects of moving
 spheres, 4D points, grouped training under a CUDA graph and grouped queries), c5 (1024
 objects, 64M world rays through the learned-culler cascade, against box + exact).
 Every line also carries the FP64 oracle timed on the host cores, an end-to-end figure
@@ -430,6 +431,61 @@ def run_c3(args):
     ctx.emit(line)
 
 
+# ---------------------------------------------------------------------------------- early-out
+def run_c2e(args):
+    """3D point queries against a solid object (16 spheres of radius 0.2-0.5), the late
+    network 3->128x4->1 (split-FP16) behind the neural early-out of Sec. 3.3 (an early
+    3->64x2->1 network trained on the complement 1 - g)."""
+    from paper_2310_06822_gb300 import inputs as I
+    from paper_2310_06822_gb300 import nb
+    ctx = Ctx(args)
+    torch, dev = ctx.torch, ctx.dev
+    sc = I.make_scene(SEED_SCENE + 10, 16, 3, 0.2, 0.5)
+    shape = nb.Shape(sc, dev)
+    late_w, early_w = [3, 128, 128, 128, 128, 1], [3, 64, 64, 1]
+    T = args.train_steps if args.train_steps != TRAIN_STEPS else 2000
+    late_t = nb.Model(late_w, infer_prec="f32", train_prec="bf16")
+    late_t.set_params(I.init_params(SEED_INIT, late_w))
+    early = nb.Model(early_w)
+    early.set_params(I.init_params(SEED_INIT + 1, early_w))
+    for t in range(T):
+        q = nb.sample(I.POINT3, BATCH, SEED_TRAIN, first=t * BATCH)
+        y = nb.label(shape, I.POINT3, q)
+        a = 1.0 + 99.0 * t / max(T - 1, 1)
+        late_t.train_step(q, y, a)
+        early.train_step(q, nb.bits_not(y, BATCH), a)
+    late = nb.Model(late_w, infer_prec="f16x3")
+    late.set_params(late_t.get_params())
+    n = args.n_eval
+    eq = nb.sample(I.POINT3, n, SEED_QUERY + 1000 * ctx.rank)
+    ey = nb.label(shape, I.POINT3, eq)
+    late.calibrate(eq, ey)
+    early.calibrate(eq, nb.bits_not(ey, n))
+    out = torch.empty(nb.n_words(n), dtype=torch.int32, device=dev)
+    bits, est = nb.query_early_out(early, late, eq, margin_early=1e-3, margin_late=MARGIN, out=out)
+    y = nb.bits_to_numpy(ey, n)
+    dec = nb.bits_to_numpy(bits, n)
+    ms, clocks = ctx.timed(lambda: nb.query_early_out(early, late, eq, margin_early=1e-3, margin_late=MARGIN,
+                                                      out=out), args.steps, args.warmup)
+    plain_ms = ctx.time_ms(lambda: late.query(eq, margin=MARGIN, out=out), max(3, args.steps // 4))
+    dplain = nb.bits_to_numpy(late.query(eq, margin=MARGIN), n)
+    if ctx.rank != 0:
+        return ctx.emit(None)
+    line = base_line(ctx, "neural-bound queries/s at 0 FN (3D points, neural early-out + split-FP16 late network)",
+                     ctx.world * n / (ms / 1000.0), "queries/s", ms, args.steps, args.warmup,
+                     "f16x3 late, f32 early",
+                     {"workload": "3D points: 16-sphere solid (radii 0.2-0.5), late MLP 3->128x4->1, early MLP "
+                                  "3->64x2->1 on 1 - g, 16M eval points (Sec. 3.3 early-out)", "n_eval": n,
+                      "train_steps": T},
+                     clocks, args.steps * 8)
+    line.update({"fn": int(np.sum(y & ~dec)), "fp_rate": float(np.mean(~y & dec)),
+                 "fp_rate_without_early_out": float(np.mean(~y & dplain)),
+                 "early_inside_fraction": est["n_early_inside"] / n,
+                 "without_early_out_queries_per_s": n / (plain_ms / 1000.0),
+                 "speedup_vs_without": plain_ms / ms, "cpu_baseline": None, "e2e": None})
+    ctx.emit(line)
+
+
 # ---------------------------------------------------------------------------------- 2D points
 def run_c1(args):
     from paper_2310_06822_gb300 import inputs as I
@@ -752,13 +808,13 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4", "c5"])
+    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c2e", "c3", "c4", "c5"])
     ap.add_argument("--train-steps", type=int, default=TRAIN_STEPS)
     ap.add_argument("--n-eval", type=int, default=N_EVAL, help="evaluation size (smaller only for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
-    {"c1": run_c1, "c2": run_c2, "c3": run_c3, "c4": run_c4, "c5": run_c5}[args.config](args)
+    {"c1": run_c1, "c2": run_c2, "c2e": run_c2e, "c3": run_c3, "c4": run_c4, "c5": run_c5}[args.config](args)
 
 
 if __name__ == "__main__":

@@ -176,6 +176,27 @@ nb_status nb_train_step(nb_model *m, const float *q, const uint32_t *label_bits,
 nb_status nb_query(nb_model *m, const float *q, int64_t n, float margin, uint32_t *out_bits, float *opt_logits,
                    nb_query_stats *dev_stats, void *stream);
 
+/* Neural early-out (Sec. 3.3): `early` is a (small) network trained and calibrated as a
+ * conservative bound of the complement 1 - g (labels inverted, e.g. by nb_bits_not), so
+ * that where it decides 0 the query is certainly inside (g = 1); `late` is the bounding
+ * network of g.  Every row is first decided by `early` (nb_query with margin_early); rows
+ * it decides 0 get bit 1 without evaluating `late`; the other rows are compacted, gathered
+ * into a library-owned buffer and decided by `late` (nb_query with margin_late), and
+ * their bits scattered back.  Both networks take the same input width.  host_stats (may
+ * be NULL) receives how many rows each network decided.  Synchronous on stream (the
+ * number of rows left for `late` is read back); the workspace, owned by `late`, grows on
+ * demand (a growth synchronises the device). */
+typedef struct {
+    uint64_t n_early_inside;  /* rows settled by the early network (bit 1) */
+    uint64_t n_late;          /* rows decided by the late network */
+} nb_early_stats;
+nb_status nb_query_early_out(nb_model *early, nb_model *late, const float *q, int64_t n, float margin_early,
+                             float margin_late, uint32_t *out_bits, nb_early_stats *host_stats, void *stream);
+
+/* out[i] = 1 - in[i] for the n bits of a label or decision array (bits past n cleared);
+ * in and out may be the same buffer.  Asynchronous on stream. */
+nb_status nb_bits_not(const uint32_t *in, int64_t n, uint32_t *out, void *stream);
+
 /* Threshold calibration (Suppl. "Numerics", output epsilon): tau = (minimum over
  * the queries labelled 1 of the network logit) - eps, rounded toward -infinity,
  * so the calibration set has no false negative.  The minimum is located with FP32

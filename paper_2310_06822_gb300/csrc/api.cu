@@ -109,6 +109,8 @@ struct nb_model {
     // library-owned scratch, grown on demand
     void *ws = nullptr;
     size_t ws_bytes = 0;
+    void *eo_ws = nullptr;  // early-out scratch (when this model is the late network)
+    size_t eo_bytes = 0;
     // low-precision weight images for the tensor-core paths
     TcModel tc{};
 };
@@ -161,6 +163,7 @@ static void free_model(nb_model *m) {
     cudaFree(m->grad);
     cudaFree(m->paramsT);
     cudaFree(m->ws);
+    cudaFree(m->eo_ws);
     nb_tc_free(&m->tc);
     delete m;
 }
@@ -422,6 +425,68 @@ extern "C" nb_status nb_query(nb_model *m, const float *q, int64_t n, float marg
         st = nb_tc_query(&m->tc, d, q, n, tau, margin, out_bits, opt_logits, dev_stats, ws, s);
     if (st != NB_OK) return st;
     return nb_launch_recheck(d, m->gamma, q, tau, out_bits, dev_stats, ws, n, s);
+}
+
+extern "C" nb_status nb_query_early_out(nb_model *early, nb_model *late, const float *q, int64_t n,
+                                        float margin_early, float margin_late, uint32_t *out_bits,
+                                        nb_early_stats *host_stats, void *stream) {
+    if (!early || !late) return nb_fail(NB_EINVAL, "nb_query_early_out: null model");
+    if (early->widths[0] != late->widths[0]) return nb_fail(NB_EINVAL, "nb_query_early_out: input widths differ");
+    if (n < 0 || n >= (int64_t)1 << 32) return nb_fail(NB_EINVAL, "nb_query_early_out: n must be in [0, 2^32)");
+    if (n > 0 && (!q || !out_bits)) return nb_fail(NB_EINVAL, "nb_query_early_out: null pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (host_stats) memset(host_stats, 0, sizeof(nb_early_stats));
+    if (n == 0) return NB_OK;
+    const int w = late->widths[0];
+    const size_t words = align256((size_t)((n + 31) / 32) * 4), list = align256((size_t)n * 4);
+    const size_t need = 256 + 2 * words + list + align256((size_t)n * w * sizeof(float));
+    if (need > late->eo_bytes) {
+        NB_CUDA(cudaDeviceSynchronize());
+        cudaFree(late->eo_ws);
+        late->eo_ws = nullptr;
+        late->eo_bytes = 0;
+        if (cudaMalloc(&late->eo_ws, need) != cudaSuccess) {
+            cudaGetLastError();
+            return nb_fail(NB_ENOMEM, "nb_query_early_out: workspace allocation failed");
+        }
+        late->eo_bytes = need;
+    }
+    char *base = (char *)late->eo_ws;
+    unsigned *count = (unsigned *)base;
+    uint32_t *bits_e = (uint32_t *)(base + 256);
+    uint32_t *bits_c = (uint32_t *)(base + 256 + words);
+    unsigned *idx = (unsigned *)(base + 256 + 2 * words);
+    float *qc = (float *)(base + 256 + 2 * words + list);
+    // 1. the early network on every row (certified decisions against its threshold)
+    nb_status st = nb_query(early, q, n, margin_early, bits_e, nullptr, nullptr, stream);
+    if (st != NB_OK) return st;
+    // 2. rows it settles are inside; the others are listed
+    st = nb_launch_early_compact(bits_e, n, count, idx, out_bits, s);
+    if (st != NB_OK) return st;
+    unsigned m = 0;
+    NB_CUDA(cudaMemcpyAsync(&m, count, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    NB_CUDA(cudaStreamSynchronize(s));
+    // 3. the late network on the listed rows only
+    if (m > 0) {
+        st = nb_launch_early_gather(q, w, idx, m, qc, s);
+        if (st != NB_OK) return st;
+        st = nb_query(late, qc, m, margin_late, bits_c, nullptr, nullptr, stream);
+        if (st != NB_OK) return st;
+        st = nb_launch_early_scatter(bits_c, idx, m, out_bits, s);
+        if (st != NB_OK) return st;
+    }
+    if (host_stats) {
+        host_stats->n_early_inside = (uint64_t)(n - m);
+        host_stats->n_late = m;
+    }
+    return NB_OK;
+}
+
+extern "C" nb_status nb_bits_not(const uint32_t *in, int64_t n, uint32_t *out, void *stream) {
+    if (n < 0) return nb_fail(NB_EINVAL, "nb_bits_not: n must be >= 0");
+    if (n == 0) return NB_OK;
+    if (!in || !out) return nb_fail(NB_EINVAL, "nb_bits_not: null pointer");
+    return nb_launch_bits_not(in, n, out, (cudaStream_t)stream);
 }
 
 extern "C" nb_status nb_calibrate(nb_model *m, const float *q, const uint32_t *label_bits, int64_t n, double eps,

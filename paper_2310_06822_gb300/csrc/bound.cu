@@ -39,12 +39,16 @@ __device__ __forceinline__ unsigned long long ord_f64(double f) {
 }
 
 // One hidden layer over a tile, in place: a <- relu(b + W a) and e <- its bound.  Each
-// thread owns MI rows x NJ neurons; the weights come straight from the transposed copy
-// (row k of W^T: 16 consecutive neurons per half-warp, shared by every warp through L1),
-// so the layer needs no staging and only two block barriers: inputs ready, inputs read.
+// thread owns MI rows x NJ neurons.  The weights are staged through shared memory KC input
+// rows at a time from the transposed copy (row k of W^T is contiguous: coalesced), and the
+// outputs overwrite the inputs after a barrier, so a CTA needs two activation buffers and
+// one weight chunk -- a third of the shared memory of separate in/out buffers -- and two
+// or more CTAs share an SM to hide the staging latency.
+constexpr int KC = 32;
 template <int NJ, int MI>
 __device__ __forceinline__ void bound_layer_tile(const float *__restrict__ Wt, const float *__restrict__ b, int K,
-                                                 int N, float g, float *a_s, float *e_s, int KP) {
+                                                 int N, float g, float *a_s, float *e_s, float *wt, int KP) {
+    constexpr int WS = 16 * NJ + 1;
     const int t = threadIdx.x, tn = t & 15, tm = t >> 4;
     float acc[MI][NJ], bnd[MI][NJ];
 #pragma unroll
@@ -58,25 +62,32 @@ __device__ __forceinline__ void bound_layer_tile(const float *__restrict__ Wt, c
             bnd[i][j] = bb;
         }
     }
-    __syncthreads();  // the layer's inputs are in place
-    for (int k = 0; k < K; k++) {
-        float a[MI], v[MI], w[NJ];
-#pragma unroll
-        for (int i = 0; i < MI; i++) {
-            const int idx = (tm + 16 * i) * KP + k;
-            a[i] = a_s[idx];
-            v[i] = __fmaf_ru(g, fabsf(a[i]), e_s[idx]);
+    for (int kc = 0; kc < K; kc += KC) {
+        const int kw = min(KC, K - kc);
+        __syncthreads();  // inputs in place, previous chunk consumed
+        for (int e = t; e < N * KC; e += blockDim.x) {
+            const int kk = e / N, nn = e % N;
+            wt[kk * WS + nn] = kk < kw ? __ldg(Wt + (size_t)(kc + kk) * N + nn) : 0.f;
         }
-        const float *wk = Wt + (size_t)k * N + tn;
+        __syncthreads();
+        for (int kk = 0; kk < kw; kk++) {
+            float a[MI], v[MI], w[NJ];
 #pragma unroll
-        for (int j = 0; j < NJ; j++) w[j] = tn + 16 * j < N ? __ldg(wk + 16 * j) : 0.f;
-#pragma unroll
-        for (int i = 0; i < MI; i++)
-#pragma unroll
-            for (int j = 0; j < NJ; j++) {
-                acc[i][j] = fmaf(a[i], w[j], acc[i][j]);
-                bnd[i][j] = __fmaf_ru(v[i], fabsf(w[j]), bnd[i][j]);
+            for (int i = 0; i < MI; i++) {
+                const int idx = (tm + 16 * i) * KP + kc + kk;
+                a[i] = a_s[idx];
+                v[i] = __fmaf_ru(g, fabsf(a[i]), e_s[idx]);
             }
+#pragma unroll
+            for (int j = 0; j < NJ; j++) w[j] = wt[kk * WS + tn + 16 * j];
+#pragma unroll
+            for (int i = 0; i < MI; i++)
+#pragma unroll
+                for (int j = 0; j < NJ; j++) {
+                    acc[i][j] = fmaf(a[i], w[j], acc[i][j]);
+                    bnd[i][j] = __fmaf_ru(v[i], fabsf(w[j]), bnd[i][j]);
+                }
+        }
     }
     __syncthreads();  // every thread has read the inputs: overwrite them
 #pragma unroll
@@ -108,7 +119,7 @@ __global__ void __launch_bounds__(256) bound_tile_kernel(MlpDesc d, GammaTab gt,
                                                          float *lo_out, unsigned *umin_bits, unsigned direct_max) {
     constexpr int TM = 16 * MI, KP = 16 * NJ + 1, TPQ = 256 / TM;
     extern __shared__ float smem[];
-    float *a0 = smem, *e0 = a0 + TM * KP;
+    float *a0 = smem, *e0 = a0 + TM * KP, *wt = e0 + TM * KP;
     __shared__ unsigned rowidx[TM];
     __shared__ float zs[TM], bs[TM];
     const int t = threadIdx.x, w0 = d.w[0];
@@ -137,7 +148,7 @@ __global__ void __launch_bounds__(256) bound_tile_kernel(MlpDesc d, GammaTab gt,
         for (int l = 0; l < d.L - 1; l++) {
             const int K = d.w[l], N = d.w[l + 1];
             const float *Wt = d.pT + d.off[l];
-            bound_layer_tile<NJ, MI>(Wt, Wt + (size_t)N * K, K, N, gt.g[l], a0, e0, KP);
+            bound_layer_tile<NJ, MI>(Wt, Wt + (size_t)N * K, K, N, gt.g[l], a0, e0, wt, KP);
         }
         __syncthreads();
         {
@@ -603,7 +614,7 @@ nb_status tile_launch(const MlpDesc &d, const GammaTab &gt, const float *q, TauF
                       const unsigned *idx, int64_t max_count, uint32_t *bits, nb_query_stats *st, unsigned *ff_count,
                       unsigned *ff_idx, float *lo_out, unsigned *umin_bits, cudaStream_t s) {
     constexpr int TM = 16 * MI, KP = 16 * NJ + 1;
-    const size_t smem = (size_t)(2 * TM * KP) * sizeof(float);
+    const size_t smem = (size_t)(2 * TM * KP + KC * (16 * NJ + 1)) * sizeof(float);
     auto k = bound_tile_kernel<NJ, MI, MODE>;
     NB_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 1;

@@ -68,6 +68,14 @@ struct QueryWs {
 
 nb_status nb_launch_fwd_f32(const MlpDesc &d, const float *q, int64_t n, TauF tau, float margin,
                             uint32_t *bits, float *logits, nb_query_stats *st, QueryWs ws, cudaStream_t s);
+// neural early-out (early.cu)
+nb_status nb_launch_early_compact(const uint32_t *bits_e, int64_t n, unsigned *count, unsigned *idx, uint32_t *out_bits,
+                                  cudaStream_t s);
+nb_status nb_launch_early_gather(const float *q, int w, const unsigned *idx, int64_t m, float *qc, cudaStream_t s);
+nb_status nb_launch_early_scatter(const uint32_t *bits_c, const unsigned *idx, int64_t m, uint32_t *out_bits,
+                                  cudaStream_t s);
+nb_status nb_launch_bits_not(const uint32_t *in, int64_t n, uint32_t *out, cudaStream_t s);
+
 // pT <- p with every weight matrix transposed, for n_objects parameter sets P apart
 nb_status nb_launch_transpose(const MlpDesc &d, float *pT, int n_objects, long long P, cudaStream_t s);
 nb_status nb_launch_recheck(const MlpDesc &d, const GammaTab &gt, const float *q, TauF tau, uint32_t *bits,

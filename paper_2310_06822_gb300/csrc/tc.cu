@@ -339,12 +339,12 @@ nb_status nb_tc_init(TcModel *tc, const MlpDesc &d, int infer_prec, int train_pr
             return nb_fail(NB_EUNSUPPORTED, "FP8 forward: the network's weights do not fit in shared memory");
         tc->img_bytes = nb_fp8_img_bytes(H, NHH);
         if (cudaMalloc(&tc->img, tc->img_bytes) != cudaSuccess ||
-            cudaMalloc(&tc->scales, sizeof(float) * NHH * H) != cudaSuccess) {
+            cudaMalloc(&tc->scales, sizeof(float) * (2 * NHH * H + H + 1)) != cudaSuccess) {
             cudaGetLastError();
             return nb_fail(NB_ENOMEM, "tensor-core image allocation failed");
         }
         cudaMemset(tc->img, 0, tc->img_bytes);
-        cudaMemset(tc->scales, 0, sizeof(float) * NHH * H);
+        cudaMemset(tc->scales, 0, sizeof(float) * (2 * NHH * H + H + 1));
     }
     if (infer_prec == NB_BF16 || infer_prec == NB_F16X3) {
         if (NH < 1) return nb_fail(NB_EUNSUPPORTED, "tensor-core forward needs at least one hidden layer");

@@ -8,7 +8,7 @@ struct TcModel {
     int infer_prec = 0, train_prec = 0;
     void *img = nullptr;     // device: packed operand images of every layer
     size_t img_bytes = 0;
-    float *scales = nullptr; // device: 1 / (power-of-two scale) of every FP8 weight row
+    float *scales = nullptr; // device (FP8): 1 / s_n of every E4M3 weight row, folded biases, head
     void *train_img = nullptr;   // device: BF16 weights for the tensor-core training step
     size_t train_img_bytes = 0;
     int *err = nullptr;      // device: status of the last bounded wait that gave up (0 = none)

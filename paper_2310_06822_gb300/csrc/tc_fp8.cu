@@ -2,10 +2,13 @@
 //
 // The hidden-to-hidden layers run on the tensor cores with E4M3 operands and FP32
 // accumulation (tcgen05.mma kind::f8f6f4).  Scales are powers of two, so applying and
-// removing them is exact: every weight row n of a layer has its own s_n (max_k |W_nk| s_n
-// in [128, 256)), every query row its own activation scale r (max_k a_k r in [128, 256),
-// E4M3's largest finite value being 448), and the accumulator D_n = sum_k q(a_k r) q(W_nk s_n)
-// is read back as D_n / (r s_n).  The first layer (fan-in = the query encoding) runs in
+// removing them is exact.  Every query row has its own activation scale r (max_k a_k r in
+// [128, 256), E4M3's largest finite value being 448).  Every weight row n of layer l has its
+// own s_n, and the layer's outputs are kept scaled by it: the epilogue computes
+// a'_n = relu(D_n / r + b_n s_n) = s_n a_n, the next layer's columns carry 1 / s_k
+// (W'_nk = W_nk s_n / s_k, s_n chosen so that max_k |W_nk / s_k| s_n is in [128, 256)) and
+// the head's weights carry 1 / s_n, so one folded bias per neuron is all the epilogue
+// reads.  The first layer (fan-in = the query encoding) runs in
 // split FP16 (three products, as in the split-FP16 kernel): quantising the query itself
 // to three mantissa bits would move it by several per cent.  The output head runs in FP32
 // on the CUDA cores.
@@ -40,7 +43,9 @@ struct Fp8Desc {
     int in, H, NHH;        // input width, hidden width, hidden-to-hidden layers
     const uint8_t *img;    // layer 0 split image, then NHH E4M3 images
     uint32_t img_bytes;
-    const float *inv_sw;   // [NHH][H] 1 / s_n of every weight row
+    const float *inv_sw;   // [NHH][H] 1 / s_n of every E4M3 weight row
+    const float *bs;       // [NHH][H] b_n s_n: the folded biases
+    const float *hw;       // [H + 1] head weights w_n / s_n of the last E4M3 layer, then its bias
     const float *p;        // FP32 master parameters
     int off[NB_MAXL];
 };
@@ -220,10 +225,9 @@ __global__ void __launch_bounds__(THREADS, 1)
                 ph ^= 1;
                 if (!ok) break;
                 tc_fence_after();
-                // this layer's output neuron c: a_c = relu(D_c inv_r / s_c + b_c)
-                const float *b = d.p + d.off[l] + (size_t)H * (l == 0 ? in : H);
-                const float *isw = d.inv_sw + (size_t)(l > 0 ? l - 1 : 0) * H;
-                const bool scaled = l > 0;
+                // this layer's output neuron c, kept scaled: relu(D_c inv_r + b_c s_c) = s_c a_c
+                // (the first layer: relu(D_c + b_c))
+                const float *b = l == 0 ? d.p + d.off[0] + (size_t)H * in : d.bs + (size_t)(l - 1) * H;
                 if (l < NL - 1) {
                     float m = 0.f;
 #pragma unroll
@@ -234,8 +238,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
                         for (int e = 0; e < 32; e++) {
                             const int nn = c0 + c * 32 + e;
-                            const float t = scaled ? fmaf(v[e] * inv_r, __ldg(isw + nn), __ldg(b + nn))
-                                                   : v[e] + __ldg(b + nn);
+                            const float t = fmaf(v[e], inv_r, __ldg(b + nn));
                             bad |= !(fabsf(t) < INFINITY);
                             m = fmaxf(m, t);
                         }
@@ -261,8 +264,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
                                 for (int u = 0; u < 4; u++) {
                                     const int nn = c0 + cp * 64 + hh * 32 + 4 * e + u;
-                                    const float t = scaled ? fmaf(v[4 * e + u] * inv_r, __ldg(isw + nn), __ldg(b + nn))
-                                                           : v[4 * e + u] + __ldg(b + nn);
+                                    const float t = fmaf(v[4 * e + u], inv_r, __ldg(b + nn));
                                     a[u] = fmaxf(t, 0.f) * rs;
                                 }
                                 w16[hh * 8 + e] = pack_e4m3x4(a[0], a[1], a[2], a[3]);
@@ -276,7 +278,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                     __syncwarp();
                     if (lane == 0) mbar_arrive(bar_ar);
                 } else {
-                    const float *head = d.p + d.off[NL];
+                    const float *head = d.hw;
                     float zp = 0.f;
 #pragma unroll
                     for (int c = 0; c < HALF / 32; c++) {
@@ -286,7 +288,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
                         for (int e = 0; e < 32; e++) {
                             const int nn = c0 + c * 32 + e;
-                            const float t = fmaf(v[e] * inv_r, __ldg(isw + nn), __ldg(b + nn));
+                            const float t = fmaf(v[e], inv_r, __ldg(b + nn));
                             bad |= !(fabsf(t) < INFINITY);
                             zp = fmaf(__ldg(head + nn), fmaxf(t, 0.f), zp);
                         }
@@ -338,23 +340,33 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
 }
 
-// 1 / s_n of every hidden-to-hidden weight row (one warp per row): s_n = 2^(8 - e),
-// max_k |W_nk| = f 2^e with f in [0.5, 1); rows of zeros get 1
-__global__ void fp8_scale_kernel(Fp8Desc d, float *inv_sw) {
+// Scales of the E4M3 layer l (one warp per weight row n): s_n = 2^(8 - e) with
+// max_k |W_nk / s'_k| = f 2^e, f in [0.5, 1), s'_k the previous E4M3 layer's row scales (1
+// for the first); rows of zeros get 1.  Writes 1 / s_n and the folded bias b_n s_n.
+__global__ void fp8_scale_kernel(Fp8Desc d, int l, float *inv_sw, float *bs) {
     const int H = d.H;
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (gw >= d.NHH * H) return;
-    const int l = 1 + gw / H, nrow = gw % H;
+    const int nrow = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (nrow >= H) return;
     const float *W = d.p + d.off[l] + (size_t)nrow * H;
+    const float *prev = l > 1 ? inv_sw + (size_t)(l - 2) * H : nullptr;
     float m = 0.f;
-    for (int k = lane; k < H; k += 32) m = fmaxf(m, fabsf(W[k]));
+    for (int k = lane; k < H; k += 32) m = fmaxf(m, fabsf(prev ? W[k] * prev[k] : W[k]));
 #pragma unroll
     for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(FULL, m, o));
     if (lane == 0) {
         float inv;
-        pow2_scale(m, inv);
-        inv_sw[gw] = inv;
+        const float sn = pow2_scale(m, inv);
+        inv_sw[(size_t)(l - 1) * H + nrow] = inv;
+        bs[(size_t)(l - 1) * H + nrow] = d.p[d.off[l] + H * H + nrow] * sn;
     }
+}
+
+// head weights of the folded form: w_n / s_n of the last E4M3 layer, then the bias
+__global__ void fp8_head_kernel(Fp8Desc d, float *hw) {
+    const int H = d.H;
+    const float *inv = d.inv_sw + (size_t)(d.NHH - 1) * H;
+    const float *w = d.p + d.off[d.NHH + 1];
+    for (int n = threadIdx.x; n <= H; n += blockDim.x) hw[n] = n < H ? w[n] * inv[n] : w[H];
 }
 
 // FP32 master weights -> operand images (one thread per 16-byte chunk): the first layer as
@@ -391,12 +403,16 @@ __global__ void pack_fp8_kernel(Fp8Desc d, uint8_t *img) {
             const uint32_t local = rel % (uint32_t)(H * H);
             const uint32_t kb = local / (uint32_t)(H * 128), rem = local % (uint32_t)(H * 128);
             const uint32_t nrow = rem / 128, pc = (rem % 128) / 16, c = pc ^ (nrow & 7);
-            const float *W = d.p + d.off[l] + (size_t)nrow * H + kb * 128 + c * 16;
+            const int k0 = (int)(kb * 128 + c * 16);
+            const float *W = d.p + d.off[l] + (size_t)nrow * H + k0;
             const float s = 1.f / d.inv_sw[(size_t)(l - 1) * H + nrow];  // exact: a power of two
+            const float *prev = l > 1 ? d.inv_sw + (size_t)(l - 2) * H + k0 : nullptr;
+            float v[16];
+#pragma unroll
+            for (int e = 0; e < 16; e++) v[e] = (prev ? W[e] * prev[e] : W[e]) * s;  // W_nk s_n / s'_k
             uint32_t w[4];
 #pragma unroll
-            for (int e = 0; e < 4; e++)
-                w[e] = pack_e4m3x4(W[4 * e] * s, W[4 * e + 1] * s, W[4 * e + 2] * s, W[4 * e + 3] * s);
+            for (int e = 0; e < 4; e++) w[e] = pack_e4m3x4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
             o = make_uint4(w[0], w[1], w[2], w[3]);
         }
         *reinterpret_cast<uint4 *>(img + byte) = o;
@@ -411,6 +427,8 @@ Fp8Desc make_desc(const TcModel *tc, const MlpDesc &d) {
     t.img = (const uint8_t *)tc->img;
     t.img_bytes = (uint32_t)tc->img_bytes;
     t.inv_sw = tc->scales;
+    t.bs = tc->scales + (size_t)t.NHH * t.H;
+    t.hw = tc->scales + (size_t)2 * t.NHH * t.H;
     t.p = d.p;
     for (int l = 0; l < d.L; l++) t.off[l] = d.off[l];
     return t;
@@ -430,8 +448,11 @@ size_t nb_fp8_smem_bytes(int H, int NHH) { return 1024 + CTL_BYTES + nb_fp8_img_
 
 nb_status nb_fp8_refresh(TcModel *tc, const MlpDesc &d, cudaStream_t s) {
     const Fp8Desc t = make_desc(tc, d);
-    const int rows = t.NHH * t.H;
-    fp8_scale_kernel<<<(rows * 32 + 255) / 256, 256, 0, s>>>(t, tc->scales);
+    for (int l = 1; l <= t.NHH; l++) {  // each layer's scales need the previous layer's
+        fp8_scale_kernel<<<(t.H * 32 + 255) / 256, 256, 0, s>>>(t, l, tc->scales, (float *)t.bs);
+        NB_CUDA(cudaGetLastError());
+    }
+    fp8_head_kernel<<<1, 256, 0, s>>>(t, (float *)t.hw);
     NB_CUDA(cudaGetLastError());
     const uint32_t nchunks = t.img_bytes / 16;
     pack_fp8_kernel<<<(nchunks + 255) / 256, 256, 0, s>>>(t, (uint8_t *)tc->img);

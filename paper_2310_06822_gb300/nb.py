@@ -29,7 +29,7 @@ EXPORTS = ["nb_model_create", "nb_model_destroy", "nb_model_param_count", "nb_mo
            "nb_plan_create", "nb_plan_destroy", "nb_group_create", "nb_group_destroy", "nb_group_param_count",
            "nb_group_set_params", "nb_group_get_params", "nb_group_get_grad", "nb_group_set_tau", "nb_group_get_tau",
            "nb_group_set_schedule", "nb_group_sync_schedule", "nb_group_reserve", "nb_train_step_grouped",
-           "nb_query_grouped", "nb_calibrate_grouped", "nb_cascade_bin", "nb_cascade_exact", "nb_sample", "nb_group_autotune"]
+           "nb_query_grouped", "nb_calibrate_grouped", "nb_cascade_bin", "nb_cascade_exact", "nb_sample", "nb_group_autotune", "nb_query_early_out", "nb_bits_not"]
 
 
 class NBError(RuntimeError):
@@ -106,6 +106,8 @@ def lib():
                 "nb_cascade_exact": ([P, P, P, P, i64, P, P, P, P, P], st),
                 "nb_sample": ([i32, i32, ctypes.c_uint64, i64, i64, P, P], st),
                 "nb_group_autotune": ([P, P, i32, i32, P, P, P, i32, i32, P, P, P], st),
+                "nb_query_early_out": ([P, P, P, i64, ctypes.c_float, ctypes.c_float, P, P, P], st),
+                "nb_bits_not": ([P, i64, P, P], st),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -451,6 +453,26 @@ def cascade_exact(ws: WorldScene, rays, pair_ray, off_d, rows: int, pass_bits=No
     """Stage 3: exact sphere tests of the rows (those with a pass bit, if given)."""
     _check(lib().nb_cascade_exact(ctypes.byref(ws._s), _ptr(rays), _ptr(pair_ray), _ptr(off_d), int(rows),
                                   _ptr(pass_bits), _ptr(ray_hits), _ptr(pair_hits), _ptr(stats), _stream(stream)))
+
+
+def bits_not(bits: torch.Tensor, n: int, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """The complement of n label or decision bits (nb_bits_not)."""
+    if out is None:
+        out = torch.empty_like(bits)
+    _check(lib().nb_bits_not(_ptr(bits), int(n), _ptr(out), _stream(stream)))
+    return out
+
+
+def query_early_out(early: Model, late: Model, q: torch.Tensor, margin_early: float = 0.0, margin_late: float = 0.0,
+                    out: torch.Tensor | None = None, stream=None):
+    """Decisions with the neural early-out (nb_query_early_out); returns (bits, stats)."""
+    n = q.shape[0]
+    if out is None:
+        out = torch.empty(n_words(n), dtype=torch.int32, device=q.device)
+    st = (ctypes.c_uint64 * 2)()
+    _check(lib().nb_query_early_out(early._h, late._h, _ptr(q), n, float(margin_early), float(margin_late),
+                                    _ptr(out), ctypes.byref(st), _stream(stream)))
+    return out, {"n_early_inside": int(st[0]), "n_late": int(st[1])}
 
 
 def step_stats_tensor(device="cuda") -> torch.Tensor:
