@@ -385,11 +385,12 @@ extern "C" nb_status nb_train_step(nb_model *m, const float *q, const uint32_t *
     const bool bf16 = m->train_prec == NB_BF16;
     TrainWs tw{};
     tw.G = bf16 ? nb_train_bf16_ctas(n) : nb_train_f32_ctas(d, n, sm_count());
-    const size_t need = align256((size_t)tw.G * m->P * sizeof(float)) + align256((size_t)tw.G * sizeof(float));
+    tw.stride = bf16 ? (m->P + 3) / 4 * 4 : m->P;  // BF16: 16-byte aligned slots for vector reductions
+    const size_t need = align256((size_t)tw.G * tw.stride * sizeof(float)) + align256((size_t)tw.G * sizeof(float));
     nb_status st = ensure_ws(m, need);
     if (st != NB_OK) return st;
     tw.partial = (float *)m->ws;
-    tw.loss_partial = (float *)((char *)m->ws + align256((size_t)tw.G * m->P * sizeof(float)));
+    tw.loss_partial = (float *)((char *)m->ws + align256((size_t)tw.G * tw.stride * sizeof(float)));
     st = bf16 ? nb_launch_train_bf16(&m->tc, d, q, label_bits, n, alpha, beta, tau, tw, dev_stats, s)
               : nb_launch_train_f32(d, q, label_bits, n, alpha, beta, tau, tw, dev_stats, s);
     if (st != NB_OK) return st;

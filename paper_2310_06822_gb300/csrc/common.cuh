@@ -95,9 +95,10 @@ nb_status nb_launch_recheck_grouped(const MlpDesc &d, const GammaTab &gt, const 
                                     QueryWs ws, int64_t n, cudaStream_t s);
 
 struct TrainWs {
-    float *partial;          // [G][P] per-CTA gradient partials
+    float *partial;          // [G][stride] per-CTA gradient partials
     float *loss_partial;     // [G]
     int G;                   // CTAs used
+    long long stride;        // floats between two CTAs' partials (0: P)
 };
 int nb_train_f32_ctas(const MlpDesc &d, int64_t n, int num_sms);
 nb_status nb_launch_train_f32(const MlpDesc &d, const float *q, const uint32_t *labels, int64_t n, float alpha,

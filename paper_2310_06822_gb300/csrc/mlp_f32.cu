@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(256) train_f32_kernel(MlpDesc d, const float *
 // Sum the per-CTA partials in CTA order (deterministic), keep the gradient, take one
 // Adam step (Kingma & Ba, in PyTorch's arithmetic order: denom = sqrt(v)/sqrt(c2) + eps,
 // theta -= (lr / c1) m / denom).
-__global__ void __launch_bounds__(256) adam_kernel(long long P, int G, const float *__restrict__ partial,
+__global__ void __launch_bounds__(256) adam_kernel(long long P, int G, long long stride, const float *__restrict__ partial,
                                                    const float *__restrict__ loss_partial, float inv_n,
                                                    float *__restrict__ params, float *__restrict__ m,
                                                    float *__restrict__ v, float *__restrict__ grad, float lr,
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(256) adam_kernel(long long P, int G, const flo
     }
     if (p >= P) return;
     float g = 0.f;
-    for (int c = 0; c < G; c++) g += partial[(size_t)c * P + p];
+    for (int c = 0; c < G; c++) g += partial[(size_t)c * stride + p];
     grad[p] = g;
     const float mm = b1 * m[p] + (1.f - b1) * g;
     const float vv = b2 * v[p] + (1.f - b2) * g * g;
@@ -189,8 +189,9 @@ nb_status nb_launch_adam(int64_t P, float inv_n, float *params, float *m, float 
                          float lr, float b1, float b2, float eps, float c1, float sqrt_c2, nb_step_stats *st,
                          cudaStream_t s) {
     const int64_t blocks = (P + 255) / 256;
-    adam_kernel<<<(unsigned)blocks, 256, 0, s>>>((long long)P, ws.G, ws.partial, ws.loss_partial, inv_n, params, m, v,
-                                                 grad, lr, b1, b2, eps, c1, sqrt_c2, st);
+    adam_kernel<<<(unsigned)blocks, 256, 0, s>>>((long long)P, ws.G, ws.stride > 0 ? ws.stride : (long long)P,
+                                                 ws.partial, ws.loss_partial, inv_n, params, m, v, grad, lr, b1, b2,
+                                                 eps, c1, sqrt_c2, st);
     NB_CUDA(cudaGetLastError());
     return NB_OK;
 }

@@ -11,8 +11,9 @@
 // A CTA walks tiles of 64 samples; per tile it keeps the input and every hidden layer's
 // activations (BF16) in shared memory for the backward pass, next to all layers' BF16
 // weights.  The head (width 1), the loss and the bias gradients run in FP32.
-// Weight-gradient partials go to the CTA's own slot with red.global.add; each address
-// has one owning thread per tile, so the slot's sums are in program order.
+// Weight-gradient partials go to the CTA's own slot with red.global.add (two adjacent
+// columns per vector reduction where the pair is 8-byte aligned); each address has one
+// owning thread per tile, so the slot's sums are in program order.
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -65,6 +66,10 @@ __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
 }
 __device__ __forceinline__ void red_add(float *p, float v) {
     asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+// p[0] += v0, p[1] += v1 in one vector reduction (p 8-byte aligned)
+__device__ __forceinline__ void red_add2(float *p, float v0, float v1) {
+    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(v0), "f"(v1) : "memory");
 }
 __device__ __forceinline__ float softplusf(float u) { return u > 0.f ? u + log1pf(expf(-u)) : log1pf(expf(u)); }
 __device__ __forceinline__ float sigmoidf(float u) {
@@ -162,8 +167,13 @@ __device__ __forceinline__ void tile_dw(const __nv_bfloat16 *DZ, int dp, const _
 #pragma unroll
             for (int h = 0; h < 2; h++) {
                 const int nn = n0 + gr + 8 * h;
-                if (k < Kreal) red_add(slotW + nn * Kreal + k, acc[j][2 * h]);
-                if (k + 1 < Kreal) red_add(slotW + nn * Kreal + k + 1, acc[j][2 * h + 1]);
+                float *dst = slotW + nn * Kreal + k;
+                if (k + 1 < Kreal && ((uintptr_t)dst & 7) == 0) {
+                    red_add2(dst, acc[j][2 * h], acc[j][2 * h + 1]);
+                } else {
+                    if (k < Kreal) red_add(dst, acc[j][2 * h]);
+                    if (k + 1 < Kreal) red_add(dst + 1, acc[j][2 * h + 1]);
+                }
             }
         }
     }
@@ -333,9 +343,9 @@ template <int H>
 __global__ void __launch_bounds__(256, 1)
     train_bf16_kernel(TrainDesc d, const float *__restrict__ q, const uint32_t *__restrict__ labels, long long n,
                       float alpha, float beta, float inv_n, TauF tau, float *__restrict__ partial,
-                      float *loss_partial, long long P, nb_step_stats *st) {
+                      float *loss_partial, long long stride, nb_step_stats *st) {
     bf_load<H>(d, d.img, d.p);
-    float *slot = partial + (size_t)blockIdx.x * P;
+    float *slot = partial + (size_t)blockIdx.x * stride;
     const long long ntiles = (n + TM - 1) / TM;
     float lossacc = 0.f;
     unsigned long long c_fn = 0, c_fp = 0, c_nf = 0;
@@ -472,17 +482,18 @@ nb_status nb_launch_train_bf16(TcModel *tc, const MlpDesc &d, const float *q, co
     const TrainDesc t = make_desc(tc, d);
     long long P = 0;
     for (int l = 0; l < d.L; l++) P += (long long)d.w[l + 1] * (d.w[l] + 1);
-    NB_CUDA(cudaMemsetAsync(ws.partial, 0, (size_t)ws.G * P * sizeof(float), s));
+    const long long stride = ws.stride > 0 ? ws.stride : P;  // slots 16-byte aligned when a multiple of 4
+    NB_CUDA(cudaMemsetAsync(ws.partial, 0, (size_t)ws.G * stride * sizeof(float), s));
     if (st) NB_CUDA(cudaMemsetAsync(st, 0, sizeof(nb_step_stats), s));
     const size_t smem = nb_train_bf16_smem(t.H, t.NH);
     if (t.H == 128) {
         NB_CUDA(cudaFuncSetAttribute(train_bf16_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         train_bf16_kernel<128><<<ws.G, 256, smem, s>>>(t, q, labels, (long long)n, alpha, beta, 1.0f / (float)n, tau,
-                                                       ws.partial, ws.loss_partial, P, st);
+                                                       ws.partial, ws.loss_partial, stride, st);
     } else {
         NB_CUDA(cudaFuncSetAttribute(train_bf16_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         train_bf16_kernel<64><<<ws.G, 256, smem, s>>>(t, q, labels, (long long)n, alpha, beta, 1.0f / (float)n, tau,
-                                                      ws.partial, ws.loss_partial, P, st);
+                                                      ws.partial, ws.loss_partial, stride, st);
     }
     NB_CUDA(cudaGetLastError());
     return NB_OK;
