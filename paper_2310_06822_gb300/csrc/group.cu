@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(256)
                        const long long *__restrict__ offsets, const float *__restrict__ q,
                        const uint32_t *__restrict__ labels, float alpha_arg, const float *sched_alpha,
                        const int *d_step, int sched_T, float beta, const TauF *taus, float *__restrict__ partial,
-                       float *loss_partial, nb_step_stats *st) {
+                       long long S, float *loss_partial, nb_step_stats *st) {
     extern __shared__ float smem[];
     __shared__ float zs[TM], dz[TM], ls[TM];
     const int t = threadIdx.x;
@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(256)
         MlpDesc dd = d;
         dd.p = d.p + (size_t)w.obj * P;
         const float inv_n = 1.0f / (float)(offsets[w.obj + 1] - offsets[w.obj]);
-        float *slot = partial + (size_t)it * P;
+        float *slot = partial + (size_t)it * S;
         float lossacc = 0.f;
         for (long long base = w.row0; base < w.row1; base += TM) {
             const int rows = (int)min((long long)TM, w.row1 - base);
@@ -83,7 +83,8 @@ __global__ void __launch_bounds__(256)
 
 // Per object: sum its items' partials in item order, keep the gradient, one Adam step.
 __global__ void __launch_bounds__(256)
-    group_adam_kernel(long long P, int n_objects, const int *__restrict__ obj_items, const float *__restrict__ partial,
+    group_adam_kernel(long long P, long long S, int n_objects, const int *__restrict__ obj_items,
+                      const float *__restrict__ partial,
                       float *__restrict__ params, float *__restrict__ m, float *__restrict__ v,
                       float *__restrict__ grad, float lr, float b1, float b2, float eps, float c1_arg,
                       float sqrt_c2_arg, const float *sched_c1, const float *sched_sqrt_c2, const int *d_step,
@@ -99,7 +100,7 @@ __global__ void __launch_bounds__(256)
         sqrt_c2 = sched_sqrt_c2[t];
     }
     float g = 0.f;
-    for (int it = obj_items[o]; it < obj_items[o + 1]; it++) g += partial[(size_t)it * P + p];
+    for (int it = obj_items[o]; it < obj_items[o + 1]; it++) g += partial[(size_t)it * S + p];
     grad[idx] = g;
     const float mm = b1 * m[idx] + (1.f - b1) * g;
     const float vv = b2 * v[idx] + (1.f - b2) * g * g;
@@ -177,7 +178,7 @@ nb_status group_train_launch(const nb_group *g, const nb_plan *pl, const float *
     MlpDesc d = nb_group_desc(g);
     k<<<grid, 256, smem, s>>>(d, g->P, pl->items, pl->n_items, pl->offsets, q, labels, alpha,
                               sched ? g->sched_alpha : nullptr, g->d_step, g->sched_T, beta, g->d_tau, partial,
-                              loss_partial, st);
+                              (long long)g->S, loss_partial, st);
     NB_CUDA(cudaGetLastError());
     return NB_OK;
 }
@@ -337,6 +338,7 @@ extern "C" nb_status nb_group_create(const int32_t *widths, int32_t n_layers, in
         o += (int64_t)widths[l + 1] * (widths[l] + 1);
     }
     g->P = o;
+    g->S = (o + 3) / 4 * 4;
     g->infer_prec = infer_prec;
     g->train_prec = train_prec;
     g->tau.assign(n_objects, 0.0);
@@ -474,7 +476,7 @@ extern "C" nb_status nb_group_set_schedule(nb_group *g, const float *host_alpha,
 extern "C" nb_status nb_group_reserve(nb_group *g, const nb_plan *pl) {
     if (!g || !pl) return nb_fail(NB_EINVAL, "nb_group_reserve: null pointer");
     if (pl->n_objects != g->n_objects) return nb_fail(NB_EINVAL, "nb_group_reserve: plan and group differ in objects");
-    const size_t train = align256((size_t)pl->n_items * g->P * sizeof(float)) + align256((size_t)pl->n_items * sizeof(float));
+    const size_t train = align256((size_t)pl->n_items * g->S * sizeof(float)) + align256((size_t)pl->n_items * sizeof(float));
     const size_t query = 256 + 2 * align256((size_t)pl->n_rows * sizeof(unsigned));
     return ensure_ws(g, train > query ? train : query);
 }
@@ -493,12 +495,12 @@ extern "C" nb_status nb_train_step_grouped(nb_group *g, const nb_plan *pl, const
     nb_status st = nb_group_reserve(g, pl);
     if (st != NB_OK) return st;
     float *partial = (float *)g->ws;
-    float *loss_partial = (float *)((char *)g->ws + align256((size_t)pl->n_items * g->P * sizeof(float)));
-    NB_CUDA(cudaMemsetAsync(partial, 0, (size_t)pl->n_items * g->P * sizeof(float), s));
+    float *loss_partial = (float *)((char *)g->ws + align256((size_t)pl->n_items * g->S * sizeof(float)));
+    NB_CUDA(cudaMemsetAsync(partial, 0, (size_t)pl->n_items * g->S * sizeof(float), s));
     if (dev_stats) NB_CUDA(cudaMemsetAsync(dev_stats, 0, sizeof(nb_step_stats), s));
     const MlpDesc d = nb_group_desc(g);
     if (g->train_prec == NB_BF16)
-        st = nb_launch_train_bf16_group(&g->tc, d, g->P, pl, q, label_bits, alpha, sched ? g->sched_alpha : nullptr,
+        st = nb_launch_train_bf16_group(&g->tc, d, g->P, g->S, pl, q, label_bits, alpha, sched ? g->sched_alpha : nullptr,
                                         g->d_step, g->sched_T, beta, g->d_tau, partial, loss_partial, dev_stats, s);
     else switch (nj_for(d.maxw)) {
     case 1: st = group_train_launch<1, 32>(g, pl, q, label_bits, alpha, sched, beta, partial, loss_partial, dev_stats, s); break;
@@ -516,7 +518,7 @@ extern "C" nb_status nb_train_step_grouped(nb_group *g, const nb_plan *pl, const
     }
     const long long total = (long long)g->n_objects * g->P;
     group_adam_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
-        g->P, g->n_objects, pl->obj_items, partial, g->params, g->m, g->v, g->grad, g->lr, g->b1, g->b2, g->eps, c1,
+        g->P, g->S, g->n_objects, pl->obj_items, partial, g->params, g->m, g->v, g->grad, g->lr, g->b1, g->b2, g->eps, c1,
         sc2, sched ? g->sched_c1 : nullptr, sched ? g->sched_sqrt_c2 : nullptr, g->d_step, g->sched_T);
     NB_CUDA(cudaGetLastError());
     group_loss_kernel<<<1, 256, 0, s>>>(g->n_objects, pl->obj_items, pl->offsets, loss_partial, dev_stats,

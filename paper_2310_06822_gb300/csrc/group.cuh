@@ -31,6 +31,7 @@ struct nb_group {
     int widths[NB_MAXL + 1] = {0};
     int off[NB_MAXL] = {0};
     int64_t P = 0;
+    int64_t S = 0;                       // floats between two work items' gradient partials (P rounded up to 4)
     int infer_prec = NB_F32, train_prec = NB_F32;
     float *params = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;  // [n_objects][P]
     float *paramsT = nullptr;            // [n_objects][P], weights transposed (re-check)
@@ -61,7 +62,8 @@ nb_status nb_tc_group_query(TcModel *tc, const MlpDesc &d, int64_t P, const nb_p
 // BF16 tensor-core grouped training (train_bf16.cu)
 nb_status nb_train_bf16_group_init(TcModel *tc, const MlpDesc &d, int n_objects);
 nb_status nb_train_bf16_group_refresh(TcModel *tc, const MlpDesc &d, int n_objects, cudaStream_t s);
-nb_status nb_launch_train_bf16_group(TcModel *tc, const MlpDesc &d, long long P, const nb_plan *pl, const float *q,
+nb_status nb_launch_train_bf16_group(TcModel *tc, const MlpDesc &d, long long P, long long S, const nb_plan *pl,
+                                     const float *q,
                                      const uint32_t *labels, float alpha, const float *sched_alpha, const int *d_step,
                                      int sched_T, float beta, const TauF *taus, float *partial, float *loss_partial,
                                      nb_step_stats *st, cudaStream_t s);

@@ -11,8 +11,8 @@
 // A CTA walks tiles of 64 samples; per tile it keeps the input and every hidden layer's
 // activations (BF16) in shared memory for the backward pass, next to all layers' BF16
 // weights.  The head (width 1), the loss and the bias gradients run in FP32.
-// Weight-gradient partials go to the CTA's own slot with red.global.add (two adjacent
-// columns per vector reduction where the pair is 8-byte aligned); each address has one
+// Weight-gradient partials go to the CTA's own slot with red.global.add (four adjacent
+// columns per vector reduction where they are 16-byte aligned); each address has one
 // owning thread per tile, so the slot's sums are in program order.
 #include <cuda_bf16.h>
 #include <math.h>
@@ -67,9 +67,10 @@ __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
 __device__ __forceinline__ void red_add(float *p, float v) {
     asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
 }
-// p[0] += v0, p[1] += v1 in one vector reduction (p 8-byte aligned)
-__device__ __forceinline__ void red_add2(float *p, float v0, float v1) {
-    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(v0), "f"(v1) : "memory");
+// p[0..3] += v0..v3 in one vector reduction (p 16-byte aligned)
+__device__ __forceinline__ void red_add4(float *p, float v0, float v1, float v2, float v3) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v0), "f"(v1), "f"(v2), "f"(v3)
+                 : "memory");
 }
 __device__ __forceinline__ float softplusf(float u) { return u > 0.f ? u + log1pf(expf(-u)) : log1pf(expf(u)); }
 __device__ __forceinline__ float sigmoidf(float u) {
@@ -160,20 +161,30 @@ __device__ __forceinline__ void tile_dw(const __nv_bfloat16 *DZ, int dp, const _
                 if (8 * (j + 1) < cw) mma_bf16(acc[j + 1], a0, a1, a2, a3, b2, b3);
             }
         }
+        // lanes 2i and 2i+1 hold columns k, k+1 and k+2, k+3 of rows gr and gr + 8: one
+        // exchange gives the even lane four columns of row gr and the odd lane four of row
+        // gr + 8, added with one vector reduction where the four are 16-byte aligned
+        const bool odd = lane & 1;
 #pragma unroll
         for (int j = 0; j < 8; j++) {
             if (8 * j >= cw) break;
-            const int k = kbeg + kc + 8 * j + gc;
+            const float s0 = odd ? acc[j][0] : acc[j][2], s1 = odd ? acc[j][1] : acc[j][3];
+            const float r0 = __shfl_xor_sync(FULL, s0, 1), r1 = __shfl_xor_sync(FULL, s1, 1);
+            const int k4 = kbeg + kc + 8 * j + (gc & ~2);  // first of the four columns
+            const int nn = n0 + gr + (odd ? 8 : 0);
+            float v[4];
+            if (odd) {
+                v[0] = r0; v[1] = r1; v[2] = acc[j][2]; v[3] = acc[j][3];
+            } else {
+                v[0] = acc[j][0]; v[1] = acc[j][1]; v[2] = r0; v[3] = r1;
+            }
+            float *dst = slotW + nn * Kreal + k4;
+            if (k4 + 3 < Kreal && ((uintptr_t)dst & 15) == 0) {
+                red_add4(dst, v[0], v[1], v[2], v[3]);
+            } else {
 #pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const int nn = n0 + gr + 8 * h;
-                float *dst = slotW + nn * Kreal + k;
-                if (k + 1 < Kreal && ((uintptr_t)dst & 7) == 0) {
-                    red_add2(dst, acc[j][2 * h], acc[j][2 * h + 1]);
-                } else {
-                    if (k < Kreal) red_add(dst, acc[j][2 * h]);
-                    if (k + 1 < Kreal) red_add(dst + 1, acc[j][2 * h + 1]);
-                }
+                for (int u = 0; u < 4; u++)
+                    if (k4 + u < Kreal) red_add(dst + u, v[u]);
             }
         }
     }
@@ -367,7 +378,7 @@ __global__ void __launch_bounds__(256, 1)
                             const long long *__restrict__ offsets, const float *__restrict__ q,
                             const uint32_t *__restrict__ labels, float alpha_arg, const float *sched_alpha,
                             const int *d_step, int sched_T, float beta, const TauF *taus, float *__restrict__ partial,
-                            float *loss_partial, long long P, nb_step_stats *st) {
+                            float *loss_partial, long long P, long long S, nb_step_stats *st) {
     float alpha = alpha_arg;
     if (sched_alpha) alpha = sched_alpha[min(*d_step, sched_T - 1)];
     unsigned long long c_fn = 0, c_fp = 0, c_nf = 0;
@@ -382,7 +393,7 @@ __global__ void __launch_bounds__(256, 1)
             cur = w.obj;
         }
         const float inv_n = 1.0f / (float)(offsets[w.obj + 1] - offsets[w.obj]);
-        float *slot = partial + (size_t)it * P;
+        float *slot = partial + (size_t)it * S;
         float lossacc = 0.f;
         for (long long base = w.row0; base < w.row1; base += TM) {
             const int rows = (int)min((long long)TM, w.row1 - base);
@@ -521,7 +532,8 @@ nb_status nb_train_bf16_group_refresh(TcModel *tc, const MlpDesc &d, int n_objec
     return NB_OK;
 }
 
-nb_status nb_launch_train_bf16_group(TcModel *tc, const MlpDesc &d, long long P, const nb_plan *pl, const float *q,
+nb_status nb_launch_train_bf16_group(TcModel *tc, const MlpDesc &d, long long P, long long S, const nb_plan *pl,
+                                     const float *q,
                                      const uint32_t *labels, float alpha, const float *sched_alpha, const int *d_step,
                                      int sched_T, float beta, const TauF *taus, float *partial, float *loss_partial,
                                      nb_step_stats *st, cudaStream_t s) {
@@ -536,13 +548,13 @@ nb_status nb_launch_train_bf16_group(TcModel *tc, const MlpDesc &d, long long P,
                                      (int)smem));
         train_bf16_group_kernel<128><<<grid, 256, smem, s>>>(t, img_elems, pl->items, pl->n_items, pl->offsets, q,
                                                              labels, alpha, sched_alpha, d_step, sched_T, beta, taus,
-                                                             partial, loss_partial, P, st);
+                                                             partial, loss_partial, P, S, st);
     } else {
         NB_CUDA(cudaFuncSetAttribute(train_bf16_group_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
         train_bf16_group_kernel<64><<<grid, 256, smem, s>>>(t, img_elems, pl->items, pl->n_items, pl->offsets, q,
                                                             labels, alpha, sched_alpha, d_step, sched_T, beta, taus,
-                                                            partial, loss_partial, P, st);
+                                                            partial, loss_partial, P, S, st);
     }
     NB_CUDA(cudaGetLastError());
     return NB_OK;
