@@ -39,7 +39,7 @@ nb_status nb_tc_query(TcModel *tc, const MlpDesc &d, const float *q, int64_t n, 
 // BF16 tensor-core training step (train_bf16.cu)
 nb_status nb_train_bf16_check(const MlpDesc &d);
 size_t nb_train_bf16_img_bytes(const MlpDesc &d);
-size_t nb_train_bf16_smem(int H, int NH);
+size_t nb_train_bf16_smem(int H, int NH, long long P);
 nb_status nb_train_bf16_refresh(TcModel *tc, const MlpDesc &d, cudaStream_t s);
 int nb_train_bf16_ctas(int64_t n);
 nb_status nb_launch_train_bf16(TcModel *tc, const MlpDesc &d, const float *q, const uint32_t *labels, int64_t n,

@@ -132,7 +132,7 @@ __device__ __forceinline__ void tile_gemm(const __nv_bfloat16 *X, int xp, int K,
 
 // slot[n][k] += sum_m DZ[m][n] A[m][k] for n < H, k < Kreal (weight gradient of one layer).
 // Warps: n-blocks of 16 x (128 / H) column groups.
-template <int H>
+template <int H, bool SACC>
 __device__ __forceinline__ void tile_dw(const __nv_bfloat16 *DZ, int dp, const __nv_bfloat16 *A, int ap, int Kp,
                                         int Kreal, float *slotW) {
     constexpr int NB = H / 16, KG = 8 / NB;  // n-blocks, column groups
@@ -179,7 +179,11 @@ __device__ __forceinline__ void tile_dw(const __nv_bfloat16 *DZ, int dp, const _
                 v[0] = acc[j][0]; v[1] = acc[j][1]; v[2] = r0; v[3] = r1;
             }
             float *dst = slotW + nn * Kreal + k4;
-            if (k4 + 3 < Kreal && ((uintptr_t)dst & 15) == 0) {
+            if (SACC) {  // the CTA's accumulator in shared memory: this lane owns these four
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+                    if (k4 + u < Kreal) dst[u] += v[u];
+            } else if (k4 + 3 < Kreal && ((uintptr_t)dst & 15) == 0) {
                 red_add4(dst, v[0], v[1], v[2], v[3]);
             } else {
 #pragma unroll
@@ -202,10 +206,12 @@ __device__ __forceinline__ void tile_dw(const __nv_bfloat16 *DZ, int dp, const _
     float *bias = reinterpret_cast<float *>(dz1 + TM * HP);                                            \
     float *head = bias + NH * H;                                                                       \
     float *zs = head + H + 4, *gs = zs + TM, *ls = gs + TM;                                            \
+    float *sacc = ls + TM; /* width 64: the CTA's gradient accumulator */                              \
     auto W_l = [&](int l) { return l == 0 ? Ws : Ws + H * XP + (size_t)(l - 1) * H * HP; };          \
     auto A_l = [&](int l) { return l == 0 ? act : act + TM * XP + (size_t)(l - 1) * TM * HP; };      \
     (void)HP;                                                                                          \
-    (void)XP
+    (void)XP;                                                                                          \
+    (void)sacc
 
 // weights of one network (bf16 image -> padded rows), its biases and head; ends synchronised
 template <int H>
@@ -237,7 +243,7 @@ __device__ __forceinline__ void bf_load(const TrainDesc &d, const __nv_bfloat16 
 
 // one tile of TM samples starting at row base: forward, loss, backward, gradient partials
 // into slot; ends synchronised
-template <int H>
+template <int H, bool SACC>
 __device__ __forceinline__ void bf_tile(const TrainDesc &d, const float *__restrict__ q,
                                         const uint32_t *__restrict__ labels, long long base, int rows, float alpha,
                                         float beta, float inv_n, TauF tau, float *__restrict__ slot, float &lossacc,
@@ -314,7 +320,7 @@ __device__ __forceinline__ void bf_tile(const TrainDesc &d, const float *__restr
         const int K = l == 0 ? d.in : H, kp = kpad(H, l);
         const __nv_bfloat16 *Al = A_l(l);
         float *gW = slot + d.off[l];
-        tile_dw<H>(dzc, HP, Al, l == 0 ? XP : HP, kp, K, gW);
+        tile_dw<H, SACC>(dzc, HP, Al, l == 0 ? XP : HP, kp, K, gW);
         for (int nn = t; nn < H; nn += blockDim.x) {
             float s = 0.f;
             for (int m = 0; m < TM; m++) s += __bfloat162float(dzc[m * HP + nn]);
@@ -328,6 +334,32 @@ __device__ __forceinline__ void bf_tile(const TrainDesc &d, const float *__restr
             dzc = dzn;
             dzn = tp;
         }
+    }
+    __syncthreads();
+}
+
+template <int H>
+__device__ __forceinline__ float *bf_sacc_ptr(const TrainDesc &d) {
+    NB_BF_SMEM;
+    (void)Ws; (void)dz0; (void)dz1; (void)bias; (void)zs; (void)gs; (void)W_l; (void)A_l; (void)t;
+    return sacc;
+}
+// width 64: zero the shared gradient accumulator / store it into a global slot and zero it
+template <int H>
+__device__ __forceinline__ void bf_sacc_zero(const TrainDesc &d, long long P) {
+    NB_BF_SMEM;
+    (void)Ws; (void)dz0; (void)dz1; (void)bias; (void)zs; (void)gs; (void)W_l; (void)A_l;
+    for (long long e = t; e < P; e += blockDim.x) sacc[e] = 0.f;
+    __syncthreads();
+}
+template <int H>
+__device__ __forceinline__ void bf_sacc_flush(const TrainDesc &d, long long P, float *__restrict__ slot) {
+    NB_BF_SMEM;
+    (void)Ws; (void)dz0; (void)dz1; (void)bias; (void)zs; (void)gs; (void)W_l; (void)A_l;
+    __syncthreads();
+    for (long long e = t; e < P; e += blockDim.x) {
+        slot[e] = sacc[e];
+        sacc[e] = 0.f;
     }
     __syncthreads();
 }
@@ -354,17 +386,21 @@ template <int H>
 __global__ void __launch_bounds__(256, 1)
     train_bf16_kernel(TrainDesc d, const float *__restrict__ q, const uint32_t *__restrict__ labels, long long n,
                       float alpha, float beta, float inv_n, TauF tau, float *__restrict__ partial,
-                      float *loss_partial, long long stride, nb_step_stats *st) {
+                      float *loss_partial, long long stride, long long P, nb_step_stats *st) {
+    constexpr bool SACC = H == 64;  // the gradient accumulator fits in shared memory
     bf_load<H>(d, d.img, d.p);
     float *slot = partial + (size_t)blockIdx.x * stride;
+    if (SACC) bf_sacc_zero<H>(d, P);
     const long long ntiles = (n + TM - 1) / TM;
     float lossacc = 0.f;
     unsigned long long c_fn = 0, c_fp = 0, c_nf = 0;
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const long long base = tile * TM;
         const int rows = (int)min((long long)TM, n - base);
-        bf_tile<H>(d, q, labels, base, rows, alpha, beta, inv_n, tau, slot, lossacc, c_fn, c_fp, c_nf);
+        bf_tile<H, SACC>(d, q, labels, base, rows, alpha, beta, inv_n, tau, SACC ? bf_sacc_ptr<H>(d) : slot,
+                         lossacc, c_fn, c_fp, c_nf);
     }
+    if (SACC) bf_sacc_flush<H>(d, P, slot);
     if (threadIdx.x == 0) loss_partial[blockIdx.x] = lossacc;
     bf_counters(st, c_fn, c_fp, c_nf);
 }
@@ -379,10 +415,12 @@ __global__ void __launch_bounds__(256, 1)
                             const uint32_t *__restrict__ labels, float alpha_arg, const float *sched_alpha,
                             const int *d_step, int sched_T, float beta, const TauF *taus, float *__restrict__ partial,
                             float *loss_partial, long long P, long long S, nb_step_stats *st) {
+    constexpr bool SACC = H == 64;  // the gradient accumulator fits in shared memory
     float alpha = alpha_arg;
     if (sched_alpha) alpha = sched_alpha[min(*d_step, sched_T - 1)];
     unsigned long long c_fn = 0, c_fp = 0, c_nf = 0;
     int cur = -1;
+    if (SACC) bf_sacc_zero<H>(d, P);
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
         const PlanItem w = items[it];
         TrainDesc dd = d;
@@ -397,8 +435,10 @@ __global__ void __launch_bounds__(256, 1)
         float lossacc = 0.f;
         for (long long base = w.row0; base < w.row1; base += TM) {
             const int rows = (int)min((long long)TM, w.row1 - base);
-            bf_tile<H>(dd, q, labels, base, rows, alpha, beta, inv_n, taus[w.obj], slot, lossacc, c_fn, c_fp, c_nf);
+            bf_tile<H, SACC>(dd, q, labels, base, rows, alpha, beta, inv_n, taus[w.obj],
+                             SACC ? bf_sacc_ptr<H>(dd) : slot, lossacc, c_fn, c_fp, c_nf);
         }
+        if (SACC) bf_sacc_flush<H>(dd, P, slot);  // one store per parameter per item
         if (threadIdx.x == 0) loss_partial[it] = lossacc;
     }
     bf_counters(st, c_fn, c_fp, c_nf);
@@ -448,12 +488,13 @@ int num_sms() {
 
 }  // namespace
 
-size_t nb_train_bf16_smem(int H, int NH) {
+size_t nb_train_bf16_smem(int H, int NH, long long P) {
     const size_t HP = H + PAD, XP = K0 + PAD;
     const size_t w = (size_t)H * XP + (size_t)(NH - 1) * H * HP;
     const size_t a = (size_t)TM * XP + (size_t)NH * TM * HP;
     const size_t dz = 2 * (size_t)TM * HP;
-    return (w + a + dz) * 2 + ((size_t)NH * H + H + 4 + 3 * TM) * 4 + 64;
+    const size_t acc = H == 64 ? (size_t)P : 0;  // width 64: the gradient accumulator
+    return (w + a + dz) * 2 + ((size_t)NH * H + H + 4 + 3 * TM + acc) * 4 + 64;
 }
 
 nb_status nb_train_bf16_check(const MlpDesc &d) {
@@ -466,7 +507,9 @@ nb_status nb_train_bf16_check(const MlpDesc &d) {
     int dev = 0, maxsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (nb_train_bf16_smem(H, NH) > (size_t)maxsm)
+    long long P = 0;
+    for (int l = 0; l < d.L; l++) P += (long long)d.w[l + 1] * (d.w[l] + 1);
+    if (nb_train_bf16_smem(H, NH, P) > (size_t)maxsm)
         return nb_fail(NB_EUNSUPPORTED, "BF16 training: the network does not fit in shared memory");
     return NB_OK;
 }
@@ -496,15 +539,15 @@ nb_status nb_launch_train_bf16(TcModel *tc, const MlpDesc &d, const float *q, co
     const long long stride = ws.stride > 0 ? ws.stride : P;  // slots 16-byte aligned when a multiple of 4
     NB_CUDA(cudaMemsetAsync(ws.partial, 0, (size_t)ws.G * stride * sizeof(float), s));
     if (st) NB_CUDA(cudaMemsetAsync(st, 0, sizeof(nb_step_stats), s));
-    const size_t smem = nb_train_bf16_smem(t.H, t.NH);
+    const size_t smem = nb_train_bf16_smem(t.H, t.NH, P);
     if (t.H == 128) {
         NB_CUDA(cudaFuncSetAttribute(train_bf16_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         train_bf16_kernel<128><<<ws.G, 256, smem, s>>>(t, q, labels, (long long)n, alpha, beta, 1.0f / (float)n, tau,
-                                                       ws.partial, ws.loss_partial, stride, st);
+                                                       ws.partial, ws.loss_partial, stride, P, st);
     } else {
         NB_CUDA(cudaFuncSetAttribute(train_bf16_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         train_bf16_kernel<64><<<ws.G, 256, smem, s>>>(t, q, labels, (long long)n, alpha, beta, 1.0f / (float)n, tau,
-                                                      ws.partial, ws.loss_partial, stride, st);
+                                                      ws.partial, ws.loss_partial, stride, P, st);
     }
     NB_CUDA(cudaGetLastError());
     return NB_OK;
@@ -539,7 +582,7 @@ nb_status nb_launch_train_bf16_group(TcModel *tc, const MlpDesc &d, long long P,
                                      nb_step_stats *st, cudaStream_t s) {
     const TrainDesc t = make_desc(tc, d);
     const long long img_elems = (long long)train_img_elems(t.H, t.NH);
-    const size_t smem = nb_train_bf16_smem(t.H, t.NH);
+    const size_t smem = nb_train_bf16_smem(t.H, t.NH, P);
     int grid = num_sms();
     if (grid > pl->n_items) grid = pl->n_items;
     if (grid < 1) return NB_OK;
