@@ -11,7 +11,7 @@ FP32 / extended-precision re-check of the margin band), inputs resident in HBM (
 per step, more than the 129 MB L2, so no flush is needed); value = rays/s over all ranks.
 
 Other configurations (--config): c1 (2D points, plain FP32), c3 (3D boxes and planes,
-256 spheres, 256-wide networks, FP8 E4M3 inference), c2e (3D points behind the neural
+256 spheres, 256-wide networks, 20k BF16 training steps, FP8 E4M3 inference), c2e (3D points behind the neural
 early-out of Sec. 3.3), c4 (256 objects of moving
 spheres, 4D points, grouped training under a CUDA graph and grouped queries), c5 (1024
 objects, 64M world rays through the learned-culler cascade, against box + exact).
@@ -332,15 +332,15 @@ def run_c3(args):
     torch, dev = ctx.torch, ctx.dev
     sc = I.make_scene(1003, 256, 3, R_LO, R_HI)
     shape = nb.Shape(sc, dev)
-    T = args.train_steps if args.train_steps != TRAIN_STEPS else 2000
+    T = args.train_steps
     B = 131072
     n_eval = args.n_eval if args.n_eval != N_EVAL else (64 << 20)
     res = {}
     for kind, w0 in ((I.BOX3, 6), (I.PLANE3, 4)):
         widths = [w0, 256, 256, 256, 256, 1]
-        # FP32 training (the BF16 training kernel holds at most 128-wide layers), a fresh
-        # GPU-sampled and labelled batch per step
-        tr = nb.Model(widths)
+        # BF16 tensor-core training (weights streamed per half layer), a fresh GPU-sampled
+        # and labelled batch per step
+        tr = nb.Model(widths, infer_prec="f32", train_prec="bf16")
         tr.set_params(I.init_params(4003 + kind, widths))
         qb = torch.empty((B, w0), dtype=torch.float32, device=dev)
         yb = torch.empty(nb.n_words(B), dtype=torch.int32, device=dev)
@@ -385,13 +385,16 @@ def run_c3(args):
     pl = res[I.PLANE3]
     pl_ms = ctx.time_ms(lambda: pl["f8"].query(pl["eq"], margin=pl["margin"], out=pl["out"]), max(3, args.steps // 4))
     pl32_ms = ctx.time_ms(lambda: pl["f32"].query(pl["eq"], margin=1e-2, out=pl["out"]), 2)
-    tr_ms = {}
+    tr_ms, tr32_ms = {}, {}
     for kind, r in res.items():
         qb = nb.sample(kind, B, 9)
         yb = nb.label(shape, kind, qb)
-        m = nb.Model(r["widths"])
+        m = nb.Model(r["widths"], infer_prec="f32", train_prec="bf16")
         m.set_params(r["params"])
-        tr_ms[kind] = ctx.time_ms(lambda: m.train_step(qb, yb, 50.0), 10)
+        tr_ms[kind] = ctx.time_ms(lambda: m.train_step(qb, yb, 50.0), 20)
+        m32 = nb.Model(r["widths"])
+        m32.set_params(r["params"])
+        tr32_ms[kind] = ctx.time_ms(lambda: m32.train_step(qb, yb, 50.0), 3)
     if ctx.rank != 0:
         return ctx.emit(None)
     pk, pk_kind = peaks()
@@ -408,19 +411,21 @@ def run_c3(args):
                 "band": {"flagged": r["qst"]["n_flagged"], "resolved_f32": r["qst"]["n_resolved_f32"],
                          "resolved_ff": r["qst"]["n_resolved_ff"], "unresolved": r["qst"]["n_unresolved"]},
                 "fp8_queries_per_s": n_eval / (q_ms / 1000.0), "fp32_plain_queries_per_s": n_eval / (q32_ms / 1000.0),
-                "train_s_fp32": r["train_s"]}
+                "train_s_bf16": r["train_s"]}
 
     line = base_line(ctx, "neural-bound queries/s at 0 FN (3D boxes, FP8 E4M3 tcgen05 forward + FP32 re-check)",
                      value, "queries/s", ms, args.steps, args.warmup, "e4m3 (fp8 operands, fp32 accumulate)",
                      {"workload": "3D box and plane queries: 256-sphere union, MLP in->256x4->1, FP8 inference, "
                                   "64M eval queries (configs[2])", "n_eval": n_eval, "batch": B, "train_steps": T,
-                      "train_precision": "fp32 (BF16 training kernel limited to width 128)",
+                      "train_precision": "bf16 tensor cores (weights streamed per half layer), fp32 master weights",
                       "l2": f"inputs {n_eval * 24 >> 20} MB per step > L2"},
                      clocks, args.steps * 3)
     line.update({"box": summary(box, ms, f32_ms), "plane": summary(pl, pl_ms, pl32_ms),
                  "speedup_vs_fp32_plain": f32_ms / ms,
-                 "train_samples_per_s_fp32": {"box": B / (tr_ms[I.BOX3] / 1000.0),
-                                              "plane": B / (tr_ms[I.PLANE3] / 1000.0)},
+                 "train_samples_per_s": {"bf16_box": B / (tr_ms[I.BOX3] / 1000.0),
+                                         "bf16_plane": B / (tr_ms[I.PLANE3] / 1000.0),
+                                         "fp32_box": B / (tr32_ms[I.BOX3] / 1000.0),
+                                         "fp32_plane": B / (tr32_ms[I.PLANE3] / 1000.0)},
                  "roofline": {"kernel": "fwd_fp8_kernel (tcgen05 kind::f8f6f4)", "bound": "tensor",
                               "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                               "traffic": None, "peak_kind": f"{pk_kind} bf16 burst x 2 (E4M3 nominal ratio)",

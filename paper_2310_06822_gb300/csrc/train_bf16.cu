@@ -132,7 +132,7 @@ __device__ __forceinline__ void tile_gemm(const __nv_bfloat16 *X, int xp, int K,
 
 // slot[n][k] += sum_m DZ[m][n] A[m][k] for n < H, k < Kreal (weight gradient of one layer).
 // Warps: n-blocks of 16 x (128 / H) column groups.
-template <int H, bool SACC>
+template <int H>
 __device__ __forceinline__ void tile_dw(const __nv_bfloat16 *DZ, int dp, const __nv_bfloat16 *A, int ap, int Kp,
                                         int Kreal, float *slotW) {
     constexpr int NB = H / 16, KG = 8 / NB;  // n-blocks, column groups
@@ -179,11 +179,7 @@ __device__ __forceinline__ void tile_dw(const __nv_bfloat16 *DZ, int dp, const _
                 v[0] = acc[j][0]; v[1] = acc[j][1]; v[2] = r0; v[3] = r1;
             }
             float *dst = slotW + nn * Kreal + k4;
-            if (SACC) {  // the CTA's accumulator in shared memory: this lane owns these four
-#pragma unroll
-                for (int u = 0; u < 4; u++)
-                    if (k4 + u < Kreal) dst[u] += v[u];
-            } else if (k4 + 3 < Kreal && ((uintptr_t)dst & 15) == 0) {
+            if (k4 + 3 < Kreal && ((uintptr_t)dst & 15) == 0) {
                 red_add4(dst, v[0], v[1], v[2], v[3]);
             } else {
 #pragma unroll
@@ -206,12 +202,10 @@ __device__ __forceinline__ void tile_dw(const __nv_bfloat16 *DZ, int dp, const _
     float *bias = reinterpret_cast<float *>(dz1 + TM * HP);                                            \
     float *head = bias + NH * H;                                                                       \
     float *zs = head + H + 4, *gs = zs + TM, *ls = gs + TM;                                            \
-    float *sacc = ls + TM; /* width 64: the CTA's gradient accumulator */                              \
     auto W_l = [&](int l) { return l == 0 ? Ws : Ws + H * XP + (size_t)(l - 1) * H * HP; };          \
     auto A_l = [&](int l) { return l == 0 ? act : act + TM * XP + (size_t)(l - 1) * TM * HP; };      \
     (void)HP;                                                                                          \
-    (void)XP;                                                                                          \
-    (void)sacc
+    (void)XP
 
 // weights of one network (bf16 image -> padded rows), its biases and head; ends synchronised
 template <int H>
@@ -243,7 +237,7 @@ __device__ __forceinline__ void bf_load(const TrainDesc &d, const __nv_bfloat16 
 
 // one tile of TM samples starting at row base: forward, loss, backward, gradient partials
 // into slot; ends synchronised
-template <int H, bool SACC>
+template <int H>
 __device__ __forceinline__ void bf_tile(const TrainDesc &d, const float *__restrict__ q,
                                         const uint32_t *__restrict__ labels, long long base, int rows, float alpha,
                                         float beta, float inv_n, TauF tau, float *__restrict__ slot, float &lossacc,
@@ -320,7 +314,7 @@ __device__ __forceinline__ void bf_tile(const TrainDesc &d, const float *__restr
         const int K = l == 0 ? d.in : H, kp = kpad(H, l);
         const __nv_bfloat16 *Al = A_l(l);
         float *gW = slot + d.off[l];
-        tile_dw<H, SACC>(dzc, HP, Al, l == 0 ? XP : HP, kp, K, gW);
+        tile_dw<H>(dzc, HP, Al, l == 0 ? XP : HP, kp, K, gW);
         for (int nn = t; nn < H; nn += blockDim.x) {
             float s = 0.f;
             for (int m = 0; m < TM; m++) s += __bfloat162float(dzc[m * HP + nn]);
@@ -334,32 +328,6 @@ __device__ __forceinline__ void bf_tile(const TrainDesc &d, const float *__restr
             dzc = dzn;
             dzn = tp;
         }
-    }
-    __syncthreads();
-}
-
-template <int H>
-__device__ __forceinline__ float *bf_sacc_ptr(const TrainDesc &d) {
-    NB_BF_SMEM;
-    (void)Ws; (void)dz0; (void)dz1; (void)bias; (void)zs; (void)gs; (void)W_l; (void)A_l; (void)t;
-    return sacc;
-}
-// width 64: zero the shared gradient accumulator / store it into a global slot and zero it
-template <int H>
-__device__ __forceinline__ void bf_sacc_zero(const TrainDesc &d, long long P) {
-    NB_BF_SMEM;
-    (void)Ws; (void)dz0; (void)dz1; (void)bias; (void)zs; (void)gs; (void)W_l; (void)A_l;
-    for (long long e = t; e < P; e += blockDim.x) sacc[e] = 0.f;
-    __syncthreads();
-}
-template <int H>
-__device__ __forceinline__ void bf_sacc_flush(const TrainDesc &d, long long P, float *__restrict__ slot) {
-    NB_BF_SMEM;
-    (void)Ws; (void)dz0; (void)dz1; (void)bias; (void)zs; (void)gs; (void)W_l; (void)A_l;
-    __syncthreads();
-    for (long long e = t; e < P; e += blockDim.x) {
-        slot[e] = sacc[e];
-        sacc[e] = 0.f;
     }
     __syncthreads();
 }
@@ -387,20 +355,16 @@ __global__ void __launch_bounds__(256, 1)
     train_bf16_kernel(TrainDesc d, const float *__restrict__ q, const uint32_t *__restrict__ labels, long long n,
                       float alpha, float beta, float inv_n, TauF tau, float *__restrict__ partial,
                       float *loss_partial, long long stride, long long P, nb_step_stats *st) {
-    constexpr bool SACC = H == 64;  // the gradient accumulator fits in shared memory
     bf_load<H>(d, d.img, d.p);
     float *slot = partial + (size_t)blockIdx.x * stride;
-    if (SACC) bf_sacc_zero<H>(d, P);
     const long long ntiles = (n + TM - 1) / TM;
     float lossacc = 0.f;
     unsigned long long c_fn = 0, c_fp = 0, c_nf = 0;
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const long long base = tile * TM;
         const int rows = (int)min((long long)TM, n - base);
-        bf_tile<H, SACC>(d, q, labels, base, rows, alpha, beta, inv_n, tau, SACC ? bf_sacc_ptr<H>(d) : slot,
-                         lossacc, c_fn, c_fp, c_nf);
+        bf_tile<H>(d, q, labels, base, rows, alpha, beta, inv_n, tau, slot, lossacc, c_fn, c_fp, c_nf);
     }
-    if (SACC) bf_sacc_flush<H>(d, P, slot);
     if (threadIdx.x == 0) loss_partial[blockIdx.x] = lossacc;
     bf_counters(st, c_fn, c_fp, c_nf);
 }
@@ -415,12 +379,10 @@ __global__ void __launch_bounds__(256, 1)
                             const uint32_t *__restrict__ labels, float alpha_arg, const float *sched_alpha,
                             const int *d_step, int sched_T, float beta, const TauF *taus, float *__restrict__ partial,
                             float *loss_partial, long long P, long long S, nb_step_stats *st) {
-    constexpr bool SACC = H == 64;  // the gradient accumulator fits in shared memory
     float alpha = alpha_arg;
     if (sched_alpha) alpha = sched_alpha[min(*d_step, sched_T - 1)];
     unsigned long long c_fn = 0, c_fp = 0, c_nf = 0;
     int cur = -1;
-    if (SACC) bf_sacc_zero<H>(d, P);
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
         const PlanItem w = items[it];
         TrainDesc dd = d;
@@ -435,10 +397,8 @@ __global__ void __launch_bounds__(256, 1)
         float lossacc = 0.f;
         for (long long base = w.row0; base < w.row1; base += TM) {
             const int rows = (int)min((long long)TM, w.row1 - base);
-            bf_tile<H, SACC>(dd, q, labels, base, rows, alpha, beta, inv_n, taus[w.obj],
-                             SACC ? bf_sacc_ptr<H>(dd) : slot, lossacc, c_fn, c_fp, c_nf);
+            bf_tile<H>(dd, q, labels, base, rows, alpha, beta, inv_n, taus[w.obj], slot, lossacc, c_fn, c_fp, c_nf);
         }
-        if (SACC) bf_sacc_flush<H>(dd, P, slot);  // one store per parameter per item
         if (threadIdx.x == 0) loss_partial[it] = lossacc;
     }
     bf_counters(st, c_fn, c_fp, c_nf);
@@ -486,22 +446,333 @@ int num_sms() {
     return sms;
 }
 
+// ------------------------------------------------------------------ width 256
+// The BF16 weights of a 256-wide network (128 KB per hidden layer) do not fit in shared
+// memory next to a tile's activations, so this form streams them: each layer's forward
+// GEMM runs in two halves of 128 output neurons and each input-gradient GEMM in two halves
+// of 128 contraction rows, every half loaded into one shared buffer just before use (the
+// first layer, 256 x 16, in one piece).  Tiles of 32 samples; the head, the loss, the bias
+// gradients and the weight-gradient partials (four-column vector reductions into the CTA's
+// slot) as in the resident form.
+constexpr int TW = 32, HW = 256, HPW = HW + PAD, XPW = K0 + PAD, HALFW = 128;
+
+struct WideSmem {
+    __nv_bfloat16 *x, *act, *dz0, *dz1, *wb;
+    float *bias, *head, *zs, *gs, *ls;
+};
+__device__ __forceinline__ WideSmem wide_smem(int NH) {
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    WideSmem m;
+    m.x = reinterpret_cast<__nv_bfloat16 *>(smem_raw);
+    m.act = m.x + TW * XPW;                      // A_1 .. A_NH, [TW][HPW] each
+    m.dz0 = m.act + (size_t)NH * TW * HPW;
+    m.dz1 = m.dz0 + TW * HPW;
+    m.wb = m.dz1 + TW * HPW;                     // [HALFW][HPW], or the first layer [HW][XPW]
+    m.bias = reinterpret_cast<float *>(m.wb + HALFW * HPW);
+    m.head = m.bias + NH * HW;
+    m.zs = m.head + HW + 4;
+    m.gs = m.zs + TW;
+    m.ls = m.gs + TW;
+    return m;
+}
+__device__ __forceinline__ __nv_bfloat16 *wide_A(const WideSmem &m, int l) {
+    return l == 0 ? m.x : m.act + (size_t)(l - 1) * TW * HPW;
+}
+
+// rows [row0, row0 + nrows) of layer l's image (kp columns) -> wb with row pitch `pitch`
+__device__ __forceinline__ void wide_load(const __nv_bfloat16 *img_l, int kp, int row0, int nrows,
+                                          __nv_bfloat16 *wb, int pitch) {
+    const int cpr = kp / 8;  // 16-byte chunks per row
+    for (int e = threadIdx.x; e < nrows * cpr; e += blockDim.x) {
+        const int r = e / cpr, c = e % cpr;
+        *reinterpret_cast<uint4 *>(wb + r * pitch + c * 8) =
+            *reinterpret_cast<const uint4 *>(img_l + (size_t)(row0 + r) * kp + c * 8);
+    }
+}
+
+// OUT[:, col0 .. col0+127] = relu(X W^T + b) for the 128 output rows of wb from wrow0
+__device__ __forceinline__ void wide_fwd_half(const __nv_bfloat16 *X, int xp, int K, const __nv_bfloat16 *wb,
+                                              int wp, int wrow0, const float *bias, int col0, __nv_bfloat16 *out) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = (warp & 1) * 16, nb = (warp >> 1) * 32;
+    const int mi = lane >> 3, r = lane & 7;
+    float acc[4][4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        uint32_t a0, a1, a2, a3;
+        ldsm_x4(smem_u32(X + (m0 + r + (mi & 1) * 8) * xp + k0 + (mi >> 1) * 8), a0, a1, a2, a3);
+#pragma unroll
+        for (int j = 0; j < 4; j += 2) {
+            uint32_t b0, b1, b2, b3;
+            ldsm_x4(smem_u32(wb + (wrow0 + nb + 8 * j + r + (mi >> 1) * 8) * wp + k0 + (mi & 1) * 8), b0, b1, b2, b3);
+            mma_bf16(acc[j], a0, a1, a2, a3, b0, b1);
+            mma_bf16(acc[j + 1], a0, a1, a2, a3, b2, b3);
+        }
+    }
+    const int gr = lane >> 2, gc = (lane & 3) * 2;
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        const int nn = col0 + nb + 8 * j + gc;
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int m = m0 + gr + 8 * h;
+            const float v0 = fmaxf(acc[j][2 * h] + bias[nn], 0.f), v1 = fmaxf(acc[j][2 * h + 1] + bias[nn + 1], 0.f);
+            *reinterpret_cast<uint32_t *>(out + m * HPW + nn) = pack2(v0, v1);
+        }
+    }
+}
+
+// acc += DZ[:, n0h .. n0h+127] W[n0h .. n0h+127][:] with wb holding those 128 rows of W
+// (input gradient, 256 output columns; warps: 2 along the 32 rows x 4 along 64 columns)
+__device__ __forceinline__ void wide_da_half(const __nv_bfloat16 *DZ, int n0h, const __nv_bfloat16 *wb,
+                                             float (&acc)[8][4]) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = (warp & 1) * 16, c0 = (warp >> 1) * 64;
+    const int mi = lane >> 3, r = lane & 7;
+    for (int k0 = 0; k0 < HALFW; k0 += 16) {
+        uint32_t a0, a1, a2, a3;
+        ldsm_x4(smem_u32(DZ + (m0 + r + (mi & 1) * 8) * HPW + n0h + k0 + (mi >> 1) * 8), a0, a1, a2, a3);
+#pragma unroll
+        for (int j = 0; j < 8; j += 2) {
+            uint32_t b0, b1, b2, b3;
+            // wb[n][k] read transposed: matrices (n0-7,k0-7) (n8-15,k0-7) (n0-7,k8-15) (n8-15,k8-15)
+            ldsm_x4_t(smem_u32(wb + (k0 + r + (mi & 1) * 8) * HPW + c0 + 8 * j + (mi >> 1) * 8), b0, b1, b2, b3);
+            mma_bf16(acc[j], a0, a1, a2, a3, b0, b1);
+            mma_bf16(acc[j + 1], a0, a1, a2, a3, b2, b3);
+        }
+    }
+}
+
+// slot[n][k] += sum_m DZ[m][n] A[m][k], n < 256, k < Kreal (Kp padded columns of A)
+__device__ __forceinline__ void wide_dw(const __nv_bfloat16 *DZ, const __nv_bfloat16 *A, int ap, int Kp, int Kreal,
+                                        float *slotW) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int mi = lane >> 3, r = lane & 7;
+    const int gr = lane >> 2, gc = (lane & 3) * 2;
+    const bool odd = lane & 1;
+    for (int kc = 0; kc < Kp; kc += 64) {
+        const int cw = min(64, Kp - kc);
+        float acc[2][8][4];
+#pragma unroll
+        for (int b = 0; b < 2; b++)
+#pragma unroll
+            for (int j = 0; j < 8; j++) acc[b][j][0] = acc[b][j][1] = acc[b][j][2] = acc[b][j][3] = 0.f;
+#pragma unroll
+        for (int m0 = 0; m0 < TW; m0 += 16) {
+            uint32_t a[2][4];
+#pragma unroll
+            for (int b = 0; b < 2; b++) {
+                const int n0 = warp * 32 + 16 * b;
+                ldsm_x4_t(smem_u32(DZ + (m0 + r + (mi >> 1) * 8) * HPW + n0 + (mi & 1) * 8), a[b][0], a[b][1], a[b][2],
+                          a[b][3]);
+            }
+#pragma unroll
+            for (int j = 0; j < 8; j += 2) {
+                if (8 * j >= cw) break;
+                uint32_t b0, b1, b2, b3;
+                ldsm_x4_t(smem_u32(A + (m0 + r + (mi & 1) * 8) * ap + kc + 8 * j + (mi >> 1) * 8), b0, b1, b2, b3);
+#pragma unroll
+                for (int b = 0; b < 2; b++) {
+                    mma_bf16(acc[b][j], a[b][0], a[b][1], a[b][2], a[b][3], b0, b1);
+                    if (8 * (j + 1) < cw) mma_bf16(acc[b][j + 1], a[b][0], a[b][1], a[b][2], a[b][3], b2, b3);
+                }
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < 2; b++) {
+            const int n0 = warp * 32 + 16 * b;
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                if (8 * j >= cw) break;
+                const float s0 = odd ? acc[b][j][0] : acc[b][j][2], s1 = odd ? acc[b][j][1] : acc[b][j][3];
+                const float r0 = __shfl_xor_sync(FULL, s0, 1), r1 = __shfl_xor_sync(FULL, s1, 1);
+                const int k4 = kc + 8 * j + (gc & ~2);
+                const int nn = n0 + gr + (odd ? 8 : 0);
+                float v[4];
+                if (odd) {
+                    v[0] = r0; v[1] = r1; v[2] = acc[b][j][2]; v[3] = acc[b][j][3];
+                } else {
+                    v[0] = acc[b][j][0]; v[1] = acc[b][j][1]; v[2] = r0; v[3] = r1;
+                }
+                float *dst = slotW + (size_t)nn * Kreal + k4;
+                if (k4 + 3 < Kreal && ((uintptr_t)dst & 15) == 0) {
+                    red_add4(dst, v[0], v[1], v[2], v[3]);
+                } else {
+#pragma unroll
+                    for (int u = 0; u < 4; u++)
+                        if (k4 + u < Kreal) red_add(dst + u, v[u]);
+                }
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256, 1)
+    train_bf16_wide_kernel(TrainDesc d, const float *__restrict__ q, const uint32_t *__restrict__ labels, long long n,
+                           float alpha, float beta, float inv_n, TauF tau, float *__restrict__ partial,
+                           float *loss_partial, long long stride, nb_step_stats *st) {
+    const int NH = d.NH, t = threadIdx.x;
+    const WideSmem sm = wide_smem(NH);
+    for (int i = t; i < NH * HW; i += blockDim.x) {
+        const int l = i / HW, j = i % HW;
+        sm.bias[i] = d.p[d.off[l] + HW * (l == 0 ? d.in : HW) + j];
+    }
+    for (int i = t; i <= HW; i += blockDim.x) sm.head[i] = d.p[d.off[NH] + i];
+    float *slot = partial + (size_t)blockIdx.x * stride;
+    const long long ntiles = (n + TW - 1) / TW;
+    float lossacc = 0.f;
+    unsigned long long c_fn = 0, c_fp = 0, c_nf = 0;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const long long base = tile * TW;
+        const int rows = (int)min((long long)TW, n - base);
+        __syncthreads();
+        for (int e = t; e < TW * K0; e += blockDim.x) {
+            const int m = e / K0, k = e % K0;
+            const float xv = (m < rows && k < d.in) ? q[(base + m) * d.in + k] : 0.f;
+            sm.x[m * XPW + k] = __float2bfloat16_rn(xv);
+        }
+        // forward: the first layer in one piece, the hidden layers in two halves
+        wide_load(d.img, K0, 0, HW, sm.wb, XPW);
+        __syncthreads();
+        wide_fwd_half(sm.x, XPW, K0, sm.wb, XPW, 0, sm.bias, 0, wide_A(sm, 1));
+        wide_fwd_half(sm.x, XPW, K0, sm.wb, XPW, HALFW, sm.bias, HALFW, wide_A(sm, 1));
+        for (int l = 1; l < NH; l++) {
+            const __nv_bfloat16 *img_l = d.img + img_off(HW, l);
+            for (int h = 0; h < 2; h++) {
+                __syncthreads();  // the buffer is free and layer l's inputs are in place
+                wide_load(img_l, HW, h * HALFW, HALFW, sm.wb, HPW);
+                __syncthreads();
+                wide_fwd_half(wide_A(sm, l), HPW, HW, sm.wb, HPW, 0, sm.bias + l * HW, h * HALFW, wide_A(sm, l + 1));
+            }
+        }
+        __syncthreads();
+        // head (FP32) and loss: 4 threads per sample
+        if (t < 4 * TW) {
+            const __nv_bfloat16 *aL = wide_A(sm, NH);
+            const int m = t >> 2, part = t & 3;
+            float sacc = 0.f;
+            for (int k = part; k < HW; k += 4) sacc = fmaf(sm.head[k], __bfloat162float(aL[m * HPW + k]), sacc);
+            sacc += __shfl_xor_sync(0xffffffffu, sacc, 1);
+            sacc += __shfl_xor_sync(0xffffffffu, sacc, 2);
+            if (part == 0) sm.zs[m] = sacc + sm.head[HW];
+        }
+        __syncthreads();
+        if (t < TW) {
+            float g = 0.f, lv = 0.f;
+            if (t < rows) {
+                const long long i = base + t;
+                const float y = (float)((labels[i >> 5] >> (i & 31)) & 1u);
+                const float z = sm.zs[t];
+                if (isfinite(z)) {
+                    lv = alpha * y * softplusf(-z) + beta * (1.f - y) * softplusf(z);
+                    const float sg = sigmoidf(z);
+                    g = (alpha * y * (sg - 1.f) + beta * (1.f - y) * sg) * inv_n;
+                    const bool dec = z >= tau.up;
+                    c_fn += (y != 0.f && !dec);
+                    c_fp += (y == 0.f && dec);
+                } else {
+                    c_nf++;
+                }
+            }
+            sm.gs[t] = g;
+            sm.ls[t] = lv;
+        }
+        __syncthreads();
+        if (t == 0)
+            for (int m = 0; m < rows; m++) lossacc += sm.ls[m];
+        // head gradients and dZ of the last hidden layer
+        {
+            const __nv_bfloat16 *aL = wide_A(sm, NH);
+            float *gW = slot + d.off[NH];
+            for (int k = t; k <= HW; k += blockDim.x) {
+                float sacc = 0.f;
+                if (k < HW)
+                    for (int m = 0; m < TW; m++) sacc = fmaf(sm.gs[m], __bfloat162float(aL[m * HPW + k]), sacc);
+                else
+                    for (int m = 0; m < TW; m++) sacc += sm.gs[m];
+                gW[k] += sacc;
+            }
+            for (int e = t; e < TW * HW; e += blockDim.x) {
+                const int m = e / HW, k = e % HW;
+                const float a = __bfloat162float(aL[m * HPW + k]);
+                sm.dz0[m * HPW + k] = __float2bfloat16_rn(a > 0.f ? sm.gs[m] * sm.head[k] : 0.f);
+            }
+        }
+        __syncthreads();
+        __nv_bfloat16 *dzc = sm.dz0, *dzn = sm.dz1;
+        for (int l = NH - 1; l >= 0; l--) {
+            const int K = l == 0 ? d.in : HW, kp = kpad(HW, l);
+            const __nv_bfloat16 *Al = wide_A(sm, l);
+            float *gW = slot + d.off[l];
+            wide_dw(dzc, Al, l == 0 ? XPW : HPW, kp, K, gW);
+            for (int nn = t; nn < HW; nn += blockDim.x) {
+                float sacc = 0.f;
+                for (int m = 0; m < TW; m++) sacc += __bfloat162float(dzc[m * HPW + nn]);
+                gW[(size_t)HW * K + nn] += sacc;
+            }
+            if (l > 0) {
+                // dA_l = dZ W_l through the ReLU of layer l's input, W_l streamed in two halves
+                float acc[8][4];
+#pragma unroll
+                for (int j = 0; j < 8; j++) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+                const __nv_bfloat16 *img_l = d.img + img_off(HW, l);
+                for (int h = 0; h < 2; h++) {
+                    __syncthreads();
+                    wide_load(img_l, HW, h * HALFW, HALFW, sm.wb, HPW);
+                    __syncthreads();
+                    wide_da_half(dzc, h * HALFW, sm.wb, acc);
+                }
+                const int warp = t >> 5, lane = t & 31;
+                const int m0 = (warp & 1) * 16, c0 = (warp >> 1) * 64;
+                const int gr = lane >> 2, gc = (lane & 3) * 2;
+#pragma unroll
+                for (int j = 0; j < 8; j++) {
+                    const int nn = c0 + 8 * j + gc;
+#pragma unroll
+                    for (int h = 0; h < 2; h++) {
+                        const int m = m0 + gr + 8 * h;
+                        const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162 *>(Al + m * HPW + nn);
+                        const float v0 = __low2float(mk) > 0.f ? acc[j][2 * h] : 0.f;
+                        const float v1 = __high2float(mk) > 0.f ? acc[j][2 * h + 1] : 0.f;
+                        *reinterpret_cast<uint32_t *>(dzn + m * HPW + nn) = pack2(v0, v1);
+                    }
+                }
+                __syncthreads();
+                __nv_bfloat16 *tp = dzc;
+                dzc = dzn;
+                dzn = tp;
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) loss_partial[blockIdx.x] = lossacc;
+    bf_counters(st, c_fn, c_fp, c_nf);
+}
+
+size_t wide_smem_bytes(int NH) {
+    const size_t bf = (size_t)TW * XPW + (size_t)NH * TW * HPW + 2 * (size_t)TW * HPW + (size_t)HALFW * HPW;
+    return bf * 2 + ((size_t)NH * HW + HW + 4 + 3 * TW) * 4 + 64;
+}
+
 }  // namespace
 
 size_t nb_train_bf16_smem(int H, int NH, long long P) {
+    if (H == 256) return wide_smem_bytes(NH);
     const size_t HP = H + PAD, XP = K0 + PAD;
     const size_t w = (size_t)H * XP + (size_t)(NH - 1) * H * HP;
     const size_t a = (size_t)TM * XP + (size_t)NH * TM * HP;
     const size_t dz = 2 * (size_t)TM * HP;
-    const size_t acc = H == 64 ? (size_t)P : 0;  // width 64: the gradient accumulator
-    return (w + a + dz) * 2 + ((size_t)NH * H + H + 4 + 3 * TM + acc) * 4 + 64;
+    (void)P;
+    return (w + a + dz) * 2 + ((size_t)NH * H + H + 4 + 3 * TM) * 4 + 64;
 }
 
 nb_status nb_train_bf16_check(const MlpDesc &d) {
     const int H = d.w[1], NH = d.L - 1;
     if (NH < 1) return nb_fail(NB_EUNSUPPORTED, "BF16 training needs at least one hidden layer");
     if (d.w[0] > K0) return nb_fail(NB_EUNSUPPORTED, "BF16 training: input width must be <= 16");
-    if (H != 64 && H != 128) return nb_fail(NB_EUNSUPPORTED, "BF16 training: hidden width must be 64 or 128");
+    if (H != 64 && H != 128 && H != 256)
+        return nb_fail(NB_EUNSUPPORTED, "BF16 training: hidden width must be 64, 128 or 256");
     for (int l = 1; l < d.L; l++)
         if (d.w[l] != H) return nb_fail(NB_EUNSUPPORTED, "BF16 training: hidden widths must be equal");
     int dev = 0, maxsm = 0;
@@ -540,7 +811,12 @@ nb_status nb_launch_train_bf16(TcModel *tc, const MlpDesc &d, const float *q, co
     NB_CUDA(cudaMemsetAsync(ws.partial, 0, (size_t)ws.G * stride * sizeof(float), s));
     if (st) NB_CUDA(cudaMemsetAsync(st, 0, sizeof(nb_step_stats), s));
     const size_t smem = nb_train_bf16_smem(t.H, t.NH, P);
-    if (t.H == 128) {
+    if (t.H == 256) {
+        // weights streamed per half layer (tiles of 32 samples)
+        NB_CUDA(cudaFuncSetAttribute(train_bf16_wide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        train_bf16_wide_kernel<<<ws.G, 256, smem, s>>>(t, q, labels, (long long)n, alpha, beta, 1.0f / (float)n, tau,
+                                                       ws.partial, ws.loss_partial, stride, st);
+    } else if (t.H == 128) {
         NB_CUDA(cudaFuncSetAttribute(train_bf16_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         train_bf16_kernel<128><<<ws.G, 256, smem, s>>>(t, q, labels, (long long)n, alpha, beta, 1.0f / (float)n, tau,
                                                        ws.partial, ws.loss_partial, stride, P, st);
@@ -556,6 +832,7 @@ nb_status nb_launch_train_bf16(TcModel *tc, const MlpDesc &d, const float *q, co
 nb_status nb_train_bf16_group_init(TcModel *tc, const MlpDesc &d, int n_objects) {
     const nb_status st = nb_train_bf16_check(d);
     if (st != NB_OK) return st;
+    if (d.w[1] == 256) return nb_fail(NB_EUNSUPPORTED, "grouped BF16 training: hidden width must be 64 or 128");
     tc->train_img_bytes = nb_train_bf16_img_bytes(d);
     if (cudaMalloc(&tc->train_img, tc->train_img_bytes * (size_t)n_objects) != cudaSuccess) {
         cudaGetLastError();

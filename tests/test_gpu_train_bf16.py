@@ -35,7 +35,10 @@ def _per_tensor(widths):
 @pytest.mark.parametrize("kind,widths,n", [("ray3", [6, 128, 128, 128, 128, 1], 65536),
                                            ("ray3", [6, 128, 128, 128, 1], 4133),
                                            ("point4t", [4, 64, 64, 64, 1], 777),
-                                           ("point3", [3, 128, 128, 1], 1)])
+                                           ("point4t", [4, 64, 64, 64, 1], 200_003),
+                                           ("point3", [3, 128, 128, 1], 1),
+                                           ("box3", [6, 256, 256, 256, 256, 1], 8191),
+                                           ("plane3", [4, 256, 256, 1], 33)])
 def test_bf16_step_gradient_direction_loss_adam(nb, kind, widths, n):
     kid = I.kind_id(kind)
     sc = I.make_scene(60, 32, 3, 0.05, 0.3, moving=(kid == I.POINT4T))
