@@ -54,7 +54,10 @@ typedef enum { NB_POINT2 = 0, NB_POINT3 = 1, NB_POINT4T = 2, NB_RAY3 = 3, NB_PLA
 /* Arithmetic of the fast forward path:
  *   NB_F32    FP32 FMA (CUDA cores), the plain single-object form;
  *   NB_BF16   tcgen05 tensor cores, BF16 operands, FP32 accumulation (one product);
- *   NB_FP8    tensor cores, FP8 e4m3 operands with per-layer scales;
+ *   NB_FP8    tcgen05 tensor cores, E4M3 operands for the hidden-to-hidden layers with
+ *             power-of-two scales per weight row and per query row (exact to apply),
+ *             the first layer in split FP16, FP32 accumulation; hidden widths 128 or
+ *             256 and at least two hidden layers;
  *   NB_F16X3  tcgen05 tensor cores, weights and activations split into FP16 hi + lo
  *             pairs and three products per layer (hi.hi + hi.lo + lo.hi), FP32
  *             accumulation: logits within a few FP32 roundings of the FP32 network. */
@@ -104,9 +107,11 @@ typedef struct nb_model nb_model;
 /* Create a bounding network h (Sec. 3.4 "Architecture"): widths[0] is the query
  * encoding width, widths[1..n_layers-1] the hidden widths (ReLU), widths[n_layers]
  * must be 1 (the logit).  Hidden widths 1..256.  infer_prec selects the nb_query
- * fast path (see nb_prec; the tensor-core paths need equal hidden widths of 64 or
- * 128, an input width <= 16 and weights that fit in shared memory, else
- * NB_EUNSUPPORTED).  train_prec selects the training step (NB_F32 or NB_BF16).
+ * fast path (see nb_prec; the tensor-core paths need equal hidden widths (64 or 128
+ * for NB_BF16 and NB_F16X3, 128 or 256 for NB_FP8), an input width <= 16 and weights
+ * that fit in shared memory, else NB_EUNSUPPORTED).  train_prec selects the training
+ * step: NB_F32, or NB_BF16 (tensor cores; equal hidden widths of 64, 128 or 256, the
+ * last with its weights streamed through shared memory).
  * Parameters start at zero; load them with nb_model_set_params.  Adam uses lr 1e-3,
  * betas (0.9, 0.999), eps 1e-8 (Sec. 3.4 "Training"); tau starts at 0, i.e. the
  * sigmoid rounded at 1/2 (Sec. 3.4).  The device is the current CUDA device. */
@@ -223,7 +228,8 @@ typedef struct nb_group nb_group;
 nb_status nb_plan_create(const int64_t *host_offsets, int32_t n_objects, int32_t chunk_rows, nb_plan **out);
 nb_status nb_plan_destroy(nb_plan *p);
 
-/* widths as for nb_model_create; infer_prec NB_F32 or NB_F16X3; train_prec NB_F32. */
+/* widths as for nb_model_create; infer_prec NB_F32 or NB_F16X3; train_prec NB_F32 or
+ * NB_BF16 (hidden widths 64 or 128). */
 nb_status nb_group_create(const int32_t *widths, int32_t n_layers, int32_t n_objects, int32_t infer_prec,
                           int32_t train_prec, nb_group **out);
 nb_status nb_group_destroy(nb_group *g);
