@@ -297,7 +297,7 @@ def run_c2(args):
                      "f16x3 (split fp16 operands, fp32 accumulate)",
                      {"workload": WORKLOAD, "n_eval": n_eval, "batch": BATCH, "train_steps": T, "margin": MARGIN,
                       "l2": "inputs 384 MB per step > 129 MB L2, no flush", "parallelism": f"replicas{ctx.world}"},
-                     clocks, args.steps * 3)
+                     clocks, args.steps * 4)  # forward, stage 1, Dot2, three-word
     line.update({
         "fn": fn, "fp": fp, "fp_rate": fp / n_eval, "positives": int(y.sum()), "tau": tau,
         "decisions_differing_from_fp32_form": differ,
@@ -419,7 +419,7 @@ def run_c3(args):
                                   "64M eval queries (configs[2])", "n_eval": n_eval, "batch": B, "train_steps": T,
                       "train_precision": "bf16 tensor cores (weights streamed per half layer), fp32 master weights",
                       "l2": f"inputs {n_eval * 24 >> 20} MB per step > L2"},
-                     clocks, args.steps * 3)
+                     clocks, args.steps * 4)  # FP8 forward, stage 1, Dot2, three-word
     line.update({"box": summary(box, ms, f32_ms), "plane": summary(pl, pl_ms, pl32_ms),
                  "speedup_vs_fp32_plain": f32_ms / ms,
                  "train_samples_per_s": {"bf16_box": B / (tr_ms[I.BOX3] / 1000.0),
@@ -485,7 +485,7 @@ def run_c2e(args):
                      {"workload": "3D points: 16-sphere solid (radii 0.2-0.5), late MLP 3->128x4->1, early MLP "
                                   "3->64x2->1 on 1 - g, 16M eval points (Sec. 3.3 early-out)", "n_eval": n,
                       "train_steps": T},
-                     clocks, args.steps * 8)
+                     clocks, args.steps * 11)  # early query (4), compact, gather, late query (4), scatter
     line.update({"fn": int(np.sum(y & ~dec)), "fp_rate": float(np.mean(~y & dec)),
                  "fp_rate_without_early_out": float(np.mean(~y & dplain)),
                  "early_inside_fraction": est["n_early_inside"] / n,
@@ -532,7 +532,7 @@ def run_c1(args):
                      {"workload": "2D points: 8-disk union, MLP 2->32x3->1 FP32, 1000 steps x 1024, 256x256 grid "
                                   "(configs[0])", "reps_of_grid_per_step": reps,
                       "l2": "grid resident in L2 (256 KB); small-case configuration"},
-                     clocks, args.steps * reps * 3)
+                     clocks, args.steps * reps * 4)  # forward, stage 1, Dot2, three-word
     line.update({"fn": int(np.sum(y & ~dec)), "fp": int(np.sum(~y & dec)), "fp_rate": float(np.mean(~y & dec)),
                  "tau": tau, "train_samples_per_s_fp32": B / (train_ms / 1000.0),
                  "cpu_baseline": {"value": cpu_v, "unit": "queries/s", "cores": cores, "kind": "oracle",
@@ -624,7 +624,7 @@ def run_c4(args):
                      {"workload": "4D space-time points: 256 objects of 16-64 moving spheres, 4->64x3->1 per object, "
                                   "uneven 4096-65536 samples per object (configs[3])", "train_steps": T,
                       "eval_per_object": NE, "l2": f"inputs {K * NE * 16 >> 20} MB per step > L2"},
-                     clocks, args.steps * 2)
+                     clocks, args.steps * 3)  # grouped forward, Dot2, three-word
     line.update({"fn": int(np.sum(y & ~dec)), "fp_rate": float(np.mean(~y & dec)),
                  "band": {"flagged": qst["n_flagged"], "unresolved": qst["n_unresolved"]},
                  "fp32_single_object_queries_per_s": K * NE / (f32_ms / 1000.0),
@@ -763,7 +763,7 @@ def run_c5(args):
                                   "object, 64M rays (configs[4])", "n_rays": NR, "train_steps": T,
                       "training": f"{n_pools} x {pool_rays} world rays through the box/ball stage, exact labels",
                       "calibration": "thresholds calibrated on the benchmark rays' own pairs"},
-                     clocks, args.steps * len(chunks) * 5)
+                     clocks, args.steps * len(chunks) * 6)  # bin x2, grouped query (3), exact
     line.update({"fn_vs_plain": int(np.sum(hp & ~hc)), "hits_equal_plain": bool(np.array_equal(hc, hp)),
                  "stages_first_chunk_ms": {"bin": t_bin, "neural": t_nn, "exact_all_pairs": t_exact_all,
                                            "exact_passed_pairs": t_exact_pass},
