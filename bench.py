@@ -125,6 +125,26 @@ def cpu_oracle_rate(widths, params, q_host, seconds=12.0):
     return n / dt, nthreads, n
 
 
+def rank_seed(seed: int, rank: int) -> int:
+    """Each replica evaluates its own queries: rank r draws the stream seed + 1000 r."""
+    return seed + 1000 * rank
+
+
+def max_over_ranks(ms: float, dist, world: int, device="cpu") -> float:
+    """The job's time is the slowest replica's (all-reduce MAX; identity on one rank)."""
+    if world <= 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank: int, world: int, ms: float) -> float:
+    """Whole-job throughput: the units of every replica over the slowest replica's time."""
+    return world * units_per_rank / (ms / 1000.0)
+
+
 class Ctx:
     """Device, ranks, CUDA events and the JSON line common to every configuration."""
 
@@ -168,11 +188,7 @@ class Ctx:
                 fn()
             self.e1.record()
             self.barrier()
-        ms = self.e0.elapsed_time(self.e1) / steps
-        if self.world > 1:
-            t = self.torch.tensor([ms], device=self.dev)
-            self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(self.e0.elapsed_time(self.e1) / steps, self.dist, self.world, self.dev)
         return ms, clk.summary()
 
     def emit(self, line):
@@ -198,7 +214,7 @@ def run_c2(args):
     n_eval = args.n_eval
     sc = I.make_scene(SEED_SCENE, N_SPHERES, 3, R_LO, R_HI)
     shape = nb.Shape(sc, dev)
-    eval_q_host = I.sample_queries(I.RAY3, SEED_QUERY + 1000 * ctx.rank, n_eval)
+    eval_q_host = I.sample_queries(I.RAY3, rank_seed(SEED_QUERY, ctx.rank), n_eval)
     eval_q = torch.as_tensor(eval_q_host, device=dev)
     eval_bits = nb.label(shape, I.RAY3, eval_q)
 
@@ -252,7 +268,7 @@ def run_c2(args):
     differ = int(np.sum(dec != dec32))
 
     ms, clocks = ctx.timed(lambda: model.query(eval_q, margin=MARGIN, out=out), args.steps, args.warmup)
-    value = ctx.world * n_eval / (ms / 1000.0)
+    value = job_value(n_eval, ctx.world, ms)
     fwd_ms = ctx.time_ms(lambda: model.query(eval_q, margin=0.0, out=out), args.steps)
     f32_ms = ctx.time_ms(lambda: plain.query(eval_q, margin=MARGIN32, out=out), 3)
 
@@ -354,7 +370,7 @@ def run_c3(args):
         train_s = time.perf_counter() - t0
         params = tr.get_params()
         # evaluation queries drawn by the GPU sampler (another stream), exact labels
-        eq = nb.sample(kind, n_eval, 3003 + kind + 1000 * ctx.rank)
+        eq = nb.sample(kind, n_eval, rank_seed(3003 + kind, ctx.rank))
         ey = nb.label(shape, kind, eq)
         f32 = nb.Model(widths)
         f32.set_params(params)
@@ -465,7 +481,7 @@ def run_c2e(args):
     early_q.set_params(early.get_params())
     early = early_q
     n = args.n_eval
-    eq = nb.sample(I.POINT3, n, SEED_QUERY + 1000 * ctx.rank)
+    eq = nb.sample(I.POINT3, n, rank_seed(SEED_QUERY, ctx.rank))
     ey = nb.label(shape, I.POINT3, eq)
     late.calibrate(eq, ey)
     early.calibrate(eq, nb.bits_not(ey, n))
