@@ -539,18 +539,30 @@ def run_c1(args):
     dec = nb.bits_to_numpy(out, grid.shape[0])
     # the 65,536-point grid is one step; repeated to get a measurable region
     reps = 50
-    ms, clocks = ctx.timed(lambda: [m.query(grid, margin=1e-3, out=out) for _ in range(reps)], args.steps,
-                           args.warmup)
-    value = ctx.world * reps * grid.shape[0] / (ms / 1000.0)
+    # a 65,536-point query is launch-bound: the 50 queries of a step are one CUDA graph
+    s_cap = torch.cuda.Stream()
+    s_cap.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s_cap):
+        with torch.cuda.graph(graph, stream=s_cap):
+            for _ in range(reps):
+                m.query(grid, margin=1e-3, out=out)
+    torch.cuda.current_stream().wait_stream(s_cap)
+    torch.cuda.synchronize()
+    eager_ms = ctx.time_ms(lambda: [m.query(grid, margin=1e-3, out=out) for _ in range(reps)], 3)
+    ms, clocks = ctx.timed(graph.replay, args.steps, args.warmup)
+    value = job_value(reps * grid.shape[0], ctx.world, ms)
+    assert np.array_equal(nb.bits_to_numpy(out, grid.shape[0]), dec)
     cpu_v, cores, cpu_n = cpu_oracle_rate(widths, m.get_params(), I.grid_points_2d(256))
     line = base_line(ctx, "neural-bound queries/s at 0 FN (2D points, plain FP32)", value, "queries/s", ms,
                      args.steps, args.warmup, "f32",
                      {"workload": "2D points: 8-disk union, MLP 2->32x3->1 FP32, 1000 steps x 1024, 256x256 grid "
-                                  "(configs[0])", "reps_of_grid_per_step": reps,
+                                  "(configs[0])", "reps_of_grid_per_step": reps, "cuda_graph": True,
                       "l2": "grid resident in L2 (256 KB); small-case configuration"},
                      clocks, args.steps * reps * 4)  # forward, stage 1, Dot2, three-word
     line.update({"fn": int(np.sum(y & ~dec)), "fp": int(np.sum(~y & dec)), "fp_rate": float(np.mean(~y & dec)),
                  "tau": tau, "train_samples_per_s_fp32": B / (train_ms / 1000.0),
+                 "without_graph_queries_per_s": reps * grid.shape[0] / (eager_ms / 1000.0),
                  "cpu_baseline": {"value": cpu_v, "unit": "queries/s", "cores": cores, "kind": "oracle",
                                   "sample": f"{cpu_n} grid points through the FP64 oracle forward"},
                  "e2e": None})
