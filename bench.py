@@ -47,7 +47,7 @@ SEED_SCENE, SEED_QUERY, SEED_INIT, SEED_TRAIN = 1001, 2001, 4001, 2018
 # fwd_split_kernel at 1,048,576 rays (25,459,968 bytes); None once the kernel changes
 TRAFFIC_BYTES_PER_RAY = 25459968 / 1048576
 METRIC = "neural-bound queries/s at 0 FN (3D rays, split-FP16 tcgen05 forward + FP32 re-check)"
-WORKLOAD = "3D ray queries: 64-sphere union, MLP 6->128x4->1, tensor-core 16-bit, 16M eval rays (configs[1])"
+WORKLOAD = "3D ray queries: 64-sphere union, MLP 6->128x4->1, tensor-core 16-bit, 16M eval rays"
 
 
 def peaks():
@@ -432,7 +432,7 @@ def run_c3(args):
     line = base_line(ctx, "neural-bound queries/s at 0 FN (3D boxes, FP8 E4M3 tcgen05 forward + FP32 re-check)",
                      value, "queries/s", ms, args.steps, args.warmup, "e4m3 (fp8 operands, fp32 accumulate)",
                      {"workload": "3D box and plane queries: 256-sphere union, MLP in->256x4->1, FP8 inference, "
-                                  "64M eval queries (configs[2])", "n_eval": n_eval, "batch": B, "train_steps": T,
+                                  "64M eval queries", "n_eval": n_eval, "batch": B, "train_steps": T,
                       "train_precision": "bf16 tensor cores (weights streamed per half layer), fp32 master weights",
                       "l2": f"inputs {n_eval * 24 >> 20} MB per step > L2"},
                      clocks, args.steps * 4)  # FP8 forward, stage 1, Dot2, three-word
@@ -556,8 +556,8 @@ def run_c1(args):
     cpu_v, cores, cpu_n = cpu_oracle_rate(widths, m.get_params(), I.grid_points_2d(256))
     line = base_line(ctx, "neural-bound queries/s at 0 FN (2D points, plain FP32)", value, "queries/s", ms,
                      args.steps, args.warmup, "f32",
-                     {"workload": "2D points: 8-disk union, MLP 2->32x3->1 FP32, 1000 steps x 1024, 256x256 grid "
-                                  "(configs[0])", "reps_of_grid_per_step": reps, "cuda_graph": True,
+                     {"workload": "2D points: 8-disk union, MLP 2->32x3->1 FP32, 1000 steps x 1024, 256x256 grid",
+                      "reps_of_grid_per_step": reps, "cuda_graph": True,
                       "l2": "grid resident in L2 (256 KB); small-case configuration"},
                      clocks, args.steps * reps * 4)  # forward, stage 1, Dot2, three-word
     line.update({"fn": int(np.sum(y & ~dec)), "fp": int(np.sum(~y & dec)), "fp_rate": float(np.mean(~y & dec)),
@@ -650,7 +650,7 @@ def run_c4(args):
     line = base_line(ctx, "grouped neural-bound queries/s at 0 FN (4D points, 256 objects, split-FP16)", value,
                      "queries/s", ms, args.steps, args.warmup, "f16x3 (split fp16 operands, fp32 accumulate)",
                      {"workload": "4D space-time points: 256 objects of 16-64 moving spheres, 4->64x3->1 per object, "
-                                  "uneven 4096-65536 samples per object (configs[3])", "train_steps": T,
+                                  "uneven 4096-65536 samples per object", "train_steps": T,
                       "eval_per_object": NE, "l2": f"inputs {K * NE * 16 >> 20} MB per step > L2"},
                      clocks, args.steps * 3)  # grouped forward, Dot2, three-word
     line.update({"fn": int(np.sum(y & ~dec)), "fp_rate": float(np.mean(~y & dec)),
@@ -788,7 +788,7 @@ def run_c5(args):
                      ctx.world * NR / (ms / 1000.0), "queries/s", ms, args.steps, args.warmup,
                      "f16x3 (split fp16 operands, fp32 accumulate)",
                      {"workload": "learned-culler cascade: 1024 objects of 32 spheres in [-10,10]^3, 6->128x3->1 per "
-                                  "object, 64M rays (configs[4])", "n_rays": NR, "train_steps": T,
+                                  "object, 64M rays", "n_rays": NR, "train_steps": T,
                       "training": f"{n_pools} x {pool_rays} world rays through the box/ball stage, exact labels",
                       "calibration": "thresholds calibrated on the benchmark rays' own pairs"},
                      clocks, args.steps * len(chunks) * 6)  # bin x2, grouped query (3), exact
