@@ -24,6 +24,8 @@
 namespace {
 
 constexpr int TM = 64;           // samples per tile
+constexpr int TPB = 512;         // threads of the resident-weight kernels: 16 warps
+constexpr int NWARP = TPB / 32;
 constexpr int K0 = 16;           // padded input width
 constexpr int PAD = 8;           // row padding (elements) against ldmatrix bank conflicts
 constexpr unsigned FULL = 0xffffffffu;
@@ -79,15 +81,17 @@ __device__ __forceinline__ float sigmoidf(float u) {
 
 // OUT[TM][N] = epilogue(X[TM][K] Y^T) with Y[N][K] row-major (forward, Y = W) or, with
 // TRANS_Y, OUT = X Y with Y[K][N] (the input gradient, Y = W read transposed).
-// Warps: 4 along the 64 rows x 2 along N.  RELU: out = relu(acc + bias) (forward);
+// Warps: 4 along the 64 rows x NWARP/4 along N.  RELU: out = relu(acc + bias) (forward);
 // otherwise out = acc masked by mask[m][n] > 0 (backward through the ReLU).
 template <int H, bool TRANS_Y, bool RELU>
 __device__ __forceinline__ void tile_gemm(const __nv_bfloat16 *X, int xp, int K, const __nv_bfloat16 *Y, int yp,
                                           const float *bias, const __nv_bfloat16 *mask, int mp, __nv_bfloat16 *out,
                                           int op) {
-    constexpr int NT = H / 16;  // n-tiles of 8 per warp (H/2 columns)
+    constexpr int NGN = NWARP / 4;        // warp groups along N
+    constexpr int NT = H / (8 * NGN);     // n-tiles of 8 per warp (H / NGN columns)
+    static_assert(NT % 2 == 0, "two n-tiles per B fragment load");
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = (warp & 3) * 16, n0 = (warp >> 2) * (H / 2);
+    const int m0 = (warp & 3) * 16, n0 = (warp >> 2) * (H / NGN);
     float acc[NT][4];
 #pragma unroll
     for (int j = 0; j < NT; j++) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
@@ -131,14 +135,17 @@ __device__ __forceinline__ void tile_gemm(const __nv_bfloat16 *X, int xp, int K,
 }
 
 // slot[n][k] += sum_m DZ[m][n] A[m][k] for n < H, k < Kreal (weight gradient of one layer).
-// Warps: n-blocks of 16 x (128 / H) column groups.
+// Warps: n-blocks of 16 x column groups (as many as the columns allow in multiples of 8;
+// warps beyond them sit out this layer).
 template <int H>
 __device__ __forceinline__ void tile_dw(const __nv_bfloat16 *DZ, int dp, const __nv_bfloat16 *A, int ap, int Kp,
                                         int Kreal, float *slotW) {
-    constexpr int NB = H / 16, KG = 8 / NB;  // n-blocks, column groups
+    constexpr int NB = H / 16, KG = NWARP / NB;  // n-blocks, column groups
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n0 = (warp % NB) * 16, kg = warp / NB;
-    const int kw = Kp / KG, kbeg = kg * kw;   // this warp's columns
+    const int kgs = max(1, min(KG, Kp / 8));  // column groups of this layer
+    if (kg >= kgs) return;
+    const int kw = Kp / kgs, kbeg = kg * kw;  // this warp's columns
     const int mi = lane >> 3, r = lane & 7;
     const int gr = lane >> 2, gc = (lane & 3) * 2;
     for (int kc = 0; kc < kw; kc += 64) {  // at most 64 columns (8 n8-tiles) of accumulators at a time
@@ -257,7 +264,7 @@ __device__ __forceinline__ void bf_tile(const TrainDesc &d, const float *__restr
         __syncthreads();
     }
     // head (FP32) and loss: 4 threads per sample
-    {
+    if (t < 4 * TM) {  // whole warps
         const __nv_bfloat16 *aL = A_l(NH);
         const int m = t >> 2, part = t & 3;
         float s = 0.f;
@@ -351,7 +358,7 @@ __device__ __forceinline__ void bf_counters(nb_step_stats *st, unsigned long lon
 }
 
 template <int H>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(TPB, 1)
     train_bf16_kernel(TrainDesc d, const float *__restrict__ q, const uint32_t *__restrict__ labels, long long n,
                       float alpha, float beta, float inv_n, TauF tau, float *__restrict__ partial,
                       float *loss_partial, long long stride, long long P, nb_step_stats *st) {
@@ -373,7 +380,7 @@ __global__ void __launch_bounds__(256, 1)
 // each); a CTA reloads weights only when its next item belongs to another object.
 // Object o's parameters start at d.p + o * P and its bf16 image at d.img + o * img_elems.
 template <int H>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(TPB, 1)
     train_bf16_group_kernel(TrainDesc d, long long img_elems, const PlanItem *__restrict__ items, int n_items,
                             const long long *__restrict__ offsets, const float *__restrict__ q,
                             const uint32_t *__restrict__ labels, float alpha_arg, const float *sched_alpha,
@@ -818,11 +825,11 @@ nb_status nb_launch_train_bf16(TcModel *tc, const MlpDesc &d, const float *q, co
                                                        ws.partial, ws.loss_partial, stride, st);
     } else if (t.H == 128) {
         NB_CUDA(cudaFuncSetAttribute(train_bf16_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        train_bf16_kernel<128><<<ws.G, 256, smem, s>>>(t, q, labels, (long long)n, alpha, beta, 1.0f / (float)n, tau,
+        train_bf16_kernel<128><<<ws.G, TPB, smem, s>>>(t, q, labels, (long long)n, alpha, beta, 1.0f / (float)n, tau,
                                                        ws.partial, ws.loss_partial, stride, P, st);
     } else {
         NB_CUDA(cudaFuncSetAttribute(train_bf16_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        train_bf16_kernel<64><<<ws.G, 256, smem, s>>>(t, q, labels, (long long)n, alpha, beta, 1.0f / (float)n, tau,
+        train_bf16_kernel<64><<<ws.G, TPB, smem, s>>>(t, q, labels, (long long)n, alpha, beta, 1.0f / (float)n, tau,
                                                       ws.partial, ws.loss_partial, stride, P, st);
     }
     NB_CUDA(cudaGetLastError());
@@ -866,13 +873,13 @@ nb_status nb_launch_train_bf16_group(TcModel *tc, const MlpDesc &d, long long P,
     if (t.H == 128) {
         NB_CUDA(cudaFuncSetAttribute(train_bf16_group_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
-        train_bf16_group_kernel<128><<<grid, 256, smem, s>>>(t, img_elems, pl->items, pl->n_items, pl->offsets, q,
+        train_bf16_group_kernel<128><<<grid, TPB, smem, s>>>(t, img_elems, pl->items, pl->n_items, pl->offsets, q,
                                                              labels, alpha, sched_alpha, d_step, sched_T, beta, taus,
                                                              partial, loss_partial, P, S, st);
     } else {
         NB_CUDA(cudaFuncSetAttribute(train_bf16_group_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
-        train_bf16_group_kernel<64><<<grid, 256, smem, s>>>(t, img_elems, pl->items, pl->n_items, pl->offsets, q,
+        train_bf16_group_kernel<64><<<grid, TPB, smem, s>>>(t, img_elems, pl->items, pl->n_items, pl->offsets, q,
                                                             labels, alpha, sched_alpha, d_step, sched_T, beta, taus,
                                                             partial, loss_partial, P, S, st);
     }
