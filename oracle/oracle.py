@@ -211,3 +211,21 @@ def benefit_break_even(t_a: float, t_b: float, p_a: float, p_b: float):
         return None, "<" if t_a < t_b else ">"
     t_star = (t_b - t_a) / (p_a - p_b)
     return t_star, ">" if p_a < p_b else "<"
+
+
+def three_way(z_outer, tau_outer: float, z_inner, tau_inner: float) -> np.ndarray:
+    """Broad-phase class of each query from a bound and an inverted bound (Sec. 5, the
+    variant with the asymmetry weights swapped): the outer network bounds g, so
+    z_outer < tau_outer means certainly outside; the inner network bounds the complement
+    1 - g (the swapped-weight network with its logit negated), so z_inner < tau_inner
+    means certainly inside.  Codes: 0 certainly outside, 1 certainly inside, 2 neither
+    (the only queries an exact test must see).  A query that both networks call certain,
+    which cannot happen on either network's calibration set, is 2."""
+    z_outer = np.asarray(z_outer, dtype=np.float64)
+    z_inner = np.asarray(z_inner, dtype=np.float64)
+    out_ = z_outer < tau_outer
+    in_ = z_inner < tau_inner
+    codes = np.full(z_outer.shape[0], 2, dtype=np.uint8)
+    codes[out_ & ~in_] = 0
+    codes[in_ & ~out_] = 1
+    return codes

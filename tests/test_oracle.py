@@ -437,3 +437,64 @@ def test_benefit_break_even_worked_example():
     t_nn, p = 0.37, 0.82
     t_star, side = O.benefit_break_even(1.0 + t_nn, 1.0, p, 1.0)
     assert side == ">" and abs(t_star - t_nn / (1 - p)) <= 1e-12
+
+
+# ----------------------------------------------------------------------------- inverted bounds
+def test_swapped_weights_equal_the_complement_with_negated_logit():
+    # Sec. 5: the inverted bound swaps the asymmetry weights.  Training on g with
+    # (alpha, beta) swapped is training on 1 - g with the logit negated: the loss is the
+    # same number and the gradient differs only in the sign of the head's entries.
+    w = [3, 16, 16, 1]
+    p = I.init_params(11, w)
+    X = I.sample_queries("point3", 12, 300)
+    y = (np.random.default_rng(13).random(300) < 0.4).astype(np.uint8)
+    alpha, beta = 1.0, 42.0
+    loss_s, g_s = O.loss_grad(w, p, X, y, beta, alpha)  # swapped weights on g
+    H = w[-2]
+    p_neg = p.copy()
+    p_neg[-(H + 1):] *= -1  # head weights and bias negated
+    loss_c, g_c = O.loss_grad(w, p_neg, X, 1 - y, alpha, beta)  # complement, usual weights
+    assert np.array_equal(O.forward(w, p_neg, X), -O.forward(w, p, X))
+    assert loss_s == loss_c
+    # dL/dz uses sigma(z) on one side and sigma(-z) = 1 - sigma(z) on the other: equal up
+    # to the rounding of that identity
+    sc = np.max(np.abs(g_s))
+    np.testing.assert_allclose(g_s[:-(H + 1)], g_c[:-(H + 1)], rtol=1e-12, atol=1e-14 * sc)
+    np.testing.assert_allclose(g_s[-(H + 1):], -g_c[-(H + 1):], rtol=1e-12, atol=1e-14 * sc)
+    # and it is not an identity of any two weightings: the unswapped loss differs
+    assert abs(O.loss_grad(w, p, X, y, alpha, beta)[0] - loss_s) > 1e-3
+
+
+def _codes_1d(w_o, b_o, tau_o, w_i, b_i, tau_i, xs):
+    X = np.array([[x] for x in xs], dtype=np.float32)
+    z_o = O.forward([1, 1], np.array([w_o, b_o], dtype=np.float32), X)
+    z_i = O.forward([1, 1], np.array([w_i, b_i], dtype=np.float32), X)
+    return O.three_way(z_o, tau_o, z_i, tau_i).tolist()
+
+
+def test_three_way_hand_worked():
+    # outer z = 2x - 1 (tau 0): certainly outside for x < 0.5
+    # inner z = -4x + 3: certainly inside where z < tau_i
+    xs = [0.0, 0.125, 0.25, 0.5, 1.0]
+    # tau_i = 2.5: inside for x > 0.125; x = 0.25 is claimed by both (a conflict -> 2),
+    # ties z = tau count as "not certain" for both networks
+    assert _codes_1d(2.0, -1.0, 0.0, -4.0, 3.0, 2.5, xs) == [0, 0, 2, 1, 1]
+    # tau_i = -2: inside only for x > 1.25; between 0.5 and 1.25 neither network is certain
+    assert _codes_1d(2.0, -1.0, 0.0, -4.0, 3.0, -2.0, [0.0, 0.5, 0.75, 1.25, 1.5]) == [0, 2, 2, 2, 1]
+
+
+def test_three_way_respects_labels_on_the_calibration_set():
+    rng = np.random.default_rng(21)
+    n = 20_000
+    y = (rng.random(n) < 0.35).astype(np.uint8)
+    # noisy logits of a bound and of a complement bound
+    z_o = np.where(y == 1, 2.0, -2.0) + rng.standard_normal(n) * 1.5
+    z_i = np.where(y == 1, -2.0, 2.0) + rng.standard_normal(n) * 1.5
+    tau_o, _ = O.calibrate(z_o, y)
+    tau_i, _ = O.calibrate(z_i, 1 - y)
+    c = O.three_way(z_o, tau_o, z_i, tau_i)
+    assert not np.any((c == 0) & (y == 1))  # certainly outside is never a hit
+    assert not np.any((c == 1) & (y == 0))  # certainly inside is never a miss
+    # on the calibration set no query is claimed by both networks
+    assert not np.any((z_o < tau_o) & (z_i < tau_i))
+    assert np.sum(c == 0) > 0 and np.sum(c == 1) > 0 and np.sum(c == 2) > 0
