@@ -493,6 +493,15 @@ def run_c2e(args):
                                                       out=out), args.steps, args.warmup)
     plain_ms = ctx.time_ms(lambda: late.query(eq, margin=MARGIN, out=out), max(3, args.steps // 4))
     dplain = nb.bits_to_numpy(late.query(eq, margin=MARGIN), n)
+    # the same two networks as a bound and an inverted bound: the broad-phase three-way
+    # class of Sec. 5 (certainly outside / certainly inside / neither)
+    codes = torch.empty(n, dtype=torch.uint8, device=dev)
+    tw_stats = torch.zeros(4, dtype=torch.int64, device=dev)
+    nb.query_three_way(late, early, eq, margin_outer=MARGIN, margin_inner=1e-3, out=codes, stats=tw_stats)
+    tw = tw_stats.cpu().numpy()
+    tc = codes.cpu().numpy()
+    tw_ms = ctx.time_ms(lambda: nb.query_three_way(late, early, eq, margin_outer=MARGIN, margin_inner=1e-3,
+                                                   out=codes), max(3, args.steps // 4))
     if ctx.rank != 0:
         return ctx.emit(None)
     line = base_line(ctx, "neural-bound queries/s at 0 FN (3D points, neural early-out + split-FP16 late network)",
@@ -506,7 +515,11 @@ def run_c2e(args):
                  "fp_rate_without_early_out": float(np.mean(~y & dplain)),
                  "early_inside_fraction": est["n_early_inside"] / n,
                  "without_early_out_queries_per_s": n / (plain_ms / 1000.0),
-                 "speedup_vs_without": plain_ms / ms, "cpu_baseline": None, "e2e": None})
+                 "speedup_vs_without": plain_ms / ms, "cpu_baseline": None, "e2e": None,
+                 "three_way": {"queries_per_s": n / (tw_ms / 1000.0), "certainly_out": int(tw[0]),
+                               "certainly_in": int(tw[1]), "neither": int(tw[2]), "conflicts": int(tw[3]),
+                               "certain_and_wrong": int(np.sum((tc == 0) & y) + np.sum((tc == 1) & ~y)),
+                               "launches": 9}})
     ctx.emit(line)
 
 

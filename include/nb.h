@@ -198,6 +198,30 @@ typedef struct {
 nb_status nb_query_early_out(nb_model *early, nb_model *late, const float *q, int64_t n, float margin_early,
                              float margin_late, uint32_t *out_bits, nb_early_stats *host_stats, void *stream);
 
+/* Inverted bounds and the broad-phase three-way test (Sec. 5): swapping the asymmetry
+ * weights gives a network that conservatively bounds where the object is certainly hit;
+ * that network with its logit negated is a bound of the complement 1 - g, trained with the
+ * usual weights on inverted labels (nb_bits_not) and calibrated on them.  `outer` is the
+ * bounding network of g (decision 0: certainly outside), `inner` the bound of 1 - g
+ * (decision 0: certainly inside).  codes[i] (one byte per query, caller-owned device
+ * buffer of n bytes) is 0 certainly outside, 1 certainly inside, 2 neither: the queries a
+ * collision test must still test exactly.  A query that both networks call certain, which
+ * no query of either calibration set can be, gets 2 and is counted as a conflict.  Both
+ * networks take the same input width; each is decided with its own margin and certified
+ * re-check as in nb_query.  dev_stats (device memory, may be NULL) is added to.
+ * Asynchronous on stream (no host synchronisation; capturable in a CUDA graph once the
+ * workspace, owned by `outer`, has grown to n queries: a growth synchronises the device).
+ * EINVAL for null models or pointers with n > 0, differing input widths, n outside
+ * [0, 2^32). */
+typedef struct {
+    uint64_t n_out;       /* code 0 */
+    uint64_t n_in;        /* code 1 */
+    uint64_t n_neither;   /* code 2, conflicts included */
+    uint64_t n_conflict;  /* both networks certain, contradicting each other */
+} nb_three_way_stats;
+nb_status nb_query_three_way(nb_model *outer, nb_model *inner, const float *q, int64_t n, float margin_outer,
+                             float margin_inner, uint8_t *codes, nb_three_way_stats *dev_stats, void *stream);
+
 /* out[i] = 1 - in[i] for the n bits of a label or decision array (bits past n cleared);
  * in and out may be the same buffer.  Asynchronous on stream. */
 nb_status nb_bits_not(const uint32_t *in, int64_t n, uint32_t *out, void *stream);

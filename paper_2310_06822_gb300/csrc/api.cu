@@ -109,7 +109,7 @@ struct nb_model {
     // library-owned scratch, grown on demand
     void *ws = nullptr;
     size_t ws_bytes = 0;
-    void *eo_ws = nullptr;  // early-out scratch (when this model is the late network)
+    void *eo_ws = nullptr;  // early-out scratch (this model as the late network) or three-way scratch (as the outer)
     size_t eo_bytes = 0;
     // low-precision weight images for the tensor-core paths
     TcModel tc{};
@@ -428,6 +428,21 @@ extern "C" nb_status nb_query(nb_model *m, const float *q, int64_t n, float marg
     return nb_launch_recheck(d, m->gamma, q, tau, out_bits, dev_stats, ws, n, s);
 }
 
+// the workspace of the early-out and three-way queries, owned by one model; grows on demand
+static nb_status ensure_eo_ws(nb_model *m, size_t need) {
+    if (need <= m->eo_bytes) return NB_OK;
+    NB_CUDA(cudaDeviceSynchronize());
+    cudaFree(m->eo_ws);
+    m->eo_ws = nullptr;
+    m->eo_bytes = 0;
+    if (cudaMalloc(&m->eo_ws, need) != cudaSuccess) {
+        cudaGetLastError();
+        return nb_fail(NB_ENOMEM, "workspace allocation failed");
+    }
+    m->eo_bytes = need;
+    return NB_OK;
+}
+
 extern "C" nb_status nb_query_early_out(nb_model *early, nb_model *late, const float *q, int64_t n,
                                         float margin_early, float margin_late, uint32_t *out_bits,
                                         nb_early_stats *host_stats, void *stream) {
@@ -441,17 +456,8 @@ extern "C" nb_status nb_query_early_out(nb_model *early, nb_model *late, const f
     const int w = late->widths[0];
     const size_t words = align256((size_t)((n + 31) / 32) * 4), list = align256((size_t)n * 4);
     const size_t need = 256 + 2 * words + list + align256((size_t)n * w * sizeof(float));
-    if (need > late->eo_bytes) {
-        NB_CUDA(cudaDeviceSynchronize());
-        cudaFree(late->eo_ws);
-        late->eo_ws = nullptr;
-        late->eo_bytes = 0;
-        if (cudaMalloc(&late->eo_ws, need) != cudaSuccess) {
-            cudaGetLastError();
-            return nb_fail(NB_ENOMEM, "nb_query_early_out: workspace allocation failed");
-        }
-        late->eo_bytes = need;
-    }
+    nb_status st = ensure_eo_ws(late, need);
+    if (st != NB_OK) return st;
     char *base = (char *)late->eo_ws;
     unsigned *count = (unsigned *)base;
     uint32_t *bits_e = (uint32_t *)(base + 256);
@@ -459,7 +465,7 @@ extern "C" nb_status nb_query_early_out(nb_model *early, nb_model *late, const f
     unsigned *idx = (unsigned *)(base + 256 + 2 * words);
     float *qc = (float *)(base + 256 + 2 * words + list);
     // 1. the early network on every row (certified decisions against its threshold)
-    nb_status st = nb_query(early, q, n, margin_early, bits_e, nullptr, nullptr, stream);
+    st = nb_query(early, q, n, margin_early, bits_e, nullptr, nullptr, stream);
     if (st != NB_OK) return st;
     // 2. rows it settles are inside; the others are listed
     st = nb_launch_early_compact(bits_e, n, count, idx, out_bits, s);
@@ -481,6 +487,27 @@ extern "C" nb_status nb_query_early_out(nb_model *early, nb_model *late, const f
         host_stats->n_late = m;
     }
     return NB_OK;
+}
+
+extern "C" nb_status nb_query_three_way(nb_model *outer, nb_model *inner, const float *q, int64_t n,
+                                        float margin_outer, float margin_inner, uint8_t *codes,
+                                        nb_three_way_stats *dev_stats, void *stream) {
+    if (!outer || !inner) return nb_fail(NB_EINVAL, "nb_query_three_way: null model");
+    if (outer->widths[0] != inner->widths[0]) return nb_fail(NB_EINVAL, "nb_query_three_way: input widths differ");
+    if (n < 0 || n >= (int64_t)1 << 32) return nb_fail(NB_EINVAL, "nb_query_three_way: n must be in [0, 2^32)");
+    if (n > 0 && (!q || !codes)) return nb_fail(NB_EINVAL, "nb_query_three_way: null pointer");
+    if (n == 0) return NB_OK;
+    const size_t words = align256((size_t)((n + 31) / 32) * 4);
+    nb_status st = ensure_eo_ws(outer, 2 * words);
+    if (st != NB_OK) return st;
+    uint32_t *bits_o = (uint32_t *)outer->eo_ws;
+    uint32_t *bits_i = (uint32_t *)((char *)outer->eo_ws + words);
+    // both bounds, each certified against its own threshold
+    st = nb_query(outer, q, n, margin_outer, bits_o, nullptr, nullptr, stream);
+    if (st != NB_OK) return st;
+    st = nb_query(inner, q, n, margin_inner, bits_i, nullptr, nullptr, stream);
+    if (st != NB_OK) return st;
+    return nb_launch_three_way(bits_o, bits_i, n, codes, dev_stats, (cudaStream_t)stream);
 }
 
 extern "C" nb_status nb_bits_not(const uint32_t *in, int64_t n, uint32_t *out, void *stream) {

@@ -75,6 +75,8 @@ nb_status nb_launch_early_gather(const float *q, int w, const unsigned *idx, int
 nb_status nb_launch_early_scatter(const uint32_t *bits_c, const unsigned *idx, int64_t m, uint32_t *out_bits,
                                   cudaStream_t s);
 nb_status nb_launch_bits_not(const uint32_t *in, int64_t n, uint32_t *out, cudaStream_t s);
+nb_status nb_launch_three_way(const uint32_t *bits_outer, const uint32_t *bits_inner, int64_t n, uint8_t *codes,
+                              nb_three_way_stats *st, cudaStream_t s);
 
 // pT <- p with every weight matrix transposed, for n_objects parameter sets P apart
 nb_status nb_launch_transpose(const MlpDesc &d, float *pT, int n_objects, long long P, cudaStream_t s);

@@ -97,3 +97,45 @@ nb_status nb_launch_bits_not(const uint32_t *in, int64_t n, uint32_t *out, cudaS
     NB_CUDA(cudaGetLastError());
     return NB_OK;
 }
+
+// Broad-phase three-way class (Sec. 5, inverted bounds): decision 0 of the outer bound is
+// "certainly outside", decision 0 of the complement bound "certainly inside"; neither, or
+// both (a conflict), leaves the query to the exact test.  One thread per query, one byte
+// out; counts reduced per warp.
+namespace {
+__global__ void three_way_kernel(const uint32_t *__restrict__ bits_o, const uint32_t *__restrict__ bits_i, long long n,
+                                 uint8_t *__restrict__ codes, nb_three_way_stats *st) {
+    unsigned long long c_out = 0, c_in = 0, c_nei = 0, c_conf = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const bool out = !((bits_o[i >> 5] >> (i & 31)) & 1u);
+        const bool in = !((bits_i[i >> 5] >> (i & 31)) & 1u);
+        const uint8_t c = (out && !in) ? 0 : ((in && !out) ? 1 : 2);
+        codes[i] = c;
+        c_out += c == 0;
+        c_in += c == 1;
+        c_nei += c == 2;
+        c_conf += in && out;
+    }
+    if (!st) return;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        c_out += __shfl_xor_sync(FULL, c_out, o);
+        c_in += __shfl_xor_sync(FULL, c_in, o);
+        c_nei += __shfl_xor_sync(FULL, c_nei, o);
+        c_conf += __shfl_xor_sync(FULL, c_conf, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (c_out) atomicAdd((unsigned long long *)&st->n_out, c_out);
+        if (c_in) atomicAdd((unsigned long long *)&st->n_in, c_in);
+        if (c_nei) atomicAdd((unsigned long long *)&st->n_neither, c_nei);
+        if (c_conf) atomicAdd((unsigned long long *)&st->n_conflict, c_conf);
+    }
+}
+}  // namespace
+
+nb_status nb_launch_three_way(const uint32_t *bits_outer, const uint32_t *bits_inner, int64_t n, uint8_t *codes,
+                              nb_three_way_stats *st, cudaStream_t s) {
+    three_way_kernel<<<grid_for(n, 256), 256, 0, s>>>(bits_outer, bits_inner, (long long)n, codes, st);
+    NB_CUDA(cudaGetLastError());
+    return NB_OK;
+}

@@ -29,7 +29,8 @@ EXPORTS = ["nb_model_create", "nb_model_destroy", "nb_model_param_count", "nb_mo
            "nb_plan_create", "nb_plan_destroy", "nb_group_create", "nb_group_destroy", "nb_group_param_count",
            "nb_group_set_params", "nb_group_get_params", "nb_group_get_grad", "nb_group_set_tau", "nb_group_get_tau",
            "nb_group_set_schedule", "nb_group_sync_schedule", "nb_group_reserve", "nb_train_step_grouped",
-           "nb_query_grouped", "nb_calibrate_grouped", "nb_cascade_bin", "nb_cascade_exact", "nb_sample", "nb_group_autotune", "nb_query_early_out", "nb_bits_not"]
+           "nb_query_grouped", "nb_calibrate_grouped", "nb_cascade_bin", "nb_cascade_exact", "nb_sample", "nb_group_autotune", "nb_query_early_out", "nb_bits_not",
+           "nb_query_three_way"]
 
 
 class NBError(RuntimeError):
@@ -108,6 +109,7 @@ def lib():
                 "nb_group_autotune": ([P, P, i32, i32, P, P, P, i32, i32, P, P, P], st),
                 "nb_query_early_out": ([P, P, P, i64, ctypes.c_float, ctypes.c_float, P, P, P], st),
                 "nb_bits_not": ([P, i64, P, P], st),
+                "nb_query_three_way": ([P, P, P, i64, ctypes.c_float, ctypes.c_float, P, P, P], st),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -473,6 +475,26 @@ def query_early_out(early: Model, late: Model, q: torch.Tensor, margin_early: fl
     _check(lib().nb_query_early_out(early._h, late._h, _ptr(q), n, float(margin_early), float(margin_late),
                                     _ptr(out), ctypes.byref(st), _stream(stream)))
     return out, {"n_early_inside": int(st[0]), "n_late": int(st[1])}
+
+
+THREE_WAY_OUT, THREE_WAY_IN, THREE_WAY_NEITHER = 0, 1, 2
+
+
+def query_three_way(outer: Model, inner: Model, q: torch.Tensor, margin_outer: float = 0.0,
+                    margin_inner: float = 0.0, out: torch.Tensor | None = None, stats: torch.Tensor | None = None,
+                    stream=None) -> torch.Tensor:
+    """Broad-phase class of each query from a bound (outer) and a bound of the complement
+    (inner) (nb_query_three_way): uint8 codes 0 certainly outside, 1 certainly inside,
+    2 neither.  stats, if given, is a device uint64 tensor of 4 (out, in, neither,
+    conflicts) that is added to."""
+    n = q.shape[0]
+    if out is None:
+        out = torch.empty(n, dtype=torch.uint8, device=q.device)
+    if stats is not None and (stats.dtype != torch.int64 or stats.numel() < 4 or not stats.is_cuda):
+        raise ValueError("stats must be a device int64 tensor of 4")
+    _check(lib().nb_query_three_way(outer._h, inner._h, _ptr(q), n, float(margin_outer), float(margin_inner),
+                                    _ptr(out), _ptr(stats), _stream(stream)))
+    return out
 
 
 def step_stats_tensor(device="cuda") -> torch.Tensor:
