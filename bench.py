@@ -689,6 +689,7 @@ def run_c5(args):
     K = 1024
     ms_ = I.make_multi_scene(5000, K, 32)
     ws = nb.WorldScene(ms_, dev)
+    ix = nb.CascadeIndex(ws)  # stage 1 walks the 4-wide tree of object boxes
     T = args.train_steps if args.train_steps != TRAIN_STEPS else 2000
     # training pairs from the deployment distribution: world rays binned and moved into
     # each object's frame by the cascade's own first stage, labelled by the exact stage
@@ -697,7 +698,7 @@ def run_c5(args):
     pools = []
     for j in range(n_pools):
         r = torch.as_tensor(I.sample_world_rays(5100 + j, pool_rays), device=dev)
-        off, off_d, pair_ray, pair_q, _ = nb.cascade_bin(ws, r, canonical=True)
+        off, off_d, pair_ray, pair_q, _ = nb.cascade_bin(ws, r, canonical=True, index=ix)
         rows = int(off[-1])
         lab = torch.zeros(nb.n_words(rows), dtype=torch.int32, device=dev)
         nb.cascade_exact(ws, r, pair_ray, off_d, rows, pair_hits=lab)
@@ -722,7 +723,7 @@ def run_c5(args):
     # over chunks of (zmin - eps rounded down) is the threshold of all pairs together
     taus = np.full(K, np.inf)
     for ch in chunks:
-        off, off_d, pair_ray, pair_q, _ = nb.cascade_bin(ws, ch, canonical=True)
+        off, off_d, pair_ray, pair_q, _ = nb.cascade_bin(ws, ch, canonical=True, index=ix)
         rows = int(off[-1])
         lab = torch.zeros(nb.n_words(rows), dtype=torch.int32, device=dev)
         nb.cascade_exact(ws, ch, pair_ray, off_d, rows, pair_hits=lab)
@@ -740,7 +741,7 @@ def run_c5(args):
     def cascade_step(collect=False):
         # box + ball binning, neural bound per object, exact test of the survivors
         for ci, ch in enumerate(chunks):
-            off, off_d, pair_ray, pair_q, st = nb.cascade_bin(ws, ch, canonical=True)
+            off, off_d, pair_ray, pair_q, st = nb.cascade_bin(ws, ch, canonical=True, index=ix)
             if collect:
                 for k in bin_stats:
                     bin_stats[k] += int(st[k])
@@ -751,7 +752,7 @@ def run_c5(args):
 
     def plain_step():
         for ci, ch in enumerate(chunks):
-            off, off_d, pair_ray, _, st = nb.cascade_bin(ws, ch, canonical=False)
+            off, off_d, pair_ray, _, st = nb.cascade_bin(ws, ch, canonical=False, index=ix)
             nb.cascade_exact(ws, ch, pair_ray, off_d, int(off[-1]), ray_hits=hits_p[ci * CH // 32:], stats=pst)
 
     est.zero_()
@@ -769,12 +770,17 @@ def run_c5(args):
     # fraction p_a does, at t_nn more per pair.  The network pays off when an exact pair
     # test costs more than t_nn / (1 - p_a).
     ch = chunks[0]
-    off, off_d, pair_ray, pair_q, _ = nb.cascade_bin(ws, ch, canonical=True)
+    off, off_d, pair_ray, pair_q, _ = nb.cascade_bin(ws, ch, canonical=True, index=ix)
     rows = int(off[-1])
     plan_c = nb.Plan(off, chunk_rows=2048)
     hb = torch.zeros(nb.n_words(ch.shape[0]), dtype=torch.int32, device=dev)
     neural = g.query(plan_c, pair_q, margin=MARGIN)
-    t_bin = ctx.time_ms(lambda: nb.cascade_bin(ws, ch, canonical=True), 2)
+    t_bin = ctx.time_ms(lambda: nb.cascade_bin(ws, ch, canonical=True, index=ix), 2)
+    # the same stage without the index: every ray against every object's box
+    t_bin_all = ctx.time_ms(lambda: nb.cascade_bin(ws, ch, canonical=True), 2)
+    t_bin_plain = ctx.time_ms(lambda: nb.cascade_bin(ws, ch, canonical=False, index=ix), 2)
+    t_bin_plain_all = ctx.time_ms(lambda: nb.cascade_bin(ws, ch, canonical=False), 2)
+    same_pairs = bool(np.array_equal(nb.cascade_bin(ws, ch, canonical=True)[0], off))
     t_nn = ctx.time_ms(lambda: g.query(plan_c, pair_q, margin=MARGIN, out=neural), 3)
     t_exact_all = ctx.time_ms(lambda: nb.cascade_exact(ws, ch, pair_ray, off_d, rows, ray_hits=hb), 3)
     t_exact_pass = ctx.time_ms(lambda: nb.cascade_exact(ws, ch, pair_ray, off_d, rows, pass_bits=neural,
@@ -789,10 +795,10 @@ def run_c5(args):
     held = torch.as_tensor(I.sample_world_rays(5999, min(NR, 4 << 20)), device=dev)
     hh_c = torch.zeros(nb.n_words(held.shape[0]), dtype=torch.int32, device=dev)
     hh_p = torch.zeros_like(hh_c)
-    off, off_d, pair_ray, pair_q, _ = nb.cascade_bin(ws, held, canonical=True)
+    off, off_d, pair_ray, pair_q, _ = nb.cascade_bin(ws, held, canonical=True, index=ix)
     neural = g.query(nb.Plan(off, chunk_rows=2048), pair_q, margin=MARGIN)
     nb.cascade_exact(ws, held, pair_ray, off_d, int(off[-1]), pass_bits=neural, ray_hits=hh_c)
-    off, off_d, pair_ray, _, _ = nb.cascade_bin(ws, held, canonical=False)
+    off, off_d, pair_ray, _, _ = nb.cascade_bin(ws, held, canonical=False, index=ix)
     nb.cascade_exact(ws, held, pair_ray, off_d, int(off[-1]), ray_hits=hh_p)
     held_fn = int(np.sum(nb.bits_to_numpy(hh_p, held.shape[0]) & ~nb.bits_to_numpy(hh_c, held.shape[0])))
     # cost of one exact pair test relative to one network query at which the cascade pays
@@ -802,12 +808,16 @@ def run_c5(args):
                      "f16x3 (split fp16 operands, fp32 accumulate)",
                      {"workload": "learned-culler cascade: 1024 objects of 32 spheres in [-10,10]^3, 6->128x3->1 per "
                                   "object, 64M rays", "n_rays": NR, "train_steps": T,
+                      "stage1": "4-wide tree of object boxes (Morton order, median splits), 2 walks per call",
                       "training": f"{n_pools} x {pool_rays} world rays through the box/ball stage, exact labels",
                       "calibration": "thresholds calibrated on the benchmark rays' own pairs"},
                      clocks, args.steps * len(chunks) * 6)  # bin x2, grouped query (3), exact
     line.update({"fn_vs_plain": int(np.sum(hp & ~hc)), "hits_equal_plain": bool(np.array_equal(hc, hp)),
                  "stages_first_chunk_ms": {"bin": t_bin, "neural": t_nn, "exact_all_pairs": t_exact_all,
                                            "exact_passed_pairs": t_exact_pass},
+                 "stage1_first_chunk_ms": {"box_ball_index": t_bin, "box_ball_every_object": t_bin_all,
+                                           "box_index": t_bin_plain, "box_every_object": t_bin_plain_all,
+                                           "index_counts_equal_every_object": same_pairs},
                  "benefit": {"p_a": p_a, "t_nn_per_pair_ns": 1e6 * t_nn_pair, "t_exact_per_pair_ns": 1e6 * t_exact_pair,
                              "break_even_exact_ns": 1e6 * break_even,
                              "exact_cost_factor_needed": break_even / max(t_exact_pair, 1e-30)},

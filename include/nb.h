@@ -341,6 +341,43 @@ typedef struct {
 nb_status nb_cascade_bin(const nb_scene *scene, const float *rays, int64_t n, int32_t canonical,
                          unsigned long long *counts, const int64_t *offsets, uint32_t *pair_ray, float *pair_q,
                          nb_cascade_stats *dev_stats, void *stream);
+/* Spatial index over the scene's objects for stage 1.  Sec. 3.2 stacks bounds into
+ * hierarchies the way bounding boxes form a BVH; the tree here follows the linear builder
+ * of the paper's BVH baseline (Sec. 4.1): objects in Morton order of their box centres
+ * (10 bits per axis over the bounding box of the centres, ties by object index), split at
+ * the median of that order, two median levels per node so that every node has up to four
+ * children, and every node holds its children's boxes (exact unions of the object boxes
+ * below them).  The floating-point slab test of stage 1 is monotone under box inclusion
+ * (a ray that passes a box passes every box containing it), so the indexed stage 1 finds
+ * exactly the pairs of nb_cascade_bin while testing only the boxes along the way.
+ * nb_cascade_index_create copies scene->aabb to the host, builds there and uploads the
+ * tree: synchronous.  EINVAL for a bad scene, ENOMEM, ECUDA. */
+typedef struct nb_cascade_index nb_cascade_index;
+nb_status nb_cascade_index_create(const nb_scene *scene, nb_cascade_index **out);
+nb_status nb_cascade_index_destroy(nb_cascade_index *index);
+/* Stage 1 through the index: arguments, results, padding rule and statistics as
+ * nb_cascade_bin (the same pairs and counts; the rows of one object may come in another
+ * order, as they may between two calls of nb_cascade_bin).  EINVAL if the index was
+ * built for another object count. */
+nb_status nb_cascade_bin_indexed(const nb_cascade_index *index, const nb_scene *scene, const float *rays, int64_t n,
+                                 int32_t canonical, unsigned long long *counts, const int64_t *offsets,
+                                 uint32_t *pair_ray, float *pair_q, nb_cascade_stats *dev_stats, void *stream);
+/* The index's tree, built on the host from host boxes (no device involved), as
+ * nb_cascade_index_create builds it.  nodes[0] is the root; a child slot c of a node holds
+ * a box (lo[axis][c], hi[axis][c]) and child[c] >= 0 (a node index), -1 - k (object k)
+ * or NB_BVH_EMPTY (unused slot, box zero).  nodes must hold
+ * nb_cascade_index_max_nodes(n_objects) entries; *n_nodes receives the count used and
+ * *depth the number of node levels.  EINVAL for n_objects outside 1 .. 4096 or null
+ * pointers. */
+#define NB_BVH_EMPTY (-2147483647 - 1)
+typedef struct {
+    float lo[3][4];
+    float hi[3][4];
+    int32_t child[4];
+} nb_bvh4_node;
+int32_t nb_cascade_index_max_nodes(int32_t n_objects);
+nb_status nb_cascade_index_build_host(const float *aabb, int32_t n_objects, nb_bvh4_node *nodes, int32_t *n_nodes,
+                                      int32_t *depth);
 /* Stage 3: rows [0, rows) with pair_ray != 0xffffffff and (pass_bits == NULL or its bit
  * set) are tested exactly against their object's spheres (integer arithmetic on the
  * grid); a hit ORs the ray's bit into ray_hits and the row's bit into pair_hits (either

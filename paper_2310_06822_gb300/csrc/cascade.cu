@@ -12,6 +12,12 @@
 #include "common.cuh"
 #include "exact.cuh"
 
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <utility>
+#include <vector>
+
 using namespace nbexact;
 
 namespace {
@@ -22,6 +28,62 @@ constexpr unsigned NO_RAY = 0xffffffffu;
 struct ObjS {
     float lo[3], hi[3], c[3];
 };
+
+// slab test of the half-line o + s d, s >= 0, against the box [lo, hi]; inv = 1 / d.
+// Monotone under box inclusion: every rounding step is monotone in lo and hi, so a ray
+// that passes a box passes every box that contains it.
+__device__ __forceinline__ bool slab_hit(const float o[3], const float d[3], const float inv[3], const float lo[3],
+                                         const float hi[3]) {
+    float t0 = 0.f, t1 = INFINITY;
+    bool hit = true;
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        if (d[i] == 0.f) {
+            hit = hit && o[i] >= lo[i] && o[i] <= hi[i];
+        } else {
+            float ta = (lo[i] - o[i]) * inv[i], tb = (hi[i] - o[i]) * inv[i];
+            if (ta > tb) {
+                const float tmp = ta;
+                ta = tb;
+                tb = tmp;
+            }
+            t0 = fmaxf(t0, ta);
+            t1 = fminf(t1, tb);
+        }
+    }
+    return hit && t0 <= t1;
+}
+
+// the ray in the frame of an object centred at c, its origin moved to where it enters the
+// ball |x| = R (R2 = R^2): q6 = (entry point, direction); false if it misses the ball
+__device__ __forceinline__ bool canon_entry(const float o[3], const float d[3], const float c[3], float R2,
+                                            float q6[6]) {
+    // object frame: w = o - c (exact on the grid); entry into |x| = R:
+    // |w + s d|^2 = R^2, s = (-b - sqrt(b^2 - |d|^2 (|w|^2 - R^2))) / |d|^2
+    float w[3];
+    for (int i = 0; i < 3; i++) w[i] = __fsub_rn(o[i], c[i]);
+    const float b = __fadd_rn(__fadd_rn(__fmul_rn(w[0], d[0]), __fmul_rn(w[1], d[1])), __fmul_rn(w[2], d[2]));
+    const float dd = __fadd_rn(__fadd_rn(__fmul_rn(d[0], d[0]), __fmul_rn(d[1], d[1])), __fmul_rn(d[2], d[2]));
+    const float ww = __fadd_rn(__fadd_rn(__fmul_rn(w[0], w[0]), __fmul_rn(w[1], w[1])), __fmul_rn(w[2], w[2]));
+    // b^2 - dd (ww - R^2) = dd R^2 - |w x d|^2 (Lagrange), free of the cancellation
+    // between the two large terms when the origin is far from the object
+    const float cx = fmaf(w[1], d[2], -__fmul_rn(w[2], d[1]));
+    const float cy = fmaf(w[2], d[0], -__fmul_rn(w[0], d[2]));
+    const float cz = fmaf(w[0], d[1], -__fmul_rn(w[1], d[0]));
+    const float cr2 = __fadd_rn(__fadd_rn(__fmul_rn(cx, cx), __fmul_rn(cy, cy)), __fmul_rn(cz, cz));
+    const float disc = __fsub_rn(__fmul_rn(dd, R2), cr2);
+    if (!(disc >= 0.f && dd > 0.f)) return false;
+    // smaller root without cancellation: s = c / (-b + sqrt(disc)) when -b > 0
+    const float sq_disc = __fsqrt_rn(disc);
+    const float cc = __fsub_rn(ww, R2);
+    float s = -b > 0.f ? __fdiv_rn(cc, __fadd_rn(-b, sq_disc)) : __fdiv_rn(__fsub_rn(-b, sq_disc), dd);
+    s = fmaxf(s, 0.f);
+    for (int i = 0; i < 3; i++) {
+        q6[i] = __fadd_rn(w[i], __fmul_rn(s, d[i]));
+        q6[3 + i] = d[i];
+    }
+    return true;
+}
 
 template <bool CANON, bool SCATTER>
 __global__ void __launch_bounds__(256)
@@ -56,54 +118,10 @@ __global__ void __launch_bounds__(256)
         for (int k = 0; k < K; k++) {
             const ObjS ob = objs[k];
             // slab test of the half-line against the box (the box is conservative: inflated)
-            float t0 = 0.f, t1 = INFINITY;
-            bool hit = valid;
-#pragma unroll
-            for (int i = 0; i < 3; i++) {
-                if (d[i] == 0.f) {
-                    hit = hit && o[i] >= ob.lo[i] && o[i] <= ob.hi[i];
-                } else {
-                    float ta = (ob.lo[i] - o[i]) * inv[i], tb = (ob.hi[i] - o[i]) * inv[i];
-                    if (ta > tb) {
-                        const float tmp = ta;
-                        ta = tb;
-                        tb = tmp;
-                    }
-                    t0 = fmaxf(t0, ta);
-                    t1 = fminf(t1, tb);
-                }
-            }
-            hit = hit && t0 <= t1;
+            const bool hit = valid && slab_hit(o, d, inv, ob.lo, ob.hi);
             float q6[6];
             bool keep = hit;
-            if (CANON && hit) {
-                // object frame: w = o - c (exact on the grid); entry into |x| = R:
-                // |w + s d|^2 = R^2, s = (-b - sqrt(b^2 - |d|^2 (|w|^2 - R^2))) / |d|^2
-                float w[3];
-                for (int i = 0; i < 3; i++) w[i] = __fsub_rn(o[i], ob.c[i]);
-                const float b = __fadd_rn(__fadd_rn(__fmul_rn(w[0], d[0]), __fmul_rn(w[1], d[1])), __fmul_rn(w[2], d[2]));
-                const float dd = __fadd_rn(__fadd_rn(__fmul_rn(d[0], d[0]), __fmul_rn(d[1], d[1])), __fmul_rn(d[2], d[2]));
-                const float ww = __fadd_rn(__fadd_rn(__fmul_rn(w[0], w[0]), __fmul_rn(w[1], w[1])), __fmul_rn(w[2], w[2]));
-                // b^2 - dd (ww - R^2) = dd R^2 - |w x d|^2 (Lagrange), free of the cancellation
-                // between the two large terms when the origin is far from the object
-                const float cx = fmaf(w[1], d[2], -__fmul_rn(w[2], d[1]));
-                const float cy = fmaf(w[2], d[0], -__fmul_rn(w[0], d[2]));
-                const float cz = fmaf(w[0], d[1], -__fmul_rn(w[1], d[0]));
-                const float cr2 = __fadd_rn(__fadd_rn(__fmul_rn(cx, cx), __fmul_rn(cy, cy)), __fmul_rn(cz, cz));
-                const float disc = __fsub_rn(__fmul_rn(dd, R2), cr2);
-                keep = disc >= 0.f && dd > 0.f;
-                if (keep) {
-                    // smaller root without cancellation: s = c / (-b + sqrt(disc)) when -b > 0
-                    const float sq_disc = __fsqrt_rn(disc);
-                    const float c = __fsub_rn(ww, R2);
-                    float s = -b > 0.f ? __fdiv_rn(c, __fadd_rn(-b, sq_disc)) : __fdiv_rn(__fsub_rn(-b, sq_disc), dd);
-                    s = fmaxf(s, 0.f);
-                    for (int i = 0; i < 3; i++) {
-                        q6[i] = __fadd_rn(w[i], __fmul_rn(s, d[i]));
-                        q6[3 + i] = d[i];
-                    }
-                }
-            }
+            if (CANON && hit) keep = canon_entry(o, d, ob.c, R2, q6);
             const unsigned bh = __ballot_sync(FULL, hit), bk = __ballot_sync(FULL, keep);
             if (lane == 0) {
                 n_aabb += __popc(bh);
@@ -126,6 +144,127 @@ __global__ void __launch_bounds__(256)
     if (st && lane == 0 && !SCATTER) {
         if (n_aabb) atomicAdd(&st->aabb_pairs, n_aabb);
         if (n_ball) atomicAdd(&st->ball_pairs, n_ball);
+    }
+}
+
+// Stage 1 through the 4-wide tree of object boxes: one ray per thread, depth-first with a
+// short stack (the builder bounds the depth, so the stack never fills; the guard only keeps
+// the writes in bounds).  Kept pairs are counted per object in shared memory.  The counting
+// call adds the block's counts to counts[] once at the end; the scatter call walks each
+// tile of rays twice: first to count, then, after one global reservation per object and
+// tile, to write each pair into its reserved row.
+constexpr int BVH_STACK = 32;
+constexpr int BVH_TPB = 256;
+
+template <class Visit>
+__device__ __forceinline__ void bvh_walk(const nb_bvh4_node *nodes, const float o[3], const float d[3],
+                                         const float inv[3], Visit visit) {
+    int stack[BVH_STACK];
+    int sp = 0, node = 0;
+    while (true) {
+        const nb_bvh4_node &nd = nodes[node];
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            const int ch = nd.child[c];
+            if (ch == NB_BVH_EMPTY) continue;
+            const float lo[3] = {nd.lo[0][c], nd.lo[1][c], nd.lo[2][c]};
+            const float hi[3] = {nd.hi[0][c], nd.hi[1][c], nd.hi[2][c]};
+            if (!slab_hit(o, d, inv, lo, hi)) continue;
+            if (ch >= 0) {
+                if (sp < BVH_STACK) stack[sp++] = ch;
+            } else {
+                visit(-1 - ch);
+            }
+        }
+        if (sp == 0) break;
+        node = stack[--sp];
+    }
+}
+
+template <bool CANON, bool SCATTER>
+__global__ void __launch_bounds__(BVH_TPB)
+    bin_bvh_kernel(int K, int n_nodes, float R2, const nb_bvh4_node *__restrict__ nodes_g, const float *__restrict__ oc,
+                   const float *__restrict__ rays, long long n, unsigned long long *counts,
+                   const long long *__restrict__ offsets, uint32_t *__restrict__ pair_ray, float *__restrict__ pair_q,
+                   nb_cascade_stats *st) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    nb_bvh4_node *nodes = reinterpret_cast<nb_bvh4_node *>(smem_raw);
+    unsigned *hist = reinterpret_cast<unsigned *>(nodes + n_nodes);
+    unsigned *base = hist + K;  // scatter call only
+    {
+        const int4 *src = reinterpret_cast<const int4 *>(nodes_g);
+        int4 *dst = reinterpret_cast<int4 *>(nodes);
+        const int words = n_nodes * (int)(sizeof(nb_bvh4_node) / sizeof(int4));
+        for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+        for (int k = threadIdx.x; k < K; k += blockDim.x) hist[k] = 0;
+    }
+    __syncthreads();
+    unsigned long long n_aabb = 0, n_ball = 0;
+    const long long tiles = (n + blockDim.x - 1) / blockDim.x;
+    for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const long long r = tile * blockDim.x + threadIdx.x;
+        const bool valid = r < n;
+        float o[3] = {0.f, 0.f, 0.f}, d[3] = {0.f, 0.f, 1.f}, inv[3];
+        if (valid)
+            for (int i = 0; i < 3; i++) {
+                o[i] = rays[r * 6 + i];
+                d[i] = rays[r * 6 + 3 + i];
+            }
+        for (int i = 0; i < 3; i++) inv[i] = 1.0f / d[i];  // +-inf for a zero component
+        auto keep_of = [&](int k, float q6[6]) {
+            if (!CANON) return true;
+            const float c[3] = {__ldg(oc + k * 3), __ldg(oc + k * 3 + 1), __ldg(oc + k * 3 + 2)};
+            return canon_entry(o, d, c, R2, q6);
+        };
+        // pass 1: count the kept pairs per object (and, counting call, the totals)
+        if (valid)
+            bvh_walk(nodes, o, d, inv, [&](int k) {
+                float q6[6];
+                const bool keep = keep_of(k, q6);
+                if (!SCATTER) {
+                    n_aabb++;
+                    n_ball += keep;
+                }
+                if (keep) atomicAdd(hist + k, 1u);
+            });
+        if (!SCATTER) continue;
+        __syncthreads();
+        // one reservation per object and tile; hist becomes the running slot
+        for (int k = threadIdx.x; k < K; k += blockDim.x) {
+            const unsigned c = hist[k];
+            if (c) base[k] = (unsigned)atomicAdd(counts + k, (unsigned long long)c);
+            hist[k] = 0;
+        }
+        __syncthreads();
+        // pass 2: the same walk, each kept pair written to its row
+        if (valid)
+            bvh_walk(nodes, o, d, inv, [&](int k) {
+                float q6[6];
+                if (!keep_of(k, q6)) return;
+                const unsigned slot = atomicAdd(hist + k, 1u);
+                const long long row = offsets[k] + base[k] + slot;
+                pair_ray[row] = (uint32_t)r;
+                if (CANON)
+                    for (int i = 0; i < 6; i++) pair_q[row * 6 + i] = q6[i];
+            });
+        __syncthreads();
+        for (int k = threadIdx.x; k < K; k += blockDim.x) hist[k] = 0;
+        __syncthreads();
+    }
+    if (SCATTER) return;
+    __syncthreads();
+    for (int k = threadIdx.x; k < K; k += blockDim.x)
+        if (hist[k]) atomicAdd(counts + k, (unsigned long long)hist[k]);
+    if (st) {
+#pragma unroll
+        for (int off = 16; off; off >>= 1) {
+            n_aabb += __shfl_xor_sync(FULL, n_aabb, off);
+            n_ball += __shfl_xor_sync(FULL, n_ball, off);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            if (n_aabb) atomicAdd(&st->aabb_pairs, n_aabb);
+            if (n_ball) atomicAdd(&st->ball_pairs, n_ball);
+        }
     }
 }
 
@@ -268,6 +407,224 @@ extern "C" nb_status nb_cascade_exact(const nb_scene *scene, const float *rays, 
                                                scene->centres, scene->radii, rays, pair_ray,
                                                (const long long *)offsets, (long long)rows, pass_bits, ray_hits, pair_hits,
                                                dev_stats);
+    NB_CUDA(cudaGetLastError());
+    return NB_OK;
+}
+
+// ------------------------------------------------------------------ spatial index of objects
+// Host builder: Morton order of the object box centres, median splits two levels at a time
+// (four children per node), child boxes the exact unions of the object boxes below them.
+namespace {
+
+constexpr int BVH_MAX_DEPTH = 10;  // 3 * depth + 1 <= BVH_STACK entries
+
+uint32_t spread10(uint32_t v) {  // bits b9..b0 -> positions 27, 24, ..., 0
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000FFu;
+    v = (v | (v << 8)) & 0x0300F00Fu;
+    v = (v | (v << 4)) & 0x030C30C3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+struct Bvh4Builder {
+    const float *aabb;
+    std::vector<int> order;
+    std::vector<nb_bvh4_node> nodes;
+    int depth = 0;
+
+    void box(int a, int b, float lo[3], float hi[3]) const {
+        for (int i = 0; i < 3; i++) {
+            lo[i] = INFINITY;
+            hi[i] = -INFINITY;
+        }
+        for (int j = a; j < b; j++) {
+            const float *bx = aabb + (size_t)order[j] * 6;
+            for (int i = 0; i < 3; i++) {
+                lo[i] = std::min(lo[i], bx[i]);
+                hi[i] = std::max(hi[i], bx[3 + i]);
+            }
+        }
+    }
+
+    int build(int a, int b, int level) {
+        const int me = (int)nodes.size();
+        nodes.push_back(nb_bvh4_node{});
+        depth = std::max(depth, level);
+        int cut[5], nc;
+        if (b - a <= 4) {
+            nc = b - a;
+            for (int c = 0; c <= nc; c++) cut[c] = a + c;
+        } else {
+            const int m = a + (b - a) / 2;
+            nc = 4;
+            cut[0] = a;
+            cut[1] = a + (m - a) / 2;
+            cut[2] = m;
+            cut[3] = m + (b - m) / 2;
+            cut[4] = b;
+        }
+        nb_bvh4_node nd{};
+        for (int c = 0; c < 4; c++) {
+            if (c >= nc) {
+                nd.child[c] = NB_BVH_EMPTY;
+                continue;
+            }
+            float lo[3], hi[3];
+            box(cut[c], cut[c + 1], lo, hi);
+            for (int i = 0; i < 3; i++) {
+                nd.lo[i][c] = lo[i];
+                nd.hi[i][c] = hi[i];
+            }
+            nd.child[c] = cut[c + 1] - cut[c] == 1 ? -1 - order[cut[c]] : build(cut[c], cut[c + 1], level + 1);
+        }
+        nodes[me] = nd;
+        return me;
+    }
+};
+
+nb_status build_bvh4(const float *aabb, int K, std::vector<nb_bvh4_node> &nodes, int &depth) {
+    for (int k = 0; k < K * 6; k++)
+        if (!std::isfinite(aabb[k])) return nb_fail(NB_EINVAL, "cascade index: non-finite object box");
+    double mn[3], mx[3];
+    for (int i = 0; i < 3; i++) {
+        mn[i] = INFINITY;
+        mx[i] = -INFINITY;
+    }
+    std::vector<double> cen((size_t)K * 3);
+    for (int k = 0; k < K; k++)
+        for (int i = 0; i < 3; i++) {
+            const double c = 0.5 * ((double)aabb[k * 6 + i] + (double)aabb[k * 6 + 3 + i]);
+            cen[(size_t)k * 3 + i] = c;
+            mn[i] = std::min(mn[i], c);
+            mx[i] = std::max(mx[i], c);
+        }
+    std::vector<std::pair<uint32_t, int>> key((size_t)K);
+    for (int k = 0; k < K; k++) {
+        uint32_t code = 0;
+        for (int i = 0; i < 3; i++) {
+            const double u = mx[i] > mn[i] ? (cen[(size_t)k * 3 + i] - mn[i]) / (mx[i] - mn[i]) : 0.0;
+            const uint32_t q = (uint32_t)std::min(1023.0, std::max(0.0, std::floor(u * 1024.0)));
+            code |= spread10(q) << (2 - i);  // x in the highest bit of each triple
+        }
+        key[k] = {code, k};
+    }
+    std::sort(key.begin(), key.end());
+    Bvh4Builder b;
+    b.aabb = aabb;
+    b.order.resize((size_t)K);
+    for (int k = 0; k < K; k++) b.order[k] = key[k].second;
+    b.nodes.reserve((size_t)std::max(1, K - 1));
+    b.build(0, K, 1);
+    if (b.depth > BVH_MAX_DEPTH) return nb_fail(NB_EINVAL, "cascade index: tree too deep");
+    nodes.swap(b.nodes);
+    depth = b.depth;
+    return NB_OK;
+}
+
+}  // namespace
+
+struct nb_cascade_index {
+    int K = 0, n_nodes = 0, depth = 0;
+    nb_bvh4_node *nodes = nullptr;  // device
+};
+
+extern "C" int32_t nb_cascade_index_max_nodes(int32_t n_objects) { return n_objects <= 2 ? 1 : n_objects - 1; }
+
+extern "C" nb_status nb_cascade_index_build_host(const float *aabb, int32_t n_objects, nb_bvh4_node *nodes,
+                                                 int32_t *n_nodes, int32_t *depth) {
+    if (n_objects < 1 || n_objects > 4096) return nb_fail(NB_EINVAL, "cascade index: n_objects must be 1..4096");
+    if (!aabb || !nodes || !n_nodes || !depth) return nb_fail(NB_EINVAL, "cascade index: null pointer");
+    std::vector<nb_bvh4_node> v;
+    int dep = 0;
+    const nb_status st = build_bvh4(aabb, n_objects, v, dep);
+    if (st != NB_OK) return st;
+    std::copy(v.begin(), v.end(), nodes);
+    *n_nodes = (int32_t)v.size();
+    *depth = dep;
+    return NB_OK;
+}
+
+extern "C" nb_status nb_cascade_index_create(const nb_scene *scene, nb_cascade_index **out) {
+    nb_status st = check_scene(scene);
+    if (st != NB_OK) return st;
+    if (!out) return nb_fail(NB_EINVAL, "nb_cascade_index_create: null out");
+    *out = nullptr;
+    const int K = scene->n_objects;
+    std::vector<float> h((size_t)K * 6);
+    NB_CUDA(cudaMemcpy(h.data(), scene->aabb, h.size() * sizeof(float), cudaMemcpyDeviceToHost));
+    std::vector<nb_bvh4_node> v;
+    int dep = 0;
+    st = build_bvh4(h.data(), K, v, dep);
+    if (st != NB_OK) return st;
+    nb_cascade_index *ix = new (std::nothrow) nb_cascade_index;
+    if (!ix) return nb_fail(NB_ENOMEM, "nb_cascade_index_create: out of host memory");
+    if (cudaMalloc(&ix->nodes, v.size() * sizeof(nb_bvh4_node)) != cudaSuccess) {
+        cudaGetLastError();
+        delete ix;
+        return nb_fail(NB_ENOMEM, "nb_cascade_index_create: device allocation failed");
+    }
+    if (cudaMemcpy(ix->nodes, v.data(), v.size() * sizeof(nb_bvh4_node), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(ix->nodes);
+        delete ix;
+        return nb_fail(NB_ECUDA, "nb_cascade_index_create: upload failed");
+    }
+    ix->K = K;
+    ix->n_nodes = (int)v.size();
+    ix->depth = dep;
+    *out = ix;
+    return NB_OK;
+}
+
+extern "C" nb_status nb_cascade_index_destroy(nb_cascade_index *index) {
+    if (!index) return NB_OK;
+    cudaFree(index->nodes);
+    delete index;
+    return NB_OK;
+}
+
+extern "C" nb_status nb_cascade_bin_indexed(const nb_cascade_index *index, const nb_scene *scene, const float *rays,
+                                            int64_t n, int32_t canonical, unsigned long long *counts,
+                                            const int64_t *offsets, uint32_t *pair_ray, float *pair_q,
+                                            nb_cascade_stats *dev_stats, void *stream) {
+    nb_status st = check_scene(scene);
+    if (st != NB_OK) return st;
+    if (!index) return nb_fail(NB_EINVAL, "nb_cascade_bin_indexed: null index");
+    if (index->K != scene->n_objects) return nb_fail(NB_EINVAL, "nb_cascade_bin_indexed: index of another scene");
+    if (n < 0 || n >= ((int64_t)1 << 32) - 1)
+        return nb_fail(NB_EINVAL, "nb_cascade_bin_indexed: n must be in [0, 2^32 - 1)");
+    if (!counts || (n > 0 && !rays)) return nb_fail(NB_EINVAL, "nb_cascade_bin_indexed: null pointer");
+    const bool scatter = offsets != nullptr;
+    if (scatter && (!pair_ray || (canonical && !pair_q)))
+        return nb_fail(NB_EINVAL, "nb_cascade_bin_indexed: scatter needs pair_ray (and pair_q when canonical)");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int K = scene->n_objects;
+    NB_CUDA(cudaMemsetAsync(counts, 0, sizeof(unsigned long long) * K, s));
+    if (dev_stats && !scatter) NB_CUDA(cudaMemsetAsync(dev_stats, 0, sizeof(nb_cascade_stats), s));
+    if (n == 0) return NB_OK;
+    const size_t smem = (size_t)index->n_nodes * sizeof(nb_bvh4_node) + (size_t)K * 4 * (scatter ? 2 : 1);
+    int dev = 0, optin = 0;
+    NB_CUDA(cudaGetDevice(&dev));
+    NB_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if (smem > (size_t)optin) return nb_fail(NB_EUNSUPPORTED, "nb_cascade_bin_indexed: tree exceeds shared memory");
+    const float R2 = scene->ball_radius * scene->ball_radius;
+    const long long tiles = (n + BVH_TPB - 1) / BVH_TPB;
+#define NB_BIN_BVH(C, S)                                                                                           \
+    do {                                                                                                           \
+        NB_CUDA(cudaFuncSetAttribute(bin_bvh_kernel<C, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+        int per_sm = 1;                                                                                            \
+        NB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bin_bvh_kernel<C, S>, BVH_TPB, smem));      \
+        const long long grid = std::min<long long>(tiles, (long long)num_sms() * std::max(1, per_sm));              \
+        bin_bvh_kernel<C, S><<<(unsigned)grid, BVH_TPB, smem, s>>>(K, index->n_nodes, R2, index->nodes,             \
+                                                                   scene->obj_centre, rays, (long long)n, counts,   \
+                                                                   (const long long *)offsets, pair_ray, pair_q,    \
+                                                                   dev_stats);                                      \
+    } while (0)
+    if (canonical && scatter) NB_BIN_BVH(true, true);
+    else if (canonical) NB_BIN_BVH(true, false);
+    else if (scatter) NB_BIN_BVH(false, true);
+    else NB_BIN_BVH(false, false);
+#undef NB_BIN_BVH
     NB_CUDA(cudaGetLastError());
     return NB_OK;
 }

@@ -30,7 +30,8 @@ EXPORTS = ["nb_model_create", "nb_model_destroy", "nb_model_param_count", "nb_mo
            "nb_group_set_params", "nb_group_get_params", "nb_group_get_grad", "nb_group_set_tau", "nb_group_get_tau",
            "nb_group_set_schedule", "nb_group_sync_schedule", "nb_group_reserve", "nb_train_step_grouped",
            "nb_query_grouped", "nb_calibrate_grouped", "nb_cascade_bin", "nb_cascade_exact", "nb_sample", "nb_group_autotune", "nb_query_early_out", "nb_bits_not",
-           "nb_query_three_way"]
+           "nb_query_three_way", "nb_cascade_index_create", "nb_cascade_index_destroy", "nb_cascade_bin_indexed",
+           "nb_cascade_index_max_nodes", "nb_cascade_index_build_host"]
 
 
 class NBError(RuntimeError):
@@ -110,6 +111,11 @@ def lib():
                 "nb_query_early_out": ([P, P, P, i64, ctypes.c_float, ctypes.c_float, P, P, P], st),
                 "nb_bits_not": ([P, i64, P, P], st),
                 "nb_query_three_way": ([P, P, P, i64, ctypes.c_float, ctypes.c_float, P, P, P], st),
+                "nb_cascade_index_create": ([P, P], st),
+                "nb_cascade_index_destroy": ([P], st),
+                "nb_cascade_bin_indexed": ([P, P, P, i64, i32, P, P, P, P, P, P], st),
+                "nb_cascade_index_max_nodes": ([i32], i32),
+                "nb_cascade_index_build_host": ([P, i32, P, P, P], st),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -427,17 +433,62 @@ class WorldScene:
                           self.aabb.data_ptr())
 
 
-def cascade_bin(ws: WorldScene, rays: torch.Tensor, canonical: bool, stream=None):
+BVH4_NODE = np.dtype([("lo", "<f4", (3, 4)), ("hi", "<f4", (3, 4)), ("child", "<i4", (4,))])
+BVH_EMPTY = -2 ** 31
+
+
+def bvh4_build_host(aabb: np.ndarray):
+    """The object tree of the cascade index built on the host (nb_cascade_index_build_host):
+    returns (nodes as a BVH4_NODE array, depth).  No device is involved."""
+    a = np.ascontiguousarray(aabb, dtype=np.float32).reshape(-1, 6)
+    K = a.shape[0]
+    L = lib()
+    nodes = np.zeros(max(1, L.nb_cascade_index_max_nodes(K)), dtype=BVH4_NODE)
+    nn, dep = ctypes.c_int32(0), ctypes.c_int32(0)
+    _check(L.nb_cascade_index_build_host(a.ctypes.data_as(ctypes.c_void_p), K,
+                                         nodes.ctypes.data_as(ctypes.c_void_p), ctypes.byref(nn), ctypes.byref(dep)))
+    return nodes[:nn.value].copy(), dep.value
+
+
+class CascadeIndex:
+    """Spatial index (4-wide tree of object boxes) of a WorldScene, for stage 1."""
+
+    def __init__(self, ws: WorldScene):
+        self.ws = ws
+        h = ctypes.c_void_p()
+        _check(lib().nb_cascade_index_create(ctypes.byref(ws._s), ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().nb_cascade_index_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cascade_bin(ws: WorldScene, rays: torch.Tensor, canonical: bool, stream=None, index: CascadeIndex | None = None):
     """Stage 1: (ray, object) pairs passing the box (and the ball when canonical), binned by
-    object into rows padded to multiples of 32.  Returns (host offsets, device offsets,
-    pair_ray, pair_q or None, stats)."""
+    object into rows padded to multiples of 32, through the spatial index when one is
+    given.  Returns (host offsets, device offsets, pair_ray, pair_q or None, stats)."""
     n = rays.shape[0]
     dev = rays.device
     counts = torch.zeros(ws.K, dtype=torch.int64, device=dev)
     st = torch.zeros(CASCADE_STATS.itemsize, dtype=torch.uint8, device=dev)
     L = lib()
-    _check(L.nb_cascade_bin(ctypes.byref(ws._s), _ptr(rays), n, int(canonical), _ptr(counts), None, None, None,
-                            _ptr(st), _stream(stream)))
+
+    def call(off_d, pair_ray, pair_q, stats):
+        if index is None:
+            return L.nb_cascade_bin(ctypes.byref(ws._s), _ptr(rays), n, int(canonical), _ptr(counts), _ptr(off_d),
+                                    _ptr(pair_ray), _ptr(pair_q), _ptr(stats), _stream(stream))
+        return L.nb_cascade_bin_indexed(index._h, ctypes.byref(ws._s), _ptr(rays), n, int(canonical), _ptr(counts),
+                                        _ptr(off_d), _ptr(pair_ray), _ptr(pair_q), _ptr(stats), _stream(stream))
+
+    _check(call(None, None, None, st))
     c = counts.cpu().numpy()
     padded = (c + 31) // 32 * 32
     off = np.concatenate([[0], np.cumsum(padded)]).astype(np.int64)
@@ -445,8 +496,7 @@ def cascade_bin(ws: WorldScene, rays: torch.Tensor, canonical: bool, stream=None
     pair_ray = torch.full((max(rows, 1),), -1, dtype=torch.int32, device=dev)
     pair_q = torch.zeros((max(rows, 1), 6), dtype=torch.float32, device=dev) if canonical else None
     off_d = torch.as_tensor(off, device=dev)
-    _check(L.nb_cascade_bin(ctypes.byref(ws._s), _ptr(rays), n, int(canonical), _ptr(counts), _ptr(off_d),
-                            _ptr(pair_ray), _ptr(pair_q), None, _stream(stream)))
+    _check(call(off_d, pair_ray, pair_q, None))
     return off, off_d, pair_ray, pair_q, _read(st, CASCADE_STATS)
 
 

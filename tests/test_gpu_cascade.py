@@ -113,3 +113,65 @@ def test_cascade_end_to_end_equals_plain_and_avoids_exact_tests(nb):
     dec = nb.bits_to_numpy(neural, rows)
     live = pair_ray.cpu().numpy() != -1
     assert not np.any(lab & ~dec & live)
+
+
+def _segments(off, pair_ray, pair_q=None):
+    """per object: its rows sorted by ray (the order within an object is free)"""
+    pr = pair_ray.cpu().numpy()
+    q = None if pair_q is None else pair_q.cpu().numpy()
+    out = []
+    for k in range(len(off) - 1):
+        seg = pr[off[k]:off[k + 1]]
+        live = seg != -1
+        o = np.argsort(seg[live], kind="stable")
+        rows = np.nonzero(live)[0][o]
+        out.append((seg[rows], None if q is None else q[off[k] + rows]))
+    return out
+
+
+@pytest.mark.parametrize("K,canonical", [(1, True), (24, False), (24, True), (300, True)])
+def test_indexed_binning_equals_every_box(nb, K, canonical):
+    ms = I.make_multi_scene(41 + K, K, 32)
+    rays = I.sample_world_rays(42 + K, 50_000).astype(np.float32)
+    # a slice of axis-parallel rays from object box faces
+    rng = np.random.default_rng(43)
+    m = 2000
+    k = rng.integers(0, K, m)
+    rays[:m, :3] = np.where(rng.random((m, 3)) < 0.5, ms.aabb[k, :3], ms.aabb[k, 3:])
+    rays[:m, 3:] = 0
+    rays[np.arange(m), 3 + rng.integers(0, 3, m)] = rng.choice([-1.0, 1.0], m)
+    ws = nb.WorldScene(ms)
+    ix = nb.CascadeIndex(ws)
+    rd = _dev(rays)
+    a = nb.cascade_bin(ws, rd, canonical=canonical)
+    b = nb.cascade_bin(ws, rd, canonical=canonical, index=ix)
+    assert np.array_equal(a[0], b[0])  # same counts, hence the same offsets
+    assert a[4]["aabb_pairs"] == b[4]["aabb_pairs"] > 0
+    assert a[4]["ball_pairs"] == b[4]["ball_pairs"]
+    for (ra, qa), (rb, qb) in zip(_segments(a[0], a[2], a[3]), _segments(b[0], b[2], b[3])):
+        assert np.array_equal(ra, rb)
+        if canonical:
+            assert np.array_equal(qa.view(np.uint32), qb.view(np.uint32))
+    ix.close()
+
+
+def test_indexed_plain_path_equals_brute_force(nb):
+    import torch
+    ms = I.make_multi_scene(51, 200, 32)
+    rays = I.sample_world_rays(52, 80_001)
+    ws = nb.WorldScene(ms)
+    ix = nb.CascadeIndex(ws)
+    rd = _dev(rays)
+    n = len(rays)
+    off, off_d, pair_ray, _, st = nb.cascade_bin(ws, rd, canonical=False, index=ix)
+    hits = torch.zeros(nb.n_words(n), dtype=torch.int32, device="cuda")
+    nb.cascade_exact(ws, rd, pair_ray, off_d, int(off[-1]), ray_hits=hits)
+    assert np.array_equal(nb.bits_to_numpy(hits, n), _brute(ms, rays))
+    # no rays: counts zero, nothing written
+    e = nb.cascade_bin(ws, rd[:0], canonical=True, index=ix)
+    assert int(e[0][-1]) == 0
+    # an index of another scene is refused
+    other = nb.WorldScene(I.make_multi_scene(53, 7, 4))
+    with pytest.raises(nb.NBError):
+        nb.cascade_bin(other, rd, canonical=False, index=ix)
+    ix.close()
