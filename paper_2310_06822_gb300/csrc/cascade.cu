@@ -149,10 +149,11 @@ __global__ void __launch_bounds__(256)
 
 // Stage 1 through the 4-wide tree of object boxes: one ray per thread, depth-first with a
 // short stack (the builder bounds the depth, so the stack never fills; the guard only keeps
-// the writes in bounds).  Kept pairs are counted per object in shared memory.  The counting
-// call adds the block's counts to counts[] once at the end; the scatter call walks each
-// tile of rays twice: first to count, then, after one global reservation per object and
-// tile, to write each pair into its reserved row.
+// the writes in bounds).  The counting call counts kept pairs per object in shared memory
+// and adds the block's counts to counts[] once at the end; the scatter call reserves each
+// pair's row with one global atomic on its object's count (a few hundred thousand pairs per
+// object, spread over the L2 slices: cheaper than walking the tree a second time to
+// reserve rows per tile).
 constexpr int BVH_STACK = 32;
 constexpr int BVH_TPB = 256;
 
@@ -189,67 +190,42 @@ __global__ void __launch_bounds__(BVH_TPB)
                    nb_cascade_stats *st) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     nb_bvh4_node *nodes = reinterpret_cast<nb_bvh4_node *>(smem_raw);
-    unsigned *hist = reinterpret_cast<unsigned *>(nodes + n_nodes);
-    unsigned *base = hist + K;  // scatter call only
+    unsigned *hist = reinterpret_cast<unsigned *>(nodes + n_nodes);  // counting call only
     {
         const int4 *src = reinterpret_cast<const int4 *>(nodes_g);
         int4 *dst = reinterpret_cast<int4 *>(nodes);
         const int words = n_nodes * (int)(sizeof(nb_bvh4_node) / sizeof(int4));
         for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
-        for (int k = threadIdx.x; k < K; k += blockDim.x) hist[k] = 0;
+        if (!SCATTER)
+            for (int k = threadIdx.x; k < K; k += blockDim.x) hist[k] = 0;
     }
     __syncthreads();
     unsigned long long n_aabb = 0, n_ball = 0;
-    const long long tiles = (n + blockDim.x - 1) / blockDim.x;
-    for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-        const long long r = tile * blockDim.x + threadIdx.x;
-        const bool valid = r < n;
-        float o[3] = {0.f, 0.f, 0.f}, d[3] = {0.f, 0.f, 1.f}, inv[3];
-        if (valid)
-            for (int i = 0; i < 3; i++) {
-                o[i] = rays[r * 6 + i];
-                d[i] = rays[r * 6 + 3 + i];
-            }
-        for (int i = 0; i < 3; i++) inv[i] = 1.0f / d[i];  // +-inf for a zero component
-        auto keep_of = [&](int k, float q6[6]) {
-            if (!CANON) return true;
-            const float c[3] = {__ldg(oc + k * 3), __ldg(oc + k * 3 + 1), __ldg(oc + k * 3 + 2)};
-            return canon_entry(o, d, c, R2, q6);
-        };
-        // pass 1: count the kept pairs per object (and, counting call, the totals)
-        if (valid)
-            bvh_walk(nodes, o, d, inv, [&](int k) {
-                float q6[6];
-                const bool keep = keep_of(k, q6);
-                if (!SCATTER) {
-                    n_aabb++;
-                    n_ball += keep;
-                }
-                if (keep) atomicAdd(hist + k, 1u);
-            });
-        if (!SCATTER) continue;
-        __syncthreads();
-        // one reservation per object and tile; hist becomes the running slot
-        for (int k = threadIdx.x; k < K; k += blockDim.x) {
-            const unsigned c = hist[k];
-            if (c) base[k] = (unsigned)atomicAdd(counts + k, (unsigned long long)c);
-            hist[k] = 0;
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
+        float o[3], d[3], inv[3];
+        for (int i = 0; i < 3; i++) {
+            o[i] = rays[r * 6 + i];
+            d[i] = rays[r * 6 + 3 + i];
         }
-        __syncthreads();
-        // pass 2: the same walk, each kept pair written to its row
-        if (valid)
-            bvh_walk(nodes, o, d, inv, [&](int k) {
-                float q6[6];
-                if (!keep_of(k, q6)) return;
-                const unsigned slot = atomicAdd(hist + k, 1u);
-                const long long row = offsets[k] + base[k] + slot;
+        for (int i = 0; i < 3; i++) inv[i] = 1.0f / d[i];  // +-inf for a zero component
+        bvh_walk(nodes, o, d, inv, [&](int k) {
+            float q6[6];
+            bool keep = true;
+            if (CANON) {
+                const float c[3] = {__ldg(oc + k * 3), __ldg(oc + k * 3 + 1), __ldg(oc + k * 3 + 2)};
+                keep = canon_entry(o, d, c, R2, q6);
+            }
+            if (!SCATTER) {
+                n_aabb++;
+                n_ball += keep;
+                if (keep) atomicAdd(hist + k, 1u);
+            } else if (keep) {
+                const long long row = offsets[k] + (long long)atomicAdd(counts + k, 1ull);
                 pair_ray[row] = (uint32_t)r;
                 if (CANON)
                     for (int i = 0; i < 6; i++) pair_q[row * 6 + i] = q6[i];
-            });
-        __syncthreads();
-        for (int k = threadIdx.x; k < K; k += blockDim.x) hist[k] = 0;
-        __syncthreads();
+            }
+        });
     }
     if (SCATTER) return;
     __syncthreads();
@@ -602,19 +578,19 @@ extern "C" nb_status nb_cascade_bin_indexed(const nb_cascade_index *index, const
     NB_CUDA(cudaMemsetAsync(counts, 0, sizeof(unsigned long long) * K, s));
     if (dev_stats && !scatter) NB_CUDA(cudaMemsetAsync(dev_stats, 0, sizeof(nb_cascade_stats), s));
     if (n == 0) return NB_OK;
-    const size_t smem = (size_t)index->n_nodes * sizeof(nb_bvh4_node) + (size_t)K * 4 * (scatter ? 2 : 1);
+    const size_t smem = (size_t)index->n_nodes * sizeof(nb_bvh4_node) + (scatter ? 0 : (size_t)K * 4);
     int dev = 0, optin = 0;
     NB_CUDA(cudaGetDevice(&dev));
     NB_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     if (smem > (size_t)optin) return nb_fail(NB_EUNSUPPORTED, "nb_cascade_bin_indexed: tree exceeds shared memory");
     const float R2 = scene->ball_radius * scene->ball_radius;
-    const long long tiles = (n + BVH_TPB - 1) / BVH_TPB;
+    const long long blocks = (n + BVH_TPB - 1) / BVH_TPB;
 #define NB_BIN_BVH(C, S)                                                                                           \
     do {                                                                                                           \
         NB_CUDA(cudaFuncSetAttribute(bin_bvh_kernel<C, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
         int per_sm = 1;                                                                                            \
         NB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bin_bvh_kernel<C, S>, BVH_TPB, smem));      \
-        const long long grid = std::min<long long>(tiles, (long long)num_sms() * std::max(1, per_sm));              \
+        const long long grid = std::min<long long>(blocks, (long long)num_sms() * std::max(1, per_sm));             \
         bin_bvh_kernel<C, S><<<(unsigned)grid, BVH_TPB, smem, s>>>(K, index->n_nodes, R2, index->nodes,             \
                                                                    scene->obj_centre, rays, (long long)n, counts,   \
                                                                    (const long long *)offsets, pair_ray, pair_q,    \
