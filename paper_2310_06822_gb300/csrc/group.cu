@@ -52,7 +52,9 @@ __global__ void __launch_bounds__(256)
     float alpha = alpha_arg;
     if (sched_alpha) alpha = sched_alpha[min(*d_step, sched_T - 1)];
     unsigned long long c_fn = 0, c_fp = 0, c_nf = 0;
-    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    int k0, k1;
+    item_range(n_items, k0, k1);
+    for (int it = k0; it < k1; it++) {
         const PlanItem w = items[it];
         MlpDesc dd = d;
         dd.p = d.p + (size_t)w.obj * P;
@@ -144,7 +146,9 @@ __global__ void __launch_bounds__(256)
     __shared__ float zs[TMF];
     const int t = threadIdx.x, lane = t & 31;
     unsigned long long c_in = 0, c_flag = 0, c_nf = 0;
-    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    int k0, k1;
+    item_range(n_items, k0, k1);
+    for (int it = k0; it < k1; it++) {
         const PlanItem w = items[it];
         MlpDesc dd = d;
         dd.p = d.p + (size_t)w.obj * P;

@@ -13,6 +13,15 @@ struct PlanItem {
     long long row0, row1;
 };
 
+// The contiguous range [k0, k1) of plan items a CTA of a grouped launch works through.
+// A plan lists an object's items one after another, so a CTA meets each object in one run
+// and loads that object's operands once per run (with CTAs striding over the items, nearly
+// every item would belong to another object than the CTA's previous one).
+__device__ __forceinline__ void item_range(int n_items, int &k0, int &k1) {
+    k0 = (int)((long long)blockIdx.x * n_items / gridDim.x);
+    k1 = (int)((long long)(blockIdx.x + 1) * n_items / gridDim.x);
+}
+
 struct nb_plan {
     int n_objects = 0;
     int n_items = 0;

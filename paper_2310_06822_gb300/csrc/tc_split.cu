@@ -475,9 +475,11 @@ __global__ void __launch_bounds__(STHREADS, 1)
         bool ok = true;
         constexpr uint32_t idesc = idesc_f16(TILE_M, H);
         const uint32_t wbase = smem_u32(Wimg);
-        for (int k = blockIdx.x; ok && k < n_items; k += gridDim.x) {
+        int k0, k1;
+        item_range(n_items, k0, k1);
+        for (int k = k0; ok && k < k1; k++) {
             const PlanItem it = items[k];
-            if (k != (int)blockIdx.x) {
+            if (k != k0) {
                 ok = gwarp_wait(bar_done, ph_done, ctl, err);
                 ph_done ^= 1;
                 if (!ok) break;
@@ -561,7 +563,9 @@ __global__ void __launch_bounds__(STHREADS, 1)
         uint32_t ph_acc = 0, ph_ready = 0, pp = 0;
         unsigned long long c_in = 0, c_flag = 0, c_nf = 0;
         bool ok = true;
-        for (int k = blockIdx.x; ok && k < n_items; k += gridDim.x) {
+        int k0, k1;
+        item_range(n_items, k0, k1);
+        for (int k = k0; ok && k < k1; k++) {
             const PlanItem it = items[k];
             ok = gwarp_wait(bar_ready, ph_ready, ctl, err);
             ph_ready ^= 1;

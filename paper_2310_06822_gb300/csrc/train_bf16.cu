@@ -390,7 +390,9 @@ __global__ void __launch_bounds__(TPB, 1)
     if (sched_alpha) alpha = sched_alpha[min(*d_step, sched_T - 1)];
     unsigned long long c_fn = 0, c_fp = 0, c_nf = 0;
     int cur = -1;
-    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    int k0, k1;
+    item_range(n_items, k0, k1);
+    for (int it = k0; it < k1; it++) {
         const PlanItem w = items[it];
         TrainDesc dd = d;
         dd.p = d.p + (size_t)w.obj * P;
