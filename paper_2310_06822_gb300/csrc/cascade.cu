@@ -156,14 +156,18 @@ __global__ void __launch_bounds__(256)
 // reserve rows per tile).
 constexpr int BVH_STACK = 32;
 constexpr int BVH_TPB = 256;
+// nodes sit in shared memory at an odd stride of 29 words (a node is 28): lanes reading
+// the same field of different nodes then hit different banks (at 28 words they would
+// share 8 banks)
+constexpr int NODE_WORDS = (int)(sizeof(nb_bvh4_node) / 4), NODE_STRIDE = NODE_WORDS + 1;
 
 template <class Visit>
-__device__ __forceinline__ void bvh_walk(const nb_bvh4_node *nodes, const float o[3], const float d[3],
+__device__ __forceinline__ void bvh_walk(const float *nodes, const float o[3], const float d[3],
                                          const float inv[3], Visit visit) {
     int stack[BVH_STACK];
     int sp = 0, node = 0;
     while (true) {
-        const nb_bvh4_node &nd = nodes[node];
+        const nb_bvh4_node &nd = *reinterpret_cast<const nb_bvh4_node *>(nodes + node * NODE_STRIDE);
 #pragma unroll
         for (int c = 0; c < 4; c++) {
             const int ch = nd.child[c];
@@ -189,13 +193,15 @@ __global__ void __launch_bounds__(BVH_TPB)
                    const long long *__restrict__ offsets, uint32_t *__restrict__ pair_ray, float *__restrict__ pair_q,
                    nb_cascade_stats *st) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    nb_bvh4_node *nodes = reinterpret_cast<nb_bvh4_node *>(smem_raw);
-    unsigned *hist = reinterpret_cast<unsigned *>(nodes + n_nodes);  // counting call only
+    float *nodes = reinterpret_cast<float *>(smem_raw);
+    float *cen = nodes + n_nodes * NODE_STRIDE;          // [K][3] object centres (canonical call)
+    unsigned *hist = reinterpret_cast<unsigned *>(cen + (CANON ? 3 * K : 0));  // counting call only
     {
-        const int4 *src = reinterpret_cast<const int4 *>(nodes_g);
-        int4 *dst = reinterpret_cast<int4 *>(nodes);
-        const int words = n_nodes * (int)(sizeof(nb_bvh4_node) / sizeof(int4));
-        for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+        const float *src = reinterpret_cast<const float *>(nodes_g);
+        for (int i = threadIdx.x; i < n_nodes * NODE_WORDS; i += blockDim.x)
+            nodes[(i / NODE_WORDS) * NODE_STRIDE + i % NODE_WORDS] = src[i];
+        if (CANON)
+            for (int i = threadIdx.x; i < 3 * K; i += blockDim.x) cen[i] = oc[i];
         if (!SCATTER)
             for (int k = threadIdx.x; k < K; k += blockDim.x) hist[k] = 0;
     }
@@ -212,8 +218,7 @@ __global__ void __launch_bounds__(BVH_TPB)
             float q6[6];
             bool keep = true;
             if (CANON) {
-                const float c[3] = {__ldg(oc + k * 3), __ldg(oc + k * 3 + 1), __ldg(oc + k * 3 + 2)};
-                keep = canon_entry(o, d, c, R2, q6);
+                keep = canon_entry(o, d, cen + 3 * k, R2, q6);
             }
             if (!SCATTER) {
                 n_aabb++;
@@ -578,7 +583,8 @@ extern "C" nb_status nb_cascade_bin_indexed(const nb_cascade_index *index, const
     NB_CUDA(cudaMemsetAsync(counts, 0, sizeof(unsigned long long) * K, s));
     if (dev_stats && !scatter) NB_CUDA(cudaMemsetAsync(dev_stats, 0, sizeof(nb_cascade_stats), s));
     if (n == 0) return NB_OK;
-    const size_t smem = (size_t)index->n_nodes * sizeof(nb_bvh4_node) + (scatter ? 0 : (size_t)K * 4);
+    const size_t smem = (size_t)index->n_nodes * NODE_STRIDE * 4 + (canonical ? (size_t)K * 12 : 0) +
+                        (scatter ? 0 : (size_t)K * 4);
     int dev = 0, optin = 0;
     NB_CUDA(cudaGetDevice(&dev));
     NB_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
