@@ -54,34 +54,53 @@ __device__ __forceinline__ bool slab_hit(const float o[3], const float d[3], con
     return hit && t0 <= t1;
 }
 
-// the ray in the frame of an object centred at c, its origin moved to where it enters the
-// ball |x| = R (R2 = R^2): q6 = (entry point, direction); false if it misses the ball
-__device__ __forceinline__ bool canon_entry(const float o[3], const float d[3], const float c[3], float R2,
-                                            float q6[6]) {
+// the ray in the frame of an object centred at c and the discriminant of its entry into the
+// ball |x| = R (R2 = R^2): the ray meets the ball iff disc >= 0 and dd > 0
+struct BallFrame {
+    float w[3], b, dd, ww, disc;
+};
+
+__device__ __forceinline__ BallFrame ball_frame(const float o[3], const float d[3], const float c[3], float R2) {
     // object frame: w = o - c (exact on the grid); entry into |x| = R:
     // |w + s d|^2 = R^2, s = (-b - sqrt(b^2 - |d|^2 (|w|^2 - R^2))) / |d|^2
-    float w[3];
-    for (int i = 0; i < 3; i++) w[i] = __fsub_rn(o[i], c[i]);
-    const float b = __fadd_rn(__fadd_rn(__fmul_rn(w[0], d[0]), __fmul_rn(w[1], d[1])), __fmul_rn(w[2], d[2]));
-    const float dd = __fadd_rn(__fadd_rn(__fmul_rn(d[0], d[0]), __fmul_rn(d[1], d[1])), __fmul_rn(d[2], d[2]));
-    const float ww = __fadd_rn(__fadd_rn(__fmul_rn(w[0], w[0]), __fmul_rn(w[1], w[1])), __fmul_rn(w[2], w[2]));
+    BallFrame f;
+    for (int i = 0; i < 3; i++) f.w[i] = __fsub_rn(o[i], c[i]);
+    const float *w = f.w;
+    f.b = __fadd_rn(__fadd_rn(__fmul_rn(w[0], d[0]), __fmul_rn(w[1], d[1])), __fmul_rn(w[2], d[2]));
+    f.dd = __fadd_rn(__fadd_rn(__fmul_rn(d[0], d[0]), __fmul_rn(d[1], d[1])), __fmul_rn(d[2], d[2]));
+    f.ww = __fadd_rn(__fadd_rn(__fmul_rn(w[0], w[0]), __fmul_rn(w[1], w[1])), __fmul_rn(w[2], w[2]));
     // b^2 - dd (ww - R^2) = dd R^2 - |w x d|^2 (Lagrange), free of the cancellation
     // between the two large terms when the origin is far from the object
     const float cx = fmaf(w[1], d[2], -__fmul_rn(w[2], d[1]));
     const float cy = fmaf(w[2], d[0], -__fmul_rn(w[0], d[2]));
     const float cz = fmaf(w[0], d[1], -__fmul_rn(w[1], d[0]));
     const float cr2 = __fadd_rn(__fadd_rn(__fmul_rn(cx, cx), __fmul_rn(cy, cy)), __fmul_rn(cz, cz));
-    const float disc = __fsub_rn(__fmul_rn(dd, R2), cr2);
-    if (!(disc >= 0.f && dd > 0.f)) return false;
+    f.disc = __fsub_rn(__fmul_rn(f.dd, R2), cr2);
+    return f;
+}
+
+__device__ __forceinline__ bool ball_met(const BallFrame &f) { return f.disc >= 0.f && f.dd > 0.f; }
+
+// q6 = (entry point into the ball, direction) of a ray that meets it
+__device__ __forceinline__ void ball_entry(const BallFrame &f, const float d[3], float R2, float q6[6]) {
     // smaller root without cancellation: s = c / (-b + sqrt(disc)) when -b > 0
-    const float sq_disc = __fsqrt_rn(disc);
-    const float cc = __fsub_rn(ww, R2);
-    float s = -b > 0.f ? __fdiv_rn(cc, __fadd_rn(-b, sq_disc)) : __fdiv_rn(__fsub_rn(-b, sq_disc), dd);
+    const float sq_disc = __fsqrt_rn(f.disc);
+    const float cc = __fsub_rn(f.ww, R2);
+    float s = -f.b > 0.f ? __fdiv_rn(cc, __fadd_rn(-f.b, sq_disc)) : __fdiv_rn(__fsub_rn(-f.b, sq_disc), f.dd);
     s = fmaxf(s, 0.f);
     for (int i = 0; i < 3; i++) {
-        q6[i] = __fadd_rn(w[i], __fmul_rn(s, d[i]));
+        q6[i] = __fadd_rn(f.w[i], __fmul_rn(s, d[i]));
         q6[3 + i] = d[i];
     }
+}
+
+// the ray in the frame of an object centred at c, its origin moved to where it enters the
+// ball: q6 = (entry point, direction); false if it misses the ball
+__device__ __forceinline__ bool canon_entry(const float o[3], const float d[3], const float c[3], float R2,
+                                            float q6[6]) {
+    const BallFrame f = ball_frame(o, d, c, R2);
+    if (!ball_met(f)) return false;
+    ball_entry(f, d, R2, q6);
     return true;
 }
 
@@ -161,31 +180,6 @@ constexpr int BVH_TPB = 256;
 // share 8 banks)
 constexpr int NODE_WORDS = (int)(sizeof(nb_bvh4_node) / 4), NODE_STRIDE = NODE_WORDS + 1;
 
-template <class Visit>
-__device__ __forceinline__ void bvh_walk(const float *nodes, const float o[3], const float d[3],
-                                         const float inv[3], Visit visit) {
-    int stack[BVH_STACK];
-    int sp = 0, node = 0;
-    while (true) {
-        const nb_bvh4_node &nd = *reinterpret_cast<const nb_bvh4_node *>(nodes + node * NODE_STRIDE);
-#pragma unroll
-        for (int c = 0; c < 4; c++) {
-            const int ch = nd.child[c];
-            if (ch == NB_BVH_EMPTY) continue;
-            const float lo[3] = {nd.lo[0][c], nd.lo[1][c], nd.lo[2][c]};
-            const float hi[3] = {nd.hi[0][c], nd.hi[1][c], nd.hi[2][c]};
-            if (!slab_hit(o, d, inv, lo, hi)) continue;
-            if (ch >= 0) {
-                if (sp < BVH_STACK) stack[sp++] = ch;
-            } else {
-                visit(-1 - ch);
-            }
-        }
-        if (sp == 0) break;
-        node = stack[--sp];
-    }
-}
-
 template <bool CANON, bool SCATTER>
 __global__ void __launch_bounds__(BVH_TPB)
     bin_bvh_kernel(int K, int n_nodes, float R2, const nb_bvh4_node *__restrict__ nodes_g, const float *__restrict__ oc,
@@ -207,30 +201,61 @@ __global__ void __launch_bounds__(BVH_TPB)
     }
     __syncthreads();
     unsigned long long n_aabb = 0, n_ball = 0;
-    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
-        float o[3], d[3], inv[3];
+    // Each lane walks its ray's tree depth-first, one node per iteration; a lane whose walk
+    // ends takes its next ray at once instead of idling until the warp's longest walk ends.
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    float o[3], d[3], inv[3];
+    int stack[BVH_STACK];
+    int sp = 0, node = 0;
+    bool live = r < n;
+    auto load_ray = [&]() {
         for (int i = 0; i < 3; i++) {
             o[i] = rays[r * 6 + i];
             d[i] = rays[r * 6 + 3 + i];
         }
         for (int i = 0; i < 3; i++) inv[i] = 1.0f / d[i];  // +-inf for a zero component
-        bvh_walk(nodes, o, d, inv, [&](int k) {
-            float q6[6];
-            bool keep = true;
-            if (CANON) {
-                keep = canon_entry(o, d, cen + 3 * k, R2, q6);
+        node = 0;
+        sp = 0;
+    };
+    if (live) load_ray();
+    while (__any_sync(FULL, live)) {
+        if (!live) continue;
+        const nb_bvh4_node &nd = *reinterpret_cast<const nb_bvh4_node *>(nodes + node * NODE_STRIDE);
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            const int ch = nd.child[c];
+            if (ch == NB_BVH_EMPTY) continue;
+            const float lo[3] = {nd.lo[0][c], nd.lo[1][c], nd.lo[2][c]};
+            const float hi[3] = {nd.hi[0][c], nd.hi[1][c], nd.hi[2][c]};
+            if (!slab_hit(o, d, inv, lo, hi)) continue;
+            if (ch >= 0) {
+                if (sp < BVH_STACK) stack[sp++] = ch;
+                continue;
             }
+            const int k = -1 - ch;  // a leaf: the pair (r, k) passes the box
             if (!SCATTER) {
+                bool keep = true;
+                if (CANON) keep = ball_met(ball_frame(o, d, cen + 3 * k, R2));
                 n_aabb++;
                 n_ball += keep;
                 if (keep) atomicAdd(hist + k, 1u);
-            } else if (keep) {
+            } else {
+                float q6[6];
+                if (CANON && !canon_entry(o, d, cen + 3 * k, R2, q6)) continue;
                 const long long row = offsets[k] + (long long)atomicAdd(counts + k, 1ull);
                 pair_ray[row] = (uint32_t)r;
                 if (CANON)
                     for (int i = 0; i < 6; i++) pair_q[row * 6 + i] = q6[i];
             }
-        });
+        }
+        if (sp > 0) {
+            node = stack[--sp];
+        } else {
+            r += stride;
+            live = r < n;
+            if (live) load_ray();
+        }
     }
     if (SCATTER) return;
     __syncthreads();
