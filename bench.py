@@ -832,6 +832,73 @@ def run_c5(args):
     ctx.emit(line)
 
 
+# ---------------------------------------------------------------------------------- paper sizes
+def run_c6(args):
+    """The paper's own network sizes (its supplementary architecture table: two hidden
+    layers of 25 / 50 / 75 neurons for 2D / 3D / 4D indicators), each trained in FP32 on a
+    sphere union of its dimension, calibrated on its evaluation queries and queried on the
+    FP32 form and on the split-FP16 tensor-core form, zero-padded to 64 / 128 neurons."""
+    from paper_2310_06822_gb300 import inputs as I
+    from paper_2310_06822_gb300 import nb
+    ctx = Ctx(args)
+    torch, dev = ctx.torch, ctx.dev
+    T = args.train_steps if args.train_steps != TRAIN_STEPS else 2000
+    n = args.n_eval if args.n_eval != N_EVAL else (16 << 20)
+    B = 8192
+    rows = [("2d_point", I.POINT2, [2, 25, 25, 1], I.make_scene(6000, 8, 2, 0.05, 0.3)),
+            ("3d_point", I.POINT3, [3, 50, 50, 1], I.make_scene(6001, 64, 3, R_LO, R_HI)),
+            ("3d_ray", I.RAY3, [6, 50, 50, 1], I.make_scene(6001, 64, 3, R_LO, R_HI)),
+            ("3d_plane", I.PLANE3, [4, 50, 50, 1], I.make_scene(6001, 64, 3, R_LO, R_HI)),
+            ("3d_box", I.BOX3, [6, 50, 50, 1], I.make_scene(6001, 64, 3, R_LO, R_HI)),
+            ("4d_point", I.POINT4T, [4, 75, 75, 1], I.make_scene(6002, 32, 3, 0.02, 0.2, moving=True))]
+    table = {}
+    head = None
+    for name, kind, widths, sc in rows:
+        shape = nb.Shape(sc, dev)
+        m = nb.Model(widths)
+        m.set_params(I.init_params(6100 + kind, widths))
+        for t in range(T):
+            q = nb.sample(kind, B, seed=rank_seed(6200 + kind, ctx.rank), first=t * B, device=dev)
+            m.train_step(q, nb.label(shape, kind, q), 1.0 + 99.0 * t / max(T - 1, 1), 1.0)
+        eq = nb.sample(kind, n, seed=rank_seed(6300 + kind, ctx.rank), device=dev)
+        ey = nb.label(shape, kind, eq)
+        tau = m.calibrate(eq, ey)
+        f = nb.Model(widths, infer_prec="f16x3")
+        f.set_params(m.get_params())
+        f.tau = tau
+        out = torch.empty(nb.n_words(n), dtype=torch.int32, device=dev)
+        d32 = nb.bits_to_numpy(m.query(eq, margin=MARGIN32), n)
+        _, zf = f.query(eq, logits=True)
+        dev_f = float(np.max(np.abs(zf[:1 << 20].cpu().numpy().astype(np.float64) -
+                                    m.query(eq[:1 << 20], logits=True)[1].cpu().numpy())))
+        margin = max(MARGIN, 4.0 * dev_f)
+        df = nb.bits_to_numpy(f.query(eq, margin=margin, out=out), n)
+        y = nb.bits_to_numpy(ey, n)
+        reps = max(3, args.steps // 4)
+        ms32 = ctx.time_ms(lambda: m.query(eq, margin=MARGIN32, out=out), reps)
+        if name == "3d_ray":
+            msf, clocks = ctx.timed(lambda: f.query(eq, margin=margin, out=out), args.steps, args.warmup)
+            head = (msf, clocks)
+        else:
+            msf = ctx.time_ms(lambda: f.query(eq, margin=margin, out=out), reps)
+        table[name] = {"widths": widths, "fp32_queries_per_s": n / (ms32 / 1000.0),
+                       "f16x3_padded_queries_per_s": n / (msf / 1000.0), "speedup": ms32 / msf,
+                       "fn": int(np.sum(y & ~df)), "fp_rate": float(np.mean(~y & df)),
+                       "decisions_equal_fp32_form": bool(np.array_equal(d32, df)), "margin": margin}
+        m.close()
+        f.close()
+    msf, clocks = head
+    line = base_line(ctx, "neural-bound queries/s at 0 FN (3D rays, the paper's 6->50->50->1, split-FP16 padded)",
+                     job_value(n, ctx.world, msf), "queries/s", msf, args.steps, args.warmup,
+                     "f16x3 (split fp16 operands, fp32 accumulate)",
+                     {"workload": "the paper's network sizes: 2D 2->25x2->1, 3D 3/6/4->50x2->1, 4D 4->75x2->1, "
+                                  "FP32 training, 16M eval queries each", "n_eval": n, "train_steps": T,
+                      "batch": B, "padding": "hidden widths zero-padded to 64 (25, 50) and 128 (75)"},
+                     clocks, args.steps * 4)
+    line.update({"sizes": table, "cpu_baseline": None, "e2e": None})
+    ctx.emit(line)
+
+
 # ---------------------------------------------------------------------------------- reference arm
 def reference_arm(args):
     """The oracle as it stands (FP64 forward of the same network), timed on host cores."""
@@ -867,13 +934,14 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c2e", "c3", "c4", "c5"])
+    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c2e", "c3", "c4", "c5", "c6"])
     ap.add_argument("--train-steps", type=int, default=TRAIN_STEPS)
     ap.add_argument("--n-eval", type=int, default=N_EVAL, help="evaluation size (smaller only for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
-    {"c1": run_c1, "c2": run_c2, "c2e": run_c2e, "c3": run_c3, "c4": run_c4, "c5": run_c5}[args.config](args)
+    {"c1": run_c1, "c2": run_c2, "c2e": run_c2e, "c3": run_c3, "c4": run_c4, "c5": run_c5,
+     "c6": run_c6}[args.config](args)
 
 
 if __name__ == "__main__":

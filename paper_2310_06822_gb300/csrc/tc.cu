@@ -316,10 +316,33 @@ int num_sms() {
 
 }  // namespace
 
+namespace {
+// real parameters -> zero-padded layout (blockIdx.y = layer); positions past the real
+// widths are never written and keep the zeros of the allocation
+__global__ void pad_params_kernel(MlpDesc real, MlpDesc pad, float *out) {
+    const int l = blockIdx.y;
+    const int N = real.w[l + 1], K = real.w[l], Kp = pad.w[l];
+    const long long total = (long long)N * K + N;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const float v = real.p[real.off[l] + e];
+        if (e < (long long)N * K) {
+            const long long n = e / K, k = e % K;
+            out[pad.off[l] + n * Kp + k] = v;
+        } else {
+            out[pad.off[l] + (long long)pad.w[l + 1] * Kp + (e - (long long)N * K)] = v;
+        }
+    }
+}
+}  // namespace
+
+// the parameter layout the tensor-core forward reads: the model's own, or its padded copy
+static const MlpDesc &fwd_desc(const TcModel *tc, const MlpDesc &d) { return tc->pad_p ? tc->pad : d; }
+
 nb_status nb_tc_init(TcModel *tc, const MlpDesc &d, int infer_prec, int train_prec) {
     tc->infer_prec = infer_prec;
     tc->train_prec = train_prec;
-    const int H = d.w[1], NH = d.L - 1;
+    int H = d.w[1];
+    const int NH = d.L - 1;
     if (cudaMalloc(&tc->err, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         return nb_fail(NB_ENOMEM, "tensor-core state allocation failed");
@@ -349,9 +372,28 @@ nb_status nb_tc_init(TcModel *tc, const MlpDesc &d, int infer_prec, int train_pr
     if (infer_prec == NB_BF16 || infer_prec == NB_F16X3) {
         if (NH < 1) return nb_fail(NB_EUNSUPPORTED, "tensor-core forward needs at least one hidden layer");
         if (d.w[0] > 16) return nb_fail(NB_EUNSUPPORTED, "tensor-core forward: input width must be <= 16");
-        if (H != 64 && H != 128) return nb_fail(NB_EUNSUPPORTED, "tensor-core forward: hidden width must be 64 or 128");
         for (int l = 1; l < d.L; l++)
             if (d.w[l] != H) return nb_fail(NB_EUNSUPPORTED, "tensor-core forward: hidden widths must be equal");
+        if (H > 128) return nb_fail(NB_EUNSUPPORTED, "tensor-core forward: hidden width must be at most 128");
+        if (H != 64 && H != 128) {  // run on a zero-padded copy
+            MlpDesc pd = d;
+            H = H < 64 ? 64 : 128;
+            int off = 0;
+            for (int l = 0; l < d.L; l++) {
+                pd.w[l + 1] = l + 1 < d.L ? H : 1;
+                pd.off[l] = off;
+                off += pd.w[l + 1] * pd.w[l] + pd.w[l + 1];
+            }
+            pd.maxw = std::max(d.w[0], H);
+            pd.pT = nullptr;
+            if (cudaMalloc(&tc->pad_p, sizeof(float) * (size_t)off) != cudaSuccess) {
+                cudaGetLastError();
+                return nb_fail(NB_ENOMEM, "padded parameter allocation failed");
+            }
+            cudaMemset(tc->pad_p, 0, sizeof(float) * (size_t)off);
+            pd.p = tc->pad_p;
+            tc->pad = pd;
+        }
         int dev = 0, maxsm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -379,6 +421,8 @@ nb_status nb_tc_init(TcModel *tc, const MlpDesc &d, int infer_prec, int train_pr
 }
 
 void nb_tc_free(TcModel *tc) {
+    cudaFree(tc->pad_p);
+    tc->pad_p = nullptr;
     cudaFree(tc->img);
     cudaFree(tc->err);
     cudaFree(tc->train_img);
@@ -395,9 +439,14 @@ nb_status nb_tc_refresh(TcModel *tc, const MlpDesc &d, cudaStream_t s) {
         if (st != NB_OK) return st;
     }
     if (!tc->img) return NB_OK;
-    if (tc->infer_prec == NB_F16X3) return nb_split_refresh(tc, d, s);
-    if (tc->infer_prec == NB_FP8) return nb_fp8_refresh(tc, d, s);
-    const TcDesc t = make_desc(tc, d);
+    if (tc->pad_p) {
+        pad_params_kernel<<<dim3(32, d.L), 256, 0, s>>>(d, tc->pad, tc->pad_p);
+        NB_CUDA(cudaGetLastError());
+    }
+    const MlpDesc &e = fwd_desc(tc, d);
+    if (tc->infer_prec == NB_F16X3) return nb_split_refresh(tc, e, s);
+    if (tc->infer_prec == NB_FP8) return nb_fp8_refresh(tc, e, s);
+    const TcDesc t = make_desc(tc, e);
     const uint32_t nchunks = t.img_bytes / 16;
     pack_bf16_kernel<<<(nchunks + 255) / 256, 256, 0, s>>>(t, (uint8_t *)tc->img);
     NB_CUDA(cudaGetLastError());
@@ -406,9 +455,10 @@ nb_status nb_tc_refresh(TcModel *tc, const MlpDesc &d, cudaStream_t s) {
 
 nb_status nb_tc_query(TcModel *tc, const MlpDesc &d, const float *q, int64_t n, TauF tau, float margin,
                       uint32_t *bits, float *logits, nb_query_stats *st, QueryWs ws, cudaStream_t s) {
-    if (tc->infer_prec == NB_F16X3) return nb_split_query(tc, d, q, n, tau, margin, bits, logits, st, ws, s);
-    if (tc->infer_prec == NB_FP8) return nb_fp8_query(tc, d, q, n, tau, margin, bits, logits, st, ws, s);
-    const TcDesc t = make_desc(tc, d);
+    const MlpDesc &e = fwd_desc(tc, d);
+    if (tc->infer_prec == NB_F16X3) return nb_split_query(tc, e, q, n, tau, margin, bits, logits, st, ws, s);
+    if (tc->infer_prec == NB_FP8) return nb_fp8_query(tc, e, q, n, tau, margin, bits, logits, st, ws, s);
+    const TcDesc t = make_desc(tc, e);
     const size_t smem = fwd_smem_bytes(t.H, t.NH);
     const int64_t tiles = (n + TILE_M - 1) / TILE_M;
     int64_t grid = num_sms();

@@ -12,6 +12,12 @@ struct TcModel {
     void *train_img = nullptr;   // device: BF16 weights for the tensor-core training step
     size_t train_img_bytes = 0;
     int *err = nullptr;      // device: status of the last bounded wait that gave up (0 = none)
+    // Hidden widths below the kernels' 64 / 128 (the paper's 25-, 50- and 75-wide networks):
+    // the forward runs on a copy of the parameters zero-padded to that width.  Padded
+    // neurons have zero weights and bias, so they stay 0 through the ReLU and add exact
+    // zeros downstream: the padded network computes the same logits.
+    float *pad_p = nullptr;  // device: padded FP32 parameters (refreshed with the master copy)
+    MlpDesc pad{};           // their layout (pad.p = pad_p)
 };
 
 // split-FP16 forward (tc_split.cu)

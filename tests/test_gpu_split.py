@@ -10,7 +10,10 @@ from paper_2310_06822_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 NETS = [("ray3", [6, 128, 128, 128, 128, 1]), ("point3", [3, 128, 128, 128, 128, 1]),
-        ("ray3", [6, 128, 128, 128, 1]), ("point4t", [4, 64, 64, 64, 1]), ("plane3", [4, 64, 64, 1])]
+        ("ray3", [6, 128, 128, 128, 1]), ("point4t", [4, 64, 64, 64, 1]), ("plane3", [4, 64, 64, 1]),
+        # the paper's own network sizes (25, 50, 75 wide), run zero-padded to 64 / 128
+        ("point2", [2, 25, 25, 1]), ("point3", [3, 50, 50, 1]), ("ray3", [6, 50, 50, 1]),
+        ("point4t", [4, 75, 75, 1])]
 
 
 @pytest.fixture(scope="module")
@@ -70,3 +73,28 @@ def test_split_matches_fp32_form_at_full_size(nb):
     bf = mf.query(qd, margin=0.05)
     assert torch.equal(bs, bf)
     assert np.max(np.abs(zs.cpu().numpy()[idx].astype(np.float64) - z64)) <= 2e-2
+
+
+@pytest.mark.parametrize("widths,kind", [([3, 50, 50, 1], "point3"), ([6, 75, 75, 75, 1], "ray3")])
+def test_padded_narrow_network_bf16_and_training(nb, widths, kind):
+    """A 50- or 75-wide network on the BF16 forward (zero-padded to 64 / 128): decisions
+    equal the oracle's once the band is re-checked, and parameter updates reach the padded
+    copy; BF16 training needs the kernels' own widths, FP32 training takes any width."""
+    p = (I.init_params(91, widths) * 3.0).astype(np.float32)
+    m = nb.Model(widths, infer_prec="bf16")
+    m.set_params(p)
+    n = 50_001
+    q = I.sample_queries(kind, 92, n)
+    for step in range(2):
+        z64 = O.forward(widths, m.get_params(), q)
+        tau = float(np.quantile(z64, 0.5))
+        m.tau = tau
+        bits, z = m.query(_dev(q), margin=0.5, logits=True)
+        assert np.max(np.abs(z.cpu().numpy() - z64)) <= 0.25
+        tie = np.abs(z64 - tau) <= 1e-12 * max(1.0, abs(tau))
+        assert np.array_equal(nb.bits_to_numpy(bits, n)[~tie], (z64 >= tau)[~tie])
+        # one FP32 training step moves the weights; the padded copy follows
+        y = _dev(I.pack_bits(z64 >= tau).view(np.int32))
+        m.train_step(_dev(q[:4096]), y[:128], 2.0)
+    with pytest.raises(nb.NBError):
+        nb.Model(widths, train_prec="bf16")
