@@ -107,9 +107,11 @@ typedef struct nb_model nb_model;
 /* Create a bounding network h (Sec. 3.4 "Architecture"): widths[0] is the query
  * encoding width, widths[1..n_layers-1] the hidden widths (ReLU), widths[n_layers]
  * must be 1 (the logit).  Hidden widths 1..256.  infer_prec selects the nb_query
- * fast path (see nb_prec; the tensor-core paths need equal hidden widths (64 or 128
- * for NB_BF16 and NB_F16X3, 128 or 256 for NB_FP8), an input width <= 16 and weights
- * that fit in shared memory, else NB_EUNSUPPORTED).  train_prec selects the training
+ * fast path (see nb_prec; the tensor-core paths need equal hidden widths (at most 128
+ * for NB_BF16 and NB_F16X3, which run widths other than 64 and 128 -- such as the
+ * paper's 25-, 50- and 75-wide networks -- on a copy of the parameters zero-padded to
+ * 64 or 128, computing the same logits; 128 or 256 for NB_FP8), an input width <= 16 and
+ * weights that fit in shared memory, else NB_EUNSUPPORTED).  train_prec selects the training
  * step: NB_F32, or NB_BF16 (tensor cores; equal hidden widths of 64, 128 or 256, the
  * last with its weights streamed through shared memory).
  * Parameters start at zero; load them with nb_model_set_params.  Adam uses lr 1e-3,
