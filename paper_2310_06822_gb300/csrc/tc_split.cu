@@ -13,9 +13,10 @@
 //                  activations as FP16 hi and lo halves (H/2 + H/2 columns), which the
 //                  MMA reads directly as its A operand -- activations never leave the SM.
 // Warp roles: two tile slots, each with its epilogue warps (one thread per query row =
-// TMEM lane; the single-model kernel splits every row's columns between two warps), and
-// one warp that allocates TMEM, loads the weights and issues the MMAs.  Layer 0 takes the input split the same way,
-// A0 = [x_hi | x_lo | x_hi | 0] against B0 = [W_hi | W_hi | W_lo | 0] (K = 64).
+// TMEM lane; the grouped kernel splits every row's columns between two warps), and one
+// warp that allocates TMEM, loads the weights and issues the MMAs.  Layer 0 takes the
+// input split the same way, A0 = [x_hi | x_lo | x_hi | 0] against
+// B0 = [W_hi | W_hi | W_lo | 0] (K = 64).
 // All waits are bounded; on expiry the kernel records NB_ETIMEOUT, drains the tensor
 // pipe and frees TMEM before returning.
 #include <cuda_fp16.h>
