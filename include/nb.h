@@ -95,10 +95,10 @@ typedef struct {
 typedef struct {
     float loss;                    /* mean asymmetric BCE of the batch, Eq. (loss) */
     float reserved;
-    unsigned long long fn;         /* batch false negatives at logit >= tau */
-    unsigned long long fp;         /* batch false positives at logit >= tau */
-    unsigned long long n_nonfinite;/* samples with a non-finite logit */
-} nb_step_stats;
+    unsigned long long fn;         /* batch false negatives at logit >= tau (added to) */
+    unsigned long long fp;         /* batch false positives at logit >= tau (added to) */
+    unsigned long long n_nonfinite;/* samples with a non-finite logit (added to) */
+} nb_step_stats;  /* loss is written by each step; the counts accumulate until the caller zeroes them */
 
 typedef struct nb_model nb_model;
 
@@ -227,6 +227,30 @@ nb_status nb_query_three_way(nb_model *outer, nb_model *inner, const float *q, i
 /* out[i] = 1 - in[i] for the n bits of a label or decision array (bits past n cleared);
  * in and out may be the same buffer.  Asynchronous on stream. */
 nb_status nb_bits_not(const uint32_t *in, int64_t n, uint32_t *out, void *stream);
+
+/* Stepwise asymmetry schedule (Sec. 3.4; Suppl. "Weight schedule"), host logic.  The
+ * loss weights change only at the end of a window of `period` iterations (10,000 in the
+ * paper), and only if that window's training batches had false negatives (the fn count
+ * the training steps add into one nb_step_stats, read once per window).  After k such
+ * adjustments alpha (the false-negative weight of Eq. (loss)) is 1 + fn_step * k and beta
+ * (the false-positive weight) is 1 / (dim_rate * k); both are 1 before the first.  The
+ * paper's rates: dim_rate 20 (2D), 100 (3D), 200 (4D); fn_step 0.2.  The supplement
+ * states the two series with the weights' roles exchanged; this reading makes the
+ * false-negative cost grow without bound, as Sec. 3.1 requires.
+ * nb_stepwise_window returns 1 when stop_windows (> 0) consecutive windows have had no
+ * false negative (training may stop), 0 otherwise, -1 for an uninitialised schedule. */
+typedef struct {
+    int32_t period;        /* iterations per window */
+    int32_t dim_rate;      /* c in beta = 1 / (c k) */
+    float fn_step;         /* growth of alpha per adjustment */
+    int32_t stop_windows;  /* consecutive windows without a false negative that end training; 0: never */
+    int32_t adjustments;   /* k */
+    int32_t clean_windows; /* consecutive windows without a false negative so far */
+    float alpha;           /* current false-negative weight */
+    float beta;            /* current false-positive weight */
+} nb_stepwise;
+nb_status nb_stepwise_init(nb_stepwise *s, int32_t period, int32_t dim_rate, float fn_step, int32_t stop_windows);
+int32_t nb_stepwise_window(nb_stepwise *s, uint64_t fn);
 
 /* Threshold calibration (Suppl. "Numerics", output epsilon): tau = (minimum over
  * the queries labelled 1 of the network logit) - eps, rounded toward -infinity,

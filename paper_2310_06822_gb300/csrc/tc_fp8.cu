@@ -158,8 +158,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                     pa ^= 1;
                     if (!ok) break;
                     tc_fence_after();
-                    if (l == 0) {
-                        for (int j = 0; j < 4; j++)
+                    if (l == 0) {  // K = 48: the fourth 16-wide block of A0 and B0 is zero
+                        for (int j = 0; j < 3; j++)
                             mma_f16_ts(tD, tA + 8 * j, sdesc_sw128(wbase + 32 * j), id16, j > 0 ? 1u : 0u);
                     } else {
                         const uint32_t wl = wbase + fp8_off(H, l);

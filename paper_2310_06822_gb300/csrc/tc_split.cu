@@ -16,7 +16,8 @@
 // TMEM lane; the grouped kernel splits every row's columns between two warps), and one
 // warp that allocates TMEM, loads the weights and issues the MMAs.  Layer 0 takes the
 // input split the same way, A0 = [x_hi | x_lo | x_hi | 0] against
-// B0 = [W_hi | W_hi | W_lo | 0] (K = 64).
+// B0 = [W_hi | W_hi | W_lo | 0] (stored K = 64; the products stop at K = 48, the zero
+// block adds nothing).
 // All waits are bounded; on expiry the kernel records NB_ETIMEOUT, drains the tensor
 // pipe and frees TMEM before returning.
 #include <cuda_fp16.h>
@@ -143,8 +144,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                         tc_fence_after();
                         const uint32_t dt = tmem + s * SLOT_COLS;
                         const uint32_t ahi = dt + H, alo = dt + H + H / 2;
-                        if (l == 0) {
-                            for (int j = 0; j < 4; j++)
+                        if (l == 0) {  // K = 48: the fourth 16-wide block of A0 and B0 is zero
+                            for (int j = 0; j < 3; j++)
                                 mma_f16_ts(dt, ahi + 8 * j, sdesc_sw128(wbase + 32 * j), idesc, j > 0 ? 1u : 0u);
                         } else {
                             const uint32_t whi = wbase + split_off(H, l), wlo = whi + 2 * H * H;
@@ -527,8 +528,8 @@ __global__ void __launch_bounds__(STHREADS, 1)
                             tc_fence_after();
                             const uint32_t dt = tmem + s * SLOT_COLS;
                             const uint32_t ahi = dt + H, alo = dt + H + H / 2;
-                            if (l == 0) {
-                                for (int j = 0; j < 4; j++)
+                            if (l == 0) {  // K = 48: the fourth 16-wide block of A0 and B0 is zero
+                                for (int j = 0; j < 3; j++)
                                     mma_f16_ts(dt, ahi + 8 * j, sdesc_sw128(wbase + 32 * j), idesc, j > 0 ? 1u : 0u);
                             } else {
                                 const uint32_t whi = wbase + split_off(H, l), wlo = whi + 2 * H * H;

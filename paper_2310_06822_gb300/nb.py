@@ -31,7 +31,7 @@ EXPORTS = ["nb_model_create", "nb_model_destroy", "nb_model_param_count", "nb_mo
            "nb_group_set_schedule", "nb_group_sync_schedule", "nb_group_reserve", "nb_train_step_grouped",
            "nb_query_grouped", "nb_calibrate_grouped", "nb_cascade_bin", "nb_cascade_exact", "nb_sample", "nb_group_autotune", "nb_query_early_out", "nb_bits_not",
            "nb_query_three_way", "nb_cascade_index_create", "nb_cascade_index_destroy", "nb_cascade_bin_indexed",
-           "nb_cascade_index_max_nodes", "nb_cascade_index_build_host"]
+           "nb_cascade_index_max_nodes", "nb_cascade_index_build_host", "nb_stepwise_init", "nb_stepwise_window"]
 
 
 class NBError(RuntimeError):
@@ -116,6 +116,8 @@ def lib():
                 "nb_cascade_bin_indexed": ([P, P, P, i64, i32, P, P, P, P, P, P], st),
                 "nb_cascade_index_max_nodes": ([i32], i32),
                 "nb_cascade_index_build_host": ([P, i32, P, P, P], st),
+                "nb_stepwise_init": ([P, i32, i32, ctypes.c_float, i32], st),
+                "nb_stepwise_window": ([P, ctypes.c_uint64], i32),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -545,6 +547,49 @@ def query_three_way(outer: Model, inner: Model, q: torch.Tensor, margin_outer: f
     _check(lib().nb_query_three_way(outer._h, inner._h, _ptr(q), n, float(margin_outer), float(margin_inner),
                                     _ptr(out), _ptr(stats), _stream(stream)))
     return out
+
+
+class _StepwiseC(ctypes.Structure):
+    _fields_ = [("period", ctypes.c_int32), ("dim_rate", ctypes.c_int32), ("fn_step", ctypes.c_float),
+                ("stop_windows", ctypes.c_int32), ("adjustments", ctypes.c_int32), ("clean_windows", ctypes.c_int32),
+                ("alpha", ctypes.c_float), ("beta", ctypes.c_float)]
+
+
+class Stepwise:
+    """Stepwise asymmetry schedule of the loss weights (nb_stepwise_*): alpha and beta
+    change at the end of a window of `period` steps that saw false negatives."""
+
+    RATES = {2: 20, 3: 100, 4: 200}
+
+    def __init__(self, dim: int = 3, period: int = 10000, fn_step: float = 0.2, stop_windows: int = 0,
+                 dim_rate: int | None = None):
+        self._s = _StepwiseC()
+        rate = dim_rate if dim_rate is not None else self.RATES[dim]
+        _check(lib().nb_stepwise_init(ctypes.byref(self._s), int(period), int(rate), float(fn_step),
+                                      int(stop_windows)))
+
+    @property
+    def alpha(self) -> float:
+        return self._s.alpha
+
+    @property
+    def beta(self) -> float:
+        return self._s.beta
+
+    @property
+    def period(self) -> int:
+        return self._s.period
+
+    @property
+    def adjustments(self) -> int:
+        return self._s.adjustments
+
+    def window(self, fn: int) -> bool:
+        """End of a window with fn false negatives; True when training may stop."""
+        r = lib().nb_stepwise_window(ctypes.byref(self._s), int(fn))
+        if r < 0:
+            raise NBError(1, "nb_stepwise_window: uninitialised schedule")
+        return r == 1
 
 
 def step_stats_tensor(device="cuda") -> torch.Tensor:

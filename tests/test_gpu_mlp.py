@@ -267,3 +267,38 @@ def test_trained_ray_network_bf16_and_f32_decisions(nb):
     df = nb.bits_to_numpy(mf.query(qd, margin=max(m32, 1e-3)), n)
     assert np.array_equal(df[~tie], truth[~tie])
     torch.cuda.synchronize()
+
+
+def test_stepwise_schedule_training_reaches_zero_fn_windows(nb):
+    """2D points, the paper's 2->25->25->1 network trained in FP32 under the stepwise
+    schedule (windows of 100 steps, 2D rates): the weights grow more asymmetric while the
+    training batches show false negatives, and training stops after three clean windows."""
+    import torch
+    widths = [2, 25, 25, 1]
+    sc = I.make_scene(1100, 8, 2, 0.05, 0.3)
+    shape = nb.Shape(sc)
+    m, _ = _model(nb, widths, 1101)
+    s = nb.Stepwise(dim=2, period=100, stop_windows=3)
+    st = nb.step_stats_tensor()
+    fns, stopped, B = [], False, 1024
+    for t in range(6000):
+        q = nb.sample(I.POINT2, B, seed=1102, first=t * B)
+        m.train_step(q, nb.label(shape, I.POINT2, q), s.alpha, s.beta, stats=st)
+        if (t + 1) % s.period == 0:
+            fn = nb.read_step_stats(st)["fn"]
+            st.zero_()
+            fns.append(fn)
+            if s.window(fn):
+                stopped = True
+                break
+    assert s.adjustments >= 1 and fns[0] > 0
+    assert stopped or s.adjustments >= 3, fns
+    if stopped:
+        assert fns[-3:] == [0, 0, 0]
+    # the calibrated bound has no false negative on its calibration set
+    grid = _dev(I.grid_points_2d(256))
+    yg = nb.label(shape, I.POINT2, grid)
+    m.calibrate(grid, yg)
+    dec = nb.bits_to_numpy(m.query(grid, margin=1e-3), 65536)
+    assert not np.any(nb.bits_to_numpy(yg, 65536) & ~dec)
+    torch.cuda.synchronize()
