@@ -183,6 +183,18 @@ nb_status nb_train_step(nb_model *m, const float *q, const uint32_t *label_bits,
 nb_status nb_query(nb_model *m, const float *q, int64_t n, float margin, uint32_t *out_bits, float *opt_logits,
                    nb_query_stats *dev_stats, void *stream);
 
+/* nb_query for queries in host memory: host_q [n][enc width] and host_bits
+ * ((n + 31) / 32 words) are host buffers; pinned (page-locked) ones let the copies overlap
+ * the forward.  The queries are streamed in chunks of chunk_rows (0: 2^22; rounded up to
+ * a multiple of 32) through two library-owned device staging buffers: while one chunk is
+ * decided on `stream`, the next is copied in on a library-owned copy stream, and each
+ * chunk's bits are copied back as soon as its decisions are final.  Decisions, margin
+ * and re-check as nb_query.  host_stats (host memory, may be NULL) receives the sums over
+ * all chunks.  Synchronous: returns when every bit is in host_bits.  The staging buffers
+ * grow on demand (a growth synchronises the device). */
+nb_status nb_query_host(nb_model *m, const float *host_q, int64_t n, float margin, uint32_t *host_bits,
+                        nb_query_stats *host_stats, int64_t chunk_rows, void *stream);
+
 /* Neural early-out (Sec. 3.3): `early` is a (small) network trained and calibrated as a
  * conservative bound of the complement 1 - g (labels inverted, e.g. by nb_bits_not), so
  * that where it decides 0 the query is certainly inside (g = 1); `late` is the bounding

@@ -4,6 +4,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -113,6 +114,13 @@ struct nb_model {
     size_t eo_bytes = 0;
     // low-precision weight images for the tensor-core paths
     TcModel tc{};
+    // nb_query_host: two device staging chunks, a copy stream and its events
+    cudaStream_t hq_stream = nullptr;
+    cudaEvent_t hq_ready[2] = {nullptr, nullptr}, hq_done[2] = {nullptr, nullptr};
+    float *hq_q[2] = {nullptr, nullptr};
+    uint32_t *hq_bits[2] = {nullptr, nullptr};
+    nb_query_stats *hq_stats = nullptr;  // [3]: one per chunk buffer and the running sum
+    int64_t hq_chunk = 0;
 };
 
 static MlpDesc desc_of(const nb_model *m) {
@@ -164,6 +172,14 @@ static void free_model(nb_model *m) {
     cudaFree(m->paramsT);
     cudaFree(m->ws);
     cudaFree(m->eo_ws);
+    for (int b = 0; b < 2; b++) {
+        cudaFree(m->hq_q[b]);
+        cudaFree(m->hq_bits[b]);
+        if (m->hq_ready[b]) cudaEventDestroy(m->hq_ready[b]);
+        if (m->hq_done[b]) cudaEventDestroy(m->hq_done[b]);
+    }
+    cudaFree(m->hq_stats);
+    if (m->hq_stream) cudaStreamDestroy(m->hq_stream);
     nb_tc_free(&m->tc);
     delete m;
 }
@@ -426,6 +442,109 @@ extern "C" nb_status nb_query(nb_model *m, const float *q, int64_t n, float marg
         st = nb_tc_query(&m->tc, d, q, n, tau, margin, out_bits, opt_logits, dev_stats, ws, s);
     if (st != NB_OK) return st;
     return nb_launch_recheck(d, m->gamma, q, tau, out_bits, dev_stats, ws, n, s);
+}
+
+// ---------------------------------------------------------------- queries from host memory
+namespace {
+__global__ void add_query_stats_kernel(nb_query_stats *sum, const nb_query_stats *part) {
+    sum->n_inside += part->n_inside;
+    sum->n_flagged += part->n_flagged;
+    sum->n_resolved_f32 += part->n_resolved_f32;
+    sum->n_resolved_ff += part->n_resolved_ff;
+    sum->n_unresolved += part->n_unresolved;
+    sum->n_nonfinite += part->n_nonfinite;
+}
+}  // namespace
+
+static nb_status ensure_host_pipe(nb_model *m, int64_t chunk) {
+    const int w = m->widths[0];
+    if (!m->hq_stream) {
+        NB_CUDA(cudaStreamCreateWithFlags(&m->hq_stream, cudaStreamNonBlocking));
+        for (int b = 0; b < 2; b++) {
+            NB_CUDA(cudaEventCreateWithFlags(&m->hq_ready[b], cudaEventDisableTiming));
+            NB_CUDA(cudaEventCreateWithFlags(&m->hq_done[b], cudaEventDisableTiming));
+        }
+        if (cudaMalloc(&m->hq_stats, 3 * sizeof(nb_query_stats)) != cudaSuccess) {
+            cudaGetLastError();
+            return nb_fail(NB_ENOMEM, "nb_query_host: allocation failed");
+        }
+    }
+    if (chunk <= m->hq_chunk) return NB_OK;
+    NB_CUDA(cudaDeviceSynchronize());
+    for (int b = 0; b < 2; b++) {
+        cudaFree(m->hq_q[b]);
+        cudaFree(m->hq_bits[b]);
+        m->hq_q[b] = nullptr;
+        m->hq_bits[b] = nullptr;
+    }
+    m->hq_chunk = 0;
+    for (int b = 0; b < 2; b++)
+        if (cudaMalloc(&m->hq_q[b], (size_t)chunk * w * sizeof(float)) != cudaSuccess ||
+            cudaMalloc(&m->hq_bits[b], (size_t)chunk / 32 * sizeof(uint32_t)) != cudaSuccess) {
+            cudaGetLastError();
+            return nb_fail(NB_ENOMEM, "nb_query_host: staging allocation failed");
+        }
+    m->hq_chunk = chunk;
+    return NB_OK;
+}
+
+extern "C" nb_status nb_query_host(nb_model *m, const float *host_q, int64_t n, float margin, uint32_t *host_bits,
+                                   nb_query_stats *host_stats, int64_t chunk_rows, void *stream) {
+    if (!m) return nb_fail(NB_EINVAL, "nb_query_host: null model");
+    if (n < 0 || n >= (int64_t)1 << 32) return nb_fail(NB_EINVAL, "nb_query_host: n must be in [0, 2^32)");
+    if (n > 0 && (!host_q || !host_bits)) return nb_fail(NB_EINVAL, "nb_query_host: null pointer");
+    if (chunk_rows < 0) return nb_fail(NB_EINVAL, "nb_query_host: chunk_rows must be >= 0");
+    if (host_stats) memset(host_stats, 0, sizeof(nb_query_stats));
+    if (n == 0) return NB_OK;
+    const int w = m->widths[0];
+    int64_t C = chunk_rows > 0 ? chunk_rows : ((int64_t)1 << 22);
+    C = (C + 31) / 32 * 32;
+    if (C > (n + 31) / 32 * 32) C = (n + 31) / 32 * 32;
+    nb_status st = ensure_host_pipe(m, C);
+    if (st != NB_OK) return st;
+    cudaStream_t S = (cudaStream_t)stream, cs = m->hq_stream;
+    nb_query_stats *sum = m->hq_stats + 2;
+    if (host_stats) NB_CUDA(cudaMemsetAsync(sum, 0, sizeof(nb_query_stats), S));
+    // copy stream: H2D(0), then for each chunk i: H2D(i + 1), D2H(i).  H2D(i + 1) reuses the
+    // buffer of chunk i - 1, whose D2H precedes it on the copy stream and waited for that
+    // chunk's query; the query of chunk i runs on `stream` while chunk i + 1 is copied in.
+    const int64_t nch = (n + C - 1) / C;
+    auto rows_of = [&](int64_t i) { return std::min<int64_t>(C, n - i * C); };
+    auto h2d = [&](int64_t i) -> nb_status {
+        const int b = (int)(i & 1);
+        NB_CUDA(cudaMemcpyAsync(m->hq_q[b], host_q + (size_t)(i * C) * w, (size_t)rows_of(i) * w * sizeof(float),
+                                cudaMemcpyHostToDevice, cs));
+        NB_CUDA(cudaEventRecord(m->hq_ready[b], cs));
+        return NB_OK;
+    };
+    NB_CUDA(cudaStreamSynchronize(S));  // the staging buffers may still serve a query on `stream`
+    st = h2d(0);
+    if (st != NB_OK) return st;
+    for (int64_t i = 0; i < nch; i++) {
+        const int b = (int)(i & 1);
+        NB_CUDA(cudaStreamWaitEvent(S, m->hq_ready[b], 0));
+        st = nb_query(m, m->hq_q[b], rows_of(i), margin, m->hq_bits[b], nullptr, host_stats ? m->hq_stats + b : nullptr,
+                      S);
+        if (st != NB_OK) return st;
+        if (host_stats) {
+            add_query_stats_kernel<<<1, 1, 0, S>>>(sum, m->hq_stats + b);
+            NB_CUDA(cudaGetLastError());
+        }
+        NB_CUDA(cudaEventRecord(m->hq_done[b], S));
+        if (i + 1 < nch) {
+            st = h2d(i + 1);
+            if (st != NB_OK) return st;
+        }
+        NB_CUDA(cudaStreamWaitEvent(cs, m->hq_done[b], 0));
+        NB_CUDA(cudaMemcpyAsync(host_bits + (size_t)(i * C) / 32, m->hq_bits[b],
+                                (size_t)((rows_of(i) + 31) / 32) * sizeof(uint32_t), cudaMemcpyDeviceToHost, cs));
+    }
+    NB_CUDA(cudaStreamSynchronize(cs));
+    if (host_stats) {
+        NB_CUDA(cudaMemcpyAsync(host_stats, sum, sizeof(nb_query_stats), cudaMemcpyDeviceToHost, S));
+        NB_CUDA(cudaStreamSynchronize(S));
+    }
+    return NB_OK;
 }
 
 // the workspace of the early-out and three-way queries, owned by one model; grows on demand

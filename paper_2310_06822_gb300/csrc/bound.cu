@@ -296,20 +296,44 @@ __device__ __forceinline__ void dot2_core(const float *__restrict__ Wt, const fl
         A[j] = 0.f;
         P[j] = 0.f;
     }
-    for (int k = 0; k < K; k++) {
-        const float hk = h[k], lk = l[k], ek = e[k];
+    // The weights of the next KB inputs are loaded while the current KB are accumulated:
+    // one warp walks one query through the network, so without this every input would
+    // wait for its weights' round trip to L2.  The arithmetic and its order are unchanged.
+    constexpr int KB = 8;
+    float wn[KB][NB];
 #pragma unroll
-        for (int j = 0; j < NB; j++) {
-            const float w = __ldg(Wr[j] + (size_t)k * N);
-            const float p = __fmul_rn(w, hk);
-            const float pq = fmaf(w, hk, -p);  // w hk = p + pq exactly
-            float t, er;
-            two_sum(s[j], p, t, er);
-            s[j] = t;
-            c[j] = __fadd_rn(__fadd_rn(c[j], er), pq);
-            c[j] = fmaf(w, lk, c[j]);
-            A[j] = __fmaf_ru(fabsf(w), fabsf(lk), __fadd_ru(A[j], __fadd_ru(fabsf(er), fabsf(pq))));
-            P[j] = __fmaf_ru(fabsf(w), ek, P[j]);
+    for (int kk = 0; kk < KB; kk++)
+#pragma unroll
+        for (int j = 0; j < NB; j++) wn[kk][j] = kk < K ? __ldg(Wr[j] + (size_t)kk * N) : 0.f;
+    for (int k0 = 0; k0 < K; k0 += KB) {
+        float wc[KB][NB];
+#pragma unroll
+        for (int kk = 0; kk < KB; kk++)
+#pragma unroll
+            for (int j = 0; j < NB; j++) wc[kk][j] = wn[kk][j];
+#pragma unroll
+        for (int kk = 0; kk < KB; kk++)
+#pragma unroll
+            for (int j = 0; j < NB; j++)
+                wn[kk][j] = k0 + KB + kk < K ? __ldg(Wr[j] + (size_t)(k0 + KB + kk) * N) : 0.f;
+#pragma unroll
+        for (int kk = 0; kk < KB; kk++) {
+            const int k = k0 + kk;
+            if (k >= K) break;
+            const float hk = h[k], lk = l[k], ek = e[k];
+#pragma unroll
+            for (int j = 0; j < NB; j++) {
+                const float w = wc[kk][j];
+                const float p = __fmul_rn(w, hk);
+                const float pq = fmaf(w, hk, -p);  // w hk = p + pq exactly
+                float t, er;
+                two_sum(s[j], p, t, er);
+                s[j] = t;
+                c[j] = __fadd_rn(__fadd_rn(c[j], er), pq);
+                c[j] = fmaf(w, lk, c[j]);
+                A[j] = __fmaf_ru(fabsf(w), fabsf(lk), __fadd_ru(A[j], __fadd_ru(fabsf(er), fabsf(pq))));
+                P[j] = __fmaf_ru(fabsf(w), ek, P[j]);
+            }
         }
     }
 #pragma unroll

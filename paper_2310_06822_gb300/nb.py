@@ -31,7 +31,8 @@ EXPORTS = ["nb_model_create", "nb_model_destroy", "nb_model_param_count", "nb_mo
            "nb_group_set_schedule", "nb_group_sync_schedule", "nb_group_reserve", "nb_train_step_grouped",
            "nb_query_grouped", "nb_calibrate_grouped", "nb_cascade_bin", "nb_cascade_exact", "nb_sample", "nb_group_autotune", "nb_query_early_out", "nb_bits_not",
            "nb_query_three_way", "nb_cascade_index_create", "nb_cascade_index_destroy", "nb_cascade_bin_indexed",
-           "nb_cascade_index_max_nodes", "nb_cascade_index_build_host", "nb_stepwise_init", "nb_stepwise_window"]
+           "nb_cascade_index_max_nodes", "nb_cascade_index_build_host", "nb_stepwise_init", "nb_stepwise_window",
+           "nb_query_host"]
 
 
 class NBError(RuntimeError):
@@ -118,6 +119,7 @@ def lib():
                 "nb_cascade_index_build_host": ([P, i32, P, P, P], st),
                 "nb_stepwise_init": ([P, i32, i32, ctypes.c_float, i32], st),
                 "nb_stepwise_window": ([P, ctypes.c_uint64], i32),
+                "nb_query_host": ([P, P, i64, ctypes.c_float, P, P, i64, P], st),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -281,6 +283,22 @@ class Model:
         _check(lib().nb_calibrate(self._h, _ptr(q), _ptr(label_bits), q.shape[0], float(eps), ctypes.byref(t),
                                   _stream(stream)))
         return t.value
+
+    def query_host(self, q, margin: float = 0.0, out=None, stats: bool = False, chunk_rows: int = 0, stream=None):
+        """Decisions for queries in host memory (nb_query_host): q a contiguous float32 CPU
+        tensor (pinned for copy/compute overlap), the bits into a CPU int32 tensor."""
+        if q.is_cuda or q.dtype != torch.float32 or not q.is_contiguous():
+            raise ValueError("q must be a contiguous float32 host tensor")
+        n = q.shape[0]
+        if out is None:
+            out = torch.empty(n_words(n), dtype=torch.int32, pin_memory=q.is_pinned())
+        st = np.zeros(1, dtype=QUERY_STATS)
+        _check(lib().nb_query_host(self._h, _ptr(q), n, float(margin), _ptr(out),
+                                   st.ctypes.data_as(ctypes.c_void_p) if stats else None, int(chunk_rows),
+                                   _stream(stream)))
+        if stats:
+            return out, {k: int(st[0][k]) for k in QUERY_STATS.names}
+        return out
 
 
 class Plan:

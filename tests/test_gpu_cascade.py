@@ -129,7 +129,8 @@ def _segments(off, pair_ray, pair_q=None):
     return out
 
 
-@pytest.mark.parametrize("K,canonical", [(1, True), (24, False), (24, True), (300, True)])
+@pytest.mark.parametrize("K,canonical", [(1, True), (24, False), (24, True), (300, True), (2048, False),
+                                         (4096, True)])
 def test_indexed_binning_equals_every_box(nb, K, canonical):
     ms = I.make_multi_scene(41 + K, K, 32)
     rays = I.sample_world_rays(42 + K, 50_000).astype(np.float32)

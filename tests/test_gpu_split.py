@@ -98,3 +98,26 @@ def test_padded_narrow_network_bf16_and_training(nb, widths, kind):
         m.train_step(_dev(q[:4096]), y[:128], 2.0)
     with pytest.raises(nb.NBError):
         nb.Model(widths, train_prec="bf16")
+
+
+@pytest.mark.parametrize("chunk_rows,pinned", [(0, True), (4096, True), (100_000, False)])
+def test_query_from_host_memory_equals_device_query(nb, chunk_rows, pinned):
+    """nb_query_host streams host queries through two staging chunks (copy on one stream,
+    decide on another): bits and statistics equal those of one device-side nb_query."""
+    import torch
+    widths = [6, 128, 128, 128, 128, 1]
+    p = (I.init_params(95, widths) * 3.0).astype(np.float32)
+    m = nb.Model(widths, infer_prec="f16x3")
+    m.set_params(p)
+    n = 300_007
+    q = I.sample_queries("ray3", 96, n)
+    m.tau = float(np.quantile(O.forward(widths, p, q[:5000]), 0.5))
+    ref, st_ref = m.query(_dev(q), margin=0.05, stats=True)
+    hq = torch.as_tensor(q)
+    if pinned:
+        hq = hq.pin_memory()
+    bits, st = m.query_host(hq, margin=0.05, stats=True, chunk_rows=chunk_rows)
+    assert np.array_equal(bits.numpy(), ref.cpu().numpy())
+    assert st == st_ref
+    # the empty call
+    assert m.query_host(hq[:0]).numel() == 0
