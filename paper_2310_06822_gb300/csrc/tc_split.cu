@@ -408,7 +408,7 @@ nb_status nb_split_query(TcModel *tc, const MlpDesc &d, const float *q, int64_t 
 namespace {
 
 struct GCtl {
-    uint64_t wbar, aready[2], accfull[2], drain, item_ready, item_done;
+    uint64_t wbar, aready[4], accfull[4], drain, item_ready, item_done;
     uint64_t pair[8];  // head-sum handshake of the two warps of each (slot, lane quarter)
     uint32_t tmem;
     int abort;
@@ -436,7 +436,13 @@ __global__ void __launch_bounds__(STHREADS, 1)
                            uint32_t *__restrict__ bits, float *__restrict__ logits, nb_query_stats *st,
                            unsigned *flag_count, unsigned *flag_idx, int *err) {
     constexpr uint32_t SLOT_COLS = 2 * H;
-    constexpr int HALF = H / 2;
+    // tile slots: as many as tensor memory holds (4 at width 64, 2 at width 128); the 16
+    // epilogue warps are shared out among them, and where a slot has 8 the two warps of a
+    // lane quarter split the columns (and exchange partial head sums)
+    constexpr int NS = 512 / (int)SLOT_COLS;
+    constexpr int WPS = SEPI / NS;
+    constexpr bool SPLIT = WPS == 8;
+    constexpr int HALF = SPLIT ? H / 2 : H;  // columns per epilogue warp
     extern __shared__ uint8_t smem_raw[];
     GCtl *ctl = reinterpret_cast<GCtl *>(smem_raw);
     uint8_t *Wimg = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023) + 1024;
@@ -447,14 +453,18 @@ __global__ void __launch_bounds__(STHREADS, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t bar_w = smem_u32(&ctl->wbar), bar_drain = smem_u32(&ctl->drain);
     const uint32_t bar_ready = smem_u32(&ctl->item_ready), bar_done = smem_u32(&ctl->item_done);
-    const uint32_t bar_ar[2] = {smem_u32(&ctl->aready[0]), smem_u32(&ctl->aready[1])};
-    const uint32_t bar_af[2] = {smem_u32(&ctl->accfull[0]), smem_u32(&ctl->accfull[1])};
+    uint32_t bar_ar[NS], bar_af[NS];
+#pragma unroll
+    for (int i = 0; i < NS; i++) {
+        bar_ar[i] = smem_u32(&ctl->aready[i]);
+        bar_af[i] = smem_u32(&ctl->accfull[i]);
+    }
     if (threadIdx.x == 0) {
         mbar_init(bar_w, 1);
-        mbar_init(bar_ar[0], 8);
-        mbar_init(bar_ar[1], 8);
-        mbar_init(bar_af[0], 1);
-        mbar_init(bar_af[1], 1);
+        for (int i = 0; i < NS; i++) {
+            mbar_init(bar_ar[i], WPS);
+            mbar_init(bar_af[i], 1);
+        }
         mbar_init(bar_drain, 1);
         mbar_init(bar_ready, 1);
         mbar_init(bar_done, SEPI);
@@ -463,7 +473,7 @@ __global__ void __launch_bounds__(STHREADS, 1)
         fence_mbar_init();
     }
     if (warp == SEPI) {
-        tmem_alloc(smem_u32(&ctl->tmem), 2 * SLOT_COLS);
+        tmem_alloc(smem_u32(&ctl->tmem), NS * SLOT_COLS);
         tmem_relinquish();
     }
     tc_fence_before();
@@ -472,7 +482,7 @@ __global__ void __launch_bounds__(STHREADS, 1)
     const uint32_t tmem = ctl->tmem;
 
     if (warp == SEPI) {
-        uint32_t ph_ar[2] = {0, 0}, ph_w = 0, ph_done = 0, ph_drain = 0;
+        uint32_t ph_ar[NS] = {}, ph_w = 0, ph_done = 0, ph_drain = 0;
         int cur_obj = -1;
         bool ok = true;
         constexpr uint32_t idesc = idesc_f16(TILE_M, H);
@@ -516,12 +526,10 @@ __global__ void __launch_bounds__(STHREADS, 1)
             const long long nt = (it.row1 - it.row0 + TILE_M - 1) / TILE_M;
             int okl = 1;
             if (lane == 0) {
-                for (long long tp = 0; okl; tp++) {
-                    const bool has[2] = {2 * tp < nt, 2 * tp + 1 < nt};
-                    if (!has[0] && !has[1]) break;
+                for (long long tp = 0; okl && NS * tp < nt; tp++) {
                     for (int l = 0; l < d.NH && okl; l++)
-                        for (int s = 0; s < 2 && okl; s++) {
-                            if (!has[s]) continue;
+                        for (int s = 0; s < NS && okl; s++) {
+                            if (NS * tp + s >= nt) continue;
                             okl = gwait(bar_ar[s], ph_ar[s], ctl, err);
                             ph_ar[s] ^= 1;
                             if (!okl) break;
@@ -555,12 +563,12 @@ __global__ void __launch_bounds__(STHREADS, 1)
         }
         __syncwarp();
     } else {
-        const int s = warp >> 3, ws = warp & 7, wq = ws & 3, hf = ws >> 2;
+        const int s = warp / WPS, ws = warp % WPS, wq = ws & 3, hf = ws >> 2;
         const int r = wq * 32 + lane;
         const int c0 = hf * HALF;  // first neuron of this warp
         const uint32_t trow = tmem + ((uint32_t)(wq * 32) << 16) + s * SLOT_COLS;
         const uint32_t tD = trow + c0, tAhi = trow + H, tAlo = trow + H + H / 2;
-        const uint32_t bar_pair = smem_u32(&ctl->pair[s * 4 + wq]);
+        const uint32_t bar_pair = SPLIT ? smem_u32(&ctl->pair[(s * 4 + wq) & 7]) : 0u;
         const int in = d.in;
         uint32_t ph_acc = 0, ph_ready = 0, pp = 0;
         unsigned long long c_in = 0, c_flag = 0, c_nf = 0;
@@ -576,12 +584,12 @@ __global__ void __launch_bounds__(STHREADS, 1)
             const long long nt = (it.row1 - it.row0 + TILE_M - 1) / TILE_M;
             float x[16];
             if (hf == 0) {
-                const long long row0 = it.row0 + (long long)s * TILE_M + r;
+                const long long row0 = it.row0 + (long long)s * TILE_M + r;  // the slot's first tile
 #pragma unroll
                 for (int kk = 0; kk < 16; kk++) x[kk] = (row0 < it.row1 && kk < in) ? __ldg(q + row0 * in + kk) : 0.f;
             }
-            for (long long tp = 0; ok && 2 * tp + s < nt; tp++) {
-                const long long trow0 = it.row0 + (2 * tp + s) * TILE_M;
+            for (long long tp = 0; ok && NS * tp + s < nt; tp++) {
+                const long long trow0 = it.row0 + (NS * tp + s) * TILE_M;
                 const long long row = trow0 + r;
                 const bool valid = row < it.row1;
                 if (hf == 0) {
@@ -603,7 +611,7 @@ __global__ void __launch_bounds__(STHREADS, 1)
                 __syncwarp();
                 if (lane == 0) mbar_arrive(bar_ar[s]);
                 if (hf == 0) {
-                    const long long nrow = trow0 + 2 * TILE_M + r;
+                    const long long nrow = trow0 + NS * TILE_M + r;
 #pragma unroll
                     for (int kk = 0; kk < 16; kk++)
                         x[kk] = (nrow < it.row1 && kk < in) ? __ldg(q + nrow * in + kk) : 0.f;
@@ -647,15 +655,19 @@ __global__ void __launch_bounds__(STHREADS, 1)
                                 zp = fmaf(head[c0 + c * 32 + e], fmaxf(v[e] + b[c * 32 + e], 0.f), zp);
                         }
                         tc_fence_before();
-                        // exchange the partial sums with the other half of the row
-                        xbuf[warp * 32 + lane] = zp;
-                        mbar_arrive(bar_pair);
-                        ok = gwait(bar_pair, pp, ctl, err);
-                        pp ^= 1;
-                        const float zo = xbuf[(warp ^ 4) * 32 + lane];
-                        ok = __all_sync(FULL, ok);
-                        if (!ok) break;
-                        z = (hf == 0 ? zp + zo : zo + zp) + head[H];
+                        if (SPLIT) {
+                            // exchange the partial sums with the other half of the row
+                            xbuf[warp * 32 + lane] = zp;
+                            mbar_arrive(bar_pair);
+                            ok = gwait(bar_pair, pp, ctl, err);
+                            pp ^= 1;
+                            const float zo = xbuf[(warp ^ 4) * 32 + lane];
+                            ok = __all_sync(FULL, ok);
+                            if (!ok) break;
+                            z = (hf == 0 ? zp + zo : zo + zp) + head[H];
+                        } else {
+                            z = zp + head[H];
+                        }
                     }
                 }
                 if (!ok) break;
@@ -694,7 +706,7 @@ __global__ void __launch_bounds__(STHREADS, 1)
     __syncthreads();
     if (warp == SEPI) {
         tc_fence_after();
-        tmem_dealloc(tmem, 2 * SLOT_COLS);
+        tmem_dealloc(tmem, NS * SLOT_COLS);
     }
 }
 
