@@ -346,7 +346,7 @@ nb_status nb_group_autotune(nb_group *g, const int64_t *host_offsets, int32_t n_
  * network, and rays asking "which rays hit any object".  Following the paper's premise
  * of a cheap conservative test in front of an expensive exact one (Sec. 1, Eq. (Benefit)),
  * the cascade is: axis-aligned box of the object -> the object's neural bound -> exact
- * sphere test; the plain path (box -> exact) is the judge: both must give the same hits.
+ * sphere test; the plain path (box -> exact) is the reference: both must give the same hits.
  * All pointers are device pointers. */
 typedef struct {
     int32_t n_objects;            /* K, 1 .. 4096 */
