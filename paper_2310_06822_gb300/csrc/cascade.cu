@@ -274,60 +274,98 @@ __global__ void __launch_bounds__(BVH_TPB)
     }
 }
 
+// the exact ray-sphere predicate on grid integers: w = C - O, hit iff |w|^2 <= r^2 or
+// (w.d > 0 and |w|^2 |d|^2 - (w.d)^2 <= r^2 |d|^2), in 64- and 128-bit integers
+__device__ __forceinline__ bool ray_sphere_exact(const int Q[6], long long DD, int c0, int c1, int c2, int rr) {
+    const int w0 = c0 - Q[0], w1 = c1 - Q[1], w2 = c2 - Q[2];
+    const long long WW = sq(w0) + sq(w1) + sq(w2), RR = sq(rr);
+    if (WW <= RR) return true;
+    const long long SD = (long long)w0 * Q[3] + (long long)w1 * Q[4] + (long long)w2 * Q[5];
+    return SD > 0 && (unsigned __int128)(unsigned long long)(WW - RR) * (unsigned long long)DD <=
+                         (unsigned __int128)(unsigned long long)SD * (unsigned long long)SD;
+}
+
+// One warp per 32 consecutive rows.  Rows are binned by object, so a warp's rows nearly
+// always belong to one object: then its lanes convert 32 of the object's spheres to grid
+// integers at a time, one each, and every lane tests its ray against them through warp
+// shuffles.  Rows of several objects in one warp are tested lane by lane.  Either way a
+// pair's test stops at its first hit, and sphere_tests counts the predicates up to it.
 __global__ void __launch_bounds__(256)
     exact_kernel(int K, int qexp, const long long *__restrict__ sph_off, const float *__restrict__ cen,
                  const float *__restrict__ rad, const float *__restrict__ rays, const uint32_t *__restrict__ pair_ray,
                  const long long *__restrict__ offsets, long long rows, const uint32_t *__restrict__ pass,
                  uint32_t *__restrict__ hits, uint32_t *__restrict__ pair_hits, nb_cascade_stats *st) {
     const float scale = ldexpf(1.0f, qexp);
+    const int lane = threadIdx.x & 31;
     unsigned long long n_pairs = 0, n_tests = 0, n_hit = 0;
-    for (long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x; row < rows;
-         row += (long long)gridDim.x * blockDim.x) {
-        const uint32_t r = pair_ray[row];
-        if (r == NO_RAY) continue;
-        if (pass && !((pass[row >> 5] >> (row & 31)) & 1u)) continue;
+    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long g = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); g * 32 < rows; g += nwarps) {
+        const long long row = g * 32 + lane;
+        const uint32_t r = row < rows ? pair_ray[row] : NO_RAY;
+        const bool live = r != NO_RAY && !(pass && !((pass[row >> 5] >> (row & 31)) & 1u));
+        if (!__any_sync(FULL, live)) continue;
+        const long long rr = min(row, rows - 1);
         int lo = 0, hi = K - 1;  // object of this row: last k with offsets[k] <= row
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (offsets[mid] <= row) lo = mid; else hi = mid - 1;
+            if (offsets[mid] <= rr) lo = mid; else hi = mid - 1;
         }
-        int Q[6];
+        int Q[6] = {0, 0, 0, 0, 0, 0};
         bool ok = true;
-        for (int i = 0; i < 6; i++) ok &= to_grid(rays[(size_t)r * 6 + i], scale, Q[i]);
-        n_pairs++;
-        int h = 1;  // an off-grid ray is a hit (conservative)
-        if (ok) {
-            h = 0;
-            const long long DD = sq(Q[3]) + sq(Q[4]) + sq(Q[5]);
-            for (long long s = sph_off[lo]; s < sph_off[lo + 1] && !h; s++) {
+        if (live)
+            for (int i = 0; i < 6; i++) ok &= to_grid(rays[(size_t)r * 6 + i], scale, Q[i]);
+        const long long DD = sq(Q[3]) + sq(Q[4]) + sq(Q[5]);
+        int h = live && !ok;  // an off-grid ray is a hit (conservative)
+        bool done = !live || !ok;
+        unsigned long long tests = 0;
+        const int obj0 = __shfl_sync(FULL, lo, 0);
+        if (__all_sync(FULL, lo == obj0)) {
+            const long long s0 = sph_off[obj0], s1 = sph_off[obj0 + 1];
+            for (long long sb = s0; sb < s1; sb += 32) {
+                if (__all_sync(FULL, done)) break;
+                int C[3] = {0, 0, 0}, Rr = 0;
+                int sok = 1;
+                if (sb + lane < s1) {
+                    const long long sj = sb + lane;
+                    sok = to_grid(cen[sj * 3], scale, C[0]) && to_grid(cen[sj * 3 + 1], scale, C[1]) &&
+                          to_grid(cen[sj * 3 + 2], scale, C[2]) && to_grid(rad[sj], scale, Rr);
+                }
+                const int cnt = (int)min(32LL, s1 - sb);
+                for (int j = 0; j < cnt; j++) {
+                    const int c0 = __shfl_sync(FULL, C[0], j), c1 = __shfl_sync(FULL, C[1], j);
+                    const int c2 = __shfl_sync(FULL, C[2], j), rj = __shfl_sync(FULL, Rr, j);
+                    const int okj = __shfl_sync(FULL, sok, j);
+                    if (done) continue;
+                    tests++;
+                    if (!okj || ray_sphere_exact(Q, DD, c0, c1, c2, rj)) {
+                        h = 1;  // an off-grid sphere counts as hit (conservative)
+                        done = true;
+                    }
+                }
+            }
+        } else {
+            for (long long sj = sph_off[lo]; !done && sj < sph_off[lo + 1]; sj++) {
                 int C[3], Rr;
-                bool sok = to_grid(cen[s * 3], scale, C[0]) && to_grid(cen[s * 3 + 1], scale, C[1]) &&
-                           to_grid(cen[s * 3 + 2], scale, C[2]) && to_grid(rad[s], scale, Rr);
-                n_tests++;
-                if (!sok) {
+                const bool sok = to_grid(cen[sj * 3], scale, C[0]) && to_grid(cen[sj * 3 + 1], scale, C[1]) &&
+                                 to_grid(cen[sj * 3 + 2], scale, C[2]) && to_grid(rad[sj], scale, Rr);
+                tests++;
+                if (!sok || ray_sphere_exact(Q, DD, C[0], C[1], C[2], Rr)) {
                     h = 1;
-                    break;
+                    done = true;
                 }
-                const int w0 = C[0] - Q[0], w1 = C[1] - Q[1], w2 = C[2] - Q[2];
-                const long long WW = sq(w0) + sq(w1) + sq(w2), RR = sq(Rr);
-                if (WW <= RR) {
-                    h = 1;
-                    break;
-                }
-                const long long SD = (long long)w0 * Q[3] + (long long)w1 * Q[4] + (long long)w2 * Q[5];
-                if (SD > 0 && (unsigned __int128)(unsigned long long)(WW - RR) * (unsigned long long)DD <=
-                                  (unsigned __int128)(unsigned long long)SD * (unsigned long long)SD)
-                    h = 1;
             }
         }
-        if (h) {
-            n_hit++;
-            if (hits) atomicOr(hits + (r >> 5), 1u << (r & 31));
-            if (pair_hits) atomicOr(pair_hits + (row >> 5), 1u << (row & 31));
+        if (live) {
+            n_pairs++;
+            n_tests += tests;
+            if (h) {
+                n_hit++;
+                if (hits) atomicOr(hits + (r >> 5), 1u << (r & 31));
+                if (pair_hits) atomicOr(pair_hits + (row >> 5), 1u << (row & 31));
+            }
         }
     }
     if (st) {
-        const int lane = threadIdx.x & 31;
 #pragma unroll
         for (int o = 16; o; o >>= 1) {
             n_pairs += __shfl_xor_sync(FULL, n_pairs, o);
