@@ -183,6 +183,20 @@ nb_status nb_train_step(nb_model *m, const float *q, const uint32_t *label_bits,
 nb_status nb_query(nb_model *m, const float *q, int64_t n, float margin, uint32_t *out_bits, float *opt_logits,
                    nb_query_stats *dev_stats, void *stream);
 
+/* Device status of a model's asynchronous work: synchronises `stream`, then returns
+ * NB_ECUDA for a pending CUDA error and NB_ETIMEOUT if one of the model's tensor-core
+ * kernels gave up a bounded wait since the last check (their waits on mbarriers poll a
+ * bounded number of times; on expiry the kernel drains its copies and products, frees
+ * tensor memory, returns and records the timeout, leaving the context usable).  The
+ * record is cleared.  nb_query_host and nb_query_early_out check by themselves. */
+nb_status nb_model_check(nb_model *m, void *stream);
+
+/* Diagnostic of that mechanism without a fault: one thread waits, with the forward
+ * kernels' bounded wait, on an mbarrier no one arrives at, gives up after `polls` polls
+ * (1 .. 2^20) and returns.  Returns NB_ETIMEOUT (the expected outcome) once the stream has
+ * drained; any other status is a failure of the mechanism. */
+nb_status nb_selftest_bounded_wait(int32_t polls, void *stream);
+
 /* nb_query for queries in host memory: host_q [n][enc width] and host_bits
  * ((n + 31) / 32 words) are host buffers; pinned (page-locked) ones let the copies overlap
  * the forward.  The queries are streamed in chunks of chunk_rows (0: 2^22; rounded up to

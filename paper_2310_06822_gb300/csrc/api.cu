@@ -444,6 +444,13 @@ extern "C" nb_status nb_query(nb_model *m, const float *q, int64_t n, float marg
     return nb_launch_recheck(d, m->gamma, q, tau, out_bits, dev_stats, ws, n, s);
 }
 
+extern "C" nb_status nb_model_check(nb_model *m, void *stream) {
+    if (!m) return nb_fail(NB_EINVAL, "nb_model_check: null model");
+    NB_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    NB_CUDA(cudaGetLastError());
+    return nb_tc_check(&m->tc);
+}
+
 // ---------------------------------------------------------------- queries from host memory
 namespace {
 __global__ void add_query_stats_kernel(nb_query_stats *sum, const nb_query_stats *part) {
@@ -544,7 +551,7 @@ extern "C" nb_status nb_query_host(nb_model *m, const float *host_q, int64_t n, 
         NB_CUDA(cudaMemcpyAsync(host_stats, sum, sizeof(nb_query_stats), cudaMemcpyDeviceToHost, S));
         NB_CUDA(cudaStreamSynchronize(S));
     }
-    return NB_OK;
+    return nb_tc_check(&m->tc);  // synchronous already: report a forward that gave up waiting
 }
 
 // the workspace of the early-out and three-way queries, owned by one model; grows on demand
@@ -605,7 +612,8 @@ extern "C" nb_status nb_query_early_out(nb_model *early, nb_model *late, const f
         host_stats->n_early_inside = (uint64_t)(n - m);
         host_stats->n_late = m;
     }
-    return NB_OK;
+    st = nb_tc_check(&early->tc);
+    return st != NB_OK ? st : nb_tc_check(&late->tc);
 }
 
 extern "C" nb_status nb_query_three_way(nb_model *outer, nb_model *inner, const float *q, int64_t n,

@@ -55,8 +55,8 @@ struct Ctl {
     int abort;
 };
 
-__device__ bool wait_bounded(uint32_t bar, uint32_t parity, Ctl *ctl, int *err) {
-    for (unsigned i = 0; i < SPIN_LIMIT; i++) {
+__device__ bool wait_bounded(uint32_t bar, uint32_t parity, Ctl *ctl, int *err, unsigned limit = SPIN_LIMIT) {
+    for (unsigned i = 0; i < limit; i++) {
         if (mbar_try_wait(bar, parity)) return true;
         if (*(volatile int *)&ctl->abort) return false;
     }
@@ -474,6 +474,45 @@ nb_status nb_tc_query(TcModel *tc, const MlpDesc &d, const float *q, int64_t n, 
                                                                   ws.flag_count, ws.flag_idx, tc->err);
     }
     NB_CUDA(cudaGetLastError());
+    return NB_OK;
+}
+
+namespace {
+// A wait that nothing completes: one thread waits on an mbarrier no one arrives at, with
+// the bounded wait of the forward kernels, gives up after `polls` polls and records
+// NB_ETIMEOUT, and the kernel returns.
+__global__ void selftest_wait_kernel(unsigned polls, int *err) {
+    __shared__ Ctl ctl;
+    const uint32_t bar = smem_u32(&ctl.wbar);
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        ctl.abort = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) wait_bounded(bar, 0, &ctl, err, polls);
+}
+}  // namespace
+
+extern "C" nb_status nb_selftest_bounded_wait(int32_t polls, void *stream) {
+    if (polls < 1 || polls > (1 << 20)) return nb_fail(NB_EINVAL, "nb_selftest_bounded_wait: polls must be 1..2^20");
+    int *err = nullptr;
+    if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return nb_fail(NB_ENOMEM, "nb_selftest_bounded_wait: allocation failed");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    int e = 0;
+    cudaError_t ce = cudaMemsetAsync(err, 0, sizeof(int), s);
+    if (ce == cudaSuccess) {
+        selftest_wait_kernel<<<1, 32, 0, s>>>((unsigned)polls, err);
+        ce = cudaGetLastError();
+    }
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(&e, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    cudaFree(err);
+    if (ce != cudaSuccess) return nb_fail(NB_ECUDA, cudaGetErrorString(ce));
+    if (e) return nb_fail((nb_status)e, "bounded device wait gave up (expected)");
     return NB_OK;
 }
 

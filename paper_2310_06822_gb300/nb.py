@@ -32,7 +32,7 @@ EXPORTS = ["nb_model_create", "nb_model_destroy", "nb_model_param_count", "nb_mo
            "nb_query_grouped", "nb_calibrate_grouped", "nb_cascade_bin", "nb_cascade_exact", "nb_sample", "nb_group_autotune", "nb_query_early_out", "nb_bits_not",
            "nb_query_three_way", "nb_cascade_index_create", "nb_cascade_index_destroy", "nb_cascade_bin_indexed",
            "nb_cascade_index_max_nodes", "nb_cascade_index_build_host", "nb_stepwise_init", "nb_stepwise_window",
-           "nb_query_host"]
+           "nb_query_host", "nb_model_check", "nb_selftest_bounded_wait"]
 
 
 class NBError(RuntimeError):
@@ -120,6 +120,8 @@ def lib():
                 "nb_stepwise_init": ([P, i32, i32, ctypes.c_float, i32], st),
                 "nb_stepwise_window": ([P, ctypes.c_uint64], i32),
                 "nb_query_host": ([P, P, i64, ctypes.c_float, P, P, i64, P], st),
+                "nb_model_check": ([P, P], st),
+                "nb_selftest_bounded_wait": ([i32, P], st),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -283,6 +285,10 @@ class Model:
         _check(lib().nb_calibrate(self._h, _ptr(q), _ptr(label_bits), q.shape[0], float(eps), ctypes.byref(t),
                                   _stream(stream)))
         return t.value
+
+    def check(self, stream=None):
+        """Raise NBError if the model's asynchronous work failed (nb_model_check)."""
+        _check(lib().nb_model_check(self._h, _stream(stream)))
 
     def query_host(self, q, margin: float = 0.0, out=None, stats: bool = False, chunk_rows: int = 0, stream=None):
         """Decisions for queries in host memory (nb_query_host): q a contiguous float32 CPU
@@ -608,6 +614,11 @@ class Stepwise:
         if r < 0:
             raise NBError(1, "nb_stepwise_window: uninitialised schedule")
         return r == 1
+
+
+def selftest_bounded_wait(polls: int = 1024, stream=None) -> int:
+    """Status of one bounded device wait that nothing completes (NB_ETIMEOUT expected)."""
+    return int(lib().nb_selftest_bounded_wait(int(polls), _stream(stream)))
 
 
 def step_stats_tensor(device="cuda") -> torch.Tensor:

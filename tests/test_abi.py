@@ -55,3 +55,10 @@ def test_host_side_argument_errors(lib):
     lib.nb_train_step.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                   ctypes.c_float, ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p]
     assert lib.nb_train_step(None, None, None, 1, 1.0, 1.0, None, None) == 1
+
+
+def test_selftest_argument_check_needs_no_device(lib):
+    lib.nb_selftest_bounded_wait.restype = ctypes.c_int
+    lib.nb_selftest_bounded_wait.argtypes = [ctypes.c_int32, ctypes.c_void_p]
+    assert lib.nb_selftest_bounded_wait(0, None) == 1  # NB_EINVAL before any device work
+    assert lib.nb_selftest_bounded_wait(1 << 21, None) == 1
