@@ -200,7 +200,8 @@ nb_status nb_selftest_bounded_wait(int32_t polls, void *stream);
 /* nb_query for queries in host memory: host_q [n][enc width] and host_bits
  * ((n + 31) / 32 words) are host buffers; pinned (page-locked) ones let the copies overlap
  * the forward.  The queries are streamed in chunks of chunk_rows (0: 2^22; rounded up to
- * a multiple of 32) through two library-owned device staging buffers: while one chunk is
+ * a multiple of 32; the first chunk a quarter of that, so the forward starts early)
+ * through two library-owned device staging buffers: while one chunk is
  * decided on `stream`, the next is copied in on a library-owned copy stream, and each
  * chunk's bits are copied back as soon as its decisions are final.  Decisions, margin
  * and re-check as nb_query.  host_stats (host memory, may be NULL) receives the sums over

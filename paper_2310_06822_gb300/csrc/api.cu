@@ -512,14 +512,20 @@ extern "C" nb_status nb_query_host(nb_model *m, const float *host_q, int64_t n, 
     cudaStream_t S = (cudaStream_t)stream, cs = m->hq_stream;
     nb_query_stats *sum = m->hq_stats + 2;
     if (host_stats) NB_CUDA(cudaMemsetAsync(sum, 0, sizeof(nb_query_stats), S));
-    // copy stream: H2D(0), then for each chunk i: H2D(i + 1), D2H(i).  H2D(i + 1) reuses the
+    // Copy stream: H2D(0), then for each chunk i: H2D(i + 1), D2H(i).  H2D(i + 1) reuses the
     // buffer of chunk i - 1, whose D2H precedes it on the copy stream and waited for that
     // chunk's query; the query of chunk i runs on `stream` while chunk i + 1 is copied in.
-    const int64_t nch = (n + C - 1) / C;
-    auto rows_of = [&](int64_t i) { return std::min<int64_t>(C, n - i * C); };
+    // chunk boundaries: the first chunk is a quarter of the others (a multiple of 32), so
+    // the forward starts after a short first copy
+    std::vector<int64_t> start;
+    const int64_t first = std::max<int64_t>(32, C / 4 / 32 * 32);
+    for (int64_t r0 = 0; r0 < n; r0 += (r0 == 0 ? first : C)) start.push_back(r0);
+    start.push_back(n);
+    const int64_t nch = (int64_t)start.size() - 1;
+    auto rows_of = [&](int64_t i) { return start[i + 1] - start[i]; };
     auto h2d = [&](int64_t i) -> nb_status {
         const int b = (int)(i & 1);
-        NB_CUDA(cudaMemcpyAsync(m->hq_q[b], host_q + (size_t)(i * C) * w, (size_t)rows_of(i) * w * sizeof(float),
+        NB_CUDA(cudaMemcpyAsync(m->hq_q[b], host_q + (size_t)start[i] * w, (size_t)rows_of(i) * w * sizeof(float),
                                 cudaMemcpyHostToDevice, cs));
         NB_CUDA(cudaEventRecord(m->hq_ready[b], cs));
         return NB_OK;
@@ -543,7 +549,7 @@ extern "C" nb_status nb_query_host(nb_model *m, const float *host_q, int64_t n, 
             if (st != NB_OK) return st;
         }
         NB_CUDA(cudaStreamWaitEvent(cs, m->hq_done[b], 0));
-        NB_CUDA(cudaMemcpyAsync(host_bits + (size_t)(i * C) / 32, m->hq_bits[b],
+        NB_CUDA(cudaMemcpyAsync(host_bits + (size_t)start[i] / 32, m->hq_bits[b],
                                 (size_t)((rows_of(i) + 31) / 32) * sizeof(uint32_t), cudaMemcpyDeviceToHost, cs));
     }
     NB_CUDA(cudaStreamSynchronize(cs));
