@@ -30,8 +30,14 @@ namespace {
 using namespace nbtc;
 
 constexpr int TILE_M = 128;
-constexpr int NEPI = 8;                    // single-model kernel: 4 epilogue warps per slot
-constexpr int THREADS = (NEPI + 1) * 32;
+// single-model kernel: 4 epilogue warps per tile slot, as many slots as tensor memory
+// holds (2 at width 128, 4 at width 64), and the MMA warp after them
+template <int H>
+struct Single {
+    static constexpr int NS = 512 / (2 * H);
+    static constexpr int NEPI = 4 * NS;
+    static constexpr int THREADS = (NEPI + 1) * 32;
+};
 constexpr unsigned SPIN_LIMIT = 1u << 22;
 constexpr unsigned FULL = 0xffffffffu;
 
@@ -50,7 +56,7 @@ __host__ __device__ inline uint32_t split_off(int H, int l) {
 }
 
 struct Ctl {
-    uint64_t wbar, aready[2], accfull[2], drain;
+    uint64_t wbar, aready[4], accfull[4], drain;
     uint32_t tmem;
     int abort;
 };
@@ -80,11 +86,12 @@ constexpr int SEPI = 16;
 constexpr int STHREADS = (SEPI + 1) * 32;
 
 template <int H>
-__global__ void __launch_bounds__(THREADS, 1)
+__global__ void __launch_bounds__(Single<H>::THREADS, 1)
     fwd_split_kernel(SplitDesc d, const float *__restrict__ q, long long n, TauF tau, float margin,
                      uint32_t *__restrict__ bits, float *__restrict__ logits, nb_query_stats *st,
                      unsigned *flag_count, unsigned *flag_idx, int *err) {
     constexpr uint32_t SLOT_COLS = 2 * H;  // accumulator H + activations H/2 hi + H/2 lo
+    constexpr int NS = Single<H>::NS, NEPI = Single<H>::NEPI, THREADS = Single<H>::THREADS;
     extern __shared__ uint8_t smem_raw[];
     Ctl *ctl = reinterpret_cast<Ctl *>(smem_raw);
     uint8_t *Wimg = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023) + 1024;
@@ -94,15 +101,19 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long ntiles = (n + TILE_M - 1) / TILE_M;
     const uint32_t bar_w = smem_u32(&ctl->wbar), bar_drain = smem_u32(&ctl->drain);
-    const uint32_t bar_ar[2] = {smem_u32(&ctl->aready[0]), smem_u32(&ctl->aready[1])};
-    const uint32_t bar_af[2] = {smem_u32(&ctl->accfull[0]), smem_u32(&ctl->accfull[1])};
+    uint32_t bar_ar[NS], bar_af[NS];
+#pragma unroll
+    for (int i = 0; i < NS; i++) {
+        bar_ar[i] = smem_u32(&ctl->aready[i]);
+        bar_af[i] = smem_u32(&ctl->accfull[i]);
+    }
 
     if (threadIdx.x == 0) {
         mbar_init(bar_w, 1);
-        mbar_init(bar_ar[0], 4);
-        mbar_init(bar_ar[1], 4);
-        mbar_init(bar_af[0], 1);
-        mbar_init(bar_af[1], 1);
+        for (int i = 0; i < NS; i++) {
+            mbar_init(bar_ar[i], 4);
+            mbar_init(bar_af[i], 1);
+        }
         mbar_init(bar_drain, 1);
         ctl->abort = 0;
         fence_mbar_init();
@@ -114,7 +125,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     for (int i = threadIdx.x; i <= H; i += THREADS) head[i] = d.p[d.off[d.NH] + i];
     if (warp == NEPI) {
-        tmem_alloc(smem_u32(&ctl->tmem), 2 * SLOT_COLS);
+        tmem_alloc(smem_u32(&ctl->tmem), NS * SLOT_COLS);
         tmem_relinquish();
     }
     tc_fence_before();
@@ -128,16 +139,14 @@ __global__ void __launch_bounds__(THREADS, 1)
             for (uint32_t o = 0; o < d.img_bytes; o += 16384)
                 bulk_g2s(smem_u32(Wimg) + o, d.img + o, min(16384u, d.img_bytes - o), bar_w);
             bool ok = wait_bounded(bar_w, 0, ctl, err);
-            uint32_t ph[2] = {0, 0};
+            uint32_t ph[NS] = {};
             constexpr uint32_t idesc = idesc_f16(TILE_M, H);
             const uint32_t wbase = smem_u32(Wimg);
             for (long long it = 0; ok; it++) {
-                const bool has[2] = {blockIdx.x + (2 * it) * gridDim.x < ntiles,
-                                     blockIdx.x + (2 * it + 1) * gridDim.x < ntiles};
-                if (!has[0] && !has[1]) break;
+                if (blockIdx.x + (NS * it) * gridDim.x >= ntiles) break;
                 for (int l = 0; l < d.NH && ok; l++)
-                    for (int s = 0; s < 2 && ok; s++) {
-                        if (!has[s]) continue;
+                    for (int s = 0; s < NS && ok; s++) {
+                        if (blockIdx.x + (NS * it + s) * gridDim.x >= ntiles) continue;
                         ok = wait_bounded(bar_ar[s], ph[s], ctl, err);
                         ph[s] ^= 1;
                         if (!ok) break;
@@ -182,7 +191,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             for (int k = 0; k < 16; k++) x[k] = (row0 < n && k < in) ? __ldg(q + row0 * in + k) : 0.f;
         }
         for (long long it = 0;; it++) {
-            const long long tile = blockIdx.x + (2 * it + s) * gridDim.x;
+            const long long tile = blockIdx.x + (NS * it + s) * gridDim.x;
             if (tile >= ntiles) break;
             const long long row = tile * TILE_M + r;
             const bool valid = row < n;
@@ -207,7 +216,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             if (lane == 0) mbar_arrive(bar_ar[s]);
             {
                 // prefetch the next tile's rows while this tile runs through the layers
-                const long long nrow = (tile + 2 * (long long)gridDim.x) * TILE_M + r;
+                const long long nrow = (tile + NS * (long long)gridDim.x) * TILE_M + r;
 #pragma unroll
                 for (int k = 0; k < 16; k++) x[k] = (nrow < n && k < in) ? __ldg(q + nrow * in + k) : 0.f;
             }
@@ -285,7 +294,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     __syncthreads();
     if (warp == NEPI) {
         tc_fence_after();
-        tmem_dealloc(tmem, 2 * SLOT_COLS);
+        tmem_dealloc(tmem, NS * SLOT_COLS);
     }
 }
 
@@ -382,15 +391,16 @@ nb_status nb_split_query(TcModel *tc, const MlpDesc &d, const float *q, int64_t 
     const size_t smem = nb_split_smem_bytes(t.H, t.NH);
     const int64_t tiles = (n + TILE_M - 1) / TILE_M;
     int64_t grid = num_sms();
-    if (grid > (tiles + 1) / 2) grid = (tiles + 1) / 2;
+    const int ns = t.H == 64 ? Single<64>::NS : Single<128>::NS;
+    if (grid > (tiles + ns - 1) / ns) grid = (tiles + ns - 1) / ns;
     if (grid < 1) grid = 1;
     if (t.H == 128) {
         NB_CUDA(cudaFuncSetAttribute(fwd_split_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        fwd_split_kernel<128><<<(unsigned)grid, THREADS, smem, s>>>(t, q, (long long)n, tau, margin, bits, logits,
+        fwd_split_kernel<128><<<(unsigned)grid, Single<128>::THREADS, smem, s>>>(t, q, (long long)n, tau, margin, bits, logits,
                                                                     st, ws.flag_count, ws.flag_idx, tc->err);
     } else {
         NB_CUDA(cudaFuncSetAttribute(fwd_split_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        fwd_split_kernel<64><<<(unsigned)grid, THREADS, smem, s>>>(t, q, (long long)n, tau, margin, bits, logits, st,
+        fwd_split_kernel<64><<<(unsigned)grid, Single<64>::THREADS, smem, s>>>(t, q, (long long)n, tau, margin, bits, logits, st,
                                                                    ws.flag_count, ws.flag_idx, tc->err);
     }
     NB_CUDA(cudaGetLastError());
