@@ -531,26 +531,34 @@ extern "C" nb_status nb_query_host(nb_model *m, const float *host_q, int64_t n, 
         return NB_OK;
     };
     NB_CUDA(cudaStreamSynchronize(S));  // the staging buffers may still serve a query on `stream`
+    // on any failure, let the copies already queued on the caller's host buffers finish
+    // before returning
+    auto drained = [&](nb_status e) {
+        cudaStreamSynchronize(cs);
+        cudaStreamSynchronize(S);
+        return e;
+    };
     st = h2d(0);
-    if (st != NB_OK) return st;
+    if (st != NB_OK) return drained(st);
     for (int64_t i = 0; i < nch; i++) {
         const int b = (int)(i & 1);
-        NB_CUDA(cudaStreamWaitEvent(S, m->hq_ready[b], 0));
+        if (cudaStreamWaitEvent(S, m->hq_ready[b], 0) != cudaSuccess)
+            return drained(nb_fail(NB_ECUDA, "nb_query_host: stream wait failed"));
         st = nb_query(m, m->hq_q[b], rows_of(i), margin, m->hq_bits[b], nullptr, host_stats ? m->hq_stats + b : nullptr,
                       S);
-        if (st != NB_OK) return st;
-        if (host_stats) {
-            add_query_stats_kernel<<<1, 1, 0, S>>>(sum, m->hq_stats + b);
-            NB_CUDA(cudaGetLastError());
-        }
-        NB_CUDA(cudaEventRecord(m->hq_done[b], S));
+        if (st != NB_OK) return drained(st);
+        if (host_stats) add_query_stats_kernel<<<1, 1, 0, S>>>(sum, m->hq_stats + b);
+        if (cudaGetLastError() != cudaSuccess || cudaEventRecord(m->hq_done[b], S) != cudaSuccess)
+            return drained(nb_fail(NB_ECUDA, "nb_query_host: launch failed"));
         if (i + 1 < nch) {
             st = h2d(i + 1);
-            if (st != NB_OK) return st;
+            if (st != NB_OK) return drained(st);
         }
-        NB_CUDA(cudaStreamWaitEvent(cs, m->hq_done[b], 0));
-        NB_CUDA(cudaMemcpyAsync(host_bits + (size_t)start[i] / 32, m->hq_bits[b],
-                                (size_t)((rows_of(i) + 31) / 32) * sizeof(uint32_t), cudaMemcpyDeviceToHost, cs));
+        if (cudaStreamWaitEvent(cs, m->hq_done[b], 0) != cudaSuccess ||
+            cudaMemcpyAsync(host_bits + (size_t)start[i] / 32, m->hq_bits[b],
+                            (size_t)((rows_of(i) + 31) / 32) * sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                            cs) != cudaSuccess)
+            return drained(nb_fail(NB_ECUDA, "nb_query_host: copy failed"));
     }
     NB_CUDA(cudaStreamSynchronize(cs));
     if (host_stats) {
