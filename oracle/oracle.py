@@ -229,3 +229,21 @@ def three_way(z_outer, tau_outer: float, z_inner, tau_inner: float) -> np.ndarra
     codes[out_ & ~in_] = 0
     codes[in_ & ~out_] = 1
     return codes
+
+
+ENC_PAPER_W = (2, 3, 4, 6, 6, 6)
+
+
+def paper_encoding(kind: int, q) -> np.ndarray:
+    """The paper's query parameterisation (Suppl. "Parameterization"), in FP64: rays as start
+    and direction (unchanged), boxes as their two corners (c - e, c + e), planes as a point
+    p0 on the plane and the normal; p0 = off n / |n|^2, the plane's point nearest the origin
+    (n . p0 = off).  Points are unchanged."""
+    q = np.asarray(q, dtype=np.float64)
+    if kind == 5:  # box: centre, half-extents -> min corner, max corner
+        return np.concatenate([q[:, :3] - q[:, 3:], q[:, :3] + q[:, 3:]], axis=1)
+    if kind == 4:  # plane: normal, offset -> p0, normal
+        nrm = q[:, :3]
+        p0 = q[:, 3:4] * nrm / np.sum(nrm * nrm, axis=1, keepdims=True)
+        return np.concatenate([p0, nrm], axis=1)
+    return q.copy()

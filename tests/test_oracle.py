@@ -498,3 +498,26 @@ def test_three_way_respects_labels_on_the_calibration_set():
     # on the calibration set no query is claimed by both networks
     assert not np.any((z_o < tau_o) & (z_i < tau_i))
     assert np.sum(c == 0) > 0 and np.sum(c == 1) > 0 and np.sum(c == 2) > 0
+
+
+# ----------------------------------------------------------------------------- paper encoding
+def test_paper_encoding_box_corners_and_plane_point():
+    box = I.sample_queries("box3", 32, 500)
+    enc = O.paper_encoding(I.BOX3, box)
+    assert enc.shape == (500, 6)
+    # the corners' midpoint is the centre and their half-difference the half-extents
+    np.testing.assert_array_equal((enc[:, :3] + enc[:, 3:]) / 2, box[:, :3].astype(np.float64))
+    np.testing.assert_array_equal((enc[:, 3:] - enc[:, :3]) / 2, box[:, 3:].astype(np.float64))
+    pl = I.sample_queries("plane3", 33, 500)
+    e = O.paper_encoding(I.PLANE3, pl)
+    n, off = pl[:, :3].astype(np.float64), pl[:, 3].astype(np.float64)
+    # p0 lies on the plane n . x = off and is its point nearest the origin (parallel to n)
+    np.testing.assert_allclose(np.sum(n * e[:, :3], axis=1), off, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(np.cross(e[:, :3], n), 0.0, atol=1e-12)
+    np.testing.assert_array_equal(e[:, 3:], n)
+    # a hand case: the plane z = 0.5 with normal (0, 0, 2), offset 1
+    h = O.paper_encoding(I.PLANE3, np.array([[0.0, 0.0, 2.0, 1.0]], dtype=np.float32))
+    assert h.tolist() == [[0.0, 0.0, 0.5, 0.0, 0.0, 2.0]]
+    # rays and points are unchanged
+    r = I.sample_queries("ray3", 34, 10)
+    assert np.array_equal(O.paper_encoding(I.RAY3, r), r.astype(np.float64))
