@@ -164,6 +164,16 @@ nb_status nb_label(const nb_shape *shape, int32_t kind, const float *q, int64_t 
  * unknown kind, qexp outside [8, 20], a negative range or a null q with n > 0. */
 nb_status nb_sample(int32_t kind, int32_t qexp, uint64_t seed, int64_t first, int64_t n, float *q, void *stream);
 
+/* The paper's query parameterisation (Suppl. "Parameterization") from the library's
+ * encodings, for networks trained on the paper's inputs: rays (start, direction) and
+ * points unchanged; boxes (centre c, half-extents e) -> corners (c - e, c + e), exact on
+ * the grid; planes (normal n, offset of n . x = off) -> (p0, n) with p0 = off n / |n|^2,
+ * the plane's point nearest the origin, in correctly rounded FP32 steps.  out holds n rows
+ * of 2, 3, 4, 6, 6, 6 floats (point2, point3, point4t, ray3, plane3, box3); labels are
+ * still computed on the library's encoding.  Device buffers, asynchronous on stream;
+ * EINVAL for an unknown kind, n < 0 or null pointers with n > 0. */
+nb_status nb_encode_paper(int32_t kind, const float *q, int64_t n, float *out, void *stream);
+
 /* One training iteration of Sec. 3.4 on a batch of n queries with labels y:
  * forward, mean asymmetric BCE of Eq. (loss) with weights alpha (on y log yhat) and
  * beta (on (1-y) log(1-yhat)), backward, deterministic gradient reduction and one

@@ -32,7 +32,7 @@ EXPORTS = ["nb_model_create", "nb_model_destroy", "nb_model_param_count", "nb_mo
            "nb_query_grouped", "nb_calibrate_grouped", "nb_cascade_bin", "nb_cascade_exact", "nb_sample", "nb_group_autotune", "nb_query_early_out", "nb_bits_not",
            "nb_query_three_way", "nb_cascade_index_create", "nb_cascade_index_destroy", "nb_cascade_bin_indexed",
            "nb_cascade_index_max_nodes", "nb_cascade_index_build_host", "nb_stepwise_init", "nb_stepwise_window",
-           "nb_query_host", "nb_model_check", "nb_selftest_bounded_wait"]
+           "nb_query_host", "nb_model_check", "nb_selftest_bounded_wait", "nb_encode_paper"]
 
 
 class NBError(RuntimeError):
@@ -122,6 +122,7 @@ def lib():
                 "nb_query_host": ([P, P, i64, ctypes.c_float, P, P, i64, P], st),
                 "nb_model_check": ([P, P], st),
                 "nb_selftest_bounded_wait": ([i32, P], st),
+                "nb_encode_paper": ([i32, P, i64, P, P], st),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -614,6 +615,19 @@ class Stepwise:
         if r < 0:
             raise NBError(1, "nb_stepwise_window: uninitialised schedule")
         return r == 1
+
+
+PAPER_ENC_WIDTH = (2, 3, 4, 6, 6, 6)
+
+
+def encode_paper(kind: int, q: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """The paper's query parameterisation of q (nb_encode_paper): box corners, plane point
+    and normal; rays and points unchanged."""
+    n = q.shape[0]
+    if out is None:
+        out = torch.empty((n, PAPER_ENC_WIDTH[kind]), dtype=torch.float32, device=q.device)
+    _check(lib().nb_encode_paper(int(kind), _ptr(q), n, _ptr(out), _stream(stream)))
+    return out
 
 
 def selftest_bounded_wait(polls: int = 1024, stream=None) -> int:

@@ -75,3 +75,21 @@ def test_fresh_batches_train_like_the_pool(nb):
     _, g = O.loss_grad(widths, p0, qh, y, 3.0, 1.0)
     gg = m.get_grad().astype(np.float64)
     assert np.linalg.norm(gg - g) <= 1e-4 * np.linalg.norm(g)
+
+
+@pytest.mark.parametrize("kind", [0, 1, 2, 3, 4, 5])
+def test_paper_encoding_equals_oracle(nb, kind):
+    """nb_encode_paper against the oracle's FP64 conversion: box corners exact, plane
+    points within a few FP32 roundings, rays and points copied."""
+    from oracle import oracle as O
+    n = 20_001
+    q = nb.sample(kind, n, seed=41)
+    e = nb.encode_paper(kind, q).cpu().numpy().astype(np.float64)
+    ref = O.paper_encoding(kind, q.cpu().numpy())
+    assert e.shape == ref.shape
+    if kind == 4:
+        np.testing.assert_allclose(e, ref, rtol=0, atol=1e-6)  # about 7 FP32 roundings of values <= 1
+        assert np.array_equal(e[:, 3:], ref[:, 3:])
+    else:
+        assert np.array_equal(e, ref)
+    assert nb.encode_paper(kind, q[:0]).shape[0] == 0
