@@ -275,7 +275,8 @@ nb_status nb_bits_not(const uint32_t *in, int64_t n, uint32_t *out, void *stream
  * states the two series with the weights' roles exchanged; this reading makes the
  * false-negative cost grow without bound, as Sec. 3.1 requires.
  * nb_stepwise_window returns 1 when stop_windows (> 0) consecutive windows have had no
- * false negative (training may stop), 0 otherwise, -1 for an uninitialised schedule. */
+ * false negative (training may stop; Sec. 3.4 stops after six), 0 otherwise, -1 for an
+ * uninitialised schedule. */
 typedef struct {
     int32_t period;        /* iterations per window */
     int32_t dim_rate;      /* c in beta = 1 / (c k) */
