@@ -125,6 +125,20 @@ def cpu_oracle_rate(widths, params, q_host, seconds=12.0):
     return n / dt, nthreads, n
 
 
+def cpu_oracle_label_rate(kind, q_host, scene, seconds=4.0):
+    """The oracle's exact labeller on a bounded sample, on the host cores."""
+    from oracle import oracle as O
+    nthreads = os.cpu_count() or 1
+    n = 4096
+    t0 = time.perf_counter()
+    O.label(kind, q_host[:n], scene, nthreads)
+    dt = time.perf_counter() - t0
+    n = int(min(len(q_host), max(4096, n * seconds / max(dt, 1e-6) * 0.5)))
+    t0 = time.perf_counter()
+    O.label(kind, q_host[:n], scene, nthreads)
+    return n / (time.perf_counter() - t0), n
+
+
 def rank_seed(seed: int, rank: int) -> int:
     """Each replica evaluates its own queries: rank r draws the stream seed + 1000 r."""
     return seed + 1000 * rank
@@ -217,6 +231,12 @@ def run_c2(args):
     eval_q_host = I.sample_queries(I.RAY3, rank_seed(SEED_QUERY, ctx.rank), n_eval)
     eval_q = torch.as_tensor(eval_q_host, device=dev)
     eval_bits = nb.label(shape, I.RAY3, eval_q)
+    # the sampler and the exact labeller over the evaluation set on their own (steps a2, a3)
+    label_ms = ctx.time_ms(lambda: nb.label(shape, I.RAY3, eval_q, out=eval_bits), 5)
+    sample_buf = torch.empty_like(eval_q)
+    nb.sample(I.RAY3, n_eval, SEED_TRAIN, out=sample_buf)
+    sample_ms = ctx.time_ms(lambda: nb.sample(I.RAY3, n_eval, SEED_TRAIN, out=sample_buf), 5)
+    del sample_buf
 
     # training on the tensor cores (BF16 operands, FP32 accumulation, FP32 master weights),
     # a fresh batch every iteration as in Alg. 1: sampled and labelled on the GPU
@@ -308,6 +328,7 @@ def run_c2(args):
     achieved = flops / (fwd_ms / 1000.0) / 1e12
     peak = float(pk.get("bf16_tflops", 1900.0))
     cpu_v, cores, cpu_n = cpu_oracle_rate(WIDTHS, params, eval_q_host)
+    cpu_label_v, cpu_label_n = cpu_oracle_label_rate(I.RAY3, eval_q_host, sc)
     line = base_line(ctx, METRIC, value, "queries/s", ms, args.steps, args.warmup,
                      "f16x3 (split fp16 operands, fp32 accumulate)",
                      {"workload": WORKLOAD, "n_eval": n_eval, "batch": BATCH, "train_steps": T, "margin": MARGIN,
@@ -333,6 +354,11 @@ def run_c2(args):
                      "peak_kind": f"{pk_kind} bf16 burst", "fwd_ms": fwd_ms, "algorithmic_flops_per_launch": flops},
         "cpu_baseline": {"value": cpu_v, "unit": "queries/s", "cores": cores, "kind": "oracle",
                          "sample": f"{cpu_n} of the evaluation rays through the FP64 oracle forward"},
+        "label_queries_per_s": n_eval / (label_ms / 1000.0),
+        "label_sphere_predicates_per_s": n_eval * N_SPHERES / (label_ms / 1000.0),
+        "sample_queries_per_s": n_eval / (sample_ms / 1000.0),
+        "cpu_oracle_label_queries_per_s": {"value": cpu_label_v, "cores": cores,
+                                           "sample": f"{cpu_label_n} of the evaluation rays, 64 spheres"},
         "e2e": {"value": ctx.world * n_eval / (e2e_ms / 1000.0), "unit": "queries/s",
                 "h2d_bytes_per_step": n_eval * 6 * 4, "d2h_bytes_per_step": nb.n_words(n_eval) * 4,
                 "call": "nb_query_host (pinned host rays, 4M-ray chunks copied in while the previous chunk runs)",
