@@ -319,8 +319,9 @@ typedef struct nb_group nb_group;
 nb_status nb_plan_create(const int64_t *host_offsets, int32_t n_objects, int32_t chunk_rows, nb_plan **out);
 nb_status nb_plan_destroy(nb_plan *p);
 
-/* widths as for nb_model_create; infer_prec NB_F32 or NB_F16X3; train_prec NB_F32 or
- * NB_BF16 (hidden widths 64 or 128). */
+/* widths as for nb_model_create; infer_prec NB_F32 (any widths) or NB_F16X3 (equal
+ * hidden widths of exactly 64 or 128: the grouped forward has no padded form); train_prec
+ * NB_F32 or NB_BF16 (equal hidden widths of 64 or 128).  EUNSUPPORTED otherwise. */
 nb_status nb_group_create(const int32_t *widths, int32_t n_layers, int32_t n_objects, int32_t infer_prec,
                           int32_t train_prec, nb_group **out);
 nb_status nb_group_destroy(nb_group *g);
