@@ -521,7 +521,7 @@ def run_c2e(args):
     plain_ms = ctx.time_ms(lambda: late.query(eq, margin=MARGIN, out=out), max(3, args.steps // 4))
     dplain = nb.bits_to_numpy(late.query(eq, margin=MARGIN), n)
     # the same two networks as a bound and an inverted bound: the broad-phase three-way
-    # class of Sec. 5 (certainly outside / certainly inside / neither)
+    # class of Sec. 4.4 (certainly outside / certainly inside / neither)
     codes = torch.empty(n, dtype=torch.uint8, device=dev)
     tw_stats = torch.zeros(4, dtype=torch.int64, device=dev)
     nb.query_three_way(late, early, eq, margin_outer=MARGIN, margin_inner=1e-3, out=codes, stats=tw_stats)

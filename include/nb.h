@@ -240,7 +240,7 @@ typedef struct {
 nb_status nb_query_early_out(nb_model *early, nb_model *late, const float *q, int64_t n, float margin_early,
                              float margin_late, uint32_t *out_bits, nb_early_stats *host_stats, void *stream);
 
-/* Inverted bounds and the broad-phase three-way test (Sec. 5): swapping the asymmetry
+/* Inverted bounds and the broad-phase three-way test (Sec. 4.4): swapping the asymmetry
  * weights gives a network that conservatively bounds where the object is certainly hit;
  * that network with its logit negated is a bound of the complement 1 - g, trained with the
  * usual weights on inverted labels (nb_bits_not) and calibrated on them.  `outer` is the

@@ -28,6 +28,11 @@
  *   orc_sample      Alg. 1's per-iteration draw of queries r ~ Uniform, made
  *                   reproducible by the counter-based Philox4x64-10 generator
  *                   (orc_philox4x64 exposes one block for its pin).
+ *   orc_canonical_ray  the cascade's network input: a ray in an object's frame,
+ *                   its origin moved to its entry into the ball around the
+ *                   object (per-object networks, Sec. 2; hierarchy of tests,
+ *                   Sec. 1), replaying the library's defined FP32 sequence;
+ *                   orc_canonical_ray_f64 is the real-valued root it is pinned to.
  *
  * Number formats: every query and sphere value is an integer multiple of
  * 2^-qexp (see inputs.py).  Integer "units" below are multiples of 2^-qexp.
@@ -663,5 +668,81 @@ int orc_sample(int kind, int qexp, uint64_t seed, int64_t first, int64_t n, floa
     if (kind < 0 || kind > 5 || qexp < 8 || qexp > 20 || first < 0 || n < 0) return -1;
     sample_ctx c = {kind, qexp, seed, first, q};
     parallel_for(n, nthreads, sample_range, &c);
+    return 0;
+}
+
+/* ------------------------------------------------ cascade: canonical ray
+ * The learned-culler cascade (Sec. 1's hierarchy of a cheap conservative test in
+ * front of an exact one; per-object networks, Sec. 2) hands each object's network
+ * the ray in that object's frame with its origin moved to where it enters the ball
+ * of radius R around the object's centre -- the distribution of ray origins the
+ * network was trained on.  The paper leaves this frame open; the library defines
+ * the transform as one fixed sequence of correctly rounded FP32 operations, and
+ * this function replays that sequence (each line one IEEE float operation, fmaf
+ * where the sequence fuses, -ffp-contract=off), so its results are the exact bits
+ * the definition prescribes:
+ *   w = o - c;  b = w.d;  dd = d.d;  ww = w.w            (sums left to right)
+ *   x = w cross d, each component fmaf(w_i, d_j, -(w_j d_i))
+ *   disc = dd R^2 - |x|^2     (Lagrange: equals b^2 - dd (ww - R^2))
+ *   met  = disc >= 0 and dd > 0
+ *   s = (ww - R^2) / (-b + sqrt(disc))   if -b > 0  (the smaller root, no cancellation)
+ *     = (-b - sqrt(disc)) / dd            otherwise
+ *   s = max(s, 0);  entry = w + s d
+ * R2 is R^2 as a float (the caller squares R in FP32).  Output q6 = (entry, d) and
+ * met (0: the ray misses the ball; q6 is then zero).
+ * orc_canonical_ray_f64 computes the same entry point in FP64 from the same float
+ * inputs; it exists only to pin the FP32 sequence against the real-valued root. */
+static void canon_f32(const float o[3], const float d[3], const float c[3], float R2, float q6[6], uint8_t *met) {
+    float w[3];
+    for (int i = 0; i < 3; i++) w[i] = o[i] - c[i];
+    const float b = ((w[0] * d[0]) + (w[1] * d[1])) + (w[2] * d[2]);
+    const float dd = ((d[0] * d[0]) + (d[1] * d[1])) + (d[2] * d[2]);
+    const float ww = ((w[0] * w[0]) + (w[1] * w[1])) + (w[2] * w[2]);
+    const float cx = fmaf(w[1], d[2], -(w[2] * d[1]));
+    const float cy = fmaf(w[2], d[0], -(w[0] * d[2]));
+    const float cz = fmaf(w[0], d[1], -(w[1] * d[0]));
+    const float cr2 = ((cx * cx) + (cy * cy)) + (cz * cz);
+    const float disc = (dd * R2) - cr2;
+    for (int i = 0; i < 6; i++) q6[i] = 0.f;
+    *met = (disc >= 0.f && dd > 0.f) ? 1 : 0;
+    if (!*met) return;
+    const float sq = sqrtf(disc);
+    const float cc = ww - R2;
+    float s = (-b > 0.f) ? cc / ((-b) + sq) : ((-b) - sq) / dd;
+    s = fmaxf(s, 0.f);
+    for (int i = 0; i < 3; i++) {
+        q6[i] = w[i] + (s * d[i]);
+        q6[3 + i] = d[i];
+    }
+}
+
+int orc_canonical_ray(const float *rays, const float *centres, int64_t n, float R2, float *q6, uint8_t *met) {
+    if (n < 0 || !(R2 >= 0.f)) return -1;
+    for (int64_t i = 0; i < n; i++) canon_f32(rays + 6 * i, rays + 6 * i + 3, centres + 3 * i, R2, q6 + 6 * i, met + i);
+    return 0;
+}
+
+/* the same entry point in FP64 (smaller root of |w + s d|^2 = R^2, clamped at s = 0) */
+int orc_canonical_ray_f64(const float *rays, const float *centres, int64_t n, double R, double *p3, uint8_t *met) {
+    if (n < 0 || !(R >= 0.0)) return -1;
+    for (int64_t i = 0; i < n; i++) {
+        double w[3], d[3], b = 0, dd = 0, ww = 0;
+        for (int k = 0; k < 3; k++) {
+            w[k] = (double)rays[6 * i + k] - (double)centres[3 * i + k];
+            d[k] = (double)rays[6 * i + 3 + k];
+            b += w[k] * d[k];
+            dd += d[k] * d[k];
+            ww += w[k] * w[k];
+        }
+        const double x0 = w[1] * d[2] - w[2] * d[1], x1 = w[2] * d[0] - w[0] * d[2], x2 = w[0] * d[1] - w[1] * d[0];
+        const double disc = dd * R * R - (x0 * x0 + x1 * x1 + x2 * x2);
+        met[i] = (disc >= 0.0 && dd > 0.0) ? 1 : 0;
+        double s = 0.0;
+        if (met[i]) {
+            s = (-b - sqrt(disc)) / dd;
+            if (s < 0.0) s = 0.0;
+        }
+        for (int k = 0; k < 3; k++) p3[3 * i + k] = met[i] ? w[k] + s * d[k] : 0.0;
+    }
     return 0;
 }

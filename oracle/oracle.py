@@ -68,6 +68,10 @@ def lib():
             L.orc_philox4x64.restype = None
             L.orc_sample.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint64, i64, i64, P, ctypes.c_int]
             L.orc_sample.restype = ctypes.c_int
+            L.orc_canonical_ray.argtypes = [P, P, i64, ctypes.c_float, P, P]
+            L.orc_canonical_ray.restype = ctypes.c_int
+            L.orc_canonical_ray_f64.argtypes = [P, P, i64, ctypes.c_double, P, P]
+            L.orc_canonical_ray_f64.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -201,7 +205,7 @@ def sample(kind: int, n: int, seed: int, first: int = 0, qexp: int = 20,
 
 
 def benefit_break_even(t_a: float, t_b: float, p_a: float, p_b: float):
-    """Eq. (Benefit), Sec. 4.3 "Tightness": with bounding method A (query time t_a,
+    """Eq. (Benefit), Sec. 5 (Discussion, "Tightness"): with bounding method A (query time t_a,
     fraction p_a of queries passed to the exact test) against method B (t_b, p_b),
     the total time of N queries is N t_i + p_i N t for an exact test of cost t, so A
     wins iff t_a + p_a t < t_b + p_b t.  Returns (t*, side): A wins for t > t* when
@@ -214,7 +218,7 @@ def benefit_break_even(t_a: float, t_b: float, p_a: float, p_b: float):
 
 
 def three_way(z_outer, tau_outer: float, z_inner, tau_inner: float) -> np.ndarray:
-    """Broad-phase class of each query from a bound and an inverted bound (Sec. 5, the
+    """Broad-phase class of each query from a bound and an inverted bound (Sec. 4.4, the
     variant with the asymmetry weights swapped): the outer network bounds g, so
     z_outer < tau_outer means certainly outside; the inner network bounds the complement
     1 - g (the swapped-weight network with its logit negated), so z_inner < tau_inner
@@ -247,3 +251,33 @@ def paper_encoding(kind: int, q) -> np.ndarray:
         p0 = q[:, 3:4] * nrm / np.sum(nrm * nrm, axis=1, keepdims=True)
         return np.concatenate([p0, nrm], axis=1)
     return q.copy()
+
+
+def canonical_ray(rays, centres, R: float = 2.0):
+    """The cascade's network input for (ray, object) pairs: the ray in the object's frame
+    with its origin moved to its entry point into the ball of radius R around the object's
+    centre, by the library's defined FP32 operation sequence (oracle.c, orc_canonical_ray).
+    rays [n][6] (origin, direction), centres [n][3] (the object of each pair).  Returns
+    (q6 float32 [n][6], met bool [n]); rows that miss the ball are zero."""
+    rays = np.ascontiguousarray(rays, dtype=np.float32)
+    centres = np.ascontiguousarray(centres, dtype=np.float32)
+    n = rays.shape[0]
+    q6 = np.zeros((n, 6), dtype=np.float32)
+    met = np.zeros(n, dtype=np.uint8)
+    R2 = np.float32(np.float32(R) * np.float32(R))
+    if lib().orc_canonical_ray(_ptr(rays), _ptr(centres), n, float(R2), _ptr(q6), _ptr(met)) != 0:
+        raise ValueError("oracle canonical_ray: bad arguments")
+    return q6, met.astype(bool)
+
+
+def canonical_ray_f64(rays, centres, R: float = 2.0):
+    """The same entry point in FP64 (smaller root of |w + s d| = R, clamped at s = 0); the
+    real-valued counterpart the FP32 sequence is pinned against.  Returns (p [n][3], met)."""
+    rays = np.ascontiguousarray(rays, dtype=np.float32)
+    centres = np.ascontiguousarray(centres, dtype=np.float32)
+    n = rays.shape[0]
+    p = np.zeros((n, 3), dtype=np.float64)
+    met = np.zeros(n, dtype=np.uint8)
+    if lib().orc_canonical_ray_f64(_ptr(rays), _ptr(centres), n, float(R), _ptr(p), _ptr(met)) != 0:
+        raise ValueError("oracle canonical_ray_f64: bad arguments")
+    return p, met.astype(bool)

@@ -4,5 +4,4 @@ Submodules:
   inputs  seeded synthetic scenes, queries and initial weights (no method arithmetic)
   nb      ctypes binding of libnb (include/nb.h); the compute runs in libnb's CUDA kernels
   build   in-tree nvcc build of libnb.so
-  report  benefit arithmetic of the paper's discussion section
 """

@@ -98,7 +98,7 @@ nb_status nb_launch_bits_not(const uint32_t *in, int64_t n, uint32_t *out, cudaS
     return NB_OK;
 }
 
-// Broad-phase three-way class (Sec. 5, inverted bounds): decision 0 of the outer bound is
+// Broad-phase three-way class (Sec. 4.4, inverted bounds): decision 0 of the outer bound is
 // "certainly outside", decision 0 of the complement bound "certainly inside"; neither, or
 // both (a conflict), leaves the query to the exact test.  One thread per query, one byte
 // out; counts reduced per warp.

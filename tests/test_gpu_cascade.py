@@ -66,6 +66,35 @@ def test_canonical_binning_keeps_every_hitting_pair(nb):
     assert np.all(np.abs(r - 2.0) < 1e-4)
 
 
+def _object_of_rows(off):
+    k = np.zeros(int(off[-1]), dtype=np.int64)
+    for j in range(len(off) - 1):
+        k[off[j]:off[j + 1]] = j
+    return k
+
+
+@pytest.mark.parametrize("K,indexed", [(24, False), (24, True), (300, True)])
+def test_canonical_rays_equal_the_oracle_bit_for_bit(nb, K, indexed):
+    """Every binned pair's network input (the ray in the object's frame, origin moved to
+    its entry into the radius-2 ball) equals the oracle's replay of the defined FP32
+    sequence bit for bit, and the oracle says the ray meets the ball."""
+    ms = I.make_multi_scene(61 + K, K, 32)
+    rays = I.sample_world_rays(62 + K, 40_003)
+    ws = nb.WorldScene(ms)
+    ix = nb.CascadeIndex(ws) if indexed else None
+    off, _, pair_ray, pair_q, st = nb.cascade_bin(ws, _dev(rays), canonical=True, index=ix)
+    pr = pair_ray.cpu().numpy()[:int(off[-1])]
+    q = pair_q.cpu().numpy()[:int(off[-1])]
+    live = pr != -1
+    assert live.sum() == st["ball_pairs"] > 0
+    k = _object_of_rows(off)[live]
+    want, met = O.canonical_ray(rays[pr[live]], ms.obj_centre[k], float(ms.ball_radius))
+    assert np.all(met)
+    assert np.array_equal(q[live].view(np.uint32), want.view(np.uint32))
+    if ix is not None:
+        ix.close()
+
+
 def test_cascade_end_to_end_equals_plain_and_avoids_exact_tests(nb):
     """16 objects, one trained 6->128x3->1 ray network each (split-FP16 queries), the
     thresholds calibrated on the cascade's own pairs: the cascade finds exactly the hits

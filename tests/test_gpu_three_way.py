@@ -1,4 +1,4 @@
-"""Inverted bounds and the broad-phase three-way test (Sec. 5): a bounding network of g
+"""Inverted bounds and the broad-phase three-way test (Sec. 4.4): a bounding network of g
 and one of the complement 1 - g (the swapped-weight network with its logit negated),
 each certified against its own threshold, classify every query as certainly outside,
 certainly inside or neither.  Codes against the oracle's two networks and thresholds,

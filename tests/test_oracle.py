@@ -441,7 +441,7 @@ def test_benefit_break_even_worked_example():
 
 # ----------------------------------------------------------------------------- inverted bounds
 def test_swapped_weights_equal_the_complement_with_negated_logit():
-    # Sec. 5: the inverted bound swaps the asymmetry weights.  Training on g with
+    # Sec. 4.4: the inverted bound swaps the asymmetry weights.  Training on g with
     # (alpha, beta) swapped is training on 1 - g with the logit negated: the loss is the
     # same number and the gradient differs only in the sign of the head's entries.
     w = [3, 16, 16, 1]
