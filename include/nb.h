@@ -471,8 +471,11 @@ nb_status nb_cascade_exact(const nb_scene *scene, const float *rays, const uint3
  *   - Networks with more than NB_NOALLOC_SCRATCH_FLOATS - 1 parameters are
  *     rejected with NB_EINVAL.
  *   - The first call on a device looks up the array's device address for the
- *     current device (cudaGetSymbolAddress); make that first call before any
- *     stream capture.
+ *     current device (cudaGetSymbolAddress) and keeps it for the life of the
+ *     process; make that first call before any stream capture.  The kept address
+ *     belongs to the device's context at that time: after the application resets
+ *     the device (cudaDeviceReset) it is stale, so do not call this entry point
+ *     on that device again in the same process.
  *   - All calls share the one array (it keeps the last call's contents; the call
  *     clears what must start at zero), so calls whose work overlaps on the GPU --
  *     on different streams or different threads -- race and must be serialised

@@ -465,16 +465,17 @@ __global__ void add_query_stats_kernel(nb_query_stats *sum, const nb_query_stats
 
 static nb_status ensure_host_pipe(nb_model *m, int64_t chunk) {
     const int w = m->widths[0];
-    if (!m->hq_stream) {
-        NB_CUDA(cudaStreamCreateWithFlags(&m->hq_stream, cudaStreamNonBlocking));
-        for (int b = 0; b < 2; b++) {
-            NB_CUDA(cudaEventCreateWithFlags(&m->hq_ready[b], cudaEventDisableTiming));
-            NB_CUDA(cudaEventCreateWithFlags(&m->hq_done[b], cudaEventDisableTiming));
-        }
-        if (cudaMalloc(&m->hq_stats, 3 * sizeof(nb_query_stats)) != cudaSuccess) {
-            cudaGetLastError();
-            return nb_fail(NB_ENOMEM, "nb_query_host: allocation failed");
-        }
+    // each piece is checked on its own, so a call after a failed set-up completes it
+    // instead of using a part that does not exist
+    if (!m->hq_stream) NB_CUDA(cudaStreamCreateWithFlags(&m->hq_stream, cudaStreamNonBlocking));
+    for (int b = 0; b < 2; b++) {
+        if (!m->hq_ready[b]) NB_CUDA(cudaEventCreateWithFlags(&m->hq_ready[b], cudaEventDisableTiming));
+        if (!m->hq_done[b]) NB_CUDA(cudaEventCreateWithFlags(&m->hq_done[b], cudaEventDisableTiming));
+    }
+    if (!m->hq_stats && cudaMalloc(&m->hq_stats, 3 * sizeof(nb_query_stats)) != cudaSuccess) {
+        cudaGetLastError();
+        m->hq_stats = nullptr;
+        return nb_fail(NB_ENOMEM, "nb_query_host: allocation failed");
     }
     if (chunk <= m->hq_chunk) return NB_OK;
     NB_CUDA(cudaDeviceSynchronize());
