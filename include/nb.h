@@ -179,8 +179,9 @@ nb_status nb_encode_paper(int32_t kind, const float *q, int64_t n, float *out, v
  * forward, mean asymmetric BCE of Eq. (loss) with weights alpha (on y log yhat) and
  * beta (on (1-y) log(1-yhat)), backward, deterministic gradient reduction and one
  * Adam step on the FP32 master weights; the low-precision copies are refreshed.
- * A sample whose logit is not finite adds nothing to the loss or the gradient (the mean
- * still divides by n) and is counted in dev_stats->n_nonfinite.
+ * A sample whose logit is not finite -- a non-finite input coordinate counts as such --
+ * adds nothing to the loss or the gradient (the mean still divides by n) and is counted in
+ * dev_stats->n_nonfinite.
  * dev_stats may be NULL.  n >= 1. */
 nb_status nb_train_step(nb_model *m, const float *q, const uint32_t *label_bits, int64_t n, float alpha,
                         float beta, nb_step_stats *dev_stats, void *stream);

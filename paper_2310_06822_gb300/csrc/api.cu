@@ -398,17 +398,18 @@ extern "C" nb_status nb_train_step(nb_model *m, const float *q, const uint32_t *
     m->step += 1;
     const double c1 = 1.0 - pow((double)m->b1, (double)m->step);
     const double c2 = 1.0 - pow((double)m->b2, (double)m->step);
-    const bool bf16 = m->train_prec == NB_BF16;
+    const bool bf16 = m->train_prec == NB_BF16, tcgen = bf16 && m->tc.train_tc;
     TrainWs tw{};
-    tw.G = bf16 ? nb_train_bf16_ctas(n) : nb_train_f32_ctas(d, n, sm_count());
+    tw.G = tcgen ? nb_train_tc_ctas(n) : bf16 ? nb_train_bf16_ctas(n) : nb_train_f32_ctas(d, n, sm_count());
     tw.stride = bf16 ? (m->P + 3) / 4 * 4 : m->P;  // BF16: 16-byte aligned slots for vector reductions
     const size_t need = align256((size_t)tw.G * tw.stride * sizeof(float)) + align256((size_t)tw.G * sizeof(float));
     nb_status st = ensure_ws(m, need);
     if (st != NB_OK) return st;
     tw.partial = (float *)m->ws;
     tw.loss_partial = (float *)((char *)m->ws + align256((size_t)tw.G * tw.stride * sizeof(float)));
-    st = bf16 ? nb_launch_train_bf16(&m->tc, d, q, label_bits, n, alpha, beta, tau, tw, dev_stats, s)
-              : nb_launch_train_f32(d, q, label_bits, n, alpha, beta, tau, tw, dev_stats, s);
+    st = tcgen  ? nb_launch_train_tc(&m->tc, d, q, label_bits, n, alpha, beta, tau, tw, dev_stats, s)
+         : bf16 ? nb_launch_train_bf16(&m->tc, d, q, label_bits, n, alpha, beta, tau, tw, dev_stats, s)
+                : nb_launch_train_f32(d, q, label_bits, n, alpha, beta, tau, tw, dev_stats, s);
     if (st != NB_OK) return st;
     st = nb_launch_adam(m->P, 1.0f / (float)n, m->params, m->adam_m, m->adam_v, m->grad, tw, m->lr, m->b1, m->b2,
                         m->eps, (float)c1, (float)sqrt(c2), dev_stats, s);

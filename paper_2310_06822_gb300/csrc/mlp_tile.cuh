@@ -185,7 +185,9 @@ __device__ __forceinline__ void train_tile(const MlpDesc &d, const float *__rest
             const long long i = base + m;
             const float y = (float)((labels[i >> 5] >> (i & 31)) & 1u);
             const float z = zs[m];
-            if (isfinite(z)) {
+            bool xfin = true;  // a non-finite input coordinate counts as a non-finite logit
+            for (int k = 0; k < w0; k++) xfin = xfin && isfinite(acts[m * KP + k]);
+            if (isfinite(z) && xfin) {
                 // Eq. (loss): -alpha y log(s) - beta (1-y) log(1-s), s = sigmoid(z)
                 lv = alpha * y * softplusf(-z) + beta * (1.f - y) * softplusf(z);
                 const float sg = sigmoidf(z);
@@ -195,6 +197,10 @@ __device__ __forceinline__ void train_tile(const MlpDesc &d, const float *__rest
                 c_fp += (y == 0.f && dec);
             } else {
                 c_nf++;
+                // the skipped sample must not meet its zero gradient with an inf or NaN
+                // activation in the weight products
+                for (int l = 0; l < L; l++)
+                    for (int k = 0; k < KP; k++) acts[(size_t)l * TM * KP + m * KP + k] = 0.f;
             }
         }
         dz[m] = g;

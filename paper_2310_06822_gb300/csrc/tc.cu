@@ -410,6 +410,7 @@ nb_status nb_tc_init(TcModel *tc, const MlpDesc &d, int infer_prec, int train_pr
     if (train_prec == NB_BF16) {
         const nb_status st = nb_train_bf16_check(d);
         if (st != NB_OK) return st;
+        tc->train_tc = nb_train_tc_supported(d) ? 1 : 0;  // same image size in either layout
         tc->train_img_bytes = nb_train_bf16_img_bytes(d);
         if (cudaMalloc(&tc->train_img, tc->train_img_bytes) != cudaSuccess) {
             cudaGetLastError();
@@ -435,7 +436,7 @@ void nb_tc_free(TcModel *tc) {
 
 nb_status nb_tc_refresh(TcModel *tc, const MlpDesc &d, cudaStream_t s) {
     if (tc->train_img) {
-        const nb_status st = nb_train_bf16_refresh(tc, d, s);
+        const nb_status st = tc->train_tc ? nb_train_tc_refresh(tc, d, s) : nb_train_bf16_refresh(tc, d, s);
         if (st != NB_OK) return st;
     }
     if (!tc->img) return NB_OK;

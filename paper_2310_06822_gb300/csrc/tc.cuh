@@ -12,6 +12,7 @@ struct TcModel {
     void *train_img = nullptr;   // device: BF16 weights for the tensor-core training step
     size_t train_img_bytes = 0;
     int *err = nullptr;      // device: status of the last bounded wait that gave up (0 = none)
+    int train_tc = 0;        // BF16 training runs the tcgen05 step (train_tc.cu) on a training image in its layout
     // Hidden widths below the kernels' 64 / 128 (the paper's 25-, 50- and 75-wide networks):
     // the forward runs on a copy of the parameters zero-padded to that width.  Padded
     // neurons have zero weights and bias, so they stay 0 through the ReLU and add exact
@@ -50,3 +51,9 @@ nb_status nb_train_bf16_refresh(TcModel *tc, const MlpDesc &d, cudaStream_t s);
 int nb_train_bf16_ctas(int64_t n);
 nb_status nb_launch_train_bf16(TcModel *tc, const MlpDesc &d, const float *q, const uint32_t *labels, int64_t n,
                                float alpha, float beta, TauF tau, TrainWs ws, nb_step_stats *st, cudaStream_t s);
+// tcgen05 BF16 training step of 128-wide networks with 2..4 hidden layers (train_tc.cu)
+bool nb_train_tc_supported(const MlpDesc &d);
+int nb_train_tc_ctas(int64_t n);
+nb_status nb_train_tc_refresh(TcModel *tc, const MlpDesc &d, cudaStream_t s);
+nb_status nb_launch_train_tc(TcModel *tc, const MlpDesc &d, const float *q, const uint32_t *labels, int64_t n,
+                             float alpha, float beta, TauF tau, TrainWs ws, nb_step_stats *st, cudaStream_t s);

@@ -185,3 +185,58 @@ __device__ __forceinline__ uint32_t pack_e4m3x4(float e0, float e1, float e2, fl
 }
 
 }  // namespace nbtc
+
+namespace nbtc {
+
+// General shared-memory matrix descriptor (tcgen05): start address, leading and stride
+// byte offsets (16-byte units) and layout (0: no swizzle, core matrices of 8 rows x 16 B;
+// 2: 128-byte swizzle).  Meaning of the offsets (canonical layouts of the PTX ISA):
+//   K-major, 128-byte swizzle:  SBO = distance between 8-row groups (LBO unused);
+//   MN-major, 128-byte swizzle: LBO = distance between 64-element blocks along M/N,
+//                               SBO = distance between 8-row groups along K;
+//   K-major, no swizzle:        LBO = distance between core matrices along K,
+//                               SBO = distance between 8-row groups along M/N;
+//   MN-major, no swizzle:       LBO = distance between 8-row groups along K,
+//                               SBO = distance between core matrices along M/N.
+__device__ __forceinline__ uint64_t sdesc_gen(uint32_t saddr, uint32_t lbo, uint32_t sbo, uint32_t layout) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)layout << 61;
+    return d;
+}
+
+// Instruction descriptor, kind::f16, D = F32, A = B = BF16; a_mn / b_mn select the
+// MN-major (transposed) form of each operand.
+__host__ __device__ constexpr uint32_t idesc_bf16_mn(int M, int N, int a_mn, int b_mn) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16) |
+           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// 8 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr)
+                 : "memory");
+#pragma unroll
+    for (int i = 0; i < 8; i++) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint4 ld_shared_v4(uint32_t addr) {
+    uint4 v;
+    asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(addr)
+                 : "memory");
+    return v;
+}
+
+// the two FP32 values of a packed BF16x2 word (lo = low half)
+__device__ __forceinline__ void unpack_bf16(uint32_t w, float &lo, float &hi) {
+    lo = __uint_as_float(w << 16);
+    hi = __uint_as_float(w & 0xffff0000u);
+}
+
+}  // namespace nbtc

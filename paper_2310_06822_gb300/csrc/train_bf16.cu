@@ -74,6 +74,12 @@ __device__ __forceinline__ void red_add4(float *p, float v0, float v1, float v2,
     asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v0), "f"(v1), "f"(v2), "f"(v3)
                  : "memory");
 }
+// every input coordinate of a sample is finite (BF16 keeps inf and NaN)
+__device__ __forceinline__ bool row_finite(const __nv_bfloat16 *x, int in) {
+    bool ok = true;
+    for (int k = 0; k < in; k++) ok = ok && ((__bfloat16_as_ushort(x[k]) & 0x7f80u) != 0x7f80u);
+    return ok;
+}
 __device__ __forceinline__ float softplusf(float u) { return u > 0.f ? u + log1pf(expf(-u)) : log1pf(expf(u)); }
 __device__ __forceinline__ float sigmoidf(float u) {
     return u >= 0.f ? 1.f / (1.f + expf(-u)) : expf(u) / (1.f + expf(u));
@@ -280,7 +286,7 @@ __device__ __forceinline__ void bf_tile(const TrainDesc &d, const float *__restr
             const long long i = base + t;
             const float y = (float)((labels[i >> 5] >> (i & 31)) & 1u);
             const float z = zs[t];
-            if (isfinite(z)) {
+            if (isfinite(z) && row_finite(act + t * XP, d.in)) {
                 lv = alpha * y * softplusf(-z) + beta * (1.f - y) * softplusf(z);
                 const float sg = sigmoidf(z);
                 g = (alpha * y * (sg - 1.f) + beta * (1.f - y) * sg) * inv_n;
@@ -293,6 +299,12 @@ __device__ __forceinline__ void bf_tile(const TrainDesc &d, const float *__restr
         }
         gs[t] = g;
         ls[t] = lv;
+        // a skipped sample must not meet its zero gradient with an inf or NaN activation
+        if (t < rows && g == 0.f && !(isfinite(zs[t]) && row_finite(act + t * XP, d.in))) {
+            for (int k = 0; k < K0; k++) act[t * XP + k] = __float2bfloat16_rn(0.f);
+            for (int l = 1; l <= NH; l++)
+                for (int k = 0; k < H; k++) A_l(l)[t * HP + k] = __float2bfloat16_rn(0.f);
+        }
     }
     __syncthreads();
     if (t == 0)
@@ -673,7 +685,7 @@ __global__ void __launch_bounds__(256, 1)
                 const long long i = base + t;
                 const float y = (float)((labels[i >> 5] >> (i & 31)) & 1u);
                 const float z = sm.zs[t];
-                if (isfinite(z)) {
+                if (isfinite(z) && row_finite(sm.x + t * XPW, d.in)) {
                     lv = alpha * y * softplusf(-z) + beta * (1.f - y) * softplusf(z);
                     const float sg = sigmoidf(z);
                     g = (alpha * y * (sg - 1.f) + beta * (1.f - y) * sg) * inv_n;
@@ -686,6 +698,11 @@ __global__ void __launch_bounds__(256, 1)
             }
             sm.gs[t] = g;
             sm.ls[t] = lv;
+            if (t < rows && !(isfinite(sm.zs[t]) && row_finite(sm.x + t * XPW, d.in))) {
+                for (int k = 0; k < K0; k++) sm.x[t * XPW + k] = __float2bfloat16_rn(0.f);
+                for (int l = 1; l <= NH; l++)
+                    for (int k = 0; k < HW; k++) wide_A(sm, l)[t * HPW + k] = __float2bfloat16_rn(0.f);
+            }
         }
         __syncthreads();
         if (t == 0)

@@ -33,7 +33,10 @@ def _per_tensor(widths):
 
 
 @pytest.mark.parametrize("kind,widths,n", [("ray3", [6, 128, 128, 128, 128, 1], 65536),
+                                           ("ray3", [6, 128, 128, 128, 128, 1], 200_003),
                                            ("ray3", [6, 128, 128, 128, 1], 4133),
+                                           ("point3", [3, 128, 128, 1], 128 * 152 * 3 + 77),
+                                           ("box3", [6, 128, 128, 128, 1], 1_000_001),
                                            ("point4t", [4, 64, 64, 64, 1], 777),
                                            ("point4t", [4, 64, 64, 64, 1], 200_003),
                                            ("point3", [3, 128, 128, 1], 1),
@@ -98,3 +101,43 @@ def test_bf16_training_run_is_conservative_after_calibration(nb):
     assert not np.any(y & ~dec)
     assert np.mean(dec & ~y) < 0.9 * np.mean(~y)
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("widths,prec", [([6, 128, 128, 128, 128, 1], "bf16"), ([6, 128, 128, 128, 1], "bf16"),
+                                         ([6, 128, 128, 1], "bf16"), ([6, 64, 64, 64, 1], "bf16"),
+                                         ([6, 256, 256, 1], "bf16"), ([6, 32, 32, 1], "f32")])
+def test_bf16_step_skips_nonfinite_rows_and_is_deterministic(nb, widths, prec):
+    """Rows with a NaN or infinite coordinate give a non-finite logit: they add nothing to
+    the loss or the gradient (the mean still divides by n) and are counted; the step on the
+    other rows matches the oracle on those rows; two identical steps give identical bits."""
+    n = 50_000
+    sc = I.make_scene(63, 32, 3, 0.05, 0.3)
+    q = I.sample_queries("ray3", 64, n)
+    y = O.label(I.RAY3, q, sc)
+    bad = np.zeros(n, dtype=bool)
+    bad[np.random.default_rng(65).choice(n, 37, replace=False)] = True
+    qb = q.copy()
+    idx = np.nonzero(bad)[0]
+    qb[idx[::2], 0] = np.nan
+    qb[idx[1::2], 4] = np.inf
+    p = I.init_params(66, widths)
+    grads = []
+    for rep in range(2):
+        m = nb.Model(widths, infer_prec="f32", train_prec=prec)
+        m.set_params(p)
+        st = nb.step_stats_tensor()
+        m.train_step(_dev(qb), _dev(I.pack_bits(y).view(np.int32)), 20.0, 1.0, stats=st)
+        s = nb.read_step_stats(st)
+        assert s["n_nonfinite"] == bad.sum()
+        grads.append(m.get_grad())
+        assert np.all(np.isfinite(grads[-1]))
+    assert np.array_equal(grads[0].view(np.uint32), grads[1].view(np.uint32))
+    good = ~bad
+    loss64, g64 = O.loss_grad(widths, p, q[good], y[good], 20.0, 1.0)
+    g64 *= good.sum() / n
+    g = grads[0].astype(np.float64)
+    for a, b in _per_tensor(widths):
+        if np.linalg.norm(g64[a:b]) == 0:
+            continue
+        cos = float(np.dot(g[a:b], g64[a:b]) / (np.linalg.norm(g[a:b]) * np.linalg.norm(g64[a:b])))
+        assert cos >= (0.999 if prec == "bf16" else 1 - 1e-8), (a, b, cos)
