@@ -74,24 +74,42 @@ __global__ void __launch_bounds__(256) train_f32_kernel(MlpDesc d, const float *
     }
 }
 
-// Sum the per-CTA partials in CTA order (deterministic), keep the gradient, take one
+// Sum the per-CTA partials (deterministic: every parameter's G partials are summed as eight
+// strided slices, c = s, s + 8, ..., added in a fixed tree), keep the gradient, take one
 // Adam step (Kingma & Ba, in PyTorch's arithmetic order: denom = sqrt(v)/sqrt(c2) + eps,
-// theta -= (lr / c1) m / denom).
-__global__ void __launch_bounds__(256) adam_kernel(long long P, int G, long long stride, const float *__restrict__ partial,
-                                                   const float *__restrict__ loss_partial, float inv_n,
-                                                   float *__restrict__ params, float *__restrict__ m,
-                                                   float *__restrict__ v, float *__restrict__ grad, float lr,
-                                                   float b1, float b2, float eps, float c1, float sqrt_c2,
-                                                   nb_step_stats *st) {
-    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p == 0 && st) {
+// theta -= (lr / c1) m / denom).  A block serves 32 parameters with 8 slices each, so every
+// thread has several independent loads in flight.
+constexpr int ADAM_P = 32, ADAM_S = 8;
+__global__ void __launch_bounds__(ADAM_P * ADAM_S) adam_kernel(long long P, int G, long long stride,
+                                                               const float *__restrict__ partial,
+                                                               const float *__restrict__ loss_partial, float inv_n,
+                                                               float *__restrict__ params, float *__restrict__ m,
+                                                               float *__restrict__ v, float *__restrict__ grad,
+                                                               float lr, float b1, float b2, float eps, float c1,
+                                                               float sqrt_c2, nb_step_stats *st) {
+    __shared__ float part[ADAM_S][ADAM_P + 1];
+    const int pc = threadIdx.x % ADAM_P, sl = threadIdx.x / ADAM_P;
+    if (blockIdx.x == 0 && st) {  // the loss: same slicing over the CTAs' loss partials
         float s = 0.f;
-        for (int c = 0; c < G; c++) s += loss_partial[c];
-        st->loss = s * inv_n;
+        for (int c = threadIdx.x; c < G; c += ADAM_P * ADAM_S) s += loss_partial[c];
+        __shared__ float ls[ADAM_P * ADAM_S];
+        ls[threadIdx.x] = s;
+        __syncthreads();
+        for (int w = ADAM_P * ADAM_S / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w) ls[threadIdx.x] += ls[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) st->loss = ls[0] * inv_n;
     }
-    if (p >= P) return;
+    const long long p = (long long)blockIdx.x * ADAM_P + pc;
     float g = 0.f;
-    for (int c = 0; c < G; c++) g += partial[(size_t)c * stride + p];
+    if (p < P)
+        for (int c = sl; c < G; c += ADAM_S) g += partial[(size_t)c * stride + p];
+    part[sl][pc] = g;
+    __syncthreads();
+    if (sl != 0 || p >= P) return;
+    g = ((part[0][pc] + part[1][pc]) + (part[2][pc] + part[3][pc])) +
+        ((part[4][pc] + part[5][pc]) + (part[6][pc] + part[7][pc]));
     grad[p] = g;
     const float mm = b1 * m[p] + (1.f - b1) * g;
     const float vv = b2 * v[p] + (1.f - b2) * g * g;
@@ -188,8 +206,8 @@ nb_status nb_launch_train_f32(const MlpDesc &d, const float *q, const uint32_t *
 nb_status nb_launch_adam(int64_t P, float inv_n, float *params, float *m, float *v, float *grad, TrainWs ws,
                          float lr, float b1, float b2, float eps, float c1, float sqrt_c2, nb_step_stats *st,
                          cudaStream_t s) {
-    const int64_t blocks = (P + 255) / 256;
-    adam_kernel<<<(unsigned)blocks, 256, 0, s>>>((long long)P, ws.G, ws.stride > 0 ? ws.stride : (long long)P,
+    const int64_t blocks = (P + ADAM_P - 1) / ADAM_P;
+    adam_kernel<<<(unsigned)blocks, ADAM_P * ADAM_S, 0, s>>>((long long)P, ws.G, ws.stride > 0 ? ws.stride : (long long)P,
                                                  ws.partial, ws.loss_partial, inv_n, params, m, v, grad, lr, b1, b2,
                                                  eps, c1, sqrt_c2, st);
     NB_CUDA(cudaGetLastError());

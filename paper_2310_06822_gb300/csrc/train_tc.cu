@@ -12,11 +12,13 @@
 // and read in whichever orientation a product needs.  dW_l of the hidden-to-hidden layers
 // accumulates in tensor memory over all of the CTA's tiles (128 columns each) and is read
 // out once at the end; the 128 remaining columns hold the current tile's forward sums or
-// input gradient.  The first layer (input width <= 16) uses 8-row x 16-byte core matrices
+// input gradient.  The first layer (input width <= 15) uses 8-row x 16-byte core matrices
 // without swizzle; its weight gradient (N = 16) goes to the scratch columns every tile and
-// is added up in registers.  The head (width 1), the loss, dL/dz and the bias gradients are
+// is added up in registers, and a constant-1 input column 15 (zero weights) makes that
+// product deliver the first layer's bias gradient too.  The head (width 1), the loss, dL/dz
+// and the other bias gradients are
 // FP32 in the epilogue warps; the bias and head gradients are summed over a warp's 32 rows
-// by a shuffle transpose-reduction and over tiles in registers.
+// by a shuffle transpose-reduction and over tiles in shared memory (one owner per sum).
 //
 // Shared memory holds every layer's BF16 weights (loaded once by the bulk-copy engine),
 // the input tile and the hidden activations A_1 .. A_{NH-1}.  The backward pass overwrites
@@ -25,8 +27,8 @@
 // (four hidden layers) it takes A_1's, and A_1 is recomputed from the input (a K = 16
 // product) before dW_1.
 //
-// Warps: 8 epilogue warps (warp w serves TMEM lanes 32 (w mod 4) .. +31, i.e. those rows,
-// and columns 64 (w / 4) .. +63 of each layer) and one warp that allocates TMEM, loads the
+// Warps: 16 epilogue warps (warp w serves TMEM lanes 32 (w mod 4) .. +31, i.e. those rows,
+// and columns 32 (w / 4) .. +31 of each layer) and one warp that allocates TMEM, loads the
 // weights and issues the MMAs from one lane.  The two sides alternate through two
 // mbarriers; every wait is bounded (on expiry the kernel records NB_ETIMEOUT, drains the
 // tensor pipe and frees TMEM before returning).
@@ -42,7 +44,7 @@ using namespace nbtc;
 
 constexpr int TM = 128;         // samples per tile = TMEM lanes
 constexpr int H = 128;          // hidden width
-constexpr int NEPI = 8;         // epilogue warps
+constexpr int NEPI = 16;        // epilogue warps
 constexpr int THREADS = (NEPI + 1) * 32;
 constexpr uint32_t W0_BYTES = 4096;     // 128 x 16 BF16, core matrices
 constexpr uint32_t WL_BYTES = 32768;    // 128 x 128 BF16, two 64-column swizzled blocks
@@ -122,7 +124,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint8_t *sA = sX + W0_BYTES;                         // A_1 .. A_{NH-1}, then F
     float *bias = reinterpret_cast<float *>(sA + (size_t)(NH - 1 + (RECOMP ? 0 : 1)) * WL_BYTES);
     float *head = bias + NH * H;                         // [H + 1], padded to 132
-    float *zpart = head + 132;                           // [4][2][32] partial head sums
+    float *zpart = head + 132;                           // [4 lane quarters][4 column quarters][32]
+    float *dbs = zpart + 512;                            // [4][NH + 1][H] bias and head-weight sums
+    float *red2 = dbs + 4 * (NH + 1) * H;                // [4][2] loss and head-bias sums
     const uint32_t sWu = smem_u32(sW), sXu = smem_u32(sX), sAu = smem_u32(sA);
     auto bufA = [&](int l) { return sAu + (uint32_t)(l - 1) * WL_BYTES; };      // A_l, l >= 1
     const uint32_t ZB = RECOMP ? bufA(1) : bufA(NH);                      // dZ_{NH-1}
@@ -138,7 +142,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         mbar_init(bar_mma, 1);
         mbar_init(bar_epi, NEPI);
         mbar_init(bar_drain, 1);
-        for (int i = 0; i < 4; i++) mbar_init(smem_u32(&ctl->pair[i]), 2);
+        for (int i = 0; i < 4; i++) mbar_init(smem_u32(&ctl->pair[i]), 4);
         ctl->abort = 0;
         fence_mbar_init();
     }
@@ -147,6 +151,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         bias[i] = d.p[d.off[l] + H * (l == 0 ? d.in : H) + j];
     }
     for (int i = threadIdx.x; i <= H; i += THREADS) head[i] = d.p[d.off[NH] + i];
+    for (int i = threadIdx.x; i < 4 * (NH + 1) * H; i += THREADS) dbs[i] = 0.f;
     if (warp == NEPI) {
         tmem_alloc(smem_u32(&ctl->tmem), 512);
         tmem_relinquish();
@@ -180,11 +185,12 @@ __global__ void __launch_bounds__(THREADS, 1)
                 mma_f16(tmem, sdesc_gen(sXu, 128, 256, 0), sdesc_gen(wimg(0), 128, 256, 0), id_fwd, 0u);
             };
             bool first = true;
+#pragma unroll 1
             for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
                 if (!epi_wait()) break;  // input tile written
                 mma_l0();
                 mma_commit(bar_mma);
-#pragma unroll
+#pragma unroll 1
                 for (int l = 1; l < NH; l++) {
                     if (!epi_wait()) break;  // A_l written
                     const uint32_t a = bufA(l), w = wimg(l);
@@ -196,7 +202,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                     mma_commit(bar_mma);
                 }
                 if (!epi_wait()) break;  // head pass: dZ_{NH-1} written
-#pragma unroll
+#pragma unroll 1
                 for (int l = NH - 1; l >= 1; l--) {
                     if (l < NH - 1 && !epi_wait()) break;  // dZ_l written (in place of A_{l+1})
                     if (RECOMP && l == 1) {
@@ -232,14 +238,16 @@ __global__ void __launch_bounds__(THREADS, 1)
         __syncwarp();
     } else {
         // ------------------------------------------------------------ epilogue warps
-        const int qd = warp & 3, hf = warp >> 2;
-        const int m = qd * 32 + lane;                      // row of the tile = TMEM lane
+        const int qd = warp & 3, cq = warp >> 2;            // lane quarter, column quarter
+        const int m = qd * 32 + lane;                        // row of the tile = TMEM lane
         const uint32_t trow = tmem + ((uint32_t)(qd * 32) << 16);
-        const uint32_t bar_pair = smem_u32(&ctl->pair[qd]);
-        uint32_t pm = 0, pp = 0;
-        float dbacc[NH][2], hacc[2] = {0.f, 0.f}, dw0acc[8];
-#pragma unroll
-        for (int l = 0; l < NH; l++) dbacc[l][0] = dbacc[l][1] = 0.f;
+        const uint32_t tcol = trow + 32 * cq;                // this thread's 32 scratch columns
+        const uint32_t blk = (uint32_t)(cq >> 1) * BLK;      // its 64-column block in a swizzled buffer
+        const int c0 = (cq & 1) * 4;                         // and its first 16-byte chunk there
+        const uint32_t bar_quad = smem_u32(&ctl->pair[qd]);
+        float *dbl = dbs + qd * (NH + 1) * H + 32 * cq + lane;  // + l H: this lane's column sums
+        uint32_t pm = 0, pq = 0;
+        float dw0acc[8];
 #pragma unroll
         for (int i = 0; i < 8; i++) dw0acc[i] = 0.f;
         float gsum = 0.f, lossacc = 0.f;
@@ -259,50 +267,51 @@ __global__ void __launch_bounds__(THREADS, 1)
         };
         // forward epilogue of layer l: A_{l+1} = relu(Z_l + b_l) -> BF16 -> dst (swizzled)
         auto fwd_pass = [&](int l, uint32_t dst) {
-            const float *b = bias + l * H + 64 * hf;
+            const float4 *b4 = reinterpret_cast<const float4 *>(bias + l * H + 32 * cq);
+            float v[32];
+            tmem_ld32(tcol, v);
+            tmem_ld_wait();
 #pragma unroll
-            for (int cc = 0; cc < 2; cc++) {
-                float v[32];
-                tmem_ld32(trow + 64 * hf + 32 * cc, v);
-                tmem_ld_wait();
-#pragma unroll
-                for (int c4 = 0; c4 < 4; c4++) {
-                    const int c = 4 * cc + c4;
-                    const float *bb = b + 8 * c;
-                    const float *vv = v + 8 * c4;
-                    st_shared_v4(dst + hf * BLK + sw_off(m, c),
-                                 pack_bf16(fmaxf(vv[0] + bb[0], 0.f), fmaxf(vv[1] + bb[1], 0.f)),
-                                 pack_bf16(fmaxf(vv[2] + bb[2], 0.f), fmaxf(vv[3] + bb[3], 0.f)),
-                                 pack_bf16(fmaxf(vv[4] + bb[4], 0.f), fmaxf(vv[5] + bb[5], 0.f)),
-                                 pack_bf16(fmaxf(vv[6] + bb[6], 0.f), fmaxf(vv[7] + bb[7], 0.f)));
-                }
+            for (int c4 = 0; c4 < 4; c4++) {
+                const float4 lo = b4[2 * c4], hi = b4[2 * c4 + 1];
+                const float bb[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+                const float *vv = v + 8 * c4;
+                st_shared_v4(dst + blk + sw_off(m, c0 + c4), pack_bf16(fmaxf(vv[0] + bb[0], 0.f), fmaxf(vv[1] + bb[1], 0.f)),
+                             pack_bf16(fmaxf(vv[2] + bb[2], 0.f), fmaxf(vv[3] + bb[3], 0.f)),
+                             pack_bf16(fmaxf(vv[4] + bb[4], 0.f), fmaxf(vv[5] + bb[5], 0.f)),
+                             pack_bf16(fmaxf(vv[6] + bb[6], 0.f), fmaxf(vv[7] + bb[7], 0.f)));
             }
         };
-        // input rows of a tile, 8 columns (8 hf ..) per thread
+        // input rows of a tile: column quarters 0 and 1 hold columns 8 cq .. 8 cq + 7
         float xr[8];
-        bool xbad = false;  // a non-finite input coordinate in this thread's half of the row
+        bool xbad = false;  // a non-finite input coordinate in this thread's part of the row
         auto x_load = [&](long long tile) {
             const long long row = tile * TM + m;
 #pragma unroll
             for (int k = 0; k < 8; k++) {
-                const int kk = 8 * hf + k;
-                xr[k] = (tile < ntiles && row < n && kk < d.in) ? __ldg(q + row * d.in + kk) : 0.f;
+                const int kk = 8 * cq + k;
+                xr[k] = (cq < 2 && tile < ntiles && row < n && kk < d.in) ? __ldg(q + row * d.in + kk) : 0.f;
             }
+            // input column 15 is constant 1 (its weights are 0): the dW_0 product's column 15
+            // is then the sum of dZ_0 over the tile's rows, the first layer's bias gradient
+            if (cq == 1) xr[7] = 1.f;
         };
         x_load(blockIdx.x);
         bool first = true;
+#pragma unroll 1
         for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
             const long long row = tile * TM + m;
             const bool valid = row < n;
             // (the previous tile's dW_0 product, the last reader of X, has completed)
-            st_shared_v4(sXu + cm_off(m, hf), pack_bf16(xr[0], xr[1]), pack_bf16(xr[2], xr[3]),
-                         pack_bf16(xr[4], xr[5]), pack_bf16(xr[6], xr[7]));
+            if (cq < 2)
+                st_shared_v4(sXu + cm_off(m, cq), pack_bf16(xr[0], xr[1]), pack_bf16(xr[2], xr[3]),
+                             pack_bf16(xr[4], xr[5]), pack_bf16(xr[6], xr[7]));
             xbad = false;
 #pragma unroll
             for (int k = 0; k < 8; k++) xbad = xbad || !isfinite(xr[k]);
             arrive();
             x_load(tile + gridDim.x);  // prefetch the next tile's input
-#pragma unroll
+#pragma unroll 1
             for (int l = 0; l < NH - 1; l++) {
                 if (!mma_wait()) break;
                 fwd_pass(l, bufA(l + 1));
@@ -311,29 +320,29 @@ __global__ void __launch_bounds__(THREADS, 1)
             if (!ok || !mma_wait()) break;
             // ---- head (FP32), loss, dL/dz, dZ_{NH-1}, head and bias gradients
             {
-                const float *b = bias + (NH - 1) * H + 64 * hf;
-                const float *hw = head + 64 * hf;
+                const float *b = bias + (NH - 1) * H + 32 * cq;
+                const float *hw = head + 32 * cq;
                 float zp = 0.f;
-#pragma unroll
-                for (int cc = 0; cc < 2; cc++) {
+                {
                     float v[32];
-                    tmem_ld32(trow + 64 * hf + 32 * cc, v);
+                    tmem_ld32(tcol, v);
                     tmem_ld_wait();
 #pragma unroll
-                    for (int e = 0; e < 32; e++) zp = fmaf(hw[32 * cc + e], fmaxf(v[e] + b[32 * cc + e], 0.f), zp);
+                    for (int e = 0; e < 32; e++) zp = fmaf(hw[e], fmaxf(v[e] + b[e], 0.f), zp);
                 }
                 // a non-finite input coordinate makes the logit non-finite (as in the exact
                 // network), whatever the ReLUs made of it
                 if (xbad) zp = __int_as_float(0x7fc00000);
-                // the two warps of a lane quarter exchange their halves of the head sum
-                zpart[(qd * 2 + hf) * 32 + lane] = zp;
+                // the four warps of a lane quarter add their parts of the head sum, all in
+                // the same order
+                zpart[(qd * 4 + cq) * 32 + lane] = zp;
                 __syncwarp();
-                if (lane == 0) mbar_arrive(bar_pair);
-                ok = warp_wait(bar_pair, pp, ctl, err);
-                pp ^= 1;
+                if (lane == 0) mbar_arrive(bar_quad);
+                ok = warp_wait(bar_quad, pq, ctl, err);
+                pq ^= 1;
                 if (!ok) break;
-                const float zo = zpart[(qd * 2 + (hf ^ 1)) * 32 + lane];
-                const float z = (zp + zo) + head[H];
+                const float *zq = zpart + qd * 128 + lane;
+                const float z = ((zq[0] + zq[32]) + (zq[64] + zq[96])) + head[H];
                 float g = 0.f;
                 const bool fin = isfinite(z);
                 if (valid) {
@@ -341,49 +350,52 @@ __global__ void __launch_bounds__(THREADS, 1)
                     if (fin) {
                         const float sg = sigmoidf(z);
                         g = (alpha * y * (sg - 1.f) + beta * (1.f - y) * sg) * inv_n;
-                        if (hf == 0) {
+                        if (cq == 0) {
                             lossacc += alpha * y * softplusf(-z) + beta * (1.f - y) * softplusf(z);
                             const bool dec = z >= tau.up;
                             c_fn += (y != 0.f && !dec);
                             c_fp += (y == 0.f && dec);
                         }
-                    } else if (hf == 0) {
+                    } else if (cq == 0) {
                         c_nf++;
                     }
                 }
-                if (hf == 0) gsum += g;
+                if (cq == 0) gsum += g;
                 if (!fin) {
                     // a sample with a non-finite logit adds nothing: clear its rows so that no
                     // inf or NaN meets a zero gradient in the weight products
-                    st_shared_v4(sXu + cm_off(m, hf), 0u, 0u, 0u, 0u);
+                    if (cq < 2) st_shared_v4(sXu + cm_off(m, cq), 0u, 0u, 0u, 0u);
                     for (int l = 1; l < NH; l++)
-                        for (int c = 0; c < 8; c++) st_shared_v4(bufA(l) + hf * BLK + sw_off(m, c), 0u, 0u, 0u, 0u);
+                        for (int c4 = 0; c4 < 4; c4++) st_shared_v4(bufA(l) + blk + sw_off(m, c0 + c4), 0u, 0u, 0u, 0u);
                 }
-#pragma unroll
-                for (int cc = 0; cc < 2; cc++) {
-                    float v[32], dz[32], ga[32];
-                    tmem_ld32(trow + 64 * hf + 32 * cc, v);
+                // dZ_{NH-1} (and its bias-gradient sums), then the head-weight gradient terms,
+                // each from a fresh read of the accumulator (fewer live registers)
+                {
+                    float v[32];
+                    tmem_ld32(tcol, v);
                     tmem_ld_wait();
 #pragma unroll
-                    for (int e = 0; e < 32; e++) {
-                        const float a = fmaxf(v[e] + b[32 * cc + e], 0.f);
-                        dz[e] = a > 0.f ? g * hw[32 * cc + e] : 0.f;
-                        ga[e] = g * a;
-                        if (!fin) ga[e] = 0.f;
-                    }
+                    for (int e = 0; e < 32; e++) v[e] = (v[e] + b[e]) > 0.f ? g * hw[e] : 0.f;
 #pragma unroll
                     for (int c4 = 0; c4 < 4; c4++) {
-                        const float *zz = dz + 8 * c4;
-                        st_shared_v4(ZB + hf * BLK + sw_off(m, 4 * cc + c4), pack_bf16(zz[0], zz[1]),
-                                     pack_bf16(zz[2], zz[3]), pack_bf16(zz[4], zz[5]), pack_bf16(zz[6], zz[7]));
+                        const float *zz = v + 8 * c4;
+                        st_shared_v4(ZB + blk + sw_off(m, c0 + c4), pack_bf16(zz[0], zz[1]), pack_bf16(zz[2], zz[3]),
+                                     pack_bf16(zz[4], zz[5]), pack_bf16(zz[6], zz[7]));
                     }
-                    dbacc[NH - 1][cc] += xsum32(dz, lane);
-                    hacc[cc] += xsum32(ga, lane);
+                    dbl[(NH - 1) * H] += xsum32(v, lane);
+                }
+                {
+                    float v[32];
+                    tmem_ld32(tcol, v);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int e = 0; e < 32; e++) v[e] = fin ? g * fmaxf(v[e] + b[e], 0.f) : 0.f;
+                    dbl[NH * H] += xsum32(v, lane);
                 }
                 arrive();
             }
             // ---- backward through the hidden layers
-#pragma unroll
+#pragma unroll 1
             for (int l = NH - 1; l >= 1; l--) {
                 if (RECOMP && l == 1) {
                     if (!mma_wait()) break;
@@ -392,106 +404,94 @@ __global__ void __launch_bounds__(THREADS, 1)
                 }
                 if (!ok || !mma_wait()) break;
                 // dZ_{l-1} = dA_l masked by A_l > 0, written over A_l
-                const uint32_t buf = bufA(l) + hf * BLK;
+                const uint32_t buf = bufA(l) + blk;
+                float v[32];
+                tmem_ld32(tcol, v);
+                tmem_ld_wait();
 #pragma unroll
-                for (int cc = 0; cc < 2; cc++) {
-                    float v[32];
-                    tmem_ld32(trow + 64 * hf + 32 * cc, v);
-                    tmem_ld_wait();
-#pragma unroll
-                    for (int c4 = 0; c4 < 4; c4++) {
-                        const uint32_t addr = buf + sw_off(m, 4 * cc + c4);
-                        const uint4 mk = ld_shared_v4(addr);
-                        const uint32_t w4[4] = {mk.x, mk.y, mk.z, mk.w};
-                        float *vv = v + 8 * c4;
-#pragma unroll
-                        for (int e = 0; e < 4; e++) {
-                            if ((w4[e] & 0x7fffu) == 0u) vv[2 * e] = 0.f;          // A_l = +-0: inactive
-                            if ((w4[e] & 0x7fff0000u) == 0u) vv[2 * e + 1] = 0.f;
-                        }
-                        st_shared_v4(addr, pack_bf16(vv[0], vv[1]), pack_bf16(vv[2], vv[3]), pack_bf16(vv[4], vv[5]),
-                                     pack_bf16(vv[6], vv[7]));
-                    }
-                    dbacc[l - 1][cc] += xsum32(v, lane);
+                for (int c4 = 0; c4 < 4; c4++) {
+                    const uint32_t addr = buf + sw_off(m, c0 + c4);
+                    const uint4 mk = ld_shared_v4(addr);
+                    float *vv = v + 8 * c4;
+                    // A_l = +-0: inactive
+                    if ((mk.x & 0x7fffu) == 0u) vv[0] = 0.f;
+                    if ((mk.x & 0x7fff0000u) == 0u) vv[1] = 0.f;
+                    if ((mk.y & 0x7fffu) == 0u) vv[2] = 0.f;
+                    if ((mk.y & 0x7fff0000u) == 0u) vv[3] = 0.f;
+                    if ((mk.z & 0x7fffu) == 0u) vv[4] = 0.f;
+                    if ((mk.z & 0x7fff0000u) == 0u) vv[5] = 0.f;
+                    if ((mk.w & 0x7fffu) == 0u) vv[6] = 0.f;
+                    if ((mk.w & 0x7fff0000u) == 0u) vv[7] = 0.f;
+                    st_shared_v4(addr, pack_bf16(vv[0], vv[1]), pack_bf16(vv[2], vv[3]), pack_bf16(vv[4], vv[5]),
+                                 pack_bf16(vv[6], vv[7]));
                 }
+                if (l > 1) dbl[(l - 1) * H] += xsum32(v, lane);  // b_0's sums come from dW_0
                 arrive();
             }
             if (!ok || !mma_wait()) break;
-            // ---- dW_0 of this tile (scratch columns 8 hf .. 8 hf + 7 of lane = neuron m)
-            {
+            // ---- dW_0 of this tile (scratch columns 8 cq .. 8 cq + 7 of lane = neuron m)
+            if (cq < 2) {
                 float v[8];
-                tmem_ld8(trow + 8 * hf, v);
+                tmem_ld8(trow + 8 * cq, v);
                 tmem_ld_wait();
 #pragma unroll
                 for (int i = 0; i < 8; i++) dw0acc[i] += v[i];
-                tc_fence_before();
             }
+            tc_fence_before();
             first = false;
         }
         // ---- the CTA's gradient partial (every element written once)
         float *slot = partial + (size_t)blockIdx.x * stride;
         if (ok) {
-            // hidden-to-hidden weight gradients from tensor memory, row m, columns 64 hf ..
-#pragma unroll
+            // hidden-to-hidden weight gradients from tensor memory: row m, columns 32 cq ..
+#pragma unroll 1
             for (int l = 1; l < NH; l++) {
-                float *dst = slot + d.off[l] + (size_t)m * H + 64 * hf;
+                float *dst = slot + d.off[l] + (size_t)m * H + 32 * cq;
+                float v[32];
+                tmem_ld32(trow + (uint32_t)(128 * l) + 32 * cq, v);
+                tmem_ld_wait();
 #pragma unroll
-                for (int cc = 0; cc < 2; cc++) {
-                    float v[32];
-                    tmem_ld32(trow + (uint32_t)(128 * l) + 64 * hf + 32 * cc, v);
-                    tmem_ld_wait();
-                    if (first) {
-#pragma unroll
-                        for (int e = 0; e < 32; e++) v[e] = 0.f;
-                    }
-#pragma unroll
-                    for (int e = 0; e < 32; e += 4)
-                        *reinterpret_cast<float4 *>(dst + 32 * cc + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+                for (int e = 0; e < 32; e += 4)
+                    *reinterpret_cast<float4 *>(dst + e) =
+                        first ? make_float4(0.f, 0.f, 0.f, 0.f) : make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+            }
+            // first layer: row m, columns 8 cq .. (the real input columns), and its bias
+            // gradient from the constant column 15
+            if (cq < 2)
+                for (int i = 0; i < 8; i++) {
+                    const int k = 8 * cq + i;
+                    if (k < d.in) slot[d.off[0] + (size_t)m * d.in + k] = dw0acc[i];
                 }
-            }
-            // first layer: row m, columns 8 hf .. (only the real input columns)
-            for (int i = 0; i < 8; i++) {
-                const int k = 8 * hf + i;
-                if (k < d.in) slot[d.off[0] + (size_t)m * d.in + k] = dw0acc[i];
-            }
+            if (cq == 1) slot[d.off[0] + (size_t)H * d.in + m] = dw0acc[7];
         }
         tc_fence_before();
-        // bias, head and loss sums: each warp's 32-row sums, combined over the four lane
-        // quarters in a fixed order (A_1's buffer is free: every product has completed)
-        float *red = reinterpret_cast<float *>(sA);  // [4][NH + 1][128], then [4][2] loss and g sums
-#pragma unroll
-        for (int l = 0; l < NH; l++)
-#pragma unroll
-            for (int cc = 0; cc < 2; cc++) red[(qd * (NH + 1) + l) * H + 64 * hf + 32 * cc + lane] = dbacc[l][cc];
-        for (int cc = 0; cc < 2; cc++) red[(qd * (NH + 1) + NH) * H + 64 * hf + 32 * cc + lane] = hacc[cc];
+        // bias, head and loss sums: each lane quarter's sums, combined in a fixed order
 #pragma unroll
         for (int o = 16; o; o >>= 1) {
             lossacc += __shfl_xor_sync(FULL, lossacc, o);
             gsum += __shfl_xor_sync(FULL, gsum, o);
         }
-        float *red2 = red + 4 * (NH + 1) * H;
-        if (hf == 0 && lane == 0) {
+        if (cq == 0 && lane == 0) {
             red2[qd * 2] = lossacc;
             red2[qd * 2 + 1] = gsum;
         }
         asm volatile("bar.sync 1, %0;" ::"r"(NEPI * 32) : "memory");
         if (ok) {
-            for (int i = threadIdx.x; i < (NH + 1) * H; i += NEPI * 32) {
-                const int l = i / H, j = i % H;
-                const float s = ((red[(0 * (NH + 1) + l) * H + j] + red[(1 * (NH + 1) + l) * H + j]) +
-                                 red[(2 * (NH + 1) + l) * H + j]) +
-                                red[(3 * (NH + 1) + l) * H + j];
+            for (int i = H + threadIdx.x; i < (NH + 1) * H; i += NEPI * 32) {  // b_1 .. b_{NH-1}, head
+                const int l = i / H;
+                const float *dq = dbs + i;
+                const float s = ((dq[0] + dq[(NH + 1) * H]) + dq[2 * (NH + 1) * H]) + dq[3 * (NH + 1) * H];
                 if (l < NH)
-                    slot[d.off[l] + (size_t)H * (l == 0 ? d.in : H) + j] = s;  // b_l
+                    slot[d.off[l] + (size_t)H * H + (i % H)] = s;  // b_l
                 else
-                    slot[d.off[NH] + j] = s;  // head weights
+                    slot[d.off[NH] + (i % H)] = s;  // head weights
             }
             if (threadIdx.x == 0) {
                 slot[d.off[NH] + H] = ((red2[1] + red2[3]) + red2[5]) + red2[7];  // head bias
                 loss_partial[blockIdx.x] = ((red2[0] + red2[2]) + red2[4]) + red2[6];
             }
         }
-        if (st && hf == 0) {
+        if (st && cq == 0) {
 #pragma unroll
             for (int o = 16; o; o >>= 1) {
                 c_fn += __shfl_xor_sync(FULL, c_fn, o);
@@ -556,7 +556,7 @@ TTDesc make_desc(const TcModel *tc, const MlpDesc &d) {
 size_t smem_bytes(int NH, bool recompute) {
     const size_t img = W0_BYTES + (size_t)(NH - 1) * WL_BYTES;
     const size_t acts = W0_BYTES + (size_t)(NH - 1 + (recompute ? 0 : 1)) * WL_BYTES;
-    return 2048 + img + acts + (size_t)(NH * H + 132 + 256) * sizeof(float);
+    return 2048 + img + acts + (size_t)(NH * H + 132 + 512 + 4 * (NH + 1) * H + 8) * sizeof(float);
 }
 
 int num_sms() {
@@ -570,14 +570,12 @@ int num_sms() {
 
 bool nb_train_tc_supported(const MlpDesc &d) {
     const int NH = d.L - 1;
-    if (NH < 2 || NH > 4 || d.w[0] > 16 || d.w[0] < 1) return false;
+    if (NH < 2 || NH > 4 || d.w[0] > 15 || d.w[0] < 1) return false;  // column 15 is the constant 1
     for (int l = 1; l < d.L; l++)
         if (d.w[l] != H) return false;
     int dev = 0, maxsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    // the end-of-kernel reduction area reuses A_1's buffer
-    if ((size_t)(4 * (NH + 1) * H + 8) * sizeof(float) > WL_BYTES) return false;
     return smem_bytes(NH, NH == 4) <= (size_t)maxsm;
 }
 
