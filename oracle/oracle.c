@@ -16,8 +16,10 @@
  *                   a lattice of sample points of the region (Sec. 4.2, "Query
  *                   types": any() over a sample of the indicator).  Test-only.
  *   orc_forward     bounding network h (Sec. 3.4 "Architecture"): MLP with ReLU
- *                   hidden layers (the configurations' activation), output logit
- *                   z; sigmoid(z) rounded to {0,1} is the decision z >= tau.
+ *                   hidden layers (the configurations' activation) or, in the
+ *                   _act forms with act = 1, the paper's sinusoidal hidden
+ *                   activation sin(z); output logit z; sigmoid(z) rounded to
+ *                   {0,1} is the decision z >= tau.
  *   orc_loss_grad   weighted binary cross-entropy of Eq. (loss) with weights
  *                   alpha(t) on y log(yhat) and beta(t) on (1-y) log(1-yhat),
  *                   mean over the batch, and its gradient by backpropagation.
@@ -314,9 +316,15 @@ static int64_t layer_offset(const int *widths, int l) {
 
 int64_t orc_param_count(const int *widths, int L) { return layer_offset(widths, L); }
 
+/* hidden activation: act 0 = ReLU max(z, 0) (the configurations), act 1 = sin(z), the
+ * sinusoidal activation of Sec. 3.4 "Architecture" (no frequency factor is stated) */
+static double activate(int act, double z) { return act ? sin(z) : (z > 0.0 ? z : 0.0); }
+/* its derivative: ReLU'(z) = 1[z > 0], sin'(z) = cos(z) */
+static double activate_d(int act, double z) { return act ? cos(z) : (z > 0.0 ? 1.0 : 0.0); }
+
 /* forward pass of one query; keeps every layer's pre-activation z_l and
  * activation a_l (a_0 = x) in acts[l] / pre[l] when they are not NULL. */
-static double forward_one(const int *widths, int L, const float *params, const float *x,
+static double forward_one(const int *widths, int L, int act, const float *params, const float *x,
                           double acts[][MAXW], double pre[][MAXW]) {
     double a[MAXW], z[MAXW];
     for (int k = 0; k < widths[0]; k++) a[k] = (double)x[k];
@@ -331,7 +339,7 @@ static double forward_one(const int *widths, int L, const float *params, const f
         }
         if (pre) memcpy(pre[l + 1], z, sizeof(double) * widths[l + 1]);
         if (l < L - 1) {
-            for (int j = 0; j < widths[l + 1]; j++) a[j] = z[j] > 0.0 ? z[j] : 0.0;
+            for (int j = 0; j < widths[l + 1]; j++) a[j] = activate(act, z[j]);
             if (acts) memcpy(acts[l + 1], a, sizeof(double) * widths[l + 1]);
         }
     }
@@ -340,7 +348,7 @@ static double forward_one(const int *widths, int L, const float *params, const f
 
 typedef struct {
     const int *widths;
-    int L;
+    int L, act;
     const float *params;
     const float *X;
     double *z;
@@ -350,18 +358,18 @@ static void fwd_range(void *p, int64_t lo, int64_t hi, int tid) {
     (void)tid;
     fwd_ctx *c = (fwd_ctx *)p;
     for (int64_t i = lo; i < hi; i++)
-        c->z[i] = forward_one(c->widths, c->L, c->params, c->X + i * c->widths[0], NULL, NULL);
+        c->z[i] = forward_one(c->widths, c->L, c->act, c->params, c->X + i * c->widths[0], NULL, NULL);
 }
 
 /* conditioning scale of the output logit: sum_k |W_L[k]| a_{L-1}[k] + |b_L|, the
  * magnitude the FP32 rounding error of the last layer is relative to */
-int orc_forward_scale(const int *widths, int L, const float *params, const float *X, int64_t n,
-                      double *scale) {
+int orc_forward_scale_act(const int *widths, int L, int act, const float *params, const float *X, int64_t n,
+                          double *scale) {
     if (L < 1 || widths[L] != 1) return -1;
     double (*acts)[MAXW] = malloc(sizeof(double) * MAXW * (L + 1));
     const float *W = params + layer_offset(widths, L - 1);
     for (int64_t i = 0; i < n; i++) {
-        forward_one(widths, L, params, X + i * widths[0], acts, NULL);
+        forward_one(widths, L, act, params, X + i * widths[0], acts, NULL);
         double s = fabs((double)W[widths[L - 1]]);
         for (int k = 0; k < widths[L - 1]; k++) s += fabs((double)W[k]) * fabs(acts[L - 1][k]);
         scale[i] = s;
@@ -370,14 +378,24 @@ int orc_forward_scale(const int *widths, int L, const float *params, const float
     return 0;
 }
 
-int orc_forward(const int *widths, int L, const float *params, const float *X, int64_t n, double *z,
-                int nthreads) {
-    if (L < 1 || widths[L] != 1) return -1;
+int orc_forward_scale(const int *widths, int L, const float *params, const float *X, int64_t n,
+                      double *scale) {
+    return orc_forward_scale_act(widths, L, 0, params, X, n, scale);
+}
+
+int orc_forward_act(const int *widths, int L, int act, const float *params, const float *X, int64_t n, double *z,
+                    int nthreads) {
+    if (L < 1 || widths[L] != 1 || act < 0 || act > 1) return -1;
     for (int l = 0; l <= L; l++)
         if (widths[l] < 1 || widths[l] > MAXW) return -1;
-    fwd_ctx c = {widths, L, params, X, z};
+    fwd_ctx c = {widths, L, act, params, X, z};
     parallel_for(n, nthreads, fwd_range, &c);
     return 0;
+}
+
+int orc_forward(const int *widths, int L, const float *params, const float *X, int64_t n, double *z,
+                int nthreads) {
+    return orc_forward_act(widths, L, 0, params, X, n, z, nthreads);
 }
 
 /* softplus(u) = log(1 + e^u), evaluated without overflow */
@@ -386,7 +404,7 @@ static double sigmoid(double u) { return u >= 0 ? 1.0 / (1.0 + exp(-u)) : exp(u)
 
 typedef struct {
     const int *widths;
-    int L;
+    int L, act;
     const float *params;
     const float *X;
     const uint8_t *y;
@@ -406,7 +424,7 @@ static void lg_range(void *p, int64_t lo, int64_t hi, int tid) {
     double delta[MAXW], dprev[MAXW];
     double loss = 0.0;
     for (int64_t i = lo; i < hi; i++) {
-        double z = forward_one(w, L, c->params, c->X + i * w[0], acts, pre);
+        double z = forward_one(w, L, c->act, c->params, c->X + i * w[0], acts, pre);
         double y = c->y[i] ? 1.0 : 0.0;
         /* Eq. (loss): -[alpha y log(s) + beta (1-y) log(1-s)], s = sigmoid(z)
          * -log(s) = softplus(-z), -log(1-s) = softplus(z) */
@@ -426,7 +444,7 @@ static void lg_range(void *p, int64_t lo, int64_t hi, int tid) {
                 for (int k = 0; k < w[l]; k++) {
                     double s2 = 0.0;
                     for (int j = 0; j < w[l + 1]; j++) s2 += (double)W[(int64_t)j * w[l] + k] * delta[j];
-                    dprev[k] = pre[l][k] > 0.0 ? s2 : 0.0;   /* ReLU'(z) = 1[z > 0] */
+                    dprev[k] = s2 * activate_d(c->act, pre[l][k]);   /* dL/dz_k = dL/da_k act'(z_k) */
                 }
                 memcpy(delta, dprev, sizeof(double) * w[l]);
             }
@@ -438,9 +456,9 @@ static void lg_range(void *p, int64_t lo, int64_t hi, int tid) {
 }
 
 /* mean asymmetric BCE over the batch and its gradient w.r.t. the flat parameters */
-int orc_loss_grad(const int *widths, int L, const float *params, const float *X, const uint8_t *y,
-                  int64_t n, double alpha, double beta, double *loss, double *grad, int nthreads) {
-    if (L < 1 || widths[L] != 1 || n < 1) return -1;
+int orc_loss_grad_act(const int *widths, int L, int act, const float *params, const float *X, const uint8_t *y,
+                      int64_t n, double alpha, double beta, double *loss, double *grad, int nthreads) {
+    if (L < 1 || widths[L] != 1 || n < 1 || act < 0 || act > 1) return -1;
     for (int l = 0; l <= L; l++)
         if (widths[l] < 1 || widths[l] > MAXW) return -1;
     if (nthreads < 1) nthreads = 1;
@@ -449,7 +467,7 @@ int orc_loss_grad(const int *widths, int L, const float *params, const float *X,
     int64_t P = layer_offset(widths, L);
     double *gpart = calloc((size_t)nthreads * P, sizeof(double));
     double *lpart = calloc((size_t)nthreads, sizeof(double));
-    lg_ctx c = {widths, L, params, X, y, alpha, beta, n, P, gpart, lpart};
+    lg_ctx c = {widths, L, act, params, X, y, alpha, beta, n, P, gpart, lpart};
     parallel_for(n, nthreads, lg_range, &c);
     double ls = 0.0;
     for (int64_t p = 0; p < P; p++) grad[p] = 0.0;
@@ -461,6 +479,11 @@ int orc_loss_grad(const int *widths, int L, const float *params, const float *X,
     free(gpart);
     free(lpart);
     return 0;
+}
+
+int orc_loss_grad(const int *widths, int L, const float *params, const float *X, const uint8_t *y,
+                  int64_t n, double alpha, double beta, double *loss, double *grad, int nthreads) {
+    return orc_loss_grad_act(widths, L, 0, params, X, y, n, alpha, beta, loss, grad, nthreads);
 }
 
 /* Adam (Kingma & Ba) step t >= 1 with bias correction, in place */

@@ -68,6 +68,13 @@ def lib():
             L.orc_philox4x64.restype = None
             L.orc_sample.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint64, i64, i64, P, ctypes.c_int]
             L.orc_sample.restype = ctypes.c_int
+            L.orc_forward_act.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P, i64, P, ctypes.c_int]
+            L.orc_forward_act.restype = ctypes.c_int
+            L.orc_forward_scale_act.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P, i64, P]
+            L.orc_forward_scale_act.restype = ctypes.c_int
+            L.orc_loss_grad_act.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P, P, i64, ctypes.c_double,
+                                            ctypes.c_double, P, P, ctypes.c_int]
+            L.orc_loss_grad_act.restype = ctypes.c_int
             L.orc_canonical_ray.argtypes = [P, P, i64, ctypes.c_float, P, P]
             L.orc_canonical_ray.restype = ctypes.c_int
             L.orc_canonical_ray_f64.argtypes = [P, P, i64, ctypes.c_double, P, P]
@@ -117,32 +124,35 @@ def param_count(widths) -> int:
     return int(lib().orc_param_count(_ptr(w), len(widths) - 1))
 
 
-def forward(widths, params: np.ndarray, X: np.ndarray, nthreads: int | None = None) -> np.ndarray:
-    """FP64 logits z of the MLP on the FP32 parameters."""
+ACTS = {"relu": 0, "sine": 1}
+
+
+def forward(widths, params: np.ndarray, X: np.ndarray, nthreads: int | None = None, act: str = "relu") -> np.ndarray:
+    """FP64 logits z of the MLP on the FP32 parameters (hidden activation ReLU or sine)."""
     w = np.ascontiguousarray(widths, dtype=np.int32)
     p = np.ascontiguousarray(params, dtype=np.float32)
     X = np.ascontiguousarray(X, dtype=np.float32)
     z = np.zeros(X.shape[0], dtype=np.float64)
-    rc = lib().orc_forward(_ptr(w), len(widths) - 1, _ptr(p), _ptr(X), X.shape[0], _ptr(z),
-                           _threads(nthreads))
+    rc = lib().orc_forward_act(_ptr(w), len(widths) - 1, ACTS[act], _ptr(p), _ptr(X), X.shape[0], _ptr(z),
+                               _threads(nthreads))
     if rc != 0:
         raise ValueError("oracle forward: bad widths")
     return z
 
 
-def forward_scale(widths, params: np.ndarray, X: np.ndarray) -> np.ndarray:
+def forward_scale(widths, params: np.ndarray, X: np.ndarray, act: str = "relu") -> np.ndarray:
     """sum_k |W_L[k]| a_{L-1}[k] + |b_L| per query (FP64): the scale the last layer's
     rounding error is relative to."""
     w = np.ascontiguousarray(widths, dtype=np.int32)
     p = np.ascontiguousarray(params, dtype=np.float32)
     X = np.ascontiguousarray(X, dtype=np.float32)
     s = np.zeros(X.shape[0], dtype=np.float64)
-    if lib().orc_forward_scale(_ptr(w), len(widths) - 1, _ptr(p), _ptr(X), X.shape[0], _ptr(s)) != 0:
+    if lib().orc_forward_scale_act(_ptr(w), len(widths) - 1, ACTS[act], _ptr(p), _ptr(X), X.shape[0], _ptr(s)) != 0:
         raise ValueError("oracle forward_scale: bad widths")
     return s
 
 
-def loss_grad(widths, params, X, y, alpha: float, beta: float, nthreads: int | None = None):
+def loss_grad(widths, params, X, y, alpha: float, beta: float, nthreads: int | None = None, act: str = "relu"):
     """Mean asymmetric BCE (Eq. loss) and its FP64 gradient w.r.t. the flat parameters."""
     w = np.ascontiguousarray(widths, dtype=np.int32)
     p = np.ascontiguousarray(params, dtype=np.float32)
@@ -150,8 +160,8 @@ def loss_grad(widths, params, X, y, alpha: float, beta: float, nthreads: int | N
     y = np.ascontiguousarray(np.asarray(y).astype(np.uint8))
     g = np.zeros(p.shape[0], dtype=np.float64)
     loss = np.zeros(1, dtype=np.float64)
-    rc = lib().orc_loss_grad(_ptr(w), len(widths) - 1, _ptr(p), _ptr(X), _ptr(y), X.shape[0],
-                             float(alpha), float(beta), _ptr(loss), _ptr(g), _threads(nthreads))
+    rc = lib().orc_loss_grad_act(_ptr(w), len(widths) - 1, ACTS[act], _ptr(p), _ptr(X), _ptr(y), X.shape[0],
+                                 float(alpha), float(beta), _ptr(loss), _ptr(g), _threads(nthreads))
     if rc != 0:
         raise ValueError("oracle loss_grad failed")
     return float(loss[0]), g
