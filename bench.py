@@ -864,7 +864,9 @@ def run_c6(args):
     """The paper's own network sizes (its supplementary architecture table: two hidden
     layers of 25 / 50 / 75 neurons for 2D / 3D / 4D indicators), each trained in FP32 on a
     sphere union of its dimension, calibrated on its evaluation queries and queried on the
-    FP32 form and on the split-FP16 tensor-core form, zero-padded to 64 / 128 neurons."""
+    FP32 form and on the split-FP16 tensor-core form, zero-padded to 64 / 128 neurons.
+    --activation sine gives every network the paper's sinusoidal hidden activation."""
+    act = args.activation
     from paper_2310_06822_gb300 import inputs as I
     from paper_2310_06822_gb300 import nb
     ctx = Ctx(args)
@@ -882,7 +884,7 @@ def run_c6(args):
     head = None
     for name, kind, widths, sc in rows:
         shape = nb.Shape(sc, dev)
-        m = nb.Model(widths)
+        m = nb.Model(widths, activation=act)
         m.set_params(I.init_params(6100 + kind, widths))
         for t in range(T):
             q = nb.sample(kind, B, seed=rank_seed(6200 + kind, ctx.rank), first=t * B, device=dev)
@@ -890,7 +892,7 @@ def run_c6(args):
         eq = nb.sample(kind, n, seed=rank_seed(6300 + kind, ctx.rank), device=dev)
         ey = nb.label(shape, kind, eq)
         tau = m.calibrate(eq, ey)
-        f = nb.Model(widths, infer_prec="f16x3")
+        f = nb.Model(widths, infer_prec="f16x3", activation=act)
         f.set_params(m.get_params())
         f.tau = tau
         out = torch.empty(nb.n_words(n), dtype=torch.int32, device=dev)
@@ -915,12 +917,14 @@ def run_c6(args):
         m.close()
         f.close()
     msf, clocks = head
-    line = base_line(ctx, "neural-bound queries/s at 0 FN (3D rays, the paper's 6->50->50->1, split-FP16 padded)",
+    line = base_line(ctx, "neural-bound queries/s at 0 FN (3D rays, the paper's 6->50->50->1%s, split-FP16 padded)"
+                     % (", sine activations" if act == "sine" else ""),
                      job_value(n, ctx.world, msf), "queries/s", msf, args.steps, args.warmup,
                      "f16x3 (split fp16 operands, fp32 accumulate)",
                      {"workload": "the paper's network sizes: 2D 2->25x2->1, 3D 3/6/4->50x2->1, 4D 4->75x2->1, "
                                   "FP32 training, 16M eval queries each", "n_eval": n, "train_steps": T,
-                      "batch": B, "padding": "hidden widths zero-padded to 64 (25, 50) and 128 (75)"},
+                      "batch": B, "padding": "hidden widths zero-padded to 64 (25, 50) and 128 (75)",
+                      "activation": act},
                      clocks, args.steps * 4)
     line.update({"sizes": table, "cpu_baseline": None, "e2e": None})
     ctx.emit(line)
@@ -964,6 +968,8 @@ def main():
     ap.add_argument("--config", default="c2", choices=["c1", "c2", "c2e", "c3", "c4", "c5", "c6"])
     ap.add_argument("--train-steps", type=int, default=TRAIN_STEPS)
     ap.add_argument("--n-eval", type=int, default=N_EVAL, help="evaluation size (smaller only for profiling)")
+    ap.add_argument("--activation", default="relu", choices=["relu", "sine"],
+                    help="hidden activation of the c6 networks (sine: the paper's sinusoidal activation)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)

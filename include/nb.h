@@ -120,6 +120,21 @@ typedef struct nb_model nb_model;
  * sigmoid rounded at 1/2 (Sec. 3.4).  The device is the current CUDA device. */
 nb_status nb_model_create(const int32_t *widths, int32_t n_layers, int32_t infer_prec,
                           int32_t train_prec, nb_model **out);
+
+/* Hidden activations: NB_ACT_RELU (the configurations') or NB_ACT_SINE, sin(z), the
+ * sinusoidal activation of Sec. 3.4 "Architecture" (no frequency factor: sin of the
+ * pre-activation itself).  nb_model_create_act is nb_model_create with the activation
+ * chosen; nb_model_create makes ReLU networks.  Sine networks run the FP32 forward
+ * (infer NB_F32) or the split-FP16 tensor-core forward (NB_F16X3, widths as there; padded
+ * neurons stay 0 since sin 0 = 0), train in FP32 (train NB_F32), and are re-checked and
+ * calibrated like ReLU networks, the rounding bounds adding the documented error of CUDA's
+ * sinf (2 ulp) and sin (2 ulp) at each activation (sin is 1-Lipschitz).  Other precisions
+ * return NB_EUNSUPPORTED; an unknown activation NB_EINVAL.  Checkpoints do not record the
+ * activation: restore a state into a model of the same activation. */
+#define NB_ACT_RELU 0
+#define NB_ACT_SINE 1
+nb_status nb_model_create_act(const int32_t *widths, int32_t n_layers, int32_t infer_prec, int32_t train_prec,
+                              int32_t activation, nb_model **out);
 nb_status nb_model_destroy(nb_model *m);
 int64_t nb_model_param_count(const nb_model *m);
 

@@ -101,6 +101,7 @@ struct nb_model {
     int off[NB_MAXL] = {0};
     int64_t P = 0;
     int infer_prec = NB_F32, train_prec = NB_F32;
+    int act = NB_ACT_RELU;
     float *params = nullptr, *adam_m = nullptr, *adam_v = nullptr, *grad = nullptr;
     float *paramsT = nullptr;  // weights transposed, for the margin re-check and calibration
     int64_t step = 0;
@@ -134,6 +135,7 @@ static MlpDesc desc_of(const nb_model *m) {
     }
     d.p = m->params;
     d.pT = m->paramsT;
+    d.act = m->act;
     return d;
 }
 
@@ -186,7 +188,17 @@ static void free_model(nb_model *m) {
 
 extern "C" nb_status nb_model_create(const int32_t *widths, int32_t n_layers, int32_t infer_prec, int32_t train_prec,
                                      nb_model **out) {
+    return nb_model_create_act(widths, n_layers, infer_prec, train_prec, NB_ACT_RELU, out);
+}
+
+extern "C" nb_status nb_model_create_act(const int32_t *widths, int32_t n_layers, int32_t infer_prec,
+                                         int32_t train_prec, int32_t activation, nb_model **out) {
     if (!widths || !out) return nb_fail(NB_EINVAL, "nb_model_create: null pointer");
+    if (activation != NB_ACT_RELU && activation != NB_ACT_SINE)
+        return nb_fail(NB_EINVAL, "nb_model_create: unknown activation");
+    if (activation == NB_ACT_SINE && ((infer_prec != NB_F32 && infer_prec != NB_F16X3) || train_prec != NB_F32))
+        return nb_fail(NB_EUNSUPPORTED,
+                       "nb_model_create: sine networks infer in NB_F32 or NB_F16X3 and train in NB_F32");
     *out = nullptr;
     if (n_layers < 1 || n_layers > NB_MAXL) return nb_fail(NB_EINVAL, "nb_model_create: n_layers must be 1..8");
     if (widths[n_layers] != 1) return nb_fail(NB_EINVAL, "nb_model_create: last width must be 1");
@@ -207,6 +219,7 @@ extern "C" nb_status nb_model_create(const int32_t *widths, int32_t n_layers, in
     m->P = o;
     m->infer_prec = infer_prec;
     m->train_prec = train_prec;
+    m->act = activation;
     nb_fill_gamma(m->widths, n_layers, &m->gamma);
     const size_t pb = (size_t)m->P * sizeof(float);
     if (cudaMalloc(&m->params, pb) != cudaSuccess || cudaMalloc(&m->adam_m, pb) != cudaSuccess ||

@@ -9,13 +9,18 @@
 //     B_n = gamma_l |b_n| + sum_k |W_nk| (gamma_l |a^_k| + e_k),
 // gamma_l = gamma_{fan-in + 8} covering the rounding of this layer's dot product
 // (at most fan-in + 8 roundings per term, any order), e_k the propagated bound of the
-// inputs; ReLU is 1-Lipschitz so e_n = B_n after it.  Every bound is accumulated with
-// upward rounding, so it only over-estimates.  One extra FMA per MAC.
+// inputs; ReLU is 1-Lipschitz so e_n = B_n after it.  The sinusoidal activation
+// (NB_ACT_SINE) is 1-Lipschitz too: e_n = B_n + 2^-22, the second term covering CUDA's
+// sinf (documented maximum error 2 ulp; |sin| <= 1, so 2 ulp <= 2^-22).  Every bound is
+// accumulated with upward rounding, so it only over-estimates.  One extra FMA per MAC.
 // Stage 2 (ff_kernel): the queries stage 1 leaves ambiguous are evaluated with
 // error-free transformations (TwoProd / TwoSum, Ogita, Rump & Oishi 2005) on activations
 // carried as float pairs, first as compensated dot products (2a, bound about
 // gamma_{3K} u |terms|), then, for the few still ambiguous, in three-word accumulation
 // (2b, bound about gamma_{4K} u^2 |terms|), each with its bound evaluated at run time.
+// Sine activations of a float pair are evaluated in FP64 (CUDA's sin, documented maximum
+// error 2 ulp) and split back into a pair; their bound adds that error, the rounding of
+// the pair to a double and of the low word (see sine_pair).
 #include <math.h>
 
 #include "common.cuh"
@@ -25,6 +30,7 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr float U = 5.9604644775390625e-08f;  // unit roundoff 2^-24
 constexpr int FF_WARPS_PER_SM = 32;              // stage-2 launch: 8 blocks of 4 warps per SM
+constexpr float E_SINF = 2.384185791015625e-07f;  // 2^-22: |sinf(x) - sin(x)| (2 ulp at |sin| <= 1)
 
 __device__ __forceinline__ unsigned ord_f32(float f) {
     unsigned u = __float_as_uint(f);
@@ -47,7 +53,7 @@ __device__ __forceinline__ unsigned long long ord_f64(double f) {
 constexpr int KC = 32;
 template <int NJ, int MI>
 __device__ __forceinline__ void bound_layer_tile(const float *__restrict__ Wt, const float *__restrict__ b, int K,
-                                                 int N, float g, float *a_s, float *e_s, float *wt, int KP) {
+                                                 int N, float g, float *a_s, float *e_s, float *wt, int KP, int act) {
     constexpr int WS = 16 * NJ + 1;
     const int t = threadIdx.x, tn = t & 15, tm = t >> 4;
     float acc[MI][NJ], bnd[MI][NJ];
@@ -96,8 +102,13 @@ __device__ __forceinline__ void bound_layer_tile(const float *__restrict__ Wt, c
         if (nn < N)
 #pragma unroll
             for (int i = 0; i < MI; i++) {
-                a_s[(tm + 16 * i) * KP + nn] = fmaxf(acc[i][j], 0.f);
-                e_s[(tm + 16 * i) * KP + nn] = bnd[i][j];
+                if (act == NB_ACT_SINE) {
+                    a_s[(tm + 16 * i) * KP + nn] = sinf(acc[i][j]);
+                    e_s[(tm + 16 * i) * KP + nn] = __fadd_ru(bnd[i][j], E_SINF);
+                } else {
+                    a_s[(tm + 16 * i) * KP + nn] = fmaxf(acc[i][j], 0.f);
+                    e_s[(tm + 16 * i) * KP + nn] = bnd[i][j];
+                }
             }
     }
 }
@@ -148,7 +159,7 @@ __global__ void __launch_bounds__(256) bound_tile_kernel(MlpDesc d, GammaTab gt,
         for (int l = 0; l < d.L - 1; l++) {
             const int K = d.w[l], N = d.w[l + 1];
             const float *Wt = d.pT + d.off[l];
-            bound_layer_tile<NJ, MI>(Wt, Wt + (size_t)N * K, K, N, gt.g[l], a0, e0, wt, KP);
+            bound_layer_tile<NJ, MI>(Wt, Wt + (size_t)N * K, K, N, gt.g[l], a0, e0, wt, KP, d.act);
         }
         __syncthreads();
         {
@@ -354,19 +365,39 @@ __device__ __forceinline__ void relu_pair(float hi, float lo, float &h2, float &
     }
 }
 
+// sin(hi + lo) as a pair (h2, l2) and what it adds to the propagated bound bd (sin is
+// 1-Lipschitz, so bd carries over): hi + lo rounded to a double (<= 2^-53 |hi + lo|),
+// CUDA's sin (2 ulp, <= 2^-52 at |sin| <= 1), and the float low word (<= 2^-48, since
+// |s - h2| <= 2^-24 |s| and the low word rounds that to 24 bits); 2^-47 + 2^-53 |x|
+// covers the sum.
+__device__ __forceinline__ void sine_pair(float hi, float lo, float bd, float &h2, float &l2, float &e2) {
+    const double sv = sin((double)hi + (double)lo);
+    h2 = (float)sv;
+    l2 = (float)(sv - (double)h2);
+    const float ax = __fadd_ru(fabsf(hi), fabsf(lo));
+    e2 = __fadd_ru(bd, __fmaf_ru(1.1102230246251565e-16f, ax, 7.105427357601002e-15f));
+}
+
+// the activation of a pair with its bound
+__device__ __forceinline__ void act_pair(int act, float hi, float lo, float bd, float &h2, float &l2, float &e2) {
+    if (act == NB_ACT_SINE) {
+        sine_pair(hi, lo, bd, h2, l2, e2);
+    } else {
+        relu_pair(hi, lo, h2, l2);
+        e2 = bd;
+    }
+}
+
 template <int NB>
 __device__ __forceinline__ void dot2_neurons_relu(const float *__restrict__ Wt, const float *__restrict__ bias, int K,
                                                   int N, int nn0, float g3, const float *h, const float *l,
-                                                  const float *e, float *h2, float *l2, float *e2) {
+                                                  const float *e, float *h2, float *l2, float *e2, int act) {
     float hi[NB], lo[NB], bd[NB];
     dot2_core<NB>(Wt, bias, K, N, nn0, g3, h, l, e, hi, lo, bd);
 #pragma unroll
     for (int j = 0; j < NB; j++) {
         const int nn = nn0 + 32 * j;
-        if (nn < N) {
-            relu_pair(hi[j], lo[j], h2[nn], l2[nn]);
-            e2[nn] = bd[j];
-        }
+        if (nn < N) act_pair(act, hi[j], lo[j], bd[j], h2[nn], l2[nn], e2[nn]);
     }
 }
 
@@ -377,7 +408,7 @@ __device__ __forceinline__ void dot2_neurons_relu(const float *__restrict__ Wt, 
 template <int NB>
 __device__ __forceinline__ void ff_neurons_relu(const float *__restrict__ Wt, const float *__restrict__ bias, int K,
                                                 int N, int nn0, float g4, const float *h, const float *l,
-                                                const float *e, float *h2, float *l2, float *e2) {
+                                                const float *e, float *h2, float *l2, float *e2, int act) {
     float s1[NB], s2[NB], s3[NB], A3[NB], P[NB];
     const float *Wr[NB];
 #pragma unroll
@@ -426,15 +457,7 @@ __device__ __forceinline__ void ff_neurons_relu(const float *__restrict__ Wt, co
             two_sum(s1[j], t2, hi, t4);
             const float lo = __fadd_rn(t4, t3);
             const float bd = __fmaf_ru(g4, A3[j], __fmaf_ru(2.f * U, __fadd_ru(fabsf(t4), fabsf(t3)), P[j]));
-            // relu(hi + lo): |lo| is far below |hi| unless hi = 0, so the sign is hi's
-            if (hi > 0.f) {
-                h2[nn] = hi;
-                l2[nn] = lo;
-            } else {
-                h2[nn] = hi == 0.f ? fmaxf(lo, 0.f) : 0.f;
-                l2[nn] = 0.f;
-            }
-            e2[nn] = bd;
+            act_pair(act, hi, lo, bd, h2[nn], l2[nn], e2[nn]);
         }
     }
 }
@@ -484,9 +507,9 @@ __global__ void __launch_bounds__(128) ff_kernel(MlpDesc d, GammaTab gt, const f
             const float *W = dd.pT + dd.off[ly];  // W_l transposed: [K][N]
             for (int nn0 = lane; nn0 < N; nn0 += 32 * 4) {
                 if (STAGE == 0)
-                    dot2_neurons_relu<4>(W, W + (size_t)N * K, K, N, nn0, gt.gd2[ly], h, l, e, h2, l2, e2);
+                    dot2_neurons_relu<4>(W, W + (size_t)N * K, K, N, nn0, gt.gd2[ly], h, l, e, h2, l2, e2, d.act);
                 else
-                    ff_neurons_relu<4>(W, W + (size_t)N * K, K, N, nn0, gt.gff[ly], h, l, e, h2, l2, e2);
+                    ff_neurons_relu<4>(W, W + (size_t)N * K, K, N, nn0, gt.gff[ly], h, l, e, h2, l2, e2, d.act);
             }
             __syncwarp();
             float *tp = h;
@@ -588,7 +611,7 @@ __global__ void __launch_bounds__(256) calib_f64_kernel(MlpDesc d, const float *
             for (int nn = lane; nn < N; nn += 32) {
                 double s = (double)__ldg(Wt + (size_t)N * K + nn);
                 for (int k = 0; k < K; k++) s = fma((double)__ldg(Wt + (size_t)k * N + nn), a[k], s);
-                a2[nn] = s > 0.0 ? s : 0.0;
+                a2[nn] = d.act == NB_ACT_SINE ? sin(s) : (s > 0.0 ? s : 0.0);
             }
             __syncwarp();
             double *tp = a;

@@ -29,6 +29,7 @@ struct MlpDesc {
     int w[NB_MAXL + 1];
     int off[NB_MAXL];        // offset of W_l in the flat parameter array; b_l follows W_l
     int maxw;                // max(w[0..L-1])
+    int act;                 // hidden activation: NB_ACT_RELU or NB_ACT_SINE
     const float *p;          // device FP32 master parameters
     const float *pT;         // the same with every W_l stored transposed ([K][N]), biases as in p
 };

@@ -158,7 +158,9 @@ template <int NJ, int TM>
 nb_status train_launch(const MlpDesc &d, const float *q, const uint32_t *labels, int64_t n, float alpha,
                        float beta, TauF tau, TrainWs ws, nb_step_stats *st, cudaStream_t s, long long P) {
     constexpr int KP = 16 * NJ + 1;
-    const size_t smem = (size_t)((d.L + 2) * TM * KP + KC * (16 * NJ + 1)) * sizeof(float);
+    const size_t smem = (size_t)((d.L + 2) * TM * KP + KC * (16 * NJ + 1) +
+                                 (d.act == NB_ACT_SINE ? d.L * TM * KP : 0)) *
+                        sizeof(float);
     auto k = train_f32_kernel<NJ, TM>;
     NB_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k<<<ws.G, 256, smem, s>>>(d, q, labels, (long long)n, alpha, beta, 1.0f / (float)n, tau, ws.partial,

@@ -13,7 +13,8 @@ constexpr unsigned FULL = 0xffffffffu;
 
 template <int NJ, int MI>
 __device__ __forceinline__ void hidden_layer_tile(const float *__restrict__ W, const float *__restrict__ b, int K,
-                                                  int N, const float *ain, float *aout, float *wt, int KP);
+                                                  int N, const float *ain, float *aout, float *wt, int KP, int act,
+                                                  float *cout);
 
 // Forward of one tile of TMF queries starting at row `base` (rows valid) with the
 // decision z >= tau: bits of the tile's 32-row words (base is a multiple of 32),
@@ -40,7 +41,7 @@ __device__ __forceinline__ void fwd_tile(const MlpDesc &d, const float *__restri
     for (int l = 0; l < d.L - 1; l++) {
         const int K = d.w[l], N = d.w[l + 1];
         const float *W = d.p + d.off[l];
-        hidden_layer_tile<NJ, TMF / 16>(W, W + (size_t)N * K, K, N, ain, aout, wt, KP);
+        hidden_layer_tile<NJ, TMF / 16>(W, W + (size_t)N * K, K, N, ain, aout, wt, KP, d.act, nullptr);
         float *tmp = ain;
         ain = aout;
         aout = tmp;
@@ -84,11 +85,14 @@ __device__ __forceinline__ void fwd_tile(const MlpDesc &d, const float *__restri
     }
 }
 
-// hidden layer l of a tile: aout[m][n] = relu(b_n + sum_k W[n][k] ain[m][k]) for MI*16 rows.
-// Thread (tm, tn) owns rows tm + 16 i and neurons tn + 16 j.
+// hidden layer l of a tile: aout[m][n] = act(b_n + sum_k W[n][k] ain[m][k]) for MI*16 rows,
+// act = ReLU or sin (NB_ACT_SINE), and, when cout is given, cout[m][n] = act'(the same sum)
+// -- cos for sine, the backward pass's factor.  Thread (tm, tn) owns rows tm + 16 i and
+// neurons tn + 16 j.
 template <int NJ, int MI>
 __device__ __forceinline__ void hidden_layer_tile(const float *__restrict__ W, const float *__restrict__ b, int K,
-                                                  int N, const float *ain, float *aout, float *wt, int KP) {
+                                                  int N, const float *ain, float *aout, float *wt, int KP, int act,
+                                                  float *cout) {
     constexpr int WS = 16 * NJ + 1;
     const int t = threadIdx.x, tn = t & 15, tm = t >> 4;
     float acc[MI][NJ];
@@ -124,7 +128,17 @@ __device__ __forceinline__ void hidden_layer_tile(const float *__restrict__ W, c
         const int nn = tn + 16 * j;
         if (nn < N)
 #pragma unroll
-            for (int i = 0; i < MI; i++) aout[(tm + 16 * i) * KP + nn] = fmaxf(acc[i][j], 0.f);
+            for (int i = 0; i < MI; i++) {
+                const int o = (tm + 16 * i) * KP + nn;
+                if (act == NB_ACT_SINE) {
+                    float sv, cv;
+                    sincosf(acc[i][j], &sv, &cv);
+                    aout[o] = sv;
+                    if (cout) cout[o] = cv;
+                } else {
+                    aout[o] = fmaxf(acc[i][j], 0.f);
+                }
+            }
     }
 }
 
@@ -137,7 +151,8 @@ __device__ __forceinline__ float sigmoidf(float u) {
 // keeping every layer's activations in shared memory, the asymmetric BCE of Eq. (loss)
 // with its derivative scaled by inv_n (batch mean), and the backward pass accumulating
 // dW and db into `slot` (a gradient partial owned by the calling CTA).
-// smem: [L][TM][KP] activations, 2 x [TM][KP] deltas, [KC][16 NJ + 1] weight chunk.
+// smem: [L][TM][KP] activations, 2 x [TM][KP] deltas, [KC][16 NJ + 1] weight chunk, and for
+// sine networks [L][TM][KP] activation derivatives cos(z) (layer l's at l).
 template <int NJ, int TM>
 __device__ __forceinline__ void train_tile(const MlpDesc &d, const float *__restrict__ q,
                                            const uint32_t *__restrict__ labels, long long base, int rows,
@@ -152,6 +167,8 @@ __device__ __forceinline__ void train_tile(const MlpDesc &d, const float *__rest
     float *dcur = acts + (size_t)L * TM * KP;
     float *dnext = dcur + TM * KP;
     float *wt = dnext + TM * KP;
+    float *cs = wt + KC * WS;  // sine networks only
+    const bool sine = d.act == NB_ACT_SINE;
     const int t = threadIdx.x, tn = t & 15, tm = t >> 4;
     const int w0 = d.w[0];
     __syncthreads();
@@ -163,7 +180,8 @@ __device__ __forceinline__ void train_tile(const MlpDesc &d, const float *__rest
         const int K = d.w[l], N = d.w[l + 1];
         const float *W = d.p + d.off[l];
         hidden_layer_tile<NJ, MI>(W, W + (size_t)N * K, K, N, acts + (size_t)l * TM * KP,
-                                  acts + (size_t)(l + 1) * TM * KP, wt, KP);
+                                  acts + (size_t)(l + 1) * TM * KP, wt, KP, d.act,
+                                  sine ? cs + (size_t)(l + 1) * TM * KP : nullptr);
     }
     __syncthreads();
     const float *aL = acts + (size_t)(L - 1) * TM * KP;
@@ -200,7 +218,10 @@ __device__ __forceinline__ void train_tile(const MlpDesc &d, const float *__rest
                 // the skipped sample must not meet its zero gradient with an inf or NaN
                 // activation in the weight products
                 for (int l = 0; l < L; l++)
-                    for (int k = 0; k < KP; k++) acts[(size_t)l * TM * KP + m * KP + k] = 0.f;
+                    for (int k = 0; k < KP; k++) {
+                        acts[(size_t)l * TM * KP + m * KP + k] = 0.f;
+                        if (sine) cs[(size_t)l * TM * KP + m * KP + k] = 0.f;
+                    }
             }
         }
         dz[m] = g;
@@ -225,7 +246,8 @@ __device__ __forceinline__ void train_tile(const MlpDesc &d, const float *__rest
             for (int e = t; e < TM * KL; e += blockDim.x) {
                 const int m = e / KL, k = e % KL;
                 const float a = aL[m * KP + k];
-                dcur[m * KP + k] = a > 0.f ? dz[m] * __ldg(WL + k) : 0.f;
+                const float dv = dz[m] * __ldg(WL + k);
+                dcur[m * KP + k] = sine ? dv * cs[(size_t)(L - 1) * TM * KP + m * KP + k] : (a > 0.f ? dv : 0.f);
             }
     }
     for (int l = L - 2; l >= 0; l--) {
@@ -246,7 +268,7 @@ __device__ __forceinline__ void train_tile(const MlpDesc &d, const float *__rest
             gW[(size_t)N * K + nn] += s;
         }
         if (l > 0) {
-            // delta_l[m][k] = (sum_n delta_{l+1}[m][n] W[n][k]) 1[a_l[m][k] > 0]
+            // delta_l[m][k] = (sum_n delta_{l+1}[m][n] W[n][k]) act'(z_l[m][k]): 1[a_l > 0] or cos
             float acc[MI][NJ];
 #pragma unroll
             for (int i = 0; i < MI; i++)
@@ -279,7 +301,8 @@ __device__ __forceinline__ void train_tile(const MlpDesc &d, const float *__rest
 #pragma unroll
                     for (int i = 0; i < MI; i++) {
                         const int m = tm + 16 * i;
-                        dnext[m * KP + k] = al[m * KP + k] > 0.f ? acc[i][j] : 0.f;
+                        dnext[m * KP + k] = sine ? acc[i][j] * cs[(size_t)l * TM * KP + m * KP + k]
+                                                 : (al[m * KP + k] > 0.f ? acc[i][j] : 0.f);
                     }
             }
             __syncthreads();

@@ -43,6 +43,7 @@ constexpr unsigned FULL = 0xffffffffu;
 
 struct SplitDesc {
     int in, H, NH;
+    int act;  // hidden activation (NB_ACT_RELU or NB_ACT_SINE)
     const uint8_t *img;
     uint32_t img_bytes;
     const float *p;
@@ -85,7 +86,13 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, Ctl *ct
 constexpr int SEPI = 16;
 constexpr int STHREADS = (SEPI + 1) * 32;
 
-template <int H>
+// hidden activation of the epilogue: ReLU, or sin for NB_ACT_SINE networks
+template <bool SINE>
+__device__ __forceinline__ float act_f(float x) {
+    return SINE ? sinf(x) : fmaxf(x, 0.f);
+}
+
+template <int H, bool SINE>
 __global__ void __launch_bounds__(Single<H>::THREADS, 1)
     fwd_split_kernel(SplitDesc d, const float *__restrict__ q, long long n, TauF tau, float margin,
                      uint32_t *__restrict__ bits, float *__restrict__ logits, nb_query_stats *st,
@@ -237,8 +244,8 @@ __global__ void __launch_bounds__(Single<H>::THREADS, 1)
                         uint32_t hi[16], lo[16];
 #pragma unroll
                         for (int e = 0; e < 16; e++) {
-                            const float a0 = fmaxf(v[2 * e] + b[c * 32 + 2 * e], 0.f);
-                            const float a1 = fmaxf(v[2 * e + 1] + b[c * 32 + 2 * e + 1], 0.f);
+                            const float a0 = act_f<SINE>(v[2 * e] + b[c * 32 + 2 * e]);
+                            const float a1 = act_f<SINE>(v[2 * e + 1] + b[c * 32 + 2 * e + 1]);
                             split_f16x2(a0, a1, hi[e], lo[e]);
                         }
                         tmem_st16(tAhi + c * 16, hi);
@@ -255,7 +262,7 @@ __global__ void __launch_bounds__(Single<H>::THREADS, 1)
                         tmem_ld32(tD + c * 32, v);
                         tmem_ld_wait();
 #pragma unroll
-                        for (int e = 0; e < 32; e++) z = fmaf(head[c * 32 + e], fmaxf(v[e] + b[c * 32 + e], 0.f), z);
+                        for (int e = 0; e < 32; e++) z = fmaf(head[c * 32 + e], act_f<SINE>(v[e] + b[c * 32 + e]), z);
                     }
                     tc_fence_before();
                     z += head[H];
@@ -355,6 +362,7 @@ SplitDesc make_desc(const TcModel *tc, const MlpDesc &d) {
     t.in = d.w[0];
     t.H = d.w[1];
     t.NH = d.L - 1;
+    t.act = d.act;
     t.img = (const uint8_t *)tc->img;
     t.img_bytes = (uint32_t)tc->img_bytes;
     t.p = d.p;
@@ -394,15 +402,21 @@ nb_status nb_split_query(TcModel *tc, const MlpDesc &d, const float *q, int64_t 
     const int ns = t.H == 64 ? Single<64>::NS : Single<128>::NS;
     if (grid > (tiles + ns - 1) / ns) grid = (tiles + ns - 1) / ns;
     if (grid < 1) grid = 1;
+#define NB_SPLIT(HV, SV)                                                                                           \
+    do {                                                                                                          \
+        NB_CUDA(cudaFuncSetAttribute(fwd_split_kernel<HV, SV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+        fwd_split_kernel<HV, SV><<<(unsigned)grid, Single<HV>::THREADS, smem, s>>>(                                 \
+            t, q, (long long)n, tau, margin, bits, logits, st, ws.flag_count, ws.flag_idx, tc->err);              \
+    } while (0)
+    const bool sine = t.act == NB_ACT_SINE;
     if (t.H == 128) {
-        NB_CUDA(cudaFuncSetAttribute(fwd_split_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        fwd_split_kernel<128><<<(unsigned)grid, Single<128>::THREADS, smem, s>>>(t, q, (long long)n, tau, margin, bits, logits,
-                                                                    st, ws.flag_count, ws.flag_idx, tc->err);
+        if (sine) NB_SPLIT(128, true);
+        else NB_SPLIT(128, false);
     } else {
-        NB_CUDA(cudaFuncSetAttribute(fwd_split_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        fwd_split_kernel<64><<<(unsigned)grid, Single<64>::THREADS, smem, s>>>(t, q, (long long)n, tau, margin, bits, logits, st,
-                                                                   ws.flag_count, ws.flag_idx, tc->err);
+        if (sine) NB_SPLIT(64, true);
+        else NB_SPLIT(64, false);
     }
+#undef NB_SPLIT
     NB_CUDA(cudaGetLastError());
     return NB_OK;
 }

@@ -18,11 +18,12 @@ from .inputs import ENC_WIDTH, POINT2, POINT4T
 
 NB_F32, NB_BF16, NB_FP8, NB_F16X3 = 0, 1, 2, 3
 PREC = {"f32": NB_F32, "bf16": NB_BF16, "fp8": NB_FP8, "f16x3": NB_F16X3}
+ACT = {"relu": 0, "sine": 1}  # NB_ACT_RELU, NB_ACT_SINE
 STATUS = {0: "NB_OK", 1: "NB_EINVAL", 2: "NB_ENOMEM", 3: "NB_ECUDA", 4: "NB_ETIMEOUT", 5: "NB_ENUMERIC",
           6: "NB_EUNSUPPORTED"}
 
 # every symbol include/nb.h declares
-EXPORTS = ["nb_model_create", "nb_model_destroy", "nb_model_param_count", "nb_model_set_params",
+EXPORTS = ["nb_model_create", "nb_model_create_act", "nb_model_destroy", "nb_model_param_count", "nb_model_set_params",
            "nb_model_get_params", "nb_model_get_grad", "nb_model_set_tau", "nb_model_get_tau",
            "nb_model_set_adam", "nb_model_state_size", "nb_model_get_state", "nb_model_set_state",
            "nb_label", "nb_train_step", "nb_query", "nb_calibrate", "nb_last_error", "nb_train_step_noalloc",
@@ -72,6 +73,7 @@ def lib():
             st = ctypes.c_int
             sig = {
                 "nb_model_create": ([P, i32, i32, i32, P], st),
+                "nb_model_create_act": ([P, i32, i32, i32, i32, P], st),
                 "nb_model_destroy": ([P], st),
                 "nb_model_param_count": ([P], i64),
                 "nb_model_set_params": ([P, P, i64], st),
@@ -201,13 +203,15 @@ def label(shape: Shape, kind: int, q: torch.Tensor, out: torch.Tensor | None = N
 class Model:
     """A bounding network h (nb_model)."""
 
-    def __init__(self, widths, infer_prec="f32", train_prec="f32"):
+    def __init__(self, widths, infer_prec="f32", train_prec="f32", activation="relu"):
         self.widths = [int(w) for w in widths]
         self.infer_prec = PREC[infer_prec] if isinstance(infer_prec, str) else int(infer_prec)
         self.train_prec = PREC[train_prec] if isinstance(train_prec, str) else int(train_prec)
+        self.activation = ACT[activation] if isinstance(activation, str) else int(activation)
         w = (ctypes.c_int32 * len(self.widths))(*self.widths)
         h = ctypes.c_void_p()
-        _check(lib().nb_model_create(w, len(self.widths) - 1, self.infer_prec, self.train_prec, ctypes.byref(h)))
+        _check(lib().nb_model_create_act(w, len(self.widths) - 1, self.infer_prec, self.train_prec, self.activation,
+                                         ctypes.byref(h)))
         self._h = h
         self.P = int(lib().nb_model_param_count(h))
 

@@ -48,6 +48,12 @@ def test_host_side_argument_errors(lib):
     w = (ctypes.c_int32 * 3)(3, 300, 1)
     assert lib.nb_model_create(w, 2, 0, 0, ctypes.byref(h)) == 1
     assert lib.nb_model_create(w, 9, 0, 0, ctypes.byref(h)) == 1
+    # activations: unknown -> NB_EINVAL; sine networks with a BF16/FP8 path -> NB_EUNSUPPORTED
+    w = (ctypes.c_int32 * 3)(3, 16, 1)
+    assert lib.nb_model_create_act(w, 2, 0, 0, 2, ctypes.byref(h)) == 1
+    assert lib.nb_model_create_act(w, 2, 0, 1, 1, ctypes.byref(h)) == 6   # sine, BF16 training
+    assert lib.nb_model_create_act(w, 2, 2, 0, 1, ctypes.byref(h)) == 6   # sine, FP8 inference
+    assert lib.nb_model_create_act(w, 2, 1, 0, 1, ctypes.byref(h)) == 6   # sine, BF16 inference
     # null model
     lib.nb_query.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_float, ctypes.c_void_p,
                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
