@@ -1,7 +1,13 @@
 // FP8 (E4M3) tensor-core forward of the bounding network h (Sec. 3.4 "Architecture").
 //
 // The hidden-to-hidden layers run on the tensor cores with E4M3 operands and FP32
-// accumulation (tcgen05.mma kind::f8f6f4).  Scales are powers of two, so applying and
+// accumulation (tcgen05.mma kind::f8f6f4), each operand split into two E4M3 terms,
+// x = x_hi + x_lo with x_lo = E4M3(x - x_hi), and three products per k-step,
+// a_hi w_hi + a_hi w_lo + a_lo w_hi (the dropped a_lo w_lo is ~2^-8 relative): about 8
+// significant bits per operand instead of 4.  On trained networks one E4M3 term was off
+// by up to ~20 in the logit (3 mantissa bits against logits in the hundreds, with
+// cancellation); two terms bring that below 1 for 1.5x the BF16 tensor work of one
+// product (E4M3 runs at twice the BF16 rate).  Scales are powers of two, so applying and
 // removing them is exact.  Every query row has its own activation scale r (max_k a_k r in
 // [128, 256), E4M3's largest finite value being 448).  Every weight row n of layer l has its
 // own s_n, and the layer's outputs are kept scaled by it: the epilogue computes
@@ -14,15 +20,19 @@
 // on the CUDA cores.
 //
 // Placement (one persistent CTA per SM): shared memory holds the first layer's split image
-// and the E4M3 images of the hidden-to-hidden layers (64 KB each at width 256), loaded once
-// by the bulk-copy engine; tensor memory holds the FP32 accumulator (H columns) and the next
-// layer's activations (H/4 columns of E4M3, or the split-FP16 query for the first layer),
-// read by the MMA as its A operand.  Warps 0-7 are the epilogue: warps w and w + 4 share the
-// TMEM lanes of quarter w mod 4 (one query row per lane) and take one half of the columns
-// each, exchanging their partial row maxima and head sums through shared memory; warp 8
-// allocates TMEM, loads the weights and issues the MMAs.  One tile is in flight: its layers
-// alternate between the tensor pipe and the epilogue.  All waits are bounded; on expiry the
-// kernel records NB_ETIMEOUT, drains the tensor pipe and frees TMEM before returning.
+// (loaded once) and two stages of the streamed hidden-layer weights: the two-term E4M3
+// images (2 H^2 bytes per layer, 384 KB for three 256-wide layers -- more than shared
+// memory) pass through in chunks of one 128-column K-block of both terms, 2 x H x 128
+// bytes, brought in by the bulk-copy engine one chunk ahead of the products that read it.
+// Tensor memory holds the FP32 accumulator (H columns) and the next layer's activations
+// (H/4 columns per E4M3 term, or the split-FP16 query for the first layer), read by the
+// MMA as its A operand.  Warps 0-7 are the epilogue: warps w and w + 4 share the TMEM lanes
+// of quarter w mod 4 (one query row per lane) and take one half of the columns each,
+// exchanging their partial row maxima and head sums through shared memory; warp 8
+// allocates TMEM and issues the MMAs; warp 9 streams the weight chunks.  One tile is in
+// flight: its layers alternate between the tensor pipe and the epilogue.  All waits are
+// bounded; on expiry the kernel records NB_ETIMEOUT, waits (bounded) for its copies in
+// flight, drains the tensor pipe and frees TMEM before returning.
 #include <cuda_fp16.h>
 
 #include "tc.cuh"
@@ -34,14 +44,14 @@ using namespace nbtc;
 
 constexpr int TILE_M = 128;
 constexpr int NEPI = 8;
-constexpr int THREADS = (NEPI + 1) * 32;
+constexpr int THREADS = (NEPI + 2) * 32;  // epilogue warps, the MMA warp, the weight-stream warp
 constexpr unsigned SPIN_LIMIT = 1u << 22;
 constexpr unsigned FULL = 0xffffffffu;
 constexpr uint32_t CTL_BYTES = 2048;  // control block and the row-exchange buffer
 
 struct Fp8Desc {
     int in, H, NHH;        // input width, hidden width, hidden-to-hidden layers
-    const uint8_t *img;    // layer 0 split image, then NHH E4M3 images
+    const uint8_t *img;    // layer 0 split image, then NHH two-term E4M3 images in chunk order
     uint32_t img_bytes;
     const float *inv_sw;   // [NHH][H] 1 / s_n of every E4M3 weight row
     const float *bs;       // [NHH][H] b_n s_n: the folded biases
@@ -50,13 +60,14 @@ struct Fp8Desc {
     int off[NB_MAXL];
 };
 
-// layer 0: H rows x 128 B (split FP16, K = 64); layer l >= 1: H/128 blocks of H rows x 128 B
-__host__ __device__ inline uint32_t fp8_off(int H, int l) {
-    return l == 0 ? 0u : (uint32_t)(H * 128 + (l - 1) * H * H);
-}
+// Image: layer 0 as H rows x 128 B (split FP16, K = 64); then, for each E4M3 layer, H / 128
+// chunks, chunk kb holding K-block kb (columns 128 kb ..) of the hi term then of the lo term,
+// H rows x 128 B each, 128-byte swizzled -- so the chunks of all layers follow each other
+// in the order the products read them.  fp8_chunk is the bytes of one chunk.
+__host__ __device__ inline uint32_t fp8_chunk(int H) { return (uint32_t)(2 * H * 128); }
 
 struct Ctl {
-    uint64_t wbar, aready, accfull, drain;
+    uint64_t wbar, aready, accfull, drain, full[2], empty[2];
     uint64_t pair[4];  // row-exchange handshake of the two warps of each lane quarter
     uint32_t tmem;
     int abort;
@@ -116,6 +127,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     Ctl *ctl = reinterpret_cast<Ctl *>(smem_raw);
     float *xbuf = reinterpret_cast<float *>(smem_raw + 128);  // [8 warps][32 lanes]
     uint8_t *Wimg = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023) + CTL_BYTES;
+    const uint32_t L0_BYTES = (uint32_t)H * 128, CHUNK = fp8_chunk(H), TERM = (uint32_t)H * 128;
+    const uint32_t stage0 = smem_u32(Wimg) + L0_BYTES;  // two stages of CHUNK bytes
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long ntiles = (n + TILE_M - 1) / TILE_M;
@@ -127,6 +140,10 @@ __global__ void __launch_bounds__(THREADS, 1)
         mbar_init(bar_ar, NEPI);
         mbar_init(bar_af, 1);
         mbar_init(bar_drain, 1);
+        for (int i = 0; i < 2; i++) {
+            mbar_init(smem_u32(&ctl->full[i]), 1);
+            mbar_init(smem_u32(&ctl->empty[i]), 1);
+        }
         for (int i = 0; i < 4; i++) mbar_init(smem_u32(&ctl->pair[i]), 64);
         ctl->abort = 0;
         fence_mbar_init();
@@ -141,17 +158,44 @@ __global__ void __launch_bounds__(THREADS, 1)
     const uint32_t tmem = ctl->tmem;
     const int NL = d.NHH + 1;  // tensor-core layers: the first layer and the E4M3 layers
 
-    if (warp == NEPI) {
+    const int CPT = d.NHH * (H / 128);  // weight chunks per tile
+    const long long my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    if (warp == NEPI + 1) {
+        // ------------------------------------------------ weight stream: chunk c -> stage c & 1
         if (lane == 0) {
-            mbar_expect_tx(bar_w, d.img_bytes);
-            for (uint32_t o = 0; o < d.img_bytes; o += 16384)
-                bulk_g2s(smem_u32(Wimg) + o, d.img + o, min(16384u, d.img_bytes - o), bar_w);
+            const long long total = my_tiles * CPT;
+            bool ok = true;
+            long long issued = 0;
+            for (long long c = 0; c < total && ok; c++) {
+                const int sidx = (int)(c & 1);
+                if (c >= 2) ok = wait_bounded(smem_u32(&ctl->empty[sidx]), (uint32_t)(((c >> 1) - 1) & 1), ctl, err);
+                if (!ok) break;
+                const uint32_t bar = smem_u32(&ctl->full[sidx]);
+                mbar_expect_tx(bar, CHUNK);
+                const uint8_t *src = d.img + L0_BYTES + (size_t)(c % CPT) * CHUNK;
+                for (uint32_t o = 0; o < CHUNK; o += 16384)
+                    bulk_g2s(stage0 + sidx * CHUNK + o, src + o, min(16384u, CHUNK - o), bar);
+                issued = c + 1;
+            }
+            // the copies of the last two chunks (every earlier one has been consumed) have
+            // landed before the CTA may exit
+            for (long long c = issued - 2; c < issued; c++)
+                if (c >= 0) wait_bounded(smem_u32(&ctl->full[c & 1]), (uint32_t)((c >> 1) & 1), ctl, err);
+        }
+        __syncwarp();
+    } else if (warp == NEPI) {
+        // ------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            mbar_expect_tx(bar_w, L0_BYTES);
+            for (uint32_t o = 0; o < L0_BYTES; o += 16384)
+                bulk_g2s(smem_u32(Wimg) + o, d.img + o, min(16384u, L0_BYTES - o), bar_w);
             bool ok = wait_bounded(bar_w, 0, ctl, err);
             uint32_t pa = 0;
             constexpr uint32_t id16 = idesc_f16(TILE_M, H);
             constexpr uint32_t id8 = idesc_e4m3(TILE_M, H);
             const uint32_t wbase = smem_u32(Wimg);
-            const uint32_t tD = tmem, tA = tmem + H;
+            const uint32_t tD = tmem, tA = tmem + H, tA1 = tmem + H + H / 4;
+            long long c = 0;
             for (long long tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
                 for (int l = 0; l < NL && ok; l++) {
                     ok = wait_bounded(bar_ar, pa, ctl, err);
@@ -162,10 +206,19 @@ __global__ void __launch_bounds__(THREADS, 1)
                         for (int j = 0; j < 3; j++)
                             mma_f16_ts(tD, tA + 8 * j, sdesc_sw128(wbase + 32 * j), id16, j > 0 ? 1u : 0u);
                     } else {
-                        const uint32_t wl = wbase + fp8_off(H, l);
-                        for (int j = 0; j < H / 32; j++) {
-                            const uint32_t kb = j >> 2, within = (j & 3) * 32;
-                            mma_f8_ts(tD, tA + 8 * j, sdesc_sw128(wl + kb * (H * 128) + within), id8, j > 0 ? 1u : 0u);
+                        for (int kb = 0; kb < H / 128 && ok; kb++, c++) {
+                            const int sidx = (int)(c & 1);
+                            ok = wait_bounded(smem_u32(&ctl->full[sidx]), (uint32_t)((c >> 1) & 1), ctl, err);
+                            if (!ok) break;
+                            tc_fence_after();
+                            const uint32_t whi = stage0 + sidx * CHUNK, wlo = whi + TERM;
+                            for (int j = 0; j < 4; j++) {  // k-steps of 32 within the K-block
+                                const uint32_t ks = (uint32_t)(kb * 4 + j), within = (uint32_t)j * 32;
+                                mma_f8_ts(tD, tA + 8 * ks, sdesc_sw128(whi + within), id8, (kb | j) ? 1u : 0u);
+                                mma_f8_ts(tD, tA + 8 * ks, sdesc_sw128(wlo + within), id8, 1u);
+                                mma_f8_ts(tD, tA1 + 8 * ks, sdesc_sw128(whi + within), id8, 1u);
+                            }
+                            mma_commit(smem_u32(&ctl->empty[sidx]));  // the stage may be refilled
                         }
                     }
                     mma_commit(bar_af);
@@ -180,7 +233,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int wq = warp & 3, half = warp >> 2;
         const int r = wq * 32 + lane;
         const uint32_t trow = tmem + ((uint32_t)(wq * 32) << 16);
-        const uint32_t tD = trow + half * HALF, tA = trow + H;
+        const uint32_t tD = trow + half * HALF, tA = trow + H, tA1 = trow + H + H / 4;
         const int c0 = half * HALF;  // first column (neuron) of this warp
         uint32_t ph = 0, pp = 0;
         unsigned long long c_in = 0, c_flag = 0, c_nf = 0;
@@ -249,10 +302,10 @@ __global__ void __launch_bounds__(THREADS, 1)
                     m = fmaxf(m, mo);
                     float inv_next;
                     const float rs = pow2_scale(m, inv_next);
-                    // 64 activations -> 16 columns of E4M3 at column (first neuron) / 4
+                    // 64 activations -> 16 columns of each E4M3 term at column (first neuron) / 4
 #pragma unroll
                     for (int cp = 0; cp < HALF / 64; cp++) {
-                        uint32_t w16[16];
+                        uint32_t whi[16], wlo[16];
 #pragma unroll
                         for (int hh = 0; hh < 2; hh++) {
                             float v[32];
@@ -267,10 +320,11 @@ __global__ void __launch_bounds__(THREADS, 1)
                                     const float t = fmaf(v[4 * e + u], inv_r, __ldg(b + nn));
                                     a[u] = fmaxf(t, 0.f) * rs;
                                 }
-                                w16[hh * 8 + e] = pack_e4m3x4(a[0], a[1], a[2], a[3]);
+                                split_e4m3x4(a, whi[hh * 8 + e], wlo[hh * 8 + e]);
                             }
                         }
-                        tmem_st16(tA + (uint32_t)(c0 + cp * 64) / 4, w16);
+                        tmem_st16(tA + (uint32_t)(c0 + cp * 64) / 4, whi);
+                        tmem_st16(tA1 + (uint32_t)(c0 + cp * 64) / 4, wlo);
                     }
                     tmem_st_wait();
                     inv_r = inv_next;
@@ -370,7 +424,8 @@ __global__ void fp8_head_kernel(Fp8Desc d, float *hw) {
 }
 
 // FP32 master weights -> operand images (one thread per 16-byte chunk): the first layer as
-// [W_hi | W_hi | W_lo | 0] in FP16 (K = 64), the others as E4M3 of W_nk s_n
+// [W_hi | W_hi | W_lo | 0] in FP16 (K = 64), the others as the two E4M3 terms of
+// W_nk s_n / s'_k (hi = E4M3 of it, lo = E4M3 of the remainder)
 __global__ void pack_fp8_kernel(Fp8Desc d, uint8_t *img) {
     const int H = d.H;
     const uint32_t nchunks = d.img_bytes / 16;
@@ -399,9 +454,10 @@ __global__ void pack_fp8_kernel(Fp8Desc d, uint8_t *img) {
             o.w = pack_f16(v[6], v[7]);
         } else {
             const uint32_t rel = byte - H * 128;
-            const int l = 1 + (int)(rel / (uint32_t)(H * H));
-            const uint32_t local = rel % (uint32_t)(H * H);
-            const uint32_t kb = local / (uint32_t)(H * 128), rem = local % (uint32_t)(H * 128);
+            const int l = 1 + (int)(rel / (uint32_t)(2 * H * H));
+            const uint32_t local = rel % (uint32_t)(2 * H * H);
+            const uint32_t kb = local / fp8_chunk(H), in_chunk = local % fp8_chunk(H);
+            const uint32_t term = in_chunk / (uint32_t)(H * 128), rem = in_chunk % (uint32_t)(H * 128);
             const uint32_t nrow = rem / 128, pc = (rem % 128) / 16, c = pc ^ (nrow & 7);
             const int k0 = (int)(kb * 128 + c * 16);
             const float *W = d.p + d.off[l] + (size_t)nrow * H + k0;
@@ -412,7 +468,12 @@ __global__ void pack_fp8_kernel(Fp8Desc d, uint8_t *img) {
             for (int e = 0; e < 16; e++) v[e] = (prev ? W[e] * prev[e] : W[e]) * s;  // W_nk s_n / s'_k
             uint32_t w[4];
 #pragma unroll
-            for (int e = 0; e < 4; e++) w[e] = pack_e4m3x4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+            for (int e = 0; e < 4; e++) {
+                const float v4[4] = {v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]};
+                uint32_t hi, lo;
+                split_e4m3x4(v4, hi, lo);
+                w[e] = term == 0 ? hi : lo;
+            }
             o = make_uint4(w[0], w[1], w[2], w[3]);
         }
         *reinterpret_cast<uint4 *>(img + byte) = o;
@@ -443,8 +504,11 @@ int sm_count() {
 
 }  // namespace
 
-size_t nb_fp8_img_bytes(int H, int NHH) { return (size_t)H * 128 + (size_t)NHH * H * H; }
-size_t nb_fp8_smem_bytes(int H, int NHH) { return 1024 + CTL_BYTES + nb_fp8_img_bytes(H, NHH); }
+size_t nb_fp8_img_bytes(int H, int NHH) { return (size_t)H * 128 + (size_t)NHH * 2 * H * H; }
+size_t nb_fp8_smem_bytes(int H, int NHH) {
+    (void)NHH;
+    return 1024 + CTL_BYTES + (size_t)H * 128 + 2 * (size_t)fp8_chunk(H);
+}
 
 nb_status nb_fp8_refresh(TcModel *tc, const MlpDesc &d, cudaStream_t s) {
     const Fp8Desc t = make_desc(tc, d);

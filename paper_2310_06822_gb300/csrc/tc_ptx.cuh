@@ -240,3 +240,26 @@ __device__ __forceinline__ void unpack_bf16(uint32_t w, float &lo, float &hi) {
 }
 
 }  // namespace nbtc
+
+namespace nbtc {
+
+// the four FP32 values of a packed E4M3x4 word (e0 in the lowest byte); exact
+__device__ __forceinline__ void unpack_e4m3x4(uint32_t w, float (&f)[4]) {
+    const uint16_t lo = (uint16_t)(w & 0xffffu), hi = (uint16_t)(w >> 16);
+    uint32_t h01, h23;
+    asm("cvt.rn.f16x2.e4m3x2 %0, %1;" : "=r"(h01) : "h"(lo));
+    asm("cvt.rn.f16x2.e4m3x2 %0, %1;" : "=r"(h23) : "h"(hi));
+    unpack_f16(h01, f[0], f[1]);
+    unpack_f16(h23, f[2], f[3]);
+}
+
+// two-term E4M3 split of four FP32 values: hi = E4M3(v), lo = E4M3(v - hi), so that
+// hi + lo carries about 8 significant bits of v (both rounded to nearest, saturating)
+__device__ __forceinline__ void split_e4m3x4(const float (&v)[4], uint32_t &hi, uint32_t &lo) {
+    hi = pack_e4m3x4(v[0], v[1], v[2], v[3]);
+    float q[4];
+    unpack_e4m3x4(hi, q);
+    lo = pack_e4m3x4(v[0] - q[0], v[1] - q[1], v[2] - q[2], v[3] - q[3]);
+}
+
+}  // namespace nbtc
