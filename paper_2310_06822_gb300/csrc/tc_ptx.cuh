@@ -263,3 +263,15 @@ __device__ __forceinline__ void split_e4m3x4(const float (&v)[4], uint32_t &hi, 
 }
 
 }  // namespace nbtc
+
+namespace nbtc {
+
+// Ties the registers of a tcgen05.ld to the tcgen05.wait::ld before it: an empty volatile
+// asm redefines every value after the wait, so the compiler cannot move a use of them
+// above the wait (volatile asm statements keep their order).
+__device__ __forceinline__ void tmem_reg_fence(float (&v)[32]) {
+#pragma unroll
+    for (int i = 0; i < 32; i++) asm volatile("" : "+f"(v[i]));
+}
+
+}  // namespace nbtc

@@ -235,35 +235,75 @@ __global__ void __launch_bounds__(Single<H>::THREADS, 1)
                 if (!ok) break;
                 tc_fence_after();
                 const float *b = bias + l * H;
-                if (l < d.NH - 1) {
+                // hidden layer: relu(acc + b) split into FP16 hi / lo for the next layer's A
+                // operand; head: z += head . relu(acc + b)
+                auto hidden_chunk = [&](const float(&v)[32], int c) {
+                    const float4 *b4 = reinterpret_cast<const float4 *>(b + c * 32);
+                    uint32_t hi[16], lo[16];
 #pragma unroll
-                    for (int c = 0; c < H / 32; c++) {
-                        float v[32];
-                        tmem_ld32(tD + c * 32, v);
-                        tmem_ld_wait();
-                        uint32_t hi[16], lo[16];
-#pragma unroll
-                        for (int e = 0; e < 16; e++) {
-                            const float a0 = act_f<SINE>(v[2 * e] + b[c * 32 + 2 * e]);
-                            const float a1 = act_f<SINE>(v[2 * e + 1] + b[c * 32 + 2 * e + 1]);
-                            split_f16x2(a0, a1, hi[e], lo[e]);
-                        }
-                        tmem_st16(tAhi + c * 16, hi);
-                        tmem_st16(tAlo + c * 16, lo);
+                    for (int e = 0; e < 8; e++) {
+                        const float4 bb = b4[e];
+                        split_f16x2(act_f<SINE>(v[4 * e] + bb.x), act_f<SINE>(v[4 * e + 1] + bb.y), hi[2 * e],
+                                    lo[2 * e]);
+                        split_f16x2(act_f<SINE>(v[4 * e + 2] + bb.z), act_f<SINE>(v[4 * e + 3] + bb.w), hi[2 * e + 1],
+                                    lo[2 * e + 1]);
                     }
-                    tmem_st_wait();
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(bar_ar[s]);
+                    tmem_st16(tAhi + c * 16, hi);
+                    tmem_st16(tAlo + c * 16, lo);
+                };
+                auto head_chunk = [&](const float(&v)[32], int c) {
+                    const float4 *b4 = reinterpret_cast<const float4 *>(b + c * 32);
+                    const float4 *h4 = reinterpret_cast<const float4 *>(head + c * 32);
+#pragma unroll
+                    for (int e = 0; e < 8; e++) {
+                        const float4 bb = b4[e], hh = h4[e];
+                        z = fmaf(hh.x, act_f<SINE>(v[4 * e] + bb.x), z);
+                        z = fmaf(hh.y, act_f<SINE>(v[4 * e + 1] + bb.y), z);
+                        z = fmaf(hh.z, act_f<SINE>(v[4 * e + 2] + bb.z), z);
+                        z = fmaf(hh.w, act_f<SINE>(v[4 * e + 3] + bb.w), z);
+                    }
+                };
+                const bool last = l == d.NH - 1;
+                auto chunk = [&](const float(&v)[32], int c) {
+                    if (last) head_chunk(v, c);
+                    else hidden_chunk(v, c);
+                };
+                if constexpr (H == 128) {
+                    // the accumulator's four 32-column chunks are read one ahead: chunk c + 1's
+                    // TMEM load is in flight while chunk c is converted
+                    float va[32], vb[32];
+                    tmem_ld32(tD, va);
+                    tmem_ld_wait();
+                    tmem_reg_fence(va);
+                    tmem_ld32(tD + 32, vb);
+                    chunk(va, 0);
+                    tmem_ld_wait();
+                    tmem_reg_fence(vb);
+                    tmem_ld32(tD + 64, va);
+                    chunk(vb, 1);
+                    tmem_ld_wait();
+                    tmem_reg_fence(va);
+                    tmem_ld32(tD + 96, vb);
+                    chunk(va, 2);
+                    tmem_ld_wait();
+                    tmem_reg_fence(vb);
+                    chunk(vb, 3);
                 } else {
 #pragma unroll
                     for (int c = 0; c < H / 32; c++) {
                         float v[32];
                         tmem_ld32(tD + c * 32, v);
                         tmem_ld_wait();
-#pragma unroll
-                        for (int e = 0; e < 32; e++) z = fmaf(head[c * 32 + e], act_f<SINE>(v[e] + b[c * 32 + e]), z);
+                        tmem_reg_fence(v);
+                        chunk(v, c);
                     }
+                }
+                if (!last) {
+                    tmem_st_wait();
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(bar_ar[s]);
+                } else {
                     tc_fence_before();
                     z += head[H];
                 }
