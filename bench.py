@@ -536,10 +536,10 @@ def run_c2e(args):
     sc = I.make_scene(SEED_SCENE + 10, 16, 3, 0.2, 0.5)
     shape = nb.Shape(sc, dev)
     late_w, early_w = [3, 128, 128, 128, 128, 1], [3, 64, 64, 1]
-    T = args.train_steps if args.train_steps != TRAIN_STEPS else 2000
+    T = args.train_steps if args.train_steps != TRAIN_STEPS else 10000
     late_t = nb.Model(late_w, infer_prec="f32", train_prec="bf16")
     late_t.set_params(I.init_params(SEED_INIT, late_w))
-    early = nb.Model(early_w)
+    early = nb.Model(early_w, train_prec="bf16")
     early.set_params(I.init_params(SEED_INIT + 1, early_w))
     for t in range(T):
         q = nb.sample(I.POINT3, BATCH, SEED_TRAIN, first=t * BATCH)
@@ -564,6 +564,7 @@ def run_c2e(args):
     ms, clocks = ctx.timed(lambda: nb.query_early_out(early, late, eq, margin_early=1e-3, margin_late=MARGIN,
                                                       out=out), args.steps, args.warmup)
     plain_ms = ctx.time_ms(lambda: late.query(eq, margin=MARGIN, out=out), max(3, args.steps // 4))
+    early_ms = ctx.time_ms(lambda: early.query(eq, margin=1e-3, out=out), max(3, args.steps // 4))
     dplain = nb.bits_to_numpy(late.query(eq, margin=MARGIN), n)
     # the same two networks as a bound and an inverted bound: the broad-phase three-way
     # class of Sec. 4.4 (certainly outside / certainly inside / neither)
@@ -588,6 +589,11 @@ def run_c2e(args):
                  "early_inside_fraction": est["n_early_inside"] / n,
                  "without_early_out_queries_per_s": n / (plain_ms / 1000.0),
                  "speedup_vs_without": plain_ms / ms, "cpu_baseline": None, "e2e": None,
+                 "inside_fraction": float(y.mean()), "early_network_alone_ms": early_ms, "late_network_alone_ms": plain_ms,
+                 # the early-out saves f T_late and costs the early network plus the compaction,
+                 # gather, scatter and host hand-over, C = T_total - (1 - f) T_late: it pays once the
+                 # settled fraction f exceeds C / T_late
+                 "break_even_settled_fraction": (ms - (1.0 - est["n_early_inside"] / n) * plain_ms) / plain_ms,
                  "three_way": {"queries_per_s": n / (tw_ms / 1000.0), "certainly_out": int(tw[0]),
                                "certainly_in": int(tw[1]), "neither": int(tw[2]), "conflicts": int(tw[3]),
                                "certain_and_wrong": int(np.sum((tc == 0) & y) + np.sum((tc == 1) & ~y)),
