@@ -3,7 +3,8 @@
 // Alg. 1 labels a region by Any(f(SampleRegion(r))); here the region is tested
 // against every ball analytically, in exact integer arithmetic on the 2^-qexp grid,
 // so the label is the query function itself, inclusive of the surface (Sec. 3.1:
-// the indicator is 1 inside and on the surface).
+// the indicator is 1 inside and on the surface).  An FP32 pre-filter settles the
+// tests that are far from tangency (exact.cuh); only the rest take the integer path.
 #include "common.cuh"
 #include "exact.cuh"
 
@@ -17,6 +18,7 @@ __global__ void __launch_bounds__(256) label_kernel(const float *__restrict__ q,
                                                     const float *__restrict__ rad, const float *__restrict__ vel,
                                                     uint32_t *__restrict__ bits, nb_label_stats *st) {
     extern __shared__ SphI sph[];
+    SphF *sphf = reinterpret_cast<SphF *>(sph + ns);  // the same balls as exact floats for the filter
     __shared__ int scene_bad;
     const float scale = ldexpf(1.0f, qexp);
     if (threadIdx.x == 0) scene_bad = 0;
@@ -29,6 +31,10 @@ __global__ void __launch_bounds__(256) label_kernel(const float *__restrict__ q,
         if (vel)
             for (int i = 0; i < 3; i++) ok &= to_grid(vel[s * 3 + i], scale, S.v[i]);
         sph[s] = S;
+        SphF F;
+        for (int i = 0; i < 3; i++) F.c[i] = i < dim ? cen[s * dim + i] : 0.f;
+        F.rr = __fmul_rn(rad[s], rad[s]);
+        sphf[s] = F;
         if (!ok) atomicOr(&scene_bad, 1);
     }
     __syncthreads();
@@ -43,15 +49,20 @@ __global__ void __launch_bounds__(256) label_kernel(const float *__restrict__ q,
         int hit = 0;
         if (i < n) {
             int Q[W];
+            float qf[W];
             bool ok = !bad;
 #pragma unroll
-            for (int k = 0; k < W; k++) ok &= to_grid(q[i * W + k], scale, Q[k]);
+            for (int k = 0; k < W; k++) {
+                qf[k] = q[i * W + k];
+                ok &= to_grid(qf[k], scale, Q[k]);
+            }
             if (KIND == NB_BOX3) ok = ok && Q[3] >= 0 && Q[4] >= 0 && Q[5] >= 0;
             if (!ok) {
                 hit = 1;
                 ninv++;
             } else {
-                hit = union_hit<KIND>(Q, sph, ns, qexp);
+                // FP32 pre-filter, the exact integer test where it cannot be sure
+                hit = union_hit_filtered<KIND>(qf, Q, sphf, sph, ns, qexp);
             }
         }
         const unsigned b = __ballot_sync(0xffffffffu, hit);
@@ -74,7 +85,7 @@ template <int KIND, int W>
 nb_status launch(const nb_shape *sh, const float *q, int64_t n, uint32_t *bits, nb_label_stats *st,
                  cudaStream_t s) {
     auto k = label_kernel<KIND, W>;
-    const size_t smem = (size_t)sh->n_spheres * sizeof(SphI);
+    const size_t smem = (size_t)sh->n_spheres * (sizeof(SphI) + sizeof(SphF));
     NB_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int dev = 0, sms = 148;
     NB_CUDA(cudaGetDevice(&dev));
