@@ -228,7 +228,11 @@ nb_status nb_selftest_bounded_wait(int32_t polls, void *stream);
 
 /* nb_query for queries in host memory: host_q [n][enc width] and host_bits
  * ((n + 31) / 32 words) are host buffers; pinned (page-locked) ones let the copies overlap
- * the forward.  The queries are streamed in chunks of chunk_rows (0: 2^22; rounded up to
+ * the forward.  With chunk_rows 0, host_q pinned and a coherent host link (NVLink-C2C,
+ * reported as native host atomics), the forward and the re-check read the rows in place
+ * from host memory; the bits are decided into a library-owned device buffer and copied
+ * back.  The caller must not write host_q during the call.  Otherwise (or with
+ * chunk_rows > 0) the queries are streamed in chunks of chunk_rows (0: 2^22; rounded up to
  * a multiple of 32; the first chunk a quarter of that, so the forward starts early)
  * through two library-owned device staging buffers: while one chunk is
  * decided on `stream`, the next is copied in on a library-owned copy stream, and each

@@ -122,6 +122,9 @@ struct nb_model {
     uint32_t *hq_bits[2] = {nullptr, nullptr};
     nb_query_stats *hq_stats = nullptr;  // [3]: one per chunk buffer and the running sum
     int64_t hq_chunk = 0;
+    // nb_query_host reading pinned host queries in place: the device copy of the bits
+    uint32_t *zc_bits = nullptr;
+    int64_t zc_words = 0;
 };
 
 static MlpDesc desc_of(const nb_model *m) {
@@ -181,6 +184,7 @@ static void free_model(nb_model *m) {
         if (m->hq_done[b]) cudaEventDestroy(m->hq_done[b]);
     }
     cudaFree(m->hq_stats);
+    cudaFree(m->zc_bits);
     if (m->hq_stream) cudaStreamDestroy(m->hq_stream);
     nb_tc_free(&m->tc);
     delete m;
@@ -510,6 +514,60 @@ static nb_status ensure_host_pipe(nb_model *m, int64_t chunk) {
     return NB_OK;
 }
 
+// The device address of pinned, mapped host memory when the link to the host is coherent
+// (NVLink-C2C on a Grace-Blackwell node: native host atomics), else null.  Over C2C the
+// forward reads its query rows from host memory at the rate it consumes them, so the
+// staging copy buys nothing; over PCIe it would starve the forward.
+static const float *mapped_host_rows(const float *host_q) {
+    int dev = 0, coherent = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&coherent, cudaDevAttrHostNativeAtomicSupported, dev) != cudaSuccess || !coherent) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, host_q) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? (const float *)a.devicePointer : nullptr;
+}
+
+// nb_query on rows the device reads in place from mapped host memory; the bits go to a
+// library-owned device buffer and are copied back once final.  Synchronous.
+static nb_status query_in_place(nb_model *m, const float *dq, int64_t n, float margin, uint32_t *host_bits,
+                                nb_query_stats *host_stats, cudaStream_t S) {
+    const int64_t words = (n + 31) / 32;
+    nb_status st = ensure_host_pipe(m, 32);  // the copy stream, events and statistics
+    if (st != NB_OK) return st;
+    if (words > m->zc_words) {
+        NB_CUDA(cudaStreamSynchronize(S));
+        cudaFree(m->zc_bits);
+        m->zc_bits = nullptr;
+        m->zc_words = 0;
+        if (cudaMalloc(&m->zc_bits, (size_t)words * sizeof(uint32_t)) != cudaSuccess) {
+            cudaGetLastError();
+            return nb_fail(NB_ENOMEM, "nb_query_host: bits buffer allocation failed");
+        }
+        m->zc_words = words;
+    }
+    nb_query_stats *sum = m->hq_stats + 2;
+    st = nb_query(m, dq, n, margin, m->zc_bits, nullptr, host_stats ? sum : nullptr, S);
+    if (st != NB_OK) {
+        cudaStreamSynchronize(S);  // kernels already queued may still read the caller's rows
+        return st;
+    }
+    if (cudaMemcpyAsync(host_bits, m->zc_bits, (size_t)words * sizeof(uint32_t), cudaMemcpyDeviceToHost, S) !=
+            cudaSuccess ||
+        (host_stats &&
+         cudaMemcpyAsync(host_stats, sum, sizeof(nb_query_stats), cudaMemcpyDeviceToHost, S) != cudaSuccess)) {
+        cudaStreamSynchronize(S);
+        return nb_fail(NB_ECUDA, "nb_query_host: copy failed");
+    }
+    NB_CUDA(cudaStreamSynchronize(S));
+    return nb_tc_check(&m->tc);
+}
+
 extern "C" nb_status nb_query_host(nb_model *m, const float *host_q, int64_t n, float margin, uint32_t *host_bits,
                                    nb_query_stats *host_stats, int64_t chunk_rows, void *stream) {
     if (!m) return nb_fail(NB_EINVAL, "nb_query_host: null model");
@@ -518,6 +576,10 @@ extern "C" nb_status nb_query_host(nb_model *m, const float *host_q, int64_t n, 
     if (chunk_rows < 0) return nb_fail(NB_EINVAL, "nb_query_host: chunk_rows must be >= 0");
     if (host_stats) memset(host_stats, 0, sizeof(nb_query_stats));
     if (n == 0) return NB_OK;
+    if (chunk_rows == 0) {
+        const float *dq = mapped_host_rows(host_q);
+        if (dq) return query_in_place(m, dq, n, margin, host_bits, host_stats, (cudaStream_t)stream);
+    }
     const int w = m->widths[0];
     int64_t C = chunk_rows > 0 ? chunk_rows : ((int64_t)1 << 22);
     C = (C + 31) / 32 * 32;

@@ -100,10 +100,11 @@ def test_padded_narrow_network_bf16_and_training(nb, widths, kind):
         nb.Model(widths, train_prec="bf16")
 
 
-@pytest.mark.parametrize("chunk_rows,pinned", [(0, True), (4096, True), (100_000, False)])
+@pytest.mark.parametrize("chunk_rows,pinned", [(0, True), (0, False), (4096, True), (100_000, False)])
 def test_query_from_host_memory_equals_device_query(nb, chunk_rows, pinned):
-    """nb_query_host streams host queries through two staging chunks (copy on one stream,
-    decide on another): bits and statistics equal those of one device-side nb_query."""
+    """nb_query_host reads pinned host queries in place over the coherent host link (chunk
+    0) or streams them through two staging chunks (copy on one stream, decide on another):
+    bits and statistics equal those of one device-side nb_query either way."""
     import torch
     widths = [6, 128, 128, 128, 128, 1]
     p = (I.init_params(95, widths) * 3.0).astype(np.float32)
