@@ -540,15 +540,17 @@ def run_c3(args):
 # ---------------------------------------------------------------------------------- early-out
 def run_c2e(args):
     """3D point queries against a solid object (16 spheres of radius 0.2-0.5), the late
-    network 3->128x4->1 (split-FP16) behind the neural early-out of Sec. 3.3 (an early
-    3->64x2->1 network trained on the complement 1 - g)."""
+    network 3->128x4->1 (split-FP16) behind the neural early-out of Sec. 3.3: an early
+    network of one hidden layer (the paper's early exit), trained on the complement 1 - g,
+    evaluated in FP32 with a rigorous error bound in the one-pass stage that settles rows
+    and gathers the others for the late network."""
     from paper_2310_06822_gb300 import inputs as I
     from paper_2310_06822_gb300 import nb
     ctx = Ctx(args)
     torch, dev = ctx.torch, ctx.dev
     sc = I.make_scene(SEED_SCENE + 10, 16, 3, 0.2, 0.5)
     shape = nb.Shape(sc, dev)
-    late_w, early_w = [3, 128, 128, 128, 128, 1], [3, 64, 64, 1]
+    late_w, early_w = [3, 128, 128, 128, 128, 1], [3, args.early_hidden, 1]
     T = args.train_steps if args.train_steps != TRAIN_STEPS else 10000
     late_t = nb.Model(late_w, infer_prec="f32", train_prec="bf16")
     late_t.set_params(I.init_params(SEED_INIT, late_w))
@@ -562,7 +564,7 @@ def run_c2e(args):
         early.train_step(q, nb.bits_not(y, BATCH), a)
     late = nb.Model(late_w, infer_prec="f16x3")
     late.set_params(late_t.get_params())
-    early_q = nb.Model(early_w, infer_prec="f16x3")  # the early network on the tensor cores too
+    early_q = nb.Model(early_w, infer_prec="f32")  # FP32: the one-pass settle stage
     early_q.set_params(early.get_params())
     early = early_q
     n = args.n_eval
@@ -592,11 +594,11 @@ def run_c2e(args):
         return ctx.emit(None)
     line = base_line(ctx, "neural-bound queries/s at 0 FN (3D points, neural early-out + split-FP16 late network)",
                      ctx.world * n / (ms / 1000.0), "queries/s", ms, args.steps, args.warmup,
-                     "f16x3 (both networks)",
-                     {"workload": "3D points: 16-sphere solid (radii 0.2-0.5), late MLP 3->128x4->1, early MLP "
-                                  "3->64x2->1 on 1 - g, 16M eval points (Sec. 3.3 early-out)", "n_eval": n,
-                      "train_steps": T},
-                     clocks, args.steps * 11)  # early query (4), compact, gather, late query (4), scatter
+                     "f32 early network, f16x3 late network",
+                     {"workload": f"3D points: 16-sphere solid (radii 0.2-0.5), late MLP 3->128x4->1, early MLP "
+                                  f"3->{args.early_hidden}->1 on 1 - g, 16M eval points (Sec. 3.3 early-out)",
+                      "n_eval": n, "train_steps": T},
+                     clocks, args.steps * 6)  # settle stage, late query (4), merge
     line.update({"fn": int(np.sum(y & ~dec)), "fp_rate": float(np.mean(~y & dec)),
                  "fp_rate_without_early_out": float(np.mean(~y & dplain)),
                  "early_inside_fraction": est["n_early_inside"] / n,
@@ -1035,6 +1037,8 @@ def main():
     ap.add_argument("--config", default="c2", choices=["c1", "c2", "c2e", "c3", "c4", "c5", "c6"])
     ap.add_argument("--train-steps", type=int, default=TRAIN_STEPS)
     ap.add_argument("--n-eval", type=int, default=N_EVAL, help="evaluation size (smaller only for profiling)")
+    ap.add_argument("--early-hidden", type=int, default=128,
+                    help="c2e: hidden width of the one-hidden-layer early network")
     ap.add_argument("--activation", default="relu", choices=["relu", "sine"],
                     help="hidden activation of the c6 networks (sine: the paper's sinusoidal activation)")
     args = ap.parse_args()

@@ -53,7 +53,9 @@ typedef enum {
 typedef enum { NB_POINT2 = 0, NB_POINT3 = 1, NB_POINT4T = 2, NB_RAY3 = 3, NB_PLANE3 = 4, NB_BOX3 = 5 } nb_kind;
 
 /* Arithmetic of the fast forward path:
- *   NB_F32    FP32 FMA (CUDA cores), the plain single-object form;
+ *   NB_F32    FP32 FMA (CUDA cores), the plain single-object form (networks with input
+ *             width <= 8 and every hidden layer but the last <= 128 wide run a query per
+ *             thread with the weights in shared memory, others in tiles of queries);
  *   NB_BF16   tcgen05 tensor cores, BF16 operands, FP32 accumulation (one product);
  *   NB_FP8    tcgen05 tensor cores, E4M3 operands for the hidden-to-hidden layers with
  *             power-of-two scales per weight row and per query row (exact to apply),
@@ -249,7 +251,12 @@ nb_status nb_query_host(nb_model *m, const float *host_q, int64_t n, float margi
  * network of g.  Every row is first decided by `early` (nb_query with margin_early); rows
  * it decides 0 get bit 1 without evaluating `late`; the other rows are compacted, gathered
  * into a library-owned buffer and decided by `late` (nb_query with margin_late), and
- * their bits scattered back.  Both networks take the same input width.  host_stats (may
+ * their bits scattered back.  When `early` has the paper's early-exit shape (one hidden
+ * ReLU layer, input width 2, 3, 4, 6 or 8, NB_F32 inference), one pass settles and
+ * gathers instead: a row is settled when its FP32 early logit plus a rigorous bound of
+ * that logit's rounding error plus margin_early is below the early threshold; every
+ * other row (non-finite ones included) goes to `late`.  Both networks take the same input
+ * width.  host_stats (may
  * be NULL) receives how many rows each network decided.  Synchronous on stream (the
  * number of rows left for `late` is read back); the workspace, owned by `late`, grows on
  * demand (a growth synchronises the device). */

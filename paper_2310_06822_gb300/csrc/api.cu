@@ -455,7 +455,8 @@ extern "C" nb_status nb_query(nb_model *m, const float *q, int64_t n, float marg
     const MlpDesc d = desc_of(m);
     const TauF tau = nb_tau_bracket(m->tau);
     if (m->infer_prec == NB_F32)
-        st = nb_launch_fwd_f32(d, q, n, tau, margin, out_bits, opt_logits, dev_stats, ws, s);
+        st = nb_narrow_eligible(d) ? nb_launch_fwd_narrow(d, q, n, tau, margin, out_bits, opt_logits, dev_stats, ws, s)
+                                   : nb_launch_fwd_f32(d, q, n, tau, margin, out_bits, opt_logits, dev_stats, ws, s);
     else
         st = nb_tc_query(&m->tc, d, q, n, tau, margin, out_bits, opt_logits, dev_stats, ws, s);
     if (st != NB_OK) return st;
@@ -681,22 +682,37 @@ extern "C" nb_status nb_query_early_out(nb_model *early, nb_model *late, const f
     uint32_t *bits_c = (uint32_t *)(base + 256 + words);
     unsigned *idx = (unsigned *)(base + 256 + 2 * words);
     float *qc = (float *)(base + 256 + 2 * words + list);
-    // 1. the early network on every row (certified decisions against its threshold)
-    st = nb_query(early, q, n, margin_early, bits_e, nullptr, nullptr, stream);
-    if (st != NB_OK) return st;
-    // 2. rows it settles are inside; the others are listed
-    st = nb_launch_early_compact(bits_e, n, count, idx, out_bits, s);
-    if (st != NB_OK) return st;
+    const MlpDesc de = desc_of(early);
+    // a one-hidden-layer FP32 early network (the paper's early exit) settles rows and
+    // gathers the others in one pass, its decisions certified by a rigorous bound
+    const bool fused = early->infer_prec == NB_F32 && nb_early_settle_eligible(de);
+    if (fused) {
+        NB_CUDA(cudaMemsetAsync(count, 0, sizeof(unsigned), s));
+        // bits_e holds each word's start in the gathered rows
+        st = nb_launch_early_settle(de, q, n, nb_tau_bracket(early->tau), margin_early, out_bits, count, bits_e, qc,
+                                    s);
+        if (st != NB_OK) return st;
+    } else {
+        // 1. the early network on every row (certified decisions against its threshold)
+        st = nb_query(early, q, n, margin_early, bits_e, nullptr, nullptr, stream);
+        if (st != NB_OK) return st;
+        // 2. rows it settles are inside; the others are listed
+        st = nb_launch_early_compact(bits_e, n, count, idx, out_bits, s);
+        if (st != NB_OK) return st;
+    }
     unsigned m = 0;
     NB_CUDA(cudaMemcpyAsync(&m, count, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     NB_CUDA(cudaStreamSynchronize(s));
-    // 3. the late network on the listed rows only
+    // 3. the late network on the remaining rows only
     if (m > 0) {
-        st = nb_launch_early_gather(q, w, idx, m, qc, s);
-        if (st != NB_OK) return st;
+        if (!fused) {
+            st = nb_launch_early_gather(q, w, idx, m, qc, s);
+            if (st != NB_OK) return st;
+        }
         st = nb_query(late, qc, m, margin_late, bits_c, nullptr, nullptr, stream);
         if (st != NB_OK) return st;
-        st = nb_launch_early_scatter(bits_c, idx, m, out_bits, s);
+        st = fused ? nb_launch_early_merge(bits_c, bits_e, n, out_bits, s)
+                   : nb_launch_early_scatter(bits_c, idx, m, out_bits, s);
         if (st != NB_OK) return st;
     }
     if (host_stats) {

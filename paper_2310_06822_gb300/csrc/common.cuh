@@ -69,6 +69,19 @@ struct QueryWs {
 
 nb_status nb_launch_fwd_f32(const MlpDesc &d, const float *q, int64_t n, TauF tau, float margin,
                             uint32_t *bits, float *logits, nb_query_stats *st, QueryWs ws, cudaStream_t s);
+// thread-per-query FP32 forward of networks with input width <= 8 and stored hidden
+// layers <= 128 wide (narrow.cu)
+bool nb_narrow_eligible(const MlpDesc &d);
+nb_status nb_launch_fwd_narrow(const MlpDesc &d, const float *q, int64_t n, TauF tau, float margin,
+                               uint32_t *bits, float *logits, nb_query_stats *st, QueryWs ws, cudaStream_t s);
+// first stage of the early-out for a one-hidden-layer ReLU early network: settled rows get
+// bit 1, the others bit 0 and are gathered (qc, [count][w0]), pos_w[w] the first gathered
+// row of word w; then the late bits of the gathered rows merged into the words (narrow.cu)
+bool nb_early_settle_eligible(const MlpDesc &d);
+nb_status nb_launch_early_settle(const MlpDesc &d, const float *q, int64_t n, TauF tau, float margin,
+                                 uint32_t *out_bits, unsigned *count, unsigned *pos_w, float *qc, cudaStream_t s);
+nb_status nb_launch_early_merge(const uint32_t *bits_c, const unsigned *pos_w, int64_t n, uint32_t *out_bits,
+                                cudaStream_t s);
 // neural early-out (early.cu)
 nb_status nb_launch_early_compact(const uint32_t *bits_e, int64_t n, unsigned *count, unsigned *idx, uint32_t *out_bits,
                                   cudaStream_t s);

@@ -62,7 +62,9 @@ __device__ __forceinline__ void fwd_tile(const MlpDesc &d, const float *__restri
         const int m = t;
         const long long i = base + m;
         const bool valid = m < rows;
-        const float z = zs[m];
+        bool xfin = true;  // a non-finite input coordinate: the logit is made NaN
+        for (int k = 0; valid && k < w0; k++) xfin = xfin && isfinite(__ldg(q + i * w0 + k));
+        const float z = xfin ? zs[m] : __int_as_float(0x7fc00000);
         const bool fin = isfinite(z);
         const bool inside = valid && fin && z >= tau.up;
         const bool flag = valid && (!fin || fabsf(z - tau.up) < margin || (z >= tau.dn && z < tau.up));

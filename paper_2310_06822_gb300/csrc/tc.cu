@@ -166,10 +166,14 @@ __global__ void __launch_bounds__(THREADS, 1)
             if (tile >= ntiles) break;
             const long long row = tile * TILE_M + r;
             const bool valid = row < n;
+            bool xbad = false;  // a non-finite input coordinate: the logit is made NaN
             {
                 float x[16];
 #pragma unroll
-                for (int k = 0; k < 16; k++) x[k] = (valid && k < d.in) ? __ldg(q + row * d.in + k) : 0.f;
+                for (int k = 0; k < 16; k++) {
+                    x[k] = (valid && k < d.in) ? __ldg(q + row * d.in + k) : 0.f;
+                    xbad = xbad || !isfinite(x[k]);
+                }
                 st_shared_v4(A + row_off + ((0u ^ sw) << 4), pack_bf16(x[0], x[1]), pack_bf16(x[2], x[3]),
                              pack_bf16(x[4], x[5]), pack_bf16(x[6], x[7]));
                 st_shared_v4(A + row_off + ((1u ^ sw) << 4), pack_bf16(x[8], x[9]), pack_bf16(x[10], x[11]),
@@ -225,6 +229,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 }
             }
             if (!ok) break;
+            if (xbad) z = __int_as_float(0x7fc00000);
             const bool fin = isfinite(z);
             const bool inside = valid && (!fin || z >= tau.up);
             const bool flag = valid && fin && (fabsf(z - tau.up) < margin || (z >= tau.dn && z < tau.up));

@@ -247,7 +247,10 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
             const long long row = tile * TILE_M + r;
             const bool valid = row < n;
+            bool xbad = false;  // a non-finite input coordinate: the logit is made NaN
             if (half == 0) {
+#pragma unroll
+                for (int k = 0; k < 16; k++) xbad = xbad || !isfinite(x[k]);
                 // A0 = [x_hi | x_lo | x_hi | 0], 16 FP16 each, two per 32-bit column
                 uint32_t w0[16], w1[16];
 #pragma unroll
@@ -358,6 +361,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
             if (!ok) break;
             if (half == 0) {
+                if (xbad) z = __int_as_float(0x7fc00000);
                 const bool fin = isfinite(z);
                 const bool inside = valid && fin && z >= tau.up;
                 // a non-finite fast logit goes to the FP32 re-check

@@ -202,6 +202,9 @@ __global__ void __launch_bounds__(Single<H>::THREADS, 1)
             if (tile >= ntiles) break;
             const long long row = tile * TILE_M + r;
             const bool valid = row < n;
+            bool xbad = false;  // a non-finite input coordinate: the logit is made NaN
+#pragma unroll
+            for (int k = 0; k < 16; k++) xbad = xbad || !isfinite(x[k]);
             {
                 // A0 = [x_hi | x_lo | x_hi | 0], 16 FP16 each, two per 32-bit column
                 uint32_t w0[16], w1[16];
@@ -309,6 +312,7 @@ __global__ void __launch_bounds__(Single<H>::THREADS, 1)
                 }
             }
             if (!ok) break;
+            if (xbad) z = __int_as_float(0x7fc00000);
             const bool fin = isfinite(z);
             const bool inside = valid && fin && z >= tau.up;
             // a non-finite fast logit (e.g. an FP16 overflow) goes to the FP32 re-check
@@ -656,7 +660,10 @@ __global__ void __launch_bounds__(STHREADS, 1)
                 const long long trow0 = it.row0 + (NS * tp + s) * TILE_M;
                 const long long row = trow0 + r;
                 const bool valid = row < it.row1;
+                bool xbad = false;  // a non-finite input coordinate: the logit is made NaN
                 if (hf == 0) {
+#pragma unroll
+                    for (int kk = 0; kk < 16; kk++) xbad = xbad || !isfinite(x[kk]);
                     uint32_t w0[16], w1[16];
 #pragma unroll
                     for (int kk = 0; kk < 8; kk++) {
@@ -736,6 +743,7 @@ __global__ void __launch_bounds__(STHREADS, 1)
                 }
                 if (!ok) break;
                 if (hf != 0) continue;
+                if (xbad) z = __int_as_float(0x7fc00000);
                 const bool fin = isfinite(z);
                 const bool inside = valid && fin && z >= tau.up;
                 const bool flag = valid && (!fin || fabsf(z - tau.up) < margin || (z >= tau.dn && z < tau.up));
