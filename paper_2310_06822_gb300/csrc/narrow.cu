@@ -346,7 +346,8 @@ __global__ void __launch_bounds__(NT, 4)
 // bound operation rounds up.  A row is settled (inside) when z + bound + margin < tau_dn
 // <= tau: its exact logit is below the early network's threshold, and the early network
 // bounds the complement 1 - g.  A word's late rows are gathered, in lane order, from
-// pos_w[word] on.
+// pos_w[word] on; a block claims its range of the gathered list with one atomic per
+// iteration (a counter shared by every block would otherwise serialise the warps).
 template <int W0>
 __global__ void __launch_bounds__(NT, 4)
     early_settle_kernel(const __grid_constant__ MlpDesc d, const __grid_constant__ NarrowDesc nd,
@@ -356,6 +357,7 @@ __global__ void __launch_bounds__(NT, 4)
     extern __shared__ __align__(16) float sm[];
     __shared__ double red[2][NT / 32];
     __shared__ float cab[2];
+    __shared__ unsigned wcnt[NT / 32], wbase;
     load_image(d, nd, sm);
     __syncthreads();
     const int t = threadIdx.x, lane = t & 31;
@@ -394,7 +396,11 @@ __global__ void __launch_bounds__(NT, 4)
     const float C_a = cab[0], C_b = cab[1];
     const float c_abs = fabsf(sm[nd.wo[1] + nd.np[0]]);
     const long long stride = (long long)gridDim.x * NT * R1;
-    for (long long base = ((long long)blockIdx.x * NT + (t & ~31)) * R1; base < n; base += stride) {
+    const int warp = t >> 5;
+    // a block takes NT R1 rows per iteration (every warp iterates alike, so the block can
+    // synchronise) and claims one range of the gathered list for all its late rows
+    for (long long bb = (long long)blockIdx.x * NT * R1; bb < n; bb += stride) {
+        const long long base = bb + (long long)warp * 32 * R1;
         float x[R1][MAXIN];
 #pragma unroll
         for (int r = 0; r < R1; r++) {
@@ -404,6 +410,7 @@ __global__ void __launch_bounds__(NT, 4)
         }
         float z[R1], sa[R1];
         one_hidden<W0, R1, true>(nd, sm, x, NB_ACT_RELU, z, sa);
+        unsigned bs[R1], bl[R1];
 #pragma unroll
         for (int r = 0; r < R1; r++) {
             const long long i = base + 32 * r + lane;
@@ -419,24 +426,36 @@ __global__ void __launch_bounds__(NT, 4)
                                           __fmul_ru(g_in, __fmaf_ru(xmax, C_a, C_b)));
             const float top = __fadd_ru(__fadd_ru(z[r], bound), margin);
             const bool settled = valid && xfin && isfinite(z[r]) && isfinite(top) && top < tau.dn;
-            const bool late = valid && !settled;
-            const unsigned bs = __ballot_sync(FULL, settled);
-            const unsigned bl = __ballot_sync(FULL, late);
-            unsigned pos = 0;
-            if (bl) {
-                if (lane == 0) pos = atomicAdd(count, (unsigned)__popc(bl));
-                pos = __shfl_sync(FULL, pos, 0);
-                if (late) {
-                    const unsigned p = pos + __popc(bl & ((1u << lane) - 1u));
+            bs[r] = __ballot_sync(FULL, settled);
+            bl[r] = __ballot_sync(FULL, valid && !settled);
+        }
+        unsigned mine = 0;  // this warp's late rows
 #pragma unroll
-                    for (int k = 0; k < W0; k++) qc[(size_t)p * W0 + k] = x[r][k];
-                }
+        for (int r = 0; r < R1; r++) mine += __popc(bl[r]);
+        if (lane == 0) wcnt[warp] = mine;
+        __syncthreads();
+        if (t == 0) {
+            unsigned tot = 0;
+            for (int w = 0; w < NT / 32; w++) tot += wcnt[w];
+            wbase = tot ? atomicAdd(count, tot) : 0u;
+        }
+        __syncthreads();
+        unsigned pos = wbase;
+        for (int w = 0; w < warp; w++) pos += wcnt[w];
+#pragma unroll
+        for (int r = 0; r < R1; r++) {
+            if ((bl[r] >> lane) & 1u) {
+                const unsigned p = pos + __popc(bl[r] & ((1u << lane) - 1u));
+#pragma unroll
+                for (int k = 0; k < W0; k++) qc[(size_t)p * W0 + k] = x[r][k];
             }
             if (lane == 0 && base + 32 * r < n) {
-                out_bits[(base >> 5) + r] = bs;
+                out_bits[(base >> 5) + r] = bs[r];
                 pos_w[(base >> 5) + r] = pos;
             }
+            pos += __popc(bl[r]);
         }
+        __syncthreads();  // wcnt and wbase are reused by the next iteration
     }
 }
 
