@@ -538,6 +538,9 @@ def run_c3(args):
 
 
 # ---------------------------------------------------------------------------------- early-out
+EARLY_STEPS_FACTOR = 4
+
+
 def run_c2e(args):
     """3D point queries against a solid object (16 spheres of radius 0.2-0.5), the late
     network 3->128x4->1 (split-FP16) behind the neural early-out of Sec. 3.3: an early
@@ -559,9 +562,14 @@ def run_c2e(args):
     for t in range(T):
         q = nb.sample(I.POINT3, BATCH, SEED_TRAIN, first=t * BATCH)
         y = nb.label(shape, I.POINT3, q)
-        a = 1.0 + 99.0 * t / max(T - 1, 1)
-        late_t.train_step(q, y, a)
-        early.train_step(q, nb.bits_not(y, BATCH), a)
+        late_t.train_step(q, y, 1.0 + 99.0 * t / max(T - 1, 1))
+    # the one-hidden-layer early network costs little to train: it gets EARLY_STEPS_FACTOR
+    # times the late network's steps (the share of rows it settles grows with them)
+    TE = EARLY_STEPS_FACTOR * T
+    for t in range(TE):
+        q = nb.sample(I.POINT3, BATCH, SEED_TRAIN, first=t * BATCH)
+        y = nb.label(shape, I.POINT3, q)
+        early.train_step(q, nb.bits_not(y, BATCH), 1.0 + 99.0 * t / max(TE - 1, 1))
     late = nb.Model(late_w, infer_prec="f16x3")
     late.set_params(late_t.get_params())
     early_q = nb.Model(early_w, infer_prec="f32")  # FP32: the one-pass settle stage
@@ -597,7 +605,7 @@ def run_c2e(args):
                      "f32 early network, f16x3 late network",
                      {"workload": f"3D points: 16-sphere solid (radii 0.2-0.5), late MLP 3->128x4->1, early MLP "
                                   f"3->{args.early_hidden}->1 on 1 - g, 16M eval points (Sec. 3.3 early-out)",
-                      "n_eval": n, "train_steps": T},
+                      "n_eval": n, "train_steps": T, "early_train_steps": TE},
                      clocks, args.steps * 6)  # settle stage, late query (4), merge
     line.update({"fn": int(np.sum(y & ~dec)), "fp_rate": float(np.mean(~y & dec)),
                  "fp_rate_without_early_out": float(np.mean(~y & dplain)),
@@ -1037,7 +1045,7 @@ def main():
     ap.add_argument("--config", default="c2", choices=["c1", "c2", "c2e", "c3", "c4", "c5", "c6"])
     ap.add_argument("--train-steps", type=int, default=TRAIN_STEPS)
     ap.add_argument("--n-eval", type=int, default=N_EVAL, help="evaluation size (smaller only for profiling)")
-    ap.add_argument("--early-hidden", type=int, default=128,
+    ap.add_argument("--early-hidden", type=int, default=64,
                     help="c2e: hidden width of the one-hidden-layer early network")
     ap.add_argument("--activation", default="relu", choices=["relu", "sine"],
                     help="hidden activation of the c6 networks (sine: the paper's sinusoidal activation)")
