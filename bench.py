@@ -47,8 +47,8 @@ MARGIN32 = 1e-2  # FP32 form: re-check band above its own logit error
 CAL_N, SEED_CAL = 4 << 20, 2101
 SEED_SCENE, SEED_QUERY, SEED_INIT, SEED_TRAIN = 1001, 2001, 4001, 2018
 # DRAM bytes (read + write) per ray of the forward kernel, from one ncu capture of
-# fwd_split_kernel at 1,048,576 rays (25,461,504 bytes); None once the kernel changes
-TRAFFIC_BYTES_PER_RAY = 25461504 / 1048576
+# fwd_split_kernel at 1,048,576 rays (25,464,832 bytes); None once the kernel changes
+TRAFFIC_BYTES_PER_RAY = 25464832 / 1048576
 METRIC = "neural-bound queries/s at 0 FN (3D rays, split-FP16 tcgen05 forward + FP32 re-check)"
 WORKLOAD = "3D ray queries: 64-sphere union, MLP 6->128x4->1, tensor-core 16-bit, 16M eval rays"
 
