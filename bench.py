@@ -49,6 +49,9 @@ SEED_SCENE, SEED_QUERY, SEED_INIT, SEED_TRAIN = 1001, 2001, 4001, 2018
 # DRAM bytes (read + write) per ray of the forward kernel, from one ncu capture of
 # fwd_split_kernel at 1,048,576 rays (25,464,832 bytes); None once the kernel changes
 TRAFFIC_BYTES_PER_RAY = 25464832 / 1048576
+# the same for fwd_fp8_kernel at 1,048,576 boxes (25,698,816 bytes: 24 B per box and the
+# weight image once per capture; scaled by boxes it slightly overcounts the image)
+TRAFFIC_BYTES_PER_BOX = 25698816 / 1048576
 METRIC = "neural-bound queries/s at 0 FN (3D rays, split-FP16 tcgen05 forward + FP32 re-check)"
 WORKLOAD = "3D ray queries: 64-sphere union, MLP 6->128x4->1, tensor-core 16-bit, 16M eval rays"
 
@@ -523,7 +526,8 @@ def run_c3(args):
                                          "fp32_plane": B / (tr32_ms[I.PLANE3] / 1000.0)},
                  "roofline": {"kernel": "fwd_fp8_kernel (tcgen05 kind::f8f6f4)", "bound": "tensor",
                               "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                              "traffic": None, "peak_kind": f"{pk_kind} bf16 burst x 2 (E4M3 nominal ratio)",
+                              "traffic": (TRAFFIC_BYTES_PER_BOX * n_eval) if TRAFFIC_BYTES_PER_BOX else None,
+                              "peak_kind": f"{pk_kind} bf16 burst x 2 (E4M3 nominal ratio)",
                               "fwd_ms": fwd_ms, "algorithmic_flops_per_launch": flops},
                  "cpu_baseline": {"value": cpu_v, "unit": "queries/s", "cores": cores, "kind": "oracle",
                                   "sample": f"{cpu_n} box queries through the FP64 oracle forward"},

@@ -8,10 +8,11 @@
 // weight is used as often as registers allow:
 //   - one hidden layer (fwd_one_hidden_kernel, early_settle_kernel): a thread carries
 //     four queries, so each loaded group of four weights feeds sixteen FMAs;
-//   - more layers (fwd_narrow_kernel): one query per thread; the first hidden layer is
-//     computed straight into registers, a later stored layer writes its outputs to the
-//     thread's own column of a shared-memory buffer ([n / 4][thread] float4s, free of bank
-//     conflicts), read back into registers by the next layer.
+//   - more layers (fwd_narrow_kernel): two queries per thread while the stored layers are
+//     at most 64 wide, else one; the first hidden layer is computed straight into
+//     registers, a later stored layer writes its outputs to the thread's own columns of a
+//     shared-memory buffer ([n / 4][R thread columns] float4s, free of bank conflicts),
+//     read back into registers by the next layer.
 // The last hidden layer is never stored: each group of four neurons is folded into the
 // head's sum as soon as it is computed.
 //
@@ -41,7 +42,7 @@ constexpr int R1 = 4;    // queries per thread in the one-hidden-layer kernels
 // Shared-memory plan of one network (floats, every block 16-byte aligned).
 //   layer l < L - 1: Wt [kp[l]][np[l]] at wo[l], then the bias [np[l]]
 //   head (l = L - 1): v [np[L - 2]] at wo[L - 1], then c
-//   activation buffer: [hp / 4][NT] float4 at abuf (when L > 3)
+//   activation buffer: [hp / 4][NT R] float4 at abuf (when L > 3), R queries per thread
 // hp: padded width of the stored hidden layers (0 for one hidden layer).
 struct NarrowDesc {
     int L, w0, act, hp;
@@ -91,25 +92,40 @@ __device__ void load_image(const MlpDesc &d, const NarrowDesc &nd, float *sm) {
     }
 }
 
-// The last hidden layer from the stored inputs in[0..HP), folded into the head:
-// z = c + sum_j v_j h_j, kept as four partial sums (neurons j = 4i + e in sum e, so the
-// dependent chains are a quarter as long) that are added pairwise at the end.
-template <int HP>
-__device__ __forceinline__ float last_layer(const NarrowDesc &nd, const float *sm, const float (&in)[HP], int act) {
+// The last hidden layer from the stored inputs in[r][0..HP) of R queries, folded into the
+// head: z[r] = c + sum_j v_j h_j, kept as four partial sums (neurons j = 4i + e in sum e,
+// so the dependent chains are a quarter as long) that are added pairwise at the end.
+template <int HP, int R>
+__device__ __forceinline__ void last_layer(const NarrowDesc &nd, const float *sm, const float (&in)[R][HP], int act,
+                                           float (&z)[R]) {
     const int l = nd.L - 2, np = nd.np[l];
     const float *Wt = sm + nd.wo[l], *b = Wt + HP * np, *v = sm + nd.wo[l + 1];
-    float4 zz = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int j0 = 0; j0 < np; j0 += 4) {
-        float4 acc = ld4(b + j0);
+    float4 zz[R];
 #pragma unroll
-        for (int k = 0; k < HP; k++) fma4(acc, ld4(Wt + k * np + j0), in[k]);
-        const float4 h = act4(acc, act), vv = ld4(v + j0);
-        zz.x = fmaf(vv.x, h.x, zz.x);
-        zz.y = fmaf(vv.y, h.y, zz.y);
-        zz.z = fmaf(vv.z, h.z, zz.z);
-        zz.w = fmaf(vv.w, h.w, zz.w);
+    for (int r = 0; r < R; r++) zz[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int j0 = 0; j0 < np; j0 += 4) {
+        const float4 bb = ld4(b + j0);
+        float4 acc[R];
+#pragma unroll
+        for (int r = 0; r < R; r++) acc[r] = bb;
+#pragma unroll
+        for (int k = 0; k < HP; k++) {
+            const float4 w = ld4(Wt + k * np + j0);
+#pragma unroll
+            for (int r = 0; r < R; r++) fma4(acc[r], w, in[r][k]);
+        }
+        const float4 vv = ld4(v + j0);
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const float4 h = act4(acc[r], act);
+            zz[r].x = fmaf(vv.x, h.x, zz[r].x);
+            zz[r].y = fmaf(vv.y, h.y, zz[r].y);
+            zz[r].z = fmaf(vv.z, h.z, zz[r].z);
+            zz[r].w = fmaf(vv.w, h.w, zz[r].w);
+        }
     }
-    return v[np] + ((zz.x + zz.y) + (zz.z + zz.w));
+#pragma unroll
+    for (int r = 0; r < R; r++) z[r] = v[np] + ((zz[r].x + zz[r].y) + (zz[r].z + zz[r].w));
 }
 
 // One hidden layer from R queries x[r][0..W0) straight into the head (the early exit of
@@ -155,111 +171,134 @@ __device__ __forceinline__ void one_hidden(const NarrowDesc &nd, const float *sm
     }
 }
 
-// The logit of a network with two or more hidden layers for the query x[0..w0) (thread
-// t's column of the buffer).  The first hidden layer goes straight into registers; a
-// stored layer after it writes its outputs to the buffer, from which the next layer
-// reloads its registers.
-template <int HP>
-__device__ __forceinline__ float narrow_forward(const NarrowDesc &nd, const float *sm, float4 *abuf,
-                                                const float (&x)[MAXIN], int t) {
-    float a[HP];
-    {  // layer 0: the query -> registers
+// The logits of R queries x[r][0..w0) through a network with two or more hidden layers
+// (thread t's R columns of the buffer).  The first hidden layer goes straight into
+// registers; a stored layer after it writes its outputs to the buffer, from which the next
+// layer reloads its registers.  Every loaded weight serves R queries.
+template <int HP, int R>
+__device__ __forceinline__ void narrow_forward(const NarrowDesc &nd, const float *sm, float4 *abuf,
+                                               const float (&x)[R][MAXIN], int t, float (&z)[R]) {
+    float a[R][HP];
+    {  // layer 0: the queries -> registers
         const float *Wt = sm + nd.wo[0], *b = Wt + nd.kp[0] * HP;
 #pragma unroll
         for (int j0 = 0; j0 < HP; j0 += 4) {
-            float4 acc = ld4(b + j0);
+            const float4 bb = ld4(b + j0);
+            float4 acc[R];
+#pragma unroll
+            for (int r = 0; r < R; r++) acc[r] = bb;
 #pragma unroll
             for (int k = 0; k < MAXIN; k++)
-                if (k < nd.w0) fma4(acc, ld4(Wt + k * HP + j0), x[k]);
-            const float4 h = act4(acc, nd.act);
-            a[j0] = h.x;
-            a[j0 + 1] = h.y;
-            a[j0 + 2] = h.z;
-            a[j0 + 3] = h.w;
+                if (k < nd.w0) {
+                    const float4 w = ld4(Wt + k * HP + j0);
+#pragma unroll
+                    for (int r = 0; r < R; r++) fma4(acc[r], w, x[r][k]);
+                }
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                const float4 h = act4(acc[r], nd.act);
+                a[r][j0] = h.x;
+                a[r][j0 + 1] = h.y;
+                a[r][j0 + 2] = h.z;
+                a[r][j0 + 3] = h.w;
+            }
         }
     }
     for (int l = 1; l <= nd.L - 3; l++) {  // stored layers: registers -> the buffer -> registers
         const float *Wt = sm + nd.wo[l], *b = Wt + HP * HP;
         for (int j0 = 0; j0 < HP; j0 += 4) {
-            float4 acc = ld4(b + j0);
+            const float4 bb = ld4(b + j0);
+            float4 acc[R];
 #pragma unroll
-            for (int k = 0; k < HP; k++) fma4(acc, ld4(Wt + k * HP + j0), a[k]);
-            abuf[(j0 >> 2) * NT + t] = act4(acc, nd.act);
+            for (int r = 0; r < R; r++) acc[r] = bb;
+#pragma unroll
+            for (int k = 0; k < HP; k++) {
+                const float4 w = ld4(Wt + k * HP + j0);
+#pragma unroll
+                for (int r = 0; r < R; r++) fma4(acc[r], w, a[r][k]);
+            }
+#pragma unroll
+            for (int r = 0; r < R; r++) abuf[(j0 >> 2) * (NT * R) + r * NT + t] = act4(acc[r], nd.act);
         }
 #pragma unroll
-        for (int k4 = 0; k4 < HP / 4; k4++) {
-            const float4 v = abuf[k4 * NT + t];
-            a[4 * k4] = v.x;
-            a[4 * k4 + 1] = v.y;
-            a[4 * k4 + 2] = v.z;
-            a[4 * k4 + 3] = v.w;
-        }
-    }
-    return last_layer<HP>(nd, sm, a, nd.act);
-}
-
-__device__ __forceinline__ void load_query(const float *__restrict__ q, long long i, bool valid, int w0,
-                                           float (&x)[MAXIN], bool &xfin) {
-    xfin = true;
+        for (int r = 0; r < R; r++)
 #pragma unroll
-    for (int k = 0; k < MAXIN; k++) {
-        x[k] = (valid && k < w0) ? __ldg(q + i * w0 + k) : 0.f;
-        xfin = xfin && isfinite(x[k]);
+            for (int k4 = 0; k4 < HP / 4; k4++) {
+                const float4 v = abuf[k4 * (NT * R) + r * NT + t];
+                a[r][4 * k4] = v.x;
+                a[r][4 * k4 + 1] = v.y;
+                a[r][4 * k4 + 2] = v.z;
+                a[r][4 * k4 + 3] = v.w;
+            }
     }
+    last_layer<HP, R>(nd, sm, a, nd.act, z);
 }
 
-// Decisions z >= tau for rows [warp base, +32) per iteration: bits, optional logits, the
-// margin band appended to flag_idx; a non-finite logit or input coordinate is flagged
-// (the re-check decides it inside).  Same contract as the tile kernel.
+// Queries per thread of the multi-layer kernel: two while their registers allow (stored
+// layers up to 64 wide), else one.
 template <int HP>
-__global__ void __launch_bounds__(NT, HP >= 128 ? 2 : 3)
+struct RowsPerThread {
+    static constexpr int value = HP <= 64 ? 2 : 1;
+};
+
+// Decisions z >= tau for 32 R consecutive rows per warp and iteration (row base + 32 r +
+// lane in slot r): bits, optional logits, the margin band appended to flag_idx; a
+// non-finite logit or input coordinate is flagged (the re-check decides it inside).  Same
+// contract as the tile kernel.
+template <int HP>
+__global__ void __launch_bounds__(NT, HP >= 64 ? 2 : 3)
     fwd_narrow_kernel(const __grid_constant__ MlpDesc d, const __grid_constant__ NarrowDesc nd,
                       const float *__restrict__ q, long long n, TauF tau, float margin, uint32_t *__restrict__ bits,
                       float *__restrict__ logits, nb_query_stats *st, unsigned *flag_count, unsigned *flag_idx) {
+    constexpr int R = RowsPerThread<HP>::value;
     extern __shared__ __align__(16) float sm[];
     load_image(d, nd, sm);
     __syncthreads();
     float4 *abuf = reinterpret_cast<float4 *>(sm + nd.abuf);
     const int t = threadIdx.x, lane = t & 31;
+    const int w0 = nd.w0;
     unsigned long long c_in = 0, c_flag = 0, c_nf = 0;
-    const long long stride = (long long)gridDim.x * NT;
-    float x[MAXIN];
-    bool xfin;
-    {
-        const long long i0 = (long long)blockIdx.x * NT + t;
-        load_query(q, i0, i0 < n, nd.w0, x, xfin);
-    }
-    for (long long base = (long long)blockIdx.x * NT + (t & ~31); base < n; base += stride) {
-        const long long i = base + lane;
-        const bool valid = i < n;
-        // the next row's coordinates are in flight while this row runs through the layers
-        float xn[MAXIN];
-        bool xnfin;
-        load_query(q, i + stride, i + stride < n, nd.w0, xn, xnfin);
-        float z = narrow_forward<HP>(nd, sm, abuf, x, t);
-        if (!xfin) z = __int_as_float(0x7fc00000);
-        const bool fin = isfinite(z);
-        const bool inside = valid && fin && z >= tau.up;
-        const bool flag = valid && (!fin || fabsf(z - tau.up) < margin || (z >= tau.dn && z < tau.up));
-        const unsigned bi = __ballot_sync(FULL, inside);
-        const unsigned bf = __ballot_sync(FULL, flag);
-        const unsigned bn = __ballot_sync(FULL, valid && !fin);
-        if (lane == 0) bits[base >> 5] = bi;
-        if (valid && logits) logits[i] = z;
-        if (bf) {
-            unsigned pos = 0;
-            if (lane == 0) pos = atomicAdd(flag_count, (unsigned)__popc(bf));
-            pos = __shfl_sync(FULL, pos, 0);
-            if (flag) flag_idx[pos + __popc(bf & ((1u << lane) - 1u))] = (unsigned)i;
-        }
-        if (lane == 0) {
-            c_in += __popc(bi);
-            c_flag += __popc(bf);
-            c_nf += __popc(bn);
-        }
+    const long long stride = (long long)gridDim.x * NT * R;
+    for (long long base = ((long long)blockIdx.x * NT + (t & ~31)) * R; base < n; base += stride) {
+        float x[R][MAXIN];
+        bool xfin[R];
 #pragma unroll
-        for (int k = 0; k < MAXIN; k++) x[k] = xn[k];
-        xfin = xnfin;
+        for (int r = 0; r < R; r++) {
+            const long long i = base + 32 * r + lane;
+            xfin[r] = true;
+#pragma unroll
+            for (int k = 0; k < MAXIN; k++) {
+                x[r][k] = (i < n && k < w0) ? __ldg(q + i * w0 + k) : 0.f;
+                xfin[r] = xfin[r] && isfinite(x[r][k]);
+            }
+        }
+        float z[R];
+        narrow_forward<HP, R>(nd, sm, abuf, x, t, z);
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const long long i = base + 32 * r + lane;
+            const bool valid = i < n;
+            const float zr = xfin[r] ? z[r] : __int_as_float(0x7fc00000);
+            const bool fin = isfinite(zr);
+            const bool inside = valid && fin && zr >= tau.up;
+            const bool flag = valid && (!fin || fabsf(zr - tau.up) < margin || (zr >= tau.dn && zr < tau.up));
+            const unsigned bi = __ballot_sync(FULL, inside);
+            const unsigned bf = __ballot_sync(FULL, flag);
+            const unsigned bn = __ballot_sync(FULL, valid && !fin);
+            if (lane == 0 && base + 32 * r < n) bits[(base >> 5) + r] = bi;
+            if (valid && logits) logits[i] = zr;
+            if (bf) {
+                unsigned pos = 0;
+                if (lane == 0) pos = atomicAdd(flag_count, (unsigned)__popc(bf));
+                pos = __shfl_sync(FULL, pos, 0);
+                if (flag) flag_idx[pos + __popc(bf & ((1u << lane) - 1u))] = (unsigned)i;
+            }
+            if (lane == 0) {
+                c_in += __popc(bi);
+                c_flag += __popc(bf);
+                c_nf += __popc(bn);
+            }
+        }
     }
     if (st && lane == 0) {
         if (c_in) atomicAdd(&st->n_inside, c_in);
@@ -518,7 +557,7 @@ bool plan(const MlpDesc &d, NarrowDesc &nd) {
     nd.wo[d.L - 1] = off;
     off += r4(nd.np[d.L - 2] + 1);
     nd.abuf = off;
-    if (d.L > 3) off += nd.hp * NT;
+    if (d.L > 3) off += nd.hp * NT * (nd.hp <= 64 ? 2 : 1);  // [hp / 4][NT * R] float4
     nd.floats = off;
     return off <= MAX_SMEM_FLOATS;
 }
@@ -554,7 +593,8 @@ float gamma_up(int k) {
 template <int HP>
 nb_status fwd_launch(const MlpDesc &d, const NarrowDesc &nd, const float *q, int64_t n, TauF tau, float margin,
                      uint32_t *bits, float *logits, nb_query_stats *st, QueryWs ws, cudaStream_t s) {
-    return launch(fwd_narrow_kernel<HP>, "fwd_narrow", nd, n, 1, s, d, nd, q, (long long)n, tau, margin, bits,
+    return launch(fwd_narrow_kernel<HP>, "fwd_narrow", nd, n, RowsPerThread<HP>::value, s, d, nd, q, (long long)n,
+                  tau, margin, bits,
                   logits, st, ws.flag_count, ws.flag_idx);
 }
 
