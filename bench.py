@@ -668,6 +668,14 @@ def run_c1(args):
     torch.cuda.current_stream().wait_stream(s_cap)
     torch.cuda.synchronize()
     eager_ms = ctx.time_ms(lambda: [m.query(grid, margin=1e-3, out=out) for _ in range(reps)], 3)
+    # end to end through the public API: the pinned host grid read in place, bits back
+    hgrid = torch.empty(grid.shape, dtype=torch.float32, pin_memory=True)
+    hgrid.copy_(grid.cpu())
+    hbits = torch.empty(nb.n_words(grid.shape[0]), dtype=torch.int32, pin_memory=True)
+    for _ in range(3):
+        m.query_host(hgrid, margin=1e-3, out=hbits)
+    e2e_ms = ctx.time_ms(lambda: [m.query_host(hgrid, margin=1e-3, out=hbits) for _ in range(reps)], 3)
+    e2e_equal = bool(np.array_equal(nb.bits_to_numpy(hbits, grid.shape[0]), dec))
     ms, clocks = ctx.timed(graph.replay, args.steps, args.warmup)
     value = job_value(reps * grid.shape[0], ctx.world, ms)
     assert np.array_equal(nb.bits_to_numpy(out, grid.shape[0]), dec)
@@ -683,7 +691,11 @@ def run_c1(args):
                  "without_graph_queries_per_s": reps * grid.shape[0] / (eager_ms / 1000.0),
                  "cpu_baseline": {"value": cpu_v, "unit": "queries/s", "cores": cores, "kind": "oracle",
                                   "sample": f"{cpu_n} grid points through the FP64 oracle forward"},
-                 "e2e": None})
+                 "e2e": {"value": ctx.world * reps * grid.shape[0] / (e2e_ms / 1000.0), "unit": "queries/s",
+                         "h2d_bytes_per_step": reps * grid.shape[0] * 2 * 4,
+                         "d2h_bytes_per_step": reps * nb.n_words(grid.shape[0]) * 4,
+                         "call": "nb_query_host per grid (pinned host points read in place over NVLink-C2C, bits "
+                                 "copied back; one synchronous call per grid)", "bits_equal_device_query": e2e_equal}})
     ctx.emit(line)
 
 
@@ -754,6 +766,9 @@ def run_c4(args):
     dec = nb.bits_to_numpy(out, K * NE)
     ms, clocks = ctx.timed(lambda: g.query(eplan, eq, margin=MARGIN, out=out), args.steps, args.warmup)
     value = ctx.world * K * NE / (ms / 1000.0)
+    # the grouped forward alone (margin 0: the re-check launches find an empty band)
+    fwd_ms = ctx.time_ms(lambda: g.query(eplan, eq, margin=0.0, out=out), max(3, args.steps // 4))
+    g.query(eplan, eq, margin=MARGIN, out=out)
     # plain FP32 single-object form: one network at a time, same weights and thresholds
     P = g.get_params()
     single = nb.Model(widths)
@@ -765,6 +780,14 @@ def run_c4(args):
                                                      out=out[o * NE // 32:(o + 1) * NE // 32]), 2))
     f32_ms = float(np.mean(o_ms)) * K
     cpu_v, cores, cpu_n = cpu_oracle_rate(widths, P[0], eq[:NE].cpu().numpy())
+    pk, pk_kind = peaks()
+    macs = sum(widths[i] * widths[i + 1] for i in range(len(widths) - 1))
+    flops = 2.0 * macs * K * NE
+    achieved = flops / (fwd_ms / 1000.0) / 1e12
+    roof_c4 = {"kernel": "fwd_split_group_kernel (tcgen05, 3 products per k-step)", "bound": "tensor",
+               "achieved": achieved, "peak": pk["bf16_tflops"], "unit": "TFLOP/s", "frac": achieved / pk["bf16_tflops"],
+               "traffic": None, "peak_kind": f"{pk_kind} bf16 burst", "fwd_ms": fwd_ms,
+               "algorithmic_flops_per_launch": flops}
     line = base_line(ctx, "grouped neural-bound queries/s at 0 FN (4D points, 256 objects, split-FP16)", value,
                      "queries/s", ms, args.steps, args.warmup, "f16x3 (split fp16 operands, fp32 accumulate)",
                      {"workload": "4D space-time points: 256 objects of 16-64 moving spheres, 4->64x3->1 per object, "
@@ -778,6 +801,7 @@ def run_c4(args):
                  "grouped_train_samples_per_s_bf16_graph": sum(counts) / (step_ms / 1000.0),
                  "autotune": {"train_chunk_rows": chunk_train, "train_ms": ms_train,
                               "query_chunk_rows": chunk_query, "query_ms": ms_query},
+                 "roofline": roof_c4,
                  "cpu_baseline": {"value": cpu_v, "unit": "queries/s", "cores": cores, "kind": "oracle",
                                   "sample": f"{cpu_n} points of object 0 through the FP64 oracle forward"},
                  "e2e": None})
@@ -988,7 +1012,16 @@ def run_c6(args):
         ms32 = ctx.time_ms(lambda: m.query(eq, margin=MARGIN32, out=out), reps)
         if name == "3d_ray":
             msf, clocks = ctx.timed(lambda: f.query(eq, margin=margin, out=out), args.steps, args.warmup)
-            head = (msf, clocks)
+            # end to end through the public API: pinned host rays read in place, bits back
+            hq = torch.empty((n, 6), dtype=torch.float32, pin_memory=True)
+            hq.copy_(eq.cpu())
+            hb = torch.empty(nb.n_words(n), dtype=torch.int32, pin_memory=True)
+            for _ in range(3):
+                f.query_host(hq, margin=margin, out=hb)
+            e2e_ms = ctx.time_ms(lambda: f.query_host(hq, margin=margin, out=hb), reps)
+            e2e_equal = bool(np.array_equal(nb.bits_to_numpy(hb, n), df))
+            head = (msf, clocks, e2e_ms, e2e_equal)
+            del hq, hb
         else:
             msf = ctx.time_ms(lambda: f.query(eq, margin=margin, out=out), reps)
         table[name] = {"widths": widths, "fp32_queries_per_s": n / (ms32 / 1000.0),
@@ -997,7 +1030,7 @@ def run_c6(args):
                        "decisions_equal_fp32_form": bool(np.array_equal(d32, df)), "margin": margin}
         m.close()
         f.close()
-    msf, clocks = head
+    msf, clocks, e2e_ms, e2e_equal = head
     line = base_line(ctx, "neural-bound queries/s at 0 FN (3D rays, the paper's 6->50->50->1%s, split-FP16 padded)"
                      % (", sine activations" if act == "sine" else ""),
                      job_value(n, ctx.world, msf), "queries/s", msf, args.steps, args.warmup,
@@ -1007,7 +1040,11 @@ def run_c6(args):
                       "batch": B, "padding": "hidden widths zero-padded to 64 (25, 50) and 128 (75)",
                       "activation": act},
                      clocks, args.steps * 4)
-    line.update({"sizes": table, "cpu_baseline": None, "e2e": None})
+    line.update({"sizes": table, "cpu_baseline": None,
+                 "e2e": {"value": ctx.world * n / (e2e_ms / 1000.0), "unit": "queries/s",
+                         "h2d_bytes_per_step": n * 6 * 4, "d2h_bytes_per_step": nb.n_words(n) * 4,
+                         "call": "nb_query_host on the 3D-ray network (pinned host rays read in place over "
+                                 "NVLink-C2C, bits copied back)", "bits_equal_device_query": e2e_equal}})
     ctx.emit(line)
 
 

@@ -184,3 +184,37 @@ def test_one_pass_early_out_non_finite_rows_go_to_the_late_network(nb):
     dec = nb.bits_to_numpy(bits, n)
     assert st["n_late"] == 2 and st["n_early_inside"] == n - 2
     assert dec.all()  # settled rows inside; the two non-finite rows inside by the late network
+
+
+@pytest.mark.parametrize("widths", [[6, 50, 50, 1], [6, 64, 1]])
+def test_narrow_full_size_16m_rays(nb, widths):
+    """16M rays, the size and launch bench.py times for the paper's 3D-ray network (and a
+    one-hidden-layer network): the thread-per-query FP32 form and the split-FP16 tensor-core
+    form decide every ray alike (both certified by the re-check); sampled logits of the FP32
+    form against the oracle, one by one."""
+    import torch
+    n = 16 << 20
+    q = nb.sample(I.RAY3, n, seed=315)
+    p = (I.init_params(316, widths) * 3.0).astype(np.float32)
+    f32 = nb.Model(widths)
+    f32.set_params(p)
+    sp = nb.Model(widths, infer_prec="f16x3")
+    sp.set_params(p)
+    idx = np.sort(np.random.default_rng(317).choice(n, 20000, replace=False))
+    qs = q[torch.as_tensor(idx, device="cuda")].cpu().numpy()
+    z64 = O.forward(widths, p, qs)
+    S = O.forward_scale(widths, p, qs)
+    _, z32 = f32.query(q, logits=True)
+    z32s = z32.cpu().numpy()[idx].astype(np.float64)
+    assert np.max(np.abs(z32s - z64) / np.maximum(np.abs(z64), S)) <= REL_F32
+    del z32
+    tau = float(np.quantile(z64, 0.5))
+    f32.tau = tau
+    sp.tau = tau
+    b32, st = f32.query(q, margin=1e-3, stats=True)
+    bsp = sp.query(q, margin=0.05)
+    assert torch.equal(b32, bsp)
+    assert st["n_unresolved"] == 0
+    dec = nb.bits_to_numpy(b32, n)[idx]
+    tie = np.abs(z64 - tau) <= 1e-12 * max(1.0, abs(tau))
+    assert np.array_equal(dec[~tie], (z64 >= tau)[~tie])
