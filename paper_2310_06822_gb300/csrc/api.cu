@@ -104,6 +104,7 @@ struct nb_model {
     int act = NB_ACT_RELU;
     float *params = nullptr, *adam_m = nullptr, *adam_v = nullptr, *grad = nullptr;
     float *paramsT = nullptr;  // weights transposed, for the margin re-check and calibration
+    bool pT_stale = false;     // paramsT lags the master weights (set by training steps)
     int64_t step = 0;
     double tau = 0.0;
     float lr = 1e-3f, b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
@@ -267,8 +268,25 @@ extern "C" int64_t nb_model_param_count(const nb_model *m) { return m ? m->P : -
 static nb_status refresh_lowp(nb_model *m, cudaStream_t s) {
     const nb_status st = nb_launch_transpose(desc_of(m), m->paramsT, 1, m->P, s);
     if (st != NB_OK) return st;
+    m->pT_stale = false;
     if (m->infer_prec == NB_F32 && m->train_prec == NB_F32) return NB_OK;
     return nb_tc_refresh(&m->tc, desc_of(m), s);
+}
+
+// after a training step: the copies the next step and the tensor-core queries read; the
+// transposed copy (read by the re-check, the calibration and the thread-per-query
+// forward) is brought up to date by the next call that reads it, on that call's stream
+static nb_status refresh_after_step(nb_model *m, cudaStream_t s) {
+    m->pT_stale = true;
+    if (m->infer_prec == NB_F32 && m->train_prec == NB_F32) return NB_OK;
+    return nb_tc_refresh(&m->tc, desc_of(m), s);
+}
+
+static nb_status ensure_pT(nb_model *m, cudaStream_t s) {
+    if (!m->pT_stale) return NB_OK;
+    const nb_status st = nb_launch_transpose(desc_of(m), m->paramsT, 1, m->P, s);
+    if (st == NB_OK) m->pT_stale = false;
+    return st;
 }
 
 extern "C" nb_status nb_model_set_params(nb_model *m, const float *host_params, int64_t n_params) {
@@ -431,7 +449,7 @@ extern "C" nb_status nb_train_step(nb_model *m, const float *q, const uint32_t *
     st = nb_launch_adam(m->P, 1.0f / (float)n, m->params, m->adam_m, m->adam_v, m->grad, tw, m->lr, m->b1, m->b2,
                         m->eps, (float)c1, (float)sqrt(c2), dev_stats, s);
     if (st != NB_OK) return st;
-    return refresh_lowp(m, s);
+    return refresh_after_step(m, s);
 }
 
 extern "C" nb_status nb_query(nb_model *m, const float *q, int64_t n, float margin, uint32_t *out_bits,
@@ -445,6 +463,8 @@ extern "C" nb_status nb_query(nb_model *m, const float *q, int64_t n, float marg
     if (n == 0) return NB_OK;
     const size_t list = align256((size_t)n * sizeof(unsigned));
     nb_status st = ensure_ws(m, 256 + 2 * list);
+    if (st != NB_OK) return st;
+    st = ensure_pT(m, s);
     if (st != NB_OK) return st;
     QueryWs ws;
     ws.flag_count = (unsigned *)m->ws;
@@ -687,6 +707,8 @@ extern "C" nb_status nb_query_early_out(nb_model *early, nb_model *late, const f
     // gathers the others in one pass, its decisions certified by a rigorous bound
     const bool fused = early->infer_prec == NB_F32 && nb_early_settle_eligible(de);
     if (fused) {
+        st = ensure_pT(early, s);
+        if (st != NB_OK) return st;
         NB_CUDA(cudaMemsetAsync(count, 0, sizeof(unsigned), s));
         // bits_e holds each word's start in the gathered rows
         st = nb_launch_early_settle(de, q, n, nb_tau_bracket(early->tau), margin_early, out_bits, count, bits_e, qc,
@@ -766,6 +788,8 @@ extern "C" nb_status nb_calibrate(nb_model *m, const float *q, const uint32_t *l
     const size_t head = 256, list = align256((size_t)n * sizeof(unsigned));
     nb_status st = ensure_ws(m, head + 2 * list);
     if (st != NB_OK) return st;
+    st = ensure_pT(m, s);
+    if (st != NB_OK) return st;
     CalibWs ws;
     ws.umin_bits = (unsigned *)m->ws;
     ws.zmin_bits = (unsigned long long *)((char *)m->ws + 64);
@@ -843,5 +867,5 @@ extern "C" nb_status nb_train_step_noalloc(nb_model *m, const float *q, const ui
     st = nb_launch_adam(m->P, 1.0f / (float)n, m->params, m->adam_m, m->adam_v, m->grad, tw, m->lr, m->b1, m->b2,
                         m->eps, (float)c1, (float)sqrt(c2), dev_stats, s);
     if (st != NB_OK) return st;
-    return refresh_lowp(m, s);
+    return refresh_after_step(m, s);
 }
