@@ -276,10 +276,10 @@ static nb_status refresh_lowp(nb_model *m, cudaStream_t s) {
 // after a training step: the copies the next step and the tensor-core queries read; the
 // transposed copy (read by the re-check, the calibration and the thread-per-query
 // forward) is brought up to date by the next call that reads it, on that call's stream
-static nb_status refresh_after_step(nb_model *m, cudaStream_t s) {
+static nb_status refresh_after_step(nb_model *m, cudaStream_t s, bool train_img_written = false) {
     m->pT_stale = true;
     if (m->infer_prec == NB_F32 && m->train_prec == NB_F32) return NB_OK;
-    return nb_tc_refresh(&m->tc, desc_of(m), s);
+    return train_img_written ? nb_tc_refresh_query(&m->tc, desc_of(m), s) : nb_tc_refresh(&m->tc, desc_of(m), s);
 }
 
 static nb_status ensure_pT(nb_model *m, cudaStream_t s) {
@@ -446,10 +446,18 @@ extern "C" nb_status nb_train_step(nb_model *m, const float *q, const uint32_t *
          : bf16 ? nb_launch_train_bf16(&m->tc, d, q, label_bits, n, alpha, beta, tau, tw, dev_stats, s)
                 : nb_launch_train_f32(d, q, label_bits, n, alpha, beta, tau, tw, dev_stats, s);
     if (st != NB_OK) return st;
+    // the tcgen05 step's BF16 image is written by the Adam step itself
+    TrainImgMap img{};
+    if (tcgen) {
+        img.img = (uint8_t *)m->tc.train_img;
+        img.NH = m->L - 1;
+        for (int l = 0; l <= m->L; l++) img.w[l] = m->widths[l];
+        for (int l = 0; l < m->L; l++) img.off[l] = m->off[l];
+    }
     st = nb_launch_adam(m->P, 1.0f / (float)n, m->params, m->adam_m, m->adam_v, m->grad, tw, m->lr, m->b1, m->b2,
-                        m->eps, (float)c1, (float)sqrt(c2), dev_stats, s);
+                        m->eps, (float)c1, (float)sqrt(c2), dev_stats, s, img);
     if (st != NB_OK) return st;
-    return refresh_after_step(m, s);
+    return refresh_after_step(m, s, tcgen);
 }
 
 extern "C" nb_status nb_query(nb_model *m, const float *q, int64_t n, float margin, uint32_t *out_bits,

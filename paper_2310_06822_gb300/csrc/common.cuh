@@ -119,6 +119,22 @@ struct TrainWs {
 int nb_train_f32_ctas(const MlpDesc &d, int64_t n, int num_sms);
 nb_status nb_launch_train_f32(const MlpDesc &d, const float *q, const uint32_t *labels, int64_t n, float alpha,
                               float beta, TauF tau, TrainWs ws, nb_step_stats *st, cudaStream_t s);
+// The BF16 copy of the hidden layers' weights that the tcgen05 training step reads (its
+// "training image"), written by the Adam step as it updates each weight; img null: none.
+// Layer 0 (128 x 16) is 8 x 16-byte core matrices; layers 1 .. NH-1 are two 64-column
+// blocks of 128 rows each, 128-byte swizzled, after the first layer's 4 KB.
+struct TrainImgMap {
+    uint8_t *img = nullptr;
+    int NH = 0;                 // hidden layers (image layers 0 .. NH - 1)
+    int w[NB_MAXL + 1] = {0};
+    int off[NB_MAXL] = {0};
+};
+__host__ __device__ __forceinline__ uint32_t nb_train_img_offset(int l, int n, int k) {
+    if (l == 0)
+        return (uint32_t)(n >> 3) * 256u + (uint32_t)(k >> 3) * 128u + (uint32_t)(n & 7) * 16u + (uint32_t)(k & 7) * 2u;
+    return 4096u + (uint32_t)(l - 1) * 32768u + (uint32_t)(k >> 6) * 16384u + (uint32_t)n * 128u +
+           ((uint32_t)(((k & 63) >> 3) ^ (n & 7)) << 4) + (uint32_t)(k & 7) * 2u;
+}
 nb_status nb_launch_adam(int64_t P, float inv_n, float *params, float *m, float *v, float *grad,
                          TrainWs ws, float lr, float b1, float b2, float eps, float c1, float sqrt_c2,
-                         nb_step_stats *st, cudaStream_t s);
+                         nb_step_stats *st, cudaStream_t s, const TrainImgMap &img = TrainImgMap{});

@@ -3,6 +3,7 @@
 //   fwd_f32_kernel     plain FP32 forward over query tiles -> decision bits, margin flags
 //   train_f32_kernel   forward + asymmetric BCE of Eq. (loss) + backward, per-CTA partials
 //   adam_kernel        deterministic reduction of the partials + Adam (Sec. 3.4 "Training")
+#include <cuda_bf16.h>
 #include <math.h>
 
 #include "common.cuh"
@@ -86,7 +87,7 @@ __global__ void __launch_bounds__(ADAM_P * ADAM_S) adam_kernel(long long P, int 
                                                                float *__restrict__ params, float *__restrict__ m,
                                                                float *__restrict__ v, float *__restrict__ grad,
                                                                float lr, float b1, float b2, float eps, float c1,
-                                                               float sqrt_c2, nb_step_stats *st) {
+                                                               float sqrt_c2, nb_step_stats *st, TrainImgMap img) {
     __shared__ float part[ADAM_S][ADAM_P + 1];
     const int pc = threadIdx.x % ADAM_P, sl = threadIdx.x / ADAM_P;
     if (blockIdx.x == 0 && st) {  // the loss: same slicing over the CTAs' loss partials
@@ -116,7 +117,21 @@ __global__ void __launch_bounds__(ADAM_P * ADAM_S) adam_kernel(long long P, int 
     m[p] = mm;
     v[p] = vv;
     const float denom = sqrtf(vv) / sqrt_c2 + eps;
-    params[p] = params[p] - (lr / c1) * (mm / denom);
+    const float np_ = params[p] - (lr / c1) * (mm / denom);
+    params[p] = np_;
+    if (img.img) {
+        // the weight's BF16 copy in the training image (biases and the head are read in
+        // FP32 from the master copy)
+        for (int l = 0; l < img.NH; l++) {
+            const long long r = p - img.off[l];
+            const int K = img.w[l], N = img.w[l + 1];
+            if (r >= 0 && r < (long long)N * K) {
+                const int n = (int)(r / K), k = (int)(r - (long long)n * K);
+                *reinterpret_cast<__nv_bfloat16 *>(img.img + nb_train_img_offset(l, n, k)) = __float2bfloat16_rn(np_);
+                break;
+            }
+        }
+    }
 }
 
 int nj_for(int maxw) {
@@ -207,11 +222,11 @@ nb_status nb_launch_train_f32(const MlpDesc &d, const float *q, const uint32_t *
 
 nb_status nb_launch_adam(int64_t P, float inv_n, float *params, float *m, float *v, float *grad, TrainWs ws,
                          float lr, float b1, float b2, float eps, float c1, float sqrt_c2, nb_step_stats *st,
-                         cudaStream_t s) {
+                         cudaStream_t s, const TrainImgMap &img) {
     const int64_t blocks = (P + ADAM_P - 1) / ADAM_P;
     adam_kernel<<<(unsigned)blocks, ADAM_P * ADAM_S, 0, s>>>((long long)P, ws.G, ws.stride > 0 ? ws.stride : (long long)P,
                                                  ws.partial, ws.loss_partial, inv_n, params, m, v, grad, lr, b1, b2,
-                                                 eps, c1, sqrt_c2, st);
+                                                 eps, c1, sqrt_c2, st, img);
     NB_CUDA(cudaGetLastError());
     return NB_OK;
 }

@@ -444,6 +444,10 @@ nb_status nb_tc_refresh(TcModel *tc, const MlpDesc &d, cudaStream_t s) {
         const nb_status st = tc->train_tc ? nb_train_tc_refresh(tc, d, s) : nb_train_bf16_refresh(tc, d, s);
         if (st != NB_OK) return st;
     }
+    return nb_tc_refresh_query(tc, d, s);
+}
+
+nb_status nb_tc_refresh_query(TcModel *tc, const MlpDesc &d, cudaStream_t s) {
     if (!tc->img) return NB_OK;
     if (tc->pad_p) {
         pad_params_kernel<<<dim3(32, d.L), 256, 0, s>>>(d, tc->pad, tc->pad_p);

@@ -41,6 +41,8 @@ nb_status nb_tc_check(TcModel *tc);
 nb_status nb_tc_init(TcModel *tc, const MlpDesc &d, int infer_prec, int train_prec);
 void nb_tc_free(TcModel *tc);
 nb_status nb_tc_refresh(TcModel *tc, const MlpDesc &d, cudaStream_t s);
+// the inference images only (the training image left as it is)
+nb_status nb_tc_refresh_query(TcModel *tc, const MlpDesc &d, cudaStream_t s);
 nb_status nb_tc_query(TcModel *tc, const MlpDesc &d, const float *q, int64_t n, TauF tau, float margin,
                       uint32_t *bits, float *logits, nb_query_stats *st, QueryWs ws, cudaStream_t s);
 // BF16 tensor-core training step (train_bf16.cu)
