@@ -218,3 +218,36 @@ def test_narrow_full_size_16m_rays(nb, widths):
     dec = nb.bits_to_numpy(b32, n)[idx]
     tie = np.abs(z64 - tau) <= 1e-12 * max(1.0, abs(tau))
     assert np.array_equal(dec[~tie], (z64 >= tau)[~tie])
+
+
+@pytest.mark.parametrize("w0,hidden", [(3, 64), (6, 200), (2, 9)])
+def test_early_settle_bound_is_sound_row_by_row(nb, w0, hidden):
+    """With the late network answering 0 for every finite row, a 1 bit marks a settled row:
+    each must have an exact (FP64) early logit below the early threshold, and every row
+    below it by more than a small slack must be settled.  The threshold sits on the median
+    logit, so half of the rows are within reach of it and many within FP32 rounding."""
+    early_w, late_w = [w0, hidden, 1], [w0, 128, 128, 128, 1]
+    early = nb.Model(early_w)
+    p = (I.init_params(318 + w0, early_w) * 3.0).astype(np.float32)
+    early.set_params(p)
+    late = nb.Model(late_w, infer_prec="f16x3")
+    late.set_params(I.init_params(319, late_w))
+    late.tau = 1e30
+    n = 300_007
+    q = np.random.default_rng(320 + w0).uniform(-1.0, 1.0, (n, w0)).astype(np.float32)
+    ze = O.forward(early_w, p, q)
+    _, z32 = early.query(_dev(q), logits=True)
+    z32 = z32.cpu().numpy()
+    # thresholds: the median exact logit, and a float just above an FP32 logit (rows whose
+    # FP32 value rounds across it)
+    for tau_e in (float(np.median(ze)), float(np.nextafter(np.float32(np.quantile(z32, 0.6)), np.float32(np.inf)))):
+        early.tau = tau_e
+        for margin in (0.0, 1e-3):
+            bits, st = nb.query_early_out(early, late, _dev(q), margin_early=margin, margin_late=0.0)
+            settled = nb.bits_to_numpy(bits, n)
+            tie = np.abs(ze - tau_e) <= 1e-12 * max(1.0, abs(tau_e))
+            assert not np.any(settled & ~tie & (ze >= tau_e)), (tau_e, margin)  # sound
+            S = O.forward_scale(early_w, p, q)
+            clear = ze < tau_e - margin - 1e-4 * S  # far below the FP32 rounding of the logit
+            assert np.all(settled[clear]), (tau_e, margin, int((clear & ~settled).sum()))
+            assert st["n_early_inside"] == int(settled.sum())
