@@ -542,7 +542,9 @@ def run_c3(args):
 
 
 # ---------------------------------------------------------------------------------- early-out
-EARLY_STEPS_FACTOR = 4
+EARLY_STEPS_FACTOR = 8
+# the one-pass settle test is certified by its own rounding bound: no extra margin
+MARGIN_EARLY = 0.0
 
 
 def run_c2e(args):
@@ -567,9 +569,9 @@ def run_c2e(args):
         q = nb.sample(I.POINT3, BATCH, SEED_TRAIN, first=t * BATCH)
         y = nb.label(shape, I.POINT3, q)
         late_t.train_step(q, y, 1.0 + 99.0 * t / max(T - 1, 1))
-    # the one-hidden-layer early network costs little to train: it gets EARLY_STEPS_FACTOR
+    # the one-hidden-layer early network costs little to train: it gets --early-steps-factor
     # times the late network's steps (the share of rows it settles grows with them)
-    TE = EARLY_STEPS_FACTOR * T
+    TE = args.early_steps_factor * T
     for t in range(TE):
         q = nb.sample(I.POINT3, BATCH, SEED_TRAIN, first=t * BATCH)
         y = nb.label(shape, I.POINT3, q)
@@ -585,10 +587,10 @@ def run_c2e(args):
     late.calibrate(eq, ey)
     early.calibrate(eq, nb.bits_not(ey, n))
     out = torch.empty(nb.n_words(n), dtype=torch.int32, device=dev)
-    bits, est = nb.query_early_out(early, late, eq, margin_early=1e-3, margin_late=MARGIN, out=out)
+    bits, est = nb.query_early_out(early, late, eq, margin_early=MARGIN_EARLY, margin_late=MARGIN, out=out)
     y = nb.bits_to_numpy(ey, n)
     dec = nb.bits_to_numpy(bits, n)
-    ms, clocks = ctx.timed(lambda: nb.query_early_out(early, late, eq, margin_early=1e-3, margin_late=MARGIN,
+    ms, clocks = ctx.timed(lambda: nb.query_early_out(early, late, eq, margin_early=MARGIN_EARLY, margin_late=MARGIN,
                                                       out=out), args.steps, args.warmup)
     plain_ms = ctx.time_ms(lambda: late.query(eq, margin=MARGIN, out=out), max(3, args.steps // 4))
     early_ms = ctx.time_ms(lambda: early.query(eq, margin=1e-3, out=out), max(3, args.steps // 4))
@@ -1088,6 +1090,8 @@ def main():
     ap.add_argument("--n-eval", type=int, default=N_EVAL, help="evaluation size (smaller only for profiling)")
     ap.add_argument("--early-hidden", type=int, default=64,
                     help="c2e: hidden width of the one-hidden-layer early network")
+    ap.add_argument("--early-steps-factor", type=int, default=EARLY_STEPS_FACTOR,
+                    help="c2e: the early network's training steps as a multiple of the late network's")
     ap.add_argument("--activation", default="relu", choices=["relu", "sine"],
                     help="hidden activation of the c6 networks (sine: the paper's sinusoidal activation)")
     args = ap.parse_args()
