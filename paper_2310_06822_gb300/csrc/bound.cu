@@ -55,16 +55,41 @@ __device__ __forceinline__ unsigned long long ord_f64(double f) {
 // outputs overwrite the inputs after a barrier, so a CTA needs two activation buffers and
 // one weight chunk -- a third of the shared memory of separate in/out buffers -- and two
 // or more CTAs share an SM to hide the staging latency.
+//
+// Shared-memory loads, not the FMA pipe, bound the scalar form (2 MI + NJ loads per
+// 2 MI NJ FMAs).  From NJ = 4 on, a thread owns groups of four consecutive neurons
+// (64 g + 4 tn + e) and the inner loop takes four inputs at a time: the activations and
+// their bounds as float4s along k, the weights as float4s along n, conflict-free (16
+// threads read 256 consecutive bytes).  The row stride is then a multiple of four.
 constexpr int KC = 32;
+template <int NJ>
+__host__ __device__ constexpr int kp_of() {
+    return NJ >= 4 ? 16 * NJ + 4 : 16 * NJ + 1;
+}
+
+// the weight chunks of the vector form: CK input rows, double-buffered (2 CK WS floats)
+template <int NJ>
+__host__ __device__ constexpr int chunk_of() {
+    return NJ >= 4 ? 16 : KC;
+}
+template <int NJ>
+__host__ __device__ constexpr int wt_floats() {
+    return NJ >= 4 ? 2 * chunk_of<NJ>() * kp_of<NJ>() : KC * kp_of<NJ>();
+}
+
 template <int NJ, int MI>
 __device__ __forceinline__ void bound_layer_tile(const float *__restrict__ Wt, const float *__restrict__ b, int K,
                                                  int N, float g, float *a_s, float *e_s, float *wt, int KP, int act) {
-    constexpr int WS = 16 * NJ + 1;
+    constexpr int WS = kp_of<NJ>();
+    constexpr bool VEC = NJ >= 4;
+    constexpr int CK = chunk_of<NJ>();
     const int t = threadIdx.x, tn = t & 15, tm = t >> 4;
+    // neuron j of this thread
+    auto neuron = [&](int j) { return VEC ? 64 * (j >> 2) + 4 * tn + (j & 3) : tn + 16 * j; };
     float acc[MI][NJ], bnd[MI][NJ];
 #pragma unroll
     for (int j = 0; j < NJ; j++) {
-        const int nn = tn + 16 * j;
+        const int nn = neuron(j);
         const float bv = nn < N ? __ldg(b + nn) : 0.f;
         const float bb = __fmul_ru(g, fabsf(bv));
 #pragma unroll
@@ -73,15 +98,55 @@ __device__ __forceinline__ void bound_layer_tile(const float *__restrict__ Wt, c
             bnd[i][j] = bb;
         }
     }
-    for (int kc = 0; kc < K; kc += KC) {
-        const int kw = min(KC, K - kc);
-        __syncthreads();  // inputs in place, previous chunk consumed
-        for (int e = t; e < N * KC; e += blockDim.x) {
+    // rows kc .. kc + kw of W^T (contiguous: kw N floats) into buffer dst, scalar loads
+    auto stage = [&](float *dst, int kc, int kw) {
+        for (int e = t; e < N * CK; e += blockDim.x) {
             const int kk = e / N, nn = e % N;
-            wt[kk * WS + nn] = kk < kw ? __ldg(Wt + (size_t)(kc + kk) * N + nn) : 0.f;
+            dst[kk * WS + nn] = kk < kw ? __ldg(Wt + (size_t)(kc + kk) * N + nn) : 0.f;
         }
-        __syncthreads();
-        for (int kk = 0; kk < kw; kk++) {
+    };
+    // one chunk's products: inputs kc .. kc + kw against the staged rows in w_s
+    auto chunk = [&](const float *w_s, int kc, int kw) {
+        int kk = 0;
+        if constexpr (VEC) {
+            for (; kk + 4 <= kw; kk += 4) {
+                float a[MI][4], v[MI][4];
+#pragma unroll
+                for (int i = 0; i < MI; i++) {
+                    const int idx = (tm + 16 * i) * KP + kc + kk;
+                    const float4 a4 = *reinterpret_cast<const float4 *>(a_s + idx);
+                    const float4 e4 = *reinterpret_cast<const float4 *>(e_s + idx);
+                    a[i][0] = a4.x;
+                    a[i][1] = a4.y;
+                    a[i][2] = a4.z;
+                    a[i][3] = a4.w;
+                    v[i][0] = __fmaf_ru(g, fabsf(a4.x), e4.x);
+                    v[i][1] = __fmaf_ru(g, fabsf(a4.y), e4.y);
+                    v[i][2] = __fmaf_ru(g, fabsf(a4.z), e4.z);
+                    v[i][3] = __fmaf_ru(g, fabsf(a4.w), e4.w);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    float w[NJ];
+#pragma unroll
+                    for (int q4 = 0; q4 < NJ / 4; q4++) {
+                        const float4 w4 = *reinterpret_cast<const float4 *>(w_s + (kk + u) * WS + 64 * q4 + 4 * tn);
+                        w[4 * q4] = w4.x;
+                        w[4 * q4 + 1] = w4.y;
+                        w[4 * q4 + 2] = w4.z;
+                        w[4 * q4 + 3] = w4.w;
+                    }
+#pragma unroll
+                    for (int i = 0; i < MI; i++)
+#pragma unroll
+                        for (int j = 0; j < NJ; j++) {
+                            acc[i][j] = fmaf(a[i][u], w[j], acc[i][j]);
+                            bnd[i][j] = __fmaf_ru(v[i][u], fabsf(w[j]), bnd[i][j]);
+                        }
+                }
+            }
+        }
+        for (; kk < kw; kk++) {
             float a[MI], v[MI], w[NJ];
 #pragma unroll
             for (int i = 0; i < MI; i++) {
@@ -90,7 +155,7 @@ __device__ __forceinline__ void bound_layer_tile(const float *__restrict__ Wt, c
                 v[i] = __fmaf_ru(g, fabsf(a[i]), e_s[idx]);
             }
 #pragma unroll
-            for (int j = 0; j < NJ; j++) w[j] = wt[kk * WS + tn + 16 * j];
+            for (int j = 0; j < NJ; j++) w[j] = w_s[kk * WS + neuron(j)];
 #pragma unroll
             for (int i = 0; i < MI; i++)
 #pragma unroll
@@ -99,11 +164,64 @@ __device__ __forceinline__ void bound_layer_tile(const float *__restrict__ Wt, c
                     bnd[i][j] = __fmaf_ru(v[i], fabsf(w[j]), bnd[i][j]);
                 }
         }
+    };
+    if constexpr (!VEC) {
+        for (int kc = 0; kc < K; kc += CK) {
+            const int kw = min(CK, K - kc);
+            __syncthreads();  // inputs in place, previous chunk consumed
+            stage(wt, kc, kw);
+            __syncthreads();
+            chunk(wt, kc, kw);
+        }
+    } else {
+        // Double-buffered chunks: the next chunk's rows are loaded into registers (float4s,
+        // when the rows are 16-byte aligned) while this chunk's products run, then stored
+        // into the other buffer; one barrier per chunk.  A buffer is rewritten only after the
+        // barrier that ends the products reading it.
+        constexpr int PRE = (CK * 16 * NJ / 4 + 255) / 256;  // float4s per thread and chunk
+        const bool vload = (N % 4 == 0) && ((reinterpret_cast<uintptr_t>(Wt) & 15u) == 0);
+        const int nch = (K + CK - 1) / CK;
+        __syncthreads();  // inputs in place, the previous layer's last chunk consumed
+        stage(wt, 0, min(CK, K));
+        __syncthreads();
+        for (int c = 0; c < nch; c++) {
+            const int kc = c * CK, kw = min(CK, K - kc);
+            const bool next = c + 1 < nch;
+            const int kn = kc + CK, kwn = next ? min(CK, K - kn) : 0;
+            float4 pre[PRE];
+            if (next && vload) {
+                const float4 *src = reinterpret_cast<const float4 *>(Wt + (size_t)kn * N);
+                const int n4 = kwn * N / 4;
+#pragma unroll
+                for (int r = 0; r < PRE; r++) {
+                    const int e4 = t + 256 * r;
+                    pre[r] = e4 < n4 ? __ldg(src + e4) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+            chunk(wt + (c & 1) * CK * WS, kc, kw);
+            if (next) {
+                float *dst = wt + ((c + 1) & 1) * CK * WS;
+                if (vload) {
+                    const int n4 = kwn * N / 4;
+#pragma unroll
+                    for (int r = 0; r < PRE; r++) {
+                        const int e4 = t + 256 * r;
+                        if (e4 < n4) {
+                            const int e = 4 * e4, kk = e / N, nn = e % N;
+                            *reinterpret_cast<float4 *>(dst + kk * WS + nn) = pre[r];
+                        }
+                    }
+                } else {
+                    stage(dst, kn, kwn);
+                }
+            }
+            __syncthreads();
+        }
     }
     __syncthreads();  // every thread has read the inputs: overwrite them
 #pragma unroll
     for (int j = 0; j < NJ; j++) {
-        const int nn = tn + 16 * j;
+        const int nn = neuron(j);
         if (nn < N)
 #pragma unroll
             for (int i = 0; i < MI; i++) {
@@ -130,11 +248,12 @@ __device__ __forceinline__ int decide_interval(float lo, float hi, TauF tau) {
 // MODE 1: calibration: lower bound of every listed (positive) query -> lo_out,
 //         minimum upper bound -> umin_bits.
 template <int NJ, int MI, int MODE>
-__global__ void __launch_bounds__(256) bound_tile_kernel(MlpDesc d, GammaTab gt, const float *__restrict__ q, TauF tau,
+__global__ void __launch_bounds__(256, 2) bound_tile_kernel(const __grid_constant__ MlpDesc d, const __grid_constant__ GammaTab gt,
+                                                         const float *__restrict__ q, TauF tau,
                                                          const unsigned *count, const unsigned *idx, uint32_t *bits,
                                                          nb_query_stats *st, unsigned *ff_count, unsigned *ff_idx,
                                                          float *lo_out, unsigned *umin_bits, unsigned direct_max) {
-    constexpr int TM = 16 * MI, KP = 16 * NJ + 1, TPQ = 256 / TM;
+    constexpr int TM = 16 * MI, KP = kp_of<NJ>(), TPQ = 256 / TM;
     extern __shared__ float smem[];
     float *a0 = smem, *e0 = a0 + TM * KP, *wt = e0 + TM * KP;
     __shared__ unsigned rowidx[TM];
@@ -667,8 +786,8 @@ template <int NJ, int MI, int MODE>
 nb_status tile_launch(const MlpDesc &d, const GammaTab &gt, const float *q, TauF tau, const unsigned *count,
                       const unsigned *idx, int64_t max_count, uint32_t *bits, nb_query_stats *st, unsigned *ff_count,
                       unsigned *ff_idx, float *lo_out, unsigned *umin_bits, cudaStream_t s) {
-    constexpr int TM = 16 * MI, KP = 16 * NJ + 1;
-    const size_t smem = (size_t)(2 * TM * KP + KC * (16 * NJ + 1)) * sizeof(float);
+    constexpr int TM = 16 * MI, KP = kp_of<NJ>();
+    const size_t smem = (size_t)(2 * TM * KP + wt_floats<NJ>()) * sizeof(float);
     auto k = bound_tile_kernel<NJ, MI, MODE>;
     NB_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 1;
