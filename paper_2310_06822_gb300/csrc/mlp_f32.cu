@@ -16,7 +16,8 @@ using namespace nbf32;
 
 // ------------------------------------------------------------------ fast FP32 forward
 template <int NJ>
-__global__ void __launch_bounds__(256) fwd_f32_kernel(MlpDesc d, const float *__restrict__ q, long long n, TauF tau,
+__global__ void __launch_bounds__(256, NJ >= 16 ? 1 : 2) fwd_f32_kernel(const __grid_constant__ MlpDesc d,
+                                                                        const float *__restrict__ q, long long n, TauF tau,
                                                       float margin, uint32_t *__restrict__ bits,
                                                       float *__restrict__ logits, nb_query_stats *st,
                                                       unsigned *flag_count, unsigned *flag_idx) {
@@ -28,7 +29,9 @@ __global__ void __launch_bounds__(256) fwd_f32_kernel(MlpDesc d, const float *__
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const long long base = tile * TMF;
         const int rows = (int)min((long long)TMF, n - base);
-        fwd_tile<NJ>(d, q, base, rows, tau, margin, bits, logits, flag_count, flag_idx, smem, zs, c_in, c_flag, c_nf);
+        // from width 49 on, the weights come from the transposed copy with float4 loads
+        fwd_tile<NJ, (NJ >= 4)>(d, q, base, rows, tau, margin, bits, logits, flag_count, flag_idx, smem, zs, c_in,
+                                c_flag, c_nf);
     }
     if (st && lane == 0 && t < TMF) {
         if (c_in) atomicAdd(&st->n_inside, c_in);
@@ -153,8 +156,7 @@ int num_sms() {
 template <int NJ>
 nb_status fwd_launch(const MlpDesc &d, const float *q, int64_t n, TauF tau, float margin, uint32_t *bits,
                      float *logits, nb_query_stats *st, QueryWs ws, cudaStream_t s) {
-    constexpr int KP = 16 * NJ + 1;
-    const size_t smem = (size_t)(2 * TMF * KP + KC * (16 * NJ + 1)) * sizeof(float);
+    const size_t smem = (size_t)fwd_tile_floats<NJ>(NJ >= 4) * sizeof(float);
     auto k = fwd_f32_kernel<NJ>;
     NB_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 1;

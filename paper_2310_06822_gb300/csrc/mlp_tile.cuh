@@ -15,18 +15,36 @@ template <int NJ, int MI>
 __device__ __forceinline__ void hidden_layer_tile(const float *__restrict__ W, const float *__restrict__ b, int K,
                                                   int N, const float *ain, float *aout, float *wt, int KP, int act,
                                                   float *cout);
+template <int NJ, int MI>
+__device__ __forceinline__ void hidden_layer_tile_t(const float *__restrict__ Wt, const float *__restrict__ b, int K,
+                                                    int N, const float *ain, float *aout, float *wt, int KP, int act);
+
+// Layout of the forward tile from the transposed weights (TR, widths above 48): rows of
+// KP_T floats (a multiple of four, for float4 loads), weights staged in two chunks of CK_T
+// input rows.
+template <int NJ>
+__host__ __device__ constexpr int kp_fwd(bool tr) {
+    return tr ? 16 * NJ + 4 : 16 * NJ + 1;
+}
+constexpr int CK_T = 16;
+template <int NJ>
+__host__ __device__ constexpr int fwd_tile_floats(bool tr) {
+    return tr ? 2 * TMF * kp_fwd<NJ>(true) + 2 * CK_T * kp_fwd<NJ>(true)
+              : 2 * TMF * kp_fwd<NJ>(false) + KC * (16 * NJ + 1);
+}
 
 // Forward of one tile of TMF queries starting at row `base` (rows valid) with the
 // decision z >= tau: bits of the tile's 32-row words (base is a multiple of 32),
 // optional logits, and the margin band appended to flag_idx.  A non-finite logit is
-// always flagged.  smem: 2 x [TMF][KP] activations + [KC][16 NJ + 1] weight chunk.
-template <int NJ>
+// always flagged.  smem: 2 x [TMF][KP] activations + [KC][16 NJ + 1] weight chunk, or
+// with TR (the weights read from the transposed copy d.pT, NJ >= 4) fwd_tile_floats<NJ>(true).
+template <int NJ, bool TR = false>
 __device__ __forceinline__ void fwd_tile(const MlpDesc &d, const float *__restrict__ q, long long base, int rows,
                                          TauF tau, float margin, uint32_t *__restrict__ bits,
                                          float *__restrict__ logits, unsigned *flag_count, unsigned *flag_idx,
                                          float *smem, float *zs, unsigned long long &c_in,
                                          unsigned long long &c_flag, unsigned long long &c_nf) {
-    constexpr int KP = 16 * NJ + 1;
+    constexpr int KP = kp_fwd<NJ>(TR);
     float *act0 = smem;
     float *act1 = act0 + TMF * KP;
     float *wt = act1 + TMF * KP;
@@ -40,8 +58,13 @@ __device__ __forceinline__ void fwd_tile(const MlpDesc &d, const float *__restri
     float *ain = act0, *aout = act1;
     for (int l = 0; l < d.L - 1; l++) {
         const int K = d.w[l], N = d.w[l + 1];
-        const float *W = d.p + d.off[l];
-        hidden_layer_tile<NJ, TMF / 16>(W, W + (size_t)N * K, K, N, ain, aout, wt, KP, d.act, nullptr);
+        if constexpr (TR) {
+            const float *Wt = d.pT + d.off[l];
+            hidden_layer_tile_t<NJ, TMF / 16>(Wt, Wt + (size_t)N * K, K, N, ain, aout, wt, KP, d.act);
+        } else {
+            const float *W = d.p + d.off[l];
+            hidden_layer_tile<NJ, TMF / 16>(W, W + (size_t)N * K, K, N, ain, aout, wt, KP, d.act, nullptr);
+        }
         float *tmp = ain;
         ain = aout;
         aout = tmp;
@@ -141,6 +164,125 @@ __device__ __forceinline__ void hidden_layer_tile(const float *__restrict__ W, c
                     aout[o] = fmaxf(acc[i][j], 0.f);
                 }
             }
+    }
+}
+
+// Hidden layer from the transposed weights Wt = W^T [K][N] (contiguous rows, 16-byte
+// aligned when N is a multiple of four), NJ >= 4: thread (tm, tn) owns rows tm + 16 i and
+// groups of four consecutive neurons 64 g + 4 tn + e; activations are read as float4s along
+// k and weights as float4s along n (16 threads read 256 consecutive bytes), so a shared-
+// memory load feeds 4 MI (activations) or 4 MI (weights) FMAs instead of MI or 1.  The
+// weights are staged in two CK_T-row buffers: the next chunk is loaded into registers while
+// the current one's products run, then stored into the other buffer; one barrier per chunk.
+// aout[m][n] = act(b_n + sum_k W[n][k] ain[m][k]); KP a multiple of four.
+template <int NJ, int MI>
+__device__ __forceinline__ void hidden_layer_tile_t(const float *__restrict__ Wt, const float *__restrict__ b, int K,
+                                                    int N, const float *ain, float *aout, float *wt, int KP, int act) {
+    constexpr int CK = CK_T;
+    const int WS = KP;
+    const int t = threadIdx.x, tn = t & 15, tm = t >> 4;
+    auto neuron = [&](int j) { return 64 * (j >> 2) + 4 * tn + (j & 3); };
+    float acc[MI][NJ];
+#pragma unroll
+    for (int j = 0; j < NJ; j++) {
+        const int nn = neuron(j);
+        const float bv = nn < N ? __ldg(b + nn) : 0.f;
+#pragma unroll
+        for (int i = 0; i < MI; i++) acc[i][j] = bv;
+    }
+    auto stage = [&](float *dst, int kc, int kw) {
+        for (int e = t; e < N * CK; e += blockDim.x) {
+            const int kk = e / N, nn = e % N;
+            dst[kk * WS + nn] = kk < kw ? __ldg(Wt + (size_t)(kc + kk) * N + nn) : 0.f;
+        }
+    };
+    auto chunk = [&](const float *w_s, int kc, int kw) {
+        int kk = 0;
+        for (; kk + 4 <= kw; kk += 4) {
+            float a[MI][4];
+#pragma unroll
+            for (int i = 0; i < MI; i++) {
+                const float4 a4 = *reinterpret_cast<const float4 *>(ain + (tm + 16 * i) * KP + kc + kk);
+                a[i][0] = a4.x;
+                a[i][1] = a4.y;
+                a[i][2] = a4.z;
+                a[i][3] = a4.w;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                float w[NJ];
+#pragma unroll
+                for (int q4 = 0; q4 < NJ / 4; q4++) {
+                    const float4 w4 = *reinterpret_cast<const float4 *>(w_s + (kk + u) * WS + 64 * q4 + 4 * tn);
+                    w[4 * q4] = w4.x;
+                    w[4 * q4 + 1] = w4.y;
+                    w[4 * q4 + 2] = w4.z;
+                    w[4 * q4 + 3] = w4.w;
+                }
+#pragma unroll
+                for (int i = 0; i < MI; i++)
+#pragma unroll
+                    for (int j = 0; j < NJ; j++) acc[i][j] = fmaf(a[i][u], w[j], acc[i][j]);
+            }
+        }
+        for (; kk < kw; kk++) {
+            float a[MI];
+#pragma unroll
+            for (int i = 0; i < MI; i++) a[i] = ain[(tm + 16 * i) * KP + kc + kk];
+#pragma unroll
+            for (int j = 0; j < NJ; j++) {
+                const float w = w_s[kk * WS + neuron(j)];
+#pragma unroll
+                for (int i = 0; i < MI; i++) acc[i][j] = fmaf(a[i], w, acc[i][j]);
+            }
+        }
+    };
+    constexpr int PRE = (CK * 16 * NJ / 4 + 255) / 256;
+    const bool vload = (N % 4 == 0) && ((reinterpret_cast<uintptr_t>(Wt) & 15u) == 0);
+    const int nch = (K + CK - 1) / CK;
+    __syncthreads();  // inputs written, the previous layer's chunks consumed
+    stage(wt, 0, min(CK, K));
+    __syncthreads();
+    for (int c = 0; c < nch; c++) {
+        const int kc = c * CK, kw = min(CK, K - kc);
+        const bool next = c + 1 < nch;
+        const int kn = kc + CK, kwn = next ? min(CK, K - kn) : 0;
+        float4 pre[PRE];
+        if (next && vload) {
+            const float4 *src = reinterpret_cast<const float4 *>(Wt + (size_t)kn * N);
+            const int n4 = kwn * N / 4;
+#pragma unroll
+            for (int r = 0; r < PRE; r++) {
+                const int e4 = t + 256 * r;
+                pre[r] = e4 < n4 ? __ldg(src + e4) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+        chunk(wt + (c & 1) * CK * WS, kc, kw);
+        if (next) {
+            float *dst = wt + ((c + 1) & 1) * CK * WS;
+            if (vload) {
+                const int n4 = kwn * N / 4;
+#pragma unroll
+                for (int r = 0; r < PRE; r++) {
+                    const int e4 = t + 256 * r;
+                    if (e4 < n4) {
+                        const int e = 4 * e4, kk = e / N, nn = e % N;
+                        *reinterpret_cast<float4 *>(dst + kk * WS + nn) = pre[r];
+                    }
+                }
+            } else {
+                stage(dst, kn, kwn);
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < NJ; j++) {
+        const int nn = neuron(j);
+        if (nn < N)
+#pragma unroll
+            for (int i = 0; i < MI; i++)
+                aout[(tm + 16 * i) * KP + nn] = act == NB_ACT_SINE ? sinf(acc[i][j]) : fmaxf(acc[i][j], 0.f);
     }
 }
 
