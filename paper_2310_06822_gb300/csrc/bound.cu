@@ -248,7 +248,7 @@ __device__ __forceinline__ int decide_interval(float lo, float hi, TauF tau) {
 // MODE 1: calibration: lower bound of every listed (positive) query -> lo_out,
 //         minimum upper bound -> umin_bits.
 template <int NJ, int MI, int MODE>
-__global__ void __launch_bounds__(256, 2) bound_tile_kernel(const __grid_constant__ MlpDesc d, const __grid_constant__ GammaTab gt,
+__global__ void __launch_bounds__(256, (NJ >= 16 && MI >= 4) ? 1 : 2) bound_tile_kernel(const __grid_constant__ MlpDesc d, const __grid_constant__ GammaTab gt,
                                                          const float *__restrict__ q, TauF tau,
                                                          const unsigned *count, const unsigned *idx, uint32_t *bits,
                                                          nb_query_stats *st, unsigned *ff_count, unsigned *ff_idx,
@@ -819,7 +819,7 @@ nb_status tile_dispatch(const MlpDesc &d, const GammaTab &gt, const float *q, Ta
     if (nj <= 8)
         return tile_launch<8, 4, MODE>(d, gt, q, tau, count, idx, max_count, bits, st, ff_count, ff_idx, lo_out,
                                        umin_bits, s);
-    return tile_launch<16, 2, MODE>(d, gt, q, tau, count, idx, max_count, bits, st, ff_count, ff_idx, lo_out,
+    return tile_launch<16, 4, MODE>(d, gt, q, tau, count, idx, max_count, bits, st, ff_count, ff_idx, lo_out,
                                     umin_bits, s);
 }
 
