@@ -540,7 +540,12 @@ bool plan(const MlpDesc &d, NarrowDesc &nd) {
     nd.act = d.act;
     int widest = 0;  // outputs of the stored layers 0 .. L - 3
     for (int l = 0; l <= d.L - 3; l++) widest = d.w[l + 1] > widest ? d.w[l + 1] : widest;
-    nd.hp = d.L == 2 ? 0 : widest <= 32 ? 32 : widest <= 64 ? 64 : widest <= 128 ? 128 : -1;
+    nd.hp = d.L == 2 ? 0
+            : widest <= 32 ? 32
+            : widest <= 64 ? 64
+            : widest <= 80 ? 80  // the paper's 75-wide networks
+            : widest <= 128 ? 128
+                            : -1;
     if (nd.hp < 0) return false;
     auto r4 = [](int v) { return (v + 3) / 4 * 4; };
     // a one-hidden-layer network runs with its input width padded to 2, 3, 4, 6 or 8
@@ -635,6 +640,7 @@ nb_status nb_launch_fwd_narrow(const MlpDesc &d, const float *q, int64_t n, TauF
     switch (nd.hp) {
     case 32: return fwd_launch<32>(d, nd, q, n, tau, margin, bits, logits, st, ws, s);
     case 64: return fwd_launch<64>(d, nd, q, n, tau, margin, bits, logits, st, ws, s);
+    case 80: return fwd_launch<80>(d, nd, q, n, tau, margin, bits, logits, st, ws, s);
     default: return fwd_launch<128>(d, nd, q, n, tau, margin, bits, logits, st, ws, s);
     }
 }
