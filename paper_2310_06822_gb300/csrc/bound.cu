@@ -848,8 +848,11 @@ nb_status nb_launch_recheck(const MlpDesc &d, const GammaTab &gt, const float *q
     ff_kernel<0><<<(unsigned)grid, 128, 0, s>>>(d, gt, q, tau, ws.ff_count, ws.ff_idx, bits, st, nullptr, 0, 0,
                                                 nullptr, ws.flag_count, ws.flag_idx);
     NB_CUDA(cudaGetLastError());
-    ff_kernel<1><<<(unsigned)grid, 128, 0, s>>>(d, gt, q, tau, ws.flag_count, ws.flag_idx, bits, st, nullptr, 0, 0,
-                                                nullptr, nullptr, nullptr);
+    // stage 2b sees the few queries stage 2a left (usually none): two CTAs per SM, so that
+    // an empty launch costs one short wave
+    const int64_t grid_b = grid < 2 * (int64_t)num_sms() ? grid : 2 * (int64_t)num_sms();
+    ff_kernel<1><<<(unsigned)grid_b, 128, 0, s>>>(d, gt, q, tau, ws.flag_count, ws.flag_idx, bits, st, nullptr, 0, 0,
+                                                  nullptr, nullptr, nullptr);
     NB_CUDA(cudaGetLastError());
     return NB_OK;
 }
